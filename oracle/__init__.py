@@ -1,0 +1,211 @@
+"""CPU FP64 oracle of the GENGA long-range kick path (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg are the only callers.  Nothing in the product
+package imports this module, and this module imports nothing from it.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64, compensated sums in
+index order).  This file compiles it with the host C compiler and wraps it
+with numpy-friendly functions.  Each function cites the part of the paper
+it follows (see the header of ``oracle.c``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = C.POINTER(C.c_double)
+_i64p = C.POINTER(C.c_int64)
+_i32p = C.POINTER(C.c_int32)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (no fast-math, no FMA contraction)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    cc = os.environ.get("CC", "gcc")
+    base = [cc, "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC", _SRC,
+            "-o", _LIB + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)   # no OpenMP: serial oracle
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        alt = os.environ.get("ORACLE_LIB")      # a mutated build, for the mutation test only
+        if alt:
+            lib = C.CDLL(alt)
+        else:
+            build()
+            lib = C.CDLL(_LIB)
+        i, d = C.c_int, C.c_double
+        sig = {
+            "oracle_threads": ([], i),
+            "oracle_set_threads": ([i], None),
+            "oracle_changeover": ([d, i], d),
+            "oracle_momentum": ([i, _dp, _dp, _dp, _dp, _dp], None),
+            "oracle_rcrit": ([i] + [_dp] * 7 + [d] * 5 + [_dp, _dp], None),
+            "oracle_pair_rcrit": ([i, d, d, d, d, d, d, d, d], d),
+            "oracle_kick_acc": ([i] + [_dp] * 6 + [d, d, d, i, i, i, _i64p] + [_dp] * 4, None),
+            "oracle_kick": ([i] + [_dp] * 7 + [d] * 5 + [i, i, d] + [_dp] * 3, None),
+            "oracle_encounters": ([i] + [_dp] * 6 + [d, d, i, _i32p, C.c_int64, d, _i32p,
+                                                    C.c_int64, _i64p], C.c_int64),
+            "oracle_kepler": ([d, _dp, d, i], i),
+            "oracle_hc_drift": ([i] + [_dp] * 7 + [d, d], None),
+            "oracle_drift": ([i] + [_dp] * 7 + [d, d, d, i], i),
+            "oracle_step": ([i] + [_dp] * 7 + [d] * 5 + [i, i, i, i], i),
+            "oracle_energy": ([i] + [_dp] * 7 + [d, d, _dp], None),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _p(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def threads() -> int:
+    return int(_load().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    _load().oracle_set_threads(int(n))
+
+
+# ------------------------------------------------------------------ Sect. 1
+def changeover(y, form: int = 0):
+    """K(y): the changeover weight (Chambers 1999 form 0, quintic form 1)."""
+    lib = _load()
+    y = np.asarray(y, dtype=np.float64)
+    out = np.array([lib.oracle_changeover(float(v), int(form)) for v in y.ravel()])
+    return out.reshape(y.shape) if y.shape else float(out[0])
+
+
+def momentum(vx, vy, vz, m):
+    P = np.zeros(3)
+    vx, vy, vz, m = map(_f64, (vx, vy, vz, m))
+    _load().oracle_momentum(len(m), _p(vx), _p(vy), _p(vz), _p(m), _p(P))
+    return P
+
+
+def rcrit(x, y, z, vx, vy, vz, m, G, Mstar, dt, n1=3.0, n2=0.4):
+    """Eq. (1): per-body osculating a_i and r_crit,i = max(n1 R_H,i, n2 dt v_i)."""
+    arrs = [_f64(v) for v in (x, y, z, vx, vy, vz, m)]
+    N = len(arrs[-1])
+    a = np.zeros(N)
+    rc = np.zeros(N)
+    _load().oracle_rcrit(N, *map(_p, arrs), G, Mstar, dt, n1, n2, _p(a), _p(rc))
+    return a, rc
+
+
+def pair_rcrit(mode, mi, mj, ai, aj, rci, rcj, n1, Mstar):
+    return float(_load().oracle_pair_rcrit(int(mode), mi, mj, ai, aj, rci, rcj, n1, Mstar))
+
+
+def kick_acc(x, y, z, m, a, rc, G, Mstar, n1=3.0, mode=1, form=0, idx=None, with_abs=False):
+    """Sect. 1 long-range sum a_i = sum_{j!=i} G m_j K (x_j-x_i)/r^3 for i in idx."""
+    arrs = [_f64(v) for v in (x, y, z, m, a, rc)]
+    N = len(arrs[3])
+    idx = np.arange(N, dtype=np.int64) if idx is None else np.ascontiguousarray(idx, np.int64)
+    n = len(idx)
+    ax, ay, az, ab = np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n)
+    _load().oracle_kick_acc(N, *map(_p, arrs), G, Mstar, n1, int(mode), int(form), n,
+                            idx.ctypes.data_as(_i64p), _p(ax), _p(ay), _p(az),
+                            _p(ab) if with_abs else None)
+    acc = np.stack([ax, ay, az])
+    return (acc, ab) if with_abs else acc
+
+
+def kick(disc_arrays, G, Mstar, dt, n1, n2, mode, form, tau):
+    """r_crit from the current state, then v += a tau (in place); returns acc."""
+    x, y, z, vx, vy, vz, m = disc_arrays
+    N = len(m)
+    ax, ay, az = np.zeros(N), np.zeros(N), np.zeros(N)
+    _load().oracle_kick(N, *map(_p, (x, y, z, vx, vy, vz, m)), G, Mstar, dt, n1, n2,
+                        int(mode), int(form), tau, _p(ax), _p(ay), _p(az))
+    return np.stack([ax, ay, az])
+
+
+def encounters(x, y, z, m, a, rc, n1, Mstar, mode=1, band=1e-9, cap=None):
+    """Pairs i<j with r_ij < r_crit,ij (lexicographic) and the +-band pairs."""
+    arrs = [_f64(v) for v in (x, y, z, m, a, rc)]
+    N = len(arrs[3])
+    lib = _load()
+    cap = cap if cap is not None else max(16, 4 * N)
+    bcap = max(16, N)
+    pairs = np.zeros(2 * cap, np.int32)
+    bpairs = np.zeros(2 * bcap, np.int32)
+    bcount = np.zeros(1, np.int64)
+    cnt = lib.oracle_encounters(N, *map(_p, arrs), n1, Mstar, int(mode),
+                                pairs.ctypes.data_as(_i32p), cap, band,
+                                bpairs.ctypes.data_as(_i32p), bcap, bcount.ctypes.data_as(_i64p))
+    if cnt > cap or bcount[0] > bcap:
+        return encounters(x, y, z, m, a, rc, n1, Mstar, mode, band,
+                          cap=int(max(cnt, bcount[0], cap) * 2))
+    return (pairs[: 2 * cnt].reshape(-1, 2).copy(),
+            bpairs[: 2 * int(bcount[0])].reshape(-1, 2).copy())
+
+
+def kepler(mu, xv, dt, max_iter=50):
+    """Universal-variable two-body drift of one body; returns (state, status)."""
+    s = _f64(np.array(xv, dtype=np.float64).copy())
+    st = _load().oracle_kepler(mu, _p(s), dt, int(max_iter))
+    return s, int(st)
+
+
+def hc_drift(arrs, Mstar, tau):
+    x, y, z, vx, vy, vz, m = arrs
+    _load().oracle_hc_drift(len(m), *map(_p, (x, y, z, vx, vy, vz, m)), Mstar, tau)
+
+
+def drift(arrs, G, Mstar, dt, max_iter=50):
+    """HC(dt/2) Kepler(dt) HC(dt/2), in place; returns the non-converged count."""
+    x, y, z, vx, vy, vz, m = arrs
+    return int(_load().oracle_drift(len(m), *map(_p, (x, y, z, vx, vy, vz, m)), G, Mstar, dt,
+                                    int(max_iter)))
+
+
+def step(arrs, G, Mstar, dt, n1, n2, mode, form, nsteps, max_iter=50):
+    """nsteps of kick(dt/2) drift(dt) kick(dt/2), in place."""
+    x, y, z, vx, vy, vz, m = arrs
+    return int(_load().oracle_step(len(m), *map(_p, (x, y, z, vx, vy, vz, m)), G, Mstar, dt,
+                                   n1, n2, int(mode), int(form), int(max_iter), int(nsteps)))
+
+
+def energy(arrs, G, Mstar):
+    """(E, Lx, Ly, Lz) of the democratic-heliocentric Hamiltonian."""
+    x, y, z, vx, vy, vz, m = [_f64(v) for v in arrs]
+    out = np.zeros(4)
+    _load().oracle_energy(len(m), *map(_p, (x, y, z, vx, vy, vz, m)), G, Mstar, _p(out))
+    return out
+
+
+def disc_arrays(disc):
+    """Writable float64 copies of a Disc's seven state arrays."""
+    return [np.array(a, dtype=np.float64, copy=True) for a in disc.arrays()]

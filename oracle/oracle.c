@@ -1,0 +1,390 @@
+/*
+ * oracle.c -- plain, slow, FP64 CPU oracle of the GENGA long-range kick path.
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the tests, the smoke check
+ * and the benchmark's CPU-baseline leg may load this file's library.  It
+ * shares no source, header, table or helper with the CUDA path.
+ *
+ * Paper: Brasser, Grimm, Hatalova & Stadel (2023), "Speeding up the GENGA
+ * N-body integrator on consumer-grade graphics cards".  What it computes:
+ *
+ *   critical radius       Sect. 1, Eq. (1):  r_crit,i = max(n1 R_H,i, n2 dt v_i),
+ *                         R_H,i = a_i (m_i / 3 M*)^(1/3)
+ *   changeover weight K   Sect. 1 (the smooth switch of the hybrid
+ *                         symplectic integrator; Chambers 1999 form)
+ *   long-range kick       Sect. 1 (the N^2 force terms):
+ *                         a_i = sum_{j!=i} G m_j K (x_j - x_i) / |x_j - x_i|^3
+ *   encounter pairs       Sect. 1 (pairs inside the changeover radius)
+ *   Kepler drift          Sect. 1 (always FP64): universal-variable f and g
+ *   energy / ang. mom.    Sect. 3.1: dE/E = E(t)/E0 - 1, dL/L = L(t)/L0 - 1
+ *
+ * Readings where the paper is silent (each one is listed in the design
+ * notes): democratic-heliocentric coordinates (heliocentric x, barycentric
+ * v; Kepler mu = G M*; the central-body momentum drift x += tau P / M*);
+ * the Kepler velocity of Eq. (1) is the heliocentric speed v + P/M*;
+ * a_i is the osculating semi-major axis with mu_i = G (M* + m_i), and
+ * r_i replaces a_i for unbound orbits; the pair radius is
+ * max(r_crit,i, r_crit,j) (mode 0) or n1 ((m_i+m_j)/3M*)^(1/3) (a_i+a_j)/2,
+ * three mutual Hill radii (mode 1); y = (r/r_crit,ij - 0.1)/0.9 with
+ * K(y) = y^2/(2y^2 - 2y + 1) (form 0) or 10y^3 - 15y^4 + 6y^5 (form 1),
+ * K = 0 for y <= 0 and 1 for y >= 1; an encounter is r_ij < r_crit,ij.
+ *
+ * Every sum over bodies is Neumaier-compensated in index order, so the
+ * result does not depend on the number of OpenMP threads.
+ * Build: cc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no fast-math).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------- sums -- */
+
+typedef struct { double s, c; } nsum;   /* Neumaier (1974) running sum */
+
+static void nadd(nsum *a, double v)
+{
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+    else                       a->c += (v - t) + a->s;
+    a->s = t;
+}
+
+static double nval(const nsum *a) { return a->s + a->c; }
+
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* ---------------------------------------------------- changeover (Sect. 1) */
+
+/* K(y): 0 for y <= 0, 1 for y >= 1, smooth in between. */
+double oracle_changeover(double y, int form)
+{
+    if (y <= 0.0) return 0.0;
+    if (y >= 1.0) return 1.0;
+    if (form == 0) {
+        double y2 = y * y;
+        return y2 / (2.0 * y2 - 2.0 * y + 1.0);
+    }
+    return y * y * y * (10.0 - 15.0 * y + 6.0 * y * y);
+}
+
+/* ------------------------------------------------ total momentum P -------- */
+
+/* P = sum_j m_j v_j (barycentric momenta of the non-central bodies). */
+void oracle_momentum(int N, const double *vx, const double *vy, const double *vz,
+                     const double *m, double *P)
+{
+    nsum px = {0, 0}, py = {0, 0}, pz = {0, 0};
+    for (int j = 0; j < N; j++) {
+        nadd(&px, m[j] * vx[j]);
+        nadd(&py, m[j] * vy[j]);
+        nadd(&pz, m[j] * vz[j]);
+    }
+    P[0] = nval(&px); P[1] = nval(&py); P[2] = nval(&pz);
+}
+
+/* ------------------------------------------- critical radius, Eq. (1) ----- */
+
+/*
+ * Per body: the osculating semi-major axis a_i (1/a = 2/r - v_hel^2/mu_i,
+ * mu_i = G (M* + m_i); a_i = r_i when 1/a <= 0) and the Eq. (1) radius
+ * r_crit,i = max(n1 a_i (m_i/3M*)^(1/3), n2 dt |v_hel,i|), v_hel = v + P/M*.
+ */
+void oracle_rcrit(int N, const double *x, const double *y, const double *z,
+                  const double *vx, const double *vy, const double *vz, const double *m,
+                  double G, double Mstar, double dt, double n1, double n2,
+                  double *a_out, double *rc_out)
+{
+    double P[3];
+    oracle_momentum(N, vx, vy, vz, m, P);
+    for (int i = 0; i < N; i++) {
+        double ux = vx[i] + P[0] / Mstar;
+        double uy = vy[i] + P[1] / Mstar;
+        double uz = vz[i] + P[2] / Mstar;
+        double v2 = ux * ux + uy * uy + uz * uz;
+        double r = sqrt(x[i] * x[i] + y[i] * y[i] + z[i] * z[i]);
+        double mu = G * (Mstar + m[i]);
+        double inva = 2.0 / r - v2 / mu;
+        double a = (inva > 0.0) ? 1.0 / inva : r;
+        double RH = a * cbrt(m[i] / (3.0 * Mstar));
+        double t1 = n1 * RH, t2 = n2 * dt * sqrt(v2);
+        a_out[i] = a;
+        rc_out[i] = (t1 > t2) ? t1 : t2;
+    }
+}
+
+/* Pair radius: mode 0 = max of the Eq. (1) radii; mode 1 = n1 mutual Hill radii. */
+double oracle_pair_rcrit(int mode, double mi, double mj, double ai, double aj,
+                         double rci, double rcj, double n1, double Mstar)
+{
+    if (mode == 0) return (rci > rcj) ? rci : rcj;
+    return n1 * cbrt((mi + mj) / (3.0 * Mstar)) * 0.5 * (ai + aj);
+}
+
+/* ---------------------------------------------- long-range kick (Sect. 1) -- */
+
+/*
+ * Accelerations of the bodies listed in idx[0..nidx): the direct sum over
+ * all j != i of G m_j K(y_ij) (x_j - x_i)/r_ij^3.  Optional absout[k] gets
+ * sum_j |a_ij| (the conditioning of body idx[k]'s sum).
+ */
+void oracle_kick_acc(int N, const double *x, const double *y, const double *z,
+                     const double *m, const double *a, const double *rc,
+                     double G, double Mstar, double n1, int mode, int form,
+                     int nidx, const int64_t *idx,
+                     double *ax, double *ay, double *az, double *absout)
+{
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int k = 0; k < nidx; k++) {
+        int i = (int)idx[k];
+        nsum sx = {0, 0}, sy = {0, 0}, sz = {0, 0}, sa = {0, 0};
+        for (int j = 0; j < N; j++) {
+            if (j == i) continue;
+            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 == 0.0) continue;          /* coincident bodies: no direction, no force */
+            double r = sqrt(r2);
+            double rcij = oracle_pair_rcrit(mode, m[i], m[j], a[i], a[j], rc[i], rc[j], n1, Mstar);
+            double K = 1.0;
+            if (r < rcij) K = oracle_changeover((r / rcij - 0.1) / 0.9, form);
+            if (K == 0.0) continue;
+            double f = G * m[j] * K / (r2 * r);
+            nadd(&sx, f * dx);
+            nadd(&sy, f * dy);
+            nadd(&sz, f * dz);
+            nadd(&sa, fabs(f) * r);
+        }
+        ax[k] = nval(&sx); ay[k] = nval(&sy); az[k] = nval(&sz);
+        if (absout) absout[k] = nval(&sa);
+    }
+}
+
+/* Kick: r_crit from the current state, then v_i += a_i tau for all i. */
+void oracle_kick(int N, const double *x, const double *y, const double *z,
+                 double *vx, double *vy, double *vz, const double *m,
+                 double G, double Mstar, double dt, double n1, double n2, int mode, int form,
+                 double tau, double *ax, double *ay, double *az)
+{
+    double *a = (double *)malloc(sizeof(double) * (N > 0 ? N : 1));
+    double *rc = (double *)malloc(sizeof(double) * (N > 0 ? N : 1));
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (N > 0 ? N : 1));
+    oracle_rcrit(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, a, rc);
+    for (int i = 0; i < N; i++) idx[i] = i;
+    oracle_kick_acc(N, x, y, z, m, a, rc, G, Mstar, n1, mode, form, N, idx, ax, ay, az, NULL);
+    for (int i = 0; i < N; i++) {
+        vx[i] += ax[i] * tau;
+        vy[i] += ay[i] * tau;
+        vz[i] += az[i] * tau;
+    }
+    free(a); free(rc); free(idx);
+}
+
+/* ------------------------------------------- encounter pairs (Sect. 1) ---- */
+
+/*
+ * All pairs i < j with r_ij < r_crit,ij, in lexicographic order.  Writes at
+ * most `cap` pairs to pairs[2k], pairs[2k+1]; returns the true count.  Pairs
+ * with |r_ij - r_crit,ij| <= band * r_crit,ij (either side) also go to
+ * band_pairs (at most band_cap; true count in *band_count).
+ */
+int64_t oracle_encounters(int N, const double *x, const double *y, const double *z,
+                          const double *m, const double *a, const double *rc,
+                          double n1, double Mstar, int mode,
+                          int32_t *pairs, int64_t cap, double band,
+                          int32_t *band_pairs, int64_t band_cap, int64_t *band_count)
+{
+    int64_t cnt = 0, bcnt = 0;
+    for (int i = 0; i < N; i++) {
+        for (int j = i + 1; j < N; j++) {
+            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            double rcij = oracle_pair_rcrit(mode, m[i], m[j], a[i], a[j], rc[i], rc[j], n1, Mstar);
+            if (r < rcij) {
+                if (cnt < cap) { pairs[2 * cnt] = i; pairs[2 * cnt + 1] = j; }
+                cnt++;
+            }
+            if (fabs(r - rcij) <= band * rcij) {
+                if (bcnt < band_cap) { band_pairs[2 * bcnt] = i; band_pairs[2 * bcnt + 1] = j; }
+                bcnt++;
+            }
+        }
+    }
+    if (band_count) *band_count = bcnt;
+    return cnt;
+}
+
+/* ------------------------------------------- Kepler drift (Sect. 1) ------- */
+
+/*
+ * Stumpff functions c0..c3 of z by Danby's method (Fundamentals of
+ * Celestial Mechanics, 2nd ed., Sect. 6.9): reduce z by powers of four
+ * until |z| <= 0.1, sum the series of c2 and c3, then undo the reduction
+ * with the quadruple-argument relations.
+ */
+static void stumpff(double z, double *c0, double *c1, double *c2, double *c3)
+{
+    int n = 0;
+    while (fabs(z) > 0.1) { z *= 0.25; n++; }
+    double s3 = (1.0 - z / 20.0 * (1.0 - z / 42.0 * (1.0 - z / 72.0 * (1.0 - z / 110.0 *
+                (1.0 - z / 156.0 * (1.0 - z / 210.0)))))) / 6.0;
+    double s2 = (1.0 - z / 12.0 * (1.0 - z / 30.0 * (1.0 - z / 56.0 * (1.0 - z / 90.0 *
+                (1.0 - z / 132.0 * (1.0 - z / 182.0)))))) / 2.0;
+    double s1 = 1.0 - z * s3;
+    double s0 = 1.0 - z * s2;
+    for (; n > 0; n--) {
+        s3 = (s2 + s0 * s3) * 0.25;
+        s2 = s1 * s1 * 0.5;
+        s1 = s1 * s0;
+        s0 = 2.0 * s0 * s0 - 1.0;
+    }
+    *c0 = s0; *c1 = s1; *c2 = s2; *c3 = s3;
+}
+
+/*
+ * Two-body drift of one body about mu for time dt, universal variables.
+ * Kepler's equation in the universal anomaly s,
+ *   F(s) = r0 G1 + eta0 G2 + mu G3 - dt = 0,   G_k = s^k c_k(beta s^2),
+ * beta = 2 mu / r0 - v0^2, eta0 = x0.v0, is solved by the Laguerre-Conway
+ * iteration (n = 5) from s = dt / r0; then the f and g functions give
+ *   x = f x0 + g v0,  v = fdot x0 + gdot v0.
+ * The iteration converges cubically, so a step |ds| <= 1e-12 |s| leaves the
+ * new iterate at rounding level.  Returns 0 when that happens within
+ * max_iter steps, else 1 (the state is still advanced with the last iterate).
+ */
+int oracle_kepler(double mu, double *xv, double dt, int max_iter)
+{
+    double x0 = xv[0], y0 = xv[1], z0 = xv[2], u0 = xv[3], v0 = xv[4], w0 = xv[5];
+    double r0 = sqrt(x0 * x0 + y0 * y0 + z0 * z0);
+    double vv = u0 * u0 + v0 * v0 + w0 * w0;
+    double eta = x0 * u0 + y0 * v0 + z0 * w0;
+    double beta = 2.0 * mu / r0 - vv;
+    double s = dt / r0;
+    double c0, c1, c2, c3;
+    int status = 1;
+    for (int it = 0; it < max_iter; it++) {
+        stumpff(beta * s * s, &c0, &c1, &c2, &c3);
+        double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
+        double F = r0 * G1 + eta * G2 + mu * G3 - dt;
+        double Fp = r0 * c0 + eta * G1 + mu * G2;
+        double Fpp = eta * c0 + (mu - beta * r0) * G1;
+        double disc = 16.0 * Fp * Fp - 20.0 * F * Fpp;
+        double den = Fp + copysign(sqrt(fabs(disc)), Fp);
+        double ds = -5.0 * F / den;
+        s += ds;
+        if (fabs(ds) <= 1e-12 * fabs(s)) { status = 0; break; }
+    }
+    stumpff(beta * s * s, &c0, &c1, &c2, &c3);
+    double G1 = s * c1, G2 = s * s * c2;
+    double r = r0 * c0 + eta * G1 + mu * G2;
+    double f = 1.0 - mu * G2 / r0;
+    double g = r0 * G1 + eta * G2;
+    double fd = -mu * G1 / (r * r0);
+    double gd = 1.0 - mu * G2 / r;
+    xv[0] = f * x0 + g * u0;  xv[1] = f * y0 + g * v0;  xv[2] = f * z0 + g * w0;
+    xv[3] = fd * x0 + gd * u0; xv[4] = fd * y0 + gd * v0; xv[5] = fd * z0 + gd * w0;
+    return status;
+}
+
+/* Central-body momentum drift: x_i += tau P / M*, P = sum_j m_j v_j. */
+void oracle_hc_drift(int N, double *x, double *y, double *z,
+                     const double *vx, const double *vy, const double *vz, const double *m,
+                     double Mstar, double tau)
+{
+    double P[3];
+    oracle_momentum(N, vx, vy, vz, m, P);
+    for (int i = 0; i < N; i++) {
+        x[i] += tau * P[0] / Mstar;
+        y[i] += tau * P[1] / Mstar;
+        z[i] += tau * P[2] / Mstar;
+    }
+}
+
+/* Drift of the step: HC(dt/2), Kepler(dt) with mu = G M*, HC(dt/2).
+ * Returns the number of bodies whose Kepler solve did not converge. */
+int oracle_drift(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                 const double *m, double G, double Mstar, double dt, int max_iter)
+{
+    int bad = 0;
+    oracle_hc_drift(N, x, y, z, vx, vy, vz, m, Mstar, 0.5 * dt);
+    #pragma omp parallel for reduction(+:bad)
+    for (int i = 0; i < N; i++) {
+        double s[6] = {x[i], y[i], z[i], vx[i], vy[i], vz[i]};
+        bad += oracle_kepler(G * Mstar, s, dt, max_iter);
+        x[i] = s[0]; y[i] = s[1]; z[i] = s[2];
+        vx[i] = s[3]; vy[i] = s[4]; vz[i] = s[5];
+    }
+    oracle_hc_drift(N, x, y, z, vx, vy, vz, m, Mstar, 0.5 * dt);
+    return bad;
+}
+
+/* Level-0 step, kick(dt/2) drift(dt) kick(dt/2), repeated nsteps times.
+ * Returns the total count of non-converged Kepler solves. */
+int oracle_step(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                const double *m, double G, double Mstar, double dt, double n1, double n2,
+                int mode, int form, int max_iter, int nsteps)
+{
+    int bad = 0;
+    size_t n = (size_t)(N > 0 ? N : 1);
+    double *ax = (double *)malloc(sizeof(double) * n);
+    double *ay = (double *)malloc(sizeof(double) * n);
+    double *az = (double *)malloc(sizeof(double) * n);
+    for (int s = 0; s < nsteps; s++) {
+        oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, 0.5 * dt, ax, ay, az);
+        bad += oracle_drift(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, max_iter);
+        oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, 0.5 * dt, ax, ay, az);
+    }
+    free(ax); free(ay); free(az);
+    return bad;
+}
+
+/* ------------------------------------- energy and angular momentum -------- */
+
+/*
+ * out[0] = E = sum m v^2/2 + |P|^2/(2 M*) - sum G M* m_i / r_i
+ *              - sum_{i<j} G m_i m_j / r_ij     (democratic-heliocentric H)
+ * out[1..3] = L = sum m_i x_i x v_i.
+ */
+void oracle_energy(int N, const double *x, const double *y, const double *z,
+                   const double *vx, const double *vy, const double *vz, const double *m,
+                   double G, double Mstar, double *out)
+{
+    nsum e = {0, 0}, lx = {0, 0}, ly = {0, 0}, lz = {0, 0};
+    double P[3];
+    oracle_momentum(N, vx, vy, vz, m, P);
+    nadd(&e, (P[0] * P[0] + P[1] * P[1] + P[2] * P[2]) / (2.0 * Mstar));
+    for (int i = 0; i < N; i++) {
+        double r = sqrt(x[i] * x[i] + y[i] * y[i] + z[i] * z[i]);
+        nadd(&e, 0.5 * m[i] * (vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i]));
+        nadd(&e, -G * Mstar * m[i] / r);
+        nadd(&lx, m[i] * (y[i] * vz[i] - z[i] * vy[i]));
+        nadd(&ly, m[i] * (z[i] * vx[i] - x[i] * vz[i]));
+        nadd(&lz, m[i] * (x[i] * vy[i] - y[i] * vx[i]));
+    }
+    for (int i = 0; i < N; i++) {
+        for (int j = i + 1; j < N; j++) {
+            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
+            nadd(&e, -G * m[i] * m[j] / sqrt(dx * dx + dy * dy + dz * dz));
+        }
+    }
+    out[0] = nval(&e);
+    out[1] = nval(&lx); out[2] = nval(&ly); out[3] = nval(&lz);
+}

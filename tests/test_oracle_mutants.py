@@ -1,0 +1,85 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a copy of oracle.c (on the CPU, in a
+temporary directory), builds it, and runs the pin suite against that build
+in a child process: the suite has to fail.  The unmodified build has to
+pass.  This checks the pins themselves, not the CUDA path.
+"""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTANTS = {
+    "changeover_denominator_sign": ("2.0 * y2 - 2.0 * y + 1.0", "2.0 * y2 - 2.0 * y - 1.0"),
+    "quintic_coefficient": ("(10.0 - 15.0 * y + 6.0 * y * y)", "(10.0 - 15.0 * y + 5.0 * y * y)"),
+    "sun_velocity_sign": ("double ux = vx[i] + P[0] / Mstar;", "double ux = vx[i] - P[0] / Mstar;"),
+    "rcrit_mu_without_mi": ("double mu = G * (Mstar + m[i]);", "double mu = G * Mstar;"),
+    "hill_radius_exponent": ("a * cbrt(m[i] / (3.0 * Mstar))", "a * sqrt(m[i] / (3.0 * Mstar))"),
+    "velocity_term_dropped_dt": ("t2 = n2 * dt * sqrt(v2)", "t2 = n2 * sqrt(v2)"),
+    "pair_radius_index": ("0.5 * (ai + aj)", "0.5 * (ai + ai)"),
+    "pair_radius_mode0_min": ("return (rci > rcj) ? rci : rcj;", "return (rci < rcj) ? rci : rcj;"),
+    "kick_offset_sign": ("double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];\n            double r2",
+                         "double dx = x[i] - x[j], dy = y[j] - y[i], dz = z[j] - z[i];\n            double r2"),
+    "kick_changeover_argument": ("K = oracle_changeover((r / rcij - 0.1) / 0.9, form);",
+                                 "K = oracle_changeover(r / rcij, form);"),
+    "kick_mass_index": ("double f = G * m[j] * K / (r2 * r);", "double f = G * m[i] * K / (r2 * r);"),
+    "kick_inverse_square": ("double f = G * m[j] * K / (r2 * r);", "double f = G * m[j] * K / r2;"),
+    "kick_missing_changeover": ("double f = G * m[j] * K / (r2 * r);", "double f = G * m[j] / (r2 * r);"),
+    "encounter_squared_distance": ("            if (r < rcij) {\n                if (cnt < cap)",
+                                   "            if (r * r < rcij) {\n                if (cnt < cap)"),
+    "sun_velocity_sign_y": ("double uy = vy[i] + P[1] / Mstar;", "double uy = vy[i] - P[1] / Mstar;"),
+    "stumpff_doubling": ("s3 = (s2 + s0 * s3) * 0.25;", "s3 = (s2 + s1 * s3) * 0.25;"),
+    "stumpff_series": ("(1.0 - z / 20.0 * (1.0 - z / 42.0", "(1.0 - z / 20.0 * (1.0 - z / 40.0"),
+    "kepler_g_sign": ("double g = r0 * G1 + eta * G2;", "double g = r0 * G1 - eta * G2;"),
+    "kepler_fdot": ("double fd = -mu * G1 / (r * r0);", "double fd = -mu * G1 / (r0 * r0);"),
+    "hc_drift_no_mass_division": ("x[i] += tau * P[0] / Mstar;", "x[i] += tau * P[0];"),
+    "drift_full_hc_halves": ("oracle_hc_drift(N, x, y, z, vx, vy, vz, m, Mstar, 0.5 * dt);\n    #pragma",
+                             "oracle_hc_drift(N, x, y, z, vx, vy, vz, m, Mstar, dt);\n    #pragma"),
+    "step_full_kick": ("mode, form, 0.5 * dt, ax, ay, az);\n        bad +=",
+                       "mode, form, dt, ax, ay, az);\n        bad +="),
+    "energy_sun_term": ("/ (2.0 * Mstar));", "/ (2.0));"),
+    "energy_pair_term_mass": ("nadd(&e, -G * m[i] * m[j] / sqrt", "nadd(&e, -G * m[i] * m[i] / sqrt"),
+    "angular_momentum_component": ("nadd(&lz, m[i] * (x[i] * vy[i] - y[i] * vx[i]));",
+                                   "nadd(&lz, m[i] * (x[i] * vy[i] + y[i] * vx[i]));"),
+}
+
+
+def _build(src_text, d):
+    c = os.path.join(d, "m.c")
+    so = os.path.join(d, "m.so")
+    with open(c, "w") as f:
+        f.write(src_text)
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-shared", "-fPIC", c, "-o", so, "-lm"],
+                   check=True, capture_output=True)
+    return so
+
+
+def _run_pins(so):
+    env = dict(os.environ, ORACLE_LIB=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name):
+    old, new = MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site for {name} not unique / not found"
+    with tempfile.TemporaryDirectory() as d:
+        so = _build(text.replace(old, new), d)
+        assert _run_pins(so) != 0, f"pins did not catch mutant {name}"
+
+
+def test_unmutated_build_passes_pins():
+    with tempfile.TemporaryDirectory() as d:
+        so = _build(open(SRC).read(), d)
+        assert _run_pins(so) == 0

@@ -1,0 +1,473 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these calls the CUDA path.  Each check targets a different part of
+the oracle so that a dropped term, a wrong sign or index, or a transposed
+operand fails at least one of them:
+
+* changeover K (Sect. 1, Chambers 1999 form): hand values, endpoints,
+  symmetry K(y) + K(1-y) = 1, flat ends, monotonicity;
+* critical radius, Eq. (1): circular-orbit values worked by hand, both
+  terms of the max, the unbound fallback, the mutual-Hill pair radius;
+* long-range kick (Sect. 1): two-body closed form and sign, the ring
+  closed form, K = 0 / K = 1/2 / K = 1 points of the changeover region,
+  Newton's third law, 40-digit brute force on a small disc;
+* encounter pairs: exhaustive enumeration and planted pairs just inside and
+  outside r_crit;
+* Kepler drift (always FP64, Sect. 1): Kepler's equation solved by 40-digit
+  bisection for elliptic, hyperbolic and parabolic orbits, time reversal,
+  two-body invariants, the iteration-cap status;
+* central-body drift: the momentum shift and dL = 0;
+* energy and angular momentum (Sect. 3.1): circular two-body closed form;
+* the step: bounded energy error that scales as dt^2, dL/L at round-off.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_08217_gb300 import discs
+
+mpmath = pytest.importorskip("mpmath")
+mp = mpmath.mp
+
+
+# ----------------------------------------------------------------- K(y) ---
+@pytest.mark.parametrize("form", [0, 1])
+def test_changeover_endpoints_symmetry_flat_ends(form):
+    K = lambda y: oracle.changeover(y, form)
+    assert K(-0.3) == 0.0 and K(0.0) == 0.0
+    assert K(1.0) == 1.0 and K(1.7) == 1.0
+    ys = np.linspace(0.0, 1.0, 201)
+    vals = oracle.changeover(ys, form)
+    assert np.all(np.diff(vals) >= 0.0)                       # monotone
+    assert np.allclose(vals + oracle.changeover(1.0 - ys, form), 1.0, atol=4e-15, rtol=0)
+    h = 1e-4                                                  # K'(0) = K'(1) = 0
+    assert K(h) / h < 1e-3 and (1.0 - K(1.0 - h)) / h < 1e-3
+    # interior slope is finite and positive (smooth, not a step)
+    assert 0.5 < (K(0.5 + h) - K(0.5 - h)) / (2 * h) < 3.0
+
+
+def test_changeover_hand_values():
+    # Chambers form y^2/(2y^2-2y+1): y=1/4 -> (1/16)/(1/8-1/2+1) = (1/16)/(5/8) = 1/10
+    assert oracle.changeover(0.25, 0) == pytest.approx(0.1, abs=1e-16)
+    assert oracle.changeover(0.5, 0) == 0.5
+    # y=3/4 -> (9/16)/(9/8-3/2+1) = (9/16)/(5/8) = 9/10
+    assert oracle.changeover(0.75, 0) == pytest.approx(0.9, abs=1e-16)
+    # quintic 10y^3-15y^4+6y^5 at y=1/4: 10/64 - 15/256 + 6/1024 = 106/1024
+    assert oracle.changeover(0.25, 1) == pytest.approx(106 / 1024, abs=1e-16)
+    assert oracle.changeover(0.5, 1) == 0.5
+
+
+# ------------------------------------------------------------ Eq. (1) -----
+def _one_body_circular(a, m, G=1.0, M=1.0, phi=0.7, inc=0.4):
+    """Body on a circular heliocentric orbit tilted by inc, DH coordinates."""
+    vh = math.sqrt(G * (M + m) / a)
+    vb = vh * M / (M + m)               # barycentric = heliocentric - Sun's velocity
+    ci, si, cp, sp = math.cos(inc), math.sin(inc), math.cos(phi), math.sin(phi)
+    arr = [np.array([a * cp]), np.array([a * sp * ci]), np.array([a * sp * si]),
+           np.array([-vb * sp]), np.array([vb * cp * ci]), np.array([vb * cp * si]),
+           np.array([m])]
+    return arr, vh
+
+
+def test_rcrit_circular_hill_term():
+    # G=1, M=1.5, m=4.5e-3: (m/3M)^(1/3) = 0.1; a=2 -> R_H = 0.2 and n1 R_H = 0.6
+    arr, vh = _one_body_circular(2.0, 4.5e-3, M=1.5)
+    a, rc = oracle.rcrit(*arr, G=1.0, Mstar=1.5, dt=1.0, n1=3.0, n2=0.4)
+    assert a[0] == pytest.approx(2.0, rel=1e-14)             # osculating a of a circle
+    assert rc[0] == pytest.approx(0.6, rel=1e-14)            # n2 dt v = 0.35 < 0.6
+
+
+def test_rcrit_circular_velocity_term():
+    arr, vh = _one_body_circular(2.0, 4.5e-3, M=1.5)
+    a, rc = oracle.rcrit(*arr, G=1.0, Mstar=1.5, dt=3.0, n1=3.0, n2=0.4)
+    # n2 dt v_hel = 0.4 * 3 * sqrt(1.5045/2) = 1.041 > 0.6: the Kepler velocity term wins
+    assert rc[0] == pytest.approx(1.2 * math.sqrt(1.5045 / 2.0), rel=1e-14)
+
+
+def test_rcrit_unbound_uses_distance():
+    arr, vh = _one_body_circular(2.0, 1e-6)
+    arr[4] = arr[4] * 2.0                                       # v > escape speed
+    a, rc = oracle.rcrit(*arr, G=1.0, Mstar=1.0, dt=1e-9, n1=3.0, n2=0.4)
+    assert a[0] == 2.0
+    assert rc[0] == pytest.approx(3.0 * 2.0 * (1e-6 / 3.0) ** (1 / 3), rel=1e-14)
+
+
+def test_pair_rcrit_modes():
+    # mode 0: the larger of the two Eq. (1) radii
+    assert oracle.pair_rcrit(0, 1e-9, 1e-3, 1, 5, 0.01, 0.3, 3.0, 1.0) == 0.3
+    # mode 1: three mutual Hill radii, (m_i+m_j)/3M = 1e-3 -> cube root 0.1, a_mean 1.5
+    assert oracle.pair_rcrit(1, 1e-3, 2e-3, 1.0, 2.0, 0, 0, 3.0, 1.0) == pytest.approx(
+        0.45, rel=1e-15)
+    # M = 2: (m_i+m_j)/3M = 1e-3 again with the masses doubled; n1 = 2
+    assert oracle.pair_rcrit(1, 2e-3, 4e-3, 1.0, 3.0, 0, 0, 2.0, 2.0) == pytest.approx(
+        0.4, rel=1e-15)
+
+
+# ----------------------------------------------------------- the kick -----
+def _kick(arr, G=1.0, M=1.0, dt=1.0, n1=3.0, n2=0.4, mode=1, form=0, with_abs=False):
+    a, rc = oracle.rcrit(*arr, G=G, Mstar=M, dt=dt, n1=n1, n2=n2)
+    return oracle.kick_acc(arr[0], arr[1], arr[2], arr[6], a, rc, G, M, n1, mode, form,
+                           with_abs=with_abs)
+
+
+def _static(pos, m):
+    pos = np.asarray(pos, float)
+    z = np.zeros(len(m))
+    return [pos[:, 0].copy(), pos[:, 1].copy(), pos[:, 2].copy(), z, z.copy(), z.copy(),
+            np.asarray(m, float)]
+
+
+def test_two_body_closed_form_and_sign():
+    arr = _static([[1.0, 0.0, 0.0], [1.0, 0.5, 0.0]], [1e-12, 4e-12])
+    acc = _kick(arr, G=2.0)
+    # a_0 = G m_1 / r^2 towards body 1 (+y); a_1 = G m_0 / r^2 towards body 0 (-y)
+    assert acc[1, 0] == pytest.approx(2.0 * 4e-12 / 0.25, rel=1e-15)
+    assert acc[1, 1] == pytest.approx(-2.0 * 1e-12 / 0.25, rel=1e-15)
+    assert acc[0, 0] == 0.0 and acc[2, 0] == 0.0
+
+
+@pytest.mark.parametrize("N", [3, 7, 16, 64])
+def test_ring_closed_form(N):
+    R, m, G = 1.3, 1e-13, 1.7
+    th = 2 * np.pi * np.arange(N) / N
+    arr = _static(np.stack([R * np.cos(th), R * np.sin(th), np.zeros(N)], 1), np.full(N, m))
+    acc = _kick(arr, G=G)
+    inward = (G * m / (4 * R * R)) * sum(1.0 / math.sin(math.pi * k / N) for k in range(1, N))
+    rad = -(acc[0] * np.cos(th) + acc[1] * np.sin(th))
+    tan = -acc[0] * np.sin(th) + acc[1] * np.cos(th)
+    assert np.allclose(rad, inward, rtol=1e-13, atol=0)
+    assert np.all(np.abs(tan) < 1e-13 * inward)
+    assert np.all(acc[2] == 0.0)
+
+
+def _pair_at_fraction(frac, form=0, mode=1):
+    """Two bodies at the same heliocentric distance, frac * r_crit,ij apart.
+
+    Both sit at r = 1 with v = 0, so a_osc = r/2 for both whatever their
+    separation, and r_crit,ij does not move when the pair is placed.
+    """
+    m = 3e-6
+
+    def place(sep):
+        ph = math.asin(sep / 2.0)
+        return _static([[math.cos(ph), math.sin(ph), 0.0], [math.cos(ph), -math.sin(ph), 0.0]],
+                       [m, m])
+
+    arr = place(1e-3)
+    a_osc, rcb = oracle.rcrit(*arr, G=1.0, Mstar=1.0, dt=1.0, n1=3.0, n2=0.4)
+    rcij = oracle.pair_rcrit(mode, m, m, a_osc[0], a_osc[1], rcb[0], rcb[1], 3.0, 1.0)
+    arr = place(frac * rcij)
+    sep = arr[1][0] - arr[1][1]
+    acc = _kick(arr, mode=mode, form=form)
+    newt = 1.0 * m / sep ** 2
+    return -acc[1, 0] / newt
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_changeover_region_in_kick(form):
+    # r >= r_crit: K = 1, plain Newtonian term
+    assert _pair_at_fraction(1.2, form) == pytest.approx(1.0, rel=1e-12)
+    # r = 0.55 r_crit: y = (0.55 - 0.1)/0.9 = 1/2 and K = 1/2 for both forms
+    assert _pair_at_fraction(0.55, form) == pytest.approx(0.5, rel=1e-9)
+    # r < 0.1 r_crit: K = 0, no long-range force
+    assert _pair_at_fraction(0.05, form) == 0.0
+
+
+def _planted_disc(N=40, seed=11):
+    d = discs.disc_uniform(N, seed, a_min=0.9, a_max=1.1, m_total=N * 2e-7)
+    arr = oracle.disc_arrays(d)
+    # plant close pairs: (1,0) at 0.3 rcrit-ish, (3,2) at 0.02 (K=0), (5,4) at 0.8
+    for (i, j, s) in [(1, 0, 3e-3), (3, 2, 1e-4), (5, 4, 9e-3)]:
+        arr[0][i] = arr[0][j] + s
+        arr[1][i] = arr[1][j]
+        arr[2][i] = arr[2][j] + 0.3 * s
+    return d, arr
+
+
+def test_newton_third_law_with_changeover_pairs():
+    d, arr = _planted_disc()
+    acc, absum = _kick(arr, G=d.G, dt=d.dt, with_abs=True)
+    m = arr[6]
+    tot = (acc * m).sum(axis=1)
+    scale = (np.abs(acc) * m).sum()
+    assert np.all(np.abs(tot) <= 1e-14 * scale)
+    assert np.all(absum >= np.sqrt((acc ** 2).sum(0)) * (1 - 1e-15))
+
+
+def test_kick_matches_40_digit_brute_force():
+    d, arr = _planted_disc()
+    G, M, n1 = d.G, 1.0, 3.0
+    a, rc = oracle.rcrit(*arr, G=G, Mstar=M, dt=d.dt, n1=n1, n2=0.4)
+    got = oracle.kick_acc(arr[0], arr[1], arr[2], arr[6], a, rc, G, M, n1, 1, 0)
+    mp.dps = 40
+    N = len(arr[6])
+    X = [[mpmath.mpf(float(arr[c][i])) for c in range(3)] for i in range(N)]
+    mm = [mpmath.mpf(float(v)) for v in arr[6]]
+    aa = [mpmath.mpf(float(v)) for v in a]
+    ref = np.zeros((3, N))
+    n_changeover = 0
+    for i in range(N):
+        s = [mpmath.mpf(0)] * 3
+        for j in range(N):
+            if j == i:
+                continue
+            d3 = [X[j][c] - X[i][c] for c in range(3)]
+            r = mpmath.sqrt(sum(v * v for v in d3))
+            rcij = n1 * mpmath.cbrt((mm[i] + mm[j]) / (3 * M)) * (aa[i] + aa[j]) / 2
+            K = mpmath.mpf(1)
+            if r < rcij:
+                n_changeover += 1
+                y = (r / rcij - mpmath.mpf("0.1")) / mpmath.mpf("0.9")
+                K = 0 if y <= 0 else (1 if y >= 1 else y * y / (2 * y * y - 2 * y + 1))
+            f = G * mm[j] * K / r ** 3
+            for c in range(3):
+                s[c] += f * d3[c]
+        ref[:, i] = [float(v) for v in s]
+    assert n_changeover >= 4                        # the planted pairs, seen from both sides
+    err = np.sqrt(((got - ref) ** 2).sum(0)) / np.sqrt((ref ** 2).sum(0))
+    assert err.max() < 1e-14
+
+
+# ---------------------------------------------------------- encounters ----
+def test_encounters_exhaustive_and_planted():
+    d, arr = _planted_disc(N=300, seed=12)
+    a, rc = oracle.rcrit(*arr, G=d.G, Mstar=1.0, dt=d.dt, n1=3.0, n2=0.4)
+    for mode in (0, 1):
+        got, band = oracle.encounters(arr[0], arr[1], arr[2], arr[6], a, rc, 3.0, 1.0, mode)
+        P = np.stack(arr[:3], 1)
+        D = np.sqrt(((P[:, None, :] - P[None, :, :]) ** 2).sum(-1))
+        if mode == 0:
+            RC = np.maximum(rc[:, None], rc[None, :])
+        else:
+            m = arr[6]
+            RC = 3.0 * np.cbrt((m[:, None] + m[None, :]) / 3.0) * 0.5 * (a[:, None] + a[None, :])
+        iu = np.triu_indices(len(a), 1)
+        want = np.stack(iu, 1)[(D < RC)[iu]]
+        assert np.array_equal(got, want)            # same set, lexicographic order
+        if mode == 1:
+            assert {(0, 1), (2, 3), (4, 5)} <= set(map(tuple, got.tolist()))
+
+
+def test_encounter_boundary_planted():
+    # both bodies at r = 1, v = 0: a_osc = 1/2 for both, so r_crit,ij is fixed
+    m = 3e-6
+
+    def place(sep):
+        ph = math.asin(sep / 2.0)
+        return _static([[math.cos(ph), math.sin(ph), 0.0], [math.cos(ph), -math.sin(ph), 0.0]],
+                       [m, m])
+
+    base = place(1e-3)
+    a, rc = oracle.rcrit(*base, G=1.0, Mstar=1.0, dt=1.0, n1=3.0, n2=0.4)
+    rcij = oracle.pair_rcrit(1, m, m, a[0], a[1], rc[0], rc[1], 3.0, 1.0)
+    for frac, inside in [(0.5, True), (0.999999, True), (1.000001, False)]:
+        arr = place(frac * rcij)
+        a2, rc2 = oracle.rcrit(*arr, G=1.0, Mstar=1.0, dt=1.0, n1=3.0, n2=0.4)
+        assert np.allclose(a2, a, rtol=1e-14)
+        got, band = oracle.encounters(arr[0], arr[1], arr[2], arr[6], a2, rc2, 3.0, 1.0, 1)
+        assert (len(got) == 1) == inside
+        assert len(band) == 0
+        got, band = oracle.encounters(arr[0], arr[1], arr[2], arr[6], a2, rc2, 3.0, 1.0, 1,
+                                      band=2e-6)
+        assert len(band) == (0 if frac == 0.5 else 1)
+
+
+# ------------------------------------------------------- Kepler drift -----
+def _mp_state_elliptic(mu, a, e, M):
+    E_lo, E_hi = mpmath.mpf(M) - 2, mpmath.mpf(M) + 2
+    f = lambda E: E - e * mpmath.sin(E) - M
+    for _ in range(200):
+        mid = (E_lo + E_hi) / 2
+        if f(mid) > 0:
+            E_hi = mid
+        else:
+            E_lo = mid
+    E = (E_lo + E_hi) / 2
+    n = mpmath.sqrt(mu / a ** 3)
+    b = a * mpmath.sqrt(1 - e * e)
+    rdot = n / (1 - e * mpmath.cos(E))
+    return [a * (mpmath.cos(E) - e), b * mpmath.sin(E), 0,
+            -a * mpmath.sin(E) * rdot, b * mpmath.cos(E) * rdot, 0]
+
+
+def _mp_state_hyperbolic(mu, a, e, M):
+    F_lo, F_hi = mpmath.mpf(-20), mpmath.mpf(20)
+    f = lambda F: e * mpmath.sinh(F) - F - M
+    for _ in range(200):
+        mid = (F_lo + F_hi) / 2
+        if f(mid) > 0:
+            F_hi = mid
+        else:
+            F_lo = mid
+    F = (F_lo + F_hi) / 2
+    n = mpmath.sqrt(mu / a ** 3)
+    b = a * mpmath.sqrt(e * e - 1)
+    Fdot = n / (e * mpmath.cosh(F) - 1)
+    return [a * (e - mpmath.cosh(F)), b * mpmath.sinh(F), 0,
+            -a * mpmath.sinh(F) * Fdot, b * mpmath.cosh(F) * Fdot, 0]
+
+
+def _mp_state_parabolic(mu, q, t):
+    k = mpmath.sqrt(2 * q ** 3 / mu)
+    lo, hi = mpmath.mpf(-100), mpmath.mpf(100)
+    f = lambda D: k * (D + D ** 3 / 3) - t
+    for _ in range(200):
+        mid = (lo + hi) / 2
+        if f(mid) > 0:
+            hi = mid
+        else:
+            lo = mid
+    D = (lo + hi) / 2
+    Ddot = 1 / (k * (1 + D * D))
+    return [q * (1 - D * D), 2 * q * D, 0, -2 * q * D * Ddot, 2 * q * Ddot, 0]
+
+
+def _rotate(s, inc=0.3, Om=1.1, om=0.4):
+    """Same rotation applied to a position/velocity pair (pure geometry)."""
+    R = np.array(mpmath.matrix([[math.cos(Om), -math.sin(Om), 0], [math.sin(Om), math.cos(Om), 0],
+                                [0, 0, 1]]).tolist(), dtype=float)
+    Ri = np.array([[1, 0, 0], [0, math.cos(inc), -math.sin(inc)], [0, math.sin(inc), math.cos(inc)]])
+    Rw = np.array([[math.cos(om), -math.sin(om), 0], [math.sin(om), math.cos(om), 0], [0, 0, 1]])
+    T = R @ Ri @ Rw
+    v = np.array([float(c) for c in s])
+    return np.concatenate([T @ v[:3], T @ v[3:]])
+
+
+@pytest.mark.parametrize("e,M0,dt,tol", [(0.0, 0.3, 17.0, 1e-13), (0.1, 1.0, 40.0, 1e-13),
+                                         (0.9, 2.5, 30.0, 1e-12), (0.99, 3.0, 25.0, 1e-10)])
+def test_kepler_elliptic_vs_bisection(e, M0, dt, tol):
+    mp.dps = 40
+    mu, a = 2.959122082855911e-4, 1.7
+    n = math.sqrt(mu / a ** 3)
+    s0 = _rotate(_mp_state_elliptic(mpmath.mpf(mu), mpmath.mpf(a), mpmath.mpf(e), mpmath.mpf(M0)))
+    s1 = _rotate(_mp_state_elliptic(mpmath.mpf(mu), mpmath.mpf(a), mpmath.mpf(e),
+                                    mpmath.mpf(M0) + mpmath.mpf(n) * dt))
+    got, st = oracle.kepler(mu, s0, dt)
+    assert st == 0
+    assert np.abs(got[:3] - s1[:3]).max() <= tol * np.abs(s1[:3]).max()
+    assert np.abs(got[3:] - s1[3:]).max() <= tol * np.abs(s1[3:]).max()
+
+
+def test_kepler_hyperbolic_vs_bisection():
+    mp.dps = 40
+    mu, a, e = 1.0, 2.0, 1.5
+    n = math.sqrt(mu / a ** 3)
+    s0 = _rotate(_mp_state_hyperbolic(mpmath.mpf(mu), mpmath.mpf(a), mpmath.mpf(e), mpmath.mpf(-0.7)))
+    s1 = _rotate(_mp_state_hyperbolic(mpmath.mpf(mu), mpmath.mpf(a), mpmath.mpf(e),
+                                      mpmath.mpf(-0.7) + mpmath.mpf(n) * 3.0))
+    got, st = oracle.kepler(mu, s0, 3.0)
+    assert st == 0
+    assert np.abs(got - s1).max() <= 1e-12 * np.abs(s1).max()
+
+
+def test_kepler_parabolic_vs_barker():
+    mp.dps = 40
+    mu, q = 1.0, 0.8
+    s0 = _rotate(_mp_state_parabolic(mpmath.mpf(mu), mpmath.mpf(q), mpmath.mpf(-1.5)))
+    s1 = _rotate(_mp_state_parabolic(mpmath.mpf(mu), mpmath.mpf(q), mpmath.mpf(-1.5 + 2.2)))
+    got, st = oracle.kepler(mu, s0, 2.2)
+    assert st == 0
+    assert np.abs(got - s1).max() <= 1e-12 * np.abs(s1).max()
+
+
+def test_kepler_time_reversal_and_invariants():
+    rng = np.random.default_rng(7)
+    mu = 2.959122082855911e-4
+    for _ in range(20):
+        a = rng.uniform(0.5, 30)
+        e = rng.uniform(0, 0.95)
+        pos, vel = discs.elements_to_cartesian(mu, np.array([a]), np.array([e]),
+                                               np.array([rng.uniform(0, 1)]), np.array([1.0]),
+                                               np.array([2.0]), np.array([rng.uniform(0, 6)]))
+        s0 = np.concatenate([pos[:, 0], vel[:, 0]])
+        dt = rng.uniform(1, 400)
+        s1, st = oracle.kepler(mu, s0, dt)
+        s2, st2 = oracle.kepler(mu, s1, -dt)
+        assert st == 0 and st2 == 0
+        assert np.abs(s2[:3] - s0[:3]).max() <= 1e-13 * np.abs(s0[:3]).max()
+        en = lambda s: 0.5 * s[3:] @ s[3:] - mu / np.linalg.norm(s[:3])
+        h = lambda s: np.cross(s[:3], s[3:])
+        assert abs(en(s1) / en(s0) - 1) < 1e-13
+        assert np.abs(h(s1) - h(s0)).max() < 1e-13 * np.linalg.norm(h(s0))
+
+
+def test_kepler_iteration_cap_status():
+    s0 = np.array([1.0, 0.0, 0.0, 0.0, 1.1, 0.0])
+    _, st = oracle.kepler(1.0, s0, 5.0, max_iter=1)
+    assert st == 1
+    _, st = oracle.kepler(1.0, s0, 5.0, max_iter=50)
+    assert st == 0
+
+
+# -------------------------------------------------- central-body drift ----
+def test_hc_drift_shift_and_angular_momentum():
+    d = discs.disc_uniform(64, 3)
+    arr = oracle.disc_arrays(d)
+    m = arr[6]
+    Ms = 1.3
+    P = np.array([math.fsum(m * arr[k]) for k in (3, 4, 5)])
+    x0 = [arr[k].copy() for k in range(3)]
+    L0 = oracle.energy(arr, d.G, Ms)[1:]
+    oracle.hc_drift(arr, Ms, 123.0)
+    for k in range(3):
+        assert np.allclose(arr[k] - x0[k], 123.0 * P[k] / Ms, rtol=1e-9, atol=1e-18)
+    L1 = oracle.energy(arr, d.G, Ms)[1:]
+    assert np.abs(L1 - L0).max() <= 1e-15 * np.linalg.norm(L0)
+
+
+# ---------------------------------------------------------- E and L -------
+def test_energy_circular_two_body_closed_form():
+    G, M, m, r = 2.959122082855911e-4, 1.3, 1e-3, 5.2
+    arr, vh = _one_body_circular(r, m, G, M)
+    E, Lx, Ly, Lz = oracle.energy(arr, G, M)
+    # H = p^2/2m + p^2/2M - G M m / r with p = m v_hel M/(M+m)  ==>  -G M m / (2r)
+    assert E == pytest.approx(-G * M * m / (2 * r), rel=1e-14)
+    # L = m x cross v: magnitude m r v_bary, along the orbit normal (0, -sin i, cos i)
+    Lmag = m * r * vh * M / (M + m)
+    assert np.allclose([Lx, Ly, Lz], [0.0, -Lmag * math.sin(0.4), Lmag * math.cos(0.4)],
+                       rtol=1e-14, atol=1e-14 * Lmag)
+
+
+def test_energy_static_hand_value():
+    # G=M=1, unit masses at +-1 on x: -GMm/r twice (-2) and -G m m / 2 (-1/2)
+    arr = _static([[1.0, 0, 0], [-1.0, 0, 0]], [1.0, 1.0])
+    assert oracle.energy(arr, 1.0, 1.0)[0] == -2.5
+
+
+# ------------------------------------------------------------- the step ---
+def _two_planets():
+    G = discs.G_GAUSS
+    m = np.array([1e-3, 3e-4])
+    pos, vh = discs.elements_to_cartesian(G * (1 + m), np.array([5.2, 9.5]), np.array([0.05, 0.05]),
+                                          np.array([0.01, 0.02]), np.array([0.3, 1.9]),
+                                          np.array([0.1, 2.2]), np.array([0.0, 2.5]))
+    vb = vh - (vh * m).sum(1, keepdims=True) / (1 + m.sum())
+    return [pos[0].copy(), pos[1].copy(), pos[2].copy(), vb[0].copy(), vb[1].copy(), vb[2].copy(), m]
+
+
+def _energy_track(dt, total, samples=200):
+    arr = _two_planets()
+    G = discs.G_GAUSS
+    E0, *L0 = oracle.energy(arr, G, 1.0)
+    n = int(round(total / dt))
+    every = n // samples
+    dE, dL = [], []
+    for _ in range(samples):
+        assert oracle.step(arr, G, 1.0, dt, 3.0, 0.4, 1, 0, every) == 0
+        E, *L = oracle.energy(arr, G, 1.0)
+        dE.append(E / E0 - 1)
+        dL.append(np.linalg.norm(np.array(L) - L0) / np.linalg.norm(L0))
+    return np.array(dE), np.array(dL)
+
+
+def test_step_energy_bounded_dt2_and_angular_momentum():
+    dE1, dL1 = _energy_track(6.0, 6.0 * 100_000)
+    dE2, _ = _energy_track(3.0, 6.0 * 100_000)
+    amp1, amp2 = np.abs(dE1).max(), np.abs(dE2).max()
+    assert amp1 < 1e-7
+    # no secular drift: the last quarter is no larger than the whole run's bound
+    assert np.abs(dE1[-50:]).max() <= 1.05 * amp1
+    assert 3.0 < amp1 / amp2 < 5.0                 # second-order map: error ~ dt^2
+    assert dL1.max() < 1e-12                       # exact pairwise antisymmetry in FP64
