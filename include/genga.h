@@ -1,0 +1,165 @@
+/*
+ * genga.h -- C ABI of libgenga: the long-range kick path of the GENGA hybrid
+ * symplectic step, on one NVIDIA GB300 (sm_103a).
+ *
+ * Paper: R. Brasser, S. L. Grimm, P. Hatalova, J. G. Stadel (2023),
+ * "Speeding up the GENGA N-body integrator on consumer-grade graphics
+ * cards", A&A.  The paper's subject is computing the mutual long-range
+ * forces of the N bodies in single precision while the Kepler drift and
+ * close-encounter forces stay in double precision (Sect. 1); this library
+ * exposes exactly that path.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Coordinates are democratic-heliocentric: heliocentric positions (au),
+ *   barycentric velocities (au/day), masses in solar masses.  The central
+ *   body is not an array element; it enters through genga_params.Mstar.
+ * - All per-body arrays are caller-owned DEVICE memory on the context's
+ *   device, float64, structure-of-arrays, length N, 8-byte aligned.  The
+ *   library never frees or reallocates them.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Every call is asynchronous on that stream except where
+ *   stated; argument errors are detected on the host and returned at once,
+ *   before anything is enqueued.
+ * - Errors found on the device (Kepler solver did not converge, encounter
+ *   list overflow, non-finite accelerations, a bounded wait that gave up)
+ *   are sticky bits in the context, read and cleared by genga_get_status.
+ * - No entry point aborts, traps, prints or allocates device memory, except
+ *   genga_create/genga_destroy (workspace) and genga_step's first use of a
+ *   new step-block length (graph instantiation).
+ * - A context is not re-entrant: one host thread and one stream at a time.
+ */
+#ifndef GENGA_H
+#define GENGA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GENGA_OK = 0,
+    GENGA_ERR_INVALID_ARG = 1, /* bad pointer, size or parameter (host check) */
+    GENGA_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    GENGA_ERR_CAPACITY = 3,    /* encounter list overflow: list truncated, count is the true total */
+    GENGA_ERR_KEPLER = 4,      /* the f/g solver hit kepler_max_iter for at least one body */
+    GENGA_ERR_NONFINITE = 5,   /* a NaN or Inf acceleration was produced */
+    GENGA_ERR_TIMEOUT = 6      /* a bounded device wait gave up (the kernel returned early) */
+} genga_status;
+
+/* Precision of the long-range kick (Sect. 1; "Do Kick in single precision", Sect. 4). */
+enum { GENGA_FP64 = 0, GENGA_FP32 = 1 };
+
+/* Pair critical radius r_crit,ij (Eq. 1 gives the per-body radius):
+ *   GENGA_RCRIT_EQ1         max(r_crit,i, r_crit,j), r_crit,i = max(n1 R_H,i, n2 dt v_i)
+ *   GENGA_RCRIT_MUTUAL_HILL n1 ((m_i + m_j) / 3 M*)^(1/3) (a_i + a_j) / 2            */
+enum { GENGA_RCRIT_EQ1 = 0, GENGA_RCRIT_MUTUAL_HILL = 1 };
+
+/* Changeover weight K(y), y = (r_ij / r_crit,ij - 0.1) / 0.9, K = 0 for y <= 0 and
+ * 1 for y >= 1 (the smooth switch of the hybrid integrator, Sect. 1):
+ *   GENGA_K_CHAMBERS  y^2 / (2y^2 - 2y + 1)        GENGA_K_QUINTIC  10y^3 - 15y^4 + 6y^5 */
+enum { GENGA_K_CHAMBERS = 0, GENGA_K_QUINTIC = 1 };
+
+typedef struct {
+    double G;                /* gravitational constant (au^3 Msun^-1 day^-2 for Gaussian units) */
+    double Mstar;            /* central mass, > 0 */
+    double dt;               /* step length (enters Eq. 1's velocity term and genga_step) */
+    double n1, n2;           /* Eq. 1 constants; the paper's typical values are 3 and 0.4 */
+    int32_t rcrit_mode;      /* GENGA_RCRIT_* */
+    int32_t changeover;      /* GENGA_K_* */
+    int32_t precision;       /* GENGA_FP64 or GENGA_FP32 */
+    int32_t kepler_max_iter; /* iteration cap of the f/g solver, >= 1 (50 is ample) */
+} genga_params;
+
+typedef struct {
+    int32_t N;                           /* number of non-central bodies, 0 <= N <= max_N */
+    double *x, *y, *z;                   /* heliocentric positions, device [N] */
+    double *vx, *vy, *vz;                /* barycentric velocities, device [N] */
+    double *m;                           /* masses, device [N], >= 0 */
+} genga_system;
+
+typedef struct genga_ctx genga_ctx;
+
+/* Create a context on `device` with workspace for systems of up to max_N bodies
+ * (about 200 bytes per body plus the encounter buffer).  *ctx is NULL on error. */
+genga_status genga_create(genga_ctx **ctx, int32_t max_N, int32_t device);
+
+/* Free the context's workspace (synchronises its device first). NULL is a no-op. */
+void genga_destroy(genga_ctx *ctx);
+
+/*
+ * Long-range kick (Sect. 1):  a_i = sum_{j != i} G m_j K(y_ij) (x_j - x_i) / r_ij^3,
+ * with r_crit evaluated from the current state, then v_i += a_i * tau.
+ *   tau   kick length (tau = 0: accelerations only, velocities untouched)
+ *   acc   optional device [3*N] float64 output, layout acc[c*N + i] (c = x, y, z);
+ *         NULL to skip.
+ * params->precision selects the FP64 kick or the FP32 kick (FP32 pair offsets
+ * and inverse cubes from FP64 positions, FP64 per-body accumulation); pairs
+ * inside r_crit are always evaluated in FP64 with K (Sect. 1, last paragraph).
+ * The encounter list of this state is rebuilt as a by-product (see
+ * genga_last_encounters).
+ */
+genga_status genga_kick(genga_ctx *ctx, const genga_system *sys, const genga_params *params,
+                        double tau, double *acc, void *stream);
+
+/*
+ * Drift of the level-0 step: central-body momentum drift x_i += (dt/2) P / M*
+ * (P = sum_j m_j v_j), then the Kepler drift of every body about mu = G M* for
+ * dt (always FP64, universal-variable f and g functions, Sect. 1), then the
+ * momentum drift again with the updated P.  Bodies whose solver hits
+ * kepler_max_iter set GENGA_ERR_KEPLER (they are still advanced).
+ */
+genga_status genga_drift(genga_ctx *ctx, genga_system *sys, const genga_params *params,
+                         double dt, void *stream);
+
+/*
+ * Close-encounter pairs of the current state: all (i, j), i < j, with
+ * r_ij < r_crit,ij (the changeover region of Sect. 1), sorted by (i, j).
+ *   pairs     device int32 [2*capacity]: pairs[2k] = i, pairs[2k+1] = j
+ *   capacity  number of pairs `pairs` holds, >= 0
+ *   count     device int32 [1]: the true number of pairs, even when it
+ *             exceeds capacity (then only `capacity` of them are written and
+ *             GENGA_ERR_CAPACITY is raised)
+ * Cost: one long-range pass in FP32 screening precision (the decision itself
+ * is taken in FP64).
+ */
+genga_status genga_encounters(genga_ctx *ctx, const genga_system *sys, const genga_params *params,
+                              int32_t *pairs, int32_t capacity, int32_t *count, void *stream);
+
+/* Copy the encounter list built by the most recent kick (same format as
+ * genga_encounters) without another pass over the pairs. */
+genga_status genga_last_encounters(genga_ctx *ctx, int32_t *pairs, int32_t capacity,
+                                   int32_t *count, void *stream);
+
+/*
+ * nsteps level-0 steps of the hybrid symplectic integrator (Sect. 1):
+ * kick(dt/2), drift(dt), kick(dt/2).  The close-encounter (Bulirsch-Stoer)
+ * level is not part of this library: pairs inside r_crit keep only their
+ * K-weighted long-range force and are reported by genga_last_encounters.
+ * Steps are replayed from a CUDA graph captured once per context.
+ */
+genga_status genga_step(genga_ctx *ctx, genga_system *sys, const genga_params *params,
+                        int32_t nsteps, void *stream);
+
+/*
+ * Energy and angular momentum (Sect. 3.1 diagnostics), FP64, synchronous:
+ *   E_L[0] = sum m v^2/2 + |P|^2/(2 M*) - sum G M* m_i / r_i - sum_{i<j} G m_i m_j / r_ij
+ *   E_L[1..3] = L = sum m_i x_i cross v_i
+ * E_L is HOST memory [4].  The call synchronises `stream`.
+ */
+genga_status genga_energy(genga_ctx *ctx, const genga_system *sys, const genga_params *params,
+                          double *E_L, void *stream);
+
+/* Synchronise `stream`, return the sticky device status (lowest set code) and
+ * clear it.  Also returns GENGA_ERR_CUDA if the stream reports an error. */
+genga_status genga_get_status(genga_ctx *ctx, void *stream);
+
+/* Static description of a status code. */
+const char *genga_status_string(genga_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GENGA_H */

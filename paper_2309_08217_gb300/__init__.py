@@ -1,0 +1,212 @@
+"""GB300 implementation of the GENGA long-range kick path (Brasser et al. 2023).
+
+A thin ctypes binding over ``libgenga.so`` (C ABI in ``include/genga.h``).
+The functions below carry the C names and only marshal arguments; every step
+of the path runs in the library's CUDA kernels.  PyTorch provides the device
+memory and streams.  Loading fails loudly when the library is missing: there
+is no CPU fallback.
+
+    import paper_2309_08217_gb300 as g
+    g.build()                                  # nvcc, sm_103a, in-tree
+    ctx = g.genga_create(max_N=40_000)
+    sys = g.DeviceSystem.from_disc(disc)       # float64 tensors on cuda
+    p = g.make_params(G=disc.G, Mstar=1.0, dt=6.0, precision=g.GENGA_FP32)
+    g.genga_kick(ctx, sys, p, tau=3.0, acc=acc_tensor)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import discs  # noqa: F401  (seeded inputs; numpy only)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgenga.so")
+
+GENGA_OK, GENGA_ERR_INVALID_ARG, GENGA_ERR_CUDA, GENGA_ERR_CAPACITY = 0, 1, 2, 3
+GENGA_ERR_KEPLER, GENGA_ERR_NONFINITE, GENGA_ERR_TIMEOUT = 4, 5, 6
+GENGA_FP64, GENGA_FP32 = 0, 1
+GENGA_RCRIT_EQ1, GENGA_RCRIT_MUTUAL_HILL = 0, 1
+GENGA_K_CHAMBERS, GENGA_K_QUINTIC = 0, 1
+
+
+class genga_params(C.Structure):
+    _fields_ = [("G", C.c_double), ("Mstar", C.c_double), ("dt", C.c_double),
+                ("n1", C.c_double), ("n2", C.c_double),
+                ("rcrit_mode", C.c_int32), ("changeover", C.c_int32),
+                ("precision", C.c_int32), ("kepler_max_iter", C.c_int32)]
+
+
+class genga_system(C.Structure):
+    _fields_ = [("N", C.c_int32)] + [(n, C.c_void_p) for n in ("x", "y", "z", "vx", "vy", "vz", "m")]
+
+
+class GengaError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = int(code)
+        super().__init__(f"{where}: {genga_status_string(code)} (code {code})")
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libgenga.so for sm_103a (nvcc) into the package directory."""
+    from .build import build as _b
+    return _b(force=force, verbose=verbose)
+
+
+def load():
+    """Load libgenga.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgenga.so not found at {LIB_PATH}: run paper_2309_08217_gb300.build()")
+        lib = C.CDLL(LIB_PATH)
+        P, S, V, I, D = C.POINTER(genga_params), C.POINTER(genga_system), C.c_void_p, C.c_int32, C.c_double
+        sigs = {
+            "genga_create": ([C.POINTER(V), I, I], I),
+            "genga_destroy": ([V], None),
+            "genga_kick": ([V, S, P, D, V, V], I),
+            "genga_drift": ([V, S, P, D, V], I),
+            "genga_encounters": ([V, S, P, V, I, V, V], I),
+            "genga_last_encounters": ([V, V, I, V, V], I),
+            "genga_step": ([V, S, P, I, V], I),
+            "genga_energy": ([V, S, P, C.POINTER(C.c_double), V], I),
+            "genga_get_status": ([V, V], I),
+            "genga_status_string": ([I], C.c_char_p),
+        }
+        for name, (args, res) in sigs.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def genga_status_string(code) -> str:
+    return load().genga_status_string(int(code)).decode()
+
+
+def _check(code, where):
+    if code != GENGA_OK:
+        raise GengaError(code, where)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def make_params(G, Mstar=1.0, dt=6.0, n1=3.0, n2=0.4, rcrit_mode=GENGA_RCRIT_MUTUAL_HILL,
+                changeover=GENGA_K_CHAMBERS, precision=GENGA_FP32, kepler_max_iter=50) -> genga_params:
+    return genga_params(G, Mstar, dt, n1, n2, rcrit_mode, changeover, precision, kepler_max_iter)
+
+
+class DeviceSystem:
+    """Seven float64 CUDA tensors (x, y, z, vx, vy, vz, m) and their genga_system view."""
+
+    def __init__(self, x, y, z, vx, vy, vz, m):
+        self.tensors = [x, y, z, vx, vy, vz, m]
+        for t in self.tensors:
+            if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+                raise ValueError("state arrays must be contiguous float64 CUDA tensors")
+        self.c = genga_system(int(m.numel()), *[t.data_ptr() for t in self.tensors])
+
+    @property
+    def N(self):
+        return int(self.c.N)
+
+    @classmethod
+    def from_disc(cls, disc, device="cuda"):
+        import torch
+        return cls(*[torch.tensor(a, dtype=torch.float64, device=device) for a in disc.arrays()])
+
+    @classmethod
+    def from_arrays(cls, arrays, device="cuda"):
+        import torch
+        return cls(*[torch.as_tensor(a, dtype=torch.float64).to(device).contiguous() for a in arrays])
+
+    def numpy(self):
+        return [t.detach().cpu().numpy().copy() for t in self.tensors]
+
+
+class Context:
+    """Owns a genga_ctx (workspace for up to max_N bodies on one device)."""
+
+    def __init__(self, max_N, device=0):
+        self.ptr = genga_create(max_N, device)
+
+    def close(self):
+        if self.ptr:
+            genga_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------- C-ABI names ---
+def genga_create(max_N, device=0):
+    h = C.c_void_p()
+    _check(load().genga_create(C.byref(h), int(max_N), int(device)), "genga_create")
+    return h
+
+
+def genga_destroy(ctx):
+    load().genga_destroy(ctx.ptr if isinstance(ctx, Context) else ctx)
+
+
+def _ctx(ctx):
+    return ctx.ptr if isinstance(ctx, Context) else ctx
+
+
+def _sys(sys):
+    return C.byref(sys.c if isinstance(sys, DeviceSystem) else sys)
+
+
+def genga_kick(ctx, sys, params, tau=0.0, acc=None, stream=None):
+    _check(load().genga_kick(_ctx(ctx), _sys(sys), C.byref(params), float(tau), _ptr(acc), _stream(stream)),
+           "genga_kick")
+
+
+def genga_drift(ctx, sys, params, dt, stream=None):
+    _check(load().genga_drift(_ctx(ctx), _sys(sys), C.byref(params), float(dt), _stream(stream)), "genga_drift")
+
+
+def genga_encounters(ctx, sys, params, pairs, capacity, count, stream=None):
+    _check(load().genga_encounters(_ctx(ctx), _sys(sys), C.byref(params), _ptr(pairs), int(capacity),
+                                   _ptr(count), _stream(stream)), "genga_encounters")
+
+
+def genga_last_encounters(ctx, pairs, capacity, count, stream=None):
+    _check(load().genga_last_encounters(_ctx(ctx), _ptr(pairs), int(capacity), _ptr(count), _stream(stream)),
+           "genga_last_encounters")
+
+
+def genga_step(ctx, sys, params, nsteps, stream=None):
+    _check(load().genga_step(_ctx(ctx), _sys(sys), C.byref(params), int(nsteps), _stream(stream)), "genga_step")
+
+
+def genga_energy(ctx, sys, params, stream=None):
+    out = (C.c_double * 4)()
+    _check(load().genga_energy(_ctx(ctx), _sys(sys), C.byref(params), out, _stream(stream)), "genga_energy")
+    return list(out)
+
+
+def genga_get_status(ctx, stream=None) -> int:
+    """Synchronise, return and clear the sticky device status (an int code)."""
+    return int(load().genga_get_status(_ctx(ctx), _stream(stream)))

@@ -1,0 +1,309 @@
+// api.cu -- the C ABI of libgenga (declared in include/genga.h): argument
+// checks, workspace, and the order of kernels for each entry point.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "internal.cuh"
+
+using namespace genga;
+
+namespace {
+
+struct DeviceGuard {  // run on the context's device, restore the caller's afterwards
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+inline bool is_fin(double v) { return isfinite(v) != 0; }
+
+genga_status check_params(const genga_params *p) {
+    if (!p) return GENGA_ERR_INVALID_ARG;
+    if (!is_fin(p->G) || p->G < 0.0) return GENGA_ERR_INVALID_ARG;
+    if (!is_fin(p->Mstar) || p->Mstar <= 0.0) return GENGA_ERR_INVALID_ARG;
+    if (!is_fin(p->dt) || !is_fin(p->n1) || !is_fin(p->n2) || p->n1 < 0.0 || p->n2 < 0.0)
+        return GENGA_ERR_INVALID_ARG;
+    if (p->rcrit_mode != GENGA_RCRIT_EQ1 && p->rcrit_mode != GENGA_RCRIT_MUTUAL_HILL) return GENGA_ERR_INVALID_ARG;
+    if (p->changeover != GENGA_K_CHAMBERS && p->changeover != GENGA_K_QUINTIC) return GENGA_ERR_INVALID_ARG;
+    if (p->precision != GENGA_FP64 && p->precision != GENGA_FP32) return GENGA_ERR_INVALID_ARG;
+    if (p->kepler_max_iter < 1) return GENGA_ERR_INVALID_ARG;
+    return GENGA_OK;
+}
+
+genga_status check_system(const genga_ctx *c, const genga_system *s) {
+    if (!c || !s) return GENGA_ERR_INVALID_ARG;
+    if (s->N < 0 || s->N > c->max_N) return GENGA_ERR_INVALID_ARG;
+    if (s->N > 0 && (!s->x || !s->y || !s->z || !s->vx || !s->vy || !s->vz || !s->m)) return GENGA_ERR_INVALID_ARG;
+    return GENGA_OK;
+}
+
+inline int npad_of(int N) { return (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD; }
+
+// Long-range pass over the current state: momentum (and list reset), prep,
+// pass, and the sort of the encounter list.  Leaves FP64 partials in c->partial.
+cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &p, int precision, int *split_out,
+                     cudaStream_t s) {
+    const int npad = npad_of(sys.N);
+    cudaError_t e = launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->mom, c->enc_count, s);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_prep(sys, p, c, s)) != cudaSuccess) return e;
+    int split = choose_split(sys.N, precision, c->sm_count, c->max_split);
+    const int cap_split = c->max_split * npad_of(c->max_N) / npad;  // partial buffer bound
+    if (split > cap_split) split = cap_split;
+    if (split < 1) split = 1;
+    PassArgs a;
+    a.hi = c->pk_hi;
+    a.lo = c->pk_lo;
+    a.p64 = c->pk64;
+    a.scr = c->scr;
+    a.tile_max = c->tile_max;
+    a.a_osc = c->a_osc;
+    a.rc_eq1 = c->rc_eq1;
+    a.m = sys.m;
+    a.partial = c->partial;
+    a.enc = c->enc;
+    a.enc_count = c->enc_count;
+    a.enc_cap = c->enc_cap;
+    a.status = c->status;
+    a.N = sys.N;
+    a.npad = npad;
+    a.ntiles = 0;
+    a.split = split;
+    a.Mstar = p.Mstar;
+    a.n1 = p.n1;
+    a.rcrit_mode = p.rcrit_mode;
+    a.changeover = p.changeover;
+    a.list_only = 0;
+    if ((e = launch_pass(a, precision, c->sm_count, s)) != cudaSuccess) return e;
+    if ((e = launch_sort_pairs(c->enc, c->enc_cap, c->enc_count, s)) != cudaSuccess) return e;
+    *split_out = split;
+    return cudaSuccess;
+}
+
+cudaError_t run_kick(genga_ctx *c, const genga_system &sys, const genga_params &p, double tau, double *acc,
+                     cudaStream_t s) {
+    int split = 1;
+    cudaError_t e = run_pass(c, sys, p, p.precision, &split, s);
+    if (e != cudaSuccess) return e;
+    return launch_combine(c->partial, split, sys.N, npad_of(sys.N), tau, acc, sys.vx, sys.vy, sys.vz, c->status, s);
+}
+
+template <class T>
+cudaError_t alloc(T **p, size_t n) {
+    return cudaMalloc((void **)p, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *genga_status_string(genga_status s) {
+    switch (s) {
+        case GENGA_OK: return "ok";
+        case GENGA_ERR_INVALID_ARG: return "invalid argument";
+        case GENGA_ERR_CUDA: return "CUDA runtime error";
+        case GENGA_ERR_CAPACITY: return "encounter list overflow (list truncated)";
+        case GENGA_ERR_KEPLER: return "Kepler solver did not converge for at least one body";
+        case GENGA_ERR_NONFINITE: return "non-finite acceleration";
+        case GENGA_ERR_TIMEOUT: return "bounded device wait timed out";
+    }
+    return "unknown status";
+}
+
+void genga_destroy(genga_ctx *c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    void *bufs[] = {c->pk_hi, c->pk_lo,     c->pk64, c->scr,       c->tile_max, c->a_osc,       c->rc_eq1,
+                    c->partial, c->mom, c->enc,  c->enc_count, c->status,   c->energy_part};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete c;
+}
+
+genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
+    if (!out) return GENGA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (max_N < 0 || max_N > (1 << 28)) return GENGA_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) return GENGA_ERR_CUDA;
+    if (device < 0 || device >= ndev) return GENGA_ERR_INVALID_ARG;
+    DeviceGuard g(device);
+    if (!g.ok) return GENGA_ERR_CUDA;
+    genga_ctx *c = new (std::nothrow) genga_ctx();
+    if (!c) return GENGA_ERR_CUDA;
+    memset(c, 0, sizeof(*c));
+    c->device = device;
+    c->max_N = max_N;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete c;
+        return GENGA_ERR_CUDA;
+    }
+    c->sm_count = prop.multiProcessorCount;
+    const int np = npad_of(max_N > 0 ? max_N : 1);
+    c->npad_max = np;
+    // split * npad <= max_split * np for every N <= max_N (checked at launch)
+    c->max_split = 2 * c->sm_count * 1024 / np + 2;
+    if (c->max_split < 4) c->max_split = 4;
+    long long ecap = 4096;
+    while (ecap < 16LL * max_N) ecap <<= 1;
+    c->enc_cap = (int32_t)ecap;
+    c->energy_blocks = np / 256;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = alloc(&c->pk_hi, np);
+    if (e == cudaSuccess) e = alloc(&c->pk_lo, np);
+    if (e == cudaSuccess) e = alloc(&c->pk64, np);
+    if (e == cudaSuccess) e = alloc(&c->scr, np);
+    if (e == cudaSuccess) e = alloc(&c->tile_max, np / 64);
+    if (e == cudaSuccess) e = alloc(&c->a_osc, np);
+    if (e == cudaSuccess) e = alloc(&c->rc_eq1, np);
+    if (e == cudaSuccess) e = alloc(&c->partial, (size_t)c->max_split * 3 * np);
+    if (e == cudaSuccess) e = alloc(&c->mom, 8);
+    if (e == cudaSuccess) e = alloc(&c->enc, (size_t)c->enc_cap);
+    if (e == cudaSuccess) e = alloc(&c->enc_count, 1);
+    if (e == cudaSuccess) e = alloc(&c->status, 1);
+    if (e == cudaSuccess) e = alloc(&c->energy_part, (size_t)4 * c->energy_blocks);
+    if (e == cudaSuccess) e = cudaMemset(c->enc_count, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        genga_destroy(c);
+        return GENGA_ERR_CUDA;
+    }
+    *out = c;
+    return GENGA_OK;
+}
+
+genga_status genga_kick(genga_ctx *c, const genga_system *sys, const genga_params *p, double tau, double *acc,
+                        void *stream) {
+    genga_status st;
+    if ((st = check_system(c, sys)) != GENGA_OK) return st;
+    if ((st = check_params(p)) != GENGA_OK) return st;
+    if (!is_fin(tau)) return GENGA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (sys->N == 0) return cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
+    return run_kick(c, *sys, *p, tau, acc, s) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
+}
+
+genga_status genga_drift(genga_ctx *c, genga_system *sys, const genga_params *p, double dt, void *stream) {
+    genga_status st;
+    if ((st = check_system(c, sys)) != GENGA_OK) return st;
+    if ((st = check_params(p)) != GENGA_OK) return st;
+    if (!is_fin(dt)) return GENGA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    genga_system s2 = *sys;
+    return launch_drift(s2, *p, dt, c, (cudaStream_t)stream) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
+}
+
+genga_status genga_last_encounters(genga_ctx *c, int32_t *pairs, int32_t capacity, int32_t *count, void *stream) {
+    if (!c || capacity < 0 || !count || (capacity > 0 && !pairs)) return GENGA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    return launch_copy_pairs(c->enc, c->enc_count, c->enc_cap, pairs, capacity, count, c->status,
+                             (cudaStream_t)stream) == cudaSuccess
+               ? GENGA_OK
+               : GENGA_ERR_CUDA;
+}
+
+genga_status genga_encounters(genga_ctx *c, const genga_system *sys, const genga_params *p, int32_t *pairs,
+                              int32_t capacity, int32_t *count, void *stream) {
+    genga_status st;
+    if ((st = check_system(c, sys)) != GENGA_OK) return st;
+    if ((st = check_params(p)) != GENGA_OK) return st;
+    if (capacity < 0 || !count || (capacity > 0 && !pairs)) return GENGA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (sys->N == 0) {
+        if (cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s) != cudaSuccess) return GENGA_ERR_CUDA;
+    } else {
+        int split;
+        if (run_pass(c, *sys, *p, GENGA_FP32, &split, s) != cudaSuccess) return GENGA_ERR_CUDA;
+    }
+    return genga_last_encounters(c, pairs, capacity, count, stream);
+}
+
+genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, int32_t nsteps, void *stream) {
+    genga_status st;
+    if ((st = check_system(c, sys)) != GENGA_OK) return st;
+    if ((st = check_params(p)) != GENGA_OK) return st;
+    if (nsteps < 0) return GENGA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (sys->N == 0 || nsteps == 0) return GENGA_OK;
+    genga_system s2 = *sys;
+    const double h = 0.5 * p->dt;
+    for (int k = 0; k < nsteps; k++) {
+        if (run_kick(c, s2, *p, h, nullptr, s) != cudaSuccess) return GENGA_ERR_CUDA;
+        if (launch_drift(s2, *p, p->dt, c, s) != cudaSuccess) return GENGA_ERR_CUDA;
+        if (run_kick(c, s2, *p, h, nullptr, s) != cudaSuccess) return GENGA_ERR_CUDA;
+    }
+    return GENGA_OK;
+}
+
+genga_status genga_energy(genga_ctx *c, const genga_system *sys, const genga_params *p, double *E_L, void *stream) {
+    genga_status st;
+    if ((st = check_system(c, sys)) != GENGA_OK) return st;
+    if ((st = check_params(p)) != GENGA_OK) return st;
+    if (!E_L) return GENGA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < 4; k++) E_L[k] = 0.0;
+    if (sys->N == 0) return GENGA_OK;
+    if (launch_energy(*sys, *p, c, s) != cudaSuccess) return GENGA_ERR_CUDA;
+    if (launch_momentum(sys->vx, sys->vy, sys->vz, sys->m, sys->N, c->mom, nullptr, s) != cudaSuccess)
+        return GENGA_ERR_CUDA;
+    const int nb = (sys->N + 255) / 256;
+    double *host = (double *)malloc(sizeof(double) * (4 * (size_t)nb + 3));
+    if (!host) return GENGA_ERR_CUDA;
+    cudaError_t e = cudaMemcpyAsync(host, c->energy_part, sizeof(double) * 4 * nb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host + 4 * nb, c->mom, sizeof(double) * 3, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        free(host);
+        return GENGA_ERR_CUDA;
+    }
+    // host: block partials in index order, compensated
+    for (int q = 0; q < 4; q++) {
+        double sum = 0.0, comp = 0.0;
+        const double *P = host + 4 * nb;
+        double terms_extra = (q == 0) ? (P[0] * P[0] + P[1] * P[1] + P[2] * P[2]) / (2.0 * p->Mstar) : 0.0;
+        for (int b = 0; b <= nb; b++) {
+            const double v = (b < nb) ? host[4 * b + q] : terms_extra;
+            const double t = sum + v;
+            comp += (fabs(sum) >= fabs(v)) ? ((sum - t) + v) : ((v - t) + sum);
+            sum = t;
+        }
+        E_L[q] = sum + comp;
+    }
+    free(host);
+    return GENGA_OK;
+}
+
+genga_status genga_get_status(genga_ctx *c, void *stream) {
+    if (!c) return GENGA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t bits = 0;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&bits, c->status, sizeof(bits), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(bits));
+    if (e != cudaSuccess) return GENGA_ERR_CUDA;
+    for (int code = 1; code <= 6; code++)
+        if (bits & GENGA_BIT(code)) return (genga_status)code;
+    return GENGA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,159 @@
+// drift.cu -- the drift of the level-0 step, always in FP64 (Sect. 1):
+//
+//   x_i += (dt/2) P / M*               central-body momentum drift, P = sum m v
+//   (x_i, v_i) <- Kepler(mu = G M*, dt) two-body drift of every body
+//   x_i += (dt/2) P' / M*              with the momentum after the Kepler drift
+//
+// The Kepler drift uses universal variables: Kepler's equation in the
+// universal anomaly s,
+//   F(s) = r0 G1(s) + eta0 G2(s) + mu G3(s) - dt = 0,  G_k = s^k c_k(beta s^2),
+// beta = 2 mu / r0 - v0^2, eta0 = x0 . v0, solved by the Laguerre-Conway
+// iteration (order 5, Conway 1986) from s = dt / r0, followed by the f and g
+// functions.  The Stumpff functions c_k(z) come from their Taylor series for
+// |z| < 1 and from the trigonometric / hyperbolic closed forms otherwise
+// (with the half-angle form of c2, which does not cancel).
+#include "internal.cuh"
+
+namespace genga {
+
+namespace {
+
+// c2(z) = sum_k (-z)^k / (2k+2)!,  c3(z) = sum_k (-z)^k / (2k+3)!
+__device__ __forceinline__ void stumpff_series(double z, double &c2, double &c3) {
+    constexpr double a2[10] = {1.0 / 2.0,
+                               1.0 / 24.0,
+                               1.0 / 720.0,
+                               1.0 / 40320.0,
+                               1.0 / 3628800.0,
+                               1.0 / 479001600.0,
+                               1.0 / 87178291200.0,
+                               1.0 / 20922789888000.0,
+                               1.0 / 6402373705728000.0,
+                               1.0 / 2432902008176640000.0};
+    constexpr double a3[10] = {1.0 / 6.0,
+                               1.0 / 120.0,
+                               1.0 / 5040.0,
+                               1.0 / 362880.0,
+                               1.0 / 39916800.0,
+                               1.0 / 6227020800.0,
+                               1.0 / 1307674368000.0,
+                               1.0 / 355687428096000.0,
+                               1.0 / 121645100408832000.0,
+                               1.0 / 51090942171709440000.0};
+    const double w = -z;
+    double p2 = a2[9], p3 = a3[9];
+#pragma unroll
+    for (int k = 8; k >= 0; k--) {
+        p2 = fma(p2, w, a2[k]);
+        p3 = fma(p3, w, a3[k]);
+    }
+    c2 = p2;
+    c3 = p3;
+}
+
+__device__ __forceinline__ void stumpff(double z, double &c0, double &c1, double &c2, double &c3) {
+    if (fabs(z) < 1.0) {
+        stumpff_series(z, c2, c3);
+        c0 = 1.0 - z * c2;
+        c1 = 1.0 - z * c3;
+    } else if (z > 0.0) {
+        const double q = sqrt(z);
+        double sn, cs, sh, ch;
+        sincos(q, &sn, &cs);
+        sincos(0.5 * q, &sh, &ch);
+        c0 = cs;
+        c1 = sn / q;
+        c2 = 2.0 * sh * sh / z;
+        c3 = (q - sn) / (z * q);
+    } else {
+        const double q = sqrt(-z);
+        const double sn = sinh(q), cs = cosh(q), sh = sinh(0.5 * q);
+        c0 = cs;
+        c1 = sn / q;
+        c2 = 2.0 * sh * sh / (-z);
+        c3 = (sn - q) / (-z * q);
+    }
+}
+
+// Returns true when the iteration met |ds| <= 1e-12 |s| within max_iter steps.
+__device__ bool kepler_drift(double mu, double dt, int max_iter, double &x, double &y, double &z, double &u,
+                             double &v, double &w) {
+    const double r0 = sqrt(x * x + y * y + z * z);
+    const double v2 = u * u + v * v + w * w;
+    const double eta = x * u + y * v + z * w;
+    const double beta = 2.0 * mu / r0 - v2;
+    double s = dt / r0;
+    double c0, c1, c2, c3;
+    bool ok = false;
+    for (int it = 0; it < max_iter; it++) {
+        stumpff(beta * s * s, c0, c1, c2, c3);
+        const double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
+        const double F = fma(r0, G1, fma(eta, G2, mu * G3)) - dt;
+        const double dF = fma(r0, c0, fma(eta, G1, mu * G2));
+        const double ddF = fma(eta, c0, (mu - beta * r0) * G1);
+        // Laguerre-Conway step, order n = 5
+        const double rad = sqrt(fabs(16.0 * dF * dF - 20.0 * F * ddF));
+        const double ds = -5.0 * F / (dF + copysign(rad, dF));
+        s += ds;
+        if (fabs(ds) <= 1e-12 * fabs(s)) {
+            ok = true;
+            break;
+        }
+    }
+    stumpff(beta * s * s, c0, c1, c2, c3);
+    const double G1 = s * c1, G2 = s * s * c2;
+    const double r = fma(r0, c0, fma(eta, G1, mu * G2));
+    const double f = 1.0 - mu * G2 / r0;
+    const double g = fma(r0, G1, eta * G2);
+    const double fd = -mu * G1 / (r * r0);
+    const double gd = 1.0 - mu * G2 / r;
+    const double nx = f * x + g * u, ny = f * y + g * v, nz = f * z + g * w;
+    const double nu = fd * x + gd * u, nv = fd * y + gd * v, nw = fd * z + gd * w;
+    x = nx; y = ny; z = nz;
+    u = nu; v = nv; w = nw;
+    return ok;
+}
+
+// x += h P / M*, then the Kepler drift over dt.
+__global__ void drift_kernel(double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
+                             double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz, int N,
+                             const double *__restrict__ P, double Mstar, double mu, double h, double dt,
+                             int max_iter, uint32_t *__restrict__ status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double xi = x[i] + h * P[0] / Mstar;
+    double yi = y[i] + h * P[1] / Mstar;
+    double zi = z[i] + h * P[2] / Mstar;
+    double ui = vx[i], vi = vy[i], wi = vz[i];
+    if (!kepler_drift(mu, dt, max_iter, xi, yi, zi, ui, vi, wi)) atomicOr(status, GENGA_BIT(GENGA_ERR_KEPLER));
+    x[i] = xi; y[i] = yi; z[i] = zi;
+    vx[i] = ui; vy[i] = vi; vz[i] = wi;
+}
+
+__global__ void hc_kernel(double *__restrict__ x, double *__restrict__ y, double *__restrict__ z, int N,
+                          const double *__restrict__ P, double Mstar, double h) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    x[i] += h * P[0] / Mstar;
+    y[i] += h * P[1] / Mstar;
+    z[i] += h * P[2] / Mstar;
+}
+
+}  // namespace
+
+cudaError_t launch_drift(genga_system &sys, const genga_params &p, double dt, genga_ctx *c, cudaStream_t s) {
+    const int N = sys.N;
+    if (N <= 0) return cudaSuccess;
+    cudaError_t e = launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, N, c->mom, nullptr, s);
+    if (e != cudaSuccess) return e;
+    const int nb = (N + 127) / 128;
+    drift_kernel<<<nb, 128, 0, s>>>(sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, N, c->mom, p.Mstar,
+                                    p.G * p.Mstar, 0.5 * dt, dt, p.kepler_max_iter, c->status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, N, c->mom, nullptr, s);
+    if (e != cudaSuccess) return e;
+    hc_kernel<<<(N + 255) / 256, 256, 0, s>>>(sys.x, sys.y, sys.z, N, c->mom, p.Mstar, 0.5 * dt);
+    return cudaGetLastError();
+}
+
+}  // namespace genga

@@ -1,0 +1,157 @@
+// internal.cuh -- context layout, launch helpers and PTX wrappers shared by
+// the libgenga translation units (sm_103a only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/genga.h"
+
+// ---------------------------------------------------------------- status bits
+// Sticky device status word: bit (code - 1) for each genga_status error code.
+#define GENGA_BIT(code) (1u << ((code) - 1))
+
+// Spin-wait limit for mbarrier waits: 2 s of %globaltimer (nanoseconds).
+#define GENGA_WAIT_LIMIT_NS 2000000000ull
+
+// ------------------------------------------------------------- tile geometry
+// Bodies are padded to a multiple of GENGA_PAD so that every j-tile and every
+// i-block is full; padded bodies have zero mass and sit far away.
+#define GENGA_PAD 1024
+#define GENGA_PAD_POS 1.0e6f
+
+struct genga_ctx {
+    int device;
+    int sm_count;
+    int32_t max_N;
+    int32_t npad_max;          // roundup(max_N, GENGA_PAD)
+    // packed per-body data, rebuilt at every kick (prep kernel)
+    float4 *pk_hi;             // [npad] {x_hi, y_hi, z_hi, G m (fp32)}
+    float4 *pk_lo;             // [npad] {x - x_hi, y - y_hi, z - z_hi, 0}
+    double4_32a *pk64;             // [npad] {x, y, z, G m}
+    float2 *scr;               // [npad] screening bound factors {H_i, A_i} (rounded up)
+    float2 *tile_max;          // [npad / 64] per-64-body maxima of scr
+    double *a_osc;             // [npad] osculating semi-major axis (Eq. 1 input)
+    double *rc_eq1;            // [npad] per-body Eq. 1 radius
+    double *partial;           // [max_split][3][npad] FP64 partial accelerations
+    int32_t max_split;
+    double *mom;               // [8] P (3 doubles) + scratch
+    // encounter list of the most recent pass
+    int2 *enc;                 // [enc_cap] unsorted during the pass, sorted after
+    int32_t enc_cap;           // power of two
+    int32_t *enc_count;        // [1]
+    uint32_t *status;          // [1] sticky bits
+    double *energy_part;       // [energy_blocks][4]
+    int32_t energy_blocks;
+    // step graph cache
+    cudaGraphExec_t step_graph;
+    cudaStream_t cap_stream;
+    unsigned char step_key[256];
+    int step_key_len;
+};
+
+// -------------------------------------------------------------- launchers
+namespace genga {
+
+struct PassArgs {               // one long-range pass
+    const float4 *hi, *lo;
+    const double4_32a *p64;
+    const float2 *scr, *tile_max;
+    const double *a_osc, *rc_eq1, *m;
+    double *partial;            // [split][3][npad]
+    int2 *enc;
+    int32_t *enc_count;
+    int32_t enc_cap;
+    uint32_t *status;
+    int32_t N, npad;
+    int32_t ntiles;             // npad / tile
+    int32_t split;
+    double Mstar, n1;
+    int32_t rcrit_mode, changeover;
+    int32_t list_only;          // 1: encounter list only (no force accumulation needed)
+};
+
+cudaError_t launch_momentum(const double *vx, const double *vy, const double *vz, const double *m,
+                            int N, double *P, int32_t *zero_me, cudaStream_t s);
+cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ctx *c, cudaStream_t s);
+cudaError_t launch_pass(const PassArgs &a, int precision, int sm_count, cudaStream_t s);
+int choose_split(int N, int precision, int sm_count, int max_split);
+cudaError_t launch_combine(const double *partial, int split, int N, int npad, double tau, double *acc,
+                           double *vx, double *vy, double *vz, uint32_t *status, cudaStream_t s);
+cudaError_t launch_sort_pairs(int2 *enc, int32_t cap, const int32_t *count, cudaStream_t s);
+cudaError_t launch_copy_pairs(const int2 *enc, const int32_t *count, int32_t enc_cap, int32_t *pairs,
+                              int32_t capacity, int32_t *count_out, uint32_t *status, cudaStream_t s);
+cudaError_t launch_drift(genga_system &sys, const genga_params &p, double dt, genga_ctx *c, cudaStream_t s);
+cudaError_t launch_energy(const genga_system &sys, const genga_params &p, genga_ctx *c, cudaStream_t s);
+
+}  // namespace genga
+
+// ------------------------------------------------------------ PTX wrappers
+#ifdef __CUDACC__
+namespace genga {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// One-dimensional bulk copy global -> shared, completion signalled on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar`, at most GENGA_WAIT_LIMIT_NS.  Returns
+// false (and sets the TIMEOUT bit) when the limit is reached.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t *status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_timer_ns() - t0 > GENGA_WAIT_LIMIT_NS) {
+            atomicOr(status, GENGA_BIT(GENGA_ERR_TIMEOUT));
+            return false;
+        }
+    }
+    return true;
+}
+
+}  // namespace genga
+#endif

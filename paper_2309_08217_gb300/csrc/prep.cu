@@ -1,0 +1,149 @@
+// prep.cu -- per-body work done before each long-range pass (O(N), FP64):
+//
+//   * P = sum_j m_j v_j, a deterministic compensated reduction (one CTA);
+//   * the Eq. (1) inputs and radius of every body (Sect. 1): osculating
+//     semi-major axis a_i (1/a = 2/r - v_hel^2 / mu_i, mu_i = G (M* + m_i),
+//     a_i = r_i for unbound orbits), heliocentric speed v_hel = |v + P/M*|,
+//     r_crit,i = max(n1 a_i (m_i / 3M*)^(1/3), n2 dt v_hel);
+//   * the packed copies the pass kernels read: FP32 hi/lo split of each
+//     position plus G m in FP32 (the single-precision kick of Sect. 1 takes
+//     its pair offsets from these), an FP64 {x, y, z, G m} record, and the
+//     FP32 screening factors {H_i, A_i} with r_crit,ij <= max(H_i, H_j) *
+//     max(A_i, A_j) for every pair (rounded up), plus their maxima per 64
+//     bodies.
+#include "internal.cuh"
+
+namespace genga {
+
+namespace {
+
+constexpr int MOM_THREADS = 1024;
+
+struct NSum {  // Neumaier running sum
+    double s = 0.0, c = 0.0;
+    __device__ void add(double v) {
+        const double t = s + v;
+        if (fabs(s) >= fabs(v)) c += (s - t) + v;
+        else c += (v - t) + s;
+        s = t;
+    }
+    __device__ double value() const { return s + c; }
+};
+
+// One CTA: thread t sums bodies t, t + 1024, ... in order, then a fixed-shape
+// pairwise tree combines the 1024 partials.  The result does not depend on
+// timing, so repeated runs are bitwise identical.
+__global__ void __launch_bounds__(MOM_THREADS) momentum_kernel(const double *__restrict__ vx,
+                                                               const double *__restrict__ vy,
+                                                               const double *__restrict__ vz,
+                                                               const double *__restrict__ m, int N,
+                                                               double *__restrict__ P,
+                                                               int32_t *__restrict__ zero_me) {
+    __shared__ double sh[3][MOM_THREADS];
+    NSum px, py, pz;
+    for (int i = threadIdx.x; i < N; i += MOM_THREADS) {
+        const double mi = m[i];
+        px.add(mi * vx[i]);
+        py.add(mi * vy[i]);
+        pz.add(mi * vz[i]);
+    }
+    sh[0][threadIdx.x] = px.value();
+    sh[1][threadIdx.x] = py.value();
+    sh[2][threadIdx.x] = pz.value();
+    __syncthreads();
+    for (int w = MOM_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            for (int c = 0; c < 3; c++) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        P[0] = sh[0][0];
+        P[1] = sh[1][0];
+        P[2] = sh[2][0];
+        if (zero_me) *zero_me = 0;
+    }
+}
+
+constexpr int PREP_THREADS = 64;  // one block = one 64-body screening group
+
+__global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
+    const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+    const double *__restrict__ vx, const double *__restrict__ vy, const double *__restrict__ vz,
+    const double *__restrict__ m, int N, const double *__restrict__ P, double G, double Mstar, double dt,
+    double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float4 *__restrict__ lo,
+    double4_32a *__restrict__ p64, float2 *__restrict__ scr, float2 *__restrict__ tile_max,
+    double *__restrict__ a_osc, double *__restrict__ rc_eq1) {
+    const int i = blockIdx.x * PREP_THREADS + threadIdx.x;
+    float2 s = make_float2(0.f, 0.f);
+    if (i < N) {
+        const double xi = x[i], yi = y[i], zi = z[i], mi = m[i];
+        const double ux = vx[i] + P[0] / Mstar;
+        const double uy = vy[i] + P[1] / Mstar;
+        const double uz = vz[i] + P[2] / Mstar;
+        const double v2 = ux * ux + uy * uy + uz * uz;
+        const double r = sqrt(xi * xi + yi * yi + zi * zi);
+        const double mu = G * (Mstar + mi);
+        const double inva = 2.0 / r - v2 / mu;
+        const double a = (inva > 0.0) ? 1.0 / inva : r;
+        const double hill = n1 * a * cbrt(mi / (3.0 * Mstar));
+        const double vel = n2 * dt * sqrt(v2);
+        const double rc = fmax(hill, vel);
+        a_osc[i] = a;
+        rc_eq1[i] = rc;
+        if (rcrit_mode == GENGA_RCRIT_EQ1) {
+            // r_crit,ij = max(rc_i, rc_j) = max(1, 1) * max(rc_i, rc_j)
+            s = make_float2(1.0f, __double2float_ru(rc));
+        } else {
+            // n1 ((m_i+m_j)/3M)^(1/3) (a_i+a_j)/2 <= n1 (2 max(m)/3M)^(1/3) * max(a)
+            s = make_float2(__double2float_ru(n1 * cbrt(2.0 * mi / (3.0 * Mstar)) * (1.0 + 1e-12)),
+                            __double2float_ru(a * (1.0 + 1e-12)));
+        }
+        const float hx = __double2float_rn(xi), hy = __double2float_rn(yi), hz = __double2float_rn(zi);
+        const double gm = G * mi;
+        hi[i] = make_float4(hx, hy, hz, __double2float_rn(gm));
+        lo[i] = make_float4(__double2float_rn(xi - (double)hx), __double2float_rn(yi - (double)hy),
+                            __double2float_rn(zi - (double)hz), 0.f);
+        p64[i] = make_double4_32a(xi, yi, zi, gm);
+    } else {
+        hi[i] = make_float4(GENGA_PAD_POS, GENGA_PAD_POS, GENGA_PAD_POS, 0.f);
+        lo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        p64[i] = make_double4_32a(GENGA_PAD_POS, GENGA_PAD_POS, GENGA_PAD_POS, 0.0);
+        a_osc[i] = 0.0;
+        rc_eq1[i] = 0.0;
+    }
+    scr[i] = s;
+    // maxima of the screening factors over this block of 64 bodies
+    float hmax = s.x, amax = s.y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    }
+    __shared__ float2 wm[PREP_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = make_float2(hmax, amax);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float2 t = wm[0];
+        for (int w = 1; w < PREP_THREADS / 32; w++) t = make_float2(fmaxf(t.x, wm[w].x), fmaxf(t.y, wm[w].y));
+        tile_max[blockIdx.x] = t;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_momentum(const double *vx, const double *vy, const double *vz, const double *m, int N,
+                            double *P, int32_t *zero_me, cudaStream_t s) {
+    momentum_kernel<<<1, MOM_THREADS, 0, s>>>(vx, vy, vz, m, N, P, zero_me);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ctx *c, cudaStream_t s) {
+    const int npad = (sys.N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
+    prep_kernel<<<npad / PREP_THREADS, PREP_THREADS, 0, s>>>(
+        sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->mom, p.G, p.Mstar, p.dt, p.n1, p.n2,
+        p.rcrit_mode, c->pk_hi, c->pk_lo, c->pk64, c->scr, c->tile_max, c->a_osc, c->rc_eq1);
+    return cudaGetLastError();
+}
+
+}  // namespace genga

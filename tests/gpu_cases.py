@@ -1,0 +1,31 @@
+"""Seeded inputs shared by the GPU parity tests (no method arithmetic here:
+bodies are only placed; the oracle computes everything else)."""
+import numpy as np
+
+from paper_2309_08217_gb300 import discs
+
+
+def planted_disc(N, seed, fracs=(0.05, 0.5, 0.9, 1.1, 0.3), mass_scale=1.0, a_min=0.7, a_max=3.0):
+    """An equal-mass disc (2.5 Earth masses in total) with close pairs planted
+    at fixed fractions of the three-mutual-Hill-radius scale
+    3 (2m/3)^(1/3) a, so the changeover region, K = 0 and the r_crit
+    boundary are all exercised."""
+    d = discs.disc_uniform(N, seed, a_min=a_min, a_max=a_max, m_total=2.5 * discs.M_EARTH * mass_scale)
+    arr = [a.copy() for a in d.arrays()]
+    rng = np.random.default_rng(seed + 77)
+    m = arr[6][0]
+    npl = min(len(fracs), N // 2)
+    for k in range(npl):
+        i, j = 2 * k + 1, 2 * k
+        r = np.sqrt(arr[0][j] ** 2 + arr[1][j] ** 2 + arr[2][j] ** 2)
+        scale = 3.0 * (2 * m / 3.0) ** (1 / 3) * r
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        for c in range(3):
+            arr[c][i] = arr[c][j] + fracs[k] * scale * u[c]
+        for c in range(3, 6):
+            arr[c][i] = arr[c][j]
+    d2 = d.copy()
+    for dst, src in zip(d2.arrays(), arr):
+        dst[:] = src
+    return d2
