@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Benchmark: pair-interactions/s of the level-0 GENGA step with the FP32
+long-range kick on a 40,000-body disc, against the FP64 kick on the same GPU.
+
+One step = kick(dt/2) + drift(dt) + kick(dt/2) through the C ABI
+(genga_step), i.e. two long-range passes of N(N-1) pair interactions each,
+plus the Eq. (1) radius, packing, encounter list and Kepler drift.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl genga|reference]
+
+Prints ONE JSON line (rank 0).  Under torchrun (N > 1) every rank runs an
+independent replica disc (seed 3 + rank): the discs share nothing, so there
+is no collective on the data path ("scaling": "weak"); the barrier and the
+max over ranks are only for timing.
+
+--impl reference times the CPU FP64 oracle on the host cores on bounded
+samples of the same workload (rows of the pair sum) and prints the same line
+with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pair-interactions/s, FP32 vs FP64 kick, N=40k, 1 GB300, accel rel-err≤2e-5"
+UNIT = "pair-interactions/s"
+WORKLOAD = ("disc40k: 40,000 equal-mass planetesimals (5 Earth masses), surface density ~ a^-1.5 on "
+            "0.5-4 au, e/i Rayleigh 0.01/0.005, dt = 6 d, r_crit = 3 mutual Hill radii, Chambers changeover")
+FLOPS_PER_PAIR = 20          # the usual convention for one gravitational pair interaction
+L2_FLUSH_BYTES = 512 << 20   # larger than the 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="genga", choices=["genga", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------- clocks -----
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        try:
+            smax = float(rows[0][2])
+        except ValueError:
+            smax = None
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# -------------------------------------------------------------- helpers ---
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kernel_traffic(kernel_file="kick.cu"):
+    """dram bytes per launch of the pass kernel from the committed ncu summary,
+    or None when the kernel source has changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2309_08217_gb300", "csrc", kernel_file)
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if rec.get("source_sha256") != sha:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def oracle_sample_rate(d, seconds, seed=0):
+    """Time the FP64 oracle's pair sum on a bounded sample of body rows;
+    returns (pairs/s, rows, threads, acc rows, row indices)."""
+    import numpy as np
+
+    import oracle
+    arr = oracle.disc_arrays(d)
+    a, rc = oracle.rcrit(*arr, G=d.G, Mstar=d.Mstar, dt=d.dt, n1=3.0, n2=0.4)
+    rng = np.random.default_rng(seed)
+    # calibrate on a few rows, then size the sample to the time budget
+    rows = 64
+    idx = np.sort(rng.choice(d.N, rows, replace=False))
+    t0 = time.perf_counter()
+    oracle.kick_acc(arr[0], arr[1], arr[2], arr[6], a, rc, d.G, d.Mstar, 3.0, 1, 0, idx=idx)
+    dt_cal = time.perf_counter() - t0
+    rows = int(min(d.N, max(64, rows * seconds / max(dt_cal, 1e-6))))
+    idx = np.sort(rng.choice(d.N, rows, replace=False))
+    t0 = time.perf_counter()
+    acc = oracle.kick_acc(arr[0], arr[1], arr[2], arr[6], a, rc, d.G, d.Mstar, 3.0, 1, 0, idx=idx)
+    el = time.perf_counter() - t0
+    return rows * (d.N - 1) / el, rows, oracle.threads(), acc, idx, el
+
+
+# ------------------------------------------------------------ reference ---
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2309_08217_gb300 import discs
+    d = discs.workload("disc40k")
+    budget = max(1.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample_rate(d, budget / 4)
+    rates, rows_all, el_all, thr = [], 0, 0.0, 1
+    for k in range(args.steps):
+        rate, rows, thr, _, _, el = oracle_sample_rate(d, budget, seed=k + 1)
+        rates.append(rate)
+        rows_all += rows
+        el_all += el
+    value = rows_all * (d.N - 1) / el_all
+    pairs_step = 2 * d.N * (d.N - 1)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": pairs_step / value * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": d.N, "pairs_per_step": pairs_step,
+                   "sample": "each step: the oracle's FP64 pair sum over a random sample of body rows "
+                             f"({rows_all // max(1, args.steps)} rows x {d.N - 1} partners on average)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                         "sample": f"{rows_all} body rows over {args.steps} steps, {el_all:.1f} s"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- genga ----
+def run_genga(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2309_08217_gb300 as g
+    from paper_2309_08217_gb300 import discs
+    if rank == 0:
+        g.build()
+    if dist:
+        dist.barrier()
+    g.load()
+
+    d = discs.disc_powerlaw(40_000, 3 + rank)          # rank 0: the disc40k workload itself
+    N = d.N
+    pairs_step = 2 * N * (N - 1)
+    ctx = g.Context(N, local)
+    p32 = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=g.GENGA_FP32)
+    p64 = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=g.GENGA_FP64)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+
+    def timed_steps(params, K, W, clocks=False):
+        s = g.DeviceSystem.from_disc(d, device=dev)
+        for _ in range(W):
+            g.genga_step(ctx, s, params, 1)
+        if g.genga_get_status(ctx) != g.GENGA_OK:
+            raise RuntimeError("device status after warm-up")
+        g.genga_profile_enable(ctx, True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        sampler = ClockSampler(local) if clocks else None
+        barrier()
+        if sampler:
+            sampler.start()
+        for k in range(K):
+            flush.zero_()                          # L2 flush between timed steps (not timed)
+            evs[k][0].record(stream)
+            g.genga_step(ctx, s, params, 1)
+            evs[k][1].record(stream)
+        barrier()
+        clk = sampler.stop() if sampler else None
+        st = g.genga_get_status(ctx)
+        if st != g.GENGA_OK:
+            raise RuntimeError(f"device status {st} after the timed steps")
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        pass_ms, launches = g.genga_profile_read(ctx)
+        g.genga_profile_enable(ctx, False)
+        return ms, pass_ms, launches, clk, s
+
+    # ---- every FP32 pass variant on this workload (the autotuner keeps the fastest)
+    variants = {}
+    _, nvar = g.genga_get_kernel_variant(ctx, N)
+    sv = g.DeviceSystem.from_disc(d, device=dev)
+    for v in range(nvar):
+        g.genga_set_kernel_variant(ctx, v)
+        for _ in range(2):
+            g.genga_kick(ctx, sv, p32, 0.0, None)
+        g.genga_profile_enable(ctx, True)
+        for _ in range(5):
+            g.genga_kick(ctx, sv, p32, 0.0, None)
+        pms, pn = g.genga_profile_read(ctx)
+        g.genga_profile_enable(ctx, False)
+        variants[str(v)] = pms / max(1, pn)
+    g.genga_set_kernel_variant(ctx, -1)
+
+    # ---- FP32 step (the headline) and FP64 step on the same GPU
+    ms32, pass32, nl32, clk, s32 = timed_steps(p32, args.steps, args.warmup, clocks=True)
+    chosen, _ = g.genga_get_kernel_variant(ctx, N)
+    ms64, pass64, nl64, _, _ = timed_steps(p64, max(1, args.fp64_steps), 3)
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms32_max = max_over_ranks(ms32)
+    ms64_max = max_over_ranks(ms64)
+    value = ws * pairs_step * args.steps / (ms32_max * 1e-3)
+    value64 = ws * pairs_step * max(1, args.fp64_steps) / (ms64_max * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in d.arrays()]
+        outh = [torch.empty_like(host[c]).pin_memory() for c in range(6)]
+        s = g.DeviceSystem.from_disc(d, device=dev)
+        for _ in range(max(3, args.warmup)):
+            g.genga_step(ctx, s, p32, 1)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            for c in range(7):
+                s.tensors[c].copy_(host[c], non_blocking=True)
+            g.genga_step(ctx, s, p32, 1)
+            for c in range(6):
+                outh[c].copy_(s.tensors[c], non_blocking=True)
+        e1.record(stream)
+        barrier()
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1))
+        e2e = {"value": ws * pairs_step * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(h.numel() * 8 for h in host)),
+               "d2h_bytes_per_step": int(sum(h.numel() * 8 for h in outh)),
+               "ms_per_step": ms_e2e / args.steps}
+
+    # ---- roofline of the dominant kernel (the FP32 long-range pass)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak32 = sms * 128 * 2 * max_mhz * 1e6 / 1e12            # FP32 CUDA-core FMA peak, TFLOP/s
+    f32_meas, f64_meas = g.genga_measure_alu_peaks(local)
+    pass_avg = pass32 / max(1, nl32)
+    pass64_avg = pass64 / max(1, nl64)
+    achieved = FLOPS_PER_PAIR * N * (N - 1) / (pass_avg * 1e-3) / 1e12
+    achieved64 = FLOPS_PER_PAIR * N * (N - 1) / (pass64_avg * 1e-3) / 1e12
+    traffic = kernel_traffic()
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s", "frac": achieved / peak32,
+            "traffic": traffic, "kernel": "pass_fp32_kernel",
+            "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x {max_mhz:.0f} MHz",
+            "flops_per_pair": FLOPS_PER_PAIR, "pass_ms_avg": pass_avg,
+            "measured_ffma_tflops": f32_meas, "frac_of_measured_ffma": achieved / f32_meas,
+            "sm_mhz_median": (clk or {}).get("sm_mhz"), "fp32_variant": chosen,
+            "fp32_variant_pass_ms": variants}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # acc rows of the GPU FP32 kick for the sampled bodies (accuracy of this very run)
+        sg = g.DeviceSystem.from_disc(d, device=dev)
+        acc = torch.zeros(3 * N, dtype=torch.float64, device=dev)
+        g.genga_kick(ctx, sg, p32, 0.0, acc)
+        gacc = acc.view(3, N).cpu().numpy()
+        rate, rows, thr, oacc, idx, el = oracle_sample_rate(d, args.cpu_seconds)
+        err = np.sqrt(((gacc[:, idx] - oacc) ** 2).sum(0)) / np.sqrt((oacc ** 2).sum(0))
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"FP64 oracle pair sum over {rows} random body rows x {N - 1} partners ({el:.1f} s)",
+               "fp32_rel_err_max_on_sample": float(err.max())}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "pairs_per_step": pairs_step,
+                   "step": "kick(dt/2) drift(dt) kick(dt/2) via genga_step; FP32 pair terms, FP64 "
+                           "accumulation, FP64 drift and close-encounter pairs",
+                   "l2": "flushed (512 MiB write) between timed steps, outside the step events",
+                   "parallelism": f"{ws} independent replica disc(s), one per GPU"},
+        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64_max / max(1, args.fp64_steps),
+                 "steps": max(1, args.fp64_steps), "pass_ms_avg": pass64_avg, "achieved_tflops": achieved64,
+                 "measured_dfma_tflops": f64_meas, "frac_of_measured_dfma": achieved64 / f64_meas,
+                 "fp32_over_fp64": value / value64},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 14 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_genga(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

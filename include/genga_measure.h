@@ -1,0 +1,47 @@
+/*
+ * genga_measure.h -- measurement hooks of libgenga.  The paper has no
+ * counterpart for these; they exist so that a benchmark can time the
+ * dominant kernel live and compare it with the chip's arithmetic peaks.
+ */
+#ifndef GENGA_MEASURE_H
+#define GENGA_MEASURE_H
+
+#include "genga.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* enable != 0: from now on, record a CUDA event pair around every launch of
+ * the long-range pass kernel, on the stream it is launched on (at most 65536
+ * pairs; later launches are not recorded).  enable == 0 stops recording.
+ * Either call discards pairs recorded so far. */
+genga_status genga_profile_enable(genga_ctx *ctx, int32_t enable);
+
+/* Synchronise the recorded events and return the summed device time of the
+ * recorded pass launches (*pass_ms) and their number (*launches); both
+ * pointers are HOST memory.  reset != 0 discards the pairs afterwards. */
+genga_status genga_profile_read(genga_ctx *ctx, double *pass_ms, int32_t *launches, int32_t reset);
+
+/* Arithmetic throughput microbenchmark on `device`: independent FFMA and
+ * DFMA chains over every SM; results in TFLOP/s (2 flops per FMA), HOST
+ * memory.  Synchronous; allocates and frees a small result buffer. */
+genga_status genga_measure_alu_peaks(int32_t device, double *fp32_tflops, double *fp64_tflops);
+
+/* Kernel variant of the FP32 long-range pass (bodies per thread, resident
+ * CTAs per SM, loop unroll).  variant >= 0 forces that variant for every
+ * size; variant = -1 (the default) lets the context time all variants the
+ * first time it meets a size bucket (a power of two of the padded N) and keep
+ * the fastest -- that first pass synchronises its stream.  Out-of-range
+ * values return GENGA_ERR_INVALID_ARG. */
+genga_status genga_set_kernel_variant(genga_ctx *ctx, int32_t variant);
+
+/* The FP32 variant the context uses for systems of N bodies (-1 when that
+ * size has not been tuned yet), and the number of variants; HOST memory. */
+genga_status genga_get_kernel_variant(genga_ctx *ctx, int32_t N, int32_t *variant, int32_t *num_variants);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GENGA_MEASURE_H */

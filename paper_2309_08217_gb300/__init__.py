@@ -79,6 +79,11 @@ def load():
             "genga_energy": ([V, S, P, C.POINTER(C.c_double), V], I),
             "genga_get_status": ([V, V], I),
             "genga_status_string": ([I], C.c_char_p),
+            "genga_profile_enable": ([V, I], I),
+            "genga_profile_read": ([V, C.POINTER(C.c_double), C.POINTER(C.c_int32), I], I),
+            "genga_measure_alu_peaks": ([I, C.POINTER(C.c_double), C.POINTER(C.c_double)], I),
+            "genga_set_kernel_variant": ([V, I], I),
+            "genga_get_kernel_variant": ([V, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], I),
         }
         for name, (args, res) in sigs.items():
             f = getattr(lib, name)
@@ -210,3 +215,35 @@ def genga_energy(ctx, sys, params, stream=None):
 def genga_get_status(ctx, stream=None) -> int:
     """Synchronise, return and clear the sticky device status (an int code)."""
     return int(load().genga_get_status(_ctx(ctx), _stream(stream)))
+
+
+# ------------------------------------------------- measurement hooks ------
+def genga_profile_enable(ctx, enable=True):
+    _check(load().genga_profile_enable(_ctx(ctx), 1 if enable else 0), "genga_profile_enable")
+
+
+def genga_profile_read(ctx, reset=True):
+    """(summed device ms, number) of the long-range pass launches recorded."""
+    ms, n = C.c_double(), C.c_int32()
+    _check(load().genga_profile_read(_ctx(ctx), C.byref(ms), C.byref(n), 1 if reset else 0),
+           "genga_profile_read")
+    return ms.value, n.value
+
+
+def genga_measure_alu_peaks(device=0):
+    """Measured FFMA and DFMA throughput of `device` in TFLOP/s."""
+    f32, f64 = C.c_double(), C.c_double()
+    _check(load().genga_measure_alu_peaks(int(device), C.byref(f32), C.byref(f64)), "genga_measure_alu_peaks")
+    return f32.value, f64.value
+
+
+def genga_set_kernel_variant(ctx, variant=-1):
+    """Force an FP32 pass variant (>= 0) or return to autotuning (-1)."""
+    _check(load().genga_set_kernel_variant(_ctx(ctx), int(variant)), "genga_set_kernel_variant")
+
+
+def genga_get_kernel_variant(ctx, N):
+    """(variant in use for N bodies or -1 if not tuned yet, number of variants)."""
+    v, n = C.c_int32(), C.c_int32()
+    _check(load().genga_get_kernel_variant(_ctx(ctx), int(N), C.byref(v), C.byref(n)), "genga_get_kernel_variant")
+    return v.value, n.value

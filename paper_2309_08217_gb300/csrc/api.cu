@@ -49,24 +49,21 @@ genga_status check_system(const genga_ctx *c, const genga_system *s) {
 
 inline int npad_of(int N) { return (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD; }
 
-// Long-range pass over the current state: momentum (and list reset), prep,
-// pass, and the sort of the encounter list.  Leaves FP64 partials in c->partial.
-cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &p, int precision, int *split_out,
-                     cudaStream_t s) {
-    const int npad = npad_of(sys.N);
-    cudaError_t e = launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->mom, c->enc_count, s);
-    if (e != cudaSuccess) return e;
-    if ((e = launch_prep(sys, p, c, s)) != cudaSuccess) return e;
-    int split = choose_split(sys.N, precision, c->sm_count, c->max_split);
-    const int cap_split = c->max_split * npad_of(c->max_N) / npad;  // partial buffer bound
-    if (split > cap_split) split = cap_split;
-    if (split < 1) split = 1;
+inline int size_bucket(int N) {
+    int b = 0;
+    for (int v = npad_of(N); v > 1; v >>= 1) b++;
+    return b < 32 ? b : 31;
+}
+
+PassArgs base_args(genga_ctx *c, const genga_system &sys, const genga_params &p) {
     PassArgs a;
     a.hi = c->pk_hi;
     a.lo = c->pk_lo;
     a.p64 = c->pk64;
     a.scr = c->scr;
-    a.tile_max = c->tile_max;
+    a.gbox_lo = c->gbox_lo;
+    a.gbox_hi = c->gbox_hi;
+    a.perm = c->perm;
     a.a_osc = c->a_osc;
     a.rc_eq1 = c->rc_eq1;
     a.m = sys.m;
@@ -76,26 +73,93 @@ cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &
     a.enc_cap = c->enc_cap;
     a.status = c->status;
     a.N = sys.N;
-    a.npad = npad;
+    a.npad = npad_of(sys.N);
     a.ntiles = 0;
-    a.split = split;
+    a.split = 1;
     a.Mstar = p.Mstar;
     a.n1 = p.n1;
     a.rcrit_mode = p.rcrit_mode;
     a.changeover = p.changeover;
     a.list_only = 0;
-    if ((e = launch_pass(a, precision, c->sm_count, s)) != cudaSuccess) return e;
+    a.work = c->work;
+    a.chunk_tiles = 1;
+    return a;
+}
+
+// The FP32 pass variant for this size: forced, already tuned, or tuned now.
+// Tuning runs every variant twice on the packed state (the encounter list
+// is cleared after each run) and keeps the fastest second run; it
+// synchronises the stream, so it is skipped while the stream is captured.
+int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
+    if (c->forced_variant >= 0) return c->forced_variant;
+    const int b = size_bucket(N);
+    if (c->f32_variant[b] >= 0) return c->f32_variant[b];
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return 0;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return 0;
+    }
+    int best = 0;
+    float best_ms = 3.0e38f;
+    for (int v = 0; v < num_fp32_variants(); v++) {
+        PassArgs a = base;
+        int grid = 1;
+        plan_pass(N, GENGA_FP32, v, c->sm_count, c->partial_cap, &a.split, &a.chunk_tiles, &grid);
+        float ms = 3.0e38f;
+        for (int rep = 0; rep < 2; rep++) {
+            cudaEventRecord(e0, s);
+            const cudaError_t e = launch_pass(a, GENGA_FP32, v, grid, s);
+            cudaEventRecord(e1, s);
+            cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s);
+            if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->f32_variant[b] = (int8_t)best;
+    return best;
+}
+
+// Long-range pass over the current state: momentum (and list reset), the
+// spatial order (skipped when the positions are those of the previous pass),
+// prep, pass, and the sort of the encounter list.  Leaves FP64 partials in
+// c->partial, indexed by position in the spatial order.
+cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &p, int precision, bool reorder,
+                     int *split_out, cudaStream_t s) {
+    const int npad = npad_of(sys.N);
+    cudaError_t e = launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->mom, c->enc_count, s);
+    if (e != cudaSuccess) return e;
+    if (reorder && (e = launch_order(sys, c, s)) != cudaSuccess) return e;
+    if ((e = launch_prep(sys, p, c, s)) != cudaSuccess) return e;
+    PassArgs a = base_args(c, sys, p);
+    const int variant = (precision == GENGA_FP32) ? fp32_variant(c, a, sys.N, s) : 0;
+    int grid = 1;
+    plan_pass(sys.N, precision, variant, c->sm_count, c->partial_cap, &a.split, &a.chunk_tiles, &grid);
+    const int split = a.split;
+    profile_before_pass(c, s);
+    e = launch_pass(a, precision, variant, grid, s);
+    profile_after_pass(c, s);
+    if (e != cudaSuccess) return e;
     if ((e = launch_sort_pairs(c->enc, c->enc_cap, c->enc_count, s)) != cudaSuccess) return e;
     *split_out = split;
     return cudaSuccess;
 }
 
 cudaError_t run_kick(genga_ctx *c, const genga_system &sys, const genga_params &p, double tau, double *acc,
-                     cudaStream_t s) {
+                     bool reorder, cudaStream_t s) {
     int split = 1;
-    cudaError_t e = run_pass(c, sys, p, p.precision, &split, s);
+    cudaError_t e = run_pass(c, sys, p, p.precision, reorder, &split, s);
     if (e != cudaSuccess) return e;
-    return launch_combine(c->partial, split, sys.N, npad_of(sys.N), tau, acc, sys.vx, sys.vy, sys.vz, c->status, s);
+    return launch_combine(c->partial, split, sys.N, npad_of(sys.N), c->perm, tau, acc, sys.vx, sys.vy, sys.vz,
+                          c->status, s);
 }
 
 template <class T>
@@ -126,8 +190,11 @@ void genga_destroy(genga_ctx *c) {
     cudaDeviceSynchronize();
     if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    void *bufs[] = {c->pk_hi, c->pk_lo,     c->pk64, c->scr,       c->tile_max, c->a_osc,       c->rc_eq1,
-                    c->partial, c->mom, c->enc,  c->enc_count, c->status,   c->energy_part};
+    profile_free(c);
+    void *bufs[] = {c->pk_hi,       c->pk_lo,       c->pk64,        c->scr,      c->gbox_lo,    c->gbox_hi,
+                    c->perm,        c->ord_keys[0], c->ord_keys[1], c->ord_vals[0], c->ord_vals[1], c->ord_hist,
+                    c->ord_rbits,   c->a_osc,       c->rc_eq1,      c->partial,  c->mom,        c->enc,
+                    c->enc_count,   c->status,      c->energy_part, c->work};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete c;
@@ -147,6 +214,8 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     memset(c, 0, sizeof(*c));
     c->device = device;
     c->max_N = max_N;
+    for (int b = 0; b < 32; b++) c->f32_variant[b] = -1;
+    c->forced_variant = -1;
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
         delete c;
@@ -155,23 +224,33 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     c->sm_count = prop.multiProcessorCount;
     const int np = npad_of(max_N > 0 ? max_N : 1);
     c->npad_max = np;
-    // split * npad <= max_split * np for every N <= max_N (checked at launch)
-    c->max_split = 2 * c->sm_count * 1024 / np + 2;
-    if (c->max_split < 4) c->max_split = 4;
+    // partial sums: split * 3 * npad doubles; the plans stay near 8 items per
+    // resident CTA, i.e. split * npad ~ 16 * SMs * 1024 (plan_pass clamps)
+    c->partial_cap = 3 * ((size_t)np * 4 + (size_t)16 * c->sm_count * 1024 + 4096);
     long long ecap = 4096;
     while (ecap < 16LL * max_N) ecap <<= 1;
     c->enc_cap = (int32_t)ecap;
     c->energy_blocks = np / 256;
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = init_pass_kernels();
     if (e == cudaSuccess) e = alloc(&c->pk_hi, np);
     if (e == cudaSuccess) e = alloc(&c->pk_lo, np);
     if (e == cudaSuccess) e = alloc(&c->pk64, np);
     if (e == cudaSuccess) e = alloc(&c->scr, np);
-    if (e == cudaSuccess) e = alloc(&c->tile_max, np / 64);
+    if (e == cudaSuccess) e = alloc(&c->gbox_lo, np / 64);
+    if (e == cudaSuccess) e = alloc(&c->gbox_hi, np / 64);
+    if (e == cudaSuccess) e = alloc(&c->perm, np);
+    for (int q = 0; q < 2; q++) {
+        if (e == cudaSuccess) e = alloc(&c->ord_keys[q], np);
+        if (e == cudaSuccess) e = alloc(&c->ord_vals[q], np);
+    }
+    if (e == cudaSuccess) e = alloc(&c->ord_hist, order_hist_entries(np));
+    if (e == cudaSuccess) e = alloc(&c->ord_rbits, 1);
     if (e == cudaSuccess) e = alloc(&c->a_osc, np);
     if (e == cudaSuccess) e = alloc(&c->rc_eq1, np);
-    if (e == cudaSuccess) e = alloc(&c->partial, (size_t)c->max_split * 3 * np);
-    if (e == cudaSuccess) e = alloc(&c->mom, 8);
+    if (e == cudaSuccess) e = alloc(&c->partial, c->partial_cap);
+    if (e == cudaSuccess) e = alloc(&c->work, 1);
+    if (e == cudaSuccess) e = alloc(&c->mom, 256);   // P, block partials, ticket
+    if (e == cudaSuccess) e = cudaMemset(c->mom, 0, 256 * sizeof(double));
     if (e == cudaSuccess) e = alloc(&c->enc, (size_t)c->enc_cap);
     if (e == cudaSuccess) e = alloc(&c->enc_count, 1);
     if (e == cudaSuccess) e = alloc(&c->status, 1);
@@ -196,7 +275,7 @@ genga_status genga_kick(genga_ctx *c, const genga_system *sys, const genga_param
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (sys->N == 0) return cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
-    return run_kick(c, *sys, *p, tau, acc, s) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
+    return run_kick(c, *sys, *p, tau, acc, true, s) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
 }
 
 genga_status genga_drift(genga_ctx *c, genga_system *sys, const genga_params *p, double dt, void *stream) {
@@ -230,7 +309,7 @@ genga_status genga_encounters(genga_ctx *c, const genga_system *sys, const genga
         if (cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s) != cudaSuccess) return GENGA_ERR_CUDA;
     } else {
         int split;
-        if (run_pass(c, *sys, *p, GENGA_FP32, &split, s) != cudaSuccess) return GENGA_ERR_CUDA;
+        if (run_pass(c, *sys, *p, GENGA_FP32, true, &split, s) != cudaSuccess) return GENGA_ERR_CUDA;
     }
     return genga_last_encounters(c, pairs, capacity, count, stream);
 }
@@ -245,10 +324,12 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
     if (sys->N == 0 || nsteps == 0) return GENGA_OK;
     genga_system s2 = *sys;
     const double h = 0.5 * p->dt;
+    // the closing kick of a step and the opening kick of the next see the same
+    // positions, so the spatial order is rebuilt only after each drift
     for (int k = 0; k < nsteps; k++) {
-        if (run_kick(c, s2, *p, h, nullptr, s) != cudaSuccess) return GENGA_ERR_CUDA;
+        if (run_kick(c, s2, *p, h, nullptr, k == 0, s) != cudaSuccess) return GENGA_ERR_CUDA;
         if (launch_drift(s2, *p, p->dt, c, s) != cudaSuccess) return GENGA_ERR_CUDA;
-        if (run_kick(c, s2, *p, h, nullptr, s) != cudaSuccess) return GENGA_ERR_CUDA;
+        if (run_kick(c, s2, *p, h, nullptr, true, s) != cudaSuccess) return GENGA_ERR_CUDA;
     }
     return GENGA_OK;
 }

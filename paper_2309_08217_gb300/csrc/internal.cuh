@@ -20,6 +20,16 @@
 #define GENGA_PAD 1024
 #define GENGA_PAD_POS 1.0e6f
 
+namespace genga {
+struct Profile {                // CUDA event pairs around pass launches
+    static constexpr int CAP = 65536;
+    cudaEvent_t *ev = nullptr;  // [2 * CAP]
+    int created = 0;
+    int n = 0;
+    bool enabled = false;
+};
+}  // namespace genga
+
 struct genga_ctx {
     int device;
     int sm_count;
@@ -30,12 +40,17 @@ struct genga_ctx {
     float4 *pk_lo;             // [npad] {x - x_hi, y - y_hi, z - z_hi, 0}
     double4_32a *pk64;             // [npad] {x, y, z, G m}
     float2 *scr;               // [npad] screening bound factors {H_i, A_i} (rounded up)
-    float2 *tile_max;          // [npad / 64] per-64-body maxima of scr
+    float4 *gbox_lo;           // [npad / 64] per 64-body group: {min x, min y, min z, max H}
+    float4 *gbox_hi;           // [npad / 64]                    {max x, max y, max z, max A}
+    uint32_t *perm;            // [npad] body at position k of the spatial order
+    uint32_t *ord_keys[2];     // [npad] radix sort keys (ping-pong)
+    uint32_t *ord_vals[2];     // [npad] radix sort values
+    uint32_t *ord_hist;        // digit histograms / offsets
+    unsigned *ord_rbits;       // [1] extent of the positions (float bits)
     double *a_osc;             // [npad] osculating semi-major axis (Eq. 1 input)
     double *rc_eq1;            // [npad] per-body Eq. 1 radius
-    double *partial;           // [max_split][3][npad] FP64 partial accelerations
-    int32_t max_split;
-    double *mom;               // [8] P (3 doubles) + scratch
+    double *partial;           // [split][3][npad] FP64 partial accelerations
+    double *mom;               // [256] P (3 doubles), momentum block partials, ticket
     // encounter list of the most recent pass
     int2 *enc;                 // [enc_cap] unsorted during the pass, sorted after
     int32_t enc_cap;           // power of two
@@ -48,6 +63,11 @@ struct genga_ctx {
     cudaStream_t cap_stream;
     unsigned char step_key[256];
     int step_key_len;
+    genga::Profile *prof;      // measurement hooks (genga_measure.h), NULL when unused
+    int32_t *work;             // [1] work-item counter of the persistent pass
+    int8_t f32_variant[32];    // autotuned FP32 pass variant per log2(npad) bucket, -1 = not tuned
+    int32_t forced_variant;    // >= 0: use this FP32 variant (genga_set_kernel_variant)
+    size_t partial_cap;        // doubles in `partial`
 };
 
 // -------------------------------------------------------------- launchers
@@ -56,7 +76,9 @@ namespace genga {
 struct PassArgs {               // one long-range pass
     const float4 *hi, *lo;
     const double4_32a *p64;
-    const float2 *scr, *tile_max;
+    const float2 *scr;
+    const float4 *gbox_lo, *gbox_hi;
+    const uint32_t *perm;
     const double *a_osc, *rc_eq1, *m;
     double *partial;            // [split][3][npad]
     int2 *enc;
@@ -69,20 +91,30 @@ struct PassArgs {               // one long-range pass
     double Mstar, n1;
     int32_t rcrit_mode, changeover;
     int32_t list_only;          // 1: encounter list only (no force accumulation needed)
+    int32_t *work;              // [1] dynamic work-item counter (zeroed before each launch)
+    int32_t chunk_tiles;        // j-tiles per work item
 };
 
 cudaError_t launch_momentum(const double *vx, const double *vy, const double *vz, const double *m,
                             int N, double *P, int32_t *zero_me, cudaStream_t s);
 cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ctx *c, cudaStream_t s);
-cudaError_t launch_pass(const PassArgs &a, int precision, int sm_count, cudaStream_t s);
-int choose_split(int N, int precision, int sm_count, int max_split);
-cudaError_t launch_combine(const double *partial, int split, int N, int npad, double tau, double *acc,
-                           double *vx, double *vy, double *vz, uint32_t *status, cudaStream_t s);
+cudaError_t launch_order(const genga_system &sys, genga_ctx *c, cudaStream_t s);
+size_t order_hist_entries(int nmax);
+cudaError_t init_pass_kernels();
+cudaError_t launch_pass(const PassArgs &a, int precision, int variant, int grid, cudaStream_t s);
+int num_fp32_variants();
+void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_cap, int *split, int *chunk_tiles,
+               int *grid);
+cudaError_t launch_combine(const double *partial, int split, int N, int npad, const uint32_t *perm, double tau,
+                           double *acc, double *vx, double *vy, double *vz, uint32_t *status, cudaStream_t s);
 cudaError_t launch_sort_pairs(int2 *enc, int32_t cap, const int32_t *count, cudaStream_t s);
 cudaError_t launch_copy_pairs(const int2 *enc, const int32_t *count, int32_t enc_cap, int32_t *pairs,
                               int32_t capacity, int32_t *count_out, uint32_t *status, cudaStream_t s);
 cudaError_t launch_drift(genga_system &sys, const genga_params &p, double dt, genga_ctx *c, cudaStream_t s);
 cudaError_t launch_energy(const genga_system &sys, const genga_params &p, genga_ctx *c, cudaStream_t s);
+void profile_before_pass(genga_ctx *c, cudaStream_t s);
+void profile_after_pass(genga_ctx *c, cudaStream_t s);
+void profile_free(genga_ctx *c);
 
 }  // namespace genga
 
@@ -104,6 +136,10 @@ __device__ __forceinline__ void fence_barrier_init() {
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {

@@ -3,28 +3,36 @@
 //   a_i = sum_{j != i} G m_j K(y_ij) (x_j - x_i) / r_ij^3,
 //   y_ij = (r_ij / r_crit,ij - 0.1) / 0.9,  K = 1 for r_ij >= r_crit,ij.
 //
-// Layout of one pass.  A CTA owns KB * BPT i-bodies (BPT per thread, held in
-// registers) and a contiguous slice of j-tiles; TILE j-bodies at a time are
-// staged into shared memory by one-dimensional bulk copies completed on an
-// mbarrier (STAGES-deep ring), and every warp reads them back as broadcasts.
-// Slices of the j range run in separate CTAs (grid.y) so that N = 40k still
-// fills all SMs; their FP64 partial sums are combined afterwards in a fixed
-// order, so results are bitwise reproducible.
+// Layout.  Bodies sit in the spatial (Morton) order of order.cu.  A CTA owns
+// KB * BPT consecutive i-bodies; warp w holds the 32 * BPT consecutive bodies
+// ibase + w*32*BPT + k*32 + lane (k < BPT) in registers, so each warp covers a
+// compact region.  j-bodies stream through shared memory in tiles of TILE
+// (one-dimensional bulk copies completed on an mbarrier, STAGES-deep ring)
+// and are read back as broadcasts.  Slices of the j range run in separate
+// CTAs (grid.y) so the grid fills the GPU; their FP64 partial sums are
+// combined afterwards in a fixed order, so results are bitwise reproducible.
 //
-// Precision.  The FP32 pass (the single-precision kick of Sect. 1) forms
-// each pair offset from the FP32 hi/lo split of the FP64 positions,
-//   dx = (x_j,hi - x_i,hi) + (x_j,lo - x_i,lo),
-// squares it in FP32, takes rsqrt on the SFU, and accumulates each tile's
-// terms in FP32 registers that are added into FP64 per-body accumulators
-// once per tile.  The FP64 pass does the same arithmetic in FP64, with its
+// Tile classes.  For every (warp, tile) the bounding boxes of the two body
+// sets give a lower bound D on every pair distance.  A tile is FAR for a warp
+// when D exceeds an upper bound of r_crit,ij over the two sets (so K = 1 for
+// every pair) and, in FP32, also 0.025 * (largest |coordinate|), which keeps
+// the offset of two rounded FP32 positions within ~5e-6 of the true offset.
+// FAR tiles run the plain loop; NEAR tiles run the screened loop below.
+//
+// Precision.  FP32 pass (the single-precision kick of Sect. 1): FAR pairs use
+// the FP32-rounded positions; NEAR pairs use the hi/lo split of the FP64
+// positions, dx = (x_j,hi - x_i,hi) + (x_j,lo - x_i,lo); r^2 in FP32, rsqrt on
+// the SFU, each tile's terms summed in FP32 registers and added into FP64
+// per-body accumulators once per tile.  FP64 pass: the same in FP64, with its
 // own inverse square root (FP32 SFU seed + one third-order correction) and
 // Neumaier-compensated accumulation every 32 terms.
 //
-// Changeover pairs.  Both passes screen every pair against an FP32 upper
-// bound of r_crit,ij (per i-body and j-tile); a pair under the bound leaves
-// the fast loop and is evaluated exactly in FP64: r_crit,ij, K and the
-// weighted force (close-encounter forces are always FP64, Sect. 1), and, if
-// r_ij < r_crit,ij and i < j, it is appended to the encounter list.
+// Screened pairs.  In NEAR tiles every pair is compared with an FP32 upper
+// bound of r_crit,ij^2; a pair under it leaves the FP32/FP64 fast arithmetic
+// and is evaluated exactly in FP64: r_crit,ij, K and the weighted force
+// (close-encounter forces are always FP64, Sect. 1), and, if r_ij < r_crit,ij,
+// it is appended to the encounter list (once, from the side with the smaller
+// body index).
 #include "internal.cuh"
 
 namespace genga {
@@ -62,9 +70,9 @@ __device__ __forceinline__ double changeover_K(double y, int form) {
     return y * y * y * (10.0 + y * (6.0 * y - 15.0));
 }
 
-// Exact FP64 treatment of one screened pair: returns the K-weighted
-// acceleration of i due to j and records (i, j) when it is an encounter.
-__device__ __noinline__ double3 screened_pair(const PassArgs &a, int i, int j) {
+// Exact FP64 treatment of one screened pair (positions i, j of the spatial
+// order): the K-weighted acceleration of i due to j; records the encounter.
+__device__ __forceinline__ double3 screened_pair(const PassArgs &a, int i, int j) {
     double3 f = make_double3(0.0, 0.0, 0.0);
     if (i >= a.N || j >= a.N || i == j) return f;
     const double4_32a pi = a.p64[i], pj = a.p64[j];
@@ -72,17 +80,18 @@ __device__ __noinline__ double3 screened_pair(const PassArgs &a, int i, int j) {
     const double r2 = dx * dx + dy * dy + dz * dz;
     if (r2 == 0.0) return f;  // coincident bodies: no direction, no force
     const double r = sqrt(r2);
+    const int oi = (int)a.perm[i], oj = (int)a.perm[j];
     double rc;
     if (a.rcrit_mode == GENGA_RCRIT_EQ1) {
         rc = fmax(a.rc_eq1[i], a.rc_eq1[j]);
     } else {
-        rc = a.n1 * cbrt((a.m[i] + a.m[j]) / (3.0 * a.Mstar)) * 0.5 * (a.a_osc[i] + a.a_osc[j]);
+        rc = a.n1 * cbrt((a.m[oi] + a.m[oj]) / (3.0 * a.Mstar)) * 0.5 * (a.a_osc[i] + a.a_osc[j]);
     }
     double K = 1.0;
     if (r < rc) {
-        if (i < j) {
+        if (oi < oj) {
             const int pos = atomicAdd(a.enc_count, 1);
-            if (pos < a.enc_cap) a.enc[pos] = make_int2(i, j);
+            if (pos < a.enc_cap) a.enc[pos] = make_int2(oi, oj);
         }
         K = changeover_K((r / rc - 0.1) / 0.9, a.changeover);
     }
@@ -102,128 +111,234 @@ __device__ __forceinline__ float screen_threshold(float H, float A, float Hm, fl
     return fmaxf(b * b * (1.0f + 0x1p-10f), 1e-30f);
 }
 
-template <int TILE>
-__device__ __forceinline__ float2 tile_maxima(const float2 *__restrict__ tm, int t) {
-    float Hm = 0.f, Am = 0.f;
+struct Box {      // bounding box of FP32 positions; w components: max H (lo), max A (hi)
+    float4 lo, hi;
+};
+
+template <int NG>
+__device__ __forceinline__ Box group_box(const float4 *__restrict__ glo, const float4 *__restrict__ ghi, int g0) {
+    Box b = {glo[g0], ghi[g0]};
 #pragma unroll
-    for (int q = 0; q < TILE / 64; q++) {
-        const float2 v = tm[t * (TILE / 64) + q];
-        Hm = fmaxf(Hm, v.x);
-        Am = fmaxf(Am, v.y);
+    for (int q = 1; q < NG; q++) {
+        const float4 l = glo[g0 + q], h = ghi[g0 + q];
+        b.lo = make_float4(fminf(b.lo.x, l.x), fminf(b.lo.y, l.y), fminf(b.lo.z, l.z), fmaxf(b.lo.w, l.w));
+        b.hi = make_float4(fmaxf(b.hi.x, h.x), fmaxf(b.hi.y, h.y), fmaxf(b.hi.z, h.z), fmaxf(b.hi.w, h.w));
     }
-    return make_float2(Hm, Am);
+    return b;
+}
+
+// True when every pair between the two boxes has K = 1 and (if fp32) offsets
+// that FP32-rounded positions give to better than ~5e-6 relative.
+__device__ __forceinline__ bool far_pair_of_boxes(const Box &u, const Box &v, bool fp32) {
+    const bool empty_u = u.lo.x > u.hi.x, empty_v = v.lo.x > v.hi.x;
+    if (empty_u || empty_v) return true;
+    const float gx = fmaxf(0.f, fmaxf(v.lo.x - u.hi.x, u.lo.x - v.hi.x));
+    const float gy = fmaxf(0.f, fmaxf(v.lo.y - u.hi.y, u.lo.y - v.hi.y));
+    const float gz = fmaxf(0.f, fmaxf(v.lo.z - u.hi.z, u.lo.z - v.hi.z));
+    const float gap2 = gx * gx + gy * gy + gz * gz;
+    float need = fmaxf(u.lo.w, v.lo.w) * fmaxf(u.hi.w, v.hi.w) * (1.0f + 0x1p-10f);  // r_crit bound
+    if (fp32) {
+        const float X = fmaxf(fmaxf(fmaxf(fabsf(u.lo.x), fabsf(u.hi.x)), fmaxf(fabsf(u.lo.y), fabsf(u.hi.y))),
+                              fmaxf(fmaxf(fabsf(u.lo.z), fabsf(u.hi.z)),
+                                    fmaxf(fmaxf(fmaxf(fabsf(v.lo.x), fabsf(v.hi.x)),
+                                                fmaxf(fabsf(v.lo.y), fabsf(v.hi.y))),
+                                          fmaxf(fabsf(v.lo.z), fabsf(v.hi.z)))));
+        need = fmaxf(need, 0.025f * X);
+    }
+    return gap2 > need * need;
 }
 
 // ----------------------------------------------------------- FP32 pass ----
-template <int BPT, int TILE, int STAGES>
-__global__ void __launch_bounds__(KB, 2) pass_fp32_kernel(const __grid_constant__ PassArgs a) {
+// Persistent and warp-specialised.  Work items are (i-block, chunk of
+// chunk_tiles j-tiles), handed out by a global counter, so busy regions of
+// the disc do not hold up the rest of the GPU.  One producer warp fetches
+// items and fills a STAGES-deep ring of j-tiles with bulk copies (mbarrier
+// "full" per slot, with a small header naming the item and tile); eight
+// consumer warps compute and release each slot on its "empty" mbarrier, so
+// warps with more NEAR work fall behind by up to STAGES tiles without
+// stalling the others.  Each item's result goes to its own partial row
+// (chunk, body), so the combined sum does not depend on which CTA ran it.
+// FAR/NEAR is decided per (warp, 64-body group of the tile).  Registers hold
+// only the FP32-rounded i positions and FP32 tile sums; FP64 per-body sums
+// live in shared memory, touched once per tile.
+constexpr int F32_CONS_WARPS = 8;
+constexpr int F32_THREADS = (F32_CONS_WARPS + 1) * 32;
+
+struct StageHdr {
+    int item, tile, flags, pad;  // flags: 1 first tile of item, 2 last tile, 4 no more work
+};
+
+template <int BPT, int TILE, int STAGES, int MINB, int UNR>
+__global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __grid_constant__ PassArgs a) {
+    constexpr int NC = F32_CONS_WARPS * 32;  // consumer threads
+    constexpr int IB = NC * BPT;             // i-bodies per item (the last i-block may be partial)
+    constexpr int NG = TILE / 64;            // 64-body groups per tile
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float4 *s_hi = reinterpret_cast<float4 *>(smem_raw);
     float4 *s_lo = s_hi + STAGES * TILE;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(s_lo + STAGES * TILE);
-    __shared__ int s_abort;
+    uint64_t *full = reinterpret_cast<uint64_t *>(s_lo + STAGES * TILE);
+    uint64_t *empty = full + STAGES;
+    StageHdr *hdr = reinterpret_cast<StageHdr *>(empty + STAGES);
+    __shared__ double s_acc[3 * BPT * NC];  // [c][k][thread]
 
-    const int tid = threadIdx.x;
-    const int ibase = blockIdx.x * (KB * BPT);
-    const int slice = blockIdx.y;
-    const int t0 = (int)((long long)a.ntiles * slice / a.split);
-    const int t1 = (int)((long long)a.ntiles * (slice + 1) / a.split);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nchunks = a.split;
+    const int nitems = ((a.npad + IB - 1) / IB) * nchunks;
 
-    float xh[BPT], yh[BPT], zh[BPT], xl[BPT], yl[BPT], zl[BPT], H[BPT], A[BPT];
-    double AX[BPT], AY[BPT], AZ[BPT];
-#pragma unroll
-    for (int k = 0; k < BPT; k++) {
-        const int i = ibase + k * KB + tid;
-        const float4 h = a.hi[i], l = a.lo[i];
-        const float2 s = a.scr[i];
-        xh[k] = h.x; yh[k] = h.y; zh[k] = h.z;
-        xl[k] = l.x; yl[k] = l.y; zl[k] = l.z;
-        H[k] = s.x; A[k] = s.y;
-        AX[k] = AY[k] = AZ[k] = 0.0;
-    }
-
-    constexpr uint32_t TB = TILE * sizeof(float4);
     if (tid == 0) {
-        for (int s = 0; s < STAGES; s++) mbar_init(&bars[s], 1);
+        for (int q = 0; q < STAGES; q++) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], F32_CONS_WARPS);
+        }
         fence_barrier_init();
-        s_abort = 0;
     }
     __syncthreads();
-    if (tid == 0) {
-        for (int s = 0; s < STAGES - 1 && t0 + s < t1; s++) {
-            mbar_arrive_expect_tx(&bars[s], 2 * TB);
-            bulk_g2s(s_hi + s * TILE, a.hi + (size_t)(t0 + s) * TILE, TB, &bars[s]);
-            bulk_g2s(s_lo + s * TILE, a.lo + (size_t)(t0 + s) * TILE, TB, &bars[s]);
+
+    if (warp == F32_CONS_WARPS) {  // ------------------------------ producer
+        if (lane != 0) return;
+        constexpr uint32_t TB = TILE * sizeof(float4);
+        unsigned n = 0;
+        for (;;) {
+            const int q = atomicAdd(a.work, 1);
+            if (q >= nitems) {
+                const int slot = n % STAGES;
+                const unsigned u = n / STAGES;
+                if (u > 0 && !mbar_wait_bounded(&empty[slot], (u - 1) & 1, a.status)) return;
+                hdr[slot] = StageHdr{q, 0, 4, 0};
+                mbar_arrive(&full[slot]);
+                return;
+            }
+            const int chunk = q % nchunks;
+            const int ta = chunk * a.chunk_tiles, tb = min(a.ntiles, ta + a.chunk_tiles);
+            for (int t = ta; t < tb; t++, n++) {
+                const int slot = n % STAGES;
+                const unsigned u = n / STAGES;
+                if (u > 0 && !mbar_wait_bounded(&empty[slot], (u - 1) & 1, a.status)) return;
+                hdr[slot] = StageHdr{q, t, (t == ta ? 1 : 0) | (t == tb - 1 ? 2 : 0), 0};
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&full[slot], 2 * TB);
+                bulk_g2s(s_hi + slot * TILE, a.hi + (size_t)t * TILE, TB, &full[slot]);
+                bulk_g2s(s_lo + slot * TILE, a.lo + (size_t)t * TILE, TB, &full[slot]);
+            }
         }
     }
 
-    for (int t = t0; t < t1; t++) {
-        const int it = t - t0;
-        const int stage = it % STAGES;
-        if (tid == 0) {
-            const int tn = t + STAGES - 1;
-            if (tn < t1) {
-                const int sn = (it + STAGES - 1) % STAGES;
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&bars[sn], 2 * TB);
-                bulk_g2s(s_hi + sn * TILE, a.hi + (size_t)tn * TILE, TB, &bars[sn]);
-                bulk_g2s(s_lo + sn * TILE, a.lo + (size_t)tn * TILE, TB, &bars[sn]);
+    // ---------------------------------------------------------- consumers
+    float xh[BPT], yh[BPT], zh[BPT];
+#pragma unroll
+    for (int k = 0; k < BPT; k++) xh[k] = yh[k] = zh[k] = 0.f;
+    Box wbox = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    int wbase = 0;
+    for (unsigned n = 0;; n++) {
+        const int slot = n % STAGES;
+        if (!mbar_wait_bounded(&full[slot], (n / STAGES) & 1, a.status)) return;
+        const StageHdr h = hdr[slot];
+        if (h.flags & 4) return;
+        if (h.flags & 1) {  // first tile of an item: load this warp's i-bodies
+            wbase = (h.item / nchunks) * IB + warp * 32 * BPT;
+            const bool in = wbase < a.npad;  // warps past the padded end hold dummy bodies
+#pragma unroll
+            for (int k = 0; k < BPT; k++) {
+                const float4 p = in ? a.hi[wbase + k * 32 + lane] : make_float4(GENGA_PAD_POS, 0.f, 0.f, 0.f);
+                xh[k] = p.x; yh[k] = p.y; zh[k] = p.z;
+#pragma unroll
+                for (int c = 0; c < 3; c++) s_acc[(c * BPT + k) * NC + tid] = 0.0;
+            }
+            if (in) {
+                wbox = group_box<BPT / 2>(a.gbox_lo, a.gbox_hi, wbase / 64);
+            } else {  // empty box: every tile is FAR, nothing is written
+                const float INF = __int_as_float(0x7f800000);
+                wbox = {make_float4(INF, INF, INF, 0.f), make_float4(-INF, -INF, -INF, 0.f)};
             }
         }
-        const float2 tm = tile_maxima<TILE>(a.tile_max, t);
-        float thr[BPT];
-#pragma unroll
-        for (int k = 0; k < BPT; k++) thr[k] = screen_threshold(H[k], A[k], tm.x, tm.y);
-
-        if (!mbar_wait_bounded(&bars[stage], (uint32_t)((it / STAGES) & 1), a.status)) s_abort = 1;
-
         float ax[BPT], ay[BPT], az[BPT];
 #pragma unroll
         for (int k = 0; k < BPT; k++) ax[k] = ay[k] = az[k] = 0.f;
-        const float4 *th = s_hi + stage * TILE;
-        const float4 *tl = s_lo + stage * TILE;
-#pragma unroll 2
-        for (int jj = 0; jj < TILE; jj++) {
-            const float4 ph = th[jj];
-            const float4 pl = tl[jj];
+        for (int g = 0; g < NG; g++) {
+            const int gidx = h.tile * NG + g;
+            const Box gb = {a.gbox_lo[gidx], a.gbox_hi[gidx]};
+            const float4 *th = s_hi + slot * TILE + g * 64;
+            if (far_pair_of_boxes(wbox, gb, true)) {
+                // every pair: K = 1, FP32-rounded positions accurate enough
+#pragma unroll(UNR)
+                for (int jj = 0; jj < 64; jj++) {
+                    const float4 ph = th[jj];
 #pragma unroll
-            for (int k = 0; k < BPT; k++) {
-                const float dx = (ph.x - xh[k]) + (pl.x - xl[k]);
-                const float dy = (ph.y - yh[k]) + (pl.y - yl[k]);
-                const float dz = (ph.z - zh[k]) + (pl.z - zl[k]);
-                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                const float ri = rsqrt_sfu(r2);
-                float s = (ph.w * ri) * (ri * ri);
-                if (r2 < thr[k]) {
-                    const double3 f = screened_pair(a, ibase + k * KB + tid, t * TILE + jj);
-                    AX[k] += f.x;
-                    AY[k] += f.y;
-                    AZ[k] += f.z;
-                    s = 0.f;
+                    for (int k = 0; k < BPT; k++) {
+                        const float dx = ph.x - xh[k];
+                        const float dy = ph.y - yh[k];
+                        const float dz = ph.z - zh[k];
+                        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                        const float ri = rsqrt_sfu(r2);
+                        const float s = (ph.w * ri) * (ri * ri);
+                        ax[k] = fmaf(s, dx, ax[k]);
+                        ay[k] = fmaf(s, dy, ay[k]);
+                        az[k] = fmaf(s, dz, az[k]);
+                    }
                 }
-                ax[k] = fmaf(s, dx, ax[k]);
-                ay[k] = fmaf(s, dy, ay[k]);
-                az[k] = fmaf(s, dz, az[k]);
+            } else {
+                const float4 *tl = s_lo + slot * TILE + g * 64;
+                float xl[BPT], yl[BPT], zl[BPT], thr[BPT];
+#pragma unroll
+                for (int k = 0; k < BPT; k++) {
+                    const int i = wbase + k * 32 + lane;
+                    const float4 l = a.lo[i];
+                    const float2 sc = a.scr[i];
+                    xl[k] = l.x; yl[k] = l.y; zl[k] = l.z;
+                    thr[k] = screen_threshold(sc.x, sc.y, gb.lo.w, gb.hi.w);
+                }
+#pragma unroll 2
+                for (int jj = 0; jj < 64; jj++) {
+                    const float4 ph = th[jj];
+                    const float4 pl = tl[jj];
+                    unsigned screened = 0u;  // bit k: pair (i_k, j) is under the screening bound
+#pragma unroll
+                    for (int k = 0; k < BPT; k++) {
+                        const float dx = (ph.x - xh[k]) + (pl.x - xl[k]);
+                        const float dy = (ph.y - yh[k]) + (pl.y - yl[k]);
+                        const float dz = (ph.z - zh[k]) + (pl.z - zl[k]);
+                        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                        const float ri = rsqrt_sfu(r2);
+                        const bool near = r2 < thr[k];
+                        screened |= (unsigned)near << k;
+                        const float s = near ? 0.f : (ph.w * ri) * (ri * ri);
+                        ax[k] = fmaf(s, dx, ax[k]);
+                        ay[k] = fmaf(s, dy, ay[k]);
+                        az[k] = fmaf(s, dz, az[k]);
+                    }
+                    if (screened) {  // rare: these pairs are evaluated exactly, in FP64
+#pragma unroll
+                        for (int k = 0; k < BPT; k++) {
+                            if (screened & (1u << k)) {
+                                const double3 f =
+                                    screened_pair(a, wbase + k * 32 + lane, h.tile * TILE + g * 64 + jj);
+                                s_acc[(0 * BPT + k) * NC + tid] += f.x;
+                                s_acc[(1 * BPT + k) * NC + tid] += f.y;
+                                s_acc[(2 * BPT + k) * NC + tid] += f.z;
+                            }
+                        }
+                    }
+                }
             }
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);  // this warp is done reading the slot
 #pragma unroll
         for (int k = 0; k < BPT; k++) {
-            AX[k] += (double)ax[k];
-            AY[k] += (double)ay[k];
-            AZ[k] += (double)az[k];
+            s_acc[(0 * BPT + k) * NC + tid] += (double)ax[k];
+            s_acc[(1 * BPT + k) * NC + tid] += (double)ay[k];
+            s_acc[(2 * BPT + k) * NC + tid] += (double)az[k];
         }
-        __syncthreads();
-        if (s_abort) break;
-    }
-
-    const size_t np = (size_t)a.npad;
-    double *out = a.partial + (size_t)slice * 3 * np;
+        if ((h.flags & 2) && wbase < a.npad) {  // last tile of the item: write its partial row
+            const size_t np = (size_t)a.npad;
+            double *out = a.partial + (size_t)(h.item % nchunks) * 3 * np;
 #pragma unroll
-    for (int k = 0; k < BPT; k++) {
-        const int i = ibase + k * KB + tid;
-        out[i] = AX[k];
-        out[np + i] = AY[k];
-        out[2 * np + i] = AZ[k];
+            for (int k = 0; k < BPT; k++) {
+                const int i = wbase + k * 32 + lane;
+#pragma unroll
+                for (int c = 0; c < 3; c++) out[c * np + i] = s_acc[(c * BPT + k) * NC + tid];
+            }
+        }
     }
 }
 
@@ -244,8 +359,9 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
     uint64_t *bars = reinterpret_cast<uint64_t *>(s_p + STAGES * TILE);
     __shared__ int s_abort;
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ibase = blockIdx.x * (KB * BPT);
+    const int wbase = ibase + warp * 32 * BPT;
     const int slice = blockIdx.y;
     const int t0 = (int)((long long)a.ntiles * slice / a.split);
     const int t1 = (int)((long long)a.ntiles * (slice + 1) / a.split);
@@ -255,13 +371,14 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
     Comp CX[BPT], CY[BPT], CZ[BPT];
 #pragma unroll
     for (int k = 0; k < BPT; k++) {
-        const int i = ibase + k * KB + tid;
+        const int i = wbase + k * 32 + lane;
         const double4_32a p = a.p64[i];
         const float2 s = a.scr[i];
         xi[k] = p.x; yi[k] = p.y; zi[k] = p.z;
         H[k] = s.x; A[k] = s.y;
         CX[k] = CY[k] = CZ[k] = Comp{0.0, 0.0};
     }
+    const Box wbox = group_box<(BPT + 1) / 2>(a.gbox_lo, a.gbox_hi, wbase / 64);
 
     constexpr uint32_t TB = TILE * sizeof(double4_32a);
     if (tid == 0) {
@@ -289,10 +406,11 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
                 bulk_g2s(s_p + sn * TILE, a.p64 + (size_t)tn * TILE, TB, &bars[sn]);
             }
         }
-        const float2 tm = tile_maxima<TILE>(a.tile_max, t);
+        const Box tbox = group_box<TILE / 64>(a.gbox_lo, a.gbox_hi, t * (TILE / 64));
+        const bool far = far_pair_of_boxes(wbox, tbox, false);
         double thr[BPT];
 #pragma unroll
-        for (int k = 0; k < BPT; k++) thr[k] = (double)screen_threshold(H[k], A[k], tm.x, tm.y);
+        for (int k = 0; k < BPT; k++) thr[k] = (double)screen_threshold(H[k], A[k], tbox.lo.w, tbox.hi.w);
 
         if (!mbar_wait_bounded(&bars[stage], (uint32_t)((it / STAGES) & 1), a.status)) s_abort = 1;
 
@@ -301,25 +419,49 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
             double px[BPT], py[BPT], pz[BPT];
 #pragma unroll
             for (int k = 0; k < BPT; k++) px[k] = py[k] = pz[k] = 0.0;
+            if (far) {
 #pragma unroll 2
-            for (int jj = j0; jj < j0 + 32; jj++) {
-                const double4_32a pj = tp[jj];
+                for (int jj = j0; jj < j0 + 32; jj++) {
+                    const double4_32a pj = tp[jj];
 #pragma unroll
-                for (int k = 0; k < BPT; k++) {
-                    const double dx = pj.x - xi[k], dy = pj.y - yi[k], dz = pj.z - zi[k];
-                    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-                    const double ri = rsqrt_fp64(r2);
-                    double s = (pj.w * ri) * (ri * ri);
-                    if (r2 < thr[k]) {
-                        const double3 f = screened_pair(a, ibase + k * KB + tid, t * TILE + jj);
-                        CX[k].add(f.x);
-                        CY[k].add(f.y);
-                        CZ[k].add(f.z);
-                        s = 0.0;
+                    for (int k = 0; k < BPT; k++) {
+                        const double dx = pj.x - xi[k], dy = pj.y - yi[k], dz = pj.z - zi[k];
+                        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+                        const double ri = rsqrt_fp64(r2);
+                        const double s = (pj.w * ri) * (ri * ri);
+                        px[k] = fma(s, dx, px[k]);
+                        py[k] = fma(s, dy, py[k]);
+                        pz[k] = fma(s, dz, pz[k]);
                     }
-                    px[k] = fma(s, dx, px[k]);
-                    py[k] = fma(s, dy, py[k]);
-                    pz[k] = fma(s, dz, pz[k]);
+                }
+            } else {
+#pragma unroll 2
+                for (int jj = j0; jj < j0 + 32; jj++) {
+                    const double4_32a pj = tp[jj];
+                    unsigned screened = 0u;
+#pragma unroll
+                    for (int k = 0; k < BPT; k++) {
+                        const double dx = pj.x - xi[k], dy = pj.y - yi[k], dz = pj.z - zi[k];
+                        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+                        const double ri = rsqrt_fp64(r2);
+                        const bool near = r2 < thr[k];
+                        screened |= (unsigned)near << k;
+                        const double s = near ? 0.0 : (pj.w * ri) * (ri * ri);
+                        px[k] = fma(s, dx, px[k]);
+                        py[k] = fma(s, dy, py[k]);
+                        pz[k] = fma(s, dz, pz[k]);
+                    }
+                    if (screened) {
+#pragma unroll
+                        for (int k = 0; k < BPT; k++) {
+                            if (screened & (1u << k)) {
+                                const double3 f = screened_pair(a, wbase + k * 32 + lane, t * TILE + jj);
+                                CX[k].add(f.x);
+                                CY[k].add(f.y);
+                                CZ[k].add(f.z);
+                            }
+                        }
+                    }
                 }
             }
 #pragma unroll
@@ -337,7 +479,7 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
     double *out = a.partial + (size_t)slice * 3 * np;
 #pragma unroll
     for (int k = 0; k < BPT; k++) {
-        const int i = ibase + k * KB + tid;
+        const int i = wbase + k * 32 + lane;
         out[i] = CX[k].s + CX[k].c;
         out[np + i] = CY[k].s + CY[k].c;
         out[2 * np + i] = CZ[k].s + CZ[k].c;
@@ -345,19 +487,21 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
 }
 
 // ------------------------------------------------------------ combine ----
-// acc_i = sum over slices (Neumaier, slice order); optional acc output and
-// v_i += acc_i * tau; non-finite accelerations raise GENGA_ERR_NONFINITE.
-__global__ void combine_kernel(const double *__restrict__ partial, int split, int N, int npad, double tau,
-                               double *__restrict__ acc, double *__restrict__ vx, double *__restrict__ vy,
-                               double *__restrict__ vz, uint32_t *__restrict__ status) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+// acc of body perm[k] = sum over slices (Neumaier, slice order); optional acc
+// output and v += acc * tau; non-finite accelerations raise NONFINITE.
+__global__ void combine_kernel(const double *__restrict__ partial, int split, int N, int npad,
+                               const uint32_t *__restrict__ perm, double tau, double *__restrict__ acc,
+                               double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
+                               uint32_t *__restrict__ status) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int i = (int)perm[k];
     double a3[3];
     bool finite = true;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         Comp s{0.0, 0.0};
-        for (int q = 0; q < split; q++) s.add(partial[((size_t)q * 3 + c) * npad + i]);
+        for (int q = 0; q < split; q++) s.add(partial[((size_t)q * 3 + c) * npad + k]);
         a3[c] = s.s + s.c;
         finite = finite && isfinite(a3[c]);
     }
@@ -422,12 +566,11 @@ __global__ void __launch_bounds__(SORT_THREADS) sort_pairs_kernel(int2 *__restri
                 const int p = q ^ j;
                 if (p > q) {
                     const bool up = (q & k) == 0;
-                    const int2 a = enc[q], b = enc[p];
-                    const unsigned long long u = pair_key(a), v = pair_key(b);
-                    if ((u > v) == up) { enc[q] = b; enc[p] = a; }
+                    const int2 u2 = enc[q], v2 = enc[p];
+                    const unsigned long long u = pair_key(u2), v = pair_key(v2);
+                    if ((u > v) == up) { enc[q] = v2; enc[p] = u2; }
                 }
             }
-            __threadfence_block();
             __syncthreads();
         }
     }
@@ -451,55 +594,98 @@ __global__ void copy_pairs_kernel(const int2 *__restrict__ enc, const int32_t *_
 }
 
 // ------------------------------------------------------------ variants ----
-template <int BPT, int TILE, int STAGES>
-size_t smem_fp32() { return (size_t)STAGES * TILE * 2 * sizeof(float4) + STAGES * sizeof(uint64_t); }
-template <int BPT, int TILE, int STAGES>
-size_t smem_fp64() { return (size_t)STAGES * TILE * sizeof(double4_32a) + STAGES * sizeof(uint64_t); }
+constexpr int F32_TILE = 256, F32_STAGES = 4;
 
-constexpr int F32_BPT = 4, F32_TILE = 256, F32_STAGES = 3;
+// FP32 pass variants (bodies per thread, CTAs per SM, FAR-loop unroll); the
+// autotuner in api.cu times them per N bucket and keeps the fastest.
+struct F32Variant {
+    int bpt, minb;
+    void (*fn)(const PassArgs);
+};
+const F32Variant kF32Variants[] = {
+    {4, 1, pass_fp32_kernel<4, F32_TILE, F32_STAGES, 1, 4>},
+    {4, 2, pass_fp32_kernel<4, F32_TILE, F32_STAGES, 2, 2>},
+    {8, 1, pass_fp32_kernel<8, F32_TILE, F32_STAGES, 1, 2>},
+    {2, 2, pass_fp32_kernel<2, F32_TILE, F32_STAGES, 2, 4>},
+};
+constexpr int kNumF32Variants = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 constexpr int F64_BPT = 2, F64_TILE = 128, F64_STAGES = 3;
+
+size_t smem_fp32() {
+    return (size_t)F32_STAGES * F32_TILE * 2 * sizeof(float4) + 2 * F32_STAGES * sizeof(uint64_t) +
+           F32_STAGES * sizeof(StageHdr);
+}
+size_t smem_fp64() { return (size_t)F64_STAGES * F64_TILE * sizeof(double4_32a) + F64_STAGES * sizeof(uint64_t); }
 
 }  // namespace
 
-int choose_split(int N, int precision, int sm_count, int max_split) {
+// Work decomposition of one pass.  FP32 (persistent): about eight work items
+// per resident CTA; split is the number of j-chunks per i-block and
+// chunk_tiles their length; grid = resident CTAs.  FP64: `split` contiguous
+// j-slices per i-block, one CTA each, sized to one wave of two CTAs per SM.
+// In both cases split * 3 * npad doubles of partial sums fit in partial_cap.
+int num_fp32_variants() { return kNumF32Variants; }
+
+void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_cap, int *split, int *chunk_tiles,
+               int *grid) {
     const int npad = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
-    const int bpt = (precision == GENGA_FP32) ? F32_BPT : F64_BPT;
-    const int tile = (precision == GENGA_FP32) ? F32_TILE : F64_TILE;
-    const int iblocks = npad / (KB * bpt);
+    const bool f32 = precision == GENGA_FP32;
+    const F32Variant &v = kF32Variants[variant];
+    const int tile = f32 ? F32_TILE : F64_TILE;
     const int ntiles = npad / tile;
-    const int want = 2 * sm_count;                  // two resident CTAs per SM
-    int split = (want + iblocks - 1) / iblocks;
-    split = split < 1 ? 1 : split;
-    split = split > ntiles ? ntiles : split;
-    split = split > max_split ? max_split : split;
-    return split;
+    const int ib = f32 ? F32_CONS_WARPS * 32 * v.bpt : KB * F64_BPT;
+    const int iblocks = (npad + ib - 1) / ib;
+    const int cap = (int)(partial_cap / (3 * (size_t)npad));
+    int sp;
+    if (f32) {
+        const int want_items = 8 * v.minb * sm_count;
+        sp = (want_items + iblocks - 1) / iblocks;
+    } else {
+        sp = 2 * sm_count / iblocks;
+    }
+    sp = sp < 1 ? 1 : sp;
+    sp = sp > ntiles ? ntiles : sp;
+    sp = sp > cap ? cap : sp;
+    sp = sp < 1 ? 1 : sp;
+    const int ct = (ntiles + sp - 1) / sp;
+    *chunk_tiles = ct;
+    *split = f32 ? (ntiles + ct - 1) / ct : sp;
+    const int nitems = iblocks * *split;
+    *grid = f32 ? (nitems < v.minb * sm_count ? nitems : v.minb * sm_count) : iblocks;
 }
 
-cudaError_t launch_pass(const PassArgs &a0, int precision, int sm_count, cudaStream_t s) {
-    (void)sm_count;
+// Dynamic shared memory above the 48 KB default needs an opt-in per kernel
+// (the FP32 pass also holds its FP64 accumulators in static shared memory).
+cudaError_t init_pass_kernels() {
+    for (int q = 0; q < kNumF32Variants; q++) {
+        cudaError_t e = cudaFuncSetAttribute(kF32Variants[q].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_fp32());
+        if (e != cudaSuccess) return e;
+    }
+    return cudaFuncSetAttribute(pass_fp64_kernel<F64_BPT, F64_TILE, F64_STAGES>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fp64());
+}
+
+cudaError_t launch_pass(const PassArgs &a0, int precision, int variant, int grid, cudaStream_t s) {
     PassArgs a = a0;
     if (precision == GENGA_FP32) {
         a.ntiles = a.npad / F32_TILE;
-        auto k = pass_fp32_kernel<F32_BPT, F32_TILE, F32_STAGES>;
-        const size_t sm = smem_fp32<F32_BPT, F32_TILE, F32_STAGES>();
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        dim3 grid(a.npad / (KB * F32_BPT), a.split);
-        k<<<grid, KB, sm, s>>>(a);
+        cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s);
+        if (e != cudaSuccess) return e;
+        kF32Variants[variant].fn<<<grid, F32_THREADS, smem_fp32(), s>>>(a);
     } else {
         a.ntiles = a.npad / F64_TILE;
         auto k = pass_fp64_kernel<F64_BPT, F64_TILE, F64_STAGES>;
-        const size_t sm = smem_fp64<F64_BPT, F64_TILE, F64_STAGES>();
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        dim3 grid(a.npad / (KB * F64_BPT), a.split);
-        k<<<grid, KB, sm, s>>>(a);
+        dim3 g(grid, a.split);
+        k<<<g, KB, smem_fp64(), s>>>(a);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine(const double *partial, int split, int N, int npad, double tau, double *acc,
-                           double *vx, double *vy, double *vz, uint32_t *status, cudaStream_t s) {
+cudaError_t launch_combine(const double *partial, int split, int N, int npad, const uint32_t *perm, double tau,
+                           double *acc, double *vx, double *vy, double *vz, uint32_t *status, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    combine_kernel<<<(N + 255) / 256, 256, 0, s>>>(partial, split, N, npad, tau, acc, vx, vy, vz, status);
+    combine_kernel<<<(N + 255) / 256, 256, 0, s>>>(partial, split, N, npad, perm, tau, acc, vx, vy, vz, status);
     return cudaGetLastError();
 }
 

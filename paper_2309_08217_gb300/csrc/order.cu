@@ -1,0 +1,170 @@
+// order.cu -- spatial order of the bodies for the long-range pass.
+//
+// Bodies are sorted along a 3-D Morton curve (10 bits per axis over the cube
+// [-R, R]^3, R = the largest |coordinate|), so that a warp's 128 i-bodies and
+// a 256-body j-tile each cover a compact region; the pass kernels then test
+// (warp, tile) bounding boxes and run most tiles without per-pair screening.
+// The order only changes which pairs share a tile, never which pairs are
+// summed, so it affects speed, not the definition of the result.
+//
+// The sort is a stable least-significant-digit radix sort of the 30-bit keys
+// with 10-bit digits (three passes of histogram / scan / scatter).  Stable
+// ranks inside a CTA come from warp match masks and per-warp digit counts, so
+// the permutation is the same on every run.
+#include "internal.cuh"
+
+namespace genga {
+
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 4;
+constexpr int RS_CHUNK = RS_THREADS * RS_ITEMS;  // keys per CTA
+constexpr int RS_BITS = 10;
+constexpr int RS_BINS = 1 << RS_BITS;
+constexpr int RS_WARPS = RS_THREADS / 32;
+
+// R = max |coordinate| (as float bits: non-negative floats order like uints).
+__global__ void extent_kernel(const double *__restrict__ x, const double *__restrict__ y,
+                              const double *__restrict__ z, int N, unsigned *__restrict__ rbits) {
+    float r = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        r = fmaxf(r, fmaxf(fabsf((float)x[i]), fmaxf(fabsf((float)y[i]), fabsf((float)z[i]))));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(rbits, __float_as_uint(r));
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 10 bits -> every third bit
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t quant10(double c, float inv) {
+    float f = ((float)c * inv + 1.0f) * 512.0f;
+    f = fminf(fmaxf(f, 0.0f), 1023.0f);
+    return (uint32_t)f;
+}
+
+__global__ void keys_kernel(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                            int N, const unsigned *__restrict__ rbits, uint32_t *__restrict__ keys,
+                            uint32_t *__restrict__ vals) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float R = fmaxf(__uint_as_float(*rbits), 1e-30f) * 1.0001f;
+    const float inv = 1.0f / R;
+    keys[i] = spread3(quant10(x[i], inv)) | (spread3(quant10(y[i], inv)) << 1) |
+              (spread3(quant10(z[i], inv)) << 2);
+    vals[i] = (uint32_t)i;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) hist_kernel(const uint32_t *__restrict__ keys, int n, int shift,
+                                                          uint32_t *__restrict__ hist, int nblk) {
+    __shared__ uint32_t h[RS_BINS];
+    for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) h[b] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * RS_CHUNK;
+#pragma unroll
+    for (int q = 0; q < RS_ITEMS; q++) {
+        const int i = base + q * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & (RS_BINS - 1)], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) hist[b * nblk + blockIdx.x] = h[b];
+}
+
+// Exclusive scan of hist[0 .. total) in place, one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) scan_kernel(uint32_t *__restrict__ hist, int total) {
+    __shared__ uint32_t part[1024];
+    const int per = (total + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(total, lo + per);
+    uint32_t s = 0;
+    for (int q = lo; q < hi; q++) s += hist[q];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan of the partials
+        const uint32_t v = (threadIdx.x >= o) ? part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - s;
+    for (int q = lo; q < hi; q++) {
+        const uint32_t v = hist[q];
+        hist[q] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) scatter_kernel(const uint32_t *__restrict__ kin,
+                                                             const uint32_t *__restrict__ vin,
+                                                             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                             int n, int shift, const uint32_t *__restrict__ offs,
+                                                             int nblk) {
+    __shared__ uint32_t run[RS_BINS];
+    __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) run[b] = offs[b * nblk + blockIdx.x];
+    const int base = blockIdx.x * RS_CHUNK;
+    for (int q = 0; q < RS_ITEMS; q++) {
+        for (int e = threadIdx.x; e < RS_WARPS * RS_BINS; e += RS_THREADS) (&wcnt[0][0])[e] = 0u;
+        __syncthreads();
+        const int i = base + q * RS_THREADS + threadIdx.x;
+        const bool valid = i < n;
+        const uint32_t key = valid ? kin[i] : 0u;
+        const uint32_t d = valid ? ((key >> shift) & (RS_BINS - 1)) : (uint32_t)RS_BINS;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned lt = (1u << lane) - 1u;
+        const uint32_t rank = __popc(peers & lt);
+        if (valid && lane == __ffs(peers) - 1) wcnt[w][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t pre = 0;
+            for (int v = 0; v < w; v++) pre += wcnt[v][d];
+            const uint32_t pos = run[d] + pre + rank;
+            kout[pos] = key;
+            vout[pos] = vin[i];
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) {
+            uint32_t t = 0;
+            for (int v = 0; v < RS_WARPS; v++) t += wcnt[v][b];
+            run[b] += t;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t order_hist_entries(int nmax) { return (size_t)RS_BINS * ((nmax + RS_CHUNK - 1) / RS_CHUNK); }
+
+// perm[k] = index of the body at position k of the Morton order (k < N).
+cudaError_t launch_order(const genga_system &sys, genga_ctx *c, cudaStream_t s) {
+    const int N = sys.N;
+    if (N <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(c->ord_rbits, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    extent_kernel<<<64, 256, 0, s>>>(sys.x, sys.y, sys.z, N, c->ord_rbits);
+    keys_kernel<<<(N + 255) / 256, 256, 0, s>>>(sys.x, sys.y, sys.z, N, c->ord_rbits, c->ord_keys[0],
+                                                c->ord_vals[0]);
+    const int nblk = (N + RS_CHUNK - 1) / RS_CHUNK;
+    int cur = 0;
+    for (int pass = 0; pass < 3; pass++) {
+        const int shift = pass * RS_BITS;
+        hist_kernel<<<nblk, RS_THREADS, 0, s>>>(c->ord_keys[cur], N, shift, c->ord_hist, nblk);
+        scan_kernel<<<1, 1024, 0, s>>>(c->ord_hist, RS_BINS * nblk);
+        uint32_t *kout = (pass == 2) ? c->ord_keys[1 - cur] : c->ord_keys[1 - cur];
+        uint32_t *vout = (pass == 2) ? c->perm : c->ord_vals[1 - cur];
+        scatter_kernel<<<nblk, RS_THREADS, 0, s>>>(c->ord_keys[cur], c->ord_vals[cur], kout, vout, N, shift,
+                                                   c->ord_hist, nblk);
+        cur = 1 - cur;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace genga

@@ -5,19 +5,19 @@
 //     semi-major axis a_i (1/a = 2/r - v_hel^2 / mu_i, mu_i = G (M* + m_i),
 //     a_i = r_i for unbound orbits), heliocentric speed v_hel = |v + P/M*|,
 //     r_crit,i = max(n1 a_i (m_i / 3M*)^(1/3), n2 dt v_hel);
-//   * the packed copies the pass kernels read: FP32 hi/lo split of each
-//     position plus G m in FP32 (the single-precision kick of Sect. 1 takes
-//     its pair offsets from these), an FP64 {x, y, z, G m} record, and the
-//     FP32 screening factors {H_i, A_i} with r_crit,ij <= max(H_i, H_j) *
-//     max(A_i, A_j) for every pair (rounded up), plus their maxima per 64
-//     bodies.
+//   * the packed copies the pass kernels read, in the spatial (Morton) order
+//     of order.cu: FP32 hi/lo split of each position plus G m in FP32 (the
+//     single-precision kick of Sect. 1 takes its pair offsets from these),
+//     an FP64 {x, y, z, G m} record, and the FP32 screening factors
+//     {H_i, A_i} with r_crit,ij <= max(H_i, H_j) * max(A_i, A_j) for every
+//     pair (rounded up); per 64-body group, the bounding box of the FP32
+//     positions and the maxima of the screening factors.
 #include "internal.cuh"
 
 namespace genga {
 
 namespace {
 
-constexpr int MOM_THREADS = 1024;
 
 struct NSum {  // Neumaier running sum
     double s = 0.0, c = 0.0;
@@ -30,18 +30,26 @@ struct NSum {  // Neumaier running sum
     __device__ double value() const { return s + c; }
 };
 
-// One CTA: thread t sums bodies t, t + 1024, ... in order, then a fixed-shape
-// pairwise tree combines the 1024 partials.  The result does not depend on
+constexpr int MOM_BLOCKS = 64, MOM_THREADS = 256;
+
+// P = sum_j m_j v_j over MOM_BLOCKS CTAs (FP64 is slow on this part, so the
+// sum is spread over many SMs).  Block b sums a contiguous chunk: each thread
+// a strided Neumaier sum, then a fixed-shape tree; the last block to finish
+// adds the block partials in index order.  The result does not depend on
 // timing, so repeated runs are bitwise identical.
 __global__ void __launch_bounds__(MOM_THREADS) momentum_kernel(const double *__restrict__ vx,
                                                                const double *__restrict__ vy,
                                                                const double *__restrict__ vz,
                                                                const double *__restrict__ m, int N,
-                                                               double *__restrict__ P,
+                                                               double *__restrict__ P, double *__restrict__ part,
+                                                               unsigned *__restrict__ ticket,
                                                                int32_t *__restrict__ zero_me) {
     __shared__ double sh[3][MOM_THREADS];
+    __shared__ bool last;
+    const int chunk = (N + MOM_BLOCKS - 1) / MOM_BLOCKS;
+    const int lo = blockIdx.x * chunk, hi = min(N, lo + chunk);
     NSum px, py, pz;
-    for (int i = threadIdx.x; i < N; i += MOM_THREADS) {
+    for (int i = lo + threadIdx.x; i < hi; i += MOM_THREADS) {
         const double mi = m[i];
         px.add(mi * vx[i]);
         py.add(mi * vy[i]);
@@ -58,25 +66,42 @@ __global__ void __launch_bounds__(MOM_THREADS) momentum_kernel(const double *__r
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        P[0] = sh[0][0];
-        P[1] = sh[1][0];
-        P[2] = sh[2][0];
+        for (int c = 0; c < 3; c++) part[3 * blockIdx.x + c] = sh[c][0];
+        __threadfence();
+        last = (atomicAdd(ticket, 1u) == MOM_BLOCKS - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 3) {
+        NSum t;
+        const volatile double *vp = part;
+        for (int b = 0; b < MOM_BLOCKS; b++) t.add(vp[3 * b + threadIdx.x]);
+        P[threadIdx.x] = t.value();
+    }
+    if (threadIdx.x == 0) {
+        *ticket = 0u;
         if (zero_me) *zero_me = 0;
     }
 }
 
-constexpr int PREP_THREADS = 64;  // one block = one 64-body screening group
+constexpr int PREP_THREADS = 64;  // one block = one 64-body group
 
+// Position k of the packed arrays holds body perm[k] (the Morton order);
+// k >= N are padding bodies: zero mass, 64 au apart, far from everything.
 __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
     const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
     const double *__restrict__ vx, const double *__restrict__ vy, const double *__restrict__ vz,
-    const double *__restrict__ m, int N, const double *__restrict__ P, double G, double Mstar, double dt,
-    double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float4 *__restrict__ lo,
-    double4_32a *__restrict__ p64, float2 *__restrict__ scr, float2 *__restrict__ tile_max,
-    double *__restrict__ a_osc, double *__restrict__ rc_eq1) {
-    const int i = blockIdx.x * PREP_THREADS + threadIdx.x;
+    const double *__restrict__ m, int N, const uint32_t *__restrict__ perm, const double *__restrict__ P, double G,
+    double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float4 *__restrict__ lo,
+    double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
+    float4 *__restrict__ gbox_hi, double *__restrict__ a_osc, double *__restrict__ rc_eq1) {
+    const int k = blockIdx.x * PREP_THREADS + threadIdx.x;
     float2 s = make_float2(0.f, 0.f);
-    if (i < N) {
+    const float INF = __int_as_float(0x7f800000);
+    float3 bl = make_float3(INF, INF, INF), bh = make_float3(-INF, -INF, -INF);
+    if (k < N) {
+        const int i = (int)perm[k];
         const double xi = x[i], yi = y[i], zi = z[i], mi = m[i];
         const double ux = vx[i] + P[0] / Mstar;
         const double uy = vy[i] + P[1] / Mstar;
@@ -89,8 +114,8 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
         const double hill = n1 * a * cbrt(mi / (3.0 * Mstar));
         const double vel = n2 * dt * sqrt(v2);
         const double rc = fmax(hill, vel);
-        a_osc[i] = a;
-        rc_eq1[i] = rc;
+        a_osc[k] = a;
+        rc_eq1[k] = rc;
         if (rcrit_mode == GENGA_RCRIT_EQ1) {
             // r_crit,ij = max(rc_i, rc_j) = max(1, 1) * max(rc_i, rc_j)
             s = make_float2(1.0f, __double2float_ru(rc));
@@ -101,32 +126,48 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
         }
         const float hx = __double2float_rn(xi), hy = __double2float_rn(yi), hz = __double2float_rn(zi);
         const double gm = G * mi;
-        hi[i] = make_float4(hx, hy, hz, __double2float_rn(gm));
-        lo[i] = make_float4(__double2float_rn(xi - (double)hx), __double2float_rn(yi - (double)hy),
+        hi[k] = make_float4(hx, hy, hz, __double2float_rn(gm));
+        lo[k] = make_float4(__double2float_rn(xi - (double)hx), __double2float_rn(yi - (double)hy),
                             __double2float_rn(zi - (double)hz), 0.f);
-        p64[i] = make_double4_32a(xi, yi, zi, gm);
+        p64[k] = make_double4_32a(xi, yi, zi, gm);
+        bl = bh = make_float3(hx, hy, hz);
     } else {
-        hi[i] = make_float4(GENGA_PAD_POS, GENGA_PAD_POS, GENGA_PAD_POS, 0.f);
-        lo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        p64[i] = make_double4_32a(GENGA_PAD_POS, GENGA_PAD_POS, GENGA_PAD_POS, 0.0);
-        a_osc[i] = 0.0;
-        rc_eq1[i] = 0.0;
+        const float px = GENGA_PAD_POS + 64.0f * (float)(k - N);
+        hi[k] = make_float4(px, GENGA_PAD_POS, GENGA_PAD_POS, 0.f);
+        lo[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        p64[k] = make_double4_32a((double)px, GENGA_PAD_POS, GENGA_PAD_POS, 0.0);
+        a_osc[k] = 0.0;
+        rc_eq1[k] = 0.0;
     }
-    scr[i] = s;
-    // maxima of the screening factors over this block of 64 bodies
+    scr[k] = s;
+    // bounding box of the group's real bodies (FP32 hi positions) and the
+    // maxima of its screening factors
     float hmax = s.x, amax = s.y;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
         amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        bl.x = fminf(bl.x, __shfl_xor_sync(0xffffffffu, bl.x, o));
+        bl.y = fminf(bl.y, __shfl_xor_sync(0xffffffffu, bl.y, o));
+        bl.z = fminf(bl.z, __shfl_xor_sync(0xffffffffu, bl.z, o));
+        bh.x = fmaxf(bh.x, __shfl_xor_sync(0xffffffffu, bh.x, o));
+        bh.y = fmaxf(bh.y, __shfl_xor_sync(0xffffffffu, bh.y, o));
+        bh.z = fmaxf(bh.z, __shfl_xor_sync(0xffffffffu, bh.z, o));
     }
-    __shared__ float2 wm[PREP_THREADS / 32];
-    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = make_float2(hmax, amax);
+    __shared__ float4 wl[PREP_THREADS / 32], wh[PREP_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) {
+        wl[threadIdx.x >> 5] = make_float4(bl.x, bl.y, bl.z, hmax);
+        wh[threadIdx.x >> 5] = make_float4(bh.x, bh.y, bh.z, amax);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float2 t = wm[0];
-        for (int w = 1; w < PREP_THREADS / 32; w++) t = make_float2(fmaxf(t.x, wm[w].x), fmaxf(t.y, wm[w].y));
-        tile_max[blockIdx.x] = t;
+        float4 l = wl[0], h = wh[0];
+        for (int w = 1; w < PREP_THREADS / 32; w++) {
+            l = make_float4(fminf(l.x, wl[w].x), fminf(l.y, wl[w].y), fminf(l.z, wl[w].z), fmaxf(l.w, wl[w].w));
+            h = make_float4(fmaxf(h.x, wh[w].x), fmaxf(h.y, wh[w].y), fmaxf(h.z, wh[w].z), fmaxf(h.w, wh[w].w));
+        }
+        gbox_lo[blockIdx.x] = l;
+        gbox_hi[blockIdx.x] = h;
     }
 }
 
@@ -134,15 +175,18 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
 
 cudaError_t launch_momentum(const double *vx, const double *vy, const double *vz, const double *m, int N,
                             double *P, int32_t *zero_me, cudaStream_t s) {
-    momentum_kernel<<<1, MOM_THREADS, 0, s>>>(vx, vy, vz, m, N, P, zero_me);
+    // P[0..2] result, P[8..8+3*MOM_BLOCKS) block partials, ticket after them
+    momentum_kernel<<<MOM_BLOCKS, MOM_THREADS, 0, s>>>(vx, vy, vz, m, N, P, P + 8,
+                                                       reinterpret_cast<unsigned *>(P + 8 + 3 * MOM_BLOCKS),
+                                                       zero_me);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ctx *c, cudaStream_t s) {
     const int npad = (sys.N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
     prep_kernel<<<npad / PREP_THREADS, PREP_THREADS, 0, s>>>(
-        sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->mom, p.G, p.Mstar, p.dt, p.n1, p.n2,
-        p.rcrit_mode, c->pk_hi, c->pk_lo, c->pk64, c->scr, c->tile_max, c->a_osc, c->rc_eq1);
+        sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->perm, c->mom, p.G, p.Mstar, p.dt, p.n1,
+        p.n2, p.rcrit_mode, c->pk_hi, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->a_osc, c->rc_eq1);
     return cudaGetLastError();
 }
 

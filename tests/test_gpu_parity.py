@@ -78,6 +78,23 @@ def test_kick_parity_modes(genga, ctx, precision, mode, form):
     assert _rel_err(got, ref).max() <= TOL[precision]
 
 
+def test_every_fp32_variant(genga, ctx):
+    """Each FP32 pass variant the autotuner may pick meets the tolerance."""
+    d = planted_disc(5000, 8)
+    ref, _, _ = _oracle_acc(d)
+    _, nvar = genga.genga_get_kernel_variant(ctx, d.N)
+    assert nvar >= 2
+    try:
+        for v in range(nvar):
+            genga.genga_set_kernel_variant(ctx, v)
+            got, _ = _gpu_acc(genga, ctx, d, 1)
+            assert _rel_err(got, ref).max() <= TOL[1], f"variant {v}"
+    finally:
+        genga.genga_set_kernel_variant(ctx, -1)
+    with pytest.raises(genga.GengaError):
+        genga.genga_set_kernel_variant(ctx, nvar)
+
+
 def test_kick_embryos_mixed_masses(genga, ctx):
     d = discs.embryo_disc(25, 2000, seed=9)
     for precision in (0, 1):
