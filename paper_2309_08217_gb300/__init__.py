@@ -83,6 +83,7 @@ def load():
             "genga_profile_read": ([V, C.POINTER(C.c_double), C.POINTER(C.c_int32), I], I),
             "genga_measure_alu_peaks": ([I, C.POINTER(C.c_double), C.POINTER(C.c_double)], I),
             "genga_set_kernel_variant": ([V, I], I),
+            "genga_kick_noalloc": ([S, P, D, V, V], I),
             "genga_get_kernel_variant": ([V, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], I),
         }
         for name, (args, res) in sigs.items():
@@ -247,3 +248,15 @@ def genga_get_kernel_variant(ctx, N):
     v, n = C.c_int32(), C.c_int32()
     _check(load().genga_get_kernel_variant(_ctx(ctx), int(N), C.byref(v), C.byref(n)), "genga_get_kernel_variant")
     return v.value, n.value
+
+
+# ------------------------------------------- kick without device allocation ---
+GENGA_NOALLOC_MAX_N = 65536
+
+
+def genga_kick_noalloc(sys, params, tau=0.0, acc=None, stream=None):
+    """FP64 kick on the current device with no device allocation (its scratch
+    is a fixed array inside the library; at most GENGA_NOALLOC_MAX_N bodies;
+    overlapping calls race on that scratch)."""
+    _check(load().genga_kick_noalloc(_sys(sys), C.byref(params), float(tau), _ptr(acc), _stream(stream)),
+           "genga_kick_noalloc")
