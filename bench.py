@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variant", type=int, default=-1, help="force an FP32 pass variant (-1: autotune)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip timing every FP32 variant")
     return ap.parse_args()
 
 
@@ -247,7 +249,7 @@ def run_genga(args):
     variants = {}
     _, nvar = g.genga_get_kernel_variant(ctx, N)
     sv = g.DeviceSystem.from_disc(d, device=dev)
-    for v in range(nvar):
+    for v in ([] if args.no_sweep else range(nvar)):
         g.genga_set_kernel_variant(ctx, v)
         for _ in range(2):
             g.genga_kick(ctx, sv, p32, 0.0, None)
@@ -257,7 +259,7 @@ def run_genga(args):
         pms, pn = g.genga_profile_read(ctx)
         g.genga_profile_enable(ctx, False)
         variants[str(v)] = pms / max(1, pn)
-    g.genga_set_kernel_variant(ctx, -1)
+    g.genga_set_kernel_variant(ctx, args.variant)
 
     # ---- FP32 step (the headline) and FP64 step on the same GPU
     ms32, pass32, nl32, clk, s32 = timed_steps(p32, args.steps, args.warmup, clocks=True)

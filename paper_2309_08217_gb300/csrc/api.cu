@@ -158,8 +158,8 @@ cudaError_t run_kick(genga_ctx *c, const genga_system &sys, const genga_params &
     int split = 1;
     cudaError_t e = run_pass(c, sys, p, p.precision, reorder, &split, s);
     if (e != cudaSuccess) return e;
-    return launch_combine(c->partial, split, sys.N, npad_of(sys.N), c->perm, tau, acc, sys.vx, sys.vy, sys.vz,
-                          c->status, s);
+    return launch_combine(c->partial, split, sys.N, npad_of(sys.N), p.precision == GENGA_FP64 ? 1 : 0, c->perm, tau,
+                          acc, sys.vx, sys.vy, sys.vz, c->status, s);
 }
 
 template <class T>
@@ -226,7 +226,7 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     c->npad_max = np;
     // partial sums: split * 3 * npad doubles; the plans stay near 8 items per
     // resident CTA, i.e. split * npad ~ 16 * SMs * 1024 (plan_pass clamps)
-    c->partial_cap = 3 * ((size_t)np * 4 + (size_t)16 * c->sm_count * 1024 + 4096);
+    c->partial_cap = 3 * ((size_t)np * 4 + (size_t)32 * c->sm_count * 1024 + 4096);
     long long ecap = 4096;
     while (ecap < 16LL * max_N) ecap <<= 1;
     c->enc_cap = (int32_t)ecap;

@@ -105,8 +105,9 @@ cudaError_t launch_pass(const PassArgs &a, int precision, int variant, int grid,
 int num_fp32_variants();
 void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_cap, int *split, int *chunk_tiles,
                int *grid);
-cudaError_t launch_combine(const double *partial, int split, int N, int npad, const uint32_t *perm, double tau,
-                           double *acc, double *vx, double *vy, double *vz, uint32_t *status, cudaStream_t s);
+cudaError_t launch_combine(const double *partial, int split, int N, int npad, int compensated, const uint32_t *perm,
+                           double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
+                           cudaStream_t s);
 cudaError_t launch_sort_pairs(int2 *enc, int32_t cap, const int32_t *count, cudaStream_t s);
 cudaError_t launch_copy_pairs(const int2 *enc, const int32_t *count, int32_t enc_cap, int32_t *pairs,
                               int32_t capacity, int32_t *count_out, uint32_t *status, cudaStream_t s);

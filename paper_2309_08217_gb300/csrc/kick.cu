@@ -168,6 +168,20 @@ struct StageHdr {
     int item, tile, flags, pad;  // flags: 1 first tile of item, 2 last tile, 4 no more work
 };
 
+// Work item q -> (i-block, j-chunk).  Round r = q / iblocks visits, for every
+// i-block, the chunk at offset 0, +1, -1, +2, -2, ... (mod nchunks) from the
+// chunk holding the i-block's own bodies: the near-diagonal chunks, where the
+// NEAR tiles and screened pairs are, are handed out first, so the costly
+// items do not end up in the tail.
+__device__ __forceinline__ void item_of(int q, int iblocks, int nchunks, int ib_bodies, int chunk_bodies, int *b,
+                                        int *c) {
+    const int r = q / iblocks;
+    *b = q - r * iblocks;
+    const int off = (r & 1) ? (r + 1) / 2 : -(r / 2);
+    const int c0 = (*b * ib_bodies) / chunk_bodies;
+    *c = ((c0 + off) % nchunks + nchunks) % nchunks;
+}
+
 template <int BPT, int TILE, int STAGES, int MINB, int UNR>
 __global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __grid_constant__ PassArgs a) {
     constexpr int NC = F32_CONS_WARPS * 32;  // consumer threads
@@ -176,14 +190,19 @@ __global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __gr
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float4 *s_hi = reinterpret_cast<float4 *>(smem_raw);
     float4 *s_lo = s_hi + STAGES * TILE;
-    uint64_t *full = reinterpret_cast<uint64_t *>(s_lo + STAGES * TILE);
+    float4 *s_glo = s_lo + STAGES * TILE;  // [STAGES][NG] group boxes of each staged tile
+    float4 *s_ghi = s_glo + STAGES * NG;
+    uint64_t *full = reinterpret_cast<uint64_t *>(s_ghi + STAGES * NG);
     uint64_t *empty = full + STAGES;
     StageHdr *hdr = reinterpret_cast<StageHdr *>(empty + STAGES);
     __shared__ double s_acc[3 * BPT * NC];  // [c][k][thread]
+    __shared__ float4 s_ilo[BPT * NC];      // lo parts of this thread's i-bodies (current item)
+    __shared__ float2 s_iscr[BPT * NC];     // and their screening factors
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nchunks = a.split;
-    const int nitems = ((a.npad + IB - 1) / IB) * nchunks;
+    const int iblocks = (a.npad + IB - 1) / IB;
+    const int nitems = iblocks * nchunks;
 
     if (tid == 0) {
         for (int q = 0; q < STAGES; q++) {
@@ -208,17 +227,21 @@ __global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __gr
                 mbar_arrive(&full[slot]);
                 return;
             }
-            const int chunk = q % nchunks;
+            int ib, chunk;
+            item_of(q, iblocks, nchunks, IB, a.chunk_tiles * TILE, &ib, &chunk);
             const int ta = chunk * a.chunk_tiles, tb = min(a.ntiles, ta + a.chunk_tiles);
             for (int t = ta; t < tb; t++, n++) {
                 const int slot = n % STAGES;
                 const unsigned u = n / STAGES;
                 if (u > 0 && !mbar_wait_bounded(&empty[slot], (u - 1) & 1, a.status)) return;
-                hdr[slot] = StageHdr{q, t, (t == ta ? 1 : 0) | (t == tb - 1 ? 2 : 0), 0};
+                hdr[slot] = StageHdr{ib * nchunks + chunk, t, (t == ta ? 1 : 0) | (t == tb - 1 ? 2 : 0), 0};
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&full[slot], 2 * TB);
+                constexpr uint32_t GB = NG * sizeof(float4);
+                mbar_arrive_expect_tx(&full[slot], 2 * TB + 2 * GB);
                 bulk_g2s(s_hi + slot * TILE, a.hi + (size_t)t * TILE, TB, &full[slot]);
                 bulk_g2s(s_lo + slot * TILE, a.lo + (size_t)t * TILE, TB, &full[slot]);
+                bulk_g2s(s_glo + slot * NG, a.gbox_lo + (size_t)t * NG, GB, &full[slot]);
+                bulk_g2s(s_ghi + slot * NG, a.gbox_hi + (size_t)t * NG, GB, &full[slot]);
             }
         }
     }
@@ -239,8 +262,11 @@ __global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __gr
             const bool in = wbase < a.npad;  // warps past the padded end hold dummy bodies
 #pragma unroll
             for (int k = 0; k < BPT; k++) {
-                const float4 p = in ? a.hi[wbase + k * 32 + lane] : make_float4(GENGA_PAD_POS, 0.f, 0.f, 0.f);
+                const int i = wbase + k * 32 + lane;
+                const float4 p = in ? a.hi[i] : make_float4(GENGA_PAD_POS, 0.f, 0.f, 0.f);
                 xh[k] = p.x; yh[k] = p.y; zh[k] = p.z;
+                s_ilo[k * NC + tid] = in ? a.lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                s_iscr[k * NC + tid] = in ? a.scr[i] : make_float2(0.f, 0.f);
 #pragma unroll
                 for (int c = 0; c < 3; c++) s_acc[(c * BPT + k) * NC + tid] = 0.0;
             }
@@ -255,8 +281,7 @@ __global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __gr
 #pragma unroll
         for (int k = 0; k < BPT; k++) ax[k] = ay[k] = az[k] = 0.f;
         for (int g = 0; g < NG; g++) {
-            const int gidx = h.tile * NG + g;
-            const Box gb = {a.gbox_lo[gidx], a.gbox_hi[gidx]};
+            const Box gb = {s_glo[slot * NG + g], s_ghi[slot * NG + g]};
             const float4 *th = s_hi + slot * TILE + g * 64;
             if (far_pair_of_boxes(wbox, gb, true)) {
                 // every pair: K = 1, FP32-rounded positions accurate enough
@@ -281,9 +306,8 @@ __global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __gr
                 float xl[BPT], yl[BPT], zl[BPT], thr[BPT];
 #pragma unroll
                 for (int k = 0; k < BPT; k++) {
-                    const int i = wbase + k * 32 + lane;
-                    const float4 l = a.lo[i];
-                    const float2 sc = a.scr[i];
+                    const float4 l = s_ilo[k * NC + tid];
+                    const float2 sc = s_iscr[k * NC + tid];
                     xl[k] = l.x; yl[k] = l.y; zl[k] = l.z;
                     thr[k] = screen_threshold(sc.x, sc.y, gb.lo.w, gb.hi.w);
                 }
@@ -487,9 +511,11 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
 }
 
 // ------------------------------------------------------------ combine ----
-// acc of body perm[k] = sum over slices (Neumaier, slice order); optional acc
-// output and v += acc * tau; non-finite accelerations raise NONFINITE.
-__global__ void combine_kernel(const double *__restrict__ partial, int split, int N, int npad,
+// acc of body perm[k] = sum over slices in slice order (Neumaier-compensated
+// for the FP64 pass; plain FP64 for the FP32 pass, whose partials carry FP32
+// rounding far above FP64's); optional acc output and v += acc * tau;
+// non-finite accelerations raise NONFINITE.
+__global__ void combine_kernel(const double *__restrict__ partial, int split, int N, int npad, int compensated,
                                const uint32_t *__restrict__ perm, double tau, double *__restrict__ acc,
                                double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
                                uint32_t *__restrict__ status) {
@@ -500,9 +526,15 @@ __global__ void combine_kernel(const double *__restrict__ partial, int split, in
     bool finite = true;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        Comp s{0.0, 0.0};
-        for (int q = 0; q < split; q++) s.add(partial[((size_t)q * 3 + c) * npad + k]);
-        a3[c] = s.s + s.c;
+        if (compensated) {
+            Comp s{0.0, 0.0};
+            for (int q = 0; q < split; q++) s.add(partial[((size_t)q * 3 + c) * npad + k]);
+            a3[c] = s.s + s.c;
+        } else {
+            double t = 0.0;
+            for (int q = 0; q < split; q++) t += partial[((size_t)q * 3 + c) * npad + k];
+            a3[c] = t;
+        }
         finite = finite && isfinite(a3[c]);
     }
     if (!finite) atomicOr(status, GENGA_BIT(GENGA_ERR_NONFINITE));
@@ -612,8 +644,8 @@ constexpr int kNumF32Variants = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 constexpr int F64_BPT = 2, F64_TILE = 128, F64_STAGES = 3;
 
 size_t smem_fp32() {
-    return (size_t)F32_STAGES * F32_TILE * 2 * sizeof(float4) + 2 * F32_STAGES * sizeof(uint64_t) +
-           F32_STAGES * sizeof(StageHdr);
+    return (size_t)F32_STAGES * F32_TILE * 2 * sizeof(float4) + (size_t)F32_STAGES * (F32_TILE / 64) * 2 * sizeof(float4) +
+           2 * F32_STAGES * sizeof(uint64_t) + F32_STAGES * sizeof(StageHdr);
 }
 size_t smem_fp64() { return (size_t)F64_STAGES * F64_TILE * sizeof(double4_32a) + F64_STAGES * sizeof(uint64_t); }
 
@@ -638,7 +670,7 @@ void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_c
     const int cap = (int)(partial_cap / (3 * (size_t)npad));
     int sp;
     if (f32) {
-        const int want_items = 8 * v.minb * sm_count;
+        const int want_items = 12 * v.minb * sm_count;
         sp = (want_items + iblocks - 1) / iblocks;
     } else {
         sp = 2 * sm_count / iblocks;
@@ -682,10 +714,12 @@ cudaError_t launch_pass(const PassArgs &a0, int precision, int variant, int grid
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine(const double *partial, int split, int N, int npad, const uint32_t *perm, double tau,
-                           double *acc, double *vx, double *vy, double *vz, uint32_t *status, cudaStream_t s) {
+cudaError_t launch_combine(const double *partial, int split, int N, int npad, int compensated, const uint32_t *perm,
+                           double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
+                           cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    combine_kernel<<<(N + 255) / 256, 256, 0, s>>>(partial, split, N, npad, perm, tau, acc, vx, vy, vz, status);
+    combine_kernel<<<(N + 255) / 256, 256, 0, s>>>(partial, split, N, npad, compensated, perm, tau, acc, vx, vy, vz,
+                                                   status);
     return cudaGetLastError();
 }
 

@@ -77,26 +77,54 @@ __global__ void __launch_bounds__(RS_THREADS) hist_kernel(const uint32_t *__rest
     for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) hist[b * nblk + blockIdx.x] = h[b];
 }
 
-// Exclusive scan of hist[0 .. total) in place, one CTA of 1024 threads.
-__global__ void __launch_bounds__(1024) scan_kernel(uint32_t *__restrict__ hist, int total) {
-    __shared__ uint32_t part[1024];
-    const int per = (total + 1023) / 1024;
-    const int lo = threadIdx.x * per, hi = min(total, lo + per);
-    uint32_t s = 0;
-    for (int q = lo; q < hi; q++) s += hist[q];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan of the partials
-        const uint32_t v = (threadIdx.x >= o) ? part[threadIdx.x - o] : 0u;
+// Exclusive scan of hist[0 .. total) in place, one CTA of 1024 threads:
+// segments of 8192 entries are loaded coalesced into shared memory, each
+// thread scans 8 consecutive entries, a warp-shuffle scan combines the
+// thread sums, and a running carry links the segments.
+constexpr int SCAN_THREADS = 1024, SCAN_PER = 8, SCAN_SEG = SCAN_THREADS * SCAN_PER;
+
+__global__ void __launch_bounds__(SCAN_THREADS) scan_kernel(uint32_t *__restrict__ hist, int total) {
+    __shared__ uint32_t seg[SCAN_SEG];
+    __shared__ uint32_t wsum[SCAN_THREADS / 32];
+    __shared__ uint32_t carry_s;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_s = 0;
+    for (int base = 0; base < total; base += SCAN_SEG) {
+        for (int q = threadIdx.x; q < SCAN_SEG; q += SCAN_THREADS)
+            seg[q] = (base + q < total) ? hist[base + q] : 0u;
         __syncthreads();
-        part[threadIdx.x] += v;
+        uint32_t v[SCAN_PER], t = 0;
+#pragma unroll
+        for (int q = 0; q < SCAN_PER; q++) {
+            v[q] = t;
+            t += seg[threadIdx.x * SCAN_PER + q];
+        }
+        uint32_t incl = t;  // inclusive scan of thread sums within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[w] = incl;
         __syncthreads();
-    }
-    uint32_t run = part[threadIdx.x] - s;
-    for (int q = lo; q < hi; q++) {
-        const uint32_t v = hist[q];
-        hist[q] = run;
-        run += v;
+        if (w == 0) {
+            uint32_t ws = wsum[lane], wi = ws;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            wsum[lane] = wi - ws;  // exclusive prefix of warp sums
+        }
+        __syncthreads();
+        const uint32_t off = carry_s + wsum[w] + incl - t;
+#pragma unroll
+        for (int q = 0; q < SCAN_PER; q++) seg[threadIdx.x * SCAN_PER + q] = off + v[q];
+        __syncthreads();
+        for (int q = threadIdx.x; q < SCAN_SEG; q += SCAN_THREADS)
+            if (base + q < total) hist[base + q] = seg[q];
+        if (threadIdx.x == SCAN_THREADS - 1) carry_s = off + t;
+        __syncthreads();
     }
 }
 
@@ -157,7 +185,7 @@ cudaError_t launch_order(const genga_system &sys, genga_ctx *c, cudaStream_t s) 
     for (int pass = 0; pass < 3; pass++) {
         const int shift = pass * RS_BITS;
         hist_kernel<<<nblk, RS_THREADS, 0, s>>>(c->ord_keys[cur], N, shift, c->ord_hist, nblk);
-        scan_kernel<<<1, 1024, 0, s>>>(c->ord_hist, RS_BINS * nblk);
+        scan_kernel<<<1, SCAN_THREADS, 0, s>>>(c->ord_hist, RS_BINS * nblk);
         uint32_t *kout = (pass == 2) ? c->ord_keys[1 - cur] : c->ord_keys[1 - cur];
         uint32_t *vout = (pass == 2) ? c->perm : c->ord_vals[1 - cur];
         scatter_kernel<<<nblk, RS_THREADS, 0, s>>>(c->ord_keys[cur], c->ord_vals[cur], kout, vout, N, shift,

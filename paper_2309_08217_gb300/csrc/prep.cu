@@ -1,6 +1,6 @@
 // prep.cu -- per-body work done before each long-range pass (O(N), FP64):
 //
-//   * P = sum_j m_j v_j, a deterministic compensated reduction (one CTA);
+//   * P = sum_j m_j v_j, a deterministic reduction over 64 CTAs;
 //   * the Eq. (1) inputs and radius of every body (Sect. 1): osculating
 //     semi-major axis a_i (1/a = 2/r - v_hel^2 / mu_i, mu_i = G (M* + m_i),
 //     a_i = r_i for unbound orbits), heliocentric speed v_hel = |v + P/M*|,
@@ -19,24 +19,14 @@ namespace genga {
 namespace {
 
 
-struct NSum {  // Neumaier running sum
-    double s = 0.0, c = 0.0;
-    __device__ void add(double v) {
-        const double t = s + v;
-        if (fabs(s) >= fabs(v)) c += (s - t) + v;
-        else c += (v - t) + s;
-        s = t;
-    }
-    __device__ double value() const { return s + c; }
-};
-
 constexpr int MOM_BLOCKS = 64, MOM_THREADS = 256;
 
-// P = sum_j m_j v_j over MOM_BLOCKS CTAs (FP64 is slow on this part, so the
-// sum is spread over many SMs).  Block b sums a contiguous chunk: each thread
-// a strided Neumaier sum, then a fixed-shape tree; the last block to finish
-// adds the block partials in index order.  The result does not depend on
-// timing, so repeated runs are bitwise identical.
+// P = sum_j m_j v_j over MOM_BLOCKS CTAs (FP64 throughput is low on this
+// part, so the few adds per body are spread over many SMs).  Block b sums a
+// contiguous chunk (strided per thread, then a fixed-shape tree); the last
+// block to finish adds the 64 block sums with a fixed warp-shuffle tree.
+// Every add happens in the same order on every run, so the result is
+// bitwise reproducible.
 __global__ void __launch_bounds__(MOM_THREADS) momentum_kernel(const double *__restrict__ vx,
                                                                const double *__restrict__ vy,
                                                                const double *__restrict__ vz,
@@ -48,16 +38,16 @@ __global__ void __launch_bounds__(MOM_THREADS) momentum_kernel(const double *__r
     __shared__ bool last;
     const int chunk = (N + MOM_BLOCKS - 1) / MOM_BLOCKS;
     const int lo = blockIdx.x * chunk, hi = min(N, lo + chunk);
-    NSum px, py, pz;
+    double px = 0.0, py = 0.0, pz = 0.0;
     for (int i = lo + threadIdx.x; i < hi; i += MOM_THREADS) {
         const double mi = m[i];
-        px.add(mi * vx[i]);
-        py.add(mi * vy[i]);
-        pz.add(mi * vz[i]);
+        px += mi * vx[i];
+        py += mi * vy[i];
+        pz += mi * vz[i];
     }
-    sh[0][threadIdx.x] = px.value();
-    sh[1][threadIdx.x] = py.value();
-    sh[2][threadIdx.x] = pz.value();
+    sh[0][threadIdx.x] = px;
+    sh[1][threadIdx.x] = py;
+    sh[2][threadIdx.x] = pz;
     __syncthreads();
     for (int w = MOM_THREADS / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) {
@@ -73,11 +63,13 @@ __global__ void __launch_bounds__(MOM_THREADS) momentum_kernel(const double *__r
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (threadIdx.x < 3) {
-        NSum t;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < 3) {  // warp c sums component c of the 64 block sums
         const volatile double *vp = part;
-        for (int b = 0; b < MOM_BLOCKS; b++) t.add(vp[3 * b + threadIdx.x]);
-        P[threadIdx.x] = t.value();
+        double t = vp[3 * lane + w] + vp[3 * (lane + 32) + w];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) P[w] = t;
     }
     if (threadIdx.x == 0) {
         *ticket = 0u;
