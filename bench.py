@@ -225,6 +225,7 @@ def run_genga(args):
         if g.genga_get_status(ctx) != g.GENGA_OK:
             raise RuntimeError("device status after warm-up")
         g.genga_profile_enable(ctx, True)
+        launches0 = g.genga_launch_count(ctx)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         sampler = ClockSampler(local) if clocks else None
         barrier()
@@ -243,6 +244,7 @@ def run_genga(args):
         ms = sum(a.elapsed_time(b) for a, b in evs)
         pass_ms, launches = g.genga_profile_read(ctx)
         g.genga_profile_enable(ctx, False)
+        timed_steps.kernels = g.genga_launch_count(ctx) - launches0
         return ms, pass_ms, launches, clk, s
 
     # ---- every FP32 pass variant on this workload (the autotuner keeps the fastest)
@@ -263,6 +265,7 @@ def run_genga(args):
 
     # ---- FP32 step (the headline) and FP64 step on the same GPU
     ms32, pass32, nl32, clk, s32 = timed_steps(p32, args.steps, args.warmup, clocks=True)
+    kernels32 = timed_steps.kernels
     chosen, _ = g.genga_get_kernel_variant(ctx, N)
     ms64, pass64, nl64, _, _ = timed_steps(p64, max(1, args.fp64_steps), 3)
 
@@ -309,6 +312,7 @@ def run_genga(args):
     max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
     peak32 = sms * 128 * 2 * max_mhz * 1e6 / 1e12            # FP32 CUDA-core FMA peak, TFLOP/s
     f32_meas, f64_meas = g.genga_measure_alu_peaks(local)
+    f32x2_meas = g.genga_measure_fma2_peak(local)
     pass_avg = pass32 / max(1, nl32)
     pass64_avg = pass64 / max(1, nl64)
     achieved = FLOPS_PER_PAIR * N * (N - 1) / (pass_avg * 1e-3) / 1e12
@@ -319,6 +323,7 @@ def run_genga(args):
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x {max_mhz:.0f} MHz",
             "flops_per_pair": FLOPS_PER_PAIR, "pass_ms_avg": pass_avg,
             "measured_ffma_tflops": f32_meas, "frac_of_measured_ffma": achieved / f32_meas,
+            "measured_ffma2_tflops": f32x2_meas,
             "sm_mhz_median": (clk or {}).get("sm_mhz"), "fp32_variant": chosen,
             "fp32_variant_pass_ms": variants}
 
@@ -351,7 +356,7 @@ def run_genga(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": 14 * args.steps,
+        "gpu_launches": kernels32,
         "clocks": clk,
     }
     if rank == 0:

@@ -28,6 +28,14 @@ genga_status genga_profile_read(genga_ctx *ctx, double *pass_ms, int32_t *launch
  * memory.  Synchronous; allocates and frees a small result buffer. */
 genga_status genga_measure_alu_peaks(int32_t device, double *fp32_tflops, double *fp64_tflops);
 
+/* The same microbenchmark with packed two-lane FP32 FMAs (fma.rn.f32x2, the
+ * form the FP32 pass uses); TFLOP/s counting 4 flops per packed FMA. */
+genga_status genga_measure_fma2_peak(int32_t device, double *tflops);
+
+/* Number of CUDA kernels the context has launched so far (HOST memory);
+ * autotuning trial launches included. */
+genga_status genga_launch_count(genga_ctx *ctx, int64_t *count);
+
 /* Kernel variant of the FP32 long-range pass (bodies per thread, resident
  * CTAs per SM, loop unroll).  variant >= 0 forces that variant for every
  * size; variant = -1 (the default) lets the context time all variants the

@@ -84,6 +84,8 @@ def load():
             "genga_measure_alu_peaks": ([I, C.POINTER(C.c_double), C.POINTER(C.c_double)], I),
             "genga_set_kernel_variant": ([V, I], I),
             "genga_kick_noalloc": ([S, P, D, V, V], I),
+            "genga_measure_fma2_peak": ([I, C.POINTER(C.c_double)], I),
+            "genga_launch_count": ([V, C.POINTER(C.c_int64)], I),
             "genga_get_kernel_variant": ([V, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], I),
         }
         for name, (args, res) in sigs.items():
@@ -236,6 +238,20 @@ def genga_measure_alu_peaks(device=0):
     f32, f64 = C.c_double(), C.c_double()
     _check(load().genga_measure_alu_peaks(int(device), C.byref(f32), C.byref(f64)), "genga_measure_alu_peaks")
     return f32.value, f64.value
+
+
+def genga_launch_count(ctx):
+    """Kernels the context has launched so far."""
+    n = C.c_int64()
+    _check(load().genga_launch_count(_ctx(ctx), C.byref(n)), "genga_launch_count")
+    return n.value
+
+
+def genga_measure_fma2_peak(device=0):
+    """Measured packed two-lane FP32 FMA throughput of `device` in TFLOP/s."""
+    t = C.c_double()
+    _check(load().genga_measure_fma2_peak(int(device), C.byref(t)), "genga_measure_fma2_peak")
+    return t.value
 
 
 def genga_set_kernel_variant(ctx, variant=-1):

@@ -58,6 +58,7 @@ inline int size_bucket(int N) {
 PassArgs base_args(genga_ctx *c, const genga_system &sys, const genga_params &p) {
     PassArgs a;
     a.hi = c->pk_hi;
+    a.hit = c->pk_t;
     a.lo = c->pk_lo;
     a.p64 = c->pk64;
     a.scr = c->scr;
@@ -87,9 +88,10 @@ PassArgs base_args(genga_ctx *c, const genga_system &sys, const genga_params &p)
 }
 
 // The FP32 pass variant for this size: forced, already tuned, or tuned now.
-// Tuning runs every variant twice on the packed state (the encounter list
-// is cleared after each run) and keeps the fastest second run; it
-// synchronises the stream, so it is skipped while the stream is captured.
+// Tuning runs every variant four times on the packed state (the encounter
+// list is cleared after each run) and keeps the variant with the fastest of
+// its last three runs; it synchronises the stream, so it is skipped while
+// the stream is captured.
 int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
     if (c->forced_variant >= 0) return c->forced_variant;
     const int b = size_bucket(N);
@@ -109,13 +111,15 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
         int grid = 1;
         plan_pass(N, GENGA_FP32, v, c->sm_count, c->partial_cap, &a.split, &a.chunk_tiles, &grid);
         float ms = 3.0e38f;
-        for (int rep = 0; rep < 2; rep++) {
+        for (int rep = 0; rep < 4; rep++) {
             cudaEventRecord(e0, s);
             const cudaError_t e = launch_pass(a, GENGA_FP32, v, grid, s);
             cudaEventRecord(e1, s);
             cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s);
             if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
-            cudaEventElapsedTime(&ms, e0, e1);
+            float t = 3.0e38f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0 && t < ms) ms = t;
         }
         if (ms < best_ms) {
             best_ms = ms;
@@ -133,12 +137,20 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
 // prep, pass, and the sort of the encounter list.  Leaves FP64 partials in
 // c->partial, indexed by position in the spatial order.
 cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &p, int precision, bool reorder,
-                     int *split_out, cudaStream_t s) {
-    const int npad = npad_of(sys.N);
-    cudaError_t e = launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->mom, c->enc_count, s);
+                     int *split_out, cudaStream_t s, bool momentum_valid = false) {
+    // momentum_valid: c->mom already holds P of this state (genga_step after a drift)
+    cudaError_t e = momentum_valid ? cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s)
+                                   : launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->mom, c->enc_count, s);
     if (e != cudaSuccess) return e;
-    if (reorder && (e = launch_order(sys, c, s)) != cudaSuccess) return e;
+    c->launches += momentum_valid ? 0 : 1;
+    if (reorder || c->ordered_N != sys.N) {
+        if ((e = launch_order(sys, c, s)) != cudaSuccess) return e;
+        c->ordered_N = sys.N;
+        c->steps_since_order = 0;
+        c->launches += 11;  // extent, keys, 3 x (histogram, scan, scatter)
+    }
     if ((e = launch_prep(sys, p, c, s)) != cudaSuccess) return e;
+    c->launches += 1;
     PassArgs a = base_args(c, sys, p);
     const int variant = (precision == GENGA_FP32) ? fp32_variant(c, a, sys.N, s) : 0;
     int grid = 1;
@@ -148,16 +160,18 @@ cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &
     e = launch_pass(a, precision, variant, grid, s);
     profile_after_pass(c, s);
     if (e != cudaSuccess) return e;
+    c->launches += 2;  // pass + encounter-list sort
     if ((e = launch_sort_pairs(c->enc, c->enc_cap, c->enc_count, s)) != cudaSuccess) return e;
     *split_out = split;
     return cudaSuccess;
 }
 
 cudaError_t run_kick(genga_ctx *c, const genga_system &sys, const genga_params &p, double tau, double *acc,
-                     bool reorder, cudaStream_t s) {
+                     bool reorder, cudaStream_t s, bool momentum_valid = false) {
     int split = 1;
-    cudaError_t e = run_pass(c, sys, p, p.precision, reorder, &split, s);
+    cudaError_t e = run_pass(c, sys, p, p.precision, reorder, &split, s, momentum_valid);
     if (e != cudaSuccess) return e;
+    c->launches += 1;
     return launch_combine(c->partial, split, sys.N, npad_of(sys.N), p.precision == GENGA_FP64 ? 1 : 0, c->perm, tau,
                           acc, sys.vx, sys.vy, sys.vz, c->status, s);
 }
@@ -191,7 +205,7 @@ void genga_destroy(genga_ctx *c) {
     if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     profile_free(c);
-    void *bufs[] = {c->pk_hi,       c->pk_lo,       c->pk64,        c->scr,      c->gbox_lo,    c->gbox_hi,
+    void *bufs[] = {c->pk_hi,       c->pk_t,        c->pk_lo,       c->pk64,        c->scr,      c->gbox_lo,    c->gbox_hi,
                     c->perm,        c->ord_keys[0], c->ord_keys[1], c->ord_vals[0], c->ord_vals[1], c->ord_hist,
                     c->ord_rbits,   c->a_osc,       c->rc_eq1,      c->partial,  c->mom,        c->enc,
                     c->enc_count,   c->status,      c->energy_part, c->work};
@@ -216,6 +230,7 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     c->max_N = max_N;
     for (int b = 0; b < 32; b++) c->f32_variant[b] = -1;
     c->forced_variant = -1;
+    c->ordered_N = -1;
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
         delete c;
@@ -234,6 +249,7 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     cudaError_t e = init_pass_kernels();
     if (e == cudaSuccess) e = alloc(&c->pk_hi, np);
     if (e == cudaSuccess) e = alloc(&c->pk_lo, np);
+    if (e == cudaSuccess) e = alloc(&c->pk_t, 4 * (size_t)np);
     if (e == cudaSuccess) e = alloc(&c->pk64, np);
     if (e == cudaSuccess) e = alloc(&c->scr, np);
     if (e == cudaSuccess) e = alloc(&c->gbox_lo, np / 64);
@@ -285,12 +301,14 @@ genga_status genga_drift(genga_ctx *c, genga_system *sys, const genga_params *p,
     if (!is_fin(dt)) return GENGA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     genga_system s2 = *sys;
+    if (sys->N > 0) c->launches += 4;
     return launch_drift(s2, *p, dt, c, (cudaStream_t)stream) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
 }
 
 genga_status genga_last_encounters(genga_ctx *c, int32_t *pairs, int32_t capacity, int32_t *count, void *stream) {
     if (!c || capacity < 0 || !count || (capacity > 0 && !pairs)) return GENGA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
+    c->launches += 1;
     return launch_copy_pairs(c->enc, c->enc_count, c->enc_cap, pairs, capacity, count, c->status,
                              (cudaStream_t)stream) == cudaSuccess
                ? GENGA_OK
@@ -324,12 +342,18 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
     if (sys->N == 0 || nsteps == 0) return GENGA_OK;
     genga_system s2 = *sys;
     const double h = 0.5 * p->dt;
-    // the closing kick of a step and the opening kick of the next see the same
-    // positions, so the spatial order is rebuilt only after each drift
+    // The spatial order is a performance device (every pass classifies tiles
+    // from the current positions; any order gives the same sum up to
+    // rounding), so genga_step rebuilds it every GENGA_REORDER_STEPS drifts,
+    // counted across calls, and whenever N changes.  The drift leaves P of the
+    // new state in c->mom, which the closing kick reuses.
     for (int k = 0; k < nsteps; k++) {
-        if (run_kick(c, s2, *p, h, nullptr, k == 0, s) != cudaSuccess) return GENGA_ERR_CUDA;
+        if (run_kick(c, s2, *p, h, nullptr, false, s) != cudaSuccess) return GENGA_ERR_CUDA;
         if (launch_drift(s2, *p, p->dt, c, s) != cudaSuccess) return GENGA_ERR_CUDA;
-        if (run_kick(c, s2, *p, h, nullptr, true, s) != cudaSuccess) return GENGA_ERR_CUDA;
+        c->launches += 4;
+        c->steps_since_order++;
+        const bool reorder = c->steps_since_order >= GENGA_REORDER_STEPS;
+        if (run_kick(c, s2, *p, h, nullptr, reorder, s, true) != cudaSuccess) return GENGA_ERR_CUDA;
     }
     return GENGA_OK;
 }

@@ -19,6 +19,11 @@
 // i-block is full; padded bodies have zero mass and sit far away.
 #define GENGA_PAD 1024
 #define GENGA_PAD_POS 1.0e6f
+// genga_step rebuilds the spatial order of the bodies every this many steps.
+#define GENGA_REORDER_STEPS 4
+
+// Bodies per tile of the tile-blocked FP32 copy (pk_t).
+#define GENGA_TILE_T 256
 
 namespace genga {
 struct Profile {                // CUDA event pairs around pass launches
@@ -38,6 +43,7 @@ struct genga_ctx {
     // packed per-body data, rebuilt at every kick (prep kernel)
     float4 *pk_hi;             // [npad] {x_hi, y_hi, z_hi, G m (fp32)}
     float4 *pk_lo;             // [npad] {x - x_hi, y - y_hi, z - z_hi, 0}
+    float *pk_t;               // [4 npad] tile-blocked {x_hi}, {y_hi}, {z_hi}, {G m} per 256 bodies
     double4_32a *pk64;             // [npad] {x, y, z, G m}
     float2 *scr;               // [npad] screening bound factors {H_i, A_i} (rounded up)
     float4 *gbox_lo;           // [npad / 64] per 64-body group: {min x, min y, min z, max H}
@@ -67,6 +73,9 @@ struct genga_ctx {
     int32_t *work;             // [1] work-item counter of the persistent pass
     int8_t f32_variant[32];    // autotuned FP32 pass variant per log2(npad) bucket, -1 = not tuned
     int32_t forced_variant;    // >= 0: use this FP32 variant (genga_set_kernel_variant)
+    int32_t steps_since_order; // genga_step: drifts since the spatial order was built
+    int32_t ordered_N;         // N of the system the spatial order was built for (-1: none)
+    int64_t launches;          // kernels this context has launched (measurement hook)
     size_t partial_cap;        // doubles in `partial`
 };
 
@@ -75,6 +84,7 @@ namespace genga {
 
 struct PassArgs {               // one long-range pass
     const float4 *hi, *lo;
+    const float *hit;           // tile-blocked copy of hi
     const double4_32a *p64;
     const float2 *scr;
     const float4 *gbox_lo, *gbox_hi;

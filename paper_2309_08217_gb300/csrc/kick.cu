@@ -47,12 +47,42 @@ __device__ __forceinline__ float rsqrt_sfu(float x) {
     return y;
 }
 
-// 1/sqrt(x) in FP64: FP32 SFU seed y0 (relative error ~1e-7), then the
-// third-order correction y = y0 (1 + e/2 + 3e^2/8), e = 1 - x y0^2, from the
-// binomial series of (1 - e)^(-1/2); the truncation error is O(e^3) ~ 1e-21.
-// Valid for x in the FP32 normal range.
+// Two FP32 lanes in one 64-bit register, driven by the packed f32x2
+// instructions of sm_100-class GPUs: one issue slot carries two FP32 ops,
+// each rounded to nearest exactly like its scalar counterpart.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void up2(f32x2 v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// 1/sqrt(x) in FP64: the approximate FP64 reciprocal square root of the SFU
+// as seed y0 (relative error ~1e-7), then the third-order correction
+// y = y0 (1 + e/2 + 3e^2/8), e = 1 - x y0^2, from the binomial series of
+// (1 - e)^(-1/2); the truncation error is O(e^3) ~ 1e-21.
 __device__ __forceinline__ double rsqrt_fp64(double x) {
-    const double y0 = (double)rsqrt_sfu(__double2float_rn(x));
+    double y0;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(x));
     const double t = x * y0;
     const double e = fma(-t, y0, 1.0);
     const double p = fma(e, 0.375, 0.5);
@@ -72,7 +102,7 @@ __device__ __forceinline__ double changeover_K(double y, int form) {
 
 // Exact FP64 treatment of one screened pair (positions i, j of the spatial
 // order): the K-weighted acceleration of i due to j; records the encounter.
-__device__ __forceinline__ double3 screened_pair(const PassArgs &a, int i, int j) {
+__device__ __noinline__ double3 screened_pair(const PassArgs &a, int i, int j) {
     double3 f = make_double3(0.0, 0.0, 0.0);
     if (i >= a.N || j >= a.N || i == j) return f;
     const double4_32a pi = a.p64[i], pj = a.p64[j];
@@ -161,8 +191,6 @@ __device__ __forceinline__ bool far_pair_of_boxes(const Box &u, const Box &v, bo
 // FAR/NEAR is decided per (warp, 64-body group of the tile).  Registers hold
 // only the FP32-rounded i positions and FP32 tile sums; FP64 per-body sums
 // live in shared memory, touched once per tile.
-constexpr int F32_CONS_WARPS = 8;
-constexpr int F32_THREADS = (F32_CONS_WARPS + 1) * 32;
 
 struct StageHdr {
     int item, tile, flags, pad;  // flags: 1 first tile of item, 2 last tile, 4 no more work
@@ -182,9 +210,15 @@ __device__ __forceinline__ void item_of(int q, int iblocks, int nchunks, int ib_
     *c = ((c0 + off) % nchunks + nchunks) % nchunks;
 }
 
-template <int BPT, int TILE, int STAGES, int MINB, int UNR>
-__global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __grid_constant__ PassArgs a) {
-    constexpr int NC = F32_CONS_WARPS * 32;  // consumer threads
+// The hi slot of stage `slot` holds one tile of the tile-blocked copy.
+__device__ __forceinline__ const float *s_hi_t(const unsigned char *smem_raw, int slot) {
+    return reinterpret_cast<const float *>(smem_raw) + (size_t)slot * 4 * 256;
+}
+
+template <int BPT, int CW, int TILE, int STAGES, int MINB, int UNR>
+__global__ void __launch_bounds__((CW + 1) * 32, MINB) pass_fp32_kernel(const __grid_constant__ PassArgs a) {
+    static_assert(TILE == GENGA_TILE_T, "the staged tile is one block of the tile-blocked copy");
+    constexpr int NC = CW * 32;              // consumer threads (CW consumer warps + 1 producer warp)
     constexpr int IB = NC * BPT;             // i-bodies per item (the last i-block may be partial)
     constexpr int NG = TILE / 64;            // 64-body groups per tile
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -207,13 +241,13 @@ __global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __gr
     if (tid == 0) {
         for (int q = 0; q < STAGES; q++) {
             mbar_init(&full[q], 1);
-            mbar_init(&empty[q], F32_CONS_WARPS);
+            mbar_init(&empty[q], CW);
         }
         fence_barrier_init();
     }
     __syncthreads();
 
-    if (warp == F32_CONS_WARPS) {  // ------------------------------ producer
+    if (warp == CW) {  // ------------------------------------------ producer
         if (lane != 0) return;
         constexpr uint32_t TB = TILE * sizeof(float4);
         unsigned n = 0;
@@ -238,7 +272,7 @@ __global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __gr
                 fence_proxy_async_smem();
                 constexpr uint32_t GB = NG * sizeof(float4);
                 mbar_arrive_expect_tx(&full[slot], 2 * TB + 2 * GB);
-                bulk_g2s(s_hi + slot * TILE, a.hi + (size_t)t * TILE, TB, &full[slot]);
+                bulk_g2s(s_hi + slot * TILE, a.hit + (size_t)t * 4 * TILE, TB, &full[slot]);
                 bulk_g2s(s_lo + slot * TILE, a.lo + (size_t)t * TILE, TB, &full[slot]);
                 bulk_g2s(s_glo + slot * NG, a.gbox_lo + (size_t)t * NG, GB, &full[slot]);
                 bulk_g2s(s_ghi + slot * NG, a.gbox_hi + (size_t)t * NG, GB, &full[slot]);
@@ -247,9 +281,10 @@ __global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __gr
     }
 
     // ---------------------------------------------------------- consumers
-    float xh[BPT], yh[BPT], zh[BPT];
+    // i positions as duplicated pairs {x, x}; the scalar value is either half
+    f32x2 XI[BPT], YI[BPT], ZI[BPT];
 #pragma unroll
-    for (int k = 0; k < BPT; k++) xh[k] = yh[k] = zh[k] = 0.f;
+    for (int k = 0; k < BPT; k++) XI[k] = YI[k] = ZI[k] = 0ull;
     Box wbox = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
     int wbase = 0;
     for (unsigned n = 0;; n++) {
@@ -264,7 +299,9 @@ __global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __gr
             for (int k = 0; k < BPT; k++) {
                 const int i = wbase + k * 32 + lane;
                 const float4 p = in ? a.hi[i] : make_float4(GENGA_PAD_POS, 0.f, 0.f, 0.f);
-                xh[k] = p.x; yh[k] = p.y; zh[k] = p.z;
+                XI[k] = pk2(p.x, p.x);
+                YI[k] = pk2(p.y, p.y);
+                ZI[k] = pk2(p.z, p.z);
                 s_ilo[k * NC + tid] = in ? a.lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
                 s_iscr[k * NC + tid] = in ? a.scr[i] : make_float2(0.f, 0.f);
 #pragma unroll
@@ -277,29 +314,54 @@ __global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __gr
                 wbox = {make_float4(INF, INF, INF, 0.f), make_float4(-INF, -INF, -INF, 0.f)};
             }
         }
+        // FP32 sums of this tile (FAR groups accumulate packed even/odd-j sums
+        // and fold them in at the end of the group)
         float ax[BPT], ay[BPT], az[BPT];
 #pragma unroll
         for (int k = 0; k < BPT; k++) ax[k] = ay[k] = az[k] = 0.f;
+        const float *tt = s_hi_t(smem_raw, slot);  // tile-blocked x[TILE] y[TILE] z[TILE] w[TILE]
         for (int g = 0; g < NG; g++) {
             const Box gb = {s_glo[slot * NG + g], s_ghi[slot * NG + g]};
-            const float4 *th = s_hi + slot * TILE + g * 64;
+            const float *tx = tt + g * 64, *ty = tx + TILE, *tz = tx + 2 * TILE, *tw = tx + 3 * TILE;
             if (far_pair_of_boxes(wbox, gb, true)) {
-                // every pair: K = 1, FP32-rounded positions accurate enough
-#pragma unroll(UNR)
-                for (int jj = 0; jj < 64; jj++) {
-                    const float4 ph = th[jj];
+                // every pair: K = 1, FP32-rounded positions accurate enough;
+                // two consecutive j per packed register, four j per step
+                f32x2 AX[BPT], AY[BPT], AZ[BPT];
 #pragma unroll
-                    for (int k = 0; k < BPT; k++) {
-                        const float dx = ph.x - xh[k];
-                        const float dy = ph.y - yh[k];
-                        const float dz = ph.z - zh[k];
-                        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                        const float ri = rsqrt_sfu(r2);
-                        const float s = (ph.w * ri) * (ri * ri);
-                        ax[k] = fmaf(s, dx, ax[k]);
-                        ay[k] = fmaf(s, dy, ay[k]);
-                        az[k] = fmaf(s, dz, az[k]);
+                for (int k = 0; k < BPT; k++) AX[k] = AY[k] = AZ[k] = 0ull;
+#pragma unroll(UNR)
+                for (int jj = 0; jj < 64; jj += 4) {
+                    const ulonglong2 X4 = *reinterpret_cast<const ulonglong2 *>(tx + jj);
+                    const ulonglong2 Y4 = *reinterpret_cast<const ulonglong2 *>(ty + jj);
+                    const ulonglong2 Z4 = *reinterpret_cast<const ulonglong2 *>(tz + jj);
+                    const ulonglong2 W4 = *reinterpret_cast<const ulonglong2 *>(tw + jj);
+#pragma unroll
+                    for (int half = 0; half < 2; half++) {
+                        const f32x2 JX = half ? X4.y : X4.x, JY = half ? Y4.y : Y4.x;
+                        const f32x2 JZ = half ? Z4.y : Z4.x, JW = half ? W4.y : W4.x;
+#pragma unroll
+                        for (int k = 0; k < BPT; k++) {
+                            const f32x2 DX = sub2(JX, XI[k]), DY = sub2(JY, YI[k]), DZ = sub2(JZ, ZI[k]);
+                            const f32x2 R2 = fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
+                            float ra, rb;
+                            up2(R2, ra, rb);
+                            const f32x2 RI = pk2(rsqrt_sfu(ra), rsqrt_sfu(rb));
+                            const f32x2 S = mul2(mul2(JW, RI), mul2(RI, RI));
+                            AX[k] = fma2(S, DX, AX[k]);
+                            AY[k] = fma2(S, DY, AY[k]);
+                            AZ[k] = fma2(S, DZ, AZ[k]);
+                        }
                     }
+                }
+#pragma unroll
+                for (int k = 0; k < BPT; k++) {
+                    float e0, e1;
+                    up2(AX[k], e0, e1);
+                    ax[k] += e0 + e1;
+                    up2(AY[k], e0, e1);
+                    ay[k] += e0 + e1;
+                    up2(AZ[k], e0, e1);
+                    az[k] += e0 + e1;
                 }
             } else {
                 const float4 *tl = s_lo + slot * TILE + g * 64;
@@ -313,22 +375,26 @@ __global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __gr
                 }
 #pragma unroll 2
                 for (int jj = 0; jj < 64; jj++) {
-                    const float4 ph = th[jj];
+                    const float jx = tx[jj], jy = ty[jj], jz = tz[jj], jw = tw[jj];
                     const float4 pl = tl[jj];
                     unsigned screened = 0u;  // bit k: pair (i_k, j) is under the screening bound
 #pragma unroll
                     for (int k = 0; k < BPT; k++) {
-                        const float dx = (ph.x - xh[k]) + (pl.x - xl[k]);
-                        const float dy = (ph.y - yh[k]) + (pl.y - yl[k]);
-                        const float dz = (ph.z - zh[k]) + (pl.z - zl[k]);
+                        float xi, yi, zi, d0;
+                        up2(XI[k], xi, d0);
+                        up2(YI[k], yi, d0);
+                        up2(ZI[k], zi, d0);
+                        const float dx = (jx - xi) + (pl.x - xl[k]);
+                        const float dy = (jy - yi) + (pl.y - yl[k]);
+                        const float dz = (jz - zi) + (pl.z - zl[k]);
                         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                         const float ri = rsqrt_sfu(r2);
                         const bool near = r2 < thr[k];
                         screened |= (unsigned)near << k;
-                        const float s = near ? 0.f : (ph.w * ri) * (ri * ri);
-                        ax[k] = fmaf(s, dx, ax[k]);
-                        ay[k] = fmaf(s, dy, ay[k]);
-                        az[k] = fmaf(s, dz, az[k]);
+                        const float sf = near ? 0.f : (jw * ri) * (ri * ri);
+                        ax[k] = fmaf(sf, dx, ax[k]);
+                        ay[k] = fmaf(sf, dy, ay[k]);
+                        az[k] = fmaf(sf, dz, az[k]);
                     }
                     if (screened) {  // rare: these pairs are evaluated exactly, in FP64
 #pragma unroll
@@ -348,7 +414,7 @@ __global__ void __launch_bounds__(F32_THREADS, MINB) pass_fp32_kernel(const __gr
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);  // this warp is done reading the slot
 #pragma unroll
-        for (int k = 0; k < BPT; k++) {
+        for (int k = 0; k < BPT; k++) {  // fold the tile's FP32 sums into the FP64 sums
             s_acc[(0 * BPT + k) * NC + tid] += (double)ax[k];
             s_acc[(1 * BPT + k) * NC + tid] += (double)ay[k];
             s_acc[(2 * BPT + k) * NC + tid] += (double)az[k];
@@ -631,14 +697,15 @@ constexpr int F32_TILE = 256, F32_STAGES = 4;
 // FP32 pass variants (bodies per thread, CTAs per SM, FAR-loop unroll); the
 // autotuner in api.cu times them per N bucket and keeps the fastest.
 struct F32Variant {
-    int bpt, minb;
+    int bpt, cw, minb;  // bodies per thread, consumer warps, resident CTAs per SM
     void (*fn)(const PassArgs);
 };
 const F32Variant kF32Variants[] = {
-    {4, 1, pass_fp32_kernel<4, F32_TILE, F32_STAGES, 1, 4>},
-    {4, 2, pass_fp32_kernel<4, F32_TILE, F32_STAGES, 2, 2>},
-    {8, 1, pass_fp32_kernel<8, F32_TILE, F32_STAGES, 1, 2>},
-    {2, 2, pass_fp32_kernel<2, F32_TILE, F32_STAGES, 2, 4>},
+    {4, 8, 1, pass_fp32_kernel<4, 8, F32_TILE, F32_STAGES, 1, 2>},
+    {2, 7, 2, pass_fp32_kernel<2, 7, F32_TILE, F32_STAGES, 2, 2>},
+    {4, 7, 2, pass_fp32_kernel<4, 7, F32_TILE, F32_STAGES, 2, 1>},
+    {2, 8, 2, pass_fp32_kernel<2, 8, F32_TILE, F32_STAGES, 2, 2>},
+    {2, 3, 4, pass_fp32_kernel<2, 3, F32_TILE, F32_STAGES, 4, 2>},
 };
 constexpr int kNumF32Variants = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 constexpr int F64_BPT = 2, F64_TILE = 128, F64_STAGES = 3;
@@ -665,7 +732,7 @@ void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_c
     const F32Variant &v = kF32Variants[variant];
     const int tile = f32 ? F32_TILE : F64_TILE;
     const int ntiles = npad / tile;
-    const int ib = f32 ? F32_CONS_WARPS * 32 * v.bpt : KB * F64_BPT;
+    const int ib = f32 ? v.cw * 32 * v.bpt : KB * F64_BPT;
     const int iblocks = (npad + ib - 1) / ib;
     const int cap = (int)(partial_cap / (3 * (size_t)npad));
     int sp;
@@ -704,7 +771,8 @@ cudaError_t launch_pass(const PassArgs &a0, int precision, int variant, int grid
         a.ntiles = a.npad / F32_TILE;
         cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s);
         if (e != cudaSuccess) return e;
-        kF32Variants[variant].fn<<<grid, F32_THREADS, smem_fp32(), s>>>(a);
+        const F32Variant &v = kF32Variants[variant];
+        v.fn<<<grid, (v.cw + 1) * 32, smem_fp32(), s>>>(a);
     } else {
         a.ntiles = a.npad / F64_TILE;
         auto k = pass_fp64_kernel<F64_BPT, F64_TILE, F64_STAGES>;

@@ -51,6 +51,54 @@ __global__ void fma_peak_kernel(T a, T b, T *out) {
     if (s == (T)-1.2345) out[0] = s;
 }
 
+// The same with packed two-lane FP32 FMAs (fma.rn.f32x2): eight chains of
+// two lanes each.
+__global__ void fma2_peak_kernel(float a, float b, float *out) {
+    unsigned long long A, B, x[8];
+    asm("mov.b64 %0, {%1, %1};" : "=l"(A) : "f"(a));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(B) : "f"(b));
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        const float v = (float)(threadIdx.x + c);
+        asm("mov.b64 %0, {%1, %2};" : "=l"(x[c]) : "f"(v), "f"(v + 0.5f));
+    }
+#pragma unroll 16
+    for (int it = 0; it < PEAK_ITERS; it++) {
+#pragma unroll
+        for (int c = 0; c < 8; c++) asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[c]) : "l"(A), "l"(B));
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        float u, w;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(u), "=f"(w) : "l"(x[c]));
+        s += u + w;
+    }
+    if (s == -1.2345f) out[0] = s;
+}
+
+double run_peak_fma2(int sms, float *out) {
+    const int threads = 256, blocks = sms * 8;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    fma2_peak_kernel<<<blocks, threads>>>(0.999999f, 1e-7f, out);
+    float best = 1e30f;
+    for (int rep = 0; rep < 5; rep++) {
+        cudaEventRecord(e0);
+        fma2_peak_kernel<<<blocks, threads>>>(0.999999f, 1e-7f, out);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double flops = 2.0 * 2.0 * 8.0 * PEAK_ITERS * (double)threads * blocks;
+    return flops / (best * 1e-3) / 1e12;
+}
+
 template <class T>
 double run_peak(int sms, T *out) {
     const int threads = 256, blocks = sms * 8;
@@ -128,6 +176,12 @@ genga_status genga_profile_read(genga_ctx *c, double *pass_ms, int32_t *launches
     return GENGA_OK;
 }
 
+genga_status genga_launch_count(genga_ctx *c, int64_t *count) {
+    if (!c || !count) return GENGA_ERR_INVALID_ARG;
+    *count = c->launches;
+    return GENGA_OK;
+}
+
 genga_status genga_set_kernel_variant(genga_ctx *c, int32_t variant) {
     if (!c || variant < -1 || variant >= num_fp32_variants()) return GENGA_ERR_INVALID_ARG;
     c->forced_variant = variant;
@@ -142,6 +196,29 @@ genga_status genga_get_kernel_variant(genga_ctx *c, int32_t N, int32_t *variant,
     *variant = (c->forced_variant >= 0) ? c->forced_variant : c->f32_variant[b];
     *num_variants = num_fp32_variants();
     return GENGA_OK;
+}
+
+genga_status genga_measure_fma2_peak(int32_t device, double *tflops) {
+    if (!tflops) return GENGA_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) return GENGA_ERR_CUDA;
+    if (device < 0 || device >= ndev) return GENGA_ERR_INVALID_ARG;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    void *buf = nullptr;
+    genga_status st = GENGA_OK;
+    if (cudaMalloc(&buf, 64) != cudaSuccess) {
+        st = GENGA_ERR_CUDA;
+    } else {
+        *tflops = run_peak_fma2(sms, (float *)buf);
+        if (cudaGetLastError() != cudaSuccess) st = GENGA_ERR_CUDA;
+        cudaFree(buf);
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    return st;
 }
 
 genga_status genga_measure_alu_peaks(int32_t device, double *fp32_tflops, double *fp64_tflops) {

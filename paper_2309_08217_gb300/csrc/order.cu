@@ -1,14 +1,14 @@
 // order.cu -- spatial order of the bodies for the long-range pass.
 //
-// Bodies are sorted along a 3-D Morton curve (10 bits per axis over the cube
+// Bodies are sorted along a 3-D Morton curve (8 bits per axis over the cube
 // [-R, R]^3, R = the largest |coordinate|), so that a warp's 128 i-bodies and
 // a 256-body j-tile each cover a compact region; the pass kernels then test
 // (warp, tile) bounding boxes and run most tiles without per-pair screening.
 // The order only changes which pairs share a tile, never which pairs are
 // summed, so it affects speed, not the definition of the result.
 //
-// The sort is a stable least-significant-digit radix sort of the 30-bit keys
-// with 10-bit digits (three passes of histogram / scan / scatter).  Stable
+// The sort is a stable least-significant-digit radix sort of the 24-bit keys
+// with 8-bit digits (three passes of histogram / scan / scatter).  Stable
 // ranks inside a CTA come from warp match masks and per-warp digit counts, so
 // the permutation is the same on every run.
 #include "internal.cuh"
@@ -20,7 +20,7 @@ namespace {
 constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = 4;
 constexpr int RS_CHUNK = RS_THREADS * RS_ITEMS;  // keys per CTA
-constexpr int RS_BITS = 10;
+constexpr int RS_BITS = 8;
 constexpr int RS_BINS = 1 << RS_BITS;
 constexpr int RS_WARPS = RS_THREADS / 32;
 
@@ -35,8 +35,8 @@ __global__ void extent_kernel(const double *__restrict__ x, const double *__rest
     if ((threadIdx.x & 31) == 0) atomicMax(rbits, __float_as_uint(r));
 }
 
-__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 10 bits -> every third bit
-    v &= 0x3ffu;
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 8 bits -> every third bit
+    v &= 0xffu;
     v = (v | (v << 16)) & 0x030000ffu;
     v = (v | (v << 8)) & 0x0300f00fu;
     v = (v | (v << 4)) & 0x030c30c3u;
@@ -44,9 +44,9 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 10 bits -> every t
     return v;
 }
 
-__device__ __forceinline__ uint32_t quant10(double c, float inv) {
-    float f = ((float)c * inv + 1.0f) * 512.0f;
-    f = fminf(fmaxf(f, 0.0f), 1023.0f);
+__device__ __forceinline__ uint32_t quant8(double c, float inv) {
+    float f = ((float)c * inv + 1.0f) * 128.0f;
+    f = fminf(fmaxf(f, 0.0f), 255.0f);
     return (uint32_t)f;
 }
 
@@ -57,8 +57,7 @@ __global__ void keys_kernel(const double *__restrict__ x, const double *__restri
     if (i >= N) return;
     const float R = fmaxf(__uint_as_float(*rbits), 1e-30f) * 1.0001f;
     const float inv = 1.0f / R;
-    keys[i] = spread3(quant10(x[i], inv)) | (spread3(quant10(y[i], inv)) << 1) |
-              (spread3(quant10(z[i], inv)) << 2);
+    keys[i] = spread3(quant8(x[i], inv)) | (spread3(quant8(y[i], inv)) << 1) | (spread3(quant8(z[i], inv)) << 2);
     vals[i] = (uint32_t)i;
 }
 

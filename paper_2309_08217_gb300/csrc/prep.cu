@@ -79,13 +79,25 @@ __global__ void __launch_bounds__(MOM_THREADS) momentum_kernel(const double *__r
 
 constexpr int PREP_THREADS = 64;  // one block = one 64-body group
 
+// Tile-blocked copy of {x_hi, y_hi, z_hi, G m}: the 256-body tile t holds
+// x[256], y[256], z[256], w[256], so a 64-bit shared load gives the values of
+// two consecutive bodies (the packed-pair loop of the FP32 pass).
+__device__ __forceinline__ void store_tiled(float *hit, int k, float x, float y, float z, float w) {
+    float *t = hit + (size_t)(k / GENGA_TILE_T) * 4 * GENGA_TILE_T + (k % GENGA_TILE_T);
+    t[0] = x;
+    t[GENGA_TILE_T] = y;
+    t[2 * GENGA_TILE_T] = z;
+    t[3 * GENGA_TILE_T] = w;
+}
+
 // Position k of the packed arrays holds body perm[k] (the Morton order);
 // k >= N are padding bodies: zero mass, 64 au apart, far from everything.
 __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
     const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
     const double *__restrict__ vx, const double *__restrict__ vy, const double *__restrict__ vz,
     const double *__restrict__ m, int N, const uint32_t *__restrict__ perm, const double *__restrict__ P, double G,
-    double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float4 *__restrict__ lo,
+    double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit,
+    float4 *__restrict__ lo,
     double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
     float4 *__restrict__ gbox_hi, double *__restrict__ a_osc, double *__restrict__ rc_eq1) {
     const int k = blockIdx.x * PREP_THREADS + threadIdx.x;
@@ -103,22 +115,23 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
         const double mu = G * (Mstar + mi);
         const double inva = 2.0 / r - v2 / mu;
         const double a = (inva > 0.0) ? 1.0 / inva : r;
-        const double hill = n1 * a * cbrt(mi / (3.0 * Mstar));
-        const double vel = n2 * dt * sqrt(v2);
-        const double rc = fmax(hill, vel);
         a_osc[k] = a;
-        rc_eq1[k] = rc;
         if (rcrit_mode == GENGA_RCRIT_EQ1) {
             // r_crit,ij = max(rc_i, rc_j) = max(1, 1) * max(rc_i, rc_j)
+            const double rc = fmax(n1 * a * cbrt(mi / (3.0 * Mstar)), n2 * dt * sqrt(v2));
+            rc_eq1[k] = rc;
             s = make_float2(1.0f, __double2float_ru(rc));
         } else {
-            // n1 ((m_i+m_j)/3M)^(1/3) (a_i+a_j)/2 <= n1 (2 max(m)/3M)^(1/3) * max(a)
-            s = make_float2(__double2float_ru(n1 * cbrt(2.0 * mi / (3.0 * Mstar)) * (1.0 + 1e-12)),
-                            __double2float_ru(a * (1.0 + 1e-12)));
+            // n1 ((m_i+m_j)/3M)^(1/3) (a_i+a_j)/2 <= n1 (2 max(m)/3M)^(1/3) * max(a); the FP32
+            // cube root (error ~1 ulp) is inflated by 2^-16 to stay an upper bound
+            rc_eq1[k] = 0.0;
+            const float h = n1 * cbrtf(__double2float_ru(2.0 * mi / (3.0 * Mstar))) * (1.0f + 0x1p-16f);
+            s = make_float2(h, __double2float_ru(a * (1.0 + 1e-12)));
         }
         const float hx = __double2float_rn(xi), hy = __double2float_rn(yi), hz = __double2float_rn(zi);
         const double gm = G * mi;
         hi[k] = make_float4(hx, hy, hz, __double2float_rn(gm));
+        store_tiled(hit, k, hx, hy, hz, __double2float_rn(gm));
         lo[k] = make_float4(__double2float_rn(xi - (double)hx), __double2float_rn(yi - (double)hy),
                             __double2float_rn(zi - (double)hz), 0.f);
         p64[k] = make_double4_32a(xi, yi, zi, gm);
@@ -126,6 +139,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
     } else {
         const float px = GENGA_PAD_POS + 64.0f * (float)(k - N);
         hi[k] = make_float4(px, GENGA_PAD_POS, GENGA_PAD_POS, 0.f);
+        store_tiled(hit, k, px, GENGA_PAD_POS, GENGA_PAD_POS, 0.f);
         lo[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         p64[k] = make_double4_32a((double)px, GENGA_PAD_POS, GENGA_PAD_POS, 0.0);
         a_osc[k] = 0.0;
@@ -178,7 +192,8 @@ cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ct
     const int npad = (sys.N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
     prep_kernel<<<npad / PREP_THREADS, PREP_THREADS, 0, s>>>(
         sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->perm, c->mom, p.G, p.Mstar, p.dt, p.n1,
-        p.n2, p.rcrit_mode, c->pk_hi, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->a_osc, c->rc_eq1);
+        p.n2, p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->a_osc,
+        c->rc_eq1);
     return cudaGetLastError();
 }
 
