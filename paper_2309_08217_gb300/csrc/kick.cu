@@ -17,7 +17,8 @@
 // when D exceeds an upper bound of r_crit,ij over the two sets (so K = 1 for
 // every pair) and, in FP32, also 0.025 * (largest |coordinate|), which keeps
 // the offset of two rounded FP32 positions within ~5e-6 of the true offset.
-// FAR tiles run the plain loop; NEAR tiles run the screened loop below.
+// FAR tiles run the plain loop (packed FP32 pairs); NEAR tiles run the
+// screened loop below.
 //
 // Precision.  FP32 pass (the single-precision kick of Sect. 1): FAR pairs use
 // the FP32-rounded positions; NEAR pairs use the hi/lo split of the FP64
@@ -702,10 +703,11 @@ struct F32Variant {
 };
 const F32Variant kF32Variants[] = {
     {4, 8, 1, pass_fp32_kernel<4, 8, F32_TILE, F32_STAGES, 1, 2>},
-    {2, 7, 2, pass_fp32_kernel<2, 7, F32_TILE, F32_STAGES, 2, 2>},
-    {4, 7, 2, pass_fp32_kernel<4, 7, F32_TILE, F32_STAGES, 2, 1>},
+    {2, 8, 2, pass_fp32_kernel<2, 8, F32_TILE, F32_STAGES, 2, 4>},
+    {2, 8, 2, pass_fp32_kernel<2, 8, F32_TILE, F32_STAGES, 2, 8>},
+    {2, 7, 2, pass_fp32_kernel<2, 7, F32_TILE, F32_STAGES, 2, 4>},
+    {2, 7, 2, pass_fp32_kernel<2, 7, F32_TILE, F32_STAGES, 2, 8>},
     {2, 8, 2, pass_fp32_kernel<2, 8, F32_TILE, F32_STAGES, 2, 2>},
-    {2, 3, 4, pass_fp32_kernel<2, 3, F32_TILE, F32_STAGES, 4, 2>},
 };
 constexpr int kNumF32Variants = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 constexpr int F64_BPT = 2, F64_TILE = 128, F64_STAGES = 3;
