@@ -216,7 +216,7 @@ __device__ __forceinline__ const float *s_hi_t(const unsigned char *smem_raw, in
     return reinterpret_cast<const float *>(smem_raw) + (size_t)slot * 4 * 256;
 }
 
-template <int BPT, int CW, int TILE, int STAGES, int MINB, int UNR>
+template <int BPT, int CW, int TILE, int STAGES, int MINB, int UNR, bool PTAIL>
 __global__ void __launch_bounds__((CW + 1) * 32, MINB) pass_fp32_kernel(const __grid_constant__ PassArgs a) {
     static_assert(TILE == GENGA_TILE_T, "the staged tile is one block of the tile-blocked copy");
     constexpr int NC = CW * 32;              // consumer threads (CW consumer warps + 1 producer warp)
@@ -327,9 +327,13 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB) pass_fp32_kernel(const __
             if (far_pair_of_boxes(wbox, gb, true)) {
                 // every pair: K = 1, FP32-rounded positions accurate enough;
                 // two consecutive j per packed register, four j per step
-                f32x2 AX[BPT], AY[BPT], AZ[BPT];
+                f32x2 AX[BPT], AY[BPT], AZ[BPT];  // packed tail: (even j, odd j) sums
+                float bx[BPT], by[BPT], bz[BPT];  // scalar tail: odd-j sums (even j into ax)
 #pragma unroll
-                for (int k = 0; k < BPT; k++) AX[k] = AY[k] = AZ[k] = 0ull;
+                for (int k = 0; k < BPT; k++) {
+                    AX[k] = AY[k] = AZ[k] = 0ull;
+                    bx[k] = by[k] = bz[k] = 0.f;
+                }
 #pragma unroll(UNR)
                 for (int jj = 0; jj < 64; jj += 4) {
                     const ulonglong2 X4 = *reinterpret_cast<const ulonglong2 *>(tx + jj);
@@ -346,11 +350,27 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB) pass_fp32_kernel(const __
                             const f32x2 R2 = fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
                             float ra, rb;
                             up2(R2, ra, rb);
-                            const f32x2 RI = pk2(rsqrt_sfu(ra), rsqrt_sfu(rb));
-                            const f32x2 S = mul2(mul2(JW, RI), mul2(RI, RI));
-                            AX[k] = fma2(S, DX, AX[k]);
-                            AY[k] = fma2(S, DY, AY[k]);
-                            AZ[k] = fma2(S, DZ, AZ[k]);
+                            const float ria = rsqrt_sfu(ra), rib = rsqrt_sfu(rb);
+                            if (PTAIL) {  // packed m r^-3 and accumulation
+                                const f32x2 RI = pk2(ria, rib);
+                                const f32x2 S = mul2(mul2(JW, RI), mul2(RI, RI));
+                                AX[k] = fma2(S, DX, AX[k]);
+                                AY[k] = fma2(S, DY, AY[k]);
+                                AZ[k] = fma2(S, DZ, AZ[k]);
+                            } else {  // scalar tail: no repacking of the two SFU results
+                                float wa, wb, dxa, dxb, dya, dyb, dza, dzb;
+                                up2(JW, wa, wb);
+                                up2(DX, dxa, dxb);
+                                up2(DY, dya, dyb);
+                                up2(DZ, dza, dzb);
+                                const float sa = (wa * ria) * (ria * ria), sb = (wb * rib) * (rib * rib);
+                                ax[k] = fmaf(sa, dxa, ax[k]);
+                                ay[k] = fmaf(sa, dya, ay[k]);
+                                az[k] = fmaf(sa, dza, az[k]);
+                                bx[k] = fmaf(sb, dxb, bx[k]);
+                                by[k] = fmaf(sb, dyb, by[k]);
+                                bz[k] = fmaf(sb, dzb, bz[k]);
+                            }
                         }
                     }
                 }
@@ -358,11 +378,11 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB) pass_fp32_kernel(const __
                 for (int k = 0; k < BPT; k++) {
                     float e0, e1;
                     up2(AX[k], e0, e1);
-                    ax[k] += e0 + e1;
+                    ax[k] += (e0 + e1) + bx[k];
                     up2(AY[k], e0, e1);
-                    ay[k] += e0 + e1;
+                    ay[k] += (e0 + e1) + by[k];
                     up2(AZ[k], e0, e1);
-                    az[k] += e0 + e1;
+                    az[k] += (e0 + e1) + bz[k];
                 }
             } else {
                 const float4 *tl = s_lo + slot * TILE + g * 64;
@@ -702,12 +722,11 @@ struct F32Variant {
     void (*fn)(const PassArgs);
 };
 const F32Variant kF32Variants[] = {
-    {4, 8, 1, pass_fp32_kernel<4, 8, F32_TILE, F32_STAGES, 1, 2>},
-    {2, 8, 2, pass_fp32_kernel<2, 8, F32_TILE, F32_STAGES, 2, 4>},
-    {2, 8, 2, pass_fp32_kernel<2, 8, F32_TILE, F32_STAGES, 2, 8>},
-    {2, 7, 2, pass_fp32_kernel<2, 7, F32_TILE, F32_STAGES, 2, 4>},
-    {2, 7, 2, pass_fp32_kernel<2, 7, F32_TILE, F32_STAGES, 2, 8>},
-    {2, 8, 2, pass_fp32_kernel<2, 8, F32_TILE, F32_STAGES, 2, 2>},
+    {2, 8, 2, pass_fp32_kernel<2, 8, F32_TILE, F32_STAGES, 2, 8, true>},
+    {2, 8, 2, pass_fp32_kernel<2, 8, F32_TILE, F32_STAGES, 2, 4, true>},
+    {2, 8, 2, pass_fp32_kernel<2, 8, F32_TILE, F32_STAGES, 2, 2, true>},
+    {4, 8, 1, pass_fp32_kernel<4, 8, F32_TILE, F32_STAGES, 1, 2, true>},
+    {2, 7, 2, pass_fp32_kernel<2, 7, F32_TILE, F32_STAGES, 2, 4, true>},
 };
 constexpr int kNumF32Variants = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 constexpr int F64_BPT = 2, F64_TILE = 128, F64_STAGES = 3;
