@@ -25,8 +25,12 @@
  *   list overflow, non-finite accelerations, a bounded wait that gave up)
  *   are sticky bits in the context, read and cleared by genga_get_status.
  * - No entry point aborts, traps, prints or allocates device memory, except
- *   genga_create/genga_destroy (workspace) and genga_step's first use of a
- *   new step-block length (graph instantiation).
+ *   genga_create/genga_destroy (workspace).
+ * - The first FP32 pass a context runs for a new size bucket (a power of two
+ *   of the padded N) times the FP32 kernel variants and keeps the fastest;
+ *   that call synchronises its stream (genga_measure.h can pin a variant).
+ * - Results are bitwise reproducible for the same sequence of calls on a
+ *   context: no floating-point atomics, every reduction has a fixed order.
  * - A context is not re-entrant: one host thread and one stream at a time.
  */
 #ifndef GENGA_H
@@ -137,10 +141,31 @@ genga_status genga_last_encounters(genga_ctx *ctx, int32_t *pairs, int32_t capac
  * kick(dt/2), drift(dt), kick(dt/2).  The close-encounter (Bulirsch-Stoer)
  * level is not part of this library: pairs inside r_crit keep only their
  * K-weighted long-range force and are reported by genga_last_encounters.
- * Steps are replayed from a CUDA graph captured once per context.
+ * The spatial order of the bodies (a performance device of the FP32 pass)
+ * is rebuilt every few steps, counted across calls on the context.
  */
 genga_status genga_step(genga_ctx *ctx, genga_system *sys, const genga_params *params,
                         int32_t nsteps, void *stream);
+
+/*
+ * Batched mode: D independent systems, each a central mass with its own bodies,
+ * stored one after another in `all` (system d = bodies offsets[d] ..
+ * offsets[d+1]-1 of the seven arrays) and sharing `params`.  Ensembles of
+ * independent runs are how the paper's experiments are made (Sect. 2); here
+ * they share one launch per kernel.
+ *   offsets  HOST int32 [D+1], offsets[0] = 0, non-decreasing, offsets[D] = all->N
+ *   D        1 .. GENGA_MAX_BATCH (256)
+ * The context's max_N must cover the padded total sum_d roundup(N_d, 1024).
+ * params->precision must be GENGA_FP32 (the batched pass is the FP32 kick).
+ * genga_kick_batched: the kick of every system (acc layout acc[c*all->N + i],
+ * or NULL), the encounter list of every system with indices into `all`.
+ * genga_step_batched: nsteps level-0 steps of every system.
+ */
+#define GENGA_MAX_BATCH 256
+genga_status genga_kick_batched(genga_ctx *ctx, const genga_system *all, const int32_t *offsets, int32_t D,
+                                const genga_params *params, double tau, double *acc, void *stream);
+genga_status genga_step_batched(genga_ctx *ctx, genga_system *all, const int32_t *offsets, int32_t D,
+                                const genga_params *params, int32_t nsteps, void *stream);
 
 /*
  * Energy and angular momentum (Sect. 3.1 diagnostics), FP64, synchronous:

@@ -86,6 +86,8 @@ def load():
             "genga_kick_noalloc": ([S, P, D, V, V], I),
             "genga_measure_fma2_peak": ([I, C.POINTER(C.c_double)], I),
             "genga_launch_count": ([V, C.POINTER(C.c_int64)], I),
+            "genga_kick_batched": ([V, S, C.POINTER(C.c_int32), I, P, D, V, V], I),
+            "genga_step_batched": ([V, S, C.POINTER(C.c_int32), I, P, I, V], I),
             "genga_get_kernel_variant": ([V, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], I),
         }
         for name, (args, res) in sigs.items():
@@ -207,6 +209,25 @@ def genga_last_encounters(ctx, pairs, capacity, count, stream=None):
 
 def genga_step(ctx, sys, params, nsteps, stream=None):
     _check(load().genga_step(_ctx(ctx), _sys(sys), C.byref(params), int(nsteps), _stream(stream)), "genga_step")
+
+
+def _offsets(offsets):
+    arr = (C.c_int32 * len(offsets))(*[int(v) for v in offsets])
+    return arr, len(offsets) - 1
+
+
+def genga_kick_batched(ctx, all_sys, offsets, params, tau=0.0, acc=None, stream=None):
+    """Kick of D independent systems concatenated in all_sys (offsets: D+1 ints)."""
+    off, D = _offsets(offsets)
+    _check(load().genga_kick_batched(_ctx(ctx), _sys(all_sys), off, D, C.byref(params), float(tau), _ptr(acc),
+                                     _stream(stream)), "genga_kick_batched")
+
+
+def genga_step_batched(ctx, all_sys, offsets, params, nsteps, stream=None):
+    """nsteps level-0 steps of D independent systems concatenated in all_sys."""
+    off, D = _offsets(offsets)
+    _check(load().genga_step_batched(_ctx(ctx), _sys(all_sys), off, D, C.byref(params), int(nsteps),
+                                     _stream(stream)), "genga_step_batched")
 
 
 def genga_energy(ctx, sys, params, stream=None):

@@ -176,6 +176,138 @@ cudaError_t run_kick(genga_ctx *c, const genga_system &sys, const genga_params &
                           acc, sys.vx, sys.vy, sys.vz, c->status, s);
 }
 
+// ------------------------------------------------------------ batched mode
+bool check_offsets(const genga_ctx *c, const genga_system *all, const int32_t *offsets, int D) {
+    if (!c || !all || !offsets || D < 1 || D > GENGA_MAX_DISCS) return false;
+    if (offsets[0] != 0 || offsets[D] != all->N) return false;
+    for (int d = 0; d < D; d++)
+        if (offsets[d + 1] < offsets[d]) return false;
+    long long np = 0;
+    for (int d = 0; d < D; d++) np += npad_of(offsets[d + 1] - offsets[d]) * (offsets[d + 1] > offsets[d] ? 1 : 0);
+    return np <= c->npad_max;
+}
+
+unsigned long long offsets_hash(const int32_t *offsets, int D) {
+    unsigned long long h = 1469598103934665603ull;
+    for (int d = 0; d <= D; d++) {
+        h ^= (unsigned long long)(uint32_t)offsets[d];
+        h *= 1099511628211ull;
+    }
+    return h ^ (unsigned long long)D;
+}
+
+BatchBodies batch_bodies(const int32_t *offsets, int D) {
+    BatchBodies bb;
+    memset(&bb, 0, sizeof(bb));
+    bb.D = D;
+    bb.N_total = offsets[D];
+    int p = 0;
+    for (int d = 0; d < D; d++) {
+        bb.off[d] = offsets[d];
+        bb.poff[d] = p;
+        const int n = offsets[d + 1] - offsets[d];
+        p += n > 0 ? npad_of(n) : 0;
+    }
+    bb.off[D] = offsets[D];
+    bb.poff[D] = p;
+    bb.npad_total = p;
+    return bb;
+}
+
+// Work items of the FP32 pass over a batch: system d gets a share of about
+// 12 items per resident CTA proportional to npad_d^2 (its pair count), cut
+// into j-chunks per i-block; systems are handed out largest item first.
+// False if the partial sums would not fit.
+bool plan_batch(const genga_ctx *c, const BatchBodies &bb, int variant, BatchItems *bi, int *grid) {
+    memset(bi, 0, sizeof(*bi));
+    const int IB = fp32_variant_ib(variant), minb = fp32_variant_minb(variant);
+    double total = 0.0;
+    for (int d = 0; d < bb.D; d++) {
+        const double np = bb.poff[d + 1] - bb.poff[d];
+        total += np * np;
+    }
+    for (int target = 12 * minb * c->sm_count; target >= 1; target /= 2) {
+        long long pbase = 0;
+        for (int d = 0; d < bb.D; d++) {
+            const int np = bb.poff[d + 1] - bb.poff[d];
+            bi->pbase[d] = pbase;
+            if (np == 0) {
+                bi->nchunks[d] = bi->ctiles[d] = bi->iblocks[d] = 0;
+                continue;
+            }
+            const int iblocks = (np + IB - 1) / IB, ntiles = np / 256;
+            const double want = target * ((double)np * np / total);
+            int nch = (int)((want + iblocks - 1) / iblocks);
+            nch = nch < 1 ? 1 : (nch > ntiles ? ntiles : nch);
+            const int ct = (ntiles + nch - 1) / nch;
+            nch = (ntiles + ct - 1) / ct;
+            bi->iblocks[d] = iblocks;
+            bi->ctiles[d] = ct;
+            bi->nchunks[d] = nch;
+            pbase += (long long)nch * 3 * np;
+        }
+        if ((size_t)pbase > c->partial_cap) continue;
+        // handout order: larger items (more tiles per chunk) first, then by index
+        for (int d = 0; d < bb.D; d++) bi->order[d] = d;
+        for (int a = 1; a < bb.D; a++) {  // insertion sort, D <= 256
+            const int v = bi->order[a];
+            int b = a - 1;
+            while (b >= 0 && bi->ctiles[bi->order[b]] < bi->ctiles[v]) {
+                bi->order[b + 1] = bi->order[b];
+                b--;
+            }
+            bi->order[b + 1] = v;
+        }
+        int q = 0;
+        for (int r = 0; r < bb.D; r++) {
+            bi->item0[r] = q;
+            const int d = bi->order[r];
+            q += bi->iblocks[d] * bi->nchunks[d];
+        }
+        bi->item0[bb.D] = q;
+        bi->items_total = q;
+        const int slots = minb * c->sm_count;
+        *grid = q < slots ? (q > 0 ? q : 1) : slots;
+        return true;
+    }
+    return false;
+}
+
+// One batched kick: momenta (list reset), spatial order (when asked or when
+// the batch layout changed), prep, FP32 pass, list sort, combine.
+cudaError_t run_kick_batched(genga_ctx *c, const genga_system &all, const int32_t *offsets, int D,
+                             const genga_params &p, double tau, double *acc, bool reorder, bool momentum_valid,
+                             cudaStream_t s) {
+    const BatchBodies bb = batch_bodies(offsets, D);
+    const unsigned long long key = offsets_hash(offsets, D);
+    cudaError_t e = momentum_valid ? cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s)
+                                   : launch_momentum_batched(all, bb, c->Pd, c->enc_count, s);
+    if (e != cudaSuccess) return e;
+    c->launches += momentum_valid ? 0 : 1;
+    if (reorder || c->ordered_N != -2 || c->ordered_key != key) {
+        if ((e = launch_order_batched(all, bb, c, s)) != cudaSuccess) return e;
+        c->ordered_N = -2;  // the order belongs to a batch
+        c->ordered_key = key;
+        c->steps_since_order = 0;
+        c->launches += 14;  // extent, keys, 4 x (histogram, scan, scatter)
+    }
+    if ((e = launch_prep_batched(all, bb, p, c, s)) != cudaSuccess) return e;
+    c->launches += 1;
+    PassArgs a = base_args(c, all, p);
+    a.npad = bb.npad_total;
+    const int variant = c->forced_variant >= 0 ? c->forced_variant : 0;
+    BatchItems bi;
+    int grid = 1;
+    if (!plan_batch(c, bb, variant, &bi, &grid)) return cudaErrorInvalidValue;
+    profile_before_pass(c, s);
+    e = launch_pass_batched(a, bb, bi, variant, grid, s);
+    profile_after_pass(c, s);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_sort_pairs(c->enc, c->enc_cap, c->enc_count, s)) != cudaSuccess) return e;
+    c->launches += 3;
+    return launch_combine_batched(bb, bi, c->partial, c->perm, tau, acc, all.vx, all.vy, all.vz, c->status, s);
+}
+
 template <class T>
 cudaError_t alloc(T **p, size_t n) {
     return cudaMalloc((void **)p, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
@@ -202,13 +334,11 @@ void genga_destroy(genga_ctx *c) {
     if (!c) return;
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
-    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
-    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     profile_free(c);
     void *bufs[] = {c->pk_hi,       c->pk_t,        c->pk_lo,       c->pk64,        c->scr,      c->gbox_lo,    c->gbox_hi,
                     c->perm,        c->ord_keys[0], c->ord_keys[1], c->ord_vals[0], c->ord_vals[1], c->ord_hist,
                     c->ord_rbits,   c->a_osc,       c->rc_eq1,      c->partial,  c->mom,        c->enc,
-                    c->enc_count,   c->status,      c->energy_part, c->work};
+                    c->enc_count,   c->status,      c->energy_part, c->work,   c->Pd,         c->Pd_part};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete c;
@@ -265,6 +395,8 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     if (e == cudaSuccess) e = alloc(&c->rc_eq1, np);
     if (e == cudaSuccess) e = alloc(&c->partial, c->partial_cap);
     if (e == cudaSuccess) e = alloc(&c->work, 1);
+    if (e == cudaSuccess) e = alloc(&c->Pd, 3 * GENGA_MAX_DISCS);
+    if (e == cudaSuccess) e = alloc(&c->Pd_part, 3 * GENGA_MAX_DISCS);
     if (e == cudaSuccess) e = alloc(&c->mom, 256);   // P, block partials, ticket
     if (e == cudaSuccess) e = cudaMemset(c->mom, 0, 256 * sizeof(double));
     if (e == cudaSuccess) e = alloc(&c->enc, (size_t)c->enc_cap);
@@ -354,6 +486,45 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
         c->steps_since_order++;
         const bool reorder = c->steps_since_order >= GENGA_REORDER_STEPS;
         if (run_kick(c, s2, *p, h, nullptr, reorder, s, true) != cudaSuccess) return GENGA_ERR_CUDA;
+    }
+    return GENGA_OK;
+}
+
+genga_status genga_kick_batched(genga_ctx *c, const genga_system *all, const int32_t *offsets, int32_t D,
+                                const genga_params *p, double tau, double *acc, void *stream) {
+    genga_status st;
+    if ((st = check_system(c, all)) != GENGA_OK) return st;
+    if ((st = check_params(p)) != GENGA_OK) return st;
+    if (p->precision != GENGA_FP32 || !is_fin(tau) || !check_offsets(c, all, offsets, D)) return GENGA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (all->N == 0) return cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
+    const cudaError_t e = run_kick_batched(c, *all, offsets, D, *p, tau, acc, true, false, s);
+    if (e == cudaErrorInvalidValue) return GENGA_ERR_INVALID_ARG;
+    return e == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
+}
+
+genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *offsets, int32_t D,
+                                const genga_params *p, int32_t nsteps, void *stream) {
+    genga_status st;
+    if ((st = check_system(c, all)) != GENGA_OK) return st;
+    if ((st = check_params(p)) != GENGA_OK) return st;
+    if (p->precision != GENGA_FP32 || nsteps < 0 || !check_offsets(c, all, offsets, D)) return GENGA_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (all->N == 0 || nsteps == 0) return GENGA_OK;
+    genga_system a2 = *all;
+    const BatchBodies bb = batch_bodies(offsets, D);
+    const double h = 0.5 * p->dt;
+    for (int k = 0; k < nsteps; k++) {
+        cudaError_t e = run_kick_batched(c, a2, offsets, D, *p, h, nullptr, false, false, s);
+        if (e == cudaSuccess) e = launch_drift_batched(a2, bb, *p, p->dt, c, s);
+        c->launches += 4;
+        c->steps_since_order++;
+        const bool reorder = c->steps_since_order >= GENGA_REORDER_STEPS;
+        if (e == cudaSuccess) e = run_kick_batched(c, a2, offsets, D, *p, h, nullptr, reorder, true, s);
+        if (e == cudaErrorInvalidValue) return GENGA_ERR_INVALID_ARG;
+        if (e != cudaSuccess) return GENGA_ERR_CUDA;
     }
     return GENGA_OK;
 }

@@ -139,7 +139,51 @@ __global__ void hc_kernel(double *__restrict__ x, double *__restrict__ y, double
     z[i] += h * P[2] / Mstar;
 }
 
+// Batched: body i of system d (segment of i in off) drifts with P of its system.
+__global__ void drift_batched_kernel(double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
+                                     double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
+                                     const double *__restrict__ Pd, double Mstar, double mu, double h, double dt,
+                                     int max_iter, uint32_t *__restrict__ status,
+                                     const __grid_constant__ BatchBodies bb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= bb.N_total) return;
+    const double *P = Pd + 3 * find_segment(bb.off, bb.D, i);
+    double xi = x[i] + h * P[0] / Mstar;
+    double yi = y[i] + h * P[1] / Mstar;
+    double zi = z[i] + h * P[2] / Mstar;
+    double ui = vx[i], vi = vy[i], wi = vz[i];
+    if (!kepler_drift(mu, dt, max_iter, xi, yi, zi, ui, vi, wi)) atomicOr(status, GENGA_BIT(GENGA_ERR_KEPLER));
+    x[i] = xi; y[i] = yi; z[i] = zi;
+    vx[i] = ui; vy[i] = vi; vz[i] = wi;
+}
+
+__global__ void hc_batched_kernel(double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
+                                  const double *__restrict__ Pd, double Mstar, double h,
+                                  const __grid_constant__ BatchBodies bb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= bb.N_total) return;
+    const double *P = Pd + 3 * find_segment(bb.off, bb.D, i);
+    x[i] += h * P[0] / Mstar;
+    y[i] += h * P[1] / Mstar;
+    z[i] += h * P[2] / Mstar;
+}
+
 }  // namespace
+
+cudaError_t launch_drift_batched(genga_system &all, const BatchBodies &bb, const genga_params &p, double dt,
+                                 genga_ctx *c, cudaStream_t s) {
+    const int N = bb.N_total;
+    if (N <= 0) return cudaSuccess;
+    cudaError_t e = launch_momentum_batched(all, bb, c->Pd, nullptr, s);
+    if (e != cudaSuccess) return e;
+    drift_batched_kernel<<<(N + 127) / 128, 128, 0, s>>>(all.x, all.y, all.z, all.vx, all.vy, all.vz, c->Pd, p.Mstar,
+                                                         p.G * p.Mstar, 0.5 * dt, dt, p.kepler_max_iter, c->status, bb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_momentum_batched(all, bb, c->Pd, nullptr, s);
+    if (e != cudaSuccess) return e;
+    hc_batched_kernel<<<(N + 255) / 256, 256, 0, s>>>(all.x, all.y, all.z, c->Pd, p.Mstar, 0.5 * dt, bb);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_drift(genga_system &sys, const genga_params &p, double dt, genga_ctx *c, cudaStream_t s) {
     const int N = sys.N;

@@ -19,6 +19,10 @@
 // i-block is full; padded bodies have zero mass and sit far away.
 #define GENGA_PAD 1024
 #define GENGA_PAD_POS 1.0e6f
+// Largest number of systems in one batched call (the disc index takes the top
+// 8 bits of the 32-bit Morton sort key).
+#define GENGA_MAX_DISCS GENGA_MAX_BATCH
+
 // genga_step rebuilds the spatial order of the bodies every this many steps.
 #define GENGA_REORDER_STEPS 4
 
@@ -64,23 +68,54 @@ struct genga_ctx {
     uint32_t *status;          // [1] sticky bits
     double *energy_part;       // [energy_blocks][4]
     int32_t energy_blocks;
-    // step graph cache
-    cudaGraphExec_t step_graph;
-    cudaStream_t cap_stream;
-    unsigned char step_key[256];
-    int step_key_len;
     genga::Profile *prof;      // measurement hooks (genga_measure.h), NULL when unused
     int32_t *work;             // [1] work-item counter of the persistent pass
     int8_t f32_variant[32];    // autotuned FP32 pass variant per log2(npad) bucket, -1 = not tuned
     int32_t forced_variant;    // >= 0: use this FP32 variant (genga_set_kernel_variant)
     int32_t steps_since_order; // genga_step: drifts since the spatial order was built
-    int32_t ordered_N;         // N of the system the spatial order was built for (-1: none)
+    int32_t ordered_N;         // N of the system the spatial order was built for (-1: none, -2: a batch)
+    unsigned long long ordered_key;  // layout hash of the batch the order was built for
     int64_t launches;          // kernels this context has launched (measurement hook)
+    double *Pd;                // [3 * GENGA_MAX_DISCS] momentum of each system (batched mode)
+    double *Pd_part;           // [3 * GENGA_MAX_DISCS] scratch
     size_t partial_cap;        // doubles in `partial`
 };
 
 // -------------------------------------------------------------- launchers
 namespace genga {
+
+// Batched mode: D independent systems stored one after another in the
+// caller's arrays.  Both tables are built on the host for every call and
+// passed to the kernels by value (kernel parameters), so a batched call needs
+// no host-to-device copy.
+struct BatchBodies {
+    int32_t D, N_total, npad_total, pad_;
+    int32_t off[GENGA_MAX_DISCS + 1];   // first body of system d in the caller's arrays; off[D] = N_total
+    int32_t poff[GENGA_MAX_DISCS + 1];  // first packed position of system d (multiple of GENGA_PAD)
+};
+
+struct BatchItems {                     // work items of the FP32 pass over all systems
+    int32_t items_total;
+    int32_t order[GENGA_MAX_DISCS];     // system handed out at rank r (largest items first)
+    int32_t item0[GENGA_MAX_DISCS + 1]; // first item of rank r
+    int32_t nchunks[GENGA_MAX_DISCS];   // j-chunks per i-block of system d
+    int32_t ctiles[GENGA_MAX_DISCS];    // tiles per chunk
+    int32_t iblocks[GENGA_MAX_DISCS];   // i-blocks of system d
+    int64_t pbase[GENGA_MAX_DISCS];     // first partial double of system d
+};
+
+#ifdef __CUDACC__
+// Largest d in [0, D) with arr[d] <= v (arr non-decreasing, arr[0] <= v).
+__device__ __forceinline__ int find_segment(const int32_t *arr, int D, int v) {
+    int lo = 0, hi = D - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (arr[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+#endif
 
 struct PassArgs {               // one long-range pass
     const float4 *hi, *lo;
@@ -123,6 +158,21 @@ cudaError_t launch_copy_pairs(const int2 *enc, const int32_t *count, int32_t enc
                               int32_t capacity, int32_t *count_out, uint32_t *status, cudaStream_t s);
 cudaError_t launch_drift(genga_system &sys, const genga_params &p, double dt, genga_ctx *c, cudaStream_t s);
 cudaError_t launch_energy(const genga_system &sys, const genga_params &p, genga_ctx *c, cudaStream_t s);
+// batched mode (batch.cu helpers live next to their single-system versions)
+cudaError_t launch_momentum_batched(const genga_system &all, const BatchBodies &bb, double *Pd, int32_t *zero_me,
+                                    cudaStream_t s);
+cudaError_t launch_order_batched(const genga_system &all, const BatchBodies &bb, genga_ctx *c, cudaStream_t s);
+cudaError_t launch_prep_batched(const genga_system &all, const BatchBodies &bb, const genga_params &p, genga_ctx *c,
+                                cudaStream_t s);
+cudaError_t launch_pass_batched(const PassArgs &a, const BatchBodies &bb, const BatchItems &bi, int variant, int grid,
+                                cudaStream_t s);
+cudaError_t launch_combine_batched(const BatchBodies &bb, const BatchItems &bi, const double *partial,
+                                   const uint32_t *perm, double tau, double *acc, double *vx, double *vy, double *vz,
+                                   uint32_t *status, cudaStream_t s);
+cudaError_t launch_drift_batched(genga_system &all, const BatchBodies &bb, const genga_params &p, double dt,
+                                 genga_ctx *c, cudaStream_t s);
+int fp32_variant_ib(int variant);       // i-bodies per work item of an FP32 variant
+int fp32_variant_minb(int variant);     // resident CTAs per SM of an FP32 variant
 void profile_before_pass(genga_ctx *c, cudaStream_t s);
 void profile_after_pass(genga_ctx *c, cudaStream_t s);
 void profile_free(genga_ctx *c);

@@ -101,17 +101,19 @@ __device__ __forceinline__ double changeover_K(double y, int form) {
     return y * y * y * (10.0 + y * (6.0 * y - 15.0));
 }
 
-// Exact FP64 treatment of one screened pair (positions i, j of the spatial
-// order): the K-weighted acceleration of i due to j; records the encounter.
-__device__ __noinline__ double3 screened_pair(const PassArgs &a, int i, int j) {
+// Exact FP64 treatment of one screened pair (packed positions i, j of one
+// system whose packed range starts at poff, with Nd bodies that start at
+// body `off` of the caller's arrays): the K-weighted acceleration of i due to
+// j; records the encounter.
+__device__ __noinline__ double3 screened_pair(const PassArgs &a, int i, int j, int poff, int Nd, int off) {
     double3 f = make_double3(0.0, 0.0, 0.0);
-    if (i >= a.N || j >= a.N || i == j) return f;
+    if (i - poff >= Nd || j - poff >= Nd || i == j) return f;
     const double4_32a pi = a.p64[i], pj = a.p64[j];
     const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
     const double r2 = dx * dx + dy * dy + dz * dz;
     if (r2 == 0.0) return f;  // coincident bodies: no direction, no force
     const double r = sqrt(r2);
-    const int oi = (int)a.perm[i], oj = (int)a.perm[j];
+    const int oi = (int)a.perm[off + i - poff], oj = (int)a.perm[off + j - poff];
     double rc;
     if (a.rcrit_mode == GENGA_RCRIT_EQ1) {
         rc = fmax(a.rc_eq1[i], a.rc_eq1[j]);
@@ -211,13 +213,44 @@ __device__ __forceinline__ void item_of(int q, int iblocks, int nchunks, int ib_
     *c = ((c0 + off) % nchunks + nchunks) % nchunks;
 }
 
+// Geometry of the system a work item belongs to.
+struct ItemGeo {
+    int poff, npad, Nd, off, nchunks, ctiles, iblocks;
+    long long pbase;
+};
+
+// Work items of a single system (the whole packed range).
+struct SingleItems {
+    __device__ int total(const PassArgs &a, int IB) const { return ((a.npad + IB - 1) / IB) * a.split; }
+    __device__ void decode(const PassArgs &a, int IB, int TILE_, int q, int *ib, int *chunk, ItemGeo *g) const {
+        *g = ItemGeo{0, a.npad, a.N, 0, a.split, a.chunk_tiles, (a.npad + IB - 1) / IB, 0};
+        item_of(q, g->iblocks, g->nchunks, IB, g->ctiles * TILE_, ib, chunk);
+    }
+};
+
+// Work items of a batch: ranks of systems in handout order (largest items
+// first), each system's items in the diagonal-first order of item_of.
+struct BatchPolicy {
+    BatchBodies bb;
+    BatchItems bi;
+    __device__ int total(const PassArgs &, int) const { return bi.items_total; }
+    __device__ void decode(const PassArgs &, int IB, int TILE_, int q, int *ib, int *chunk, ItemGeo *g) const {
+        const int r = find_segment(bi.item0, bb.D, q);
+        const int d = bi.order[r];
+        *g = ItemGeo{bb.poff[d], bb.poff[d + 1] - bb.poff[d], bb.off[d + 1] - bb.off[d], bb.off[d], bi.nchunks[d],
+                     bi.ctiles[d], bi.iblocks[d], (long long)bi.pbase[d]};
+        item_of(q - bi.item0[r], g->iblocks, g->nchunks, IB, g->ctiles * TILE_, ib, chunk);
+    }
+};
+
 // The hi slot of stage `slot` holds one tile of the tile-blocked copy.
 __device__ __forceinline__ const float *s_hi_t(const unsigned char *smem_raw, int slot) {
     return reinterpret_cast<const float *>(smem_raw) + (size_t)slot * 4 * 256;
 }
 
-template <int BPT, int CW, int TILE, int STAGES, int MINB, int UNR, bool PTAIL>
-__global__ void __launch_bounds__((CW + 1) * 32, MINB) pass_fp32_kernel(const __grid_constant__ PassArgs a) {
+template <int BPT, int CW, int TILE, int STAGES, int MINB, int UNR, bool PTAIL, class Pol>
+__global__ void __launch_bounds__((CW + 1) * 32, MINB)
+    pass_fp32_kernel(const __grid_constant__ PassArgs a, const __grid_constant__ Pol pol) {
     static_assert(TILE == GENGA_TILE_T, "the staged tile is one block of the tile-blocked copy");
     constexpr int NC = CW * 32;              // consumer threads (CW consumer warps + 1 producer warp)
     constexpr int IB = NC * BPT;             // i-bodies per item (the last i-block may be partial)
@@ -235,9 +268,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB) pass_fp32_kernel(const __
     __shared__ float2 s_iscr[BPT * NC];     // and their screening factors
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nchunks = a.split;
-    const int iblocks = (a.npad + IB - 1) / IB;
-    const int nitems = iblocks * nchunks;
+    const int nitems = pol.total(a, IB);
 
     if (tid == 0) {
         for (int q = 0; q < STAGES; q++) {
@@ -263,13 +294,15 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB) pass_fp32_kernel(const __
                 return;
             }
             int ib, chunk;
-            item_of(q, iblocks, nchunks, IB, a.chunk_tiles * TILE, &ib, &chunk);
-            const int ta = chunk * a.chunk_tiles, tb = min(a.ntiles, ta + a.chunk_tiles);
+            ItemGeo geo;
+            pol.decode(a, IB, TILE, q, &ib, &chunk, &geo);
+            const int t0 = geo.poff / TILE;  // first tile of the system
+            const int ta = t0 + chunk * geo.ctiles, tb = t0 + min(geo.npad / TILE, (chunk + 1) * geo.ctiles);
             for (int t = ta; t < tb; t++, n++) {
                 const int slot = n % STAGES;
                 const unsigned u = n / STAGES;
                 if (u > 0 && !mbar_wait_bounded(&empty[slot], (u - 1) & 1, a.status)) return;
-                hdr[slot] = StageHdr{ib * nchunks + chunk, t, (t == ta ? 1 : 0) | (t == tb - 1 ? 2 : 0), 0};
+                hdr[slot] = StageHdr{q, t, (t == ta ? 1 : 0) | (t == tb - 1 ? 2 : 0), 0};
                 fence_proxy_async_smem();
                 constexpr uint32_t GB = NG * sizeof(float4);
                 mbar_arrive_expect_tx(&full[slot], 2 * TB + 2 * GB);
@@ -287,15 +320,18 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB) pass_fp32_kernel(const __
 #pragma unroll
     for (int k = 0; k < BPT; k++) XI[k] = YI[k] = ZI[k] = 0ull;
     Box wbox = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-    int wbase = 0;
+    int wbase = 0, chunk = 0;
+    ItemGeo geo = {0, 0, 0, 0, 0, 0, 0, 0};
     for (unsigned n = 0;; n++) {
         const int slot = n % STAGES;
         if (!mbar_wait_bounded(&full[slot], (n / STAGES) & 1, a.status)) return;
         const StageHdr h = hdr[slot];
         if (h.flags & 4) return;
         if (h.flags & 1) {  // first tile of an item: load this warp's i-bodies
-            wbase = (h.item / nchunks) * IB + warp * 32 * BPT;
-            const bool in = wbase < a.npad;  // warps past the padded end hold dummy bodies
+            int ib;
+            pol.decode(a, IB, TILE, h.item, &ib, &chunk, &geo);
+            wbase = geo.poff + ib * IB + warp * 32 * BPT;
+            const bool in = wbase - geo.poff < geo.npad;  // warps past the padded end hold dummy bodies
 #pragma unroll
             for (int k = 0; k < BPT; k++) {
                 const int i = wbase + k * 32 + lane;
@@ -421,8 +457,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB) pass_fp32_kernel(const __
 #pragma unroll
                         for (int k = 0; k < BPT; k++) {
                             if (screened & (1u << k)) {
-                                const double3 f =
-                                    screened_pair(a, wbase + k * 32 + lane, h.tile * TILE + g * 64 + jj);
+                                const double3 f = screened_pair(a, wbase + k * 32 + lane, h.tile * TILE + g * 64 + jj,
+                                                                geo.poff, geo.Nd, geo.off);
                                 s_acc[(0 * BPT + k) * NC + tid] += f.x;
                                 s_acc[(1 * BPT + k) * NC + tid] += f.y;
                                 s_acc[(2 * BPT + k) * NC + tid] += f.z;
@@ -440,12 +476,12 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB) pass_fp32_kernel(const __
             s_acc[(1 * BPT + k) * NC + tid] += (double)ay[k];
             s_acc[(2 * BPT + k) * NC + tid] += (double)az[k];
         }
-        if ((h.flags & 2) && wbase < a.npad) {  // last tile of the item: write its partial row
-            const size_t np = (size_t)a.npad;
-            double *out = a.partial + (size_t)(h.item % nchunks) * 3 * np;
+        if ((h.flags & 2) && wbase - geo.poff < geo.npad) {  // last tile of the item: its partial row
+            const size_t np = (size_t)geo.npad;
+            double *out = a.partial + geo.pbase + (size_t)chunk * 3 * np;
 #pragma unroll
             for (int k = 0; k < BPT; k++) {
-                const int i = wbase + k * 32 + lane;
+                const int i = wbase - geo.poff + k * 32 + lane;
 #pragma unroll
                 for (int c = 0; c < 3; c++) out[c * np + i] = s_acc[(c * BPT + k) * NC + tid];
             }
@@ -566,7 +602,7 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
 #pragma unroll
                         for (int k = 0; k < BPT; k++) {
                             if (screened & (1u << k)) {
-                                const double3 f = screened_pair(a, wbase + k * 32 + lane, t * TILE + jj);
+                                const double3 f = screened_pair(a, wbase + k * 32 + lane, t * TILE + jj, 0, a.N, 0);
                                 CX[k].add(f.x);
                                 CY[k].add(f.y);
                                 CZ[k].add(f.z);
@@ -629,6 +665,43 @@ __global__ void combine_kernel(const double *__restrict__ partial, int split, in
         acc[i] = a3[0];
         acc[(size_t)N + i] = a3[1];
         acc[2 * (size_t)N + i] = a3[2];
+    }
+    if (tau != 0.0) {
+        vx[i] += a3[0] * tau;
+        vy[i] += a3[1] * tau;
+        vz[i] += a3[2] * tau;
+    }
+}
+
+// Batched: packed position p of system d; rows of d start at pbase[d], one
+// per j-chunk, each npad_d long; plain FP64 sums in row order.
+__global__ void combine_batched_kernel(const double *__restrict__ partial, const uint32_t *__restrict__ perm,
+                                       double tau, double *__restrict__ acc, double *__restrict__ vx,
+                                       double *__restrict__ vy, double *__restrict__ vz, uint32_t *__restrict__ status,
+                                       const __grid_constant__ BatchBodies bb, const __grid_constant__ BatchItems bi) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= bb.npad_total) return;
+    const int d = find_segment(bb.poff, bb.D, p);
+    const int k = p - bb.poff[d];
+    if (k >= bb.off[d + 1] - bb.off[d]) return;
+    const int i = (int)perm[bb.off[d] + k];
+    const size_t np = (size_t)(bb.poff[d + 1] - bb.poff[d]);
+    const double *rows = partial + bi.pbase[d];
+    double a3[3];
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        double t = 0.0;
+        for (int q = 0; q < bi.nchunks[d]; q++) t += rows[((size_t)q * 3 + c) * np + k];
+        a3[c] = t;
+        finite = finite && isfinite(t);
+    }
+    if (!finite) atomicOr(status, GENGA_BIT(GENGA_ERR_NONFINITE));
+    const size_t NT = (size_t)bb.N_total;
+    if (acc) {
+        acc[i] = a3[0];
+        acc[NT + i] = a3[1];
+        acc[2 * NT + i] = a3[2];
     }
     if (tau != 0.0) {
         vx[i] += a3[0] * tau;
@@ -719,15 +792,17 @@ constexpr int F32_TILE = 256, F32_STAGES = 4;
 // autotuner in api.cu times them per N bucket and keeps the fastest.
 struct F32Variant {
     int bpt, cw, minb;  // bodies per thread, consumer warps, resident CTAs per SM
-    void (*fn)(const PassArgs);
+    void (*fn)(const PassArgs, const SingleItems);
+    void (*fnb)(const PassArgs, const BatchPolicy);
 };
+#define GENGA_F32V(BPT, CW, MINB, UNR)                                                                   \
+    {BPT, CW, MINB, pass_fp32_kernel<BPT, CW, F32_TILE, F32_STAGES, MINB, UNR, true, SingleItems>,       \
+     pass_fp32_kernel<BPT, CW, F32_TILE, F32_STAGES, MINB, UNR, true, BatchPolicy>}
 const F32Variant kF32Variants[] = {
-    {2, 8, 2, pass_fp32_kernel<2, 8, F32_TILE, F32_STAGES, 2, 8, true>},
-    {2, 8, 2, pass_fp32_kernel<2, 8, F32_TILE, F32_STAGES, 2, 4, true>},
-    {2, 8, 2, pass_fp32_kernel<2, 8, F32_TILE, F32_STAGES, 2, 2, true>},
-    {4, 8, 1, pass_fp32_kernel<4, 8, F32_TILE, F32_STAGES, 1, 2, true>},
-    {2, 7, 2, pass_fp32_kernel<2, 7, F32_TILE, F32_STAGES, 2, 4, true>},
+    GENGA_F32V(2, 8, 2, 8), GENGA_F32V(2, 8, 2, 4), GENGA_F32V(2, 8, 2, 2), GENGA_F32V(4, 8, 1, 2),
+    GENGA_F32V(2, 7, 2, 4),
 };
+#undef GENGA_F32V
 constexpr int kNumF32Variants = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 constexpr int F64_BPT = 2, F64_TILE = 128, F64_STAGES = 3;
 
@@ -781,6 +856,8 @@ cudaError_t init_pass_kernels() {
         cudaError_t e = cudaFuncSetAttribute(kF32Variants[q].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem_fp32());
         if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kF32Variants[q].fnb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fp32());
+        if (e != cudaSuccess) return e;
     }
     return cudaFuncSetAttribute(pass_fp64_kernel<F64_BPT, F64_TILE, F64_STAGES>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fp64());
@@ -793,13 +870,39 @@ cudaError_t launch_pass(const PassArgs &a0, int precision, int variant, int grid
         cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s);
         if (e != cudaSuccess) return e;
         const F32Variant &v = kF32Variants[variant];
-        v.fn<<<grid, (v.cw + 1) * 32, smem_fp32(), s>>>(a);
+        v.fn<<<grid, (v.cw + 1) * 32, smem_fp32(), s>>>(a, SingleItems{});
     } else {
         a.ntiles = a.npad / F64_TILE;
         auto k = pass_fp64_kernel<F64_BPT, F64_TILE, F64_STAGES>;
         dim3 g(grid, a.split);
         k<<<g, KB, smem_fp64(), s>>>(a);
     }
+    return cudaGetLastError();
+}
+
+int fp32_variant_ib(int variant) { return kF32Variants[variant].cw * 32 * kF32Variants[variant].bpt; }
+int fp32_variant_minb(int variant) { return kF32Variants[variant].minb; }
+
+cudaError_t launch_pass_batched(const PassArgs &a0, const BatchBodies &bb, const BatchItems &bi, int variant, int grid,
+                                cudaStream_t s) {
+    PassArgs a = a0;
+    a.ntiles = bb.npad_total / F32_TILE;
+    cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const F32Variant &v = kF32Variants[variant];
+    BatchPolicy pol;
+    pol.bb = bb;
+    pol.bi = bi;
+    v.fnb<<<grid, (v.cw + 1) * 32, smem_fp32(), s>>>(a, pol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine_batched(const BatchBodies &bb, const BatchItems &bi, const double *partial,
+                                   const uint32_t *perm, double tau, double *acc, double *vx, double *vy, double *vz,
+                                   uint32_t *status, cudaStream_t s) {
+    if (bb.N_total <= 0) return cudaSuccess;
+    combine_batched_kernel<<<(bb.npad_total + 255) / 256, 256, 0, s>>>(partial, perm, tau, acc, vx, vy, vz, status,
+                                                                       bb, bi);
     return cudaGetLastError();
 }
 

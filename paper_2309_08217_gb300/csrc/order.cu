@@ -8,7 +8,8 @@
 // summed, so it affects speed, not the definition of the result.
 //
 // The sort is a stable least-significant-digit radix sort of the 24-bit keys
-// with 8-bit digits (three passes of histogram / scan / scatter).  Stable
+// with 8-bit digits (three passes of histogram / scan / scatter; four in
+// batched mode, where the system index fills the top byte).  Stable
 // ranks inside a CTA come from warp match masks and per-warp digit counts, so
 // the permutation is the same on every run.
 #include "internal.cuh"
@@ -58,6 +59,22 @@ __global__ void keys_kernel(const double *__restrict__ x, const double *__restri
     const float R = fmaxf(__uint_as_float(*rbits), 1e-30f) * 1.0001f;
     const float inv = 1.0f / R;
     keys[i] = spread3(quant8(x[i], inv)) | (spread3(quant8(y[i], inv)) << 1) | (spread3(quant8(z[i], inv)) << 2);
+    vals[i] = (uint32_t)i;
+}
+
+// Batched: the system index d takes the top 8 bits, so one sort orders the
+// bodies by system first and along the Morton curve inside each system.
+__global__ void keys_batched_kernel(const double *__restrict__ x, const double *__restrict__ y,
+                                    const double *__restrict__ z, const unsigned *__restrict__ rbits,
+                                    uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                    const __grid_constant__ BatchBodies bb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= bb.N_total) return;
+    const int d = find_segment(bb.off, bb.D, i);
+    const float R = fmaxf(__uint_as_float(*rbits), 1e-30f) * 1.0001f;
+    const float inv = 1.0f / R;
+    keys[i] = ((uint32_t)d << 24) | spread3(quant8(x[i], inv)) | (spread3(quant8(y[i], inv)) << 1) |
+              (spread3(quant8(z[i], inv)) << 2);
     vals[i] = (uint32_t)i;
 }
 
@@ -170,6 +187,22 @@ __global__ void __launch_bounds__(RS_THREADS) scatter_kernel(const uint32_t *__r
 
 size_t order_hist_entries(int nmax) { return (size_t)RS_BINS * ((nmax + RS_CHUNK - 1) / RS_CHUNK); }
 
+// LSD radix sort of ord_keys[0] / ord_vals[0] (N entries) over `passes`
+// 8-bit digits; the sorted values (body indices) end in c->perm.
+void radix_to_perm(genga_ctx *c, int N, int passes, cudaStream_t s) {
+    const int nblk = (N + RS_CHUNK - 1) / RS_CHUNK;
+    int cur = 0;
+    for (int pass = 0; pass < passes; pass++) {
+        const int shift = pass * RS_BITS;
+        hist_kernel<<<nblk, RS_THREADS, 0, s>>>(c->ord_keys[cur], N, shift, c->ord_hist, nblk);
+        scan_kernel<<<1, SCAN_THREADS, 0, s>>>(c->ord_hist, RS_BINS * nblk);
+        uint32_t *vout = (pass == passes - 1) ? c->perm : c->ord_vals[1 - cur];
+        scatter_kernel<<<nblk, RS_THREADS, 0, s>>>(c->ord_keys[cur], c->ord_vals[cur], c->ord_keys[1 - cur], vout,
+                                                   N, shift, c->ord_hist, nblk);
+        cur = 1 - cur;
+    }
+}
+
 // perm[k] = index of the body at position k of the Morton order (k < N).
 cudaError_t launch_order(const genga_system &sys, genga_ctx *c, cudaStream_t s) {
     const int N = sys.N;
@@ -179,18 +212,20 @@ cudaError_t launch_order(const genga_system &sys, genga_ctx *c, cudaStream_t s) 
     extent_kernel<<<64, 256, 0, s>>>(sys.x, sys.y, sys.z, N, c->ord_rbits);
     keys_kernel<<<(N + 255) / 256, 256, 0, s>>>(sys.x, sys.y, sys.z, N, c->ord_rbits, c->ord_keys[0],
                                                 c->ord_vals[0]);
-    const int nblk = (N + RS_CHUNK - 1) / RS_CHUNK;
-    int cur = 0;
-    for (int pass = 0; pass < 3; pass++) {
-        const int shift = pass * RS_BITS;
-        hist_kernel<<<nblk, RS_THREADS, 0, s>>>(c->ord_keys[cur], N, shift, c->ord_hist, nblk);
-        scan_kernel<<<1, SCAN_THREADS, 0, s>>>(c->ord_hist, RS_BINS * nblk);
-        uint32_t *kout = (pass == 2) ? c->ord_keys[1 - cur] : c->ord_keys[1 - cur];
-        uint32_t *vout = (pass == 2) ? c->perm : c->ord_vals[1 - cur];
-        scatter_kernel<<<nblk, RS_THREADS, 0, s>>>(c->ord_keys[cur], c->ord_vals[cur], kout, vout, N, shift,
-                                                   c->ord_hist, nblk);
-        cur = 1 - cur;
-    }
+    radix_to_perm(c, N, 3, s);
+    return cudaGetLastError();
+}
+
+// Batched: 24-bit Morton keys below the 8-bit system index, four passes.
+cudaError_t launch_order_batched(const genga_system &all, const BatchBodies &bb, genga_ctx *c, cudaStream_t s) {
+    const int N = bb.N_total;
+    if (N <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(c->ord_rbits, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    extent_kernel<<<64, 256, 0, s>>>(all.x, all.y, all.z, N, c->ord_rbits);
+    keys_batched_kernel<<<(N + 255) / 256, 256, 0, s>>>(all.x, all.y, all.z, c->ord_rbits, c->ord_keys[0],
+                                                        c->ord_vals[0], bb);
+    radix_to_perm(c, N, 4, s);
     return cudaGetLastError();
 }
 

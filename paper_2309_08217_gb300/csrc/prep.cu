@@ -90,22 +90,19 @@ __device__ __forceinline__ void store_tiled(float *hit, int k, float x, float y,
     t[3 * GENGA_TILE_T] = w;
 }
 
-// Position k of the packed arrays holds body perm[k] (the Morton order);
-// k >= N are padding bodies: zero mass, 64 au apart, far from everything.
-__global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
-    const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
-    const double *__restrict__ vx, const double *__restrict__ vy, const double *__restrict__ vz,
-    const double *__restrict__ m, int N, const uint32_t *__restrict__ perm, const double *__restrict__ P, double G,
-    double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit,
-    float4 *__restrict__ lo,
-    double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
-    float4 *__restrict__ gbox_hi, double *__restrict__ a_osc, double *__restrict__ rc_eq1) {
-    const int k = blockIdx.x * PREP_THREADS + threadIdx.x;
+// Fills packed position k with body i (i >= 0) or with padding body number
+// `pad` (i < 0); returns the screening factors and the FP32 position.
+__device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double *__restrict__ x,
+                                           const double *__restrict__ y, const double *__restrict__ z,
+                                           const double *__restrict__ vx, const double *__restrict__ vy,
+                                           const double *__restrict__ vz, const double *__restrict__ m,
+                                           const double *__restrict__ P, double G, double Mstar, double dt, double n1,
+                                           double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit,
+                                           float4 *__restrict__ lo, double4_32a *__restrict__ p64,
+                                           float2 *__restrict__ scr, double *__restrict__ a_osc,
+                                           double *__restrict__ rc_eq1, float3 *pos, bool *real) {
     float2 s = make_float2(0.f, 0.f);
-    const float INF = __int_as_float(0x7f800000);
-    float3 bl = make_float3(INF, INF, INF), bh = make_float3(-INF, -INF, -INF);
-    if (k < N) {
-        const int i = (int)perm[k];
+    if (i >= 0) {
         const double xi = x[i], yi = y[i], zi = z[i], mi = m[i];
         const double ux = vx[i] + P[0] / Mstar;
         const double uy = vy[i] + P[1] / Mstar;
@@ -135,19 +132,29 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
         lo[k] = make_float4(__double2float_rn(xi - (double)hx), __double2float_rn(yi - (double)hy),
                             __double2float_rn(zi - (double)hz), 0.f);
         p64[k] = make_double4_32a(xi, yi, zi, gm);
-        bl = bh = make_float3(hx, hy, hz);
+        *pos = make_float3(hx, hy, hz);
+        *real = true;
     } else {
-        const float px = GENGA_PAD_POS + 64.0f * (float)(k - N);
+        const float px = GENGA_PAD_POS + 64.0f * (float)pad;
         hi[k] = make_float4(px, GENGA_PAD_POS, GENGA_PAD_POS, 0.f);
         store_tiled(hit, k, px, GENGA_PAD_POS, GENGA_PAD_POS, 0.f);
         lo[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         p64[k] = make_double4_32a((double)px, GENGA_PAD_POS, GENGA_PAD_POS, 0.0);
         a_osc[k] = 0.0;
         rc_eq1[k] = 0.0;
+        *real = false;
     }
     scr[k] = s;
-    // bounding box of the group's real bodies (FP32 hi positions) and the
-    // maxima of its screening factors
+    return s;
+}
+
+// Bounding box of the group's real bodies (FP32 hi positions) and the maxima
+// of its screening factors; one block = one 64-body group.
+__device__ __forceinline__ void group_reduce_store(float2 s, float3 pos, bool real, float4 *__restrict__ gbox_lo,
+                                                   float4 *__restrict__ gbox_hi) {
+    const float INF = __int_as_float(0x7f800000);
+    float3 bl = real ? pos : make_float3(INF, INF, INF);
+    float3 bh = real ? pos : make_float3(-INF, -INF, -INF);
     float hmax = s.x, amax = s.y;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -177,6 +184,71 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
     }
 }
 
+// Position k of the packed arrays holds body perm[k] (the Morton order);
+// k >= N are padding bodies: zero mass, 64 au apart, far from everything.
+__global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
+    const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+    const double *__restrict__ vx, const double *__restrict__ vy, const double *__restrict__ vz,
+    const double *__restrict__ m, int N, const uint32_t *__restrict__ perm, const double *__restrict__ P, double G,
+    double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit,
+    float4 *__restrict__ lo, double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
+    float4 *__restrict__ gbox_hi, double *__restrict__ a_osc, double *__restrict__ rc_eq1) {
+    const int k = blockIdx.x * PREP_THREADS + threadIdx.x;
+    float3 pos = make_float3(0.f, 0.f, 0.f);
+    bool real = false;
+    const float2 s = prep_body(k, k < N ? (int)perm[k] : -1, k - N, x, y, z, vx, vy, vz, m, P, G, Mstar, dt, n1, n2,
+                               rcrit_mode, hi, hit, lo, p64, scr, a_osc, rc_eq1, &pos, &real);
+    group_reduce_store(s, pos, real, gbox_lo, gbox_hi);
+}
+
+// Batched: packed position p belongs to system d = segment of p in poff; its
+// k-th body (k = p - poff[d]) is body perm[off[d] + k] of the caller's arrays
+// (the batched Morton sort keeps each system's bodies together).
+__global__ void __launch_bounds__(PREP_THREADS) prep_batched_kernel(
+    const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+    const double *__restrict__ vx, const double *__restrict__ vy, const double *__restrict__ vz,
+    const double *__restrict__ m, const uint32_t *__restrict__ perm, const double *__restrict__ Pd, double G,
+    double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit,
+    float4 *__restrict__ lo, double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
+    float4 *__restrict__ gbox_hi, double *__restrict__ a_osc, double *__restrict__ rc_eq1,
+    const __grid_constant__ BatchBodies bb) {
+    const int p = blockIdx.x * PREP_THREADS + threadIdx.x;
+    const int d = find_segment(bb.poff, bb.D, p);
+    const int k = p - bb.poff[d], Nd = bb.off[d + 1] - bb.off[d];
+    float3 pos = make_float3(0.f, 0.f, 0.f);
+    bool real = false;
+    const float2 s = prep_body(p, k < Nd ? (int)perm[bb.off[d] + k] : -1, k - Nd, x, y, z, vx, vy, vz, m, Pd + 3 * d, G,
+                               Mstar, dt, n1, n2, rcrit_mode, hi, hit, lo, p64, scr, a_osc, rc_eq1, &pos, &real);
+    group_reduce_store(s, pos, real, gbox_lo, gbox_hi);
+}
+
+// Batched momentum: block d sums system d (strided per thread, fixed tree).
+__global__ void __launch_bounds__(MOM_THREADS) momentum_batched_kernel(
+    const double *__restrict__ vx, const double *__restrict__ vy, const double *__restrict__ vz,
+    const double *__restrict__ m, double *__restrict__ Pd, int32_t *__restrict__ zero_me,
+    const __grid_constant__ BatchBodies bb) {
+    __shared__ double sh[3][MOM_THREADS];
+    const int d = blockIdx.x;
+    double px = 0.0, py = 0.0, pz = 0.0;
+    for (int i = bb.off[d] + threadIdx.x; i < bb.off[d + 1]; i += MOM_THREADS) {
+        const double mi = m[i];
+        px += mi * vx[i];
+        py += mi * vy[i];
+        pz += mi * vz[i];
+    }
+    sh[0][threadIdx.x] = px;
+    sh[1][threadIdx.x] = py;
+    sh[2][threadIdx.x] = pz;
+    __syncthreads();
+    for (int w = MOM_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 3; c++) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) Pd[3 * d + threadIdx.x] = sh[threadIdx.x][0];
+    if (d == 0 && threadIdx.x == 0 && zero_me) *zero_me = 0;
+}
+
 }  // namespace
 
 cudaError_t launch_momentum(const double *vx, const double *vy, const double *vz, const double *m, int N,
@@ -194,6 +266,24 @@ cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ct
         sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->perm, c->mom, p.G, p.Mstar, p.dt, p.n1,
         p.n2, p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->a_osc,
         c->rc_eq1);
+    return cudaGetLastError();
+}
+
+}  // namespace genga
+
+namespace genga {
+
+cudaError_t launch_momentum_batched(const genga_system &all, const BatchBodies &bb, double *Pd, int32_t *zero_me,
+                                    cudaStream_t s) {
+    momentum_batched_kernel<<<bb.D, MOM_THREADS, 0, s>>>(all.vx, all.vy, all.vz, all.m, Pd, zero_me, bb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_batched(const genga_system &all, const BatchBodies &bb, const genga_params &p, genga_ctx *c,
+                                cudaStream_t s) {
+    prep_batched_kernel<<<bb.npad_total / PREP_THREADS, PREP_THREADS, 0, s>>>(
+        all.x, all.y, all.z, all.vx, all.vy, all.vz, all.m, c->perm, c->Pd, p.G, p.Mstar, p.dt, p.n1, p.n2,
+        p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->a_osc, c->rc_eq1, bb);
     return cudaGetLastError();
 }
 
