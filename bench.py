@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variant", type=int, default=-1, help="force an FP32 pass variant (-1: autotune)")
     ap.add_argument("--no-sweep", action="store_true", help="skip timing every FP32 variant")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-disc batched workload")
+    ap.add_argument("--batched-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -183,6 +185,59 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------- batched ----
+BATCH_WORKLOAD = ("batch256: 256 independent discs, N_d = floor(exp U(ln 1000, ln 16000)) planetesimals each "
+                  "(2.5 Earth masses, 0.5-4 au), FP32 kick, dt = 6 d")
+
+
+def run_batched(g, torch, dev, stream, flush, args, rank):
+    """genga_step_batched over 256 discs against genga_step on each disc in turn."""
+    import numpy as np
+    from paper_2309_08217_gb300 import discs
+    ds = discs.batch_of_discs(256, 4 + 1000 * rank)
+    sizes = np.array([d.N for d in ds])
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).tolist()
+    padded = int(sum((n + 1023) // 1024 * 1024 for n in sizes))
+    pairs_step = 2 * int((sizes * (sizes - 1)).sum())
+    p = g.make_params(G=ds[0].G, Mstar=1.0, dt=6.0, precision=g.GENGA_FP32)
+    K, W = max(1, args.batched_steps), 3
+
+    def timed(step_once):
+        for _ in range(W):
+            step_once()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize(dev)
+        for k in range(K):
+            flush.zero_()
+            evs[k][0].record(stream)
+            step_once()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    ctxb = g.Context(padded, dev.index)
+    allsys = g.DeviceSystem.from_arrays([np.concatenate([d.arrays()[c] for d in ds]) for c in range(7)], device=dev)
+    ms_b = timed(lambda: g.genga_step_batched(ctxb, allsys, offsets, p, 1))
+    if g.genga_get_status(ctxb) != g.GENGA_OK:
+        raise RuntimeError("device status after the batched steps")
+    ctxb.close()
+    ctxs = g.Context(int(sizes.max()), dev.index)
+    systems = [g.DeviceSystem.from_disc(d, device=dev) for d in ds]
+
+    def sequential():
+        for sd in systems:
+            g.genga_step(ctxs, sd, p, 1)
+    ms_s = timed(sequential)
+    if g.genga_get_status(ctxs) != g.GENGA_OK:
+        raise RuntimeError("device status after the sequential steps")
+    ctxs.close()
+    vb = pairs_step * K / (ms_b * 1e-3)
+    vs = pairs_step * K / (ms_s * 1e-3)
+    return {"workload": BATCH_WORKLOAD, "discs": len(ds), "bodies": int(sizes.sum()), "pairs_per_step": pairs_step,
+            "steps": K, "value": vb, "unit": UNIT, "ms_per_step": ms_b / K, "sequential_value": vs,
+            "sequential_ms_per_step": ms_s / K, "speedup_vs_sequential": vb / vs}
+
+
 # --------------------------------------------------------------- genga ----
 def run_genga(args):
     import numpy as np
@@ -267,6 +322,7 @@ def run_genga(args):
     ms32, pass32, nl32, clk, s32 = timed_steps(p32, args.steps, args.warmup, clocks=True)
     kernels32 = timed_steps.kernels
     chosen, _ = g.genga_get_kernel_variant(ctx, N)
+    tuner_ms = g.genga_tuning_times(ctx, N)
     ms64, pass64, nl64, _, _ = timed_steps(p64, max(1, args.fp64_steps), 3)
 
     def max_over_ranks(x):
@@ -325,7 +381,12 @@ def run_genga(args):
             "measured_ffma_tflops": f32_meas, "frac_of_measured_ffma": achieved / f32_meas,
             "measured_ffma2_tflops": f32x2_meas,
             "sm_mhz_median": (clk or {}).get("sm_mhz"), "fp32_variant": chosen,
-            "fp32_variant_pass_ms": variants}
+            "fp32_variant_pass_ms": variants, "autotuner_pass_ms": tuner_ms}
+
+    # ---- batched: 256 independent discs in one call vs one call per disc
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(g, torch, dev, stream, flush, args, rank)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -354,6 +415,7 @@ def run_genga(args):
                  "measured_dfma_tflops": f64_meas, "frac_of_measured_dfma": achieved64 / f64_meas,
                  "fp32_over_fp64": value / value64},
         "roofline": roof,
+        "batched": batched,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": kernels32,

@@ -32,6 +32,10 @@ genga_status genga_measure_alu_peaks(int32_t device, double *fp32_tflops, double
  * form the FP32 pass uses); TFLOP/s counting 4 flops per packed FMA. */
 genga_status genga_measure_fma2_peak(int32_t device, double *tflops);
 
+/* The autotuner's measured pass time (ms) of each FP32 variant for systems of
+ * N bodies (0 where not measured); ms is HOST memory [n]. */
+genga_status genga_tuning_times(genga_ctx *ctx, int32_t N, float *ms, int32_t n);
+
 /* Number of CUDA kernels the context has launched so far (HOST memory);
  * autotuning trial launches included. */
 genga_status genga_launch_count(genga_ctx *ctx, int64_t *count);

@@ -87,6 +87,7 @@ def load():
             "genga_measure_fma2_peak": ([I, C.POINTER(C.c_double)], I),
             "genga_launch_count": ([V, C.POINTER(C.c_int64)], I),
             "genga_kick_batched": ([V, S, C.POINTER(C.c_int32), I, P, D, V, V], I),
+            "genga_tuning_times": ([V, I, C.POINTER(C.c_float), I], I),
             "genga_step_batched": ([V, S, C.POINTER(C.c_int32), I, P, I, V], I),
             "genga_get_kernel_variant": ([V, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], I),
         }
@@ -273,6 +274,14 @@ def genga_measure_fma2_peak(device=0):
     t = C.c_double()
     _check(load().genga_measure_fma2_peak(int(device), C.byref(t)), "genga_measure_fma2_peak")
     return t.value
+
+
+def genga_tuning_times(ctx, N):
+    """The autotuner's pass time (ms) of each FP32 variant for N bodies."""
+    n = genga_get_kernel_variant(ctx, N)[1]
+    arr = (C.c_float * n)()
+    _check(load().genga_tuning_times(_ctx(ctx), int(N), arr, n), "genga_tuning_times")
+    return list(arr)
 
 
 def genga_set_kernel_variant(ctx, variant=-1):

@@ -121,6 +121,7 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
             cudaEventElapsedTime(&t, e0, e1);
             if (rep > 0 && t < ms) ms = t;
         }
+        if (v < 8) c->tune_ms[b][v] = ms;
         if (ms < best_ms) {
             best_ms = ms;
             best = v;

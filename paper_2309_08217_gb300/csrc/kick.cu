@@ -320,18 +320,19 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
 #pragma unroll
     for (int k = 0; k < BPT; k++) XI[k] = YI[k] = ZI[k] = 0ull;
     Box wbox = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-    int wbase = 0, chunk = 0;
-    ItemGeo geo = {0, 0, 0, 0, 0, 0, 0, 0};
+    int wbase = 0;
+    bool in = false;  // this warp holds real i-bodies of the current item
     for (unsigned n = 0;; n++) {
         const int slot = n % STAGES;
         if (!mbar_wait_bounded(&full[slot], (n / STAGES) & 1, a.status)) return;
         const StageHdr h = hdr[slot];
         if (h.flags & 4) return;
         if (h.flags & 1) {  // first tile of an item: load this warp's i-bodies
-            int ib;
+            int ib, chunk;
+            ItemGeo geo;
             pol.decode(a, IB, TILE, h.item, &ib, &chunk, &geo);
             wbase = geo.poff + ib * IB + warp * 32 * BPT;
-            const bool in = wbase - geo.poff < geo.npad;  // warps past the padded end hold dummy bodies
+            in = wbase - geo.poff < geo.npad;  // warps past the padded end hold dummy bodies
 #pragma unroll
             for (int k = 0; k < BPT; k++) {
                 const int i = wbase + k * 32 + lane;
@@ -457,6 +458,9 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
 #pragma unroll
                         for (int k = 0; k < BPT; k++) {
                             if (screened & (1u << k)) {
+                                int ib_, ch_;
+                                ItemGeo geo;
+                                pol.decode(a, IB, TILE, h.item, &ib_, &ch_, &geo);
                                 const double3 f = screened_pair(a, wbase + k * 32 + lane, h.tile * TILE + g * 64 + jj,
                                                                 geo.poff, geo.Nd, geo.off);
                                 s_acc[(0 * BPT + k) * NC + tid] += f.x;
@@ -476,7 +480,10 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
             s_acc[(1 * BPT + k) * NC + tid] += (double)ay[k];
             s_acc[(2 * BPT + k) * NC + tid] += (double)az[k];
         }
-        if ((h.flags & 2) && wbase - geo.poff < geo.npad) {  // last tile of the item: its partial row
+        if ((h.flags & 2) && in) {  // last tile of the item: write its partial row
+            int ib, chunk;
+            ItemGeo geo;
+            pol.decode(a, IB, TILE, h.item, &ib, &chunk, &geo);
             const size_t np = (size_t)geo.npad;
             double *out = a.partial + geo.pbase + (size_t)chunk * 3 * np;
 #pragma unroll

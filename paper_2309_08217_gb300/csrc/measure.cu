@@ -182,6 +182,15 @@ genga_status genga_launch_count(genga_ctx *c, int64_t *count) {
     return GENGA_OK;
 }
 
+genga_status genga_tuning_times(genga_ctx *c, int32_t N, float *ms, int32_t n) {
+    if (!c || !ms || n < 0 || N < 0) return GENGA_ERR_INVALID_ARG;
+    int b = 0;
+    for (int v = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD; v > 1; v >>= 1) b++;
+    b = b < 32 ? b : 31;
+    for (int q = 0; q < n; q++) ms[q] = (q < 8 && q < num_fp32_variants()) ? c->tune_ms[b][q] : 0.f;
+    return GENGA_OK;
+}
+
 genga_status genga_set_kernel_variant(genga_ctx *c, int32_t variant) {
     if (!c || variant < -1 || variant >= num_fp32_variants()) return GENGA_ERR_INVALID_ARG;
     c->forced_variant = variant;
