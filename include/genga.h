@@ -86,7 +86,7 @@ typedef struct {
 typedef struct genga_ctx genga_ctx;
 
 /* Create a context on `device` with workspace for systems of up to max_N bodies
- * (about 200 bytes per body plus the encounter buffer).  *ctx is NULL on error. */
+ * (about 250 bytes per body plus the encounter buffer).  *ctx is NULL on error. */
 genga_status genga_create(genga_ctx **ctx, int32_t max_N, int32_t device);
 
 /* Free the context's workspace (synchronises its device first). NULL is a no-op. */

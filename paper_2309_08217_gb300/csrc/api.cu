@@ -59,6 +59,7 @@ PassArgs base_args(genga_ctx *c, const genga_system &sys, const genga_params &p)
     PassArgs a;
     a.hi = c->pk_hi;
     a.hit = c->pk_t;
+    a.hid = c->pk_d;
     a.lo = c->pk_lo;
     a.p64 = c->pk64;
     a.scr = c->scr;
@@ -336,7 +337,7 @@ void genga_destroy(genga_ctx *c) {
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
     profile_free(c);
-    void *bufs[] = {c->pk_hi,       c->pk_t,        c->pk_lo,       c->pk64,        c->scr,      c->gbox_lo,    c->gbox_hi,
+    void *bufs[] = {c->pk_hi,       c->pk_t,        c->pk_d,        c->pk_lo,       c->pk64,        c->scr,      c->gbox_lo,    c->gbox_hi,
                     c->perm,        c->ord_keys[0], c->ord_keys[1], c->ord_vals[0], c->ord_vals[1], c->ord_hist,
                     c->ord_rbits,   c->a_osc,       c->rc_eq1,      c->partial,  c->mom,        c->enc,
                     c->enc_count,   c->status,      c->energy_part, c->work,   c->Pd,         c->Pd_part};
@@ -381,6 +382,7 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     if (e == cudaSuccess) e = alloc(&c->pk_hi, np);
     if (e == cudaSuccess) e = alloc(&c->pk_lo, np);
     if (e == cudaSuccess) e = alloc(&c->pk_t, 4 * (size_t)np);
+    if (e == cudaSuccess) e = alloc(&c->pk_d, 2 * (size_t)np);
     if (e == cudaSuccess) e = alloc(&c->pk64, np);
     if (e == cudaSuccess) e = alloc(&c->scr, np);
     if (e == cudaSuccess) e = alloc(&c->gbox_lo, np / 64);

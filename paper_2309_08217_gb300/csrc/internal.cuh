@@ -48,6 +48,7 @@ struct genga_ctx {
     float4 *pk_hi;             // [npad] {x_hi, y_hi, z_hi, G m (fp32)}
     float4 *pk_lo;             // [npad] {x - x_hi, y - y_hi, z - z_hi, 0}
     float *pk_t;               // [4 npad] tile-blocked {x_hi}, {y_hi}, {z_hi}, {G m} per 256 bodies
+    float4 *pk_d;              // [2 npad] duplicated pairs {x_hi, x_hi, y_hi, y_hi}, {z_hi, z_hi, G m, G m}
     double4_32a *pk64;             // [npad] {x, y, z, G m}
     float2 *scr;               // [npad] screening bound factors {H_i, A_i} (rounded up)
     float4 *gbox_lo;           // [npad / 64] per 64-body group: {min x, min y, min z, max H}
@@ -121,6 +122,7 @@ __device__ __forceinline__ int find_segment(const int32_t *arr, int D, int v) {
 struct PassArgs {               // one long-range pass
     const float4 *hi, *lo;
     const float *hit;           // tile-blocked copy of hi
+    const float4 *hid;          // duplicated-pair copy of hi (two float4 per body)
     const double4_32a *p64;
     const float2 *scr;
     const float4 *gbox_lo, *gbox_hi;

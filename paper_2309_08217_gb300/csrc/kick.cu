@@ -71,6 +71,11 @@ __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
     f32x2 r;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
@@ -243,21 +248,36 @@ struct BatchPolicy {
     }
 };
 
-// The hi slot of stage `slot` holds one tile of the tile-blocked copy.
-__device__ __forceinline__ const float *s_hi_t(const unsigned char *smem_raw, int slot) {
-    return reinterpret_cast<const float *>(smem_raw) + (size_t)slot * 4 * 256;
+// Scalar value of i-body k from its packed register: the j-packed loop keeps
+// {x_k, x_k}, the i-packed loop {x_2q, x_2q+1} in register q.
+template <bool IPACK>
+__device__ __forceinline__ float ival(const f32x2 *V, int k) {
+    float e, o;
+    up2(V[IPACK ? k >> 1 : k], e, o);
+    return (IPACK && (k & 1)) ? o : e;
 }
 
-template <int BPT, int CW, int TILE, int STAGES, int MINB, int UNR, bool PTAIL, class Pol>
+// Two packed-loop flavours (the autotuner picks per size):
+//   j-packed (IPACK = false): a lane pair holds two consecutive j-bodies
+//     against one i-body held twice; j-tiles staged tile-blocked
+//     x[TILE] y[TILE] z[TILE] w[TILE] (one 128-bit load covers four j);
+//   i-packed (IPACK = true): a lane pair holds two i-bodies of the thread
+//     against one j-body held twice; j-tiles staged as the duplicated-pair
+//     copy {x, x, y, y}, {z, z, w, w} (two 128-bit loads per j).  Half the
+//     registers for i positions and sums, so more bodies per thread fit.
+template <int BPT, int CW, int TILE, int STAGES, int MINB, int UNR, bool IPACK, class Pol>
 __global__ void __launch_bounds__((CW + 1) * 32, MINB)
     pass_fp32_kernel(const __grid_constant__ PassArgs a, const __grid_constant__ Pol pol) {
     static_assert(TILE == GENGA_TILE_T, "the staged tile is one block of the tile-blocked copy");
+    static_assert(!IPACK || BPT % 2 == 0, "the i-packed loop pairs the bodies of a thread");
     constexpr int NC = CW * 32;              // consumer threads (CW consumer warps + 1 producer warp)
     constexpr int IB = NC * BPT;             // i-bodies per item (the last i-block may be partial)
     constexpr int NG = TILE / 64;            // 64-body groups per tile
+    constexpr int HF4 = IPACK ? 2 * TILE : TILE;  // float4 per staged hi slot
+    constexpr int NP = IPACK ? BPT / 2 : BPT;     // packed registers per i coordinate
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float4 *s_hi = reinterpret_cast<float4 *>(smem_raw);
-    float4 *s_lo = s_hi + STAGES * TILE;
+    float4 *s_lo = s_hi + STAGES * HF4;
     float4 *s_glo = s_lo + STAGES * TILE;  // [STAGES][NG] group boxes of each staged tile
     float4 *s_ghi = s_glo + STAGES * NG;
     uint64_t *full = reinterpret_cast<uint64_t *>(s_ghi + STAGES * NG);
@@ -266,6 +286,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
     __shared__ double s_acc[3 * BPT * NC];  // [c][k][thread]
     __shared__ float4 s_ilo[BPT * NC];      // lo parts of this thread's i-bodies (current item)
     __shared__ float2 s_iscr[BPT * NC];     // and their screening factors
+    __shared__ unsigned long long s_mask[BPT * NC];  // screened j of the current NEAR group, per i-body
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nitems = pol.total(a, IB);
@@ -281,7 +302,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
 
     if (warp == CW) {  // ------------------------------------------ producer
         if (lane != 0) return;
-        constexpr uint32_t TB = TILE * sizeof(float4);
+        constexpr uint32_t TBH = HF4 * sizeof(float4), TBL = TILE * sizeof(float4);
         unsigned n = 0;
         for (;;) {
             const int q = atomicAdd(a.work, 1);
@@ -305,9 +326,11 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                 hdr[slot] = StageHdr{q, t, (t == ta ? 1 : 0) | (t == tb - 1 ? 2 : 0), 0};
                 fence_proxy_async_smem();
                 constexpr uint32_t GB = NG * sizeof(float4);
-                mbar_arrive_expect_tx(&full[slot], 2 * TB + 2 * GB);
-                bulk_g2s(s_hi + slot * TILE, a.hit + (size_t)t * 4 * TILE, TB, &full[slot]);
-                bulk_g2s(s_lo + slot * TILE, a.lo + (size_t)t * TILE, TB, &full[slot]);
+                mbar_arrive_expect_tx(&full[slot], TBH + TBL + 2 * GB);
+                const void *src_hi = IPACK ? static_cast<const void *>(a.hid + (size_t)t * 2 * TILE)
+                                           : static_cast<const void *>(a.hit + (size_t)t * 4 * TILE);
+                bulk_g2s(s_hi + slot * HF4, src_hi, TBH, &full[slot]);
+                bulk_g2s(s_lo + slot * TILE, a.lo + (size_t)t * TILE, TBL, &full[slot]);
                 bulk_g2s(s_glo + slot * NG, a.gbox_lo + (size_t)t * NG, GB, &full[slot]);
                 bulk_g2s(s_ghi + slot * NG, a.gbox_hi + (size_t)t * NG, GB, &full[slot]);
             }
@@ -315,10 +338,9 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
     }
 
     // ---------------------------------------------------------- consumers
-    // i positions as duplicated pairs {x, x}; the scalar value is either half
-    f32x2 XI[BPT], YI[BPT], ZI[BPT];
+    f32x2 XI[NP], YI[NP], ZI[NP];
 #pragma unroll
-    for (int k = 0; k < BPT; k++) XI[k] = YI[k] = ZI[k] = 0ull;
+    for (int q = 0; q < NP; q++) XI[q] = YI[q] = ZI[q] = 0ull;
     Box wbox = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
     int wbase = 0;
     bool in = false;  // this warp holds real i-bodies of the current item
@@ -333,17 +355,23 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
             pol.decode(a, IB, TILE, h.item, &ib, &chunk, &geo);
             wbase = geo.poff + ib * IB + warp * 32 * BPT;
             in = wbase - geo.poff < geo.npad;  // warps past the padded end hold dummy bodies
+            float4 p[BPT];
 #pragma unroll
             for (int k = 0; k < BPT; k++) {
                 const int i = wbase + k * 32 + lane;
-                const float4 p = in ? a.hi[i] : make_float4(GENGA_PAD_POS, 0.f, 0.f, 0.f);
-                XI[k] = pk2(p.x, p.x);
-                YI[k] = pk2(p.y, p.y);
-                ZI[k] = pk2(p.z, p.z);
+                p[k] = in ? a.hi[i] : make_float4(GENGA_PAD_POS, 0.f, 0.f, 0.f);
                 s_ilo[k * NC + tid] = in ? a.lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
                 s_iscr[k * NC + tid] = in ? a.scr[i] : make_float2(0.f, 0.f);
 #pragma unroll
                 for (int c = 0; c < 3; c++) s_acc[(c * BPT + k) * NC + tid] = 0.0;
+                s_mask[k * NC + tid] = 0ull;
+            }
+#pragma unroll
+            for (int q = 0; q < NP; q++) {
+                const float4 &u = p[IPACK ? 2 * q : q], &v = p[IPACK ? 2 * q + 1 : q];
+                XI[q] = pk2(u.x, v.x);
+                YI[q] = pk2(u.y, v.y);
+                ZI[q] = pk2(u.z, v.z);
             }
             if (in) {
                 wbox = group_box<BPT / 2>(a.gbox_lo, a.gbox_hi, wbase / 64);
@@ -352,128 +380,178 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                 wbox = {make_float4(INF, INF, INF, 0.f), make_float4(-INF, -INF, -INF, 0.f)};
             }
         }
-        // FP32 sums of this tile (FAR groups accumulate packed even/odd-j sums
-        // and fold them in at the end of the group)
+        // FP32 sums of this tile: i-packed, packed pairs TX; j-packed, scalar
+        // ax (FAR groups accumulate packed even/odd-j sums and fold them in at
+        // the end of the group)
+        f32x2 TX[IPACK ? NP : 1], TY[IPACK ? NP : 1], TZ[IPACK ? NP : 1];
         float ax[BPT], ay[BPT], az[BPT];
 #pragma unroll
+        for (int q = 0; q < (IPACK ? NP : 1); q++) TX[q] = TY[q] = TZ[q] = 0ull;
+#pragma unroll
         for (int k = 0; k < BPT; k++) ax[k] = ay[k] = az[k] = 0.f;
-        const float *tt = s_hi_t(smem_raw, slot);  // tile-blocked x[TILE] y[TILE] z[TILE] w[TILE]
+        const float4 *th = s_hi + slot * HF4;
         for (int g = 0; g < NG; g++) {
             const Box gb = {s_glo[slot * NG + g], s_ghi[slot * NG + g]};
-            const float *tx = tt + g * 64, *ty = tx + TILE, *tz = tx + 2 * TILE, *tw = tx + 3 * TILE;
+            const float *tx = reinterpret_cast<const float *>(th) + g * 64, *ty = tx + TILE, *tz = tx + 2 * TILE,
+                        *tw = tx + 3 * TILE;     // j-packed layout
+            const float4 *td = th + g * 128;  // i-packed layout: two float4 per j
             if (far_pair_of_boxes(wbox, gb, true)) {
-                // every pair: K = 1, FP32-rounded positions accurate enough;
-                // two consecutive j per packed register, four j per step
-                f32x2 AX[BPT], AY[BPT], AZ[BPT];  // packed tail: (even j, odd j) sums
-                float bx[BPT], by[BPT], bz[BPT];  // scalar tail: odd-j sums (even j into ax)
-#pragma unroll
-                for (int k = 0; k < BPT; k++) {
-                    AX[k] = AY[k] = AZ[k] = 0ull;
-                    bx[k] = by[k] = bz[k] = 0.f;
-                }
+                // every pair: K = 1, FP32-rounded positions accurate enough
+                if constexpr (IPACK) {
 #pragma unroll(UNR)
-                for (int jj = 0; jj < 64; jj += 4) {
-                    const ulonglong2 X4 = *reinterpret_cast<const ulonglong2 *>(tx + jj);
-                    const ulonglong2 Y4 = *reinterpret_cast<const ulonglong2 *>(ty + jj);
-                    const ulonglong2 Z4 = *reinterpret_cast<const ulonglong2 *>(tz + jj);
-                    const ulonglong2 W4 = *reinterpret_cast<const ulonglong2 *>(tw + jj);
+                    for (int jj = 0; jj < 64; jj++) {
+                        const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(td + 2 * jj);      // {xx}, {yy}
+                        const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(td + 2 * jj + 1);  // {zz}, {ww}
 #pragma unroll
-                    for (int half = 0; half < 2; half++) {
-                        const f32x2 JX = half ? X4.y : X4.x, JY = half ? Y4.y : Y4.x;
-                        const f32x2 JZ = half ? Z4.y : Z4.x, JW = half ? W4.y : W4.x;
-#pragma unroll
-                        for (int k = 0; k < BPT; k++) {
-                            const f32x2 DX = sub2(JX, XI[k]), DY = sub2(JY, YI[k]), DZ = sub2(JZ, ZI[k]);
+                        for (int q = 0; q < NP; q++) {
+                            const f32x2 DX = sub2(A.x, XI[q]), DY = sub2(A.y, YI[q]), DZ = sub2(B.x, ZI[q]);
                             const f32x2 R2 = fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
                             float ra, rb;
                             up2(R2, ra, rb);
-                            const float ria = rsqrt_sfu(ra), rib = rsqrt_sfu(rb);
-                            if (PTAIL) {  // packed m r^-3 and accumulation
-                                const f32x2 RI = pk2(ria, rib);
+                            const f32x2 RI = pk2(rsqrt_sfu(ra), rsqrt_sfu(rb));
+                            const f32x2 S = mul2(mul2(B.y, RI), mul2(RI, RI));
+                            TX[q] = fma2(S, DX, TX[q]);
+                            TY[q] = fma2(S, DY, TY[q]);
+                            TZ[q] = fma2(S, DZ, TZ[q]);
+                        }
+                    }
+                } else {
+                    // two consecutive j per packed register, four j per step
+                    f32x2 AX[BPT], AY[BPT], AZ[BPT];  // (even j, odd j) sums
+#pragma unroll
+                    for (int k = 0; k < BPT; k++) AX[k] = AY[k] = AZ[k] = 0ull;
+#pragma unroll(UNR)
+                    for (int jj = 0; jj < 64; jj += 4) {
+                        const ulonglong2 X4 = *reinterpret_cast<const ulonglong2 *>(tx + jj);
+                        const ulonglong2 Y4 = *reinterpret_cast<const ulonglong2 *>(ty + jj);
+                        const ulonglong2 Z4 = *reinterpret_cast<const ulonglong2 *>(tz + jj);
+                        const ulonglong2 W4 = *reinterpret_cast<const ulonglong2 *>(tw + jj);
+#pragma unroll
+                        for (int half = 0; half < 2; half++) {
+                            const f32x2 JX = half ? X4.y : X4.x, JY = half ? Y4.y : Y4.x;
+                            const f32x2 JZ = half ? Z4.y : Z4.x, JW = half ? W4.y : W4.x;
+#pragma unroll
+                            for (int k = 0; k < BPT; k++) {
+                                const f32x2 DX = sub2(JX, XI[k]), DY = sub2(JY, YI[k]), DZ = sub2(JZ, ZI[k]);
+                                const f32x2 R2 = fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
+                                float ra, rb;
+                                up2(R2, ra, rb);
+                                const f32x2 RI = pk2(rsqrt_sfu(ra), rsqrt_sfu(rb));
                                 const f32x2 S = mul2(mul2(JW, RI), mul2(RI, RI));
                                 AX[k] = fma2(S, DX, AX[k]);
                                 AY[k] = fma2(S, DY, AY[k]);
                                 AZ[k] = fma2(S, DZ, AZ[k]);
-                            } else {  // scalar tail: no repacking of the two SFU results
-                                float wa, wb, dxa, dxb, dya, dyb, dza, dzb;
-                                up2(JW, wa, wb);
-                                up2(DX, dxa, dxb);
-                                up2(DY, dya, dyb);
-                                up2(DZ, dza, dzb);
-                                const float sa = (wa * ria) * (ria * ria), sb = (wb * rib) * (rib * rib);
-                                ax[k] = fmaf(sa, dxa, ax[k]);
-                                ay[k] = fmaf(sa, dya, ay[k]);
-                                az[k] = fmaf(sa, dza, az[k]);
-                                bx[k] = fmaf(sb, dxb, bx[k]);
-                                by[k] = fmaf(sb, dyb, by[k]);
-                                bz[k] = fmaf(sb, dzb, bz[k]);
                             }
                         }
                     }
-                }
-#pragma unroll
-                for (int k = 0; k < BPT; k++) {
-                    float e0, e1;
-                    up2(AX[k], e0, e1);
-                    ax[k] += (e0 + e1) + bx[k];
-                    up2(AY[k], e0, e1);
-                    ay[k] += (e0 + e1) + by[k];
-                    up2(AZ[k], e0, e1);
-                    az[k] += (e0 + e1) + bz[k];
-                }
-            } else {
-                const float4 *tl = s_lo + slot * TILE + g * 64;
-                float xl[BPT], yl[BPT], zl[BPT], thr[BPT];
-#pragma unroll
-                for (int k = 0; k < BPT; k++) {
-                    const float4 l = s_ilo[k * NC + tid];
-                    const float2 sc = s_iscr[k * NC + tid];
-                    xl[k] = l.x; yl[k] = l.y; zl[k] = l.z;
-                    thr[k] = screen_threshold(sc.x, sc.y, gb.lo.w, gb.hi.w);
-                }
-#pragma unroll 2
-                for (int jj = 0; jj < 64; jj++) {
-                    const float jx = tx[jj], jy = ty[jj], jz = tz[jj], jw = tw[jj];
-                    const float4 pl = tl[jj];
-                    unsigned screened = 0u;  // bit k: pair (i_k, j) is under the screening bound
 #pragma unroll
                     for (int k = 0; k < BPT; k++) {
-                        float xi, yi, zi, d0;
-                        up2(XI[k], xi, d0);
-                        up2(YI[k], yi, d0);
-                        up2(ZI[k], zi, d0);
-                        const float dx = (jx - xi) + (pl.x - xl[k]);
-                        const float dy = (jy - yi) + (pl.y - yl[k]);
-                        const float dz = (jz - zi) + (pl.z - zl[k]);
-                        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                        const float ri = rsqrt_sfu(r2);
-                        const bool near = r2 < thr[k];
-                        screened |= (unsigned)near << k;
-                        const float sf = near ? 0.f : (jw * ri) * (ri * ri);
-                        ax[k] = fmaf(sf, dx, ax[k]);
-                        ay[k] = fmaf(sf, dy, ay[k]);
-                        az[k] = fmaf(sf, dz, az[k]);
+                        float e0, e1;
+                        up2(AX[k], e0, e1);
+                        ax[k] += e0 + e1;
+                        up2(AY[k], e0, e1);
+                        ay[k] += e0 + e1;
+                        up2(AZ[k], e0, e1);
+                        az[k] += e0 + e1;
                     }
-                    if (screened) {  // rare: these pairs are evaluated exactly, in FP64
+                }
+            } else {
+                // NEAR group: hi/lo offsets, every pair screened; sums into sx, sy, sz
+                auto near_group = [&](float(&sx)[BPT], float(&sy)[BPT], float(&sz)[BPT]) {
+                    const float4 *tl = s_lo + slot * TILE + g * 64;
+                    float xl[BPT], yl[BPT], zl[BPT], thr[BPT];
+#pragma unroll
+                    for (int k = 0; k < BPT; k++) {
+                        const float4 l = s_ilo[k * NC + tid];
+                        const float2 sc = s_iscr[k * NC + tid];
+                        xl[k] = l.x; yl[k] = l.y; zl[k] = l.z;
+                        thr[k] = screen_threshold(sc.x, sc.y, gb.lo.w, gb.hi.w);
+                    }
+#pragma unroll 2
+                    for (int jj = 0; jj < 64; jj++) {
+                        float jx, jy, jz, jw;
+                        if constexpr (IPACK) {
+                            const float4 A = td[2 * jj], B = td[2 * jj + 1];
+                            jx = A.x; jy = A.z; jz = B.x; jw = B.z;
+                        } else {
+                            jx = tx[jj]; jy = ty[jj]; jz = tz[jj]; jw = tw[jj];
+                        }
+                        const float4 pl = tl[jj];
+                        unsigned screened = 0u;  // bit k: pair (i_k, j) is under the screening bound
 #pragma unroll
                         for (int k = 0; k < BPT; k++) {
-                            if (screened & (1u << k)) {
-                                int ib_, ch_;
-                                ItemGeo geo;
-                                pol.decode(a, IB, TILE, h.item, &ib_, &ch_, &geo);
-                                const double3 f = screened_pair(a, wbase + k * 32 + lane, h.tile * TILE + g * 64 + jj,
-                                                                geo.poff, geo.Nd, geo.off);
-                                s_acc[(0 * BPT + k) * NC + tid] += f.x;
-                                s_acc[(1 * BPT + k) * NC + tid] += f.y;
-                                s_acc[(2 * BPT + k) * NC + tid] += f.z;
-                            }
+                            const float dx = (jx - ival<IPACK>(XI, k)) + (pl.x - xl[k]);
+                            const float dy = (jy - ival<IPACK>(YI, k)) + (pl.y - yl[k]);
+                            const float dz = (jz - ival<IPACK>(ZI, k)) + (pl.z - zl[k]);
+                            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                            const float ri = rsqrt_sfu(r2);
+                            const bool near = r2 < thr[k];
+                            screened |= (unsigned)near << k;
+                            const float sf = near ? 0.f : (jw * ri) * (ri * ri);
+                            sx[k] = fmaf(sf, dx, sx[k]);
+                            sy[k] = fmaf(sf, dy, sy[k]);
+                            sz[k] = fmaf(sf, dz, sz[k]);
+                        }
+                        if (screened) {  // rare: noted here, evaluated after the loop
+#pragma unroll
+                            for (int k = 0; k < BPT; k++)
+                                if (screened & (1u << k)) s_mask[k * NC + tid] |= 1ull << jj;
                         }
                     }
+                    // the screened pairs of this group, exactly in FP64 (the
+                    // pair of a body with itself contributes nothing)
+#pragma unroll 1
+                    for (int k = 0; k < BPT; k++) {
+                        unsigned long long msk = s_mask[k * NC + tid];
+                        if (!msk) continue;
+                        s_mask[k * NC + tid] = 0ull;
+                        const int i = wbase + k * 32 + lane;
+                        int ib_, ch_;
+                        ItemGeo geo;
+                        pol.decode(a, IB, TILE, h.item, &ib_, &ch_, &geo);
+                        double fx = 0.0, fy = 0.0, fz = 0.0;
+                        do {
+                            const int jj = __ffsll((long long)msk) - 1;
+                            msk &= msk - 1;
+                            const int j = h.tile * TILE + g * 64 + jj;
+                            if (j != i) {
+                                const double3 f = screened_pair(a, i, j, geo.poff, geo.Nd, geo.off);
+                                fx += f.x;
+                                fy += f.y;
+                                fz += f.z;
+                            }
+                        } while (msk);
+                        s_acc[(0 * BPT + k) * NC + tid] += fx;
+                        s_acc[(1 * BPT + k) * NC + tid] += fy;
+                        s_acc[(2 * BPT + k) * NC + tid] += fz;
+                    }
+                };
+                if constexpr (IPACK) {
+                    float nx[BPT], ny[BPT], nz[BPT];
+#pragma unroll
+                    for (int k = 0; k < BPT; k++) nx[k] = ny[k] = nz[k] = 0.f;
+                    near_group(nx, ny, nz);
+#pragma unroll
+                    for (int q = 0; q < NP; q++) {
+                        TX[q] = add2(TX[q], pk2(nx[2 * q], nx[2 * q + 1]));
+                        TY[q] = add2(TY[q], pk2(ny[2 * q], ny[2 * q + 1]));
+                        TZ[q] = add2(TZ[q], pk2(nz[2 * q], nz[2 * q + 1]));
+                    }
+                } else {
+                    near_group(ax, ay, az);
                 }
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);  // this warp is done reading the slot
+        if constexpr (IPACK) {
+#pragma unroll
+            for (int k = 0; k < BPT; k++) {
+                ax[k] = ival<true>(TX, k);
+                ay[k] = ival<true>(TY, k);
+                az[k] = ival<true>(TZ, k);
+            }
+        }
 #pragma unroll
         for (int k = 0; k < BPT; k++) {  // fold the tile's FP32 sums into the FP64 sums
             s_acc[(0 * BPT + k) * NC + tid] += (double)ax[k];
@@ -795,27 +873,33 @@ __global__ void copy_pairs_kernel(const int2 *__restrict__ enc, const int32_t *_
 // ------------------------------------------------------------ variants ----
 constexpr int F32_TILE = 256, F32_STAGES = 4;
 
-// FP32 pass variants (bodies per thread, CTAs per SM, FAR-loop unroll); the
-// autotuner in api.cu times them per N bucket and keeps the fastest.
+// FP32 pass variants (packing, bodies per thread, consumer warps, CTAs per
+// SM, FAR-loop unroll); the autotuner in api.cu times them per N bucket and
+// keeps the fastest.
 struct F32Variant {
+    bool ipack;
     int bpt, cw, minb;  // bodies per thread, consumer warps, resident CTAs per SM
     void (*fn)(const PassArgs, const SingleItems);
     void (*fnb)(const PassArgs, const BatchPolicy);
 };
-#define GENGA_F32V(BPT, CW, MINB, UNR)                                                                   \
-    {BPT, CW, MINB, pass_fp32_kernel<BPT, CW, F32_TILE, F32_STAGES, MINB, UNR, true, SingleItems>,       \
-     pass_fp32_kernel<BPT, CW, F32_TILE, F32_STAGES, MINB, UNR, true, BatchPolicy>}
+#define GENGA_F32V(IP, BPT, CW, MINB, UNR)                                                          \
+    {IP, BPT, CW, MINB, pass_fp32_kernel<BPT, CW, F32_TILE, F32_STAGES, MINB, UNR, IP, SingleItems>, \
+     pass_fp32_kernel<BPT, CW, F32_TILE, F32_STAGES, MINB, UNR, IP, BatchPolicy>}
 const F32Variant kF32Variants[] = {
-    GENGA_F32V(2, 8, 2, 8), GENGA_F32V(2, 8, 2, 4), GENGA_F32V(2, 8, 2, 2), GENGA_F32V(4, 8, 1, 2),
-    GENGA_F32V(2, 7, 2, 4),
+    GENGA_F32V(false, 2, 8, 2, 8), GENGA_F32V(false, 2, 8, 2, 4), GENGA_F32V(true, 2, 8, 2, 4),
+    GENGA_F32V(true, 2, 8, 2, 8),  GENGA_F32V(true, 2, 10, 2, 4), GENGA_F32V(true, 2, 11, 2, 4),
+    GENGA_F32V(true, 4, 8, 2, 2),  GENGA_F32V(true, 2, 8, 2, 2),
 };
 #undef GENGA_F32V
 constexpr int kNumF32Variants = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
+static_assert(kNumF32Variants <= 8, "the context records tuning times of at most 8 variants");
 constexpr int F64_BPT = 2, F64_TILE = 128, F64_STAGES = 3;
 
-size_t smem_fp32() {
-    return (size_t)F32_STAGES * F32_TILE * 2 * sizeof(float4) + (size_t)F32_STAGES * (F32_TILE / 64) * 2 * sizeof(float4) +
-           2 * F32_STAGES * sizeof(uint64_t) + F32_STAGES * sizeof(StageHdr);
+size_t smem_fp32(bool ipack) {
+    const size_t hf4 = ipack ? 2 * F32_TILE : F32_TILE;
+    return (size_t)F32_STAGES * (hf4 + F32_TILE) * sizeof(float4) +
+           (size_t)F32_STAGES * (F32_TILE / 64) * 2 * sizeof(float4) + 2 * F32_STAGES * sizeof(uint64_t) +
+           F32_STAGES * sizeof(StageHdr);
 }
 size_t smem_fp64() { return (size_t)F64_STAGES * F64_TILE * sizeof(double4_32a) + F64_STAGES * sizeof(uint64_t); }
 
@@ -860,10 +944,10 @@ void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_c
 // (the FP32 pass also holds its FP64 accumulators in static shared memory).
 cudaError_t init_pass_kernels() {
     for (int q = 0; q < kNumF32Variants; q++) {
-        cudaError_t e = cudaFuncSetAttribute(kF32Variants[q].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_fp32());
+        const int sm = (int)smem_fp32(kF32Variants[q].ipack);
+        cudaError_t e = cudaFuncSetAttribute(kF32Variants[q].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(kF32Variants[q].fnb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fp32());
+        e = cudaFuncSetAttribute(kF32Variants[q].fnb, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e != cudaSuccess) return e;
     }
     return cudaFuncSetAttribute(pass_fp64_kernel<F64_BPT, F64_TILE, F64_STAGES>,
@@ -877,7 +961,7 @@ cudaError_t launch_pass(const PassArgs &a0, int precision, int variant, int grid
         cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s);
         if (e != cudaSuccess) return e;
         const F32Variant &v = kF32Variants[variant];
-        v.fn<<<grid, (v.cw + 1) * 32, smem_fp32(), s>>>(a, SingleItems{});
+        v.fn<<<grid, (v.cw + 1) * 32, smem_fp32(v.ipack), s>>>(a, SingleItems{});
     } else {
         a.ntiles = a.npad / F64_TILE;
         auto k = pass_fp64_kernel<F64_BPT, F64_TILE, F64_STAGES>;
@@ -900,7 +984,7 @@ cudaError_t launch_pass_batched(const PassArgs &a0, const BatchBodies &bb, const
     BatchPolicy pol;
     pol.bb = bb;
     pol.bi = bi;
-    v.fnb<<<grid, (v.cw + 1) * 32, smem_fp32(), s>>>(a, pol);
+    v.fnb<<<grid, (v.cw + 1) * 32, smem_fp32(v.ipack), s>>>(a, pol);
     return cudaGetLastError();
 }
 

@@ -90,6 +90,13 @@ __device__ __forceinline__ void store_tiled(float *hit, int k, float x, float y,
     t[3 * GENGA_TILE_T] = w;
 }
 
+// Duplicated-pair copy: body k as {x, x, y, y}, {z, z, w, w}, so a 64-bit
+// lane pair broadcasts one j-body to two i-bodies (the i-packed FP32 loop).
+__device__ __forceinline__ void store_dup(float4 *hid, int k, float x, float y, float z, float w) {
+    hid[2 * (size_t)k] = make_float4(x, x, y, y);
+    hid[2 * (size_t)k + 1] = make_float4(z, z, w, w);
+}
+
 // Fills packed position k with body i (i >= 0) or with padding body number
 // `pad` (i < 0); returns the screening factors and the FP32 position.
 __device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double *__restrict__ x,
@@ -97,7 +104,7 @@ __device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double 
                                            const double *__restrict__ vx, const double *__restrict__ vy,
                                            const double *__restrict__ vz, const double *__restrict__ m,
                                            const double *__restrict__ P, double G, double Mstar, double dt, double n1,
-                                           double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit,
+                                           double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
                                            float4 *__restrict__ lo, double4_32a *__restrict__ p64,
                                            float2 *__restrict__ scr, double *__restrict__ a_osc,
                                            double *__restrict__ rc_eq1, float3 *pos, bool *real) {
@@ -129,6 +136,7 @@ __device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double 
         const double gm = G * mi;
         hi[k] = make_float4(hx, hy, hz, __double2float_rn(gm));
         store_tiled(hit, k, hx, hy, hz, __double2float_rn(gm));
+        store_dup(hid, k, hx, hy, hz, __double2float_rn(gm));
         lo[k] = make_float4(__double2float_rn(xi - (double)hx), __double2float_rn(yi - (double)hy),
                             __double2float_rn(zi - (double)hz), 0.f);
         p64[k] = make_double4_32a(xi, yi, zi, gm);
@@ -138,6 +146,7 @@ __device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double 
         const float px = GENGA_PAD_POS + 64.0f * (float)pad;
         hi[k] = make_float4(px, GENGA_PAD_POS, GENGA_PAD_POS, 0.f);
         store_tiled(hit, k, px, GENGA_PAD_POS, GENGA_PAD_POS, 0.f);
+        store_dup(hid, k, px, GENGA_PAD_POS, GENGA_PAD_POS, 0.f);
         lo[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         p64[k] = make_double4_32a((double)px, GENGA_PAD_POS, GENGA_PAD_POS, 0.0);
         a_osc[k] = 0.0;
@@ -190,14 +199,14 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
     const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
     const double *__restrict__ vx, const double *__restrict__ vy, const double *__restrict__ vz,
     const double *__restrict__ m, int N, const uint32_t *__restrict__ perm, const double *__restrict__ P, double G,
-    double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit,
+    double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
     float4 *__restrict__ lo, double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
     float4 *__restrict__ gbox_hi, double *__restrict__ a_osc, double *__restrict__ rc_eq1) {
     const int k = blockIdx.x * PREP_THREADS + threadIdx.x;
     float3 pos = make_float3(0.f, 0.f, 0.f);
     bool real = false;
     const float2 s = prep_body(k, k < N ? (int)perm[k] : -1, k - N, x, y, z, vx, vy, vz, m, P, G, Mstar, dt, n1, n2,
-                               rcrit_mode, hi, hit, lo, p64, scr, a_osc, rc_eq1, &pos, &real);
+                               rcrit_mode, hi, hit, hid, lo, p64, scr, a_osc, rc_eq1, &pos, &real);
     group_reduce_store(s, pos, real, gbox_lo, gbox_hi);
 }
 
@@ -208,7 +217,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_batched_kernel(
     const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
     const double *__restrict__ vx, const double *__restrict__ vy, const double *__restrict__ vz,
     const double *__restrict__ m, const uint32_t *__restrict__ perm, const double *__restrict__ Pd, double G,
-    double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit,
+    double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
     float4 *__restrict__ lo, double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
     float4 *__restrict__ gbox_hi, double *__restrict__ a_osc, double *__restrict__ rc_eq1,
     const __grid_constant__ BatchBodies bb) {
@@ -218,7 +227,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_batched_kernel(
     float3 pos = make_float3(0.f, 0.f, 0.f);
     bool real = false;
     const float2 s = prep_body(p, k < Nd ? (int)perm[bb.off[d] + k] : -1, k - Nd, x, y, z, vx, vy, vz, m, Pd + 3 * d, G,
-                               Mstar, dt, n1, n2, rcrit_mode, hi, hit, lo, p64, scr, a_osc, rc_eq1, &pos, &real);
+                               Mstar, dt, n1, n2, rcrit_mode, hi, hit, hid, lo, p64, scr, a_osc, rc_eq1, &pos, &real);
     group_reduce_store(s, pos, real, gbox_lo, gbox_hi);
 }
 
@@ -264,7 +273,7 @@ cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ct
     const int npad = (sys.N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
     prep_kernel<<<npad / PREP_THREADS, PREP_THREADS, 0, s>>>(
         sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->perm, c->mom, p.G, p.Mstar, p.dt, p.n1,
-        p.n2, p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->a_osc,
+        p.n2, p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_d, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->a_osc,
         c->rc_eq1);
     return cudaGetLastError();
 }
@@ -283,7 +292,7 @@ cudaError_t launch_prep_batched(const genga_system &all, const BatchBodies &bb, 
                                 cudaStream_t s) {
     prep_batched_kernel<<<bb.npad_total / PREP_THREADS, PREP_THREADS, 0, s>>>(
         all.x, all.y, all.z, all.vx, all.vy, all.vz, all.m, c->perm, c->Pd, p.G, p.Mstar, p.dt, p.n1, p.n2,
-        p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->a_osc, c->rc_eq1, bb);
+        p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_d, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->a_osc, c->rc_eq1, bb);
     return cudaGetLastError();
 }
 
