@@ -122,7 +122,7 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
             cudaEventElapsedTime(&t, e0, e1);
             if (rep > 0 && t < ms) ms = t;
         }
-        if (v < 8) c->tune_ms[b][v] = ms;
+        if (v < GENGA_MAX_VARIANTS) c->tune_ms[b][v] = ms;
         if (ms < best_ms) {
             best_ms = ms;
             best = v;
@@ -217,7 +217,7 @@ BatchBodies batch_bodies(const int32_t *offsets, int D) {
 }
 
 // Work items of the FP32 pass over a batch: system d gets a share of about
-// 12 items per resident CTA proportional to npad_d^2 (its pair count), cut
+// 24 items per resident CTA proportional to npad_d^2 (its pair count), cut
 // into j-chunks per i-block; systems are handed out largest item first.
 // False if the partial sums would not fit.
 bool plan_batch(const genga_ctx *c, const BatchBodies &bb, int variant, BatchItems *bi, int *grid) {
@@ -228,7 +228,7 @@ bool plan_batch(const genga_ctx *c, const BatchBodies &bb, int variant, BatchIte
         const double np = bb.poff[d + 1] - bb.poff[d];
         total += np * np;
     }
-    for (int target = 12 * minb * c->sm_count; target >= 1; target /= 2) {
+    for (int target = 24 * minb * c->sm_count; target >= 1; target /= 2) {
         long long pbase = 0;
         for (int d = 0; d < bb.D; d++) {
             const int np = bb.poff[d + 1] - bb.poff[d];
@@ -371,8 +371,9 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     c->sm_count = prop.multiProcessorCount;
     const int np = npad_of(max_N > 0 ? max_N : 1);
     c->npad_max = np;
-    // partial sums: split * 3 * npad doubles; the plans stay near 8 items per
-    // resident CTA, i.e. split * npad ~ 16 * SMs * 1024 (plan_pass clamps)
+    // partial sums: split * 3 * npad doubles; the plans stay near 24 items of
+    // at most 512 bodies per resident CTA, i.e. split * npad <~ 24 * SMs * 1024
+    // (plan_pass clamps)
     c->partial_cap = 3 * ((size_t)np * 4 + (size_t)32 * c->sm_count * 1024 + 4096);
     long long ecap = 4096;
     while (ecap < 16LL * max_N) ecap <<= 1;

@@ -39,6 +39,8 @@ struct Profile {                // CUDA event pairs around pass launches
 };
 }  // namespace genga
 
+#define GENGA_MAX_VARIANTS 16  // FP32 pass variants the context records tuning times for
+
 struct genga_ctx {
     int device;
     int sm_count;
@@ -72,7 +74,7 @@ struct genga_ctx {
     genga::Profile *prof;      // measurement hooks (genga_measure.h), NULL when unused
     int32_t *work;             // [1] work-item counter of the persistent pass
     int8_t f32_variant[32];    // autotuned FP32 pass variant per log2(npad) bucket, -1 = not tuned
-    float tune_ms[32][8];      // the autotuner's time of each variant per bucket
+    float tune_ms[32][GENGA_MAX_VARIANTS];  // the autotuner's time of each variant per bucket
     int32_t forced_variant;    // >= 0: use this FP32 variant (genga_set_kernel_variant)
     int32_t steps_since_order; // genga_step: drifts since the spatial order was built
     int32_t ordered_N;         // N of the system the spatial order was built for (-1: none, -2: a batch)

@@ -719,80 +719,76 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
 }
 
 // ------------------------------------------------------------ combine ----
-// acc of body perm[k] = sum over slices in slice order (Neumaier-compensated
-// for the FP64 pass; plain FP64 for the FP32 pass, whose partials carry FP32
-// rounding far above FP64's); optional acc output and v += acc * tau;
-// non-finite accelerations raise NONFINITE.
+// One thread per (body, component): the body's partial rows summed in row
+// order (Neumaier-compensated for the FP64 pass; plain FP64 for the FP32
+// pass, whose partials carry FP32 rounding far above FP64's).  The rows are
+// fetched COMBINE_BATCH at a time before any of them is added, so a thread
+// waits for a few memory round trips, not one per row.  Then the optional
+// acc output and v_c += acc_c * tau for the body's caller index; non-finite
+// accelerations raise NONFINITE.
+constexpr int COMBINE_BATCH = 16;
+
+template <bool COMP>
+__device__ __forceinline__ double ordered_row_sum(const double *__restrict__ p, size_t stride, int nrows) {
+    Comp s{0.0, 0.0};
+    double t = 0.0;
+    for (int q0 = 0; q0 < nrows; q0 += COMBINE_BATCH) {
+        double v[COMBINE_BATCH];
+#pragma unroll
+        for (int u = 0; u < COMBINE_BATCH; u++) v[u] = (q0 + u < nrows) ? p[(size_t)(q0 + u) * stride] : 0.0;
+#pragma unroll
+        for (int u = 0; u < COMBINE_BATCH; u++) {
+            if (q0 + u < nrows) {
+                if (COMP)
+                    s.add(v[u]);
+                else
+                    t += v[u];
+            }
+        }
+    }
+    return COMP ? s.s + s.c : t;
+}
+
+__device__ __forceinline__ void apply_component(double t, int c, int i, size_t NT, double tau, double *acc,
+                                                double *vx, double *vy, double *vz, uint32_t *status) {
+    if (!isfinite(t)) atomicOr(status, GENGA_BIT(GENGA_ERR_NONFINITE));
+    if (acc) acc[c * NT + i] = t;
+    if (tau != 0.0) {
+        double *v = c == 0 ? vx : (c == 1 ? vy : vz);
+        v[i] += t * tau;
+    }
+}
+
+// grid (ceil(N / 256), 3): blockIdx.y is the component
 __global__ void combine_kernel(const double *__restrict__ partial, int split, int N, int npad, int compensated,
                                const uint32_t *__restrict__ perm, double tau, double *__restrict__ acc,
                                double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
                                uint32_t *__restrict__ status) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
     if (k >= N) return;
-    const int i = (int)perm[k];
-    double a3[3];
-    bool finite = true;
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        if (compensated) {
-            Comp s{0.0, 0.0};
-            for (int q = 0; q < split; q++) s.add(partial[((size_t)q * 3 + c) * npad + k]);
-            a3[c] = s.s + s.c;
-        } else {
-            double t = 0.0;
-            for (int q = 0; q < split; q++) t += partial[((size_t)q * 3 + c) * npad + k];
-            a3[c] = t;
-        }
-        finite = finite && isfinite(a3[c]);
-    }
-    if (!finite) atomicOr(status, GENGA_BIT(GENGA_ERR_NONFINITE));
-    if (acc) {
-        acc[i] = a3[0];
-        acc[(size_t)N + i] = a3[1];
-        acc[2 * (size_t)N + i] = a3[2];
-    }
-    if (tau != 0.0) {
-        vx[i] += a3[0] * tau;
-        vy[i] += a3[1] * tau;
-        vz[i] += a3[2] * tau;
-    }
+    const double *p = partial + (size_t)c * npad + k;
+    const size_t stride = 3 * (size_t)npad;
+    const double t = compensated ? ordered_row_sum<true>(p, stride, split) : ordered_row_sum<false>(p, stride, split);
+    apply_component(t, c, (int)perm[k], (size_t)N, tau, acc, vx, vy, vz, status);
 }
 
 // Batched: packed position p of system d; rows of d start at pbase[d], one
-// per j-chunk, each npad_d long; plain FP64 sums in row order.
+// per j-chunk, each npad_d long; plain FP64 sums in row order.  grid
+// (ceil(npad_total / 256), 3).
 __global__ void combine_batched_kernel(const double *__restrict__ partial, const uint32_t *__restrict__ perm,
                                        double tau, double *__restrict__ acc, double *__restrict__ vx,
                                        double *__restrict__ vy, double *__restrict__ vz, uint32_t *__restrict__ status,
                                        const __grid_constant__ BatchBodies bb, const __grid_constant__ BatchItems bi) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
     if (p >= bb.npad_total) return;
     const int d = find_segment(bb.poff, bb.D, p);
     const int k = p - bb.poff[d];
     if (k >= bb.off[d + 1] - bb.off[d]) return;
-    const int i = (int)perm[bb.off[d] + k];
     const size_t np = (size_t)(bb.poff[d + 1] - bb.poff[d]);
-    const double *rows = partial + bi.pbase[d];
-    double a3[3];
-    bool finite = true;
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        double t = 0.0;
-        for (int q = 0; q < bi.nchunks[d]; q++) t += rows[((size_t)q * 3 + c) * np + k];
-        a3[c] = t;
-        finite = finite && isfinite(t);
-    }
-    if (!finite) atomicOr(status, GENGA_BIT(GENGA_ERR_NONFINITE));
-    const size_t NT = (size_t)bb.N_total;
-    if (acc) {
-        acc[i] = a3[0];
-        acc[NT + i] = a3[1];
-        acc[2 * NT + i] = a3[2];
-    }
-    if (tau != 0.0) {
-        vx[i] += a3[0] * tau;
-        vy[i] += a3[1] * tau;
-        vz[i] += a3[2] * tau;
-    }
+    const double t = ordered_row_sum<false>(partial + bi.pbase[d] + (size_t)c * np + k, 3 * np, bi.nchunks[d]);
+    apply_component(t, c, (int)perm[bb.off[d] + k], (size_t)bb.N_total, tau, acc, vx, vy, vz, status);
 }
 
 // ------------------------------------------------------ encounter list ----
@@ -871,42 +867,42 @@ __global__ void copy_pairs_kernel(const int2 *__restrict__ enc, const int32_t *_
 }
 
 // ------------------------------------------------------------ variants ----
-constexpr int F32_TILE = 256, F32_STAGES = 4;
+constexpr int F32_TILE = 256;
 
 // FP32 pass variants (packing, bodies per thread, consumer warps, CTAs per
-// SM, FAR-loop unroll); the autotuner in api.cu times them per N bucket and
-// keeps the fastest.
+// SM, FAR-loop unroll, ring stages); the autotuner in api.cu times them per N
+// bucket and keeps the fastest.  The first entry is the default where no
+// tuning is possible (stream capture, batched passes).
 struct F32Variant {
     bool ipack;
-    int bpt, cw, minb;  // bodies per thread, consumer warps, resident CTAs per SM
+    int bpt, cw, minb, stages;  // bodies per thread, consumer warps, resident CTAs per SM, ring depth
     void (*fn)(const PassArgs, const SingleItems);
     void (*fnb)(const PassArgs, const BatchPolicy);
 };
-#define GENGA_F32V(IP, BPT, CW, MINB, UNR)                                                          \
-    {IP, BPT, CW, MINB, pass_fp32_kernel<BPT, CW, F32_TILE, F32_STAGES, MINB, UNR, IP, SingleItems>, \
-     pass_fp32_kernel<BPT, CW, F32_TILE, F32_STAGES, MINB, UNR, IP, BatchPolicy>}
+#define GENGA_F32V(IP, BPT, CW, MINB, UNR, ST)                                                    \
+    {IP, BPT, CW, MINB, ST, pass_fp32_kernel<BPT, CW, F32_TILE, ST, MINB, UNR, IP, SingleItems>, \
+     pass_fp32_kernel<BPT, CW, F32_TILE, ST, MINB, UNR, IP, BatchPolicy>}
 const F32Variant kF32Variants[] = {
-    GENGA_F32V(false, 2, 8, 2, 8), GENGA_F32V(false, 2, 8, 2, 4), GENGA_F32V(true, 2, 8, 2, 4),
-    GENGA_F32V(true, 2, 8, 2, 8),  GENGA_F32V(true, 2, 10, 2, 4), GENGA_F32V(true, 2, 11, 2, 4),
-    GENGA_F32V(true, 4, 8, 2, 2),  GENGA_F32V(true, 2, 8, 2, 2),
+    GENGA_F32V(true, 2, 8, 2, 4, 4), GENGA_F32V(true, 2, 4, 4, 8, 3),  GENGA_F32V(true, 2, 4, 4, 4, 3),
+    GENGA_F32V(true, 2, 8, 2, 4, 3), GENGA_F32V(true, 2, 8, 2, 8, 4),  GENGA_F32V(false, 2, 8, 2, 8, 4),
+    GENGA_F32V(true, 2, 16, 1, 8, 4), GENGA_F32V(true, 4, 8, 2, 2, 4),
 };
 #undef GENGA_F32V
 constexpr int kNumF32Variants = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
-static_assert(kNumF32Variants <= 8, "the context records tuning times of at most 8 variants");
+static_assert(kNumF32Variants <= GENGA_MAX_VARIANTS, "the context records tuning times of GENGA_MAX_VARIANTS variants");
 constexpr int F64_BPT = 2, F64_TILE = 128, F64_STAGES = 3;
 
-size_t smem_fp32(bool ipack) {
+size_t smem_fp32(bool ipack, int stages) {
     const size_t hf4 = ipack ? 2 * F32_TILE : F32_TILE;
-    return (size_t)F32_STAGES * (hf4 + F32_TILE) * sizeof(float4) +
-           (size_t)F32_STAGES * (F32_TILE / 64) * 2 * sizeof(float4) + 2 * F32_STAGES * sizeof(uint64_t) +
-           F32_STAGES * sizeof(StageHdr);
+    return (size_t)stages * (hf4 + F32_TILE) * sizeof(float4) + (size_t)stages * (F32_TILE / 64) * 2 * sizeof(float4) +
+           2 * stages * sizeof(uint64_t) + stages * sizeof(StageHdr);
 }
 size_t smem_fp64() { return (size_t)F64_STAGES * F64_TILE * sizeof(double4_32a) + F64_STAGES * sizeof(uint64_t); }
 
 }  // namespace
 
-// Work decomposition of one pass.  FP32 (persistent): about eight work items
-// per resident CTA; split is the number of j-chunks per i-block and
+// Work decomposition of one pass.  FP32 (persistent): about 24 work items
+// per resident CTA (finer items shorten the tail where CTAs run out of work); split is the number of j-chunks per i-block and
 // chunk_tiles their length; grid = resident CTAs.  FP64: `split` contiguous
 // j-slices per i-block, one CTA each, sized to one wave of two CTAs per SM.
 // In both cases split * 3 * npad doubles of partial sums fit in partial_cap.
@@ -924,7 +920,7 @@ void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_c
     const int cap = (int)(partial_cap / (3 * (size_t)npad));
     int sp;
     if (f32) {
-        const int want_items = 12 * v.minb * sm_count;
+        const int want_items = 24 * v.minb * sm_count;
         sp = (want_items + iblocks - 1) / iblocks;
     } else {
         sp = 2 * sm_count / iblocks;
@@ -944,7 +940,7 @@ void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_c
 // (the FP32 pass also holds its FP64 accumulators in static shared memory).
 cudaError_t init_pass_kernels() {
     for (int q = 0; q < kNumF32Variants; q++) {
-        const int sm = (int)smem_fp32(kF32Variants[q].ipack);
+        const int sm = (int)smem_fp32(kF32Variants[q].ipack, kF32Variants[q].stages);
         cudaError_t e = cudaFuncSetAttribute(kF32Variants[q].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(kF32Variants[q].fnb, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -961,7 +957,7 @@ cudaError_t launch_pass(const PassArgs &a0, int precision, int variant, int grid
         cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s);
         if (e != cudaSuccess) return e;
         const F32Variant &v = kF32Variants[variant];
-        v.fn<<<grid, (v.cw + 1) * 32, smem_fp32(v.ipack), s>>>(a, SingleItems{});
+        v.fn<<<grid, (v.cw + 1) * 32, smem_fp32(v.ipack, v.stages), s>>>(a, SingleItems{});
     } else {
         a.ntiles = a.npad / F64_TILE;
         auto k = pass_fp64_kernel<F64_BPT, F64_TILE, F64_STAGES>;
@@ -984,7 +980,7 @@ cudaError_t launch_pass_batched(const PassArgs &a0, const BatchBodies &bb, const
     BatchPolicy pol;
     pol.bb = bb;
     pol.bi = bi;
-    v.fnb<<<grid, (v.cw + 1) * 32, smem_fp32(v.ipack), s>>>(a, pol);
+    v.fnb<<<grid, (v.cw + 1) * 32, smem_fp32(v.ipack, v.stages), s>>>(a, pol);
     return cudaGetLastError();
 }
 
@@ -992,7 +988,7 @@ cudaError_t launch_combine_batched(const BatchBodies &bb, const BatchItems &bi, 
                                    const uint32_t *perm, double tau, double *acc, double *vx, double *vy, double *vz,
                                    uint32_t *status, cudaStream_t s) {
     if (bb.N_total <= 0) return cudaSuccess;
-    combine_batched_kernel<<<(bb.npad_total + 255) / 256, 256, 0, s>>>(partial, perm, tau, acc, vx, vy, vz, status,
+    combine_batched_kernel<<<dim3((bb.npad_total + 255) / 256, 3), 256, 0, s>>>(partial, perm, tau, acc, vx, vy, vz, status,
                                                                        bb, bi);
     return cudaGetLastError();
 }
@@ -1001,7 +997,7 @@ cudaError_t launch_combine(const double *partial, int split, int N, int npad, in
                            double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
                            cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    combine_kernel<<<(N + 255) / 256, 256, 0, s>>>(partial, split, N, npad, compensated, perm, tau, acc, vx, vy, vz,
+    combine_kernel<<<dim3((N + 255) / 256, 3), 256, 0, s>>>(partial, split, N, npad, compensated, perm, tau, acc, vx, vy, vz,
                                                    status);
     return cudaGetLastError();
 }

@@ -187,7 +187,7 @@ genga_status genga_tuning_times(genga_ctx *c, int32_t N, float *ms, int32_t n) {
     int b = 0;
     for (int v = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD; v > 1; v >>= 1) b++;
     b = b < 32 ? b : 31;
-    for (int q = 0; q < n; q++) ms[q] = (q < 8 && q < num_fp32_variants()) ? c->tune_ms[b][q] : 0.f;
+    for (int q = 0; q < n; q++) ms[q] = (q < GENGA_MAX_VARIANTS && q < num_fp32_variants()) ? c->tune_ms[b][q] : 0.f;
     return GENGA_OK;
 }
 
