@@ -89,9 +89,9 @@ PassArgs base_args(genga_ctx *c, const genga_system &sys, const genga_params &p)
 }
 
 // The FP32 pass variant for this size: forced, already tuned, or tuned now.
-// Tuning runs every variant four times on the packed state (the encounter
-// list is cleared after each run) and keeps the variant with the fastest of
-// its last three runs; it synchronises the stream, so it is skipped while
+// Tuning runs every variant's pass and combine (with no kick applied) four
+// times on the packed state (the encounter list is cleared after each run)
+// and keeps the variant with the fastest of its last three runs; it synchronises the stream, so it is skipped while
 // the stream is captured.
 int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
     if (c->forced_variant >= 0) return c->forced_variant;
@@ -112,9 +112,12 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
         int grid = 1;
         plan_pass(N, GENGA_FP32, v, c->sm_count, c->partial_cap, &a.split, &a.chunk_tiles, &grid);
         float ms = 3.0e38f;
-        for (int rep = 0; rep < 4; rep++) {
+        for (int rep = 0; rep < 4; rep++) {  // pass + combine (no kick applied, no output)
             cudaEventRecord(e0, s);
-            const cudaError_t e = launch_pass(a, GENGA_FP32, v, grid, s);
+            cudaError_t e = launch_pass(a, GENGA_FP32, v, grid, s);
+            if (e == cudaSuccess)
+                e = launch_combine(c->partial, a.split, N, a.npad, 0, c->perm, 0.0, nullptr, nullptr, nullptr, nullptr,
+                                   c->status, s);
             cudaEventRecord(e1, s);
             cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s);
             if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
@@ -162,8 +165,8 @@ cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &
     e = launch_pass(a, precision, variant, grid, s);
     profile_after_pass(c, s);
     if (e != cudaSuccess) return e;
-    c->launches += 2;  // pass + encounter-list sort
-    if ((e = launch_sort_pairs(c->enc, c->enc_cap, c->enc_count, s)) != cudaSuccess) return e;
+    c->launches += 1;
+    c->enc_sorted = false;  // sorted when the list is read
     *split_out = split;
     return cudaSuccess;
 }
@@ -217,7 +220,7 @@ BatchBodies batch_bodies(const int32_t *offsets, int D) {
 }
 
 // Work items of the FP32 pass over a batch: system d gets a share of about
-// 24 items per resident CTA proportional to npad_d^2 (its pair count), cut
+// 96 items per SM proportional to npad_d^2 (its pair count), cut
 // into j-chunks per i-block; systems are handed out largest item first.
 // False if the partial sums would not fit.
 bool plan_batch(const genga_ctx *c, const BatchBodies &bb, int variant, BatchItems *bi, int *grid) {
@@ -228,7 +231,7 @@ bool plan_batch(const genga_ctx *c, const BatchBodies &bb, int variant, BatchIte
         const double np = bb.poff[d + 1] - bb.poff[d];
         total += np * np;
     }
-    for (int target = 24 * minb * c->sm_count; target >= 1; target /= 2) {
+    for (int target = 96 * c->sm_count; target >= 1; target /= 2) {
         long long pbase = 0;
         for (int d = 0; d < bb.D; d++) {
             const int np = bb.poff[d + 1] - bb.poff[d];
@@ -305,8 +308,8 @@ cudaError_t run_kick_batched(genga_ctx *c, const genga_system &all, const int32_
     e = launch_pass_batched(a, bb, bi, variant, grid, s);
     profile_after_pass(c, s);
     if (e != cudaSuccess) return e;
-    if ((e = launch_sort_pairs(c->enc, c->enc_cap, c->enc_count, s)) != cudaSuccess) return e;
-    c->launches += 3;
+    c->enc_sorted = false;
+    c->launches += 2;
     return launch_combine_batched(bb, bi, c->partial, c->perm, tau, acc, all.vx, all.vy, all.vz, c->status, s);
 }
 
@@ -371,10 +374,10 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     c->sm_count = prop.multiProcessorCount;
     const int np = npad_of(max_N > 0 ? max_N : 1);
     c->npad_max = np;
-    // partial sums: split * 3 * npad doubles; the plans stay near 24 items of
-    // at most 512 bodies per resident CTA, i.e. split * npad <~ 24 * SMs * 1024
-    // (plan_pass clamps)
-    c->partial_cap = 3 * ((size_t)np * 4 + (size_t)32 * c->sm_count * 1024 + 4096);
+    // partial sums: split * 3 * npad doubles; the plans stay near 96 items per
+    // SM of up to 512 bodies, i.e. split * npad <~ 96 * SMs * 512 (plan_pass
+    // clamps larger i-blocks to this)
+    c->partial_cap = 3 * ((size_t)np * 4 + (size_t)96 * c->sm_count * 512 + 4096);
     long long ecap = 4096;
     while (ecap < 16LL * max_N) ecap <<= 1;
     c->enc_cap = (int32_t)ecap;
@@ -444,9 +447,14 @@ genga_status genga_drift(genga_ctx *c, genga_system *sys, const genga_params *p,
 genga_status genga_last_encounters(genga_ctx *c, int32_t *pairs, int32_t capacity, int32_t *count, void *stream) {
     if (!c || capacity < 0 || !count || (capacity > 0 && !pairs)) return GENGA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->enc_sorted) {  // the list is in discovery order until first read
+        if (launch_sort_pairs(c->enc, c->enc_cap, c->enc_count, s) != cudaSuccess) return GENGA_ERR_CUDA;
+        c->enc_sorted = true;
+        c->launches += 1;
+    }
     c->launches += 1;
-    return launch_copy_pairs(c->enc, c->enc_count, c->enc_cap, pairs, capacity, count, c->status,
-                             (cudaStream_t)stream) == cudaSuccess
+    return launch_copy_pairs(c->enc, c->enc_count, c->enc_cap, pairs, capacity, count, c->status, s) == cudaSuccess
                ? GENGA_OK
                : GENGA_ERR_CUDA;
 }
@@ -461,6 +469,7 @@ genga_status genga_encounters(genga_ctx *c, const genga_system *sys, const genga
     cudaStream_t s = (cudaStream_t)stream;
     if (sys->N == 0) {
         if (cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s) != cudaSuccess) return GENGA_ERR_CUDA;
+        c->enc_sorted = true;
     } else {
         int split;
         if (run_pass(c, *sys, *p, GENGA_FP32, true, &split, s) != cudaSuccess) return GENGA_ERR_CUDA;

@@ -8,8 +8,8 @@
 // universal anomaly s,
 //   F(s) = r0 G1(s) + eta0 G2(s) + mu G3(s) - dt = 0,  G_k = s^k c_k(beta s^2),
 // beta = 2 mu / r0 - v0^2, eta0 = x0 . v0, solved by the Laguerre-Conway
-// iteration (order 5, Conway 1986) from s = dt / r0, followed by the f and g
-// functions.  The Stumpff functions c_k(z) come from their Taylor series for
+// iteration (order 5, Conway 1986) from a second-order estimate of s, followed
+// by the f and g functions.  The Stumpff functions c_k(z) come from their Taylor series for
 // |z| < 1 and from the trigonometric / hyperbolic closed forms otherwise
 // (with the half-angle form of c2, which does not cancel).
 #include "internal.cuh"
@@ -18,7 +18,10 @@ namespace genga {
 
 namespace {
 
-// c2(z) = sum_k (-z)^k / (2k+2)!,  c3(z) = sum_k (-z)^k / (2k+3)!
+// c2(z) = sum_k (-z)^k / (2k+2)!,  c3(z) = sum_k (-z)^k / (2k+3)!, the
+// first NT terms (10 terms reach rounding level for |z| < 1, 6 for
+// |z| < 0.1: the next terms are below 2^-53 of the sums)
+template <int NT>
 __device__ __forceinline__ void stumpff_series(double z, double &c2, double &c3) {
     constexpr double a2[10] = {1.0 / 2.0,
                                1.0 / 24.0,
@@ -41,9 +44,9 @@ __device__ __forceinline__ void stumpff_series(double z, double &c2, double &c3)
                                1.0 / 121645100408832000.0,
                                1.0 / 51090942171709440000.0};
     const double w = -z;
-    double p2 = a2[9], p3 = a3[9];
+    double p2 = a2[NT - 1], p3 = a3[NT - 1];
 #pragma unroll
-    for (int k = 8; k >= 0; k--) {
+    for (int k = NT - 2; k >= 0; k--) {
         p2 = fma(p2, w, a2[k]);
         p3 = fma(p3, w, a3[k]);
     }
@@ -52,8 +55,12 @@ __device__ __forceinline__ void stumpff_series(double z, double &c2, double &c3)
 }
 
 __device__ __forceinline__ void stumpff(double z, double &c0, double &c1, double &c2, double &c3) {
-    if (fabs(z) < 1.0) {
-        stumpff_series(z, c2, c3);
+    if (fabs(z) < 0.1) {  // the usual case: dt small against the orbital period
+        stumpff_series<6>(z, c2, c3);
+        c0 = 1.0 - z * c2;
+        c1 = 1.0 - z * c3;
+    } else if (fabs(z) < 1.0) {
+        stumpff_series<10>(z, c2, c3);
         c0 = 1.0 - z * c2;
         c1 = 1.0 - z * c3;
     } else if (z > 0.0) {
@@ -78,11 +85,20 @@ __device__ __forceinline__ void stumpff(double z, double &c0, double &c1, double
 // Returns true when the iteration met |ds| <= 1e-12 |s| within max_iter steps.
 __device__ bool kepler_drift(double mu, double dt, int max_iter, double &x, double &y, double &z, double &u,
                              double &v, double &w) {
-    const double r0 = sqrt(x * x + y * y + z * z);
+    // FP64 divisions and square roots as series-corrected SFU seeds (the
+    // FP64 pipe is the slow one on this GPU)
+    const double rr = x * x + y * y + z * z;
+    const double ir0 = rsqrt_fp64(rr);
+    const double r0 = rr * ir0;
     const double v2 = u * u + v * v + w * w;
     const double eta = x * u + y * v + z * w;
-    const double beta = 2.0 * mu / r0 - v2;
-    double s = dt / r0;
+    const double beta = 2.0 * mu * ir0 - v2;
+    // start from the second-order expansion of s(t) = int dt / r,
+    // s ~ dt / r0 - eta dt^2 / (2 r0^3), which saves about one iteration on
+    // near-circular orbits; plain dt / r0 where the correction is not small
+    const double q = dt * ir0;
+    const double corr = 0.5 * eta * q * ir0;
+    double s = fabs(corr) < 0.25 ? q * (1.0 - corr) : q;
     double c0, c1, c2, c3;
     bool ok = false;
     for (int it = 0; it < max_iter; it++) {
@@ -93,7 +109,7 @@ __device__ bool kepler_drift(double mu, double dt, int max_iter, double &x, doub
         const double ddF = fma(eta, c0, (mu - beta * r0) * G1);
         // Laguerre-Conway step, order n = 5
         const double rad = sqrt(fabs(16.0 * dF * dF - 20.0 * F * ddF));
-        const double ds = -5.0 * F / (dF + copysign(rad, dF));
+        const double ds = -5.0 * F * rcp_fp64(dF + copysign(rad, dF));
         s += ds;
         if (fabs(ds) <= 1e-12 * fabs(s)) {
             ok = true;
@@ -103,10 +119,11 @@ __device__ bool kepler_drift(double mu, double dt, int max_iter, double &x, doub
     stumpff(beta * s * s, c0, c1, c2, c3);
     const double G1 = s * c1, G2 = s * s * c2;
     const double r = fma(r0, c0, fma(eta, G1, mu * G2));
-    const double f = 1.0 - mu * G2 / r0;
+    const double ir = rcp_fp64(r);
+    const double f = 1.0 - mu * G2 * ir0;
     const double g = fma(r0, G1, eta * G2);
-    const double fd = -mu * G1 / (r * r0);
-    const double gd = 1.0 - mu * G2 / r;
+    const double fd = -mu * G1 * ir * ir0;
+    const double gd = 1.0 - mu * G2 * ir;
     const double nx = f * x + g * u, ny = f * y + g * v, nz = f * z + g * w;
     const double nu = fd * x + gd * u, nv = fd * y + gd * v, nw = fd * z + gd * w;
     x = nx; y = ny; z = nz;
@@ -114,16 +131,16 @@ __device__ bool kepler_drift(double mu, double dt, int max_iter, double &x, doub
     return ok;
 }
 
-// x += h P / M*, then the Kepler drift over dt.
+// x += (h / M*) P, then the Kepler drift over dt.
 __global__ void drift_kernel(double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
                              double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz, int N,
-                             const double *__restrict__ P, double Mstar, double mu, double h, double dt,
+                             const double *__restrict__ P, double hM, double mu, double dt,
                              int max_iter, uint32_t *__restrict__ status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double xi = x[i] + h * P[0] / Mstar;
-    double yi = y[i] + h * P[1] / Mstar;
-    double zi = z[i] + h * P[2] / Mstar;
+    double xi = fma(hM, P[0], x[i]);
+    double yi = fma(hM, P[1], y[i]);
+    double zi = fma(hM, P[2], z[i]);
     double ui = vx[i], vi = vy[i], wi = vz[i];
     if (!kepler_drift(mu, dt, max_iter, xi, yi, zi, ui, vi, wi)) atomicOr(status, GENGA_BIT(GENGA_ERR_KEPLER));
     x[i] = xi; y[i] = yi; z[i] = zi;
@@ -131,26 +148,26 @@ __global__ void drift_kernel(double *__restrict__ x, double *__restrict__ y, dou
 }
 
 __global__ void hc_kernel(double *__restrict__ x, double *__restrict__ y, double *__restrict__ z, int N,
-                          const double *__restrict__ P, double Mstar, double h) {
+                          const double *__restrict__ P, double hM) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    x[i] += h * P[0] / Mstar;
-    y[i] += h * P[1] / Mstar;
-    z[i] += h * P[2] / Mstar;
+    x[i] = fma(hM, P[0], x[i]);
+    y[i] = fma(hM, P[1], y[i]);
+    z[i] = fma(hM, P[2], z[i]);
 }
 
 // Batched: body i of system d (segment of i in off) drifts with P of its system.
 __global__ void drift_batched_kernel(double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
                                      double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
-                                     const double *__restrict__ Pd, double Mstar, double mu, double h, double dt,
+                                     const double *__restrict__ Pd, double hM, double mu, double dt,
                                      int max_iter, uint32_t *__restrict__ status,
                                      const __grid_constant__ BatchBodies bb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= bb.N_total) return;
     const double *P = Pd + 3 * find_segment(bb.off, bb.D, i);
-    double xi = x[i] + h * P[0] / Mstar;
-    double yi = y[i] + h * P[1] / Mstar;
-    double zi = z[i] + h * P[2] / Mstar;
+    double xi = fma(hM, P[0], x[i]);
+    double yi = fma(hM, P[1], y[i]);
+    double zi = fma(hM, P[2], z[i]);
     double ui = vx[i], vi = vy[i], wi = vz[i];
     if (!kepler_drift(mu, dt, max_iter, xi, yi, zi, ui, vi, wi)) atomicOr(status, GENGA_BIT(GENGA_ERR_KEPLER));
     x[i] = xi; y[i] = yi; z[i] = zi;
@@ -158,14 +175,14 @@ __global__ void drift_batched_kernel(double *__restrict__ x, double *__restrict_
 }
 
 __global__ void hc_batched_kernel(double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
-                                  const double *__restrict__ Pd, double Mstar, double h,
+                                  const double *__restrict__ Pd, double hM,
                                   const __grid_constant__ BatchBodies bb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= bb.N_total) return;
     const double *P = Pd + 3 * find_segment(bb.off, bb.D, i);
-    x[i] += h * P[0] / Mstar;
-    y[i] += h * P[1] / Mstar;
-    z[i] += h * P[2] / Mstar;
+    x[i] = fma(hM, P[0], x[i]);
+    y[i] = fma(hM, P[1], y[i]);
+    z[i] = fma(hM, P[2], z[i]);
 }
 
 }  // namespace
@@ -176,12 +193,12 @@ cudaError_t launch_drift_batched(genga_system &all, const BatchBodies &bb, const
     if (N <= 0) return cudaSuccess;
     cudaError_t e = launch_momentum_batched(all, bb, c->Pd, nullptr, s);
     if (e != cudaSuccess) return e;
-    drift_batched_kernel<<<(N + 127) / 128, 128, 0, s>>>(all.x, all.y, all.z, all.vx, all.vy, all.vz, c->Pd, p.Mstar,
-                                                         p.G * p.Mstar, 0.5 * dt, dt, p.kepler_max_iter, c->status, bb);
+    drift_batched_kernel<<<(N + 127) / 128, 128, 0, s>>>(all.x, all.y, all.z, all.vx, all.vy, all.vz, c->Pd,
+                                                         0.5 * dt / p.Mstar, p.G * p.Mstar, dt, p.kepler_max_iter, c->status, bb);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = launch_momentum_batched(all, bb, c->Pd, nullptr, s);
     if (e != cudaSuccess) return e;
-    hc_batched_kernel<<<(N + 255) / 256, 256, 0, s>>>(all.x, all.y, all.z, c->Pd, p.Mstar, 0.5 * dt, bb);
+    hc_batched_kernel<<<(N + 255) / 256, 256, 0, s>>>(all.x, all.y, all.z, c->Pd, 0.5 * dt / p.Mstar, bb);
     return cudaGetLastError();
 }
 
@@ -191,12 +208,12 @@ cudaError_t launch_drift(genga_system &sys, const genga_params &p, double dt, ge
     cudaError_t e = launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, N, c->mom, nullptr, s);
     if (e != cudaSuccess) return e;
     const int nb = (N + 127) / 128;
-    drift_kernel<<<nb, 128, 0, s>>>(sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, N, c->mom, p.Mstar,
-                                    p.G * p.Mstar, 0.5 * dt, dt, p.kepler_max_iter, c->status);
+    drift_kernel<<<nb, 128, 0, s>>>(sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, N, c->mom,
+                                    0.5 * dt / p.Mstar, p.G * p.Mstar, dt, p.kepler_max_iter, c->status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, N, c->mom, nullptr, s);
     if (e != cudaSuccess) return e;
-    hc_kernel<<<(N + 255) / 256, 256, 0, s>>>(sys.x, sys.y, sys.z, N, c->mom, p.Mstar, 0.5 * dt);
+    hc_kernel<<<(N + 255) / 256, 256, 0, s>>>(sys.x, sys.y, sys.z, N, c->mom, 0.5 * dt / p.Mstar);
     return cudaGetLastError();
 }
 

@@ -68,6 +68,7 @@ struct genga_ctx {
     int2 *enc;                 // [enc_cap] unsorted during the pass, sorted after
     int32_t enc_cap;           // power of two
     int32_t *enc_count;        // [1]
+    bool enc_sorted;           // the list has been sorted since the pass that built it
     uint32_t *status;          // [1] sticky bits
     double *energy_part;       // [energy_blocks][4]
     int32_t energy_blocks;
@@ -187,6 +188,29 @@ void profile_free(genga_ctx *c);
 // ------------------------------------------------------------ PTX wrappers
 #ifdef __CUDACC__
 namespace genga {
+
+// 1/sqrt(x) in FP64: the approximate FP64 reciprocal square root of the SFU
+// as seed y0 (relative error ~1e-7), then the third-order correction
+// y = y0 (1 + e/2 + 3e^2/8), e = 1 - x y0^2, from the binomial series of
+// (1 - e)^(-1/2); the truncation error is O(e^3) ~ 1e-21.
+__device__ __forceinline__ double rsqrt_fp64(double x) {
+    double y0;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(x));
+    const double t = x * y0;
+    const double e = fma(-t, y0, 1.0);
+    const double p = fma(e, 0.375, 0.5);
+    return fma(y0 * e, p, y0);
+}
+
+// 1/x in FP64 (x normal): the approximate FP64 reciprocal of the SFU as seed
+// y0, then the third-order correction y = y0 (1 + e + e^2), e = 1 - x y0,
+// from the geometric series of 1 / (1 - e); truncation error O(e^3).
+__device__ __forceinline__ double rcp_fp64(double x) {
+    double y0;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(x));
+    const double e = fma(-x, y0, 1.0);
+    return fma(y0, fma(e, e, e), y0);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -82,19 +82,6 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
     return r;
 }
 
-// 1/sqrt(x) in FP64: the approximate FP64 reciprocal square root of the SFU
-// as seed y0 (relative error ~1e-7), then the third-order correction
-// y = y0 (1 + e/2 + 3e^2/8), e = 1 - x y0^2, from the binomial series of
-// (1 - e)^(-1/2); the truncation error is O(e^3) ~ 1e-21.
-__device__ __forceinline__ double rsqrt_fp64(double x) {
-    double y0;
-    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(x));
-    const double t = x * y0;
-    const double e = fma(-t, y0, 1.0);
-    const double p = fma(e, 0.375, 0.5);
-    return fma(y0 * e, p, y0);
-}
-
 // Changeover weight K(y) (Sect. 1): 0 for y <= 0, 1 for y >= 1.
 __device__ __forceinline__ double changeover_K(double y, int form) {
     if (y <= 0.0) return 0.0;
@@ -868,6 +855,7 @@ __global__ void copy_pairs_kernel(const int2 *__restrict__ enc, const int32_t *_
 
 // ------------------------------------------------------------ variants ----
 constexpr int F32_TILE = 256;
+constexpr int F32_ITEMS_PER_SM = 96;
 
 // FP32 pass variants (packing, bodies per thread, consumer warps, CTAs per
 // SM, FAR-loop unroll, ring stages); the autotuner in api.cu times them per N
@@ -901,8 +889,9 @@ size_t smem_fp64() { return (size_t)F64_STAGES * F64_TILE * sizeof(double4_32a) 
 
 }  // namespace
 
-// Work decomposition of one pass.  FP32 (persistent): about 24 work items
-// per resident CTA (finer items shorten the tail where CTAs run out of work); split is the number of j-chunks per i-block and
+// Work decomposition of one pass.  FP32 (persistent): about F32_ITEMS_PER_SM
+// work items per SM (finer items shorten the tail where CTAs run out of
+// work; each item also adds a partial row of its i-block to the combine); split is the number of j-chunks per i-block and
 // chunk_tiles their length; grid = resident CTAs.  FP64: `split` contiguous
 // j-slices per i-block, one CTA each, sized to one wave of two CTAs per SM.
 // In both cases split * 3 * npad doubles of partial sums fit in partial_cap.
@@ -920,7 +909,7 @@ void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_c
     const int cap = (int)(partial_cap / (3 * (size_t)npad));
     int sp;
     if (f32) {
-        const int want_items = 24 * v.minb * sm_count;
+        const int want_items = F32_ITEMS_PER_SM * sm_count;
         sp = (want_items + iblocks - 1) / iblocks;
     } else {
         sp = 2 * sm_count / iblocks;

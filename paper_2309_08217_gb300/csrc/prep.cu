@@ -110,15 +110,20 @@ __device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double 
                                            double *__restrict__ rc_eq1, float3 *pos, bool *real) {
     float2 s = make_float2(0.f, 0.f);
     if (i >= 0) {
+        // osculating a from the heliocentric velocity u = v + P / M*:
+        // 1/a = 2/r - u^2 / (G (M* + m)); FP64 reciprocals by series-corrected
+        // SFU seeds (the FP64 pipe is the slow one on this GPU)
         const double xi = x[i], yi = y[i], zi = z[i], mi = m[i];
-        const double ux = vx[i] + P[0] / Mstar;
-        const double uy = vy[i] + P[1] / Mstar;
-        const double uz = vz[i] + P[2] / Mstar;
+        const double iM = rcp_fp64(Mstar);
+        const double ux = fma(P[0], iM, vx[i]);
+        const double uy = fma(P[1], iM, vy[i]);
+        const double uz = fma(P[2], iM, vz[i]);
         const double v2 = ux * ux + uy * uy + uz * uz;
-        const double r = sqrt(xi * xi + yi * yi + zi * zi);
+        const double r2 = xi * xi + yi * yi + zi * zi;
+        const double ri = rsqrt_fp64(r2);
         const double mu = G * (Mstar + mi);
-        const double inva = 2.0 / r - v2 / mu;
-        const double a = (inva > 0.0) ? 1.0 / inva : r;
+        const double inva = 2.0 * ri - v2 * rcp_fp64(mu);
+        const double a = (inva > 0.0) ? rcp_fp64(inva) : r2 * ri;
         a_osc[k] = a;
         if (rcrit_mode == GENGA_RCRIT_EQ1) {
             // r_crit,ij = max(rc_i, rc_j) = max(1, 1) * max(rc_i, rc_j)
