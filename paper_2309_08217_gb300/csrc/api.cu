@@ -84,7 +84,10 @@ PassArgs base_args(genga_ctx *c, const genga_system &sys, const genga_params &p)
     a.changeover = p.changeover;
     a.list_only = 0;
     a.work = c->work;
-    a.chunk_tiles = 1;
+    a.ntier = 1;
+    a.excess = 0;
+    a.tier_len[0] = 1;
+    a.tier_n[0] = 1;
     return a;
 }
 
@@ -110,7 +113,7 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
     for (int v = 0; v < num_fp32_variants(); v++) {
         PassArgs a = base;
         int grid = 1;
-        plan_pass(N, GENGA_FP32, v, c->sm_count, c->partial_cap, &a.split, &a.chunk_tiles, &grid);
+        plan_pass(N, GENGA_FP32, v, c->sm_count, c->partial_cap, &a, &grid);
         float ms = 3.0e38f;
         for (int rep = 0; rep < 4; rep++) {  // pass + combine (no kick applied, no output)
             cudaEventRecord(e0, s);
@@ -159,7 +162,7 @@ cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &
     PassArgs a = base_args(c, sys, p);
     const int variant = (precision == GENGA_FP32) ? fp32_variant(c, a, sys.N, s) : 0;
     int grid = 1;
-    plan_pass(sys.N, precision, variant, c->sm_count, c->partial_cap, &a.split, &a.chunk_tiles, &grid);
+    plan_pass(sys.N, precision, variant, c->sm_count, c->partial_cap, &a, &grid);
     const int split = a.split;
     profile_before_pass(c, s);
     e = launch_pass(a, precision, variant, grid, s);
@@ -237,7 +240,7 @@ bool plan_batch(const genga_ctx *c, const BatchBodies &bb, int variant, BatchIte
             const int np = bb.poff[d + 1] - bb.poff[d];
             bi->pbase[d] = pbase;
             if (np == 0) {
-                bi->nchunks[d] = bi->ctiles[d] = bi->iblocks[d] = 0;
+                bi->nchunks[d] = bi->blen[d] = bi->iblocks[d] = 0;
                 continue;
             }
             const int iblocks = (np + IB - 1) / IB, ntiles = np / 256;
@@ -247,7 +250,7 @@ bool plan_batch(const genga_ctx *c, const BatchBodies &bb, int variant, BatchIte
             const int ct = (ntiles + nch - 1) / nch;
             nch = (ntiles + ct - 1) / ct;
             bi->iblocks[d] = iblocks;
-            bi->ctiles[d] = ct;
+            bi->blen[d] = ct;
             bi->nchunks[d] = nch;
             pbase += (long long)nch * 3 * np;
         }
@@ -257,7 +260,7 @@ bool plan_batch(const genga_ctx *c, const BatchBodies &bb, int variant, BatchIte
         for (int a = 1; a < bb.D; a++) {  // insertion sort, D <= 256
             const int v = bi->order[a];
             int b = a - 1;
-            while (b >= 0 && bi->ctiles[bi->order[b]] < bi->ctiles[v]) {
+            while (b >= 0 && bi->blen[bi->order[b]] < bi->blen[v]) {
                 bi->order[b + 1] = bi->order[b];
                 b--;
             }

@@ -40,6 +40,7 @@ struct Profile {                // CUDA event pairs around pass launches
 }  // namespace genga
 
 #define GENGA_MAX_VARIANTS 16  // FP32 pass variants the context records tuning times for
+#define GENGA_MAX_TIERS 8      // chunk-length tiers of an FP32 pass plan
 
 struct genga_ctx {
     int device;
@@ -104,7 +105,7 @@ struct BatchItems {                     // work items of the FP32 pass over all 
     int32_t order[GENGA_MAX_DISCS];     // system handed out at rank r (largest items first)
     int32_t item0[GENGA_MAX_DISCS + 1]; // first item of rank r
     int32_t nchunks[GENGA_MAX_DISCS];   // j-chunks per i-block of system d
-    int32_t ctiles[GENGA_MAX_DISCS];    // tiles per chunk
+    int32_t blen[GENGA_MAX_DISCS];      // tiles per chunk (the first one shorter by nchunks * blen - tiles)
     int32_t iblocks[GENGA_MAX_DISCS];   // i-blocks of system d
     int64_t pbase[GENGA_MAX_DISCS];     // first partial double of system d
 };
@@ -143,7 +144,11 @@ struct PassArgs {               // one long-range pass
     int32_t rcrit_mode, changeover;
     int32_t list_only;          // 1: encounter list only (no force accumulation needed)
     int32_t *work;              // [1] dynamic work-item counter (zeroed before each launch)
-    int32_t chunk_tiles;        // j-tiles per work item
+    // FP32: the j-chunks of every i-block in tiers (see plan_pass): tier t has
+    // tier_n[t] chunks of tier_len[t] tiles, the first chunk being `excess`
+    // tiles shorter; split = sum of tier_n = partial rows per body
+    int32_t ntier, excess;
+    int32_t tier_len[GENGA_MAX_TIERS], tier_n[GENGA_MAX_TIERS];
 };
 
 cudaError_t launch_momentum(const double *vx, const double *vy, const double *vz, const double *m,
@@ -154,9 +159,8 @@ size_t order_hist_entries(int nmax);
 cudaError_t init_pass_kernels();
 cudaError_t launch_pass(const PassArgs &a, int precision, int variant, int grid, cudaStream_t s);
 int num_fp32_variants();
-void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_cap, int *split, int *chunk_tiles,
-               int *grid);
-cudaError_t launch_combine(const double *partial, int split, int N, int npad, int compensated, const uint32_t *perm,
+void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_cap, PassArgs *a, int *grid);
+cudaError_t launch_combine(const double *partial, int split, int N, int npad, int fp64_rows, const uint32_t *perm,
                            double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
                            cudaStream_t s);
 cudaError_t launch_sort_pairs(int2 *enc, int32_t cap, const int32_t *count, cudaStream_t s);

@@ -23,8 +23,10 @@
 // Precision.  FP32 pass (the single-precision kick of Sect. 1): FAR pairs use
 // the FP32-rounded positions; NEAR pairs use the hi/lo split of the FP64
 // positions, dx = (x_j,hi - x_i,hi) + (x_j,lo - x_i,lo); r^2 in FP32, rsqrt on
-// the SFU, each tile's terms summed in FP32 registers and added into FP64
-// per-body accumulators once per tile.  FP64 pass: the same in FP64, with its
+// the SFU, each tile's terms summed in FP32 registers and added once per tile
+// into double-float (hi + lo, ~48-bit) per-body accumulators, which are also
+// the partial rows the combine adds up; FP64 appears only in screened pairs
+// and in the final hi + lo.  FP64 pass: the same in FP64, with its
 // own inverse square root (FP32 SFU seed + one third-order correction) and
 // Neumaier-compensated accumulation every 32 terms.
 //
@@ -34,6 +36,9 @@
 // (close-encounter forces are always FP64, Sect. 1), and, if r_ij < r_crit,ij,
 // it is appended to the encounter list (once, from the side with the smaller
 // body index).
+#include <algorithm>
+#include <cmath>
+
 #include "internal.cuh"
 
 namespace genga {
@@ -175,8 +180,8 @@ __device__ __forceinline__ bool far_pair_of_boxes(const Box &u, const Box &v, bo
 
 // ----------------------------------------------------------- FP32 pass ----
 // Persistent and warp-specialised.  Work items are (i-block, chunk of
-// chunk_tiles j-tiles), handed out by a global counter, so busy regions of
-// the disc do not hold up the rest of the GPU.  One producer warp fetches
+// j-tiles), handed out by a global counter, so busy regions of the disc do
+// not hold up the rest of the GPU.  One producer warp fetches
 // items and fills a STAGES-deep ring of j-tiles with bulk copies (mbarrier
 // "full" per slot, with a small header naming the item and tile); eight
 // consumer warps compute and release each slot on its "empty" mbarrier, so
@@ -184,56 +189,104 @@ __device__ __forceinline__ bool far_pair_of_boxes(const Box &u, const Box &v, bo
 // stalling the others.  Each item's result goes to its own partial row
 // (chunk, body), so the combined sum does not depend on which CTA ran it.
 // FAR/NEAR is decided per (warp, 64-body group of the tile).  Registers hold
-// only the FP32-rounded i positions and FP32 tile sums; FP64 per-body sums
-// live in shared memory, touched once per tile.
+// only the FP32-rounded i positions and FP32 tile sums; the double-float
+// per-body sums live in shared memory, touched once per tile.
 
 struct StageHdr {
     int item, tile, flags, pad;  // flags: 1 first tile of item, 2 last tile, 4 no more work
 };
 
-// Work item q -> (i-block, j-chunk).  Round r = q / iblocks visits, for every
-// i-block, the chunk at offset 0, +1, -1, +2, -2, ... (mod nchunks) from the
-// chunk holding the i-block's own bodies: the near-diagonal chunks, where the
-// NEAR tiles and screened pairs are, are handed out first, so the costly
-// items do not end up in the tail.
-__device__ __forceinline__ void item_of(int q, int iblocks, int nchunks, int ib_bodies, int chunk_bodies, int *b,
-                                        int *c) {
-    const int r = q / iblocks;
-    *b = q - r * iblocks;
-    const int off = (r & 1) ? (r + 1) / 2 : -(r / 2);
-    const int c0 = (*b * ib_bodies) / chunk_bodies;
-    *c = ((c0 + off) % nchunks + nchunks) % nchunks;
+// Work item q -> (i-block b, chunk k), k-major: q = k * iblocks + b.  Chunk k
+// of an i-block covers the j-tiles of ranks u in the i-block's own order of
+// tiles by distance from its diagonal tile (ranks 0, 1, 2, 3, 4, ... are the
+// offsets 0, +1, -1, +2, -2, ...).  Chunk lengths come in tiers of
+// decreasing length: the near tiles, with the NEAR groups and screened
+// pairs, go out first in long items; the pass ends with single far tiles, so
+// the CTAs run out of work at nearly the same time while the partial rows
+// (one per chunk) stay few.
+__device__ __forceinline__ void item_of(int q, int iblocks, int *b, int *k) {
+    *k = q / iblocks;
+    *b = q - *k * iblocks;
 }
 
-// Geometry of the system a work item belongs to.
+// Ranks [u0, u1) of chunk k: tiers of cnt[t] chunks of len[t] ranks, the
+// first chunk shorter by `excess`.
+__device__ __forceinline__ void chunk_ranks(int k, int ntier, int excess, const int *len, const int *cnt, int *u0,
+                                            int *u1) {
+    int u = -excess;
+    for (int t = 0; t < ntier; t++) {
+        if (k < cnt[t]) {
+            const int a = u + k * len[t];
+            *u0 = a > 0 ? a : 0;
+            *u1 = a + len[t];
+            return;
+        }
+        k -= cnt[t];
+        u += cnt[t] * len[t];
+    }
+    *u0 = *u1 = 0;  // not reached for k < the number of chunks
+}
+
+__device__ __forceinline__ int tile_of_rank(int tdiag, int u, int ntiles) {
+    const int off = (u & 1) ? (u + 1) / 2 : -(u / 2);
+    return ((tdiag + off) % ntiles + ntiles) % ntiles;
+}
+
+// Geometry of the system a work item belongs to, with its chunk tiers.
 struct ItemGeo {
-    int poff, npad, Nd, off, nchunks, ctiles, iblocks;
+    int poff, npad, Nd, off, nchunks, iblocks, ntier, excess;
+    const int *tlen, *tcnt;
     long long pbase;
 };
 
 // Work items of a single system (the whole packed range).
 struct SingleItems {
     __device__ int total(const PassArgs &a, int IB) const { return ((a.npad + IB - 1) / IB) * a.split; }
-    __device__ void decode(const PassArgs &a, int IB, int TILE_, int q, int *ib, int *chunk, ItemGeo *g) const {
-        *g = ItemGeo{0, a.npad, a.N, 0, a.split, a.chunk_tiles, (a.npad + IB - 1) / IB, 0};
-        item_of(q, g->iblocks, g->nchunks, IB, g->ctiles * TILE_, ib, chunk);
+    __device__ void decode(const PassArgs &a, int IB, int, int q, int *ib, int *chunk, ItemGeo *g) const {
+        *g = ItemGeo{0, a.npad, a.N, 0, a.split, (a.npad + IB - 1) / IB, a.ntier, a.excess, a.tier_len, a.tier_n, 0};
+        item_of(q, g->iblocks, ib, chunk);
     }
 };
 
 // Work items of a batch: ranks of systems in handout order (largest items
-// first), each system's items in the diagonal-first order of item_of.
+// first), each system's items in the order of item_of, one tier of chunks
+// per system (the small systems handed out last make the tail).
 struct BatchPolicy {
     BatchBodies bb;
     BatchItems bi;
     __device__ int total(const PassArgs &, int) const { return bi.items_total; }
-    __device__ void decode(const PassArgs &, int IB, int TILE_, int q, int *ib, int *chunk, ItemGeo *g) const {
+    __device__ void decode(const PassArgs &, int, int, int q, int *ib, int *chunk, ItemGeo *g) const {
         const int r = find_segment(bi.item0, bb.D, q);
         const int d = bi.order[r];
-        *g = ItemGeo{bb.poff[d], bb.poff[d + 1] - bb.poff[d], bb.off[d + 1] - bb.off[d], bb.off[d], bi.nchunks[d],
-                     bi.ctiles[d], bi.iblocks[d], (long long)bi.pbase[d]};
-        item_of(q - bi.item0[r], g->iblocks, g->nchunks, IB, g->ctiles * TILE_, ib, chunk);
+        const int np = bb.poff[d + 1] - bb.poff[d];
+        *g = ItemGeo{bb.poff[d],        np, bb.off[d + 1] - bb.off[d], bb.off[d], bi.nchunks[d], bi.iblocks[d], 1,
+                     bi.nchunks[d] * bi.blen[d] - np / GENGA_TILE_T, &bi.blen[d], &bi.nchunks[d],
+                     (long long)bi.pbase[d]};
+        item_of(q - bi.item0[r], g->iblocks, ib, chunk);
     }
 };
+
+// Double-float accumulator: value = hi + lo, |lo| <= ulp(hi) / 2, about 48
+// significant bits from FP32 arithmetic alone (Knuth's two-sum followed by
+// a fast-two-sum renormalisation).  The FP32 pass accumulates and stores its
+// per-body sums this way: this GPU's FP64 pipe runs at 1/64 of its FP32 rate.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF a, float bh, float bl) {  // a + (bh + bl)
+    const float s = a.hi + bh;
+    const float bp = s - a.hi;
+    const float e = (a.hi - (s - bp)) + (bh - bp);
+    const float l = (a.lo + bl) + e;
+    const float h = s + l;
+    return DF{h, l - (h - s)};
+}
+
+__device__ __forceinline__ DF df_of_double(double x) {
+    const float h = __double2float_rn(x);
+    return DF{h, __double2float_rn(x - (double)h)};
+}
 
 // Scalar value of i-body k from its packed register: the j-packed loop keeps
 // {x_k, x_k}, the i-packed loop {x_2q, x_2q+1} in register q.
@@ -270,7 +323,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
     uint64_t *full = reinterpret_cast<uint64_t *>(s_ghi + STAGES * NG);
     uint64_t *empty = full + STAGES;
     StageHdr *hdr = reinterpret_cast<StageHdr *>(empty + STAGES);
-    __shared__ double s_acc[3 * BPT * NC];  // [c][k][thread]
+    __shared__ DF s_acc[3 * BPT * NC];      // [c][k][thread] double-float per-body sums
     __shared__ float4 s_ilo[BPT * NC];      // lo parts of this thread's i-bodies (current item)
     __shared__ float2 s_iscr[BPT * NC];     // and their screening factors
     __shared__ unsigned long long s_mask[BPT * NC];  // screened j of the current NEAR group, per i-body
@@ -304,13 +357,16 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
             int ib, chunk;
             ItemGeo geo;
             pol.decode(a, IB, TILE, q, &ib, &chunk, &geo);
-            const int t0 = geo.poff / TILE;  // first tile of the system
-            const int ta = t0 + chunk * geo.ctiles, tb = t0 + min(geo.npad / TILE, (chunk + 1) * geo.ctiles);
-            for (int t = ta; t < tb; t++, n++) {
+            const int t0 = geo.poff / TILE, nt = geo.npad / TILE;  // first tile and tiles of the system
+            const int tdiag = (ib * IB) / TILE;                      // the i-block's diagonal tile
+            int u0, u1;
+            chunk_ranks(chunk, geo.ntier, geo.excess, geo.tlen, geo.tcnt, &u0, &u1);
+            for (int ur = u0; ur < u1; ur++, n++) {
+                const int t = t0 + tile_of_rank(tdiag, ur, nt);
                 const int slot = n % STAGES;
                 const unsigned u = n / STAGES;
                 if (u > 0 && !mbar_wait_bounded(&empty[slot], (u - 1) & 1, a.status)) return;
-                hdr[slot] = StageHdr{q, t, (t == ta ? 1 : 0) | (t == tb - 1 ? 2 : 0), 0};
+                hdr[slot] = StageHdr{q, t, (ur == u0 ? 1 : 0) | (ur == u1 - 1 ? 2 : 0), 0};
                 fence_proxy_async_smem();
                 constexpr uint32_t GB = NG * sizeof(float4);
                 mbar_arrive_expect_tx(&full[slot], TBH + TBL + 2 * GB);
@@ -350,7 +406,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                 s_ilo[k * NC + tid] = in ? a.lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
                 s_iscr[k * NC + tid] = in ? a.scr[i] : make_float2(0.f, 0.f);
 #pragma unroll
-                for (int c = 0; c < 3; c++) s_acc[(c * BPT + k) * NC + tid] = 0.0;
+                for (int c = 0; c < 3; c++) s_acc[(c * BPT + k) * NC + tid] = DF{0.f, 0.f};
                 s_mask[k * NC + tid] = 0ull;
             }
 #pragma unroll
@@ -508,9 +564,13 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                                 fz += f.z;
                             }
                         } while (msk);
-                        s_acc[(0 * BPT + k) * NC + tid] += fx;
-                        s_acc[(1 * BPT + k) * NC + tid] += fy;
-                        s_acc[(2 * BPT + k) * NC + tid] += fz;
+                        const double f3[3] = {fx, fy, fz};
+#pragma unroll
+                        for (int c = 0; c < 3; c++) {
+                            DF &t = s_acc[(c * BPT + k) * NC + tid];
+                            const DF d = df_of_double(f3[c]);
+                            t = df_add(t, d.hi, d.lo);
+                        }
                     }
                 };
                 if constexpr (IPACK) {
@@ -540,22 +600,29 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
             }
         }
 #pragma unroll
-        for (int k = 0; k < BPT; k++) {  // fold the tile's FP32 sums into the FP64 sums
-            s_acc[(0 * BPT + k) * NC + tid] += (double)ax[k];
-            s_acc[(1 * BPT + k) * NC + tid] += (double)ay[k];
-            s_acc[(2 * BPT + k) * NC + tid] += (double)az[k];
+        for (int k = 0; k < BPT; k++) {  // fold the tile's FP32 sums into the double-float sums
+            DF &tx_ = s_acc[(0 * BPT + k) * NC + tid];
+            DF &ty_ = s_acc[(1 * BPT + k) * NC + tid];
+            DF &tz_ = s_acc[(2 * BPT + k) * NC + tid];
+            tx_ = df_add(tx_, ax[k], 0.f);
+            ty_ = df_add(ty_, ay[k], 0.f);
+            tz_ = df_add(tz_, az[k], 0.f);
         }
         if ((h.flags & 2) && in) {  // last tile of the item: write its partial row
             int ib, chunk;
             ItemGeo geo;
             pol.decode(a, IB, TILE, h.item, &ib, &chunk, &geo);
             const size_t np = (size_t)geo.npad;
-            double *out = a.partial + geo.pbase + (size_t)chunk * 3 * np;
+            // partial rows of the FP32 pass: double-float pairs (8 bytes, like a double)
+            float2 *out = reinterpret_cast<float2 *>(a.partial + geo.pbase) + (size_t)chunk * 3 * np;
 #pragma unroll
             for (int k = 0; k < BPT; k++) {
                 const int i = wbase - geo.poff + k * 32 + lane;
 #pragma unroll
-                for (int c = 0; c < 3; c++) out[c * np + i] = s_acc[(c * BPT + k) * NC + tid];
+                for (int c = 0; c < 3; c++) {
+                    const DF t = s_acc[(c * BPT + k) * NC + tid];
+                    out[c * np + i] = make_float2(t.hi, t.lo);
+                }
             }
         }
     }
@@ -707,33 +774,39 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
 
 // ------------------------------------------------------------ combine ----
 // One thread per (body, component): the body's partial rows summed in row
-// order (Neumaier-compensated for the FP64 pass; plain FP64 for the FP32
-// pass, whose partials carry FP32 rounding far above FP64's).  The rows are
-// fetched COMBINE_BATCH at a time before any of them is added, so a thread
-// waits for a few memory round trips, not one per row.  Then the optional
-// acc output and v_c += acc_c * tau for the body's caller index; non-finite
+// order -- double-float pairs of the FP32 pass in double-float arithmetic,
+// FP64 rows of the FP64 pass Neumaier-compensated.  The rows are fetched
+// COMBINE_BATCH at a time before any of them is added, so a thread waits for
+// a few memory round trips, not one per row.  Then the optional acc output
+// and v_c += acc_c * tau for the body's caller index; non-finite
 // accelerations raise NONFINITE.
 constexpr int COMBINE_BATCH = 16;
 
-template <bool COMP>
-__device__ __forceinline__ double ordered_row_sum(const double *__restrict__ p, size_t stride, int nrows) {
+__device__ __forceinline__ double df_row_sum(const float2 *__restrict__ p, size_t stride, int nrows) {
+    DF t{0.f, 0.f};
+    for (int q0 = 0; q0 < nrows; q0 += COMBINE_BATCH) {
+        float2 v[COMBINE_BATCH];
+#pragma unroll
+        for (int u = 0; u < COMBINE_BATCH; u++)
+            v[u] = (q0 + u < nrows) ? p[(size_t)(q0 + u) * stride] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < COMBINE_BATCH; u++)
+            if (q0 + u < nrows) t = df_add(t, v[u].x, v[u].y);
+    }
+    return (double)t.hi + (double)t.lo;
+}
+
+__device__ __forceinline__ double comp_row_sum(const double *__restrict__ p, size_t stride, int nrows) {
     Comp s{0.0, 0.0};
-    double t = 0.0;
     for (int q0 = 0; q0 < nrows; q0 += COMBINE_BATCH) {
         double v[COMBINE_BATCH];
 #pragma unroll
         for (int u = 0; u < COMBINE_BATCH; u++) v[u] = (q0 + u < nrows) ? p[(size_t)(q0 + u) * stride] : 0.0;
 #pragma unroll
-        for (int u = 0; u < COMBINE_BATCH; u++) {
-            if (q0 + u < nrows) {
-                if (COMP)
-                    s.add(v[u]);
-                else
-                    t += v[u];
-            }
-        }
+        for (int u = 0; u < COMBINE_BATCH; u++)
+            if (q0 + u < nrows) s.add(v[u]);
     }
-    return COMP ? s.s + s.c : t;
+    return s.s + s.c;
 }
 
 __device__ __forceinline__ void apply_component(double t, int c, int i, size_t NT, double tau, double *acc,
@@ -747,21 +820,21 @@ __device__ __forceinline__ void apply_component(double t, int c, int i, size_t N
 }
 
 // grid (ceil(N / 256), 3): blockIdx.y is the component
-__global__ void combine_kernel(const double *__restrict__ partial, int split, int N, int npad, int compensated,
+__global__ void combine_kernel(const double *__restrict__ partial, int split, int N, int npad, int fp64_rows,
                                const uint32_t *__restrict__ perm, double tau, double *__restrict__ acc,
                                double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
                                uint32_t *__restrict__ status) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
     if (k >= N) return;
-    const double *p = partial + (size_t)c * npad + k;
-    const size_t stride = 3 * (size_t)npad;
-    const double t = compensated ? ordered_row_sum<true>(p, stride, split) : ordered_row_sum<false>(p, stride, split);
+    const size_t off = (size_t)c * npad + k, stride = 3 * (size_t)npad;
+    const double t = fp64_rows ? comp_row_sum(partial + off, stride, split)
+                               : df_row_sum(reinterpret_cast<const float2 *>(partial) + off, stride, split);
     apply_component(t, c, (int)perm[k], (size_t)N, tau, acc, vx, vy, vz, status);
 }
 
 // Batched: packed position p of system d; rows of d start at pbase[d], one
-// per j-chunk, each npad_d long; plain FP64 sums in row order.  grid
+// per j-chunk, each npad_d long (double-float pairs of the FP32 pass).  grid
 // (ceil(npad_total / 256), 3).
 __global__ void combine_batched_kernel(const double *__restrict__ partial, const uint32_t *__restrict__ perm,
                                        double tau, double *__restrict__ acc, double *__restrict__ vx,
@@ -774,7 +847,8 @@ __global__ void combine_batched_kernel(const double *__restrict__ partial, const
     const int k = p - bb.poff[d];
     if (k >= bb.off[d + 1] - bb.off[d]) return;
     const size_t np = (size_t)(bb.poff[d + 1] - bb.poff[d]);
-    const double t = ordered_row_sum<false>(partial + bi.pbase[d] + (size_t)c * np + k, 3 * np, bi.nchunks[d]);
+    const double t =
+        df_row_sum(reinterpret_cast<const float2 *>(partial + bi.pbase[d]) + (size_t)c * np + k, 3 * np, bi.nchunks[d]);
     apply_component(t, c, (int)perm[bb.off[d] + k], (size_t)bb.N_total, tau, acc, vx, vy, vz, status);
 }
 
@@ -855,7 +929,7 @@ __global__ void copy_pairs_kernel(const int2 *__restrict__ enc, const int32_t *_
 
 // ------------------------------------------------------------ variants ----
 constexpr int F32_TILE = 256;
-constexpr int F32_ITEMS_PER_SM = 96;
+constexpr int F32_TAIL_ITEMS = 5;  // single-tile work items per resident CTA at the end of a pass
 
 // FP32 pass variants (packing, bodies per thread, consumer warps, CTAs per
 // SM, FAR-loop unroll, ring stages); the autotuner in api.cu times them per N
@@ -889,40 +963,73 @@ size_t smem_fp64() { return (size_t)F64_STAGES * F64_TILE * sizeof(double4_32a) 
 
 }  // namespace
 
-// Work decomposition of one pass.  FP32 (persistent): about F32_ITEMS_PER_SM
-// work items per SM (finer items shorten the tail where CTAs run out of
-// work; each item also adds a partial row of its i-block to the combine); split is the number of j-chunks per i-block and
-// chunk_tiles their length; grid = resident CTAs.  FP64: `split` contiguous
-// j-slices per i-block, one CTA each, sized to one wave of two CTAs per SM.
-// In both cases split * 3 * npad doubles of partial sums fit in partial_cap.
+// Work decomposition of one pass.
+// FP32 (persistent): split j-chunks per i-block in tiers of chunk lengths,
+// built from the end of the pass: F32_TAIL_ITEMS single tiles per resident
+// CTA come last; each earlier tier has chunks as long as the work of all the
+// tiers after it per CTA (so an item of that tier started late still ends
+// while the later, shorter items keep the other CTAs busy) and about as much
+// work as they have together; lengths stop growing at half a CTA's share of
+// the pass, and the first tier takes what is left (its first chunk made
+// shorter to fit).  split = partial rows per body; grid = resident CTAs.
+// FP64: `split` contiguous j-slices per i-block, one CTA each, sized to one
+// wave of two CTAs per SM.  In both cases split * 3 * npad partial sums
+// (8 bytes each) fit in partial_cap.
 int num_fp32_variants() { return kNumF32Variants; }
 
-void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_cap, int *split, int *chunk_tiles,
-               int *grid) {
+void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_cap, PassArgs *a, int *grid) {
     const int npad = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
-    const bool f32 = precision == GENGA_FP32;
-    const F32Variant &v = kF32Variants[variant];
-    const int tile = f32 ? F32_TILE : F64_TILE;
-    const int ntiles = npad / tile;
-    const int ib = f32 ? v.cw * 32 * v.bpt : KB * F64_BPT;
-    const int iblocks = (npad + ib - 1) / ib;
     const int cap = (int)(partial_cap / (3 * (size_t)npad));
-    int sp;
-    if (f32) {
-        const int want_items = F32_ITEMS_PER_SM * sm_count;
-        sp = (want_items + iblocks - 1) / iblocks;
-    } else {
-        sp = 2 * sm_count / iblocks;
+    if (precision != GENGA_FP32) {
+        const int ntiles = npad / F64_TILE, iblocks = (npad + KB * F64_BPT - 1) / (KB * F64_BPT);
+        int sp = 2 * sm_count / iblocks;
+        sp = sp > ntiles ? ntiles : sp;
+        sp = sp > cap ? cap : sp;
+        a->split = sp < 1 ? 1 : sp;
+        a->ntier = 1;
+        a->excess = 0;
+        a->tier_len[0] = 1;
+        a->tier_n[0] = a->split;
+        *grid = iblocks;
+        return;
     }
-    sp = sp < 1 ? 1 : sp;
-    sp = sp > ntiles ? ntiles : sp;
-    sp = sp > cap ? cap : sp;
-    sp = sp < 1 ? 1 : sp;
-    const int ct = (ntiles + sp - 1) / sp;
-    *chunk_tiles = ct;
-    *split = f32 ? (ntiles + ct - 1) / ct : sp;
-    const int nitems = iblocks * *split;
-    *grid = f32 ? (nitems < v.minb * sm_count ? nitems : v.minb * sm_count) : iblocks;
+    const F32Variant &v = kF32Variants[variant];
+    const int ntiles = npad / F32_TILE, ib = v.cw * 32 * v.bpt, iblocks = (npad + ib - 1) / ib;
+    const int ctas = v.minb * sm_count;
+    const double r = (double)iblocks / ctas;  // single-tile items per CTA of one chunk per i-block
+    const int lmax = std::max(1, (int)(0.5 * ntiles * r));
+    int len[GENGA_MAX_TIERS], cnt[GENGA_MAX_TIERS], nt = 0, rows = 0;
+    int R = ntiles;
+    double drain = 0.0;  // work per CTA of the tiers already placed (after this one in time)
+    while (R > 0) {
+        int L = nt == 0 ? 1 : std::min(lmax, std::max(1, (int)drain));
+        int n = nt == 0 ? (int)std::ceil(F32_TAIL_ITEMS / r) : (int)std::ceil(drain / (L * r));
+        n = std::max(1, n);
+        if (nt == GENGA_MAX_TIERS - 1 || L == lmax || (long long)n * L >= R) n = (R + L - 1) / L;  // last tier
+        len[nt] = L;
+        cnt[nt] = n;
+        nt++;
+        rows += n;
+        R -= n * L;
+        drain += n * L * r;
+    }
+    if (rows > cap) {  // too many partial rows: one tier of equal chunks
+        const int L = (ntiles + cap - 1) / cap;
+        nt = 1;
+        len[0] = L;
+        cnt[0] = (ntiles + L - 1) / L;
+        R = ntiles - cnt[0] * L;
+        rows = cnt[0];
+    }
+    a->ntier = nt;
+    a->excess = -R;  // the first-processed chunk is this much shorter
+    for (int t = 0; t < nt; t++) {  // first-processed tier first
+        a->tier_len[t] = len[nt - 1 - t];
+        a->tier_n[t] = cnt[nt - 1 - t];
+    }
+    a->split = rows;
+    const int nitems = iblocks * rows;
+    *grid = nitems < ctas ? nitems : ctas;
 }
 
 // Dynamic shared memory above the 48 KB default needs an opt-in per kernel
@@ -982,11 +1089,11 @@ cudaError_t launch_combine_batched(const BatchBodies &bb, const BatchItems &bi, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine(const double *partial, int split, int N, int npad, int compensated, const uint32_t *perm,
+cudaError_t launch_combine(const double *partial, int split, int N, int npad, int fp64_rows, const uint32_t *perm,
                            double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
                            cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    combine_kernel<<<dim3((N + 255) / 256, 3), 256, 0, s>>>(partial, split, N, npad, compensated, perm, tau, acc, vx, vy, vz,
+    combine_kernel<<<dim3((N + 255) / 256, 3), 256, 0, s>>>(partial, split, N, npad, fp64_rows, perm, tau, acc, vx, vy, vz,
                                                    status);
     return cudaGetLastError();
 }
