@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip timing every FP32 variant")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-disc batched workload")
     ap.add_argument("--batched-steps", type=int, default=5)
+    ap.add_argument("--conservation", default=None,
+                    help="instead of the benchmark: energy and angular-momentum drift of FP32 vs FP64 runs, "
+                         "comma-separated workload:steps:sample_every (e.g. embryo6625:20000:1000,giants100k:100:10)")
     return ap.parse_args()
 
 
@@ -430,8 +433,67 @@ def run_genga(args):
     return 0
 
 
+# ------------------------------------------------------- conservation ----
+def run_conservation(args):
+    """Relative energy error and |dL/L| along FP32-kick and FP64-kick runs from
+    the same seeded state (one JSON line per workload).  genga_step leaves the
+    (1 - K) part of encounter pairs unintegrated (no Bulirsch-Stoer level), so
+    both runs carry that same approximation: the comparison is FP32 against
+    FP64 under one treatment."""
+    import numpy as np
+    import torch
+
+    import paper_2309_08217_gb300 as g
+    from paper_2309_08217_gb300 import discs
+    g.build()
+    g.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    for spec in args.conservation.split(","):
+        name, steps, every = spec.split(":")
+        steps, every = int(steps), int(every)
+        d = discs.workload(name)
+        ctx = g.Context(d.N, 0)
+        out = {"mode": "conservation", "workload": name, "N": d.N, "dt": d.dt, "steps": steps,
+               "sample_every": every, "data": "synthetic"}
+        for label, prec in (("fp32", g.GENGA_FP32), ("fp64", g.GENGA_FP64)):
+            p = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=prec)
+            s = g.DeviceSystem.from_disc(d, device=dev)
+            E0, *L0 = g.genga_energy(ctx, s, p)
+            L0 = np.array(L0)
+            dE, dLmag, dLvec = [], [], []
+            t_ms = 0.0
+            done = 0
+            while done < steps:
+                k = min(every, steps - done)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                g.genga_step(ctx, s, p, k)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                t_ms += e0.elapsed_time(e1)
+                done += k
+                E, *L = g.genga_energy(ctx, s, p)
+                L = np.array(L)
+                dE.append(E / E0 - 1.0)
+                dLmag.append(np.linalg.norm(L) / np.linalg.norm(L0) - 1.0)
+                dLvec.append(np.linalg.norm(L - L0) / np.linalg.norm(L0))
+            st = g.genga_get_status(ctx)
+            out[label] = {"dE_E_final": dE[-1], "dE_E_max_abs": float(np.max(np.abs(dE))),
+                          "dL_L_final": dLmag[-1], "dL_L_max_abs": float(np.max(np.abs(dLmag))),
+                          "dLvec_L_max": float(np.max(dLvec)), "ms_per_step": t_ms / steps, "status": st,
+                          "dE_E_series": [float(v) for v in dE]}
+        out["fp32_over_fp64_dL"] = out["fp32"]["dLvec_L_max"] / max(out["fp64"]["dLvec_L_max"], 1e-300)
+        out["fp32_over_fp64_dE"] = out["fp32"]["dE_E_max_abs"] / max(out["fp64"]["dE_E_max_abs"], 1e-300)
+        print(json.dumps(out), flush=True)
+        ctx.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.conservation:
+        return run_conservation(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_genga(args)
