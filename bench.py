@@ -118,6 +118,28 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(rank):
+    """Seed of the disc a rank steps: rank 0 runs the disc40k workload itself
+    (seed 3); every other rank an independent replica of the same recipe."""
+    return 3 + rank
+
+
+def max_over_ranks(x, dist=None, device=None):
+    """The slowest rank's time (the job ends when the last rank does)."""
+    if dist is None or not dist.is_initialized():
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(ws, pairs_per_step, steps, ms_max):
+    """Whole-job pair-interactions/s: every rank did `steps` steps of its own
+    replica, the job took the slowest rank's time."""
+    return ws * pairs_per_step * steps / (ms_max * 1e-3)
+
+
 def kernel_traffic(kernel_file="kick.cu"):
     """dram bytes per launch of the pass kernel from the committed ncu summary,
     or None when the kernel source has changed since it was captured."""
@@ -193,7 +215,7 @@ BATCH_WORKLOAD = ("batch256: 256 independent discs, N_d = floor(exp U(ln 1000, l
                   "(2.5 Earth masses, 0.5-4 au), FP32 kick, dt = 6 d")
 
 
-def run_batched(g, torch, dev, stream, flush, args, rank):
+def run_batched(g, torch, dev, stream, flush, args, rank, ws=1, dist=None):
     """genga_step_batched over 256 discs against genga_step on each disc in turn."""
     import numpy as np
     from paper_2309_08217_gb300 import discs
@@ -234,8 +256,10 @@ def run_batched(g, torch, dev, stream, flush, args, rank):
     if g.genga_get_status(ctxs) != g.GENGA_OK:
         raise RuntimeError("device status after the sequential steps")
     ctxs.close()
-    vb = pairs_step * K / (ms_b * 1e-3)
-    vs = pairs_step * K / (ms_s * 1e-3)
+    ms_b = max_over_ranks(ms_b, dist, dev)
+    ms_s = max_over_ranks(ms_s, dist, dev)
+    vb = weak_value(ws, pairs_step, K, ms_b)
+    vs = weak_value(ws, pairs_step, K, ms_s)
     return {"workload": BATCH_WORKLOAD, "discs": len(ds), "bodies": int(sizes.sum()), "pairs_per_step": pairs_step,
             "steps": K, "value": vb, "unit": UNIT, "ms_per_step": ms_b / K, "sequential_value": vs,
             "sequential_ms_per_step": ms_s / K, "speedup_vs_sequential": vb / vs}
@@ -262,7 +286,7 @@ def run_genga(args):
         dist.barrier()
     g.load()
 
-    d = discs.disc_powerlaw(40_000, 3 + rank)          # rank 0: the disc40k workload itself
+    d = discs.disc_powerlaw(40_000, replica_seed(rank))  # rank 0: the disc40k workload itself
     N = d.N
     pairs_step = 2 * N * (N - 1)
     ctx = g.Context(N, local)
@@ -328,17 +352,10 @@ def run_genga(args):
     tuner_ms = g.genga_tuning_times(ctx, N)
     ms64, pass64, nl64, _, _ = timed_steps(p64, max(1, args.fp64_steps), 3)
 
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    ms32_max = max_over_ranks(ms32)
-    ms64_max = max_over_ranks(ms64)
-    value = ws * pairs_step * args.steps / (ms32_max * 1e-3)
-    value64 = ws * pairs_step * max(1, args.fp64_steps) / (ms64_max * 1e-3)
+    ms32_max = max_over_ranks(ms32, dist, dev)
+    ms64_max = max_over_ranks(ms64, dist, dev)
+    value = weak_value(ws, pairs_step, args.steps, ms32_max)
+    value64 = weak_value(ws, pairs_step, max(1, args.fp64_steps), ms64_max)
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -359,8 +376,8 @@ def run_genga(args):
                 outh[c].copy_(s.tensors[c], non_blocking=True)
         e1.record(stream)
         barrier()
-        ms_e2e = max_over_ranks(e0.elapsed_time(e1))
-        e2e = {"value": ws * pairs_step * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        e2e = {"value": weak_value(ws, pairs_step, args.steps, ms_e2e), "unit": UNIT,
                "h2d_bytes_per_step": int(sum(h.numel() * 8 for h in host)),
                "d2h_bytes_per_step": int(sum(h.numel() * 8 for h in outh)),
                "ms_per_step": ms_e2e / args.steps}
@@ -389,7 +406,7 @@ def run_genga(args):
     # ---- batched: 256 independent discs in one call vs one call per disc
     batched = None
     if not args.no_batched:
-        batched = run_batched(g, torch, dev, stream, flush, args, rank)
+        batched = run_batched(g, torch, dev, stream, flush, args, rank, ws, dist)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
