@@ -52,6 +52,16 @@ genga_status genga_set_kernel_variant(genga_ctx *ctx, int32_t variant);
  * size has not been tuned yet), and the number of variants; HOST memory. */
 genga_status genga_get_kernel_variant(genga_ctx *ctx, int32_t N, int32_t *variant, int32_t *num_variants);
 
+/* Step graphs: genga_step and genga_step_batched capture a CUDA graph of 4
+ * steps (one rebuild of the spatial order per block) and replay it for the
+ * whole 4-step blocks of a call, once the order has just been rebuilt and the
+ * FP32 variant is tuned; the graph is captured again when the arrays, N, the
+ * batch layout, the parameters or the variant change.  enable = 0 launches
+ * every step's kernels one by one (same kernels, same order, bitwise the
+ * same results).  Enabled by default; profiling also uses the step-by-step
+ * path. */
+genga_status genga_set_step_graphs(genga_ctx *ctx, int32_t enable);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,7 @@ def load():
             "genga_profile_read": ([V, C.POINTER(C.c_double), C.POINTER(C.c_int32), I], I),
             "genga_measure_alu_peaks": ([I, C.POINTER(C.c_double), C.POINTER(C.c_double)], I),
             "genga_set_kernel_variant": ([V, I], I),
+            "genga_set_step_graphs": ([V, I], I),
             "genga_kick_noalloc": ([S, P, D, V, V], I),
             "genga_measure_fma2_peak": ([I, C.POINTER(C.c_double)], I),
             "genga_launch_count": ([V, C.POINTER(C.c_int64)], I),
@@ -282,6 +283,11 @@ def genga_tuning_times(ctx, N):
     arr = (C.c_float * n)()
     _check(load().genga_tuning_times(_ctx(ctx), int(N), arr, n), "genga_tuning_times")
     return list(arr)
+
+
+def genga_set_step_graphs(ctx, enable=True):
+    """Replay captured 4-step graphs in genga_step / genga_step_batched (default) or not."""
+    _check(load().genga_set_step_graphs(_ctx(ctx), int(bool(enable))), "genga_set_step_graphs")
 
 
 def genga_set_kernel_variant(ctx, variant=-1):

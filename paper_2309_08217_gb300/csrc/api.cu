@@ -316,6 +316,66 @@ cudaError_t run_kick_batched(genga_ctx *c, const genga_system &all, const int32_
     return launch_combine_batched(bb, bi, c->partial, c->perm, tau, acc, all.vx, all.vy, all.vz, c->status, s);
 }
 
+// ------------------------------------------------------------ step graphs
+// genga_step and genga_step_batched replay a CUDA graph of GENGA_REORDER_STEPS
+// steps -- one rebuild of the spatial order per block, so every block leaves
+// the context as it found it -- once the order has just been rebuilt and the
+// FP32 variant is tuned.  The graph is captured on an internal stream the
+// first time and whenever the key (arrays, N, batch layout, parameters,
+// variant) changes, and launched on the caller's stream.  Profiling
+// (genga_measure.h) keeps the step-by-step path, whose events are per pass.
+
+unsigned long long mix(unsigned long long h, unsigned long long v) {
+    h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    return h;
+}
+
+unsigned long long step_key(const genga_system &sys, const genga_params &p, int variant, unsigned long long layout) {
+    unsigned long long h = 1469598103934665603ull;
+    const double *arrs[7] = {sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, sys.m};
+    for (const double *a : arrs) h = mix(h, (unsigned long long)(uintptr_t)a);
+    h = mix(h, (unsigned long long)sys.N);
+    const unsigned char *pb = reinterpret_cast<const unsigned char *>(&p);
+    for (size_t k = 0; k < sizeof(p); k++) h = mix(h, pb[k]);
+    h = mix(h, (unsigned long long)(variant + 1));
+    return mix(h, layout);
+}
+
+bool graphs_usable(const genga_ctx *c) { return c->step_graphs && c->cap_stream && !(c->prof && c->prof->enabled); }
+
+// The graph for `key`, capturing `block(stream)` if needed; false (nothing
+// captured, state unchanged) when capture is not possible.
+template <class Block>
+bool step_graph(genga_ctx *c, unsigned long long key, Block block) {
+    if (c->step_exec && c->step_key == key) return true;
+    if (c->step_exec) {
+        cudaGraphExecDestroy(c->step_exec);
+        c->step_exec = nullptr;
+    }
+    const long long l0 = c->launches;
+    const int since0 = c->steps_since_order;
+    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    const cudaError_t eb = block(c->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &graph);
+    const long long per = c->launches - l0;
+    c->launches = l0;  // nothing ran yet
+    c->steps_since_order = since0;
+    cudaGraphExec_t exec = nullptr;
+    if (eb != cudaSuccess || ee != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();  // clear a capture error; the caller runs step by step
+        return false;
+    }
+    cudaGraphDestroy(graph);
+    c->step_exec = exec;
+    c->step_key = key;
+    c->step_launches = (int32_t)per;
+    return true;
+}
+
+bool fp32_tuned(const genga_ctx *c, int N) { return c->forced_variant >= 0 || c->f32_variant[size_bucket(N)] >= 0; }
+
 template <class T>
 cudaError_t alloc(T **p, size_t n) {
     return cudaMalloc((void **)p, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
@@ -343,6 +403,8 @@ void genga_destroy(genga_ctx *c) {
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
     profile_free(c);
+    if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     void *bufs[] = {c->pk_hi,       c->pk_t,        c->pk_d,        c->pk_lo,       c->pk64,        c->scr,      c->gbox_lo,    c->gbox_hi,
                     c->perm,        c->ord_keys[0], c->ord_keys[1], c->ord_vals[0], c->ord_vals[1], c->ord_hist,
                     c->ord_rbits,   c->a_osc,       c->rc_eq1,      c->partial,  c->mom,        c->enc,
@@ -369,6 +431,7 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     for (int b = 0; b < 32; b++) c->f32_variant[b] = -1;
     c->forced_variant = -1;
     c->ordered_N = -1;
+    c->step_graphs = 1;
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
         delete c;
@@ -386,6 +449,7 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     c->enc_cap = (int32_t)ecap;
     c->energy_blocks = np / 256;
     cudaError_t e = init_pass_kernels();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = alloc(&c->pk_hi, np);
     if (e == cudaSuccess) e = alloc(&c->pk_lo, np);
     if (e == cudaSuccess) e = alloc(&c->pk_t, 4 * (size_t)np);
@@ -495,14 +559,43 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
     // rounding), so genga_step rebuilds it every GENGA_REORDER_STEPS drifts,
     // counted across calls, and whenever N changes.  The drift leaves P of the
     // new state in c->mom, which the closing kick reuses.
-    for (int k = 0; k < nsteps; k++) {
-        if (run_kick(c, s2, *p, h, nullptr, false, s) != cudaSuccess) return GENGA_ERR_CUDA;
-        if (launch_drift(s2, *p, p->dt, c, s) != cudaSuccess) return GENGA_ERR_CUDA;
+    auto one_step = [&](cudaStream_t q) -> cudaError_t {
+        cudaError_t e = run_kick(c, s2, *p, h, nullptr, false, q);
+        if (e == cudaSuccess) e = launch_drift(s2, *p, p->dt, c, q);
         c->launches += 4;
         c->steps_since_order++;
         const bool reorder = c->steps_since_order >= GENGA_REORDER_STEPS;
-        if (run_kick(c, s2, *p, h, nullptr, reorder, s, true) != cudaSuccess) return GENGA_ERR_CUDA;
+        if (e == cudaSuccess) e = run_kick(c, s2, *p, h, nullptr, reorder, q, true);
+        return e;
+    };
+    int k = 0;
+    auto aligned = [&]() {
+        return c->steps_since_order == 0 && c->ordered_N == s2.N && (p->precision != GENGA_FP32 || fp32_tuned(c, s2.N));
+    };
+    for (; k < nsteps && !(aligned() && nsteps - k >= GENGA_REORDER_STEPS); k++)
+        if (one_step(s) != cudaSuccess) return GENGA_ERR_CUDA;
+    if (k < nsteps && graphs_usable(c)) {
+        const int variant = p->precision == GENGA_FP32 ? (c->forced_variant >= 0 ? c->forced_variant
+                                                                                 : c->f32_variant[size_bucket(s2.N)])
+                                                       : -1;
+        const unsigned long long key = step_key(s2, *p, variant, 0);
+        const bool ok = step_graph(c, key, [&](cudaStream_t q) {
+            for (int b = 0; b < GENGA_REORDER_STEPS; b++) {
+                const cudaError_t e = one_step(q);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        });
+        if (ok) {
+            for (; nsteps - k >= GENGA_REORDER_STEPS; k += GENGA_REORDER_STEPS) {
+                if (cudaGraphLaunch(c->step_exec, s) != cudaSuccess) return GENGA_ERR_CUDA;
+                c->launches += c->step_launches;
+            }
+            c->enc_sorted = false;
+        }
     }
+    for (; k < nsteps; k++)
+        if (one_step(s) != cudaSuccess) return GENGA_ERR_CUDA;
     return GENGA_OK;
 }
 
@@ -531,16 +624,47 @@ genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *
     if (all->N == 0 || nsteps == 0) return GENGA_OK;
     genga_system a2 = *all;
     const BatchBodies bb = batch_bodies(offsets, D);
+    const unsigned long long layout = offsets_hash(offsets, D);
     const double h = 0.5 * p->dt;
-    for (int k = 0; k < nsteps; k++) {
-        cudaError_t e = run_kick_batched(c, a2, offsets, D, *p, h, nullptr, false, false, s);
-        if (e == cudaSuccess) e = launch_drift_batched(a2, bb, *p, p->dt, c, s);
+    auto one_step = [&](cudaStream_t q) -> cudaError_t {
+        cudaError_t e = run_kick_batched(c, a2, offsets, D, *p, h, nullptr, false, false, q);
+        if (e == cudaSuccess) e = launch_drift_batched(a2, bb, *p, p->dt, c, q);
         c->launches += 4;
         c->steps_since_order++;
         const bool reorder = c->steps_since_order >= GENGA_REORDER_STEPS;
-        if (e == cudaSuccess) e = run_kick_batched(c, a2, offsets, D, *p, h, nullptr, reorder, true, s);
-        if (e == cudaErrorInvalidValue) return GENGA_ERR_INVALID_ARG;
-        if (e != cudaSuccess) return GENGA_ERR_CUDA;
+        if (e == cudaSuccess) e = run_kick_batched(c, a2, offsets, D, *p, h, nullptr, reorder, true, q);
+        return e;
+    };
+    auto status_of = [](cudaError_t e) {
+        return e == cudaErrorInvalidValue ? GENGA_ERR_INVALID_ARG : GENGA_ERR_CUDA;
+    };
+    auto aligned = [&]() { return c->steps_since_order == 0 && c->ordered_N == -2 && c->ordered_key == layout; };
+    int k = 0;
+    for (; k < nsteps && !(aligned() && nsteps - k >= GENGA_REORDER_STEPS); k++) {
+        const cudaError_t e = one_step(s);
+        if (e != cudaSuccess) return status_of(e);
+    }
+    if (k < nsteps && graphs_usable(c)) {
+        const int variant = c->forced_variant >= 0 ? c->forced_variant : 0;
+        const unsigned long long key = step_key(a2, *p, variant, mix(layout, 0xba7c4ull));
+        const bool ok = step_graph(c, key, [&](cudaStream_t q) {
+            for (int b = 0; b < GENGA_REORDER_STEPS; b++) {
+                const cudaError_t e = one_step(q);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        });
+        if (ok) {
+            for (; nsteps - k >= GENGA_REORDER_STEPS; k += GENGA_REORDER_STEPS) {
+                if (cudaGraphLaunch(c->step_exec, s) != cudaSuccess) return GENGA_ERR_CUDA;
+                c->launches += c->step_launches;
+            }
+            c->enc_sorted = false;
+        }
+    }
+    for (; k < nsteps; k++) {
+        const cudaError_t e = one_step(s);
+        if (e != cudaSuccess) return status_of(e);
     }
     return GENGA_OK;
 }

@@ -81,6 +81,12 @@ struct genga_ctx {
     int32_t steps_since_order; // genga_step: drifts since the spatial order was built
     int32_t ordered_N;         // N of the system the spatial order was built for (-1: none, -2: a batch)
     unsigned long long ordered_key;  // layout hash of the batch the order was built for
+    // captured graph of GENGA_REORDER_STEPS steps (genga_step / genga_step_batched)
+    cudaStream_t cap_stream;   // internal stream the graphs are captured on
+    cudaGraphExec_t step_exec; // NULL until captured
+    unsigned long long step_key;  // arrays, sizes, layout, parameters and variant it was captured for
+    int32_t step_launches;     // kernels one replay launches
+    int32_t step_graphs;       // 1: use step graphs (default), 0: always launch step by step
     int64_t launches;          // kernels this context has launched (measurement hook)
     double *Pd;                // [3 * GENGA_MAX_DISCS] momentum of each system (batched mode)
     double *Pd_part;           // [3 * GENGA_MAX_DISCS] scratch

@@ -197,6 +197,12 @@ genga_status genga_set_kernel_variant(genga_ctx *c, int32_t variant) {
     return GENGA_OK;
 }
 
+genga_status genga_set_step_graphs(genga_ctx *c, int32_t enable) {
+    if (!c) return GENGA_ERR_INVALID_ARG;
+    c->step_graphs = enable ? 1 : 0;
+    return GENGA_OK;
+}
+
 genga_status genga_get_kernel_variant(genga_ctx *c, int32_t N, int32_t *variant, int32_t *num_variants) {
     if (!c || !variant || !num_variants || N < 0) return GENGA_ERR_INVALID_ARG;
     int b = 0;
