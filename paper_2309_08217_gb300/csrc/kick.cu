@@ -969,7 +969,7 @@ size_t smem_fp64() { return (size_t)F64_STAGES * F64_TILE * sizeof(double4_32a) 
 // CTA come last; each earlier tier has chunks as long as the work of all the
 // tiers after it per CTA (so an item of that tier started late still ends
 // while the later, shorter items keep the other CTAs busy) and about as much
-// work as they have together; lengths stop growing at half a CTA's share of
+// work as they have together; lengths stop growing at a quarter of a CTA's share of
 // the pass, and the first tier takes what is left (its first chunk made
 // shorter to fit).  split = partial rows per body; grid = resident CTAs.
 // FP64: `split` contiguous j-slices per i-block, one CTA each, sized to one
@@ -997,7 +997,7 @@ void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_c
     const int ntiles = npad / F32_TILE, ib = v.cw * 32 * v.bpt, iblocks = (npad + ib - 1) / ib;
     const int ctas = v.minb * sm_count;
     const double r = (double)iblocks / ctas;  // single-tile items per CTA of one chunk per i-block
-    const int lmax = std::max(1, (int)(0.5 * ntiles * r));
+    const int lmax = std::max(1, (int)(0.25 * ntiles * r));
     int len[GENGA_MAX_TIERS], cnt[GENGA_MAX_TIERS], nt = 0, rows = 0;
     int R = ntiles;
     double drain = 0.0;  // work per CTA of the tiers already placed (after this one in time)
