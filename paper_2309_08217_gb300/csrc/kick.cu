@@ -320,7 +320,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
     float4 *s_lo = s_hi + STAGES * HF4;
     float4 *s_glo = s_lo + STAGES * TILE;  // [STAGES][NG] group boxes of each staged tile
     float4 *s_ghi = s_glo + STAGES * NG;
-    uint64_t *full = reinterpret_cast<uint64_t *>(s_ghi + STAGES * NG);
+    float4 *s_tb = s_ghi + STAGES * NG;  // [STAGES][2] box of each staged tile (union of its groups)
+    uint64_t *full = reinterpret_cast<uint64_t *>(s_tb + 2 * STAGES);
     uint64_t *empty = full + STAGES;
     StageHdr *hdr = reinterpret_cast<StageHdr *>(empty + STAGES);
     __shared__ DF s_acc[3 * BPT * NC];      // [c][k][thread] double-float per-body sums
@@ -367,6 +368,9 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                 const unsigned u = n / STAGES;
                 if (u > 0 && !mbar_wait_bounded(&empty[slot], (u - 1) & 1, a.status)) return;
                 hdr[slot] = StageHdr{q, t, (ur == u0 ? 1 : 0) | (ur == u1 - 1 ? 2 : 0), 0};
+                const Box tbx = group_box<NG>(a.gbox_lo, a.gbox_hi, t * NG);
+                s_tb[2 * slot] = tbx.lo;
+                s_tb[2 * slot + 1] = tbx.hi;
                 fence_proxy_async_smem();
                 constexpr uint32_t GB = NG * sizeof(float4);
                 mbar_arrive_expect_tx(&full[slot], TBH + TBL + 2 * GB);
@@ -433,12 +437,15 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
 #pragma unroll
         for (int k = 0; k < BPT; k++) ax[k] = ay[k] = az[k] = 0.f;
         const float4 *th = s_hi + slot * HF4;
+        // a tile FAR as a whole needs no per-group test (the tile box holds
+        // every group box, so its gap is smaller and its bound larger)
+        const bool tile_far = far_pair_of_boxes(wbox, Box{s_tb[2 * slot], s_tb[2 * slot + 1]}, true);
         for (int g = 0; g < NG; g++) {
             const Box gb = {s_glo[slot * NG + g], s_ghi[slot * NG + g]};
             const float *tx = reinterpret_cast<const float *>(th) + g * 64, *ty = tx + TILE, *tz = tx + 2 * TILE,
                         *tw = tx + 3 * TILE;     // j-packed layout
             const float4 *td = th + g * 128;  // i-packed layout: two float4 per j
-            if (far_pair_of_boxes(wbox, gb, true)) {
+            if (tile_far || far_pair_of_boxes(wbox, gb, true)) {
                 // every pair: K = 1, FP32-rounded positions accurate enough
                 if constexpr (IPACK) {
 #pragma unroll(UNR)
@@ -956,7 +963,7 @@ constexpr int F64_BPT = 2, F64_TILE = 128, F64_STAGES = 3;
 
 size_t smem_fp32(bool ipack, int stages) {
     const size_t hf4 = ipack ? 2 * F32_TILE : F32_TILE;
-    return (size_t)stages * (hf4 + F32_TILE) * sizeof(float4) + (size_t)stages * (F32_TILE / 64) * 2 * sizeof(float4) +
+    return (size_t)stages * (hf4 + F32_TILE) * sizeof(float4) + (size_t)stages * (F32_TILE / 64 + 1) * 2 * sizeof(float4) +
            2 * stages * sizeof(uint64_t) + stages * sizeof(StageHdr);
 }
 size_t smem_fp64() { return (size_t)F64_STAGES * F64_TILE * sizeof(double4_32a) + F64_STAGES * sizeof(uint64_t); }
