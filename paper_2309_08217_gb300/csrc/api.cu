@@ -152,7 +152,7 @@ cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &
     if (e != cudaSuccess) return e;
     c->launches += momentum_valid ? 0 : 1;
     if (reorder || c->ordered_N != sys.N) {
-        if ((e = launch_order(sys, c, s)) != cudaSuccess) return e;
+        if ((e = launch_order(sys, p.Mstar, c, s)) != cudaSuccess) return e;
         c->ordered_N = sys.N;
         c->steps_since_order = 0;
         c->launches += 11;  // extent, keys, 3 x (histogram, scan, scatter)
@@ -293,7 +293,7 @@ cudaError_t run_kick_batched(genga_ctx *c, const genga_system &all, const int32_
     if (e != cudaSuccess) return e;
     c->launches += momentum_valid ? 0 : 1;
     if (reorder || c->ordered_N != -2 || c->ordered_key != key) {
-        if ((e = launch_order_batched(all, bb, c, s)) != cudaSuccess) return e;
+        if ((e = launch_order_batched(all, bb, p.Mstar, c, s)) != cudaSuccess) return e;
         c->ordered_N = -2;  // the order belongs to a batch
         c->ordered_key = key;
         c->steps_since_order = 0;

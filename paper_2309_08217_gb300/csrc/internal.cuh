@@ -25,6 +25,9 @@
 
 // genga_step rebuilds the spatial order of the bodies every this many steps.
 #define GENGA_REORDER_STEPS 4
+// Bodies heavier than this fraction of the central mass are ordered after the
+// others (their large r_crit bound would make a group of planetesimals NEAR).
+#define GENGA_HEAVY_MASS 1e-7
 
 // Bodies per tile of the tile-blocked FP32 copy (pk_t).
 #define GENGA_TILE_T 256
@@ -160,7 +163,7 @@ struct PassArgs {               // one long-range pass
 cudaError_t launch_momentum(const double *vx, const double *vy, const double *vz, const double *m,
                             int N, double *P, int32_t *zero_me, cudaStream_t s);
 cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ctx *c, cudaStream_t s);
-cudaError_t launch_order(const genga_system &sys, genga_ctx *c, cudaStream_t s);
+cudaError_t launch_order(const genga_system &sys, double Mstar, genga_ctx *c, cudaStream_t s);
 size_t order_hist_entries(int nmax);
 cudaError_t init_pass_kernels();
 cudaError_t launch_pass(const PassArgs &a, int precision, int variant, int grid, cudaStream_t s);
@@ -177,7 +180,8 @@ cudaError_t launch_energy(const genga_system &sys, const genga_params &p, genga_
 // batched mode (batch.cu helpers live next to their single-system versions)
 cudaError_t launch_momentum_batched(const genga_system &all, const BatchBodies &bb, double *Pd, int32_t *zero_me,
                                     cudaStream_t s);
-cudaError_t launch_order_batched(const genga_system &all, const BatchBodies &bb, genga_ctx *c, cudaStream_t s);
+cudaError_t launch_order_batched(const genga_system &all, const BatchBodies &bb, double Mstar, genga_ctx *c,
+                                 cudaStream_t s);
 cudaError_t launch_prep_batched(const genga_system &all, const BatchBodies &bb, const genga_params &p, genga_ctx *c,
                                 cudaStream_t s);
 cudaError_t launch_pass_batched(const PassArgs &a, const BatchBodies &bb, const BatchItems &bi, int variant, int grid,

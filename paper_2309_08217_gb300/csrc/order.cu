@@ -1,15 +1,19 @@
 // order.cu -- spatial order of the bodies for the long-range pass.
 //
-// Bodies are sorted along a 3-D Morton curve (8 bits per axis over the cube
-// [-R, R]^3, R = the largest |coordinate|), so that a warp's 128 i-bodies and
-// a 256-body j-tile each cover a compact region; the pass kernels then test
+// Bodies are sorted along a 3-D Morton curve (7 bits per axis over the cube
+// [-R, R]^3, R = the largest |coordinate|), so that a warp's i-bodies and a
+// 256-body j-tile each cover a compact region; the pass kernels then test
 // (warp, tile) bounding boxes and run most tiles without per-pair screening.
-// The order only changes which pairs share a tile, never which pairs are
-// summed, so it affects speed, not the definition of the result.
+// Massive bodies (m > GENGA_HEAVY_MASS * M*: embryos, giant planets) come
+// after all others: their r_crit bound is large, and inside a group of
+// planetesimals one of them would make every group NEAR for its warp.  The
+// order only changes which pairs share a tile, never which pairs are summed,
+// so it affects speed, not the definition of the result.
 //
-// The sort is a stable least-significant-digit radix sort of the 24-bit keys
-// with 8-bit digits (three passes of histogram / scan / scatter; four in
-// batched mode, where the system index fills the top byte).  Stable
+// The sort is a stable least-significant-digit radix sort of the 22-bit keys
+// (heavy flag above the 21 Morton bits) with 8-bit digits (three passes of
+// histogram / scan / scatter; four in batched mode, where the system index
+// fills the top byte).  Stable
 // ranks inside a CTA come from warp match masks and per-warp digit counts, so
 // the permutation is the same on every run.
 #include "internal.cuh"
@@ -45,36 +49,41 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 8 bits -> every th
     return v;
 }
 
-__device__ __forceinline__ uint32_t quant8(double c, float inv) {
-    float f = ((float)c * inv + 1.0f) * 128.0f;
-    f = fminf(fmaxf(f, 0.0f), 255.0f);
+__device__ __forceinline__ uint32_t quant7(double c, float inv) {
+    float f = ((float)c * inv + 1.0f) * 64.0f;
+    f = fminf(fmaxf(f, 0.0f), 127.0f);
     return (uint32_t)f;
 }
 
+// Heavy flag and 21-bit Morton code of one body.
+__device__ __forceinline__ uint32_t body_key(double x, double y, double z, double m, double heavy_mass, float inv) {
+    const uint32_t heavy = m > heavy_mass ? 1u : 0u;
+    return (heavy << 21) | spread3(quant7(x, inv)) | (spread3(quant7(y, inv)) << 1) | (spread3(quant7(z, inv)) << 2);
+}
+
 __global__ void keys_kernel(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
-                            int N, const unsigned *__restrict__ rbits, uint32_t *__restrict__ keys,
-                            uint32_t *__restrict__ vals) {
+                            const double *__restrict__ m, int N, double heavy_mass, const unsigned *__restrict__ rbits,
+                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float R = fmaxf(__uint_as_float(*rbits), 1e-30f) * 1.0001f;
     const float inv = 1.0f / R;
-    keys[i] = spread3(quant8(x[i], inv)) | (spread3(quant8(y[i], inv)) << 1) | (spread3(quant8(z[i], inv)) << 2);
+    keys[i] = body_key(x[i], y[i], z[i], m[i], heavy_mass, inv);
     vals[i] = (uint32_t)i;
 }
 
 // Batched: the system index d takes the top 8 bits, so one sort orders the
 // bodies by system first and along the Morton curve inside each system.
 __global__ void keys_batched_kernel(const double *__restrict__ x, const double *__restrict__ y,
-                                    const double *__restrict__ z, const unsigned *__restrict__ rbits,
-                                    uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                                    const __grid_constant__ BatchBodies bb) {
+                                    const double *__restrict__ z, const double *__restrict__ m, double heavy_mass,
+                                    const unsigned *__restrict__ rbits, uint32_t *__restrict__ keys,
+                                    uint32_t *__restrict__ vals, const __grid_constant__ BatchBodies bb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= bb.N_total) return;
     const int d = find_segment(bb.off, bb.D, i);
     const float R = fmaxf(__uint_as_float(*rbits), 1e-30f) * 1.0001f;
     const float inv = 1.0f / R;
-    keys[i] = ((uint32_t)d << 24) | spread3(quant8(x[i], inv)) | (spread3(quant8(y[i], inv)) << 1) |
-              (spread3(quant8(z[i], inv)) << 2);
+    keys[i] = ((uint32_t)d << 24) | body_key(x[i], y[i], z[i], m[i], heavy_mass, inv);
     vals[i] = (uint32_t)i;
 }
 
@@ -204,27 +213,28 @@ void radix_to_perm(genga_ctx *c, int N, int passes, cudaStream_t s) {
 }
 
 // perm[k] = index of the body at position k of the Morton order (k < N).
-cudaError_t launch_order(const genga_system &sys, genga_ctx *c, cudaStream_t s) {
+cudaError_t launch_order(const genga_system &sys, double Mstar, genga_ctx *c, cudaStream_t s) {
     const int N = sys.N;
     if (N <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(c->ord_rbits, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     extent_kernel<<<64, 256, 0, s>>>(sys.x, sys.y, sys.z, N, c->ord_rbits);
-    keys_kernel<<<(N + 255) / 256, 256, 0, s>>>(sys.x, sys.y, sys.z, N, c->ord_rbits, c->ord_keys[0],
-                                                c->ord_vals[0]);
+    keys_kernel<<<(N + 255) / 256, 256, 0, s>>>(sys.x, sys.y, sys.z, sys.m, N, GENGA_HEAVY_MASS * Mstar,
+                                                c->ord_rbits, c->ord_keys[0], c->ord_vals[0]);
     radix_to_perm(c, N, 3, s);
     return cudaGetLastError();
 }
 
-// Batched: 24-bit Morton keys below the 8-bit system index, four passes.
-cudaError_t launch_order_batched(const genga_system &all, const BatchBodies &bb, genga_ctx *c, cudaStream_t s) {
+// Batched: the 22-bit keys below the 8-bit system index, four passes.
+cudaError_t launch_order_batched(const genga_system &all, const BatchBodies &bb, double Mstar, genga_ctx *c,
+                                 cudaStream_t s) {
     const int N = bb.N_total;
     if (N <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(c->ord_rbits, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     extent_kernel<<<64, 256, 0, s>>>(all.x, all.y, all.z, N, c->ord_rbits);
-    keys_batched_kernel<<<(N + 255) / 256, 256, 0, s>>>(all.x, all.y, all.z, c->ord_rbits, c->ord_keys[0],
-                                                        c->ord_vals[0], bb);
+    keys_batched_kernel<<<(N + 255) / 256, 256, 0, s>>>(all.x, all.y, all.z, all.m, GENGA_HEAVY_MASS * Mstar,
+                                                        c->ord_rbits, c->ord_keys[0], c->ord_vals[0], bb);
     radix_to_perm(c, N, 4, s);
     return cudaGetLastError();
 }
