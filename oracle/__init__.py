@@ -64,15 +64,15 @@ def _load():
             "oracle_momentum": ([i, _dp, _dp, _dp, _dp, _dp], None),
             "oracle_rcrit": ([i] + [_dp] * 7 + [d] * 5 + [_dp, _dp], None),
             "oracle_pair_rcrit": ([i, d, d, d, d, d, d, d, d], d),
-            "oracle_kick_acc": ([i] + [_dp] * 6 + [d, d, d, i, i, i, _i64p] + [_dp] * 4, None),
-            "oracle_kick": ([i] + [_dp] * 7 + [d] * 5 + [i, i, d] + [_dp] * 3, None),
-            "oracle_encounters": ([i] + [_dp] * 6 + [d, d, i, _i32p, C.c_int64, d, _i32p,
+            "oracle_kick_acc": ([i] + [_dp] * 6 + [d, d, d, i, i, i, i, _i64p] + [_dp] * 4, None),
+            "oracle_kick": ([i] + [_dp] * 7 + [d] * 5 + [i, i, i, d] + [_dp] * 3, None),
+            "oracle_encounters": ([i] + [_dp] * 6 + [d, d, i, i, _i32p, C.c_int64, d, _i32p,
                                                     C.c_int64, _i64p], C.c_int64),
             "oracle_kepler": ([d, _dp, d, i], i),
             "oracle_hc_drift": ([i] + [_dp] * 7 + [d, d], None),
             "oracle_drift": ([i] + [_dp] * 7 + [d, d, d, i], i),
-            "oracle_step": ([i] + [_dp] * 7 + [d] * 5 + [i, i, i, i], i),
-            "oracle_energy": ([i] + [_dp] * 7 + [d, d, _dp], None),
+            "oracle_step": ([i] + [_dp] * 7 + [d] * 5 + [i, i, i, i, i], i),
+            "oracle_energy": ([i] + [_dp] * 7 + [d, d, i, _dp], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -128,31 +128,32 @@ def pair_rcrit(mode, mi, mj, ai, aj, rci, rcj, n1, Mstar):
     return float(_load().oracle_pair_rcrit(int(mode), mi, mj, ai, aj, rci, rcj, n1, Mstar))
 
 
-def kick_acc(x, y, z, m, a, rc, G, Mstar, n1=3.0, mode=1, form=0, idx=None, with_abs=False):
-    """Sect. 1 long-range sum a_i = sum_{j!=i} G m_j K (x_j-x_i)/r^3 for i in idx."""
+def kick_acc(x, y, z, m, a, rc, G, Mstar, n1=3.0, mode=1, form=0, idx=None, with_abs=False, n_big=-1):
+    """Sect. 1 long-range sum a_i = sum_{j!=i} G m_j K (x_j-x_i)/r^3 for i in idx
+    (n_big >= 0: test-particle mode 2, no force between bodies >= n_big)."""
     arrs = [_f64(v) for v in (x, y, z, m, a, rc)]
     N = len(arrs[3])
     idx = np.arange(N, dtype=np.int64) if idx is None else np.ascontiguousarray(idx, np.int64)
     n = len(idx)
     ax, ay, az, ab = np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n)
-    _load().oracle_kick_acc(N, *map(_p, arrs), G, Mstar, n1, int(mode), int(form), n,
+    _load().oracle_kick_acc(N, *map(_p, arrs), G, Mstar, n1, int(mode), int(form), int(n_big), n,
                             idx.ctypes.data_as(_i64p), _p(ax), _p(ay), _p(az),
                             _p(ab) if with_abs else None)
     acc = np.stack([ax, ay, az])
     return (acc, ab) if with_abs else acc
 
 
-def kick(disc_arrays, G, Mstar, dt, n1, n2, mode, form, tau):
+def kick(disc_arrays, G, Mstar, dt, n1, n2, mode, form, tau, n_big=-1):
     """r_crit from the current state, then v += a tau (in place); returns acc."""
     x, y, z, vx, vy, vz, m = disc_arrays
     N = len(m)
     ax, ay, az = np.zeros(N), np.zeros(N), np.zeros(N)
     _load().oracle_kick(N, *map(_p, (x, y, z, vx, vy, vz, m)), G, Mstar, dt, n1, n2,
-                        int(mode), int(form), tau, _p(ax), _p(ay), _p(az))
+                        int(mode), int(form), int(n_big), tau, _p(ax), _p(ay), _p(az))
     return np.stack([ax, ay, az])
 
 
-def encounters(x, y, z, m, a, rc, n1, Mstar, mode=1, band=1e-9, cap=None):
+def encounters(x, y, z, m, a, rc, n1, Mstar, mode=1, band=1e-9, cap=None, n_big=-1):
     """Pairs i<j with r_ij < r_crit,ij (lexicographic) and the +-band pairs."""
     arrs = [_f64(v) for v in (x, y, z, m, a, rc)]
     N = len(arrs[3])
@@ -162,12 +163,12 @@ def encounters(x, y, z, m, a, rc, n1, Mstar, mode=1, band=1e-9, cap=None):
     pairs = np.zeros(2 * cap, np.int32)
     bpairs = np.zeros(2 * bcap, np.int32)
     bcount = np.zeros(1, np.int64)
-    cnt = lib.oracle_encounters(N, *map(_p, arrs), n1, Mstar, int(mode),
+    cnt = lib.oracle_encounters(N, *map(_p, arrs), n1, Mstar, int(mode), int(n_big),
                                 pairs.ctypes.data_as(_i32p), cap, band,
                                 bpairs.ctypes.data_as(_i32p), bcap, bcount.ctypes.data_as(_i64p))
     if cnt > cap or bcount[0] > bcap:
         return encounters(x, y, z, m, a, rc, n1, Mstar, mode, band,
-                          cap=int(max(cnt, bcount[0], cap) * 2))
+                          cap=int(max(cnt, bcount[0], cap) * 2), n_big=n_big)
     return (pairs[: 2 * cnt].reshape(-1, 2).copy(),
             bpairs[: 2 * int(bcount[0])].reshape(-1, 2).copy())
 
@@ -191,18 +192,18 @@ def drift(arrs, G, Mstar, dt, max_iter=50):
                                     int(max_iter)))
 
 
-def step(arrs, G, Mstar, dt, n1, n2, mode, form, nsteps, max_iter=50):
+def step(arrs, G, Mstar, dt, n1, n2, mode, form, nsteps, max_iter=50, n_big=-1):
     """nsteps of kick(dt/2) drift(dt) kick(dt/2), in place."""
     x, y, z, vx, vy, vz, m = arrs
     return int(_load().oracle_step(len(m), *map(_p, (x, y, z, vx, vy, vz, m)), G, Mstar, dt,
-                                   n1, n2, int(mode), int(form), int(max_iter), int(nsteps)))
+                                   n1, n2, int(mode), int(form), int(n_big), int(max_iter), int(nsteps)))
 
 
-def energy(arrs, G, Mstar):
+def energy(arrs, G, Mstar, n_big=-1):
     """(E, Lx, Ly, Lz) of the democratic-heliocentric Hamiltonian."""
     x, y, z, vx, vy, vz, m = [_f64(v) for v in arrs]
     out = np.zeros(4)
-    _load().oracle_energy(len(m), *map(_p, (x, y, z, vx, vy, vz, m)), G, Mstar, _p(out))
+    _load().oracle_energy(len(m), *map(_p, (x, y, z, vx, vy, vz, m)), G, Mstar, int(n_big), _p(out))
     return out
 
 

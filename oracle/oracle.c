@@ -143,13 +143,25 @@ double oracle_pair_rcrit(int mode, double mi, double mj, double ai, double aj,
 /* ---------------------------------------------- long-range kick (Sect. 1) -- */
 
 /*
+ * Test-particle mode 2 (Sect. 3, the giant-planet runs): with n_big >= 0,
+ * bodies n_big..N-1 are test particles that feel the bodies 0..n_big-1 but
+ * not each other, while those feel everything; a pair of two test particles
+ * has no force, no encounter and no potential energy.  n_big < 0: every pair
+ * interacts.
+ */
+static int tp_pair(int n_big, int i, int j)
+{
+    return n_big >= 0 && i >= n_big && j >= n_big;
+}
+
+/*
  * Accelerations of the bodies listed in idx[0..nidx): the direct sum over
  * all j != i of G m_j K(y_ij) (x_j - x_i)/r_ij^3.  Optional absout[k] gets
  * sum_j |a_ij| (the conditioning of body idx[k]'s sum).
  */
 void oracle_kick_acc(int N, const double *x, const double *y, const double *z,
                      const double *m, const double *a, const double *rc,
-                     double G, double Mstar, double n1, int mode, int form,
+                     double G, double Mstar, double n1, int mode, int form, int n_big,
                      int nidx, const int64_t *idx,
                      double *ax, double *ay, double *az, double *absout)
 {
@@ -158,7 +170,7 @@ void oracle_kick_acc(int N, const double *x, const double *y, const double *z,
         int i = (int)idx[k];
         nsum sx = {0, 0}, sy = {0, 0}, sz = {0, 0}, sa = {0, 0};
         for (int j = 0; j < N; j++) {
-            if (j == i) continue;
+            if (j == i || tp_pair(n_big, i, j)) continue;
             double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
             double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 == 0.0) continue;          /* coincident bodies: no direction, no force */
@@ -182,14 +194,14 @@ void oracle_kick_acc(int N, const double *x, const double *y, const double *z,
 void oracle_kick(int N, const double *x, const double *y, const double *z,
                  double *vx, double *vy, double *vz, const double *m,
                  double G, double Mstar, double dt, double n1, double n2, int mode, int form,
-                 double tau, double *ax, double *ay, double *az)
+                 int n_big, double tau, double *ax, double *ay, double *az)
 {
     double *a = (double *)malloc(sizeof(double) * (N > 0 ? N : 1));
     double *rc = (double *)malloc(sizeof(double) * (N > 0 ? N : 1));
     int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (N > 0 ? N : 1));
     oracle_rcrit(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, a, rc);
     for (int i = 0; i < N; i++) idx[i] = i;
-    oracle_kick_acc(N, x, y, z, m, a, rc, G, Mstar, n1, mode, form, N, idx, ax, ay, az, NULL);
+    oracle_kick_acc(N, x, y, z, m, a, rc, G, Mstar, n1, mode, form, n_big, N, idx, ax, ay, az, NULL);
     for (int i = 0; i < N; i++) {
         vx[i] += ax[i] * tau;
         vy[i] += ay[i] * tau;
@@ -208,13 +220,14 @@ void oracle_kick(int N, const double *x, const double *y, const double *z,
  */
 int64_t oracle_encounters(int N, const double *x, const double *y, const double *z,
                           const double *m, const double *a, const double *rc,
-                          double n1, double Mstar, int mode,
+                          double n1, double Mstar, int mode, int n_big,
                           int32_t *pairs, int64_t cap, double band,
                           int32_t *band_pairs, int64_t band_cap, int64_t *band_count)
 {
     int64_t cnt = 0, bcnt = 0;
     for (int i = 0; i < N; i++) {
         for (int j = i + 1; j < N; j++) {
+            if (tp_pair(n_big, i, j)) continue;
             double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
             double r = sqrt(dx * dx + dy * dy + dz * dz);
             double rcij = oracle_pair_rcrit(mode, m[i], m[j], a[i], a[j], rc[i], rc[j], n1, Mstar);
@@ -340,7 +353,7 @@ int oracle_drift(int N, double *x, double *y, double *z, double *vx, double *vy,
  * Returns the total count of non-converged Kepler solves. */
 int oracle_step(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
                 const double *m, double G, double Mstar, double dt, double n1, double n2,
-                int mode, int form, int max_iter, int nsteps)
+                int mode, int form, int n_big, int max_iter, int nsteps)
 {
     int bad = 0;
     size_t n = (size_t)(N > 0 ? N : 1);
@@ -348,9 +361,9 @@ int oracle_step(int N, double *x, double *y, double *z, double *vx, double *vy, 
     double *ay = (double *)malloc(sizeof(double) * n);
     double *az = (double *)malloc(sizeof(double) * n);
     for (int s = 0; s < nsteps; s++) {
-        oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, 0.5 * dt, ax, ay, az);
+        oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, n_big, 0.5 * dt, ax, ay, az);
         bad += oracle_drift(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, max_iter);
-        oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, 0.5 * dt, ax, ay, az);
+        oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, n_big, 0.5 * dt, ax, ay, az);
     }
     free(ax); free(ay); free(az);
     return bad;
@@ -360,12 +373,13 @@ int oracle_step(int N, double *x, double *y, double *z, double *vx, double *vy, 
 
 /*
  * out[0] = E = sum m v^2/2 + |P|^2/(2 M*) - sum G M* m_i / r_i
- *              - sum_{i<j} G m_i m_j / r_ij     (democratic-heliocentric H)
+ *              - sum_{i<j} G m_i m_j / r_ij     (democratic-heliocentric H;
+ *                test-particle pairs excluded when n_big >= 0)
  * out[1..3] = L = sum m_i x_i x v_i.
  */
 void oracle_energy(int N, const double *x, const double *y, const double *z,
                    const double *vx, const double *vy, const double *vz, const double *m,
-                   double G, double Mstar, double *out)
+                   double G, double Mstar, int n_big, double *out)
 {
     nsum e = {0, 0}, lx = {0, 0}, ly = {0, 0}, lz = {0, 0};
     double P[3];
@@ -381,6 +395,7 @@ void oracle_energy(int N, const double *x, const double *y, const double *z,
     }
     for (int i = 0; i < N; i++) {
         for (int j = i + 1; j < N; j++) {
+            if (tp_pair(n_big, i, j)) continue;
             double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
             nadd(&e, -G * m[i] * m[j] / sqrt(dx * dx + dy * dy + dz * dz));
         }

@@ -41,10 +41,14 @@ MUTANTS = {
     "hc_drift_no_mass_division": ("x[i] += tau * P[0] / Mstar;", "x[i] += tau * P[0];"),
     "drift_full_hc_halves": ("oracle_hc_drift(N, x, y, z, vx, vy, vz, m, Mstar, 0.5 * dt);\n    #pragma",
                              "oracle_hc_drift(N, x, y, z, vx, vy, vz, m, Mstar, dt);\n    #pragma"),
-    "step_full_kick": ("mode, form, 0.5 * dt, ax, ay, az);\n        bad +=",
-                       "mode, form, dt, ax, ay, az);\n        bad +="),
+    "step_full_kick": ("mode, form, n_big, 0.5 * dt, ax, ay, az);\n        bad +=",
+                       "mode, form, n_big, dt, ax, ay, az);\n        bad +="),
     "energy_sun_term": ("/ (2.0 * Mstar));", "/ (2.0));"),
     "energy_pair_term_mass": ("nadd(&e, -G * m[i] * m[j] / sqrt", "nadd(&e, -G * m[i] * m[i] / sqrt"),
+    "tp2_either_test_particle": ("return n_big >= 0 && i >= n_big && j >= n_big;",
+                                 "return n_big >= 0 && (i >= n_big || j >= n_big);"),
+    "tp2_encounters_not_skipped": ("            if (tp_pair(n_big, i, j)) continue;\n            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];\n            double r = sqrt",
+                                   "            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];\n            double r = sqrt"),
     "angular_momentum_component": ("nadd(&lz, m[i] * (x[i] * vy[i] - y[i] * vx[i]));",
                                    "nadd(&lz, m[i] * (x[i] * vy[i] + y[i] * vx[i]));"),
 }

@@ -471,3 +471,95 @@ def test_step_energy_bounded_dt2_and_angular_momentum():
     assert np.abs(dE1[-50:]).max() <= 1.05 * amp1
     assert 3.0 < amp1 / amp2 < 5.0                 # second-order map: error ~ dt^2
     assert dL1.max() < 1e-12                       # exact pairwise antisymmetry in FP64
+
+
+# ----------------------------------------------- test-particle mode 2 ---
+# (Sect. 3, giant-planet runs: planets feel the planetesimals, planetesimals
+# feel the planets but not each other; n_big bodies first, then the test
+# particles.)
+def _kick_tp(arr, n_big, G=1.0, M=1.0, dt=1.0, n1=3.0, n2=0.4, mode=1, form=0):
+    a, rc = oracle.rcrit(*arr, G=G, Mstar=M, dt=dt, n1=n1, n2=n2)
+    return oracle.kick_acc(arr[0], arr[1], arr[2], arr[6], a, rc, G, M, n1, mode, form, n_big=n_big)
+
+
+def test_tp2_off_equals_all_big():
+    d, arr = _planted_disc()
+    full = _kick_tp(arr, -1, G=d.G, dt=d.dt)
+    for nb in (len(arr[6]), len(arr[6]) + 7):
+        assert np.array_equal(_kick_tp(arr, nb, G=d.G, dt=d.dt), full)
+
+
+def test_tp2_only_test_particles_feel_nothing():
+    d, arr = _planted_disc()
+    assert np.all(_kick_tp(arr, 0, G=d.G, dt=d.dt) == 0.0)
+    a, rc = oracle.rcrit(*arr, G=d.G, Mstar=1.0, dt=d.dt, n1=3.0, n2=0.4)
+    pairs, _ = oracle.encounters(arr[0], arr[1], arr[2], arr[6], a, rc, 3.0, 1.0, n_big=0)
+    assert len(pairs) == 0
+    # energy: no pair term at all, only kinetic + |P|^2/2M* - sum G M* m / r
+    x, y, z, vx, vy, vz, m = [np.asarray(v) for v in arr]
+    P = np.array([(m * vx).sum(), (m * vy).sum(), (m * vz).sum()])
+    E = (0.5 * m * (vx * vx + vy * vy + vz * vz)).sum() + P @ P / 2.0 - (d.G * m / np.sqrt(x * x + y * y + z * z)).sum()
+    assert oracle.energy(arr, d.G, 1.0, n_big=0)[0] == pytest.approx(E, rel=1e-14)
+
+
+def test_tp2_is_the_sum_with_massless_test_particles():
+    # a sparse system (every pair far outside r_crit, K = 1): a test particle's
+    # acceleration is the full sum with every test particle's mass set to 0,
+    # a big body's acceleration is the full sum
+    rng = np.random.default_rng(5)
+    N, nb = 24, 5
+    th = rng.uniform(0, 2 * np.pi, N)
+    r = 1.0 + 0.15 * np.arange(N) + rng.uniform(0, 0.02, N)
+    arr = _static(np.stack([r * np.cos(th), r * np.sin(th), 0.01 * rng.standard_normal(N)], 1),
+                  np.concatenate([np.full(nb, 3e-9), np.full(N - nb, 1e-10)]))
+    got = _kick_tp(arr, nb)
+    full = _kick_tp(arr, -1)
+    light = [v.copy() for v in arr]
+    light[6][nb:] = 0.0
+    ref_tp = _kick_tp(light, -1)
+    assert np.array_equal(got[:, :nb], full[:, :nb])
+    assert np.allclose(got[:, nb:], ref_tp[:, nb:], rtol=1e-14, atol=0)
+    assert not np.allclose(got[:, nb:], full[:, nb:], rtol=1e-6, atol=0)   # the TP-TP terms are gone
+
+
+def test_tp2_newton_third_law_and_encounters():
+    d, arr = _planted_disc()
+    nb = 3          # planted pairs: (1,0) big-big, (3,2) big-TP, (5,4) TP-TP
+    acc = _kick_tp(arr, nb, G=d.G, dt=d.dt)
+    m = arr[6]
+    assert np.all(np.abs((acc * m).sum(1)) <= 1e-14 * (np.abs(acc) * m).sum())
+    a, rc = oracle.rcrit(*arr, G=d.G, Mstar=1.0, dt=d.dt, n1=3.0, n2=0.4)
+    full, _ = oracle.encounters(arr[0], arr[1], arr[2], m, a, rc, 3.0, 1.0)
+    tp, _ = oracle.encounters(arr[0], arr[1], arr[2], m, a, rc, 3.0, 1.0, n_big=nb)
+    want = [p for p in map(tuple, full.tolist()) if not (p[0] >= nb and p[1] >= nb)]
+    assert list(map(tuple, tp.tolist())) == want
+    assert (4, 5) in map(tuple, full.tolist()) and (4, 5) not in map(tuple, tp.tolist())
+
+
+def test_tp2_step_conserves_its_energy():
+    # two planets and twelve massive test particles between them: the TP2
+    # dynamics is Hamiltonian with the TP-TP potential left out, so its
+    # energy stays bounded and L is conserved to round-off
+    G = discs.G_GAUSS
+    pl = _two_planets()
+    n = 12
+    a_tp = np.linspace(6.5, 8.0, n)
+    pos, vh = discs.elements_to_cartesian(G * (1 + 1e-8), a_tp, np.full(n, 0.01), np.full(n, 0.01),
+                                          np.linspace(0, 6, n), np.linspace(1, 3, n), np.linspace(0, 5, n))
+    m = np.concatenate([pl[6], np.full(n, 1e-8)])
+    arr = [np.concatenate([pl[c], (pos if c < 3 else vh)[c % 3]]) for c in range(6)] + [m]
+    vb = np.stack(arr[3:6])
+    vb -= (vb * m).sum(1, keepdims=True) / (1 + m.sum())
+    arr[3], arr[4], arr[5] = vb[0].copy(), vb[1].copy(), vb[2].copy()
+    E0, *L0 = oracle.energy(arr, G, 1.0, n_big=2)
+    dE, dL = [], []
+    for _ in range(40):
+        assert oracle.step(arr, G, 1.0, 20.0, 3.0, 0.4, 1, 0, 250, n_big=2) == 0
+        E, *L = oracle.energy(arr, G, 1.0, n_big=2)
+        dE.append(E / E0 - 1)
+        dL.append(np.linalg.norm(np.array(L) - L0) / np.linalg.norm(L0))
+    assert np.abs(dE).max() < 1e-6 and np.abs(dE[-10:]).max() <= 1.05 * np.abs(dE).max()
+    assert max(dL) < 1e-12
+    # the same run with the TP-TP potential counted drifts more: the energy
+    # that TP2 conserves is the one without it (check the definition, not a fit)
+    assert oracle.energy(arr, G, 1.0, n_big=2)[0] != oracle.energy(arr, G, 1.0)[0]
