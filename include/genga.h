@@ -74,6 +74,12 @@ typedef struct {
     int32_t changeover;      /* GENGA_K_* */
     int32_t precision;       /* GENGA_FP64 or GENGA_FP32 */
     int32_t kepler_max_iter; /* iteration cap of the f/g solver, >= 1 (50 is ample) */
+    int32_t n_big;           /* test-particle mode 2 (the giant-planet runs of Sect. 3): with
+                                n_big >= 0, bodies n_big..N-1 (of each system in batched mode)
+                                are test particles that feel bodies 0..n_big-1 but not each
+                                other, while those feel everything -- a pair of two test
+                                particles has no force, no encounter and no potential energy;
+                                -1: every pair interacts */
 } genga_params;
 
 typedef struct {

@@ -35,7 +35,7 @@ class genga_params(C.Structure):
     _fields_ = [("G", C.c_double), ("Mstar", C.c_double), ("dt", C.c_double),
                 ("n1", C.c_double), ("n2", C.c_double),
                 ("rcrit_mode", C.c_int32), ("changeover", C.c_int32),
-                ("precision", C.c_int32), ("kepler_max_iter", C.c_int32)]
+                ("precision", C.c_int32), ("kepler_max_iter", C.c_int32), ("n_big", C.c_int32)]
 
 
 class genga_system(C.Structure):
@@ -121,8 +121,9 @@ def _stream(stream):
 
 
 def make_params(G, Mstar=1.0, dt=6.0, n1=3.0, n2=0.4, rcrit_mode=GENGA_RCRIT_MUTUAL_HILL,
-                changeover=GENGA_K_CHAMBERS, precision=GENGA_FP32, kepler_max_iter=50) -> genga_params:
-    return genga_params(G, Mstar, dt, n1, n2, rcrit_mode, changeover, precision, kepler_max_iter)
+                changeover=GENGA_K_CHAMBERS, precision=GENGA_FP32, kepler_max_iter=50, n_big=-1) -> genga_params:
+    """n_big >= 0: test-particle mode 2 (bodies n_big.. feel the first n_big bodies, not each other)."""
+    return genga_params(G, Mstar, dt, n1, n2, rcrit_mode, changeover, precision, kepler_max_iter, n_big)
 
 
 class DeviceSystem:

@@ -37,6 +37,7 @@ genga_status check_params(const genga_params *p) {
     if (p->changeover != GENGA_K_CHAMBERS && p->changeover != GENGA_K_QUINTIC) return GENGA_ERR_INVALID_ARG;
     if (p->precision != GENGA_FP64 && p->precision != GENGA_FP32) return GENGA_ERR_INVALID_ARG;
     if (p->kepler_max_iter < 1) return GENGA_ERR_INVALID_ARG;
+    if (p->n_big < -1) return GENGA_ERR_INVALID_ARG;
     return GENGA_OK;
 }
 
@@ -65,6 +66,8 @@ PassArgs base_args(genga_ctx *c, const genga_system &sys, const genga_params &p)
     a.scr = c->scr;
     a.gbox_lo = c->gbox_lo;
     a.gbox_hi = c->gbox_hi;
+    a.gflag = c->gflag;
+    a.n_big = p.n_big;
     a.perm = c->perm;
     a.a_osc = c->a_osc;
     a.rc_eq1 = c->rc_eq1;
@@ -152,7 +155,7 @@ cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &
     if (e != cudaSuccess) return e;
     c->launches += momentum_valid ? 0 : 1;
     if (reorder || c->ordered_N != sys.N) {
-        if ((e = launch_order(sys, p.Mstar, c, s)) != cudaSuccess) return e;
+        if ((e = launch_order(sys, p.Mstar, p.n_big, c, s)) != cudaSuccess) return e;
         c->ordered_N = sys.N;
         c->steps_since_order = 0;
         c->launches += 11;  // extent, keys, 3 x (histogram, scan, scatter)
@@ -293,7 +296,7 @@ cudaError_t run_kick_batched(genga_ctx *c, const genga_system &all, const int32_
     if (e != cudaSuccess) return e;
     c->launches += momentum_valid ? 0 : 1;
     if (reorder || c->ordered_N != -2 || c->ordered_key != key) {
-        if ((e = launch_order_batched(all, bb, p.Mstar, c, s)) != cudaSuccess) return e;
+        if ((e = launch_order_batched(all, bb, p.Mstar, p.n_big, c, s)) != cudaSuccess) return e;
         c->ordered_N = -2;  // the order belongs to a batch
         c->ordered_key = key;
         c->steps_since_order = 0;
@@ -405,7 +408,7 @@ void genga_destroy(genga_ctx *c) {
     profile_free(c);
     if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    void *bufs[] = {c->pk_hi,       c->pk_t,        c->pk_d,        c->pk_lo,       c->pk64,        c->scr,      c->gbox_lo,    c->gbox_hi,
+    void *bufs[] = {c->pk_hi,       c->pk_t,        c->pk_d,        c->pk_lo,       c->pk64,        c->scr,      c->gbox_lo,    c->gbox_hi,    c->gflag,
                     c->perm,        c->ord_keys[0], c->ord_keys[1], c->ord_vals[0], c->ord_vals[1], c->ord_hist,
                     c->ord_rbits,   c->a_osc,       c->rc_eq1,      c->partial,  c->mom,        c->enc,
                     c->enc_count,   c->status,      c->energy_part, c->work,   c->Pd,         c->Pd_part};
@@ -458,6 +461,7 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     if (e == cudaSuccess) e = alloc(&c->scr, np);
     if (e == cudaSuccess) e = alloc(&c->gbox_lo, np / 64);
     if (e == cudaSuccess) e = alloc(&c->gbox_hi, np / 64);
+    if (e == cudaSuccess) e = alloc(&c->gflag, np / 64);
     if (e == cudaSuccess) e = alloc(&c->perm, np);
     for (int q = 0; q < 2; q++) {
         if (e == cudaSuccess) e = alloc(&c->ord_keys[q], np);

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(EN_THREADS) energy_kernel(const double *__rest
                                                             const double *__restrict__ vy,
                                                             const double *__restrict__ vz,
                                                             const double *__restrict__ m, int N, double G,
-                                                            double Mstar, double *__restrict__ part) {
+                                                            double Mstar, int n_big, double *__restrict__ part) {
     __shared__ double sh[4][EN_THREADS];
     const int i = blockIdx.x * EN_THREADS + threadIdx.x;
     double e = 0.0, lx = 0.0, ly = 0.0, lz = 0.0;
@@ -41,7 +41,9 @@ __global__ void __launch_bounds__(EN_THREADS) energy_kernel(const double *__rest
         const double xi = x[i], yi = y[i], zi = z[i], mi = m[i];
         const double ui = vx[i], vi = vy[i], wi = vz[i];
         NS pot;
-        for (int j = i + 1; j < N; j++) {
+        // test-particle mode 2: no potential between two test particles
+        const int jend = (n_big >= 0 && i >= n_big) ? i + 1 : N;  // j > i >= n_big: both test particles
+        for (int j = i + 1; j < jend; j++) {
             const double dx = x[j] - xi, dy = y[j] - yi, dz = z[j] - zi;
             pot.add(m[j] / sqrt(dx * dx + dy * dy + dz * dz));
         }
@@ -74,7 +76,7 @@ cudaError_t launch_energy(const genga_system &sys, const genga_params &p, genga_
     const int nb = (sys.N + EN_THREADS - 1) / EN_THREADS;
     if (nb == 0) return cudaSuccess;
     energy_kernel<<<nb, EN_THREADS, 0, s>>>(sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, sys.m, sys.N, p.G,
-                                            p.Mstar, c->energy_part);
+                                            p.Mstar, p.n_big, c->energy_part);
     return cudaGetLastError();
 }
 

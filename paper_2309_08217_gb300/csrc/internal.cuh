@@ -28,6 +28,10 @@
 // Bodies heavier than this fraction of the central mass are ordered after the
 // others (their large r_crit bound would make a group of planetesimals NEAR).
 #define GENGA_HEAVY_MASS 1e-7
+// Group flags (test-particle mode 2): the group holds a body that is not a
+// test particle / a test particle.
+#define GENGA_GROUP_BIG 1
+#define GENGA_GROUP_TP 2
 
 // Bodies per tile of the tile-blocked FP32 copy (pk_t).
 #define GENGA_TILE_T 256
@@ -59,6 +63,7 @@ struct genga_ctx {
     float2 *scr;               // [npad] screening bound factors {H_i, A_i} (rounded up)
     float4 *gbox_lo;           // [npad / 64] per 64-body group: {min x, min y, min z, max H}
     float4 *gbox_hi;           // [npad / 64]                    {max x, max y, max z, max A}
+    int32_t *gflag;            // [npad / 64] GENGA_GROUP_BIG | GENGA_GROUP_TP (test-particle mode 2)
     uint32_t *perm;            // [npad] body at position k of the spatial order
     uint32_t *ord_keys[2];     // [npad] radix sort keys (ping-pong)
     uint32_t *ord_vals[2];     // [npad] radix sort values
@@ -139,6 +144,8 @@ struct PassArgs {               // one long-range pass
     const double4_32a *p64;
     const float2 *scr;
     const float4 *gbox_lo, *gbox_hi;
+    const int32_t *gflag;       // per 64-body group: GENGA_GROUP_BIG | GENGA_GROUP_TP
+    int32_t n_big;              // test-particle mode 2 (genga_params.n_big)
     const uint32_t *perm;
     const double *a_osc, *rc_eq1, *m;
     double *partial;            // [split][3][npad]
@@ -163,7 +170,7 @@ struct PassArgs {               // one long-range pass
 cudaError_t launch_momentum(const double *vx, const double *vy, const double *vz, const double *m,
                             int N, double *P, int32_t *zero_me, cudaStream_t s);
 cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ctx *c, cudaStream_t s);
-cudaError_t launch_order(const genga_system &sys, double Mstar, genga_ctx *c, cudaStream_t s);
+cudaError_t launch_order(const genga_system &sys, double Mstar, int n_big, genga_ctx *c, cudaStream_t s);
 size_t order_hist_entries(int nmax);
 cudaError_t init_pass_kernels();
 cudaError_t launch_pass(const PassArgs &a, int precision, int variant, int grid, cudaStream_t s);
@@ -180,8 +187,8 @@ cudaError_t launch_energy(const genga_system &sys, const genga_params &p, genga_
 // batched mode (batch.cu helpers live next to their single-system versions)
 cudaError_t launch_momentum_batched(const genga_system &all, const BatchBodies &bb, double *Pd, int32_t *zero_me,
                                     cudaStream_t s);
-cudaError_t launch_order_batched(const genga_system &all, const BatchBodies &bb, double Mstar, genga_ctx *c,
-                                 cudaStream_t s);
+cudaError_t launch_order_batched(const genga_system &all, const BatchBodies &bb, double Mstar, int n_big,
+                                 genga_ctx *c, cudaStream_t s);
 cudaError_t launch_prep_batched(const genga_system &all, const BatchBodies &bb, const genga_params &p, genga_ctx *c,
                                 cudaStream_t s);
 cudaError_t launch_pass_batched(const PassArgs &a, const BatchBodies &bb, const BatchItems &bi, int variant, int grid,

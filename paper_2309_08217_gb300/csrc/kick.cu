@@ -105,6 +105,7 @@ __device__ __forceinline__ double changeover_K(double y, int form) {
 __device__ __noinline__ double3 screened_pair(const PassArgs &a, int i, int j, int poff, int Nd, int off) {
     double3 f = make_double3(0.0, 0.0, 0.0);
     if (i - poff >= Nd || j - poff >= Nd || i == j) return f;
+    if (a.n_big >= 0 && a.lo[i].w != 0.f && a.lo[j].w != 0.f) return f;  // two test particles (mode 2)
     const double4_32a pi = a.p64[i], pj = a.p64[j];
     const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
     const double r2 = dx * dx + dy * dy + dz * dz;
@@ -321,7 +322,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
     float4 *s_glo = s_lo + STAGES * TILE;  // [STAGES][NG] group boxes of each staged tile
     float4 *s_ghi = s_glo + STAGES * NG;
     float4 *s_tb = s_ghi + STAGES * NG;  // [STAGES][2] box of each staged tile (union of its groups)
-    uint64_t *full = reinterpret_cast<uint64_t *>(s_tb + 2 * STAGES);
+    int32_t *s_gf = reinterpret_cast<int32_t *>(s_tb + 2 * STAGES);  // [STAGES][NG + 1] group flags, tile flags
+    uint64_t *full = reinterpret_cast<uint64_t *>(s_gf + STAGES * (NG + 4));
     uint64_t *empty = full + STAGES;
     StageHdr *hdr = reinterpret_cast<StageHdr *>(empty + STAGES);
     __shared__ DF s_acc[3 * BPT * NC];      // [c][k][thread] double-float per-body sums
@@ -371,6 +373,16 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                 const Box tbx = group_box<NG>(a.gbox_lo, a.gbox_hi, t * NG);
                 s_tb[2 * slot] = tbx.lo;
                 s_tb[2 * slot + 1] = tbx.hi;
+                if (a.n_big >= 0) {  // test-particle mode 2: which kinds of bodies the groups hold
+                    int32_t tf = 0;
+#pragma unroll
+                    for (int q = 0; q < NG; q++) {
+                        const int32_t f = a.gflag[(size_t)t * NG + q];
+                        s_gf[slot * (NG + 4) + q] = f;
+                        tf |= f;
+                    }
+                    s_gf[slot * (NG + 4) + NG] = tf;
+                }
                 fence_proxy_async_smem();
                 constexpr uint32_t GB = NG * sizeof(float4);
                 mbar_arrive_expect_tx(&full[slot], TBH + TBL + 2 * GB);
@@ -391,6 +403,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
     Box wbox = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
     int wbase = 0;
     bool in = false;  // this warp holds real i-bodies of the current item
+    int32_t wflag = GENGA_GROUP_BIG;  // kinds of bodies the warp holds (test-particle mode 2)
     for (unsigned n = 0;; n++) {
         const int slot = n % STAGES;
         if (!mbar_wait_bounded(&full[slot], (n / STAGES) & 1, a.status)) return;
@@ -420,6 +433,12 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                 YI[q] = pk2(u.y, v.y);
                 ZI[q] = pk2(u.z, v.z);
             }
+            wflag = GENGA_GROUP_BIG;
+            if (in && a.n_big >= 0) {
+                wflag = 0;
+#pragma unroll
+                for (int q = 0; q < BPT / 2; q++) wflag |= a.gflag[wbase / 64 + q];
+            }
             if (in) {
                 wbox = group_box<BPT / 2>(a.gbox_lo, a.gbox_hi, wbase / 64);
             } else {  // empty box: every tile is FAR, nothing is written
@@ -437,15 +456,26 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
 #pragma unroll
         for (int k = 0; k < BPT; k++) ax[k] = ay[k] = az[k] = 0.f;
         const float4 *th = s_hi + slot * HF4;
+        // test-particle mode 2: a warp of test particles skips the groups of
+        // test particles; a warp holding test particles runs the groups that
+        // hold test particles through the NEAR loop, which masks their pairs
+        const bool tp2 = a.n_big >= 0;
+        const int32_t tflag = tp2 ? s_gf[slot * (NG + 4) + NG] : GENGA_GROUP_BIG;
+        const bool tile_skip = tp2 && !(wflag & GENGA_GROUP_BIG) && !(tflag & GENGA_GROUP_BIG);
+        const bool tile_mixed = tp2 && (wflag & GENGA_GROUP_TP) && (tflag & GENGA_GROUP_TP);
         // a tile FAR as a whole needs no per-group test (the tile box holds
         // every group box, so its gap is smaller and its bound larger)
-        const bool tile_far = far_pair_of_boxes(wbox, Box{s_tb[2 * slot], s_tb[2 * slot + 1]}, true);
-        for (int g = 0; g < NG; g++) {
+        const bool tile_far =
+            !tile_mixed && far_pair_of_boxes(wbox, Box{s_tb[2 * slot], s_tb[2 * slot + 1]}, true);
+        for (int g = 0; g < (tile_skip ? 0 : NG); g++) {
+            const int32_t gflag = tp2 ? s_gf[slot * (NG + 4) + g] : GENGA_GROUP_BIG;
+            if (tp2 && !(wflag & GENGA_GROUP_BIG) && !(gflag & GENGA_GROUP_BIG)) continue;  // no pair interacts
+            const bool masked = tp2 && (wflag & GENGA_GROUP_TP) && (gflag & GENGA_GROUP_TP);
             const Box gb = {s_glo[slot * NG + g], s_ghi[slot * NG + g]};
             const float *tx = reinterpret_cast<const float *>(th) + g * 64, *ty = tx + TILE, *tz = tx + 2 * TILE,
                         *tw = tx + 3 * TILE;     // j-packed layout
             const float4 *td = th + g * 128;  // i-packed layout: two float4 per j
-            if (tile_far || far_pair_of_boxes(wbox, gb, true)) {
+            if (!masked && (tile_far || far_pair_of_boxes(wbox, gb, true))) {
                 // every pair: K = 1, FP32-rounded positions accurate enough
                 if constexpr (IPACK) {
 #pragma unroll(UNR)
@@ -510,12 +540,14 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                 auto near_group = [&](float(&sx)[BPT], float(&sy)[BPT], float(&sz)[BPT]) {
                     const float4 *tl = s_lo + slot * TILE + g * 64;
                     float xl[BPT], yl[BPT], zl[BPT], thr[BPT];
+                    unsigned itp = 0u;  // bit k: i_k is a test particle (masked groups only)
 #pragma unroll
                     for (int k = 0; k < BPT; k++) {
                         const float4 l = s_ilo[k * NC + tid];
                         const float2 sc = s_iscr[k * NC + tid];
                         xl[k] = l.x; yl[k] = l.y; zl[k] = l.z;
                         thr[k] = screen_threshold(sc.x, sc.y, gb.lo.w, gb.hi.w);
+                        itp |= (unsigned)(masked && l.w != 0.f) << k;
                     }
 #pragma unroll 2
                     for (int jj = 0; jj < 64; jj++) {
@@ -535,9 +567,10 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                             const float dz = (jz - ival<IPACK>(ZI, k)) + (pl.z - zl[k]);
                             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                             const float ri = rsqrt_sfu(r2);
-                            const bool near = r2 < thr[k];
+                            const bool skip = (itp >> k & 1u) && pl.w != 0.f;  // two test particles
+                            const bool near = r2 < thr[k] && !skip;
                             screened |= (unsigned)near << k;
-                            const float sf = near ? 0.f : (jw * ri) * (ri * ri);
+                            const float sf = (near || skip) ? 0.f : (jw * ri) * (ri * ri);
                             sx[k] = fmaf(sf, dx, sx[k]);
                             sy[k] = fmaf(sf, dy, sy[k]);
                             sz[k] = fmaf(sf, dz, sz[k]);
@@ -672,6 +705,17 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
         CX[k] = CY[k] = CZ[k] = Comp{0.0, 0.0};
     }
     const Box wbox = group_box<(BPT + 1) / 2>(a.gbox_lo, a.gbox_hi, wbase / 64);
+    // test-particle mode 2: kinds of bodies the warp holds; its test particles
+    const bool tp2 = a.n_big >= 0;
+    int32_t wflag = GENGA_GROUP_BIG;
+    unsigned itp = 0u;
+    if (tp2) {
+        wflag = 0;
+#pragma unroll
+        for (int q = 0; q < (BPT + 1) / 2; q++) wflag |= a.gflag[wbase / 64 + q];
+#pragma unroll
+        for (int k = 0; k < BPT; k++) itp |= (unsigned)(a.lo[wbase + k * 32 + lane].w != 0.f) << k;
+    }
 
     constexpr uint32_t TB = TILE * sizeof(double4_32a);
     if (tid == 0) {
@@ -700,7 +744,15 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
             }
         }
         const Box tbox = group_box<TILE / 64>(a.gbox_lo, a.gbox_hi, t * (TILE / 64));
-        const bool far = far_pair_of_boxes(wbox, tbox, false);
+        int32_t tflag = GENGA_GROUP_BIG;
+        if (tp2) {
+            tflag = 0;
+#pragma unroll
+            for (int q = 0; q < TILE / 64; q++) tflag |= a.gflag[t * (TILE / 64) + q];
+        }
+        const bool skip_tile = tp2 && !(wflag & GENGA_GROUP_BIG) && !(tflag & GENGA_GROUP_BIG);
+        const bool masked = tp2 && (wflag & GENGA_GROUP_TP) && (tflag & GENGA_GROUP_TP);
+        const bool far = !masked && far_pair_of_boxes(wbox, tbox, false);
         double thr[BPT];
 #pragma unroll
         for (int k = 0; k < BPT; k++) thr[k] = (double)screen_threshold(H[k], A[k], tbox.lo.w, tbox.hi.w);
@@ -708,7 +760,7 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
         if (!mbar_wait_bounded(&bars[stage], (uint32_t)((it / STAGES) & 1), a.status)) s_abort = 1;
 
         const double4_32a *tp = s_p + stage * TILE;
-        for (int j0 = 0; j0 < TILE; j0 += 32) {
+        for (int j0 = 0; j0 < (skip_tile ? 0 : TILE); j0 += 32) {
             double px[BPT], py[BPT], pz[BPT];
 #pragma unroll
             for (int k = 0; k < BPT; k++) px[k] = py[k] = pz[k] = 0.0;
@@ -731,15 +783,17 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
 #pragma unroll 2
                 for (int jj = j0; jj < j0 + 32; jj++) {
                     const double4_32a pj = tp[jj];
+                    const bool jtp = masked && a.lo[t * TILE + jj].w != 0.f;  // j is a test particle
                     unsigned screened = 0u;
 #pragma unroll
                     for (int k = 0; k < BPT; k++) {
                         const double dx = pj.x - xi[k], dy = pj.y - yi[k], dz = pj.z - zi[k];
                         const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
                         const double ri = rsqrt_fp64(r2);
-                        const bool near = r2 < thr[k];
+                        const bool skip = jtp && (itp >> k & 1u);  // two test particles: no force
+                        const bool near = r2 < thr[k] && !skip;
                         screened |= (unsigned)near << k;
-                        const double s = near ? 0.0 : (pj.w * ri) * (ri * ri);
+                        const double s = (near || skip) ? 0.0 : (pj.w * ri) * (ri * ri);
                         px[k] = fma(s, dx, px[k]);
                         py[k] = fma(s, dy, py[k]);
                         pz[k] = fma(s, dz, pz[k]);
@@ -964,6 +1018,7 @@ constexpr int F64_BPT = 2, F64_TILE = 128, F64_STAGES = 3;
 size_t smem_fp32(bool ipack, int stages) {
     const size_t hf4 = ipack ? 2 * F32_TILE : F32_TILE;
     return (size_t)stages * (hf4 + F32_TILE) * sizeof(float4) + (size_t)stages * (F32_TILE / 64 + 1) * 2 * sizeof(float4) +
+           (size_t)stages * (F32_TILE / 64 + 4) * sizeof(int32_t) +
            2 * stages * sizeof(uint64_t) + stages * sizeof(StageHdr);
 }
 size_t smem_fp64() { return (size_t)F64_STAGES * F64_TILE * sizeof(double4_32a) + F64_STAGES * sizeof(uint64_t); }

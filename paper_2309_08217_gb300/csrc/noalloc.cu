@@ -116,15 +116,16 @@ __device__ double na_changeover(double y, int form) {
 __global__ void na_acc(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
                        double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
                        const double *__restrict__ m, int N, double G, double Mstar, double n1, int mode, int form,
-                       double tau, double *__restrict__ acc, const double *scratch) {
+                       int n_big, double tau, double *__restrict__ acc, const double *scratch) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double *A = scratch + NA_OFF_A, *RC = scratch + NA_OFF_RC, *H = scratch + NA_OFF_H;
     const double xi = x[i], yi = y[i], zi = z[i], mi = m[i], ai = A[i], rci = RC[i], hi = H[i];
     NaSum sx, sy, sz;
     double px = 0.0, py = 0.0, pz = 0.0;
+    const bool tp_i = n_big >= 0 && i >= n_big;  // test-particle mode 2: no force between test particles
     for (int j = 0; j < N; j++) {
-        if (j != i) {
+        if (j != i && !(tp_i && j >= n_big)) {
             const double dx = x[j] - xi, dy = y[j] - yi, dz = z[j] - zi;
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 > 0.0) {
@@ -195,7 +196,7 @@ extern "C" genga_status genga_kick_noalloc(const genga_system *sys, const genga_
         return GENGA_ERR_INVALID_ARG;
     if (p->precision != GENGA_FP64 || !(p->Mstar > 0.0) || !(p->G >= 0.0) || p->n1 < 0.0 || p->n2 < 0.0 ||
         (p->rcrit_mode != GENGA_RCRIT_EQ1 && p->rcrit_mode != GENGA_RCRIT_MUTUAL_HILL) ||
-        (p->changeover != GENGA_K_CHAMBERS && p->changeover != GENGA_K_QUINTIC) || !isfinite(tau))
+        (p->changeover != GENGA_K_CHAMBERS && p->changeover != GENGA_K_QUINTIC) || p->n_big < -1 || !isfinite(tau))
         return GENGA_ERR_INVALID_ARG;
     if (sys->N == 0) return GENGA_OK;
     double *scratch = nullptr;
@@ -209,6 +210,6 @@ extern "C" genga_status genga_kick_noalloc(const genga_system *sys, const genga_
     na_rcrit<<<nb, NA_THREADS, 0, s>>>(sys->x, sys->y, sys->z, sys->vx, sys->vy, sys->vz, sys->m, N, p->G,
                                        p->Mstar, p->dt, p->n1, p->n2, scratch);
     na_acc<<<nb, NA_THREADS, 0, s>>>(sys->x, sys->y, sys->z, sys->vx, sys->vy, sys->vz, sys->m, N, p->G, p->Mstar,
-                                     p->n1, p->rcrit_mode, p->changeover, tau, acc, scratch);
+                                     p->n1, p->rcrit_mode, p->changeover, p->n_big, tau, acc, scratch);
     return cudaGetLastError() == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
 }

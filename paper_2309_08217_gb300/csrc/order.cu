@@ -55,20 +55,24 @@ __device__ __forceinline__ uint32_t quant7(double c, float inv) {
     return (uint32_t)f;
 }
 
-// Heavy flag and 21-bit Morton code of one body.
-__device__ __forceinline__ uint32_t body_key(double x, double y, double z, double m, double heavy_mass, float inv) {
-    const uint32_t heavy = m > heavy_mass ? 1u : 0u;
+// Heavy flag and 21-bit Morton code of one body (k = its index in its system;
+// in test-particle mode 2 the flag marks the bodies that are not test
+// particles, so groups hold one kind only).
+__device__ __forceinline__ uint32_t body_key(double x, double y, double z, double m, double heavy_mass, int k,
+                                             int n_big, float inv) {
+    const uint32_t heavy = (n_big >= 0 ? k < n_big : m > heavy_mass) ? 1u : 0u;
     return (heavy << 21) | spread3(quant7(x, inv)) | (spread3(quant7(y, inv)) << 1) | (spread3(quant7(z, inv)) << 2);
 }
 
 __global__ void keys_kernel(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
-                            const double *__restrict__ m, int N, double heavy_mass, const unsigned *__restrict__ rbits,
+                            const double *__restrict__ m, int N, double heavy_mass, int n_big,
+                            const unsigned *__restrict__ rbits,
                             uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float R = fmaxf(__uint_as_float(*rbits), 1e-30f) * 1.0001f;
     const float inv = 1.0f / R;
-    keys[i] = body_key(x[i], y[i], z[i], m[i], heavy_mass, inv);
+    keys[i] = body_key(x[i], y[i], z[i], m[i], heavy_mass, i, n_big, inv);
     vals[i] = (uint32_t)i;
 }
 
@@ -76,6 +80,7 @@ __global__ void keys_kernel(const double *__restrict__ x, const double *__restri
 // bodies by system first and along the Morton curve inside each system.
 __global__ void keys_batched_kernel(const double *__restrict__ x, const double *__restrict__ y,
                                     const double *__restrict__ z, const double *__restrict__ m, double heavy_mass,
+                                    int n_big,
                                     const unsigned *__restrict__ rbits, uint32_t *__restrict__ keys,
                                     uint32_t *__restrict__ vals, const __grid_constant__ BatchBodies bb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -83,7 +88,7 @@ __global__ void keys_batched_kernel(const double *__restrict__ x, const double *
     const int d = find_segment(bb.off, bb.D, i);
     const float R = fmaxf(__uint_as_float(*rbits), 1e-30f) * 1.0001f;
     const float inv = 1.0f / R;
-    keys[i] = ((uint32_t)d << 24) | body_key(x[i], y[i], z[i], m[i], heavy_mass, inv);
+    keys[i] = ((uint32_t)d << 24) | body_key(x[i], y[i], z[i], m[i], heavy_mass, i - bb.off[d], n_big, inv);
     vals[i] = (uint32_t)i;
 }
 
@@ -213,28 +218,28 @@ void radix_to_perm(genga_ctx *c, int N, int passes, cudaStream_t s) {
 }
 
 // perm[k] = index of the body at position k of the Morton order (k < N).
-cudaError_t launch_order(const genga_system &sys, double Mstar, genga_ctx *c, cudaStream_t s) {
+cudaError_t launch_order(const genga_system &sys, double Mstar, int n_big, genga_ctx *c, cudaStream_t s) {
     const int N = sys.N;
     if (N <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(c->ord_rbits, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     extent_kernel<<<64, 256, 0, s>>>(sys.x, sys.y, sys.z, N, c->ord_rbits);
-    keys_kernel<<<(N + 255) / 256, 256, 0, s>>>(sys.x, sys.y, sys.z, sys.m, N, GENGA_HEAVY_MASS * Mstar,
+    keys_kernel<<<(N + 255) / 256, 256, 0, s>>>(sys.x, sys.y, sys.z, sys.m, N, GENGA_HEAVY_MASS * Mstar, n_big,
                                                 c->ord_rbits, c->ord_keys[0], c->ord_vals[0]);
     radix_to_perm(c, N, 3, s);
     return cudaGetLastError();
 }
 
 // Batched: the 22-bit keys below the 8-bit system index, four passes.
-cudaError_t launch_order_batched(const genga_system &all, const BatchBodies &bb, double Mstar, genga_ctx *c,
-                                 cudaStream_t s) {
+cudaError_t launch_order_batched(const genga_system &all, const BatchBodies &bb, double Mstar, int n_big,
+                                 genga_ctx *c, cudaStream_t s) {
     const int N = bb.N_total;
     if (N <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(c->ord_rbits, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     extent_kernel<<<64, 256, 0, s>>>(all.x, all.y, all.z, N, c->ord_rbits);
     keys_batched_kernel<<<(N + 255) / 256, 256, 0, s>>>(all.x, all.y, all.z, all.m, GENGA_HEAVY_MASS * Mstar,
-                                                        c->ord_rbits, c->ord_keys[0], c->ord_vals[0], bb);
+                                                        n_big, c->ord_rbits, c->ord_keys[0], c->ord_vals[0], bb);
     radix_to_perm(c, N, 4, s);
     return cudaGetLastError();
 }

@@ -107,7 +107,7 @@ __device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double 
                                            double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
                                            float4 *__restrict__ lo, double4_32a *__restrict__ p64,
                                            float2 *__restrict__ scr, double *__restrict__ a_osc,
-                                           double *__restrict__ rc_eq1, float3 *pos, bool *real) {
+                                           double *__restrict__ rc_eq1, bool tp, float3 *pos, bool *real) {
     float2 s = make_float2(0.f, 0.f);
     if (i >= 0) {
         // osculating a from the heliocentric velocity u = v + P / M*:
@@ -143,7 +143,7 @@ __device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double 
         store_tiled(hit, k, hx, hy, hz, __double2float_rn(gm));
         store_dup(hid, k, hx, hy, hz, __double2float_rn(gm));
         lo[k] = make_float4(__double2float_rn(xi - (double)hx), __double2float_rn(yi - (double)hy),
-                            __double2float_rn(zi - (double)hz), 0.f);
+                            __double2float_rn(zi - (double)hz), tp ? 1.f : 0.f);  // w: test particle (mode 2)
         p64[k] = make_double4_32a(xi, yi, zi, gm);
         *pos = make_float3(hx, hy, hz);
         *real = true;
@@ -162,10 +162,14 @@ __device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double 
     return s;
 }
 
-// Bounding box of the group's real bodies (FP32 hi positions) and the maxima
-// of its screening factors; one block = one 64-body group.
-__device__ __forceinline__ void group_reduce_store(float2 s, float3 pos, bool real, float4 *__restrict__ gbox_lo,
-                                                   float4 *__restrict__ gbox_hi) {
+// Bounding box of the group's real bodies (FP32 hi positions), the maxima of
+// its screening factors and its flags (GENGA_GROUP_BIG: holds a body that is
+// not a test particle, GENGA_GROUP_TP: holds a test particle); one block =
+// one 64-body group.
+__device__ __forceinline__ void group_reduce_store(float2 s, float3 pos, bool real, bool tp,
+                                                   float4 *__restrict__ gbox_lo, float4 *__restrict__ gbox_hi,
+                                                   int32_t *__restrict__ gflag) {
+    const unsigned big_w = __ballot_sync(0xffffffffu, real && !tp), tp_w = __ballot_sync(0xffffffffu, real && tp);
     const float INF = __int_as_float(0x7f800000);
     float3 bl = real ? pos : make_float3(INF, INF, INF);
     float3 bh = real ? pos : make_float3(-INF, -INF, -INF);
@@ -182,19 +186,24 @@ __device__ __forceinline__ void group_reduce_store(float2 s, float3 pos, bool re
         bh.z = fmaxf(bh.z, __shfl_xor_sync(0xffffffffu, bh.z, o));
     }
     __shared__ float4 wl[PREP_THREADS / 32], wh[PREP_THREADS / 32];
+    __shared__ int32_t wf[PREP_THREADS / 32];
     if ((threadIdx.x & 31) == 0) {
         wl[threadIdx.x >> 5] = make_float4(bl.x, bl.y, bl.z, hmax);
         wh[threadIdx.x >> 5] = make_float4(bh.x, bh.y, bh.z, amax);
+        wf[threadIdx.x >> 5] = (big_w ? GENGA_GROUP_BIG : 0) | (tp_w ? GENGA_GROUP_TP : 0);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         float4 l = wl[0], h = wh[0];
+        int32_t f = wf[0];
         for (int w = 1; w < PREP_THREADS / 32; w++) {
+            f |= wf[w];
             l = make_float4(fminf(l.x, wl[w].x), fminf(l.y, wl[w].y), fminf(l.z, wl[w].z), fmaxf(l.w, wl[w].w));
             h = make_float4(fmaxf(h.x, wh[w].x), fmaxf(h.y, wh[w].y), fmaxf(h.z, wh[w].z), fmaxf(h.w, wh[w].w));
         }
         gbox_lo[blockIdx.x] = l;
         gbox_hi[blockIdx.x] = h;
+        gflag[blockIdx.x] = f;
     }
 }
 
@@ -206,13 +215,16 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
     const double *__restrict__ m, int N, const uint32_t *__restrict__ perm, const double *__restrict__ P, double G,
     double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
     float4 *__restrict__ lo, double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
-    float4 *__restrict__ gbox_hi, double *__restrict__ a_osc, double *__restrict__ rc_eq1) {
+    float4 *__restrict__ gbox_hi, int32_t *__restrict__ gflag, double *__restrict__ a_osc,
+    double *__restrict__ rc_eq1, int n_big) {
     const int k = blockIdx.x * PREP_THREADS + threadIdx.x;
     float3 pos = make_float3(0.f, 0.f, 0.f);
     bool real = false;
-    const float2 s = prep_body(k, k < N ? (int)perm[k] : -1, k - N, x, y, z, vx, vy, vz, m, P, G, Mstar, dt, n1, n2,
-                               rcrit_mode, hi, hit, hid, lo, p64, scr, a_osc, rc_eq1, &pos, &real);
-    group_reduce_store(s, pos, real, gbox_lo, gbox_hi);
+    const int i = k < N ? (int)perm[k] : -1;
+    const bool tp = i >= 0 && n_big >= 0 && i >= n_big;
+    const float2 s = prep_body(k, i, k - N, x, y, z, vx, vy, vz, m, P, G, Mstar, dt, n1, n2,
+                               rcrit_mode, hi, hit, hid, lo, p64, scr, a_osc, rc_eq1, tp, &pos, &real);
+    group_reduce_store(s, pos, real, tp, gbox_lo, gbox_hi, gflag);
 }
 
 // Batched: packed position p belongs to system d = segment of p in poff; its
@@ -224,16 +236,18 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_batched_kernel(
     const double *__restrict__ m, const uint32_t *__restrict__ perm, const double *__restrict__ Pd, double G,
     double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
     float4 *__restrict__ lo, double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
-    float4 *__restrict__ gbox_hi, double *__restrict__ a_osc, double *__restrict__ rc_eq1,
-    const __grid_constant__ BatchBodies bb) {
+    float4 *__restrict__ gbox_hi, int32_t *__restrict__ gflag, double *__restrict__ a_osc,
+    double *__restrict__ rc_eq1, int n_big, const __grid_constant__ BatchBodies bb) {
     const int p = blockIdx.x * PREP_THREADS + threadIdx.x;
     const int d = find_segment(bb.poff, bb.D, p);
     const int k = p - bb.poff[d], Nd = bb.off[d + 1] - bb.off[d];
     float3 pos = make_float3(0.f, 0.f, 0.f);
     bool real = false;
-    const float2 s = prep_body(p, k < Nd ? (int)perm[bb.off[d] + k] : -1, k - Nd, x, y, z, vx, vy, vz, m, Pd + 3 * d, G,
-                               Mstar, dt, n1, n2, rcrit_mode, hi, hit, hid, lo, p64, scr, a_osc, rc_eq1, &pos, &real);
-    group_reduce_store(s, pos, real, gbox_lo, gbox_hi);
+    const int i = k < Nd ? (int)perm[bb.off[d] + k] : -1;
+    const bool tp = i >= 0 && n_big >= 0 && i - bb.off[d] >= n_big;
+    const float2 s = prep_body(p, i, k - Nd, x, y, z, vx, vy, vz, m, Pd + 3 * d, G, Mstar, dt, n1, n2, rcrit_mode, hi,
+                               hit, hid, lo, p64, scr, a_osc, rc_eq1, tp, &pos, &real);
+    group_reduce_store(s, pos, real, tp, gbox_lo, gbox_hi, gflag);
 }
 
 // Batched momentum: block d sums system d (strided per thread, fixed tree).
@@ -278,8 +292,8 @@ cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ct
     const int npad = (sys.N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
     prep_kernel<<<npad / PREP_THREADS, PREP_THREADS, 0, s>>>(
         sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->perm, c->mom, p.G, p.Mstar, p.dt, p.n1,
-        p.n2, p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_d, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->a_osc,
-        c->rc_eq1);
+        p.n2, p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_d, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->gflag,
+        c->a_osc, c->rc_eq1, p.n_big);
     return cudaGetLastError();
 }
 
@@ -297,7 +311,8 @@ cudaError_t launch_prep_batched(const genga_system &all, const BatchBodies &bb, 
                                 cudaStream_t s) {
     prep_batched_kernel<<<bb.npad_total / PREP_THREADS, PREP_THREADS, 0, s>>>(
         all.x, all.y, all.z, all.vx, all.vy, all.vz, all.m, c->perm, c->Pd, p.G, p.Mstar, p.dt, p.n1, p.n2,
-        p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_d, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->a_osc, c->rc_eq1, bb);
+        p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_d, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->gflag, c->a_osc,
+        c->rc_eq1, p.n_big, bb);
     return cudaGetLastError();
 }
 
