@@ -462,7 +462,11 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
         const bool tp2 = a.n_big >= 0;
         const int32_t tflag = tp2 ? s_gf[slot * (NG + 4) + NG] : GENGA_GROUP_BIG;
         const bool tile_skip = tp2 && !(wflag & GENGA_GROUP_BIG) && !(tflag & GENGA_GROUP_BIG);
-        const bool tile_mixed = tp2 && (wflag & GENGA_GROUP_TP) && (tflag & GENGA_GROUP_TP);
+        // a warp of both kinds against a tile of test particles: every pair of
+        // its test-particle lanes is excluded, so the tile is run as usual and
+        // those lanes' tile sums are dropped
+        const bool drop_tp = tp2 && (wflag & GENGA_GROUP_TP) && (wflag & GENGA_GROUP_BIG) && !(tflag & GENGA_GROUP_BIG);
+        const bool tile_mixed = tp2 && !drop_tp && (wflag & GENGA_GROUP_TP) && (tflag & GENGA_GROUP_TP);
         // a tile FAR as a whole needs no per-group test (the tile box holds
         // every group box, so its gap is smaller and its bound larger)
         const bool tile_far =
@@ -470,7 +474,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
         for (int g = 0; g < (tile_skip ? 0 : NG); g++) {
             const int32_t gflag = tp2 ? s_gf[slot * (NG + 4) + g] : GENGA_GROUP_BIG;
             if (tp2 && !(wflag & GENGA_GROUP_BIG) && !(gflag & GENGA_GROUP_BIG)) continue;  // no pair interacts
-            const bool masked = tp2 && (wflag & GENGA_GROUP_TP) && (gflag & GENGA_GROUP_TP);
+            const bool masked = tile_mixed && (wflag & GENGA_GROUP_TP) && (gflag & GENGA_GROUP_TP);
             const Box gb = {s_glo[slot * NG + g], s_ghi[slot * NG + g]};
             const float *tx = reinterpret_cast<const float *>(th) + g * 64, *ty = tx + TILE, *tz = tx + 2 * TILE,
                         *tw = tx + 3 * TILE;     // j-packed layout
@@ -639,6 +643,11 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                 az[k] = ival<true>(TZ, k);
             }
         }
+        if (drop_tp) {
+#pragma unroll
+            for (int k = 0; k < BPT; k++)
+                if (s_ilo[k * NC + tid].w != 0.f) ax[k] = ay[k] = az[k] = 0.f;
+        }
 #pragma unroll
         for (int k = 0; k < BPT; k++) {  // fold the tile's FP32 sums into the double-float sums
             DF &tx_ = s_acc[(0 * BPT + k) * NC + tid];
@@ -751,7 +760,10 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
             for (int q = 0; q < TILE / 64; q++) tflag |= a.gflag[t * (TILE / 64) + q];
         }
         const bool skip_tile = tp2 && !(wflag & GENGA_GROUP_BIG) && !(tflag & GENGA_GROUP_BIG);
-        const bool masked = tp2 && (wflag & GENGA_GROUP_TP) && (tflag & GENGA_GROUP_TP);
+        // both kinds in the warp, test particles only in the tile: run it as
+        // usual and drop the test-particle lanes' sums
+        const bool drop_tp = tp2 && (wflag & GENGA_GROUP_TP) && (wflag & GENGA_GROUP_BIG) && !(tflag & GENGA_GROUP_BIG);
+        const bool masked = tp2 && !drop_tp && (wflag & GENGA_GROUP_TP) && (tflag & GENGA_GROUP_TP);
         const bool far = !masked && far_pair_of_boxes(wbox, tbox, false);
         double thr[BPT];
 #pragma unroll
@@ -813,6 +825,7 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
             }
 #pragma unroll
             for (int k = 0; k < BPT; k++) {
+                if (drop_tp && (itp >> k & 1u)) px[k] = py[k] = pz[k] = 0.0;
                 CX[k].add(px[k]);
                 CY[k].add(py[k]);
                 CZ[k].add(pz[k]);
