@@ -87,6 +87,9 @@ PassArgs base_args(genga_ctx *c, const genga_system &sys, const genga_params &p)
     a.changeover = p.changeover;
     a.list_only = 0;
     a.work = c->work;
+    a.tp_b0 = 0;
+    a.tp_t0 = 0;
+    a.tp_rows_end = 0;
     a.ntier = 1;
     a.excess = 0;
     a.tier_len[0] = 1;
@@ -122,7 +125,7 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
             cudaEventRecord(e0, s);
             cudaError_t e = launch_pass(a, GENGA_FP32, v, grid, s);
             if (e == cudaSuccess)
-                e = launch_combine(c->partial, a.split, N, a.npad, 0, c->perm, 0.0, nullptr, nullptr, nullptr, nullptr,
+                e = launch_combine(c->partial, a.split, a.tp_rows_end, N, a.npad, 0, c->perm, 0.0, nullptr, nullptr, nullptr, nullptr,
                                    c->status, s);
             cudaEventRecord(e1, s);
             cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s);
@@ -148,15 +151,16 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
 // prep, pass, and the sort of the encounter list.  Leaves FP64 partials in
 // c->partial, indexed by position in the spatial order.
 cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &p, int precision, bool reorder,
-                     int *split_out, cudaStream_t s, bool momentum_valid = false) {
+                     int *split_out, cudaStream_t s, bool momentum_valid = false, int *one_row_out = nullptr) {
     // momentum_valid: c->mom already holds P of this state (genga_step after a drift)
     cudaError_t e = momentum_valid ? cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s)
                                    : launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->mom, c->enc_count, s);
     if (e != cudaSuccess) return e;
     c->launches += momentum_valid ? 0 : 1;
-    if (reorder || c->ordered_N != sys.N) {
+    if (reorder || c->ordered_N != sys.N || c->ordered_nbig != p.n_big) {
         if ((e = launch_order(sys, p.Mstar, p.n_big, c, s)) != cudaSuccess) return e;
         c->ordered_N = sys.N;
+        c->ordered_nbig = p.n_big;
         c->steps_since_order = 0;
         c->launches += 11;  // extent, keys, 3 x (histogram, scan, scatter)
     }
@@ -174,17 +178,18 @@ cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &
     c->launches += 1;
     c->enc_sorted = false;  // sorted when the list is read
     *split_out = split;
+    if (one_row_out) *one_row_out = a.tp_rows_end;
     return cudaSuccess;
 }
 
 cudaError_t run_kick(genga_ctx *c, const genga_system &sys, const genga_params &p, double tau, double *acc,
                      bool reorder, cudaStream_t s, bool momentum_valid = false) {
-    int split = 1;
-    cudaError_t e = run_pass(c, sys, p, p.precision, reorder, &split, s, momentum_valid);
+    int split = 1, one_row = 0;
+    cudaError_t e = run_pass(c, sys, p, p.precision, reorder, &split, s, momentum_valid, &one_row);
     if (e != cudaSuccess) return e;
     c->launches += 1;
-    return launch_combine(c->partial, split, sys.N, npad_of(sys.N), p.precision == GENGA_FP64 ? 1 : 0, c->perm, tau,
-                          acc, sys.vx, sys.vy, sys.vz, c->status, s);
+    return launch_combine(c->partial, split, one_row, sys.N, npad_of(sys.N), p.precision == GENGA_FP64 ? 1 : 0,
+                          c->perm, tau, acc, sys.vx, sys.vy, sys.vz, c->status, s);
 }
 
 // ------------------------------------------------------------ batched mode
@@ -574,7 +579,8 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
     };
     int k = 0;
     auto aligned = [&]() {
-        return c->steps_since_order == 0 && c->ordered_N == s2.N && (p->precision != GENGA_FP32 || fp32_tuned(c, s2.N));
+        return c->steps_since_order == 0 && c->ordered_N == s2.N && c->ordered_nbig == p->n_big &&
+               (p->precision != GENGA_FP32 || fp32_tuned(c, s2.N));
     };
     for (; k < nsteps && !(aligned() && nsteps - k >= GENGA_REORDER_STEPS); k++)
         if (one_step(s) != cudaSuccess) return GENGA_ERR_CUDA;

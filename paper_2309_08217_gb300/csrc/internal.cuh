@@ -89,6 +89,7 @@ struct genga_ctx {
     int32_t steps_since_order; // genga_step: drifts since the spatial order was built
     int32_t ordered_N;         // N of the system the spatial order was built for (-1: none, -2: a batch)
     unsigned long long ordered_key;  // layout hash of the batch the order was built for
+    int32_t ordered_nbig;      // genga_params.n_big the order was built for (mode 2 needs big bodies last)
     // captured graph of GENGA_REORDER_STEPS steps (genga_step / genga_step_batched)
     cudaStream_t cap_stream;   // internal stream the graphs are captured on
     cudaGraphExec_t step_exec; // NULL until captured
@@ -164,6 +165,12 @@ struct PassArgs {               // one long-range pass
     // tier_n[t] chunks of tier_len[t] tiles, the first chunk being `excess`
     // tiles shorter; split = sum of tier_n = partial rows per body
     int32_t ntier, excess;
+    // test-particle mode 2 plan (tp_b0 > 0): i-blocks 0..tp_b0-1 hold test
+    // particles only and get one item over tiles tp_t0.. (those with big
+    // bodies, ordered last), writing partial row 0 only; the others get the
+    // tiered chunks of every tile
+    int32_t tp_b0, tp_t0;
+    int32_t tp_rows_end;        // packed positions below it have one partial row (tp_b0 i-blocks)
     int32_t tier_len[GENGA_MAX_TIERS], tier_n[GENGA_MAX_TIERS];
 };
 
@@ -176,7 +183,8 @@ cudaError_t init_pass_kernels();
 cudaError_t launch_pass(const PassArgs &a, int precision, int variant, int grid, cudaStream_t s);
 int num_fp32_variants();
 void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_cap, PassArgs *a, int *grid);
-cudaError_t launch_combine(const double *partial, int split, int N, int npad, int fp64_rows, const uint32_t *perm,
+cudaError_t launch_combine(const double *partial, int split, int one_row_end, int N, int npad, int fp64_rows,
+                           const uint32_t *perm,
                            double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
                            cudaStream_t s);
 cudaError_t launch_sort_pairs(int2 *enc, int32_t cap, const int32_t *count, cudaStream_t s);

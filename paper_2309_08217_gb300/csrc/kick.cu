@@ -238,14 +238,25 @@ struct ItemGeo {
     int poff, npad, Nd, off, nchunks, iblocks, ntier, excess;
     const int *tlen, *tcnt;
     long long pbase;
+    int dt0;  // >= 0: the item covers tiles dt0.. of its system directly (test-particle i-blocks)
 };
 
 // Work items of a single system (the whole packed range).
 struct SingleItems {
-    __device__ int total(const PassArgs &a, int IB) const { return ((a.npad + IB - 1) / IB) * a.split; }
+    __device__ int total(const PassArgs &a, int IB) const {
+        return ((a.npad + IB - 1) / IB - a.tp_b0) * a.split + a.tp_b0;
+    }
     __device__ void decode(const PassArgs &a, int IB, int, int q, int *ib, int *chunk, ItemGeo *g) const {
-        *g = ItemGeo{0, a.npad, a.N, 0, a.split, (a.npad + IB - 1) / IB, a.ntier, a.excess, a.tier_len, a.tier_n, 0};
-        item_of(q, g->iblocks, ib, chunk);
+        const int nA = (a.npad + IB - 1) / IB - a.tp_b0;  // i-blocks with every tile (all of them without mode 2)
+        *g = ItemGeo{0, a.npad, a.N, 0, a.split, nA, a.ntier, a.excess, a.tier_len, a.tier_n, 0, -1};
+        if (q < nA * a.split) {
+            item_of(q, nA, ib, chunk);
+            *ib += a.tp_b0;
+        } else {  // a test-particle i-block: the tiles with big bodies, row 0
+            *ib = q - nA * a.split;
+            *chunk = 0;
+            g->dt0 = a.tp_t0;
+        }
     }
 };
 
@@ -262,7 +273,7 @@ struct BatchPolicy {
         const int np = bb.poff[d + 1] - bb.poff[d];
         *g = ItemGeo{bb.poff[d],        np, bb.off[d + 1] - bb.off[d], bb.off[d], bi.nchunks[d], bi.iblocks[d], 1,
                      bi.nchunks[d] * bi.blen[d] - np / GENGA_TILE_T, &bi.blen[d], &bi.nchunks[d],
-                     (long long)bi.pbase[d]};
+                     (long long)bi.pbase[d], -1};
         item_of(q - bi.item0[r], g->iblocks, ib, chunk);
     }
 };
@@ -363,9 +374,14 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
             const int t0 = geo.poff / TILE, nt = geo.npad / TILE;  // first tile and tiles of the system
             const int tdiag = (ib * IB) / TILE;                      // the i-block's diagonal tile
             int u0, u1;
-            chunk_ranks(chunk, geo.ntier, geo.excess, geo.tlen, geo.tcnt, &u0, &u1);
+            if (geo.dt0 >= 0) {
+                u0 = geo.dt0;
+                u1 = nt;
+            } else {
+                chunk_ranks(chunk, geo.ntier, geo.excess, geo.tlen, geo.tcnt, &u0, &u1);
+            }
             for (int ur = u0; ur < u1; ur++, n++) {
-                const int t = t0 + tile_of_rank(tdiag, ur, nt);
+                const int t = t0 + (geo.dt0 >= 0 ? ur : tile_of_rank(tdiag, ur, nt));
                 const int slot = n % STAGES;
                 const unsigned u = n / STAGES;
                 if (u > 0 && !mbar_wait_bounded(&empty[slot], (u - 1) & 1, a.status)) return;
@@ -698,8 +714,12 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
     const int ibase = blockIdx.x * (KB * BPT);
     const int wbase = ibase + warp * 32 * BPT;
     const int slice = blockIdx.y;
-    const int t0 = (int)((long long)a.ntiles * slice / a.split);
-    const int t1 = (int)((long long)a.ntiles * (slice + 1) / a.split);
+    // test-particle mode 2 plan: an i-block of test particles only needs the
+    // tiles from the first big body on, in its first slice (partial row 0)
+    const bool tp_block = (int)blockIdx.x < a.tp_b0;
+    if (tp_block && slice != 0) return;
+    const int t0 = tp_block ? a.tp_t0 : (int)((long long)a.ntiles * slice / a.split);
+    const int t1 = tp_block ? a.ntiles : (int)((long long)a.ntiles * (slice + 1) / a.split);
 
     double xi[BPT], yi[BPT], zi[BPT];
     float H[BPT], A[BPT];
@@ -894,7 +914,8 @@ __device__ __forceinline__ void apply_component(double t, int c, int i, size_t N
 }
 
 // grid (ceil(N / 256), 3): blockIdx.y is the component
-__global__ void combine_kernel(const double *__restrict__ partial, int split, int N, int npad, int fp64_rows,
+__global__ void combine_kernel(const double *__restrict__ partial, int split, int one_row_end, int N, int npad,
+                               int fp64_rows,
                                const uint32_t *__restrict__ perm, double tau, double *__restrict__ acc,
                                double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
                                uint32_t *__restrict__ status) {
@@ -902,8 +923,9 @@ __global__ void combine_kernel(const double *__restrict__ partial, int split, in
     const int c = blockIdx.y;
     if (k >= N) return;
     const size_t off = (size_t)c * npad + k, stride = 3 * (size_t)npad;
-    const double t = fp64_rows ? comp_row_sum(partial + off, stride, split)
-                               : df_row_sum(reinterpret_cast<const float2 *>(partial) + off, stride, split);
+    const int rows = k < one_row_end ? 1 : split;  // test-particle i-blocks of a mode-2 plan: row 0 only
+    const double t = fp64_rows ? comp_row_sum(partial + off, stride, rows)
+                               : df_row_sum(reinterpret_cast<const float2 *>(partial) + off, stride, rows);
     apply_component(t, c, (int)perm[k], (size_t)N, tau, acc, vx, vy, vz, status);
 }
 
@@ -1052,12 +1074,31 @@ size_t smem_fp64() { return (size_t)F64_STAGES * F64_TILE * sizeof(double4_32a) 
 // (8 bytes each) fit in partial_cap.
 int num_fp32_variants() { return kNumF32Variants; }
 
+// Test-particle mode 2 (n_big >= 0): the big bodies are ordered after the
+// test particles, so i-blocks that end before position N - n_big hold test
+// particles only: their one item covers the tiles from the first big body on
+// (TP-only tiles have no pair with them); the i-blocks from there on get the
+// whole plan.  Sets tp_b0, tp_t0, tp_rows_end; returns the i-blocks with the
+// whole plan.
+int plan_tp2(int N, int iblocks, int ib, int tile, PassArgs *a) {
+    a->tp_b0 = a->tp_t0 = a->tp_rows_end = 0;
+    if (a->n_big < 0 || a->n_big == 0 || a->n_big >= N) return iblocks;
+    const int first_big = N - a->n_big;
+    const int b0 = first_big / ib;
+    if (b0 <= 0) return iblocks;
+    a->tp_b0 = b0;
+    a->tp_t0 = first_big / tile;
+    a->tp_rows_end = b0 * ib;
+    return iblocks - b0;
+}
+
 void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_cap, PassArgs *a, int *grid) {
     const int npad = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
     const int cap = (int)(partial_cap / (3 * (size_t)npad));
     if (precision != GENGA_FP32) {
         const int ntiles = npad / F64_TILE, iblocks = (npad + KB * F64_BPT - 1) / (KB * F64_BPT);
-        int sp = 2 * sm_count / iblocks;
+        const int nA = plan_tp2(N, iblocks, KB * F64_BPT, F64_TILE, a);
+        int sp = 2 * sm_count / nA;
         sp = sp > ntiles ? ntiles : sp;
         sp = sp > cap ? cap : sp;
         a->split = sp < 1 ? 1 : sp;
@@ -1071,7 +1112,8 @@ void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_c
     const F32Variant &v = kF32Variants[variant];
     const int ntiles = npad / F32_TILE, ib = v.cw * 32 * v.bpt, iblocks = (npad + ib - 1) / ib;
     const int ctas = v.minb * sm_count;
-    const double r = (double)iblocks / ctas;  // single-tile items per CTA of one chunk per i-block
+    const int nA = plan_tp2(N, iblocks, ib, F32_TILE, a);
+    const double r = (double)nA / ctas;  // single-tile items per CTA of one chunk per i-block
     const int lmax = std::max(1, (int)(0.25 * ntiles * r));
     int len[GENGA_MAX_TIERS], cnt[GENGA_MAX_TIERS], nt = 0, rows = 0;
     int R = ntiles;
@@ -1103,7 +1145,7 @@ void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_c
         a->tier_n[t] = cnt[nt - 1 - t];
     }
     a->split = rows;
-    const int nitems = iblocks * rows;
+    const int nitems = nA * rows + a->tp_b0;
     *grid = nitems < ctas ? nitems : ctas;
 }
 
@@ -1164,11 +1206,12 @@ cudaError_t launch_combine_batched(const BatchBodies &bb, const BatchItems &bi, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine(const double *partial, int split, int N, int npad, int fp64_rows, const uint32_t *perm,
+cudaError_t launch_combine(const double *partial, int split, int one_row_end, int N, int npad, int fp64_rows,
+                           const uint32_t *perm,
                            double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
                            cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    combine_kernel<<<dim3((N + 255) / 256, 3), 256, 0, s>>>(partial, split, N, npad, fp64_rows, perm, tau, acc, vx, vy, vz,
+    combine_kernel<<<dim3((N + 255) / 256, 3), 256, 0, s>>>(partial, split, one_row_end, N, npad, fp64_rows, perm, tau, acc, vx, vy, vz,
                                                    status);
     return cudaGetLastError();
 }
