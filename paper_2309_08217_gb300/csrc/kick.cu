@@ -37,6 +37,7 @@
 // it is appended to the encounter list (once, from the side with the smaller
 // body index).
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 
 #include "internal.cuh"
@@ -317,7 +318,7 @@ __device__ __forceinline__ float ival(const f32x2 *V, int k) {
 //     against one j-body held twice; j-tiles staged as the duplicated-pair
 //     copy {x, x, y, y}, {z, z, w, w} (two 128-bit loads per j).  Half the
 //     registers for i positions and sums, so more bodies per thread fit.
-template <int BPT, int CW, int TILE, int STAGES, int MINB, int UNR, bool IPACK, class Pol>
+template <int BPT, int CW, int TILE, int STAGES, int MINB, int UNR, bool IPACK, class Pol, bool TP>
 __global__ void __launch_bounds__((CW + 1) * 32, MINB)
     pass_fp32_kernel(const __grid_constant__ PassArgs a, const __grid_constant__ Pol pol) {
     static_assert(TILE == GENGA_TILE_T, "the staged tile is one block of the tile-blocked copy");
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                 const Box tbx = group_box<NG>(a.gbox_lo, a.gbox_hi, t * NG);
                 s_tb[2 * slot] = tbx.lo;
                 s_tb[2 * slot + 1] = tbx.hi;
-                if (a.n_big >= 0) {  // test-particle mode 2: which kinds of bodies the groups hold
+                if constexpr (TP) {  // test-particle mode 2: which kinds of bodies the groups hold
                     int32_t tf = 0;
 #pragma unroll
                     for (int q = 0; q < NG; q++) {
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                 ZI[q] = pk2(u.z, v.z);
             }
             wflag = GENGA_GROUP_BIG;
-            if (in && a.n_big >= 0) {
+            if (TP && in) {
                 wflag = 0;
 #pragma unroll
                 for (int q = 0; q < BPT / 2; q++) wflag |= a.gflag[wbase / 64 + q];
@@ -475,7 +476,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
         // test-particle mode 2: a warp of test particles skips the groups of
         // test particles; a warp holding test particles runs the groups that
         // hold test particles through the NEAR loop, which masks their pairs
-        const bool tp2 = a.n_big >= 0;
+        constexpr bool tp2 = TP;  // the kernel instantiated for test-particle mode 2 (n_big >= 0)
         const int32_t tflag = tp2 ? s_gf[slot * (NG + 4) + NG] : GENGA_GROUP_BIG;
         const bool tile_skip = tp2 && !(wflag & GENGA_GROUP_BIG) && !(tflag & GENGA_GROUP_BIG);
         // a warp of both kinds against a tile of test particles: every pair of
@@ -487,7 +488,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
         // every group box, so its gap is smaller and its bound larger)
         const bool tile_far =
             !tile_mixed && far_pair_of_boxes(wbox, Box{s_tb[2 * slot], s_tb[2 * slot + 1]}, true);
-        for (int g = 0; g < (tile_skip ? 0 : NG); g++) {
+        for (int g = 0; g < NG; g++) {
+            if (tile_skip) break;
             const int32_t gflag = tp2 ? s_gf[slot * (NG + 4) + g] : GENGA_GROUP_BIG;
             if (tp2 && !(wflag & GENGA_GROUP_BIG) && !(gflag & GENGA_GROUP_BIG)) continue;  // no pair interacts
             const bool masked = tile_mixed && (wflag & GENGA_GROUP_TP) && (gflag & GENGA_GROUP_TP);
@@ -557,7 +559,10 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                 }
             } else {
                 // NEAR group: hi/lo offsets, every pair screened; sums into sx, sy, sz
-                auto near_group = [&](float(&sx)[BPT], float(&sy)[BPT], float(&sz)[BPT]) {
+                // MASK: the group and the warp both hold test particles (mode 2):
+                // pairs of two test particles are skipped pair by pair
+                auto near_group = [&](auto mask_tag, float(&sx)[BPT], float(&sy)[BPT], float(&sz)[BPT]) {
+                    constexpr bool MASK = decltype(mask_tag)::value;
                     const float4 *tl = s_lo + slot * TILE + g * 64;
                     float xl[BPT], yl[BPT], zl[BPT], thr[BPT];
                     unsigned itp = 0u;  // bit k: i_k is a test particle (masked groups only)
@@ -567,7 +572,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                         const float2 sc = s_iscr[k * NC + tid];
                         xl[k] = l.x; yl[k] = l.y; zl[k] = l.z;
                         thr[k] = screen_threshold(sc.x, sc.y, gb.lo.w, gb.hi.w);
-                        itp |= (unsigned)(masked && l.w != 0.f) << k;
+                        if constexpr (MASK) itp |= (unsigned)(l.w != 0.f) << k;
                     }
 #pragma unroll 2
                     for (int jj = 0; jj < 64; jj++) {
@@ -587,7 +592,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                             const float dz = (jz - ival<IPACK>(ZI, k)) + (pl.z - zl[k]);
                             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                             const float ri = rsqrt_sfu(r2);
-                            const bool skip = (itp >> k & 1u) && pl.w != 0.f;  // two test particles
+                            bool skip = false;
+                            if constexpr (MASK) skip = (itp >> k & 1u) && pl.w != 0.f;  // two test particles
                             const bool near = r2 < thr[k] && !skip;
                             screened |= (unsigned)near << k;
                             const float sf = (near || skip) ? 0.f : (jw * ri) * (ri * ri);
@@ -637,7 +643,10 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                     float nx[BPT], ny[BPT], nz[BPT];
 #pragma unroll
                     for (int k = 0; k < BPT; k++) nx[k] = ny[k] = nz[k] = 0.f;
-                    near_group(nx, ny, nz);
+                    if (masked)
+                        near_group(std::true_type{}, nx, ny, nz);
+                    else
+                        near_group(std::false_type{}, nx, ny, nz);
 #pragma unroll
                     for (int q = 0; q < NP; q++) {
                         TX[q] = add2(TX[q], pk2(nx[2 * q], nx[2 * q + 1]));
@@ -645,7 +654,10 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                         TZ[q] = add2(TZ[q], pk2(nz[2 * q], nz[2 * q + 1]));
                     }
                 } else {
-                    near_group(ax, ay, az);
+                    if (masked)
+                        near_group(std::true_type{}, ax, ay, az);
+                    else
+                        near_group(std::false_type{}, ax, ay, az);
                 }
             }
         }
@@ -1036,10 +1048,19 @@ struct F32Variant {
     int bpt, cw, minb, stages;  // bodies per thread, consumer warps, resident CTAs per SM, ring depth
     void (*fn)(const PassArgs, const SingleItems);
     void (*fnb)(const PassArgs, const BatchPolicy);
+    void (*fn_tp)(const PassArgs, const SingleItems);  // test-particle mode 2 instantiations
+    void (*fnb_tp)(const PassArgs, const BatchPolicy);
 };
-#define GENGA_F32V(IP, BPT, CW, MINB, UNR, ST)                                                    \
-    {IP, BPT, CW, MINB, ST, pass_fp32_kernel<BPT, CW, F32_TILE, ST, MINB, UNR, IP, SingleItems>, \
-     pass_fp32_kernel<BPT, CW, F32_TILE, ST, MINB, UNR, IP, BatchPolicy>}
+#define GENGA_F32V(IP, BPT, CW, MINB, UNR, ST)                                                           \
+    {IP,                                                                                                 \
+     BPT,                                                                                                \
+     CW,                                                                                                 \
+     MINB,                                                                                               \
+     ST,                                                                                                 \
+     pass_fp32_kernel<BPT, CW, F32_TILE, ST, MINB, UNR, IP, SingleItems, false>,                        \
+     pass_fp32_kernel<BPT, CW, F32_TILE, ST, MINB, UNR, IP, BatchPolicy, false>,                        \
+     pass_fp32_kernel<BPT, CW, F32_TILE, ST, MINB, UNR, IP, SingleItems, true>,                         \
+     pass_fp32_kernel<BPT, CW, F32_TILE, ST, MINB, UNR, IP, BatchPolicy, true>}
 const F32Variant kF32Variants[] = {
     GENGA_F32V(true, 2, 8, 2, 4, 4), GENGA_F32V(true, 2, 4, 4, 8, 3),  GENGA_F32V(true, 2, 4, 4, 4, 3),
     GENGA_F32V(true, 2, 8, 2, 4, 3), GENGA_F32V(true, 2, 8, 2, 8, 4),  GENGA_F32V(false, 2, 8, 2, 8, 4),
@@ -1158,6 +1179,10 @@ cudaError_t init_pass_kernels() {
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(kF32Variants[q].fnb, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kF32Variants[q].fn_tp, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kF32Variants[q].fnb_tp, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e != cudaSuccess) return e;
     }
     return cudaFuncSetAttribute(pass_fp64_kernel<F64_BPT, F64_TILE, F64_STAGES>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fp64());
@@ -1170,7 +1195,7 @@ cudaError_t launch_pass(const PassArgs &a0, int precision, int variant, int grid
         cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s);
         if (e != cudaSuccess) return e;
         const F32Variant &v = kF32Variants[variant];
-        v.fn<<<grid, (v.cw + 1) * 32, smem_fp32(v.ipack, v.stages), s>>>(a, SingleItems{});
+        (a.n_big >= 0 ? v.fn_tp : v.fn)<<<grid, (v.cw + 1) * 32, smem_fp32(v.ipack, v.stages), s>>>(a, SingleItems{});
     } else {
         a.ntiles = a.npad / F64_TILE;
         auto k = pass_fp64_kernel<F64_BPT, F64_TILE, F64_STAGES>;
@@ -1193,7 +1218,7 @@ cudaError_t launch_pass_batched(const PassArgs &a0, const BatchBodies &bb, const
     BatchPolicy pol;
     pol.bb = bb;
     pol.bi = bi;
-    v.fnb<<<grid, (v.cw + 1) * 32, smem_fp32(v.ipack, v.stages), s>>>(a, pol);
+    (a.n_big >= 0 ? v.fnb_tp : v.fnb)<<<grid, (v.cw + 1) * 32, smem_fp32(v.ipack, v.stages), s>>>(a, pol);
     return cudaGetLastError();
 }
 
