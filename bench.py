@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip timing every FP32 variant")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-disc batched workload")
     ap.add_argument("--batched-steps", type=int, default=5)
+    ap.add_argument("--no-tp2", action="store_true", help="skip the test-particle-mode-2 kicks on giants100k")
     ap.add_argument("--conservation", default=None,
                     help="instead of the benchmark: energy and angular-momentum drift of FP32 vs FP64 runs, "
                          "comma-separated workload:steps:sample_every (e.g. embryo6625:20000:1000,giants100k:100:10)")
@@ -270,6 +271,41 @@ def run_batched(g, torch, dev, stream, flush, args, rank, ws=1, dist=None):
                              "how": "genga_step_batched(.., 4): one captured CUDA graph per 4-step block"}}
 
 
+# ----------------------------------------------------------------- TP2 ----
+def run_tp2(g, torch, dev, stream, flush):
+    """giants100k (4 giants + 100,000 planetesimals): the FP32 kick with every
+    pair against test-particle mode 2 (planetesimals feel the giants only,
+    the paper's setting for its giant-planet runs), and the FP64 mode-2 kick."""
+    from paper_2309_08217_gb300 import discs
+    d = discs.workload("giants100k")
+    ctx = g.Context(d.N, dev.index)
+    out = {"workload": "giants100k: 4 giants + 100,000 planetesimals (35 Earth masses) on 16-30 au, dt = 36.5 d",
+           "n_big": 4}
+    try:
+        for label, nb, prec in (("fp32_all_pairs", -1, g.GENGA_FP32), ("fp32_tp2", 4, g.GENGA_FP32),
+                                ("fp64_tp2", 4, g.GENGA_FP64)):
+            p = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=prec, n_big=nb)
+            s = g.DeviceSystem.from_disc(d, device=dev)
+            for _ in range(3):
+                g.genga_kick(ctx, s, p, 0.0, None)
+            K = 5
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            torch.cuda.synchronize(dev)
+            for k in range(K):
+                flush.zero_()
+                evs[k][0].record(stream)
+                g.genga_kick(ctx, s, p, 0.0, None)
+                evs[k][1].record(stream)
+            torch.cuda.synchronize(dev)
+            if g.genga_get_status(ctx) != g.GENGA_OK:
+                raise RuntimeError("device status after the mode-2 kicks")
+            out[label + "_kick_ms"] = sum(a.elapsed_time(b) for a, b in evs) / K
+    finally:
+        ctx.close()
+    out["tp2_speedup_fp32"] = out["fp32_all_pairs_kick_ms"] / out["fp32_tp2_kick_ms"]
+    return out
+
+
 # --------------------------------------------------------------- genga ----
 def run_genga(args):
     import numpy as np
@@ -434,6 +470,8 @@ def run_genga(args):
     if not args.no_batched:
         batched = run_batched(g, torch, dev, stream, flush, args, rank, ws, dist)
 
+    tp2 = None if args.no_tp2 else run_tp2(g, torch, dev, stream, flush)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         # acc rows of the GPU FP32 kick for the sampled bodies (accuracy of this very run)
@@ -463,6 +501,7 @@ def run_genga(args):
         "roofline": roof,
         "graph_blocks": graph,
         "batched": batched,
+        "tp2": tp2,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": kernels32,
