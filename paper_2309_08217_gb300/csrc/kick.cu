@@ -1070,6 +1070,7 @@ const F32Variant kF32Variants[] = {
 constexpr int kNumF32Variants = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 static_assert(kNumF32Variants <= GENGA_MAX_VARIANTS, "the context records tuning times of GENGA_MAX_VARIANTS variants");
 constexpr int F64_BPT = 2, F64_TILE = 128, F64_STAGES = 3;
+constexpr int F64_WAVES = 16;  // FP64 pass: j-slices so that the CTAs fill about this many waves
 
 size_t smem_fp32(bool ipack, int stages) {
     const size_t hf4 = ipack ? 2 * F32_TILE : F32_TILE;
@@ -1090,8 +1091,9 @@ size_t smem_fp64() { return (size_t)F64_STAGES * F64_TILE * sizeof(double4_32a) 
 // work as they have together; lengths stop growing at a quarter of a CTA's share of
 // the pass, and the first tier takes what is left (its first chunk made
 // shorter to fit).  split = partial rows per body; grid = resident CTAs.
-// FP64: `split` contiguous j-slices per i-block, one CTA each, sized to one
-// wave of two CTAs per SM.  In both cases split * 3 * npad partial sums
+// FP64: `split` contiguous j-slices per i-block, one CTA each, sized to
+// F64_WAVES waves of two CTAs per SM (one wave left the SMs holding a second
+// CTA to finish alone).  In both cases split * 3 * npad partial sums
 // (8 bytes each) fit in partial_cap.
 int num_fp32_variants() { return kNumF32Variants; }
 
@@ -1119,7 +1121,7 @@ void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_c
     if (precision != GENGA_FP32) {
         const int ntiles = npad / F64_TILE, iblocks = (npad + KB * F64_BPT - 1) / (KB * F64_BPT);
         const int nA = plan_tp2(N, iblocks, KB * F64_BPT, F64_TILE, a);
-        int sp = 2 * sm_count / nA;
+        int sp = (F64_WAVES * 2 * sm_count + nA - 1) / nA;  // several waves of 2 CTAs per SM: even end
         sp = sp > ntiles ? ntiles : sp;
         sp = sp > cap ? cap : sp;
         a->split = sp < 1 ? 1 : sp;
