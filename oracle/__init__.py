@@ -73,6 +73,12 @@ def _load():
             "oracle_drift": ([i] + [_dp] * 7 + [d, d, d, i], i),
             "oracle_step": ([i] + [_dp] * 7 + [d] * 5 + [i, i, i, i, i], i),
             "oracle_energy": ([i] + [_dp] * 7 + [d, d, i, _dp], None),
+            "oracle_groups": ([i, C.c_int64, _i32p, _i32p], i),
+            "oracle_bs_acc": ([i, _i32p] + [_dp] * 6 + [d, d, d, i, i, i, _dp], None),
+            "oracle_bs_group": ([i, _i32p] + [_dp] * 9 + [d, d, d, i, i, i, d, d], i),
+            "oracle_drift_groups": ([i] + [_dp] * 9 + [C.c_int64, _i32p, d, d, d, i, i, i, d, d, i,
+                                                       C.POINTER(C.c_int)], i),
+            "oracle_step_bs": ([i] + [_dp] * 7 + [d] * 5 + [i, i, i, i, d, i, C.POINTER(C.c_int)], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -192,11 +198,72 @@ def drift(arrs, G, Mstar, dt, max_iter=50):
                                     int(max_iter)))
 
 
-def step(arrs, G, Mstar, dt, n1, n2, mode, form, nsteps, max_iter=50, n_big=-1):
-    """nsteps of kick(dt/2) drift(dt) kick(dt/2), in place."""
+def step(arrs, G, Mstar, dt, n1, n2, mode, form, nsteps, max_iter=50, n_big=-1, bs_tol=0.0,
+         forced=None):
+    """nsteps of kick(dt/2) drift(dt) kick(dt/2), in place.  bs_tol > 0: the
+    drift integrates the encounter groups of each step's first kick with the
+    Bulirsch-Stoer level at that tolerance (forced: optional one-element list
+    that accumulates the forced acceptances).  Returns the Kepler cap count."""
     x, y, z, vx, vy, vz, m = arrs
-    return int(_load().oracle_step(len(m), *map(_p, (x, y, z, vx, vy, vz, m)), G, Mstar, dt,
-                                   n1, n2, int(mode), int(form), int(n_big), int(max_iter), int(nsteps)))
+    if bs_tol <= 0.0:
+        return int(_load().oracle_step(len(m), *map(_p, (x, y, z, vx, vy, vz, m)), G, Mstar, dt,
+                                       n1, n2, int(mode), int(form), int(n_big), int(max_iter),
+                                       int(nsteps)))
+    f = C.c_int(0)
+    bad = int(_load().oracle_step_bs(len(m), *map(_p, (x, y, z, vx, vy, vz, m)), G, Mstar, dt,
+                                     n1, n2, int(mode), int(form), int(n_big), int(max_iter),
+                                     float(bs_tol), int(nsteps), C.byref(f)))
+    if forced is not None:
+        forced[0] += f.value
+    return bad
+
+
+# ------------------------------------------- close-encounter level, Sect. 1
+def groups(N, pairs):
+    """Connected components of the encounter pairs: label[v] = smallest body
+    of v's group, -1 for bodies in no pair; returns (label, number of groups)."""
+    pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    label = np.zeros(max(N, 1), np.int32)
+    ng = _load().oracle_groups(int(N), len(pairs), pairs.ctypes.data_as(_i32p),
+                               label.ctypes.data_as(_i32p))
+    return label[:N], int(ng)
+
+
+def bs_acc(x, y, z, m, a, rc, members, G, Mstar, n1, mode, form, n_big=-1):
+    """Level-1 acceleration of each member of a group: the central body plus
+    the (1 - K) part of the members' pair forces; shape (3, len(members))."""
+    mem = np.ascontiguousarray(np.asarray(members, dtype=np.int32))
+    out = np.zeros(3 * max(len(mem), 1))
+    _load().oracle_bs_acc(len(mem), mem.ctypes.data_as(_i32p), *map(_p, map(_f64, (x, y, z, m, a, rc))),
+                          G, Mstar, n1, int(mode), int(form), int(n_big), _p(out))
+    return out[: 3 * len(mem)].reshape(-1, 3).T.copy()
+
+
+def bs_group(arrs, members, a, rc, G, Mstar, n1, mode, form, dt, tol, n_big=-1):
+    """Bulirsch-Stoer integration of one group (ascending body indices) over
+    dt under the central body and the (1 - K) part of the members' pair
+    forces, in place; returns 1 if an acceptance was forced, else 0."""
+    x, y, z, vx, vy, vz, m = arrs
+    mem = np.ascontiguousarray(np.asarray(members, dtype=np.int32))
+    a, rc = _f64(a), _f64(rc)
+    return int(_load().oracle_bs_group(len(mem), mem.ctypes.data_as(_i32p),
+                                       *map(_p, (x, y, z, vx, vy, vz, m, a, rc)), G, Mstar, n1,
+                                       int(mode), int(form), int(n_big), float(dt), float(tol)))
+
+
+def drift_groups(arrs, a, rc, pairs, G, Mstar, n1, mode, form, dt, tol, n_big=-1, max_iter=50):
+    """HC(dt/2); Kepler for bodies outside the groups of `pairs`, the
+    Bulirsch-Stoer level for each group; HC(dt/2).  In place; returns
+    (Kepler cap count, groups with a forced acceptance)."""
+    x, y, z, vx, vy, vz, m = arrs
+    pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    a, rc = _f64(a), _f64(rc)
+    f = C.c_int(0)
+    bad = int(_load().oracle_drift_groups(len(m), *map(_p, (x, y, z, vx, vy, vz, m, a, rc)),
+                                          len(pairs), pairs.ctypes.data_as(_i32p), G, Mstar, n1,
+                                          int(mode), int(form), int(n_big), float(dt), float(tol),
+                                          int(max_iter), C.byref(f)))
+    return bad, f.value
 
 
 def energy(arrs, G, Mstar, n_big=-1):

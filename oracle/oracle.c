@@ -16,6 +16,10 @@
  *                         a_i = sum_{j!=i} G m_j K (x_j - x_i) / |x_j - x_i|^3
  *   encounter pairs       Sect. 1 (pairs inside the changeover radius)
  *   Kepler drift          Sect. 1 (always FP64): universal-variable f and g
+ *   close-encounter level Sect. 1 (level 1 of the hybrid integrator): the
+ *                         connected groups of encounter pairs are integrated
+ *                         over the drift with a Bulirsch-Stoer method under the
+ *                         central body and the (1 - K) part of their mutual forces
  *   energy / ang. mom.    Sect. 3.1: dE/E = E(t)/E0 - 1, dL/L = L(t)/L0 - 1
  *
  * Readings where the paper is silent (each one is listed in the design
@@ -29,8 +33,10 @@
  * K(y) = y^2/(2y^2 - 2y + 1) (form 0) or 10y^3 - 15y^4 + 6y^5 (form 1),
  * K = 0 for y <= 0 and 1 for y >= 1; an encounter is r_ij < r_crit,ij.
  *
- * Every sum over bodies is Neumaier-compensated in index order, so the
- * result does not depend on the number of OpenMP threads.
+ * Every sum over all bodies is Neumaier-compensated in index order, so the
+ * result does not depend on the number of OpenMP threads; the group forces
+ * of the close-encounter level are plain sums in index order (a group holds
+ * a few bodies).
  * Build: cc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no fast-math).
  */
 #include <math.h>
@@ -366,6 +372,312 @@ int oracle_step(int N, double *x, double *y, double *z, double *vx, double *vy, 
         oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, n_big, 0.5 * dt, ax, ay, az);
     }
     free(ax); free(ay); free(az);
+    return bad;
+}
+
+/* --------------------------------- close-encounter level (Sect. 1) ------- */
+
+/*
+ * Groups: the connected components of the graph whose edges are the
+ * encounter pairs.  label[v] = the smallest body index in v's component for
+ * every body that appears in a pair, -1 for every other body.  Plain
+ * union-find (each union hangs the larger root under the smaller one).
+ * Returns the number of groups.
+ */
+static int uf_root(int32_t *parent, int v)
+{
+    while (parent[v] != v) v = parent[v];
+    return v;
+}
+
+int oracle_groups(int N, int64_t npairs, const int32_t *pairs, int32_t *label)
+{
+    for (int v = 0; v < N; v++) label[v] = -1;
+    for (int64_t p = 0; p < npairs; p++) {
+        label[pairs[2 * p]] = pairs[2 * p];
+        label[pairs[2 * p + 1]] = pairs[2 * p + 1];
+    }
+    for (int64_t p = 0; p < npairs; p++) {
+        int ri = uf_root(label, pairs[2 * p]), rj = uf_root(label, pairs[2 * p + 1]);
+        if (ri < rj) label[rj] = ri;
+        else if (rj < ri) label[ri] = rj;
+    }
+    int ngroups = 0;
+    for (int v = 0; v < N; v++) {
+        if (label[v] < 0) continue;
+        label[v] = uf_root(label, v);   /* roots are smaller than v: already final */
+        if (label[v] == v) ngroups++;
+    }
+    return ngroups;
+}
+
+/*
+ * One group of n bodies (body indices mem[0] < mem[1] < ...).  What the
+ * Bulirsch-Stoer level integrates over the drift (the level-1 Hamiltonian
+ * of the hybrid step): every member moves about the central body
+ * (mu = G M*, as in the Kepler drift) and feels the other members through
+ * the part of their pair force the kick leaves out,
+ *   dv_i/dt = -mu x_i/|x_i|^3 + sum_{j in group} G m_j (1 - K(y_ij)) (x_j - x_i)/r_ij^3,
+ * with r_crit,ij from the a_i, r_crit,i of the step's first kick (fixed over
+ * the drift), so that kick + group force = the whole Newtonian pair force.
+ */
+typedef struct {
+    int n;
+    const int32_t *mem;
+    const double *m, *a, *rc;
+    double G, Mstar, n1;
+    int mode, form, n_big;
+} bs_group;
+
+/* State layout: s[6k + 0..2] = position, s[6k + 3..5] = velocity of member k. */
+static void bs_deriv(const bs_group *g, const double *s, double *ds)
+{
+    for (int i = 0; i < g->n; i++) {
+        const double *xi = s + 6 * i;
+        int bi = g->mem[i];
+        double r2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+        double r = sqrt(r2);
+        double c = -g->G * g->Mstar / (r2 * r);
+        double ax = c * xi[0], ay = c * xi[1], az = c * xi[2];
+        for (int j = 0; j < g->n; j++) {
+            int bj = g->mem[j];
+            if (j == i || tp_pair(g->n_big, bi, bj)) continue;
+            const double *xj = s + 6 * j;
+            double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
+            double q2 = dx * dx + dy * dy + dz * dz;
+            if (q2 == 0.0) continue;
+            double q = sqrt(q2);
+            double rcij = oracle_pair_rcrit(g->mode, g->m[bi], g->m[bj], g->a[bi], g->a[bj],
+                                            g->rc[bi], g->rc[bj], g->n1, g->Mstar);
+            if (q >= rcij) continue;                  /* K = 1: all of it is in the kick */
+            double w = 1.0 - oracle_changeover((q / rcij - 0.1) / 0.9, g->form);
+            double f = g->G * g->m[bj] * w / (q2 * q);
+            ax += f * dx;
+            ay += f * dy;
+            az += f * dz;
+        }
+        double *d = ds + 6 * i;
+        d[0] = xi[3]; d[1] = xi[4]; d[2] = xi[5];
+        d[3] = ax;    d[4] = ay;    d[5] = az;
+    }
+}
+
+/* The level-1 acceleration of each member of a group (bs_deriv's velocity
+ * half) at the given state: acc[3k + c] for member k. */
+void oracle_bs_acc(int n, const int32_t *mem, const double *x, const double *y, const double *z,
+                   const double *m, const double *a, const double *rc, double G, double Mstar,
+                   double n1, int mode, int form, int n_big, double *acc)
+{
+    bs_group g = {n, mem, m, a, rc, G, Mstar, n1, mode, form, n_big};
+    double *s = (double *)calloc((size_t)(6 * n > 0 ? 6 * n : 1), sizeof(double));
+    double *ds = (double *)calloc((size_t)(6 * n > 0 ? 6 * n : 1), sizeof(double));
+    for (int k = 0; k < n; k++) {
+        s[6 * k] = x[mem[k]]; s[6 * k + 1] = y[mem[k]]; s[6 * k + 2] = z[mem[k]];
+    }
+    bs_deriv(&g, s, ds);
+    for (int k = 0; k < n; k++)
+        for (int c = 0; c < 3; c++) acc[3 * k + c] = ds[6 * k + 3 + c];
+    free(s);
+    free(ds);
+}
+
+/*
+ * Modified midpoint rule (Gragg) over a sub-step h with nsub steps of
+ * H = h/nsub from y0 (f0 = f(y0)):
+ *   z_0 = y0,  z_1 = z_0 + H f(z_0),  z_{k+1} = z_{k-1} + 2H f(z_k),
+ *   result = (z_nsub + z_{nsub-1} + H f(z_nsub)) / 2,
+ * whose error expands in even powers of H (what the extrapolation removes).
+ */
+static void bs_midpoint(const bs_group *g, const double *y0, const double *f0, double h, int nsub,
+                        double *out, double *zp, double *zc, double *zn, double *fz)
+{
+    int L = 6 * g->n;
+    double H = h / nsub;
+    for (int q = 0; q < L; q++) { zp[q] = y0[q]; zc[q] = y0[q] + H * f0[q]; }
+    for (int k = 1; k < nsub; k++) {
+        bs_deriv(g, zc, fz);
+        for (int q = 0; q < L; q++) zn[q] = zp[q] + 2.0 * H * fz[q];
+        for (int q = 0; q < L; q++) { zp[q] = zc[q]; zc[q] = zn[q]; }
+    }
+    bs_deriv(g, zc, fz);
+    for (int q = 0; q < L; q++) out[q] = 0.5 * (zc[q] + zp[q] + H * fz[q]);
+}
+
+#define BS_KMAX 8            /* extrapolation columns: midpoint step counts 2, 4, ..., 16 */
+#define BS_GROW_COL 2        /* a sub-step accepted by column <= 2 doubles the next one */
+#define BS_MIN_FRAC 0x1p-30  /* smallest sub-step, as a fraction of the drift */
+#define BS_MAX_ATTEMPTS 4096 /* sub-step attempts per group and drift */
+
+static int bs_n(int k) { return 2 * (k + 1); }
+
+/*
+ * Bulirsch-Stoer integration of one group over dt (Stoer & Bulirsch,
+ * Introduction to Numerical Analysis, Sect. 7.2.14): each sub-step h runs the
+ * modified midpoint rule with n_k = 2, 4, ..., 16 steps and extrapolates the
+ * results to H -> 0 with the Aitken-Neville scheme in H^2,
+ *   T[k][j] = T[k][j-1] + (T[k][j-1] - T[k-1][j-1]) * n_{k-j}^2 / (n_k^2 - n_{k-j}^2).
+ * Column k (k >= 1) is accepted when, for every member,
+ *   max_c |T[k][k] - T[k][k-1]| <= tol * |x| (position) and tol * |v| (velocity)
+ * (norms of the member's state at the start of the sub-step; 1 where zero).
+ * A sub-step with no accepted column is halved; one accepted at a column
+ * <= BS_GROW_COL doubles the next.  Sub-steps are fractions of dt; a sub-step
+ * at BS_MIN_FRAC, or the last of BS_MAX_ATTEMPTS attempts (which covers the
+ * rest of dt), is accepted at the last column anyway.  Updates the members'
+ * entries of x..vz; returns 1 if such a forced acceptance happened, else 0.
+ */
+int oracle_bs_group(int n, const int32_t *mem, double *x, double *y, double *z,
+                    double *vx, double *vy, double *vz, const double *m, const double *a,
+                    const double *rc, double G, double Mstar, double n1, int mode, int form,
+                    int n_big, double dt, double tol)
+{
+    bs_group g = {n, mem, m, a, rc, G, Mstar, n1, mode, form, n_big};
+    int L = 6 * n;
+    double *buf = (double *)malloc(sizeof(double) * (size_t)L * (7 + BS_KMAX * BS_KMAX));
+    double *yv = buf, *f0 = yv + L, *zp = f0 + L, *zc = zp + L, *zn = zc + L, *fz = zn + L,
+           *sc = fz + L, *T = sc + L;       /* T[(k * BS_KMAX + j) * L + q] */
+    for (int k = 0; k < n; k++) {
+        int b = mem[k];
+        double *s = yv + 6 * k;
+        s[0] = x[b]; s[1] = y[b]; s[2] = z[b]; s[3] = vx[b]; s[4] = vy[b]; s[5] = vz[b];
+    }
+    double done = 0.0, frac = 1.0;           /* fractions of dt: exact binary values */
+    int forced = 0;
+    for (int att = 0; att < BS_MAX_ATTEMPTS && done < 1.0; att++) {
+        int last = (att == BS_MAX_ATTEMPTS - 1);
+        if (last) frac = 1.0 - done;
+        double h = frac * dt;
+        for (int k = 0; k < n; k++) {        /* error scales of this sub-step */
+            const double *s = yv + 6 * k;
+            double px = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+            double pv = sqrt(s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
+            sc[6 * k] = px > 0.0 ? px : 1.0;
+            sc[6 * k + 3] = pv > 0.0 ? pv : 1.0;
+        }
+        bs_deriv(&g, yv, f0);
+        int acc_col = -1;
+        for (int k = 0; k < BS_KMAX; k++) {
+            double *Tk0 = T + (size_t)(k * BS_KMAX) * L;
+            bs_midpoint(&g, yv, f0, h, bs_n(k), Tk0, zp, zc, zn, fz);
+            for (int j = 1; j <= k; j++) {
+                double nk = bs_n(k), nkj = bs_n(k - j);
+                double cf = (nkj * nkj) / (nk * nk - nkj * nkj);
+                double *Tkj = T + (size_t)(k * BS_KMAX + j) * L;
+                const double *Tkj1 = T + (size_t)(k * BS_KMAX + j - 1) * L;
+                const double *Tk1j1 = T + (size_t)((k - 1) * BS_KMAX + j - 1) * L;
+                for (int q = 0; q < L; q++) Tkj[q] = Tkj1[q] + (Tkj1[q] - Tk1j1[q]) * cf;
+            }
+            if (k == 0) continue;
+            const double *Tkk = T + (size_t)(k * BS_KMAX + k) * L;
+            const double *Tkm = T + (size_t)(k * BS_KMAX + k - 1) * L;
+            double err = 0.0;
+            for (int q = 0; q < L; q++) {
+                double e = fabs(Tkk[q] - Tkm[q]) / sc[6 * (q / 6) + ((q % 6) < 3 ? 0 : 3)];
+                if (e > err) err = e;
+            }
+            if (err <= tol) { acc_col = k; break; }
+        }
+        if (acc_col < 0 && (frac <= BS_MIN_FRAC || last)) {
+            acc_col = BS_KMAX - 1;              /* forced: keep the last column */
+            forced = 1;
+        }
+        if (acc_col < 0) { frac *= 0.5; continue; }
+        const double *Tacc = T + (size_t)(acc_col * BS_KMAX + acc_col) * L;
+        for (int q = 0; q < L; q++) yv[q] = Tacc[q];
+        done += frac;
+        if (acc_col <= BS_GROW_COL) frac *= 2.0;
+        if (frac > 1.0 - done) frac = 1.0 - done;
+    }
+    for (int k = 0; k < n; k++) {
+        int b = mem[k];
+        const double *s = yv + 6 * k;
+        x[b] = s[0]; y[b] = s[1]; z[b] = s[2]; vx[b] = s[3]; vy[b] = s[4]; vz[b] = s[5];
+    }
+    free(buf);
+    return forced;
+}
+
+/*
+ * Drift of the hybrid step with the close-encounter level: HC(dt/2); every
+ * body outside the groups of `pairs` (the encounter pairs of the step's
+ * first kick) on its Kepler orbit, every group by oracle_bs_group (a, rc from
+ * that kick); HC(dt/2).  Returns the number of Kepler solves that hit the
+ * cap; *bs_forced (optional) gets the number of groups with a forced
+ * Bulirsch-Stoer acceptance.
+ */
+int oracle_drift_groups(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                        const double *m, const double *a, const double *rc,
+                        int64_t npairs, const int32_t *pairs, double G, double Mstar, double n1,
+                        int mode, int form, int n_big, double dt, double tol, int max_iter,
+                        int *bs_forced)
+{
+    int bad = 0, forced = 0;
+    size_t n = (size_t)(N > 0 ? N : 1);
+    int32_t *label = (int32_t *)malloc(sizeof(int32_t) * n);
+    int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * n);
+    oracle_groups(N, npairs, pairs, label);
+    oracle_hc_drift(N, x, y, z, vx, vy, vz, m, Mstar, 0.5 * dt);
+    #pragma omp parallel for reduction(+:bad)
+    for (int i = 0; i < N; i++) {
+        if (label[i] >= 0) continue;
+        double s[6] = {x[i], y[i], z[i], vx[i], vy[i], vz[i]};
+        bad += oracle_kepler(G * Mstar, s, dt, max_iter);
+        x[i] = s[0]; y[i] = s[1]; z[i] = s[2];
+        vx[i] = s[3]; vy[i] = s[4]; vz[i] = s[5];
+    }
+    for (int r = 0; r < N; r++) {
+        if (label[r] != r) continue;         /* r is the smallest member of its group */
+        int cnt = 0;
+        for (int v = r; v < N; v++)
+            if (label[v] == r) mem[cnt++] = v;
+        forced += oracle_bs_group(cnt, mem, x, y, z, vx, vy, vz, m, a, rc, G, Mstar, n1, mode, form,
+                                  n_big, dt, tol);
+    }
+    oracle_hc_drift(N, x, y, z, vx, vy, vz, m, Mstar, 0.5 * dt);
+    if (bs_forced) *bs_forced = forced;
+    free(label);
+    free(mem);
+    return bad;
+}
+
+/*
+ * Hybrid step with the close-encounter level, repeated nsteps times:
+ * r_crit and the encounter pairs of the state, kick(dt/2), the drift of
+ * oracle_drift_groups, kick(dt/2).  Returns the Kepler cap count; *bs_forced
+ * (optional) accumulates the forced Bulirsch-Stoer acceptances.
+ */
+int oracle_step_bs(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                   const double *m, double G, double Mstar, double dt, double n1, double n2,
+                   int mode, int form, int n_big, int max_iter, double tol, int nsteps, int *bs_forced)
+{
+    int bad = 0, forced = 0;
+    size_t n = (size_t)(N > 0 ? N : 1);
+    double *ax = (double *)malloc(sizeof(double) * n);
+    double *ay = (double *)malloc(sizeof(double) * n);
+    double *az = (double *)malloc(sizeof(double) * n);
+    double *a = (double *)malloc(sizeof(double) * n);
+    double *rc = (double *)malloc(sizeof(double) * n);
+    int64_t cap = 16 * (int64_t)n;
+    int32_t *pairs = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)cap);
+    for (int s = 0; s < nsteps; s++) {
+        oracle_rcrit(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, a, rc);
+        int64_t np = oracle_encounters(N, x, y, z, m, a, rc, n1, Mstar, mode, n_big, pairs, cap,
+                                       0.0, NULL, 0, NULL);
+        if (np > cap) {                       /* grow and list again */
+            free(pairs);
+            cap = np;
+            pairs = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)cap);
+            np = oracle_encounters(N, x, y, z, m, a, rc, n1, Mstar, mode, n_big, pairs, cap,
+                                   0.0, NULL, 0, NULL);
+        }
+        oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, n_big, 0.5 * dt, ax, ay, az);
+        int f = 0;
+        bad += oracle_drift_groups(N, x, y, z, vx, vy, vz, m, a, rc, np, pairs, G, Mstar, n1, mode, form,
+                                   n_big, dt, tol, max_iter, &f);
+        forced += f;
+        oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, n_big, 0.5 * dt, ax, ay, az);
+    }
+    if (bs_forced) *bs_forced += forced;
+    free(ax); free(ay); free(az); free(a); free(rc); free(pairs);
     return bad;
 }
 

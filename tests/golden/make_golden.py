@@ -3,8 +3,9 @@
 The fixture is a 24-body disc (seed 24) with three planted close pairs:
 one at ~0.5 r_crit (changeover region), one at ~0.05 r_crit (K = 0) and
 one just outside r_crit.  It stores the oracle's critical radii, kick
-accelerations, encounter pairs and the state after one level-0 step, so a
-later change of the oracle's arithmetic shows up as a diff of this file.
+accelerations, encounter pairs and the state after one level-0 step and
+after one step with the close-encounter level, so a later change of the
+oracle's arithmetic shows up as a diff of this file.
 
 Run:  python tests/golden/make_golden.py
 """
@@ -54,6 +55,12 @@ def main():
     bad = oracle.step(st, G, M, d.dt, 3.0, 0.4, 1, 0, 1)
     out["after_one_step_mode1_form0"] = [v.tolist() for v in st]
     out["kepler_failures"] = bad
+    # the same step with the close-encounter level (Bulirsch-Stoer groups, tolerance 1e-12)
+    st = [np.array(v) for v in out["state"]]
+    forced = [0]
+    out["kepler_failures_bs"] = oracle.step(st, G, M, d.dt, 3.0, 0.4, 1, 0, 1, bs_tol=1e-12, forced=forced)
+    out["bs_forced"] = forced[0]
+    out["after_one_step_bs_mode1_form0"] = [v.tolist() for v in st]
     out["energy"] = oracle.energy([np.array(v) for v in out["state"]], G, M).tolist()
     with open(os.path.join(HERE, "oracle_disc24.json"), "w") as f:
         json.dump(out, f, indent=1)

@@ -39,3 +39,13 @@ def test_oracle_reproduces_stored_fixture():
     assert oracle.step(st, G, M, dt, 3.0, 0.4, 1, 0, 1) == 0
     for v, w in zip(st, g["after_one_step_mode1_form0"]):
         assert np.allclose(v, np.array(w), rtol=1e-13, atol=1e-18)
+    # with the close-encounter level the planted pairs (0,1), (2,3) are two groups
+    st = [np.array(v) for v in g["state"]]
+    forced = [0]
+    assert oracle.step(st, G, M, dt, 3.0, 0.4, 1, 0, 1, bs_tol=1e-12, forced=forced) == 0
+    assert forced[0] == 0 == g["bs_forced"]
+    for v, w in zip(st, g["after_one_step_bs_mode1_form0"]):
+        assert np.allclose(v, np.array(w), rtol=1e-12, atol=1e-18)
+    moved = [np.abs(np.array(u) - np.array(w)).max()
+             for u, w in zip(g["after_one_step_bs_mode1_form0"], g["after_one_step_mode1_form0"])]
+    assert max(moved) > 1e-9          # the level changes the planted pairs' motion

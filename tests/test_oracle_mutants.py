@@ -39,8 +39,8 @@ MUTANTS = {
     "kepler_g_sign": ("double g = r0 * G1 + eta * G2;", "double g = r0 * G1 - eta * G2;"),
     "kepler_fdot": ("double fd = -mu * G1 / (r * r0);", "double fd = -mu * G1 / (r0 * r0);"),
     "hc_drift_no_mass_division": ("x[i] += tau * P[0] / Mstar;", "x[i] += tau * P[0];"),
-    "drift_full_hc_halves": ("oracle_hc_drift(N, x, y, z, vx, vy, vz, m, Mstar, 0.5 * dt);\n    #pragma",
-                             "oracle_hc_drift(N, x, y, z, vx, vy, vz, m, Mstar, dt);\n    #pragma"),
+    "drift_full_hc_halves": ("Mstar, 0.5 * dt);\n    #pragma omp parallel for reduction(+:bad)\n    for (int i = 0; i < N; i++) {\n        double s[6]",
+                             "Mstar, dt);\n    #pragma omp parallel for reduction(+:bad)\n    for (int i = 0; i < N; i++) {\n        double s[6]"),
     "step_full_kick": ("mode, form, n_big, 0.5 * dt, ax, ay, az);\n        bad +=",
                        "mode, form, n_big, dt, ax, ay, az);\n        bad +="),
     "energy_sun_term": ("/ (2.0 * Mstar));", "/ (2.0));"),
@@ -51,6 +51,17 @@ MUTANTS = {
                                    "            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];\n            double r = sqrt"),
     "angular_momentum_component": ("nadd(&lz, m[i] * (x[i] * vy[i] - y[i] * vx[i]));",
                                    "nadd(&lz, m[i] * (x[i] * vy[i] + y[i] * vx[i]));"),
+    # close-encounter level
+    "groups_count_every_member": ("if (label[v] == v) ngroups++;", "ngroups++;"),
+    "level1_central_sign": ("double c = -g->G * g->Mstar / (r2 * r);", "double c = g->G * g->Mstar / (r2 * r);"),
+    "level1_weight_is_K": ("double w = 1.0 - oracle_changeover(", "double w = oracle_changeover("),
+    "level1_offset_sign": ("double dx = xj[0] - xi[0], dy", "double dx = xi[0] - xj[0], dy"),
+    "level1_mass_index": ("double f = g->G * g->m[bj] * w", "double f = g->G * g->m[bi] * w"),
+    "level1_tp_pairs_kept": ("if (j == i || tp_pair(g->n_big, bi, bj)) continue;", "if (j == i) continue;"),
+    "midpoint_step_factor": ("zn[q] = zp[q] + 2.0 * H * fz[q];", "zn[q] = zp[q] + H * fz[q];"),
+    "extrapolation_in_h_not_h2": ("double cf = (nkj * nkj) / (nk * nk - nkj * nkj);",
+                                  "double cf = nkj / (nk - nkj);"),
+    "members_also_kepler_drifted": ("        if (label[i] >= 0) continue;\n", ""),
 }
 
 
@@ -67,7 +78,8 @@ def _build(src_text, d):
 def _run_pins(so):
     env = dict(os.environ, ORACLE_LIB=so)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_bs.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return r.returncode
 
