@@ -22,8 +22,9 @@
  *   stated; argument errors are detected on the host and returned at once,
  *   before anything is enqueued.
  * - Errors found on the device (Kepler solver did not converge, encounter
- *   list overflow, non-finite accelerations, a bounded wait that gave up)
- *   are sticky bits in the context, read and cleared by genga_get_status.
+ *   list overflow, non-finite accelerations, a bounded wait that gave up, a
+ *   forced close-encounter sub-step) are sticky bits in the context, read
+ *   and cleared by genga_get_status.
  * - No entry point aborts, traps, prints or allocates device memory, except
  *   genga_create/genga_destroy (workspace).
  * - The first FP32 pass a context runs for a new size bucket (a power of two
@@ -49,7 +50,10 @@ typedef enum {
     GENGA_ERR_CAPACITY = 3,    /* encounter list overflow: list truncated, count is the true total */
     GENGA_ERR_KEPLER = 4,      /* the f/g solver hit kepler_max_iter for at least one body */
     GENGA_ERR_NONFINITE = 5,   /* a NaN or Inf acceleration was produced */
-    GENGA_ERR_TIMEOUT = 6      /* a bounded device wait gave up (the kernel returned early) */
+    GENGA_ERR_TIMEOUT = 6,     /* a bounded device wait gave up (the kernel returned early) */
+    GENGA_ERR_BS = 7           /* close-encounter level: a group's Bulirsch-Stoer integration
+                                  needed a forced sub-step, or the groups did not fit the
+                                  workspace (those bodies then got the Kepler drift) */
 } genga_status;
 
 /* Precision of the long-range kick (Sect. 1; "Do Kick in single precision", Sect. 4). */
@@ -80,6 +84,11 @@ typedef struct {
                                 other, while those feel everything -- a pair of two test
                                 particles has no force, no encounter and no potential energy;
                                 -1: every pair interacts */
+    double bs_tol;           /* close-encounter level (level 1 of the hybrid integrator, Sect. 1):
+                                > 0: genga_drift / genga_step integrate every group of
+                                encounter pairs of the preceding kick with a Bulirsch-Stoer
+                                method at this relative tolerance (1e-12 is typical);
+                                0: off, every body gets the Kepler drift */
 } genga_params;
 
 typedef struct {
@@ -92,7 +101,8 @@ typedef struct {
 typedef struct genga_ctx genga_ctx;
 
 /* Create a context on `device` with workspace for systems of up to max_N bodies
- * (about 250 bytes per body plus the encounter buffer).  *ctx is NULL on error. */
+ * (about 930 bytes per body, 660 of them the close-encounter workspace, plus
+ * the encounter buffer).  *ctx is NULL on error. */
 genga_status genga_create(genga_ctx **ctx, int32_t max_N, int32_t device);
 
 /* Free the context's workspace (synchronises its device first). NULL is a no-op. */
@@ -114,11 +124,22 @@ genga_status genga_kick(genga_ctx *ctx, const genga_system *sys, const genga_par
                         double tau, double *acc, void *stream);
 
 /*
- * Drift of the level-0 step: central-body momentum drift x_i += (dt/2) P / M*
+ * Drift of the step: central-body momentum drift x_i += (dt/2) P / M*
  * (P = sum_j m_j v_j), then the Kepler drift of every body about mu = G M* for
  * dt (always FP64, universal-variable f and g functions, Sect. 1), then the
  * momentum drift again with the updated P.  Bodies whose solver hits
  * kepler_max_iter set GENGA_ERR_KEPLER (they are still advanced).
+ *
+ * With params->bs_tol > 0 the close-encounter level replaces the Kepler drift
+ * for the members of every group: the connected components of the encounter
+ * pairs of the most recent kick on this context (genga_kick, genga_step,
+ * genga_encounters).  Each group is integrated over dt in FP64 by a
+ * Bulirsch-Stoer method (modified midpoint rule with 2, 4, ..., 16 steps,
+ * polynomial extrapolation, relative tolerance bs_tol on each member's |x|
+ * and |v|) under the central body and the (1 - K) part of the members' pair
+ * forces, with r_crit,ij of that kick, so the kick and this level together
+ * apply the whole pair force.  Pair lists of another system are ignored
+ * where their indices exceed N.
  */
 genga_status genga_drift(genga_ctx *ctx, genga_system *sys, const genga_params *params,
                          double dt, void *stream);
@@ -143,12 +164,15 @@ genga_status genga_last_encounters(genga_ctx *ctx, int32_t *pairs, int32_t capac
                                    int32_t *count, void *stream);
 
 /*
- * nsteps level-0 steps of the hybrid symplectic integrator (Sect. 1):
- * kick(dt/2), drift(dt), kick(dt/2).  The close-encounter (Bulirsch-Stoer)
- * level is not part of this library: pairs inside r_crit keep only their
- * K-weighted long-range force and are reported by genga_last_encounters.
- * The spatial order of the bodies (a performance device of the FP32 pass)
- * is rebuilt every few steps, counted across calls on the context.
+ * nsteps steps of the hybrid symplectic integrator (Sect. 1): kick(dt/2),
+ * drift(dt), kick(dt/2).  With params->bs_tol > 0 the drift integrates the
+ * groups of encounter pairs of the step's first kick on the close-encounter
+ * level (see genga_drift); with bs_tol = 0 every body gets the Kepler drift
+ * and pairs inside r_crit keep only their K-weighted force (exact for
+ * systems without encounters).  The encounter list of the last kick stays
+ * readable through genga_last_encounters.  The spatial order of the bodies
+ * (a performance device of the FP32 pass) is rebuilt every few steps,
+ * counted across calls on the context.
  */
 genga_status genga_step(genga_ctx *ctx, genga_system *sys, const genga_params *params,
                         int32_t nsteps, void *stream);

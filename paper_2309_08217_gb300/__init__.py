@@ -25,7 +25,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgenga.so")
 
 GENGA_OK, GENGA_ERR_INVALID_ARG, GENGA_ERR_CUDA, GENGA_ERR_CAPACITY = 0, 1, 2, 3
-GENGA_ERR_KEPLER, GENGA_ERR_NONFINITE, GENGA_ERR_TIMEOUT = 4, 5, 6
+GENGA_ERR_KEPLER, GENGA_ERR_NONFINITE, GENGA_ERR_TIMEOUT, GENGA_ERR_BS = 4, 5, 6, 7
 GENGA_FP64, GENGA_FP32 = 0, 1
 GENGA_RCRIT_EQ1, GENGA_RCRIT_MUTUAL_HILL = 0, 1
 GENGA_K_CHAMBERS, GENGA_K_QUINTIC = 0, 1
@@ -35,7 +35,8 @@ class genga_params(C.Structure):
     _fields_ = [("G", C.c_double), ("Mstar", C.c_double), ("dt", C.c_double),
                 ("n1", C.c_double), ("n2", C.c_double),
                 ("rcrit_mode", C.c_int32), ("changeover", C.c_int32),
-                ("precision", C.c_int32), ("kepler_max_iter", C.c_int32), ("n_big", C.c_int32)]
+                ("precision", C.c_int32), ("kepler_max_iter", C.c_int32), ("n_big", C.c_int32),
+                ("bs_tol", C.c_double)]
 
 
 class genga_system(C.Structure):
@@ -121,9 +122,12 @@ def _stream(stream):
 
 
 def make_params(G, Mstar=1.0, dt=6.0, n1=3.0, n2=0.4, rcrit_mode=GENGA_RCRIT_MUTUAL_HILL,
-                changeover=GENGA_K_CHAMBERS, precision=GENGA_FP32, kepler_max_iter=50, n_big=-1) -> genga_params:
-    """n_big >= 0: test-particle mode 2 (bodies n_big.. feel the first n_big bodies, not each other)."""
-    return genga_params(G, Mstar, dt, n1, n2, rcrit_mode, changeover, precision, kepler_max_iter, n_big)
+                changeover=GENGA_K_CHAMBERS, precision=GENGA_FP32, kepler_max_iter=50, n_big=-1,
+                bs_tol=0.0) -> genga_params:
+    """n_big >= 0: test-particle mode 2 (bodies n_big.. feel the first n_big bodies, not each other).
+    bs_tol > 0: the drift integrates the close-encounter groups (Bulirsch-Stoer, that tolerance)."""
+    return genga_params(G, Mstar, dt, n1, n2, rcrit_mode, changeover, precision, kepler_max_iter, n_big,
+                        bs_tol)
 
 
 class DeviceSystem:

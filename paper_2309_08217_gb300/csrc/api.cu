@@ -38,6 +38,7 @@ genga_status check_params(const genga_params *p) {
     if (p->precision != GENGA_FP64 && p->precision != GENGA_FP32) return GENGA_ERR_INVALID_ARG;
     if (p->kepler_max_iter < 1) return GENGA_ERR_INVALID_ARG;
     if (p->n_big < -1) return GENGA_ERR_INVALID_ARG;
+    if (!is_fin(p->bs_tol) || p->bs_tol < 0.0) return GENGA_ERR_INVALID_ARG;
     return GENGA_OK;
 }
 
@@ -343,8 +344,14 @@ unsigned long long step_key(const genga_system &sys, const genga_params &p, int 
     const double *arrs[7] = {sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, sys.m};
     for (const double *a : arrs) h = mix(h, (unsigned long long)(uintptr_t)a);
     h = mix(h, (unsigned long long)sys.N);
-    const unsigned char *pb = reinterpret_cast<const unsigned char *>(&p);
-    for (size_t k = 0; k < sizeof(p); k++) h = mix(h, pb[k]);
+    const double dv[6] = {p.G, p.Mstar, p.dt, p.n1, p.n2, p.bs_tol};  // fields, not the struct's padding
+    for (double d : dv) {
+        unsigned long long bits;
+        memcpy(&bits, &d, sizeof(bits));
+        h = mix(h, bits);
+    }
+    const int32_t iv[5] = {p.rcrit_mode, p.changeover, p.precision, p.kepler_max_iter, p.n_big};
+    for (int32_t v : iv) h = mix(h, (unsigned long long)(uint32_t)v);
     h = mix(h, (unsigned long long)(variant + 1));
     return mix(h, layout);
 }
@@ -402,6 +409,7 @@ const char *genga_status_string(genga_status s) {
         case GENGA_ERR_KEPLER: return "Kepler solver did not converge for at least one body";
         case GENGA_ERR_NONFINITE: return "non-finite acceleration";
         case GENGA_ERR_TIMEOUT: return "bounded device wait timed out";
+        case GENGA_ERR_BS: return "close-encounter level: forced Bulirsch-Stoer sub-step or groups over capacity";
     }
     return "unknown status";
 }
@@ -416,7 +424,9 @@ void genga_destroy(genga_ctx *c) {
     void *bufs[] = {c->pk_hi,       c->pk_t,        c->pk_d,        c->pk_lo,       c->pk64,        c->scr,      c->gbox_lo,    c->gbox_hi,    c->gflag,
                     c->perm,        c->ord_keys[0], c->ord_keys[1], c->ord_vals[0], c->ord_vals[1], c->ord_hist,
                     c->ord_rbits,   c->a_osc,       c->rc_eq1,      c->partial,  c->mom,        c->enc,
-                    c->enc_count,   c->status,      c->energy_part, c->work,   c->Pd,         c->Pd_part};
+                    c->enc_count,   c->status,      c->energy_part, c->work,   c->Pd,         c->Pd_part,
+                    c->grp,         c->gmark,       c->gslot,       c->iperm,  c->gbody,      c->gmem,
+                    c->gstart,      c->gsize,       c->gcur,        c->gcount, c->bs_tp,      c->bs_work};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete c;
@@ -486,6 +496,24 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     if (e == cudaSuccess) e = alloc(&c->enc_count, 1);
     if (e == cudaSuccess) e = alloc(&c->status, 1);
     if (e == cudaSuccess) e = alloc(&c->energy_part, (size_t)4 * c->energy_blocks);
+    // close-encounter level: labels and marks start cleared (-1 / 0) and are
+    // cleared again by the level-1 kernel for every member it moves
+    c->bs_slots = np < GENGA_BS_MAX_SLOTS ? np : GENGA_BS_MAX_SLOTS;
+    if (e == cudaSuccess) e = alloc(&c->grp, np);
+    if (e == cudaSuccess) e = alloc(&c->gmark, np);
+    if (e == cudaSuccess) e = alloc(&c->gslot, np);
+    if (e == cudaSuccess) e = alloc(&c->iperm, np);
+    if (e == cudaSuccess) e = alloc(&c->gbody, c->bs_slots);
+    if (e == cudaSuccess) e = alloc(&c->gmem, c->bs_slots);
+    if (e == cudaSuccess) e = alloc(&c->gstart, c->bs_slots);
+    if (e == cudaSuccess) e = alloc(&c->gsize, c->bs_slots);
+    if (e == cudaSuccess) e = alloc(&c->gcur, c->bs_slots);
+    if (e == cudaSuccess) e = alloc(&c->gcount, 1);
+    if (e == cudaSuccess) e = alloc(&c->bs_tp, c->bs_slots);
+    if (e == cudaSuccess) e = alloc(&c->bs_work, (size_t)GENGA_BS_FIELDS * c->bs_slots);
+    if (e == cudaSuccess) e = cudaMemset(c->grp, 0xff, sizeof(int32_t) * (size_t)np);
+    if (e == cudaSuccess) e = cudaMemset(c->gmark, 0, sizeof(int32_t) * (size_t)np);
+    if (e == cudaSuccess) e = cudaMemset(c->gcount, 0, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->enc_count, 0, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -516,7 +544,7 @@ genga_status genga_drift(genga_ctx *c, genga_system *sys, const genga_params *p,
     if (!is_fin(dt)) return GENGA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     genga_system s2 = *sys;
-    if (sys->N > 0) c->launches += 4;
+    if (sys->N > 0) c->launches += p->bs_tol > 0.0 ? 6 : 4;
     return launch_drift(s2, *p, dt, c, (cudaStream_t)stream) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
 }
 
@@ -571,7 +599,7 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
     auto one_step = [&](cudaStream_t q) -> cudaError_t {
         cudaError_t e = run_kick(c, s2, *p, h, nullptr, false, q);
         if (e == cudaSuccess) e = launch_drift(s2, *p, p->dt, c, q);
-        c->launches += 4;
+        c->launches += p->bs_tol > 0.0 ? 6 : 4;
         c->steps_since_order++;
         const bool reorder = c->steps_since_order >= GENGA_REORDER_STEPS;
         if (e == cudaSuccess) e = run_kick(c, s2, *p, h, nullptr, reorder, q, true);
@@ -639,7 +667,7 @@ genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *
     auto one_step = [&](cudaStream_t q) -> cudaError_t {
         cudaError_t e = run_kick_batched(c, a2, offsets, D, *p, h, nullptr, false, false, q);
         if (e == cudaSuccess) e = launch_drift_batched(a2, bb, *p, p->dt, c, q);
-        c->launches += 4;
+        c->launches += p->bs_tol > 0.0 ? 6 : 4;
         c->steps_since_order++;
         const bool reorder = c->steps_since_order >= GENGA_REORDER_STEPS;
         if (e == cudaSuccess) e = run_kick_batched(c, a2, offsets, D, *p, h, nullptr, reorder, true, q);
@@ -727,7 +755,7 @@ genga_status genga_get_status(genga_ctx *c, void *stream) {
     if (e == cudaSuccess) e = cudaMemcpy(&bits, c->status, sizeof(bits), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(bits));
     if (e != cudaSuccess) return GENGA_ERR_CUDA;
-    for (int code = 1; code <= 6; code++)
+    for (int code = 1; code <= 7; code++)
         if (bits & GENGA_BIT(code)) return (genga_status)code;
     return GENGA_OK;
 }

@@ -1,8 +1,10 @@
-// drift.cu -- the drift of the level-0 step, always in FP64 (Sect. 1):
+// drift.cu -- the drift of the hybrid step, always in FP64 (Sect. 1):
 //
 //   x_i += (dt/2) P / M*               central-body momentum drift, P = sum m v
-//   (x_i, v_i) <- Kepler(mu = G M*, dt) two-body drift of every body
-//   x_i += (dt/2) P' / M*              with the momentum after the Kepler drift
+//   (x_i, v_i) <- Kepler(mu = G M*, dt) two-body drift of every body outside
+//                                      the close-encounter groups (those move
+//                                      on level 1, encounter.cu, when enabled)
+//   x_i += (dt/2) P' / M*              with the momentum after the drift
 //
 // The Kepler drift uses universal variables: Kepler's equation in the
 // universal anomaly s,
@@ -131,16 +133,22 @@ __device__ bool kepler_drift(double mu, double dt, int max_iter, double &x, doub
     return ok;
 }
 
-// x += (h / M*) P, then the Kepler drift over dt.
+// x += (h / M*) P, then the Kepler drift over dt, except for members of a
+// close-encounter group (grp[i] >= 0; grp may be NULL), which the
+// close-encounter level moves instead.
 __global__ void drift_kernel(double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
                              double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz, int N,
                              const double *__restrict__ P, double hM, double mu, double dt,
-                             int max_iter, uint32_t *__restrict__ status) {
+                             int max_iter, uint32_t *__restrict__ status, const int32_t *__restrict__ grp) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     double xi = fma(hM, P[0], x[i]);
     double yi = fma(hM, P[1], y[i]);
     double zi = fma(hM, P[2], z[i]);
+    if (grp && grp[i] >= 0) {
+        x[i] = xi; y[i] = yi; z[i] = zi;
+        return;
+    }
     double ui = vx[i], vi = vy[i], wi = vz[i];
     if (!kepler_drift(mu, dt, max_iter, xi, yi, zi, ui, vi, wi)) atomicOr(status, GENGA_BIT(GENGA_ERR_KEPLER));
     x[i] = xi; y[i] = yi; z[i] = zi;
@@ -161,13 +169,17 @@ __global__ void drift_batched_kernel(double *__restrict__ x, double *__restrict_
                                      double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
                                      const double *__restrict__ Pd, double hM, double mu, double dt,
                                      int max_iter, uint32_t *__restrict__ status,
-                                     const __grid_constant__ BatchBodies bb) {
+                                     const int32_t *__restrict__ grp, const __grid_constant__ BatchBodies bb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= bb.N_total) return;
     const double *P = Pd + 3 * find_segment(bb.off, bb.D, i);
     double xi = fma(hM, P[0], x[i]);
     double yi = fma(hM, P[1], y[i]);
     double zi = fma(hM, P[2], z[i]);
+    if (grp && grp[i] >= 0) {
+        x[i] = xi; y[i] = yi; z[i] = zi;
+        return;
+    }
     double ui = vx[i], vi = vy[i], wi = vz[i];
     if (!kepler_drift(mu, dt, max_iter, xi, yi, zi, ui, vi, wi)) atomicOr(status, GENGA_BIT(GENGA_ERR_KEPLER));
     x[i] = xi; y[i] = yi; z[i] = zi;
@@ -187,15 +199,72 @@ __global__ void hc_batched_kernel(double *__restrict__ x, double *__restrict__ y
 
 }  // namespace
 
+// The close-encounter level around the Kepler drift: groups before it (so
+// that it skips their members), the level-1 integration after it.  N bodies
+// of the caller's arrays `sys` (all systems of a batch).
+cudaError_t launch_level1_groups(const genga_system &sys, genga_ctx *c, cudaStream_t s) {
+    GroupArgs g;
+    g.enc = c->enc;
+    g.enc_count = c->enc_count;
+    g.enc_cap = c->enc_cap;
+    g.N = sys.N;
+    g.slots = c->bs_slots;
+    g.grp = c->grp;
+    g.gmark = c->gmark;
+    g.gslot = c->gslot;
+    g.gbody = c->gbody;
+    g.gmem = c->gmem;
+    g.gstart = c->gstart;
+    g.gsize = c->gsize;
+    g.gcur = c->gcur;
+    g.gcount = c->gcount;
+    g.status = c->status;
+    return launch_groups(g, s);
+}
+
+cudaError_t launch_level1(genga_system &sys, const genga_params &p, double dt, genga_ctx *c, cudaStream_t s) {
+    BSArgs b;
+    b.x = sys.x; b.y = sys.y; b.z = sys.z;
+    b.vx = sys.vx; b.vy = sys.vy; b.vz = sys.vz;
+    b.m = sys.m;
+    b.iperm = c->iperm;
+    b.a_osc = c->a_osc;
+    b.rc_eq1 = c->rc_eq1;
+    b.lo = c->pk_lo;
+    b.gcount = c->gcount;
+    b.gstart = c->gstart;
+    b.gsize = c->gsize;
+    b.gmem = c->gmem;
+    b.gbody = c->gbody;
+    b.grp = c->grp;
+    b.gmark = c->gmark;
+    b.tpf = c->bs_tp;
+    b.bs = c->bs_work;
+    b.slots = c->bs_slots;
+    b.G = p.G;
+    b.Mstar = p.Mstar;
+    b.n1 = p.n1;
+    b.dt = dt;
+    b.tol = p.bs_tol;
+    b.rcrit_mode = p.rcrit_mode;
+    b.changeover = p.changeover;
+    b.status = c->status;
+    return launch_bs(b, c->sm_count, s);
+}
+
 cudaError_t launch_drift_batched(genga_system &all, const BatchBodies &bb, const genga_params &p, double dt,
                                  genga_ctx *c, cudaStream_t s) {
     const int N = bb.N_total;
     if (N <= 0) return cudaSuccess;
+    const bool level1 = p.bs_tol > 0.0;
     cudaError_t e = launch_momentum_batched(all, bb, c->Pd, nullptr, s);
+    if (e == cudaSuccess && level1) e = launch_level1_groups(all, c, s);
     if (e != cudaSuccess) return e;
     drift_batched_kernel<<<(N + 127) / 128, 128, 0, s>>>(all.x, all.y, all.z, all.vx, all.vy, all.vz, c->Pd,
-                                                         0.5 * dt / p.Mstar, p.G * p.Mstar, dt, p.kepler_max_iter, c->status, bb);
+                                                         0.5 * dt / p.Mstar, p.G * p.Mstar, dt, p.kepler_max_iter, c->status,
+                                                         level1 ? c->grp : nullptr, bb);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (level1 && (e = launch_level1(all, p, dt, c, s)) != cudaSuccess) return e;
     e = launch_momentum_batched(all, bb, c->Pd, nullptr, s);
     if (e != cudaSuccess) return e;
     hc_batched_kernel<<<(N + 255) / 256, 256, 0, s>>>(all.x, all.y, all.z, c->Pd, 0.5 * dt / p.Mstar, bb);
@@ -205,12 +274,16 @@ cudaError_t launch_drift_batched(genga_system &all, const BatchBodies &bb, const
 cudaError_t launch_drift(genga_system &sys, const genga_params &p, double dt, genga_ctx *c, cudaStream_t s) {
     const int N = sys.N;
     if (N <= 0) return cudaSuccess;
+    const bool level1 = p.bs_tol > 0.0;
     cudaError_t e = launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, N, c->mom, nullptr, s);
+    if (e == cudaSuccess && level1) e = launch_level1_groups(sys, c, s);
     if (e != cudaSuccess) return e;
     const int nb = (N + 127) / 128;
     drift_kernel<<<nb, 128, 0, s>>>(sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, N, c->mom,
-                                    0.5 * dt / p.Mstar, p.G * p.Mstar, dt, p.kepler_max_iter, c->status);
+                                    0.5 * dt / p.Mstar, p.G * p.Mstar, dt, p.kepler_max_iter, c->status,
+                                    level1 ? c->grp : nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (level1 && (e = launch_level1(sys, p, dt, c, s)) != cudaSuccess) return e;
     e = launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, N, c->mom, nullptr, s);
     if (e != cudaSuccess) return e;
     hc_kernel<<<(N + 255) / 256, 256, 0, s>>>(sys.x, sys.y, sys.z, N, c->mom, 0.5 * dt / p.Mstar);

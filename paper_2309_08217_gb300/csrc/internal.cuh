@@ -36,6 +36,11 @@
 // Bodies per tile of the tile-blocked FP32 copy (pk_t).
 #define GENGA_TILE_T 256
 
+// Close-encounter level: doubles of level-1 workspace per group member
+// (encounter.cu), and the most members one drift can integrate.
+#define GENGA_BS_FIELDS 80
+#define GENGA_BS_MAX_SLOTS (1 << 20)
+
 namespace genga {
 struct Profile {                // CUDA event pairs around pass launches
     static constexpr int CAP = 65536;
@@ -97,6 +102,18 @@ struct genga_ctx {
     int32_t step_launches;     // kernels one replay launches
     int32_t step_graphs;       // 1: use step graphs (default), 0: always launch step by step
     int64_t launches;          // kernels this context has launched (measurement hook)
+    // close-encounter level (encounter.cu): groups of the most recent kick's pairs
+    int32_t bs_slots;          // members one drift can hold: min(npad_max, GENGA_BS_MAX_SLOTS)
+    int32_t *grp;              // [npad_max] group label of each body (smallest member), -1: none
+    int32_t *gmark;            // [npad_max] 1 while the body is a member
+    int32_t *gslot;            // [npad_max] group number of each group's smallest member
+    uint32_t *iperm;           // [npad_max] packed position of each body (written by prep)
+    int32_t *gbody;            // [bs_slots] members in discovery order, then sorted per group
+    int32_t *gmem;             // [bs_slots] members grouped
+    int32_t *gstart, *gsize, *gcur;  // [bs_slots] per group: first slot, members, placement cursor
+    int32_t *gcount;           // [1] number of groups
+    int32_t *bs_tp;            // [bs_slots] member is a test particle (mode 2)
+    double *bs_work;           // [GENGA_BS_FIELDS * bs_slots] level-1 integration state
     double *Pd;                // [3 * GENGA_MAX_DISCS] momentum of each system (batched mode)
     double *Pd_part;           // [3 * GENGA_MAX_DISCS] scratch
     size_t partial_cap;        // doubles in `partial`
@@ -174,6 +191,31 @@ struct PassArgs {               // one long-range pass
     int32_t tier_len[GENGA_MAX_TIERS], tier_n[GENGA_MAX_TIERS];
 };
 
+struct GroupArgs {              // grouping of the encounter pairs (one CTA)
+    const int2 *enc;
+    const int32_t *enc_count;
+    int32_t enc_cap, N, slots;
+    int32_t *grp, *gmark, *gslot, *gbody, *gmem, *gstart, *gsize, *gcur, *gcount;
+    uint32_t *status;
+};
+
+struct BSArgs {                 // level-1 integration of the groups (one warp per group)
+    double *x, *y, *z, *vx, *vy, *vz;
+    const double *m;
+    const uint32_t *iperm;      // packed position of each body: a_osc, rc_eq1, lo.w (test particle)
+    const double *a_osc, *rc_eq1;
+    const float4 *lo;
+    const int32_t *gcount, *gstart, *gsize, *gmem;
+    int32_t *gbody, *grp, *gmark, *tpf;
+    double *bs;                 // GENGA_BS_FIELDS fields of `slots` doubles
+    int32_t slots;
+    double G, Mstar, n1, dt, tol;
+    int32_t rcrit_mode, changeover;
+    uint32_t *status;
+};
+
+cudaError_t launch_groups(const GroupArgs &g, cudaStream_t s);
+cudaError_t launch_bs(const BSArgs &b, int sm_count, cudaStream_t s);
 cudaError_t launch_momentum(const double *vx, const double *vy, const double *vz, const double *m,
                             int N, double *P, int32_t *zero_me, cudaStream_t s);
 cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ctx *c, cudaStream_t s);

@@ -11,7 +11,9 @@
 //     an FP64 {x, y, z, G m} record, and the FP32 screening factors
 //     {H_i, A_i} with r_crit,ij <= max(H_i, H_j) * max(A_i, A_j) for every
 //     pair (rounded up); per 64-body group, the bounding box of the FP32
-//     positions and the maxima of the screening factors.
+//     positions and the maxima of the screening factors;
+//   * iperm: the packed position of every body (the close-encounter level
+//     reads a_i, r_crit,i and the test-particle flag of its members there).
 #include "internal.cuh"
 
 namespace genga {
@@ -216,11 +218,12 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
     double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
     float4 *__restrict__ lo, double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
     float4 *__restrict__ gbox_hi, int32_t *__restrict__ gflag, double *__restrict__ a_osc,
-    double *__restrict__ rc_eq1, int n_big) {
+    double *__restrict__ rc_eq1, int n_big, uint32_t *__restrict__ iperm) {
     const int k = blockIdx.x * PREP_THREADS + threadIdx.x;
     float3 pos = make_float3(0.f, 0.f, 0.f);
     bool real = false;
     const int i = k < N ? (int)perm[k] : -1;
+    if (i >= 0) iperm[i] = (uint32_t)k;
     const bool tp = i >= 0 && n_big >= 0 && i >= n_big;
     const float2 s = prep_body(k, i, k - N, x, y, z, vx, vy, vz, m, P, G, Mstar, dt, n1, n2,
                                rcrit_mode, hi, hit, hid, lo, p64, scr, a_osc, rc_eq1, tp, &pos, &real);
@@ -237,13 +240,14 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_batched_kernel(
     double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
     float4 *__restrict__ lo, double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
     float4 *__restrict__ gbox_hi, int32_t *__restrict__ gflag, double *__restrict__ a_osc,
-    double *__restrict__ rc_eq1, int n_big, const __grid_constant__ BatchBodies bb) {
+    double *__restrict__ rc_eq1, int n_big, uint32_t *__restrict__ iperm, const __grid_constant__ BatchBodies bb) {
     const int p = blockIdx.x * PREP_THREADS + threadIdx.x;
     const int d = find_segment(bb.poff, bb.D, p);
     const int k = p - bb.poff[d], Nd = bb.off[d + 1] - bb.off[d];
     float3 pos = make_float3(0.f, 0.f, 0.f);
     bool real = false;
     const int i = k < Nd ? (int)perm[bb.off[d] + k] : -1;
+    if (i >= 0) iperm[i] = (uint32_t)p;
     const bool tp = i >= 0 && n_big >= 0 && i - bb.off[d] >= n_big;
     const float2 s = prep_body(p, i, k - Nd, x, y, z, vx, vy, vz, m, Pd + 3 * d, G, Mstar, dt, n1, n2, rcrit_mode, hi,
                                hit, hid, lo, p64, scr, a_osc, rc_eq1, tp, &pos, &real);
@@ -293,7 +297,7 @@ cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ct
     prep_kernel<<<npad / PREP_THREADS, PREP_THREADS, 0, s>>>(
         sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->perm, c->mom, p.G, p.Mstar, p.dt, p.n1,
         p.n2, p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_d, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->gflag,
-        c->a_osc, c->rc_eq1, p.n_big);
+        c->a_osc, c->rc_eq1, p.n_big, c->iperm);
     return cudaGetLastError();
 }
 
@@ -312,7 +316,7 @@ cudaError_t launch_prep_batched(const genga_system &all, const BatchBodies &bb, 
     prep_batched_kernel<<<bb.npad_total / PREP_THREADS, PREP_THREADS, 0, s>>>(
         all.x, all.y, all.z, all.vx, all.vy, all.vz, all.m, c->perm, c->Pd, p.G, p.Mstar, p.dt, p.n1, p.n2,
         p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_d, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->gflag, c->a_osc,
-        c->rc_eq1, p.n_big, bb);
+        c->rc_eq1, p.n_big, c->iperm, bb);
     return cudaGetLastError();
 }
 

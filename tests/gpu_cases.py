@@ -29,3 +29,29 @@ def planted_disc(N, seed, fracs=(0.05, 0.5, 0.9, 1.1, 0.3), mass_scale=1.0, a_mi
     for dst, src in zip(d2.arrays(), arr):
         dst[:] = src
     return d2
+
+
+def orbiting_pairs_disc(N, seed, fracs=(0.05, 0.5, 0.9, 1.1, 0.3)):
+    """planted_disc with each planted pair set on a circular orbit about its
+    centre of mass (relative speed sqrt(G (m_i + m_j) / r) perpendicular to the
+    separation), so the close pairs revolve instead of falling onto each other."""
+    d = planted_disc(N, seed, fracs)
+    arr = [a.copy() for a in d.arrays()]
+    rng = np.random.default_rng(seed + 91)
+    npl = min(len(fracs), N // 2)
+    for k in range(npl):
+        i, j = 2 * k + 1, 2 * k
+        sep = np.array([arr[c][i] - arr[c][j] for c in range(3)])
+        r = np.linalg.norm(sep)
+        w = rng.normal(size=3)
+        w -= w @ sep / r ** 2 * sep
+        w /= np.linalg.norm(w)
+        vrel = np.sqrt(d.G * (arr[6][i] + arr[6][j]) / r)
+        mi, mj = arr[6][i], arr[6][j]
+        for c in range(3):   # relative velocity split so the pair's momentum is unchanged
+            arr[3 + c][i] += mj / (mi + mj) * vrel * w[c]
+            arr[3 + c][j] -= mi / (mi + mj) * vrel * w[c]
+    d2 = d.copy()
+    for dst, src in zip(d2.arrays(), arr):
+        dst[:] = src
+    return d2

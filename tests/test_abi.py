@@ -42,9 +42,30 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_status_strings(lib):
     import paper_2309_08217_gb300 as g
-    for code in range(7):
+    for code in range(8):
         assert len(g.genga_status_string(code)) > 0
+        assert g.genga_status_string(code) != "unknown status"
     assert g.genga_status_string(99) == "unknown status"
+
+
+def _struct_fields(name):
+    text = open(os.path.join(HEADER_DIR, "genga.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + ";", text).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        names = decl.split(None, 1)[1]
+        fields += [n.strip().lstrip("*") for n in names.split(",")]
+    return fields
+
+
+def test_binding_structs_match_the_header():
+    import paper_2309_08217_gb300 as g
+    assert [f[0] for f in g.genga_params._fields_] == _struct_fields("genga_params")
+    assert [f[0] for f in g.genga_system._fields_] == _struct_fields("genga_system")
 
 
 def test_host_argument_checks_without_device(lib):
