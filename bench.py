@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-disc batched workload")
     ap.add_argument("--batched-steps", type=int, default=5)
     ap.add_argument("--no-tp2", action="store_true", help="skip the test-particle-mode-2 kicks on giants100k")
+    ap.add_argument("--bs-tol", type=float, default=1e-12,
+                    help="tolerance of the close-encounter (Bulirsch-Stoer) level of the step; 0: level off")
     ap.add_argument("--conservation", default=None,
                     help="instead of the benchmark: energy and angular-momentum drift of FP32 vs FP64 runs, "
                          "comma-separated workload:steps:sample_every (e.g. embryo6625:20000:1000,giants100k:100:10)")
@@ -225,7 +227,7 @@ def run_batched(g, torch, dev, stream, flush, args, rank, ws=1, dist=None):
     offsets = np.concatenate([[0], np.cumsum(sizes)]).tolist()
     padded = int(sum((n + 1023) // 1024 * 1024 for n in sizes))
     pairs_step = 2 * int((sizes * (sizes - 1)).sum())
-    p = g.make_params(G=ds[0].G, Mstar=1.0, dt=6.0, precision=g.GENGA_FP32)
+    p = g.make_params(G=ds[0].G, Mstar=1.0, dt=6.0, precision=g.GENGA_FP32, bs_tol=args.bs_tol)
     K, W = max(1, args.batched_steps), 3
 
     def timed(step_once):
@@ -331,8 +333,8 @@ def run_genga(args):
     N = d.N
     pairs_step = 2 * N * (N - 1)
     ctx = g.Context(N, local)
-    p32 = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=g.GENGA_FP32)
-    p64 = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=g.GENGA_FP64)
+    p32 = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=g.GENGA_FP32, bs_tol=args.bs_tol)
+    p64 = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=g.GENGA_FP64, bs_tol=args.bs_tol)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -392,6 +394,26 @@ def run_genga(args):
     chosen, _ = g.genga_get_kernel_variant(ctx, N)
     tuner_ms = g.genga_tuning_times(ctx, N)
     ms64, pass64, nl64, _, _ = timed_steps(p64, max(1, args.fp64_steps), 3)
+
+    # ---- what the close-encounter level costs: the same FP32 steps with it off
+    level1 = None
+    if args.bs_tol > 0:
+        cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+        cap = 1 << 16
+        pbuf = torch.zeros(2 * cap, dtype=torch.int32, device=dev)
+        s1 = g.DeviceSystem.from_disc(d, device=dev)
+        g.genga_kick(ctx, s1, p32, 0.0, None)
+        g.genga_last_encounters(ctx, pbuf, cap, cnt)
+        pairs0 = int(cnt.item())
+        g.genga_get_status(ctx)          # (a list longer than cap only truncates this copy)
+        p32_off = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=g.GENGA_FP32, bs_tol=0.0)
+        ms_off, _, _, _, _ = timed_steps(p32_off, args.steps, args.warmup)
+        g.genga_get_status(ctx)
+        ms_off = max_over_ranks(ms_off, dist, dev)
+        level1 = {"bs_tol": args.bs_tol, "encounter_pairs_t0": pairs0,
+                  "ms_per_step_level_off": ms_off / args.steps,
+                  "ms_per_step_level_on": max_over_ranks(ms32, dist, dev) / args.steps,
+                  "how": "the headline FP32 steps again with bs_tol = 0 (every body on its Kepler orbit)"}
 
     # ---- the same FP32 steps launched as captured 4-step graphs (genga_step(.., 4)),
     # L2 flushed between blocks
@@ -491,7 +513,9 @@ def run_genga(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "pairs_per_step": pairs_step,
                    "step": "kick(dt/2) drift(dt) kick(dt/2) via genga_step; FP32 pair terms, FP64 "
-                           "accumulation, FP64 drift and close-encounter pairs",
+                           "accumulation, FP64 drift and close-encounter pairs"
+                           + (f"; encounter groups integrated on the Bulirsch-Stoer level (tol {args.bs_tol:g})"
+                              if args.bs_tol > 0 else "; close-encounter level off"),
                    "l2": "flushed (512 MiB write) between timed steps, outside the step events",
                    "parallelism": f"{ws} independent replica disc(s), one per GPU"},
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64_max / max(1, args.fp64_steps),
@@ -500,6 +524,7 @@ def run_genga(args):
                  "fp32_over_fp64": value / value64},
         "roofline": roof,
         "graph_blocks": graph,
+        "level1": level1,
         "batched": batched,
         "tp2": tp2,
         "cpu_baseline": cpu,
@@ -519,10 +544,9 @@ def run_genga(args):
 # ------------------------------------------------------- conservation ----
 def run_conservation(args):
     """Relative energy error and |dL/L| along FP32-kick and FP64-kick runs from
-    the same seeded state (one JSON line per workload).  genga_step leaves the
-    (1 - K) part of encounter pairs unintegrated (no Bulirsch-Stoer level), so
-    both runs carry that same approximation: the comparison is FP32 against
-    FP64 under one treatment."""
+    the same seeded state (one JSON line per workload), both with the
+    close-encounter level at --bs-tol (0: every body on its Kepler orbit, the
+    (1 - K) part of encounter pairs then left out on both sides)."""
     import numpy as np
     import torch
 
@@ -538,9 +562,9 @@ def run_conservation(args):
         d = discs.workload(name)
         ctx = g.Context(d.N, 0)
         out = {"mode": "conservation", "workload": name, "N": d.N, "dt": d.dt, "steps": steps,
-               "sample_every": every, "data": "synthetic"}
+               "sample_every": every, "data": "synthetic", "bs_tol": args.bs_tol}
         for label, prec in (("fp32", g.GENGA_FP32), ("fp64", g.GENGA_FP64)):
-            p = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=prec)
+            p = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=prec, bs_tol=args.bs_tol)
             s = g.DeviceSystem.from_disc(d, device=dev)
             E0, *L0 = g.genga_energy(ctx, s, p)
             L0 = np.array(L0)

@@ -101,8 +101,8 @@ typedef struct {
 typedef struct genga_ctx genga_ctx;
 
 /* Create a context on `device` with workspace for systems of up to max_N bodies
- * (about 930 bytes per body, 660 of them the close-encounter workspace, plus
- * the encounter buffer).  *ctx is NULL on error. */
+ * (about 270 bytes per body, plus 1.9 KB per body for the first 262,144 bodies:
+ * the close-encounter workspace, plus the encounter buffer).  *ctx is NULL on error. */
 genga_status genga_create(genga_ctx **ctx, int32_t max_N, int32_t device);
 
 /* Free the context's workspace (synchronises its device first). NULL is a no-op. */

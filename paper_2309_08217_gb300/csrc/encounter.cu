@@ -197,29 +197,21 @@ __global__ void __launch_bounds__(GROUP_THREADS) group_kernel(const __grid_const
     if (tid == 0) *a.gcount = ng;
 }
 
-// Changeover weight K(y) of the kick (Sect. 1): 0 for y <= 0, 1 for y >= 1.
-__device__ __forceinline__ double changeover_weight(double y, int form) {
-    if (y <= 0.0) return 0.0;
-    if (y >= 1.0) return 1.0;
-    if (form == GENGA_K_CHAMBERS) {
-        const double y2 = y * y;
-        return y2 / (2.0 * y2 - 2.0 * y + 1.0);
-    }
-    return y * y * y * (10.0 + y * (6.0 * y - 15.0));
-}
-
 // Scratch fields of the level-1 workspace, each `slots` doubles (slot = the
 // member's position in gmem/gbody):
+constexpr int BS_PAIR_TAB = 16;    // groups of up to this many members keep their pair radii
 enum : int {
-    F_Y = 0,                       // accepted state x, y, z, vx, vy, vz
-    F_Z = 6,                       // three rotating midpoint states (6 fields each)
-    F_F0 = F_Z + 18,               // acceleration at the accepted state
-    F_T = F_F0 + 3,                // extrapolation row, BS_KMAX x 6 fields
-    F_SC = F_T + 6 * BS_KMAX,      // error scales |x|, |v| of the sub-step
-    F_M = F_SC + 2,                // mass
-    F_A = F_M + 1,                 // osculating a of the first kick
-    F_RC = F_A + 1,                // Eq. 1 radius of the first kick
-    F_COUNT = F_RC + 1
+    F_Y = 0,                              // accepted state x, y, z, vx, vy, vz
+    F_F0 = F_Y + 6,                       // acceleration at the accepted state
+    F_ISC = F_F0 + 3,                     // 1/|x|, 1/|v| of the sub-step (error scales)
+    F_M = F_ISC + 2,                      // mass
+    F_A = F_M + 1,                        // osculating a of the first kick
+    F_RC = F_A + 1,                       // Eq. 1 radius of the first kick
+    F_Z = F_RC + 1,                       // per column k: three rotating midpoint states (18 fields)
+    F_T = F_Z + 18 * BS_KMAX,             // per column k: the smoothed midpoint result T[k][0] (6 fields)
+    F_PR2 = F_T + 6 * BS_KMAX,            // r_crit,ij^2 with the first BS_PAIR_TAB members
+    F_PIN = F_PR2 + BS_PAIR_TAB,          // 1 / (0.9 r_crit,ij)
+    F_COUNT = F_PIN + BS_PAIR_TAB
 };
 static_assert(F_COUNT == GENGA_BS_FIELDS, "level-1 workspace fields");
 
@@ -230,40 +222,78 @@ struct Work {  // field f of slot s: base[f * stride + s]
     __device__ __forceinline__ double &operator()(int field, int s) const { return base[(size_t)field * stride + s]; }
 };
 
-// Level-1 acceleration of the member in slot s with the positions of buffer
-// field p (fields p, p+1, p+2); members in slots [s0, s0 + n).
-__device__ void level1_acc(const BSArgs &a, const Work &W, int s, int s0, int n, int p, double &ax, double &ay,
-                           double &az) {
+// Aitken-Neville coefficients n_{k-j}^2 / (n_k^2 - n_{k-j}^2), n_k = 2 (k + 1),
+// at [k * BS_KMAX + j] (correctly rounded quotients of integers).
+struct NevilleTable {
+    double c[BS_KMAX * BS_KMAX];
+    constexpr NevilleTable() : c() {
+        for (int k = 0; k < BS_KMAX; k++)
+            for (int j = 1; j <= k; j++) {
+                const double nk = 2.0 * (k + 1), nkj = 2.0 * (k - j + 1);
+                c[k * BS_KMAX + j] = (nkj * nkj) / (nk * nk - nkj * nkj);
+            }
+    }
+};
+__constant__ NevilleTable c_neville = NevilleTable();
+
+// Pair radius r_crit,ij of two members (the kick's rule, Eq. 1 inputs of that kick).
+__device__ __forceinline__ double pair_radius(const BSArgs &a, double mi, double mj, double ai, double aj, double rci,
+                                              double rcj) {
+    return (a.rcrit_mode == GENGA_RCRIT_EQ1) ? fmax(rci, rcj)
+                                             : a.n1 * cbrt((mi + mj) / (3.0 * a.Mstar)) * 0.5 * (ai + aj);
+}
+
+// 1 - K(y) from y = q / (0.9 r_crit) - 1/9, with K the kick's changeover weight
+// (Sect. 1): 1 for y <= 0, 0 for y >= 1.
+__device__ __forceinline__ double level1_weight(double y, int form) {
+    if (y <= 0.0) return 1.0;
+    if (y >= 1.0) return 0.0;
+    if (form == GENGA_K_CHAMBERS) {
+        const double y2 = y * y;
+        return 1.0 - y2 * rcp_fp64(fma(2.0 * y, y - 1.0, 1.0));  // y^2 / (2y^2 - 2y + 1)
+    }
+    return 1.0 - y * y * y * (10.0 + y * (6.0 * y - 15.0));
+}
+
+// Level-1 acceleration of the member in slot s with positions in fields
+// (p, p+1, p+2); members in slots [s0, s0 + n).  FP64 throughout; the square
+// root and the reciprocals come from series-corrected SFU seeds (the FP64 pipe
+// of this GPU takes about 64 cycles per warp instruction, whatever the number
+// of active lanes, so the instruction count is the cost).
+__device__ void level1_acc(const BSArgs &a, const Work &W, int s, int s0, int n, int p, bool tab, double &ax,
+                           double &ay, double &az) {
     const double *__restrict__ px = W.f(p);
     const double *__restrict__ py = W.f(p + 1);
     const double *__restrict__ pz = W.f(p + 2);
-    const double *__restrict__ M = W.f(F_M);
-    const double *__restrict__ A = W.f(F_A);
-    const double *__restrict__ RC = W.f(F_RC);
     const double xi = px[s], yi = py[s], zi = pz[s];
-    const double r2 = xi * xi + yi * yi + zi * zi;
-    const double r = sqrt(r2);
-    const double c = -a.G * a.Mstar / (r2 * r);
+    const double ir = rsqrt_fp64(xi * xi + yi * yi + zi * zi);
+    const double c = -a.G * a.Mstar * (ir * ir * ir);
     ax = c * xi;
     ay = c * yi;
     az = c * zi;
     const bool tpi = a.tpf[s] != 0;
-    const double mi = M[s], ai = A[s], rci = RC[s];
+    const double *__restrict__ M = W.f(F_M);
     for (int t = s0; t < s0 + n; t++) {
         if (t == s || (tpi && a.tpf[t] != 0)) continue;
         const double dx = px[t] - xi, dy = py[t] - yi, dz = pz[t] - zi;
         const double q2 = dx * dx + dy * dy + dz * dz;
         if (q2 == 0.0) continue;
-        const double q = sqrt(q2);
-        const double rc = (a.rcrit_mode == GENGA_RCRIT_EQ1)
-                              ? fmax(rci, RC[t])
-                              : a.n1 * cbrt((mi + M[t]) / (3.0 * a.Mstar)) * 0.5 * (ai + A[t]);
-        if (q >= rc) continue;  // K = 1: the kick has all of it
-        const double w = 1.0 - changeover_weight((q / rc - 0.1) / 0.9, a.changeover);
-        const double f = a.G * M[t] * w / (q2 * q);
-        ax += f * dx;
-        ay += f * dy;
-        az += f * dz;
+        double rc2, inv9;
+        if (tab) {
+            rc2 = W(F_PR2 + (t - s0), s);
+            inv9 = W(F_PIN + (t - s0), s);
+        } else {
+            const double rc = pair_radius(a, W(F_M, s), M[t], W(F_A, s), W(F_A, t), W(F_RC, s), W(F_RC, t));
+            rc2 = rc * rc;
+            inv9 = 1.0 / (0.9 * rc);
+        }
+        if (q2 >= rc2) continue;  // K = 1: the kick has all of it
+        const double iq = rsqrt_fp64(q2);
+        const double w = level1_weight(fma(q2 * iq, inv9, -1.0 / 9.0), a.changeover);
+        const double f = a.G * M[t] * w * (iq * iq * iq);
+        ax = fma(f, dx, ax);
+        ay = fma(f, dy, ay);
+        az = fma(f, dz, az);
     }
 }
 
@@ -273,34 +303,215 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-// One warp per group.  Sub-steps are fractions of dt (exact binary values):
-// each runs the modified midpoint rule with n_k = 2 (k + 1) steps,
+// One warp per group.  Sub-steps are fractions of dt (exact binary values);
+// each runs the modified midpoint rule with n_k = 2 (k + 1) steps for all
+// BS_KMAX columns k at once -- the columns are independent, so lane
+// 8 q' + k integrates column k for the members q', q' + 4, ... and one
+// sub-step costs 2 BS_KMAX force evaluations in sequence instead of their sum:
 //   z_0 = y, z_1 = z_0 + H f(z_0), z_{m+1} = z_{m-1} + 2H f(z_m),
 //   T[k][0] = (z_n + z_{n-1} + H f(z_n)) / 2,
-// and the Aitken-Neville table
-//   T[k][j] = T[k][j-1] + (T[k][j-1] - T[k-1][j-1]) n_{k-j}^2 / (n_k^2 - n_{k-j}^2);
-// column k >= 1 is accepted when max |T[k][k] - T[k][k-1]| <= tol |x| (position
-// components) and tol |v| (velocity components) for every member.  No
-// accepted column: the sub-step is halved; accepted by column <= BS_GROW_COL:
-// the next one is doubled.  At BS_MIN_FRAC, at the last of BS_MAX_ATTEMPTS
-// attempts (which takes the rest of dt) or past BS_TIME_LIMIT_NS the last
-// column is accepted anyway and GENGA_ERR_BS is raised.  Only row k of the
-// table is kept: T[k][j-1] overwrites T[k-1][j-1] once T[k][j] is formed.
-__global__ void __launch_bounds__(32 * BS_WARPS) bs_kernel(const __grid_constant__ BSArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * BS_WARPS + (threadIdx.x >> 5), nw = gridDim.x * BS_WARPS;
-    const int ng = *a.gcount;
-    const Work W{a.bs, (size_t)a.slots};
-    for (int g = gw; g < ng; g += nw) {
-        const int s0 = a.gstart[g], n = a.gsize[g];
-        // members in ascending body order (the order of every sum below)
-        for (int q = lane; q < n; q += 32) {
-            const int v = a.gmem[s0 + q];
-            int rank = 0;
-            for (int r = 0; r < n; r++) rank += (a.gmem[s0 + r] < v) ? 1 : 0;
-            a.gbody[s0 + rank] = v;
+// then the Aitken-Neville table
+//   T[k][j] = T[k][j-1] + (T[k][j-1] - T[k-1][j-1]) n_{k-j}^2 / (n_k^2 - n_{k-j}^2)
+// per member and component.  The first column k >= 1 with
+// max |T[k][k] - T[k][k-1]| <= tol |x| (positions) and tol |v| (velocities)
+// over all members is accepted -- the same values and the same choice as
+// building the columns one after another.  No accepted column: the sub-step
+// is halved; accepted by column <= BS_GROW_COL: the next one is doubled.  At
+// BS_MIN_FRAC, at the last of BS_MAX_ATTEMPTS attempts (which takes the rest
+// of dt) or past BS_TIME_LIMIT_NS the last column is accepted anyway and
+// GENGA_ERR_BS is raised.
+__device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+// Warp maximum of non-negative doubles, compared as integers (their bit
+// patterns order like the values), off the FP64 pipe.
+__device__ __forceinline__ double warp_max_nonneg(double v) {
+    long long b = __double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long t = __shfl_xor_sync(0xffffffffu, b, o);
+        b = t > b ? t : b;
+    }
+    return __longlong_as_double(b);
+}
+
+__device__ __forceinline__ bool ge_nonneg(double a, double b) {  // a >= b for a, b >= 0, on the integer pipe
+    return __double_as_longlong(a) >= __double_as_longlong(b);
+}
+
+// Groups of up to 4 members, everything in registers: lane 8 q + k holds
+// member q (q < n) for extrapolation column k; partners' positions come from
+// lanes 8 p + k by shuffles.  The same arithmetic as bs_general, in the same
+// order (central term, then partners in ascending body order).
+__device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, bool &forced) {
+    const int k = lane & 7, q = lane >> 3;
+    const bool act = q < n;
+    const int nk = 2 * (k + 1);
+    double y[6] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0};  // inactive lanes: a harmless circular state
+    double mq = 0.0, aq = 1.0, rcq = 1.0;
+    int tpq = 0, v = -1;
+    if (act) {
+        v = a.gbody[s0 + q];
+        const int kp = (int)a.iperm[v];
+        y[0] = a.x[v]; y[1] = a.y[v]; y[2] = a.z[v];
+        y[3] = a.vx[v]; y[4] = a.vy[v]; y[5] = a.vz[v];
+        mq = a.m[v];
+        aq = a.a_osc[kp];
+        rcq = a.rc_eq1[kp];
+        tpq = a.lo[kp].w != 0.f ? 1 : 0;
+    }
+    // partner constants (fixed over the drift)
+    double gm[4], rc2[4], lo2[4], inv9[4];
+    bool use[4];
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        const double mp = shfl_d(mq, 8 * p), ap = shfl_d(aq, 8 * p), rcp = shfl_d(rcq, 8 * p);
+        const int tpp = __shfl_sync(0xffffffffu, tpq, 8 * p);
+        use[p] = act && p < n && p != q && !(tpq && tpp);
+        double rc = 1.0;
+        if (use[p]) rc = pair_radius(a, mq, mp, aq, ap, rcq, rcp);
+        gm[p] = a.G * mp;
+        rc2[p] = rc * rc;
+        lo2[p] = (0.1 * rc) * (0.1 * rc);
+        inv9[p] = 1.0 / (0.9 * rc);
+    }
+    const double mgm = -a.G * a.Mstar;
+    // level-1 acceleration of this lane's member at (x, y, z) of its column
+    auto accel = [&](double x, double yy, double z, double &ax, double &ay, double &az) {
+        double px[4], py[4], pz[4];
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+            px[p] = shfl_d(x, 8 * p + k);
+            py[p] = shfl_d(yy, 8 * p + k);
+            pz[p] = shfl_d(z, 8 * p + k);
         }
-        __syncwarp();
+        const double ir = rsqrt_fp64(x * x + yy * yy + z * z);
+        const double c = mgm * (ir * ir * ir);
+        ax = c * x;
+        ay = c * yy;
+        az = c * z;
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+            if (!use[p]) continue;
+            const double dx = px[p] - x, dy = py[p] - yy, dz = pz[p] - z;
+            const double q2 = dx * dx + dy * dy + dz * dz;
+            if (__double_as_longlong(q2) == 0 || ge_nonneg(q2, rc2[p])) continue;  // coincident / K = 1
+            const double iq = rsqrt_fp64(q2);
+            const double w = ge_nonneg(lo2[p], q2) ? 1.0 : level1_weight(fma(q2 * iq, inv9[p], -1.0 / 9.0), a.changeover);
+            const double f = gm[p] * w * (iq * iq * iq);
+            ax = fma(f, dx, ax);
+            ay = fma(f, dy, ay);
+            az = fma(f, dz, az);
+        }
+    };
+    double done = 0.0, frac = 1.0;
+    for (int att = 0; att < BS_MAX_ATTEMPTS && done < 1.0; att++) {
+        int late = 0;
+        if (lane == 0) late = (global_timer_ns() - t0 > BS_TIME_LIMIT_NS) ? 1 : 0;
+        late = __shfl_sync(0xffffffffu, late, 0);
+        const bool last = (att == BS_MAX_ATTEMPTS - 1) || late;
+        if (last) frac = 1.0 - done;
+        const double h = frac * a.dt;
+        const double H = h / nk;
+        const double px2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2], pv2 = y[3] * y[3] + y[4] * y[4] + y[5] * y[5];
+        const double isx = px2 > 0.0 ? rsqrt_fp64(px2) : 1.0, isv = pv2 > 0.0 ? rsqrt_fp64(pv2) : 1.0;
+        double f0x, f0y, f0z;
+        accel(y[0], y[1], y[2], f0x, f0y, f0z);
+        const double f0[6] = {y[3], y[4], y[5], f0x, f0y, f0z};
+        double zp[6], zc[6], T[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            zp[c] = y[c];
+            zc[c] = fma(H, f0[c], y[c]);
+            T[c] = 0.0;
+        }
+        for (int m = 1; m <= 2 * BS_KMAX; m++) {  // every lane evaluates (the shuffles need all lanes)
+            double ax, ay, az;
+            accel(zc[0], zc[1], zc[2], ax, ay, az);
+            const double fv[6] = {zc[3], zc[4], zc[5], ax, ay, az};
+            if (m < nk) {
+#pragma unroll
+                for (int c = 0; c < 6; c++) {
+                    const double zn = fma(2.0 * H, fv[c], zp[c]);
+                    zp[c] = zc[c];
+                    zc[c] = zn;
+                }
+            } else if (m == nk) {
+#pragma unroll
+                for (int c = 0; c < 6; c++) T[c] = 0.5 * (zc[c] + zp[c] + H * fv[c]);
+            }
+        }
+        // lane 8 q + c (c < 6): component c of member q over the columns; the
+        // source lane of column kk sends each of its six components in turn
+        const int c = k;
+        double tk[BS_KMAX];
+#pragma unroll
+        for (int kk = 0; kk < BS_KMAX; kk++) {
+            tk[kk] = 0.0;
+#pragma unroll
+            for (int cc = 0; cc < 6; cc++) {
+                const double t = shfl_d(T[cc], 8 * q + kk);
+                if (cc == c) tk[kk] = t;
+            }
+        }
+        const bool item = act && c < 6;
+        const double isc = c < 3 ? isx : isv;
+        double row[BS_KMAX], diag[BS_KMAX], ek[BS_KMAX];
+#pragma unroll
+        for (int kk = 0; kk < BS_KMAX; kk++) {
+            double cur = tk[kk], dprev = 0.0;
+#pragma unroll
+            for (int j = 1; j <= kk; j++) {
+                const double prev = row[j - 1];
+                row[j - 1] = cur;
+                dprev = cur;
+                cur = fma(cur - prev, c_neville.c[kk * BS_KMAX + j], cur);
+            }
+            row[kk] = cur;
+            diag[kk] = cur;
+            ek[kk] = (item && kk >= 1) ? fabs(cur - dprev) * isc : 0.0;
+        }
+        int acc_col = -1;
+#pragma unroll
+        for (int kk = 1; kk < BS_KMAX; kk++) {
+            const double e = warp_max_nonneg(ek[kk]);
+            if (acc_col < 0 && e <= a.tol) acc_col = kk;
+        }
+        if (acc_col < 0 && (frac <= BS_MIN_FRAC || last)) {
+            acc_col = BS_KMAX - 1;
+            forced = true;
+        }
+        if (acc_col < 0) {
+            frac *= 0.5;
+            continue;
+        }
+        double pick = diag[0];
+#pragma unroll
+        for (int kk = 1; kk < BS_KMAX; kk++)
+            if (kk == acc_col) pick = diag[kk];
+#pragma unroll
+        for (int cc = 0; cc < 6; cc++) {
+            const double nv = shfl_d(pick, 8 * q + cc);
+            if (act) y[cc] = nv;
+        }
+        done += frac;
+        if (acc_col <= BS_GROW_COL) frac *= 2.0;
+        if (frac > 1.0 - done) frac = 1.0 - done;
+    }
+    if (act && k == 0) {
+        a.x[v] = y[0]; a.y[v] = y[1]; a.z[v] = y[2];
+        a.vx[v] = y[3]; a.vy[v] = y[4]; a.vz[v] = y[5];
+        a.grp[v] = -1;
+        a.gmark[v] = 0;
+    }
+}
+
+__device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0, bool &forced) {
+    const int kcol = lane & 7, qs = lane >> 3;
+    const int nk = 2 * (kcol + 1);
+    const Work W{a.bs, (size_t)a.slots};
+    const int fz = F_Z + 18 * kcol;  // this lane's column: buffers fz + 6 b + c
+    {
+        const bool tab = n <= BS_PAIR_TAB;
         for (int q = lane; q < n; q += 32) {
             const int s = s0 + q, v = a.gbody[s];
             const int k = (int)a.iperm[v];
@@ -316,10 +527,17 @@ __global__ void __launch_bounds__(32 * BS_WARPS) bs_kernel(const __grid_constant
             a.tpf[s] = a.lo[k].w != 0.f ? 1 : 0;
         }
         __syncwarp();
-        uint64_t t0 = 0;
-        if (lane == 0) t0 = global_timer_ns();
+        if (tab) {  // pair radii, fixed over the drift
+            for (int idx = lane; idx < n * n; idx += 32) {
+                const int si = s0 + idx / n, ti = idx % n;
+                const double rc = pair_radius(a, W(F_M, si), W(F_M, s0 + ti), W(F_A, si), W(F_A, s0 + ti),
+                                              W(F_RC, si), W(F_RC, s0 + ti));
+                W(F_PR2 + ti, si) = rc * rc;
+                W(F_PIN + ti, si) = 1.0 / (0.9 * rc);
+            }
+            __syncwarp();
+        }
         double done = 0.0, frac = 1.0;
-        bool forced = false;
         for (int att = 0; att < BS_MAX_ATTEMPTS && done < 1.0; att++) {
             int late = 0;
             if (lane == 0) late = (global_timer_ns() - t0 > BS_TIME_LIMIT_NS) ? 1 : 0;
@@ -331,75 +549,80 @@ __global__ void __launch_bounds__(32 * BS_WARPS) bs_kernel(const __grid_constant
                 const int s = s0 + q;
                 const double x = W(F_Y, s), y = W(F_Y + 1, s), z = W(F_Y + 2, s);
                 const double u = W(F_Y + 3, s), v = W(F_Y + 4, s), w = W(F_Y + 5, s);
-                const double px = sqrt(x * x + y * y + z * z), pv = sqrt(u * u + v * v + w * w);
-                W(F_SC, s) = px > 0.0 ? px : 1.0;
-                W(F_SC + 1, s) = pv > 0.0 ? pv : 1.0;
+                const double px2 = x * x + y * y + z * z, pv2 = u * u + v * v + w * w;
+                W(F_ISC, s) = px2 > 0.0 ? rsqrt_fp64(px2) : 1.0;
+                W(F_ISC + 1, s) = pv2 > 0.0 ? rsqrt_fp64(pv2) : 1.0;
                 double ax, ay, az;
-                level1_acc(a, W, s, s0, n, F_Y, ax, ay, az);
+                level1_acc(a, W, s, s0, n, F_Y, tab, ax, ay, az);
                 W(F_F0, s) = ax;
                 W(F_F0 + 1, s) = ay;
                 W(F_F0 + 2, s) = az;
             }
             __syncwarp();
-            int acc_col = -1;
-            for (int k = 0; k < BS_KMAX; k++) {
-                const int nsub = 2 * (k + 1);
-                const double H = h / nsub;
-                for (int q = lane; q < n; q += 32) {  // z_0 = y, z_1 = y + H f(y)
-                    const int s = s0 + q;
-                    for (int c = 0; c < 6; c++) {
-                        const double yc = W(F_Y + c, s);
-                        const double fc = c < 3 ? W(F_Y + 3 + c, s) : W(F_F0 + c - 3, s);
-                        W(F_Z + c, s) = yc;
-                        W(F_Z + 6 + c, s) = yc + H * fc;
-                    }
-                }
-                __syncwarp();
-                int bp = 0, bc = 1, bn = 2;
-                for (int mstep = 1; mstep < nsub; mstep++) {
-                    for (int q = lane; q < n; q += 32) {
-                        const int s = s0 + q;
-                        double ax, ay, az;
-                        level1_acc(a, W, s, s0, n, F_Z + 6 * bc, ax, ay, az);
-                        for (int c = 0; c < 6; c++) {
-                            const double fc = c < 3 ? W(F_Z + 6 * bc + 3 + c, s) : (c == 3 ? ax : (c == 4 ? ay : az));
-                            W(F_Z + 6 * bn + c, s) = W(F_Z + 6 * bp + c, s) + 2.0 * H * fc;
-                        }
-                    }
-                    __syncwarp();
-                    const int t = bp;
-                    bp = bc;
-                    bc = bn;
-                    bn = t;
-                }
-                double err = 0.0;
-                for (int q = lane; q < n; q += 32) {  // smoothing step, extrapolation, error
-                    const int s = s0 + q;
-                    double ax, ay, az;
-                    level1_acc(a, W, s, s0, n, F_Z + 6 * bc, ax, ay, az);
-                    const double sx = W(F_SC, s), sv = W(F_SC + 1, s);
-                    for (int c = 0; c < 6; c++) {
-                        const double fc = c < 3 ? W(F_Z + 6 * bc + 3 + c, s) : (c == 3 ? ax : (c == 4 ? ay : az));
-                        double cur = 0.5 * (W(F_Z + 6 * bc + c, s) + W(F_Z + 6 * bp + c, s) + H * fc);
-                        for (int j = 1; j <= k; j++) {
-                            const double nk = nsub, nkj = 2 * (k - j + 1);
-                            const double cf = (nkj * nkj) / (nk * nk - nkj * nkj);
-                            double &slot = W(F_T + 6 * (j - 1) + c, s);
-                            const double prev = slot;  // T[k-1][j-1]
-                            slot = cur;                // T[k][j-1]
-                            cur = cur + (cur - prev) * cf;
-                        }
-                        W(F_T + 6 * k + c, s) = cur;
-                        if (k >= 1) err = fmax(err, fabs(cur - W(F_T + 6 * (k - 1) + c, s)) / (c < 3 ? sx : sv));
-                    }
-                }
-                err = warp_max(err);
-                __syncwarp();
-                if (k >= 1 && err <= a.tol) {
-                    acc_col = k;
-                    break;
+            const double H = h / nk;
+            for (int q = qs; q < n; q += 4) {  // z_0 = y, z_1 = y + H f(y), every column
+                const int s = s0 + q;
+                for (int c = 0; c < 6; c++) {
+                    const double yc = W(F_Y + c, s);
+                    const double fc = c < 3 ? W(F_Y + 3 + c, s) : W(F_F0 + c - 3, s);
+                    W(fz + c, s) = yc;
+                    W(fz + 6 + c, s) = fma(H, fc, yc);
                 }
             }
+            __syncwarp();
+            // stage m: z_{m+1} from z_m (m < n_k) or the smoothing step (m = n_k);
+            // after m - 1 stages z_m is buffer m mod 3 and z_{m-1} buffer (m - 1) mod 3
+            for (int m = 1; m <= 2 * BS_KMAX; m++) {
+                if (m <= nk) {
+                    const int bc = m % 3, bp = (m + 2) % 3, bn = (m + 1) % 3;
+                    for (int q = qs; q < n; q += 4) {
+                        const int s = s0 + q;
+                        double ax, ay, az;
+                        level1_acc(a, W, s, s0, n, fz + 6 * bc, tab, ax, ay, az);
+                        const double fv[6] = {W(fz + 6 * bc + 3, s), W(fz + 6 * bc + 4, s), W(fz + 6 * bc + 5, s),
+                                              ax, ay, az};
+                        if (m < nk) {
+                            for (int c = 0; c < 6; c++)
+                                W(fz + 6 * bn + c, s) = fma(2.0 * H, fv[c], W(fz + 6 * bp + c, s));
+                        } else {
+                            for (int c = 0; c < 6; c++)
+                                W(F_T + 6 * kcol + c, s) =
+                                    0.5 * (W(fz + 6 * bc + c, s) + W(fz + 6 * bp + c, s) + H * fv[c]);
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            // extrapolation and error per (member, component); lane handles items lane, lane + 32, ...
+            double ek[BS_KMAX];
+            for (int k = 0; k < BS_KMAX; k++) ek[k] = 0.0;
+            for (int item = lane; item < 6 * n; item += 32) {
+                const int q = item / 6, c = item % 6, s = s0 + q;
+                const double isc = W(F_ISC + (c < 3 ? 0 : 1), s);
+                double row[BS_KMAX];   // row k of the table, in place
+                double diag[BS_KMAX];  // T[k][k]
+                for (int k = 0; k < BS_KMAX; k++) {
+                    double cur = W(F_T + 6 * k + c, s);
+                    double diag_prev = 0.0;
+                    for (int j = 1; j <= k; j++) {
+                        const double prev = row[j - 1];  // T[k-1][j-1]
+                        row[j - 1] = cur;                // T[k][j-1]
+                        diag_prev = cur;
+                        cur = fma(cur - prev, c_neville.c[k * BS_KMAX + j], cur);
+                    }
+                    row[k] = cur;
+                    diag[k] = cur;
+                    if (k >= 1) ek[k] = fmax(ek[k], fabs(cur - diag_prev) * isc);
+                }
+                // the candidates T[k][k] stay in W(F_T) for the accepted column
+                for (int k = 0; k < BS_KMAX; k++) W(F_T + 6 * k + c, s) = diag[k];
+            }
+            int acc_col = -1;
+            for (int k = 1; k < BS_KMAX; k++) {
+                const double e = warp_max(ek[k]);
+                if (acc_col < 0 && e <= a.tol) acc_col = k;
+            }
+            __syncwarp();
             if (acc_col < 0 && (frac <= BS_MIN_FRAC || last)) {
                 acc_col = BS_KMAX - 1;
                 forced = true;
@@ -428,6 +651,31 @@ __global__ void __launch_bounds__(32 * BS_WARPS) bs_kernel(const __grid_constant
             a.grp[v] = -1;
             a.gmark[v] = 0;
         }
+    }
+}
+
+// One warp per group: members sorted by body index, then the register path
+// (n <= 4) or the workspace path.
+__global__ void __launch_bounds__(32 * BS_WARPS) bs_kernel(const __grid_constant__ BSArgs a) {
+    static_assert(BS_KMAX == 8, "lane = 8 * member slice + column");
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * BS_WARPS + (threadIdx.x >> 5), nw = gridDim.x * BS_WARPS;
+    const int ng = *a.gcount;
+    for (int g = gw; g < ng; g += nw) {
+        const int s0 = a.gstart[g], n = a.gsize[g];
+        // members in ascending body order (the order of every sum)
+        for (int q = lane; q < n; q += 32) {
+            const int v = a.gmem[s0 + q];
+            int rank = 0;
+            for (int r = 0; r < n; r++) rank += (a.gmem[s0 + r] < v) ? 1 : 0;
+            a.gbody[s0 + rank] = v;
+        }
+        __syncwarp();
+        uint64_t t0 = 0;
+        if (lane == 0) t0 = global_timer_ns();
+        bool forced = false;
+        if (n <= 4) bs_small(a, s0, n, lane, t0, forced);
+        else bs_general(a, s0, n, lane, t0, forced);
         if (forced && lane == 0) atomicOr(a.status, GENGA_BIT(GENGA_ERR_BS));
         __syncwarp();
     }

@@ -38,8 +38,8 @@
 
 // Close-encounter level: doubles of level-1 workspace per group member
 // (encounter.cu), and the most members one drift can integrate.
-#define GENGA_BS_FIELDS 80
-#define GENGA_BS_MAX_SLOTS (1 << 20)
+#define GENGA_BS_FIELDS 238
+#define GENGA_BS_MAX_SLOTS (1 << 18)
 
 namespace genga {
 struct Profile {                // CUDA event pairs around pass launches
