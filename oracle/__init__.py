@@ -79,6 +79,10 @@ def _load():
             "oracle_drift_groups": ([i] + [_dp] * 9 + [C.c_int64, _i32p, d, d, d, i, i, i, d, d, i,
                                                        C.POINTER(C.c_int)], i),
             "oracle_step_bs": ([i] + [_dp] * 7 + [d] * 5 + [i, i, i, i, d, i, C.POINTER(C.c_int)], i),
+            "oracle_step_full": ([i] + [_dp] * 8 + [_i32p] + [d] * 5 + [i, i, i, i, d, d, d, i,
+                                                                        C.POINTER(C.c_int), C.POINTER(C.c_int)], i),
+            "oracle_bs_group_full": ([i, _i32p] + [_dp] * 10 + [_i32p, d, d, d, i, i, i, d, d,
+                                                                  C.POINTER(C.c_int)], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -199,12 +203,31 @@ def drift(arrs, G, Mstar, dt, max_iter=50):
 
 
 def step(arrs, G, Mstar, dt, n1, n2, mode, form, nsteps, max_iter=50, n_big=-1, bs_tol=0.0,
-         forced=None):
+         forced=None, radius=None, dead=None, r_in=0.0, r_out=0.0, merges=None):
     """nsteps of kick(dt/2) drift(dt) kick(dt/2), in place.  bs_tol > 0: the
     drift integrates the encounter groups of each step's first kick with the
     Bulirsch-Stoer level at that tolerance (forced: optional one-element list
-    that accumulates the forced acceptances).  Returns the Kepler cap count."""
+    that accumulates the forced acceptances).  radius (per body, float64,
+    updated) turns on perfect mergers inside that level, r_in / r_out (> 0)
+    the removal radii; dead (per body, int32, updated) marks the bodies merged
+    away or removed (they stay as massless ghosts); merges: optional
+    one-element list that accumulates the mergers.  Returns the Kepler cap
+    count."""
     x, y, z, vx, vy, vz, m = arrs
+    if radius is not None or dead is not None or r_in > 0.0 or r_out > 0.0:
+        assert bs_tol > 0.0 and dead is not None and dead.dtype == np.int32
+        f, mg = C.c_int(0), C.c_int(0)
+        rp = _p(radius) if radius is not None else None
+        bad = int(_load().oracle_step_full(len(m), *map(_p, (x, y, z, vx, vy, vz, m)), rp,
+                                           dead.ctypes.data_as(_i32p), G, Mstar, dt, n1, n2, int(mode),
+                                           int(form), int(n_big), int(max_iter), float(bs_tol),
+                                           float(r_in), float(r_out), int(nsteps), C.byref(f),
+                                           C.byref(mg)))
+        if forced is not None:
+            forced[0] += f.value
+        if merges is not None:
+            merges[0] += mg.value
+        return bad
     if bs_tol <= 0.0:
         return int(_load().oracle_step(len(m), *map(_p, (x, y, z, vx, vy, vz, m)), G, Mstar, dt,
                                        n1, n2, int(mode), int(form), int(n_big), int(max_iter),
@@ -239,13 +262,26 @@ def bs_acc(x, y, z, m, a, rc, members, G, Mstar, n1, mode, form, n_big=-1):
     return out[: 3 * len(mem)].reshape(-1, 3).T.copy()
 
 
-def bs_group(arrs, members, a, rc, G, Mstar, n1, mode, form, dt, tol, n_big=-1):
+def bs_group(arrs, members, a, rc, G, Mstar, n1, mode, form, dt, tol, n_big=-1, radius=None,
+             dead=None, merges=None):
     """Bulirsch-Stoer integration of one group (ascending body indices) over
     dt under the central body and the (1 - K) part of the members' pair
-    forces, in place; returns 1 if an acceptance was forced, else 0."""
+    forces, in place; returns 1 if an acceptance was forced, else 0.  With
+    radius (and dead, int32 per body) overlapping members merge after every
+    accepted sub-step (m, radius and dead updated in place)."""
     x, y, z, vx, vy, vz, m = arrs
     mem = np.ascontiguousarray(np.asarray(members, dtype=np.int32))
     a, rc = _f64(a), _f64(rc)
+    if radius is not None:
+        assert dead is not None and dead.dtype == np.int32
+        mg = C.c_int(0)
+        f = int(_load().oracle_bs_group_full(len(mem), mem.ctypes.data_as(_i32p),
+                                             *map(_p, (x, y, z, vx, vy, vz, m, a, rc, radius)),
+                                             dead.ctypes.data_as(_i32p), G, Mstar, n1, int(mode), int(form),
+                                             int(n_big), float(dt), float(tol), C.byref(mg)))
+        if merges is not None:
+            merges[0] += mg.value
+        return f
     return int(_load().oracle_bs_group(len(mem), mem.ctypes.data_as(_i32p),
                                        *map(_p, (x, y, z, vx, vy, vz, m, a, rc)), G, Mstar, n1,
                                        int(mode), int(form), int(n_big), float(dt), float(tol)))

@@ -20,6 +20,9 @@
  *                         connected groups of encounter pairs are integrated
  *                         over the drift with a Bulirsch-Stoer method under the
  *                         central body and the (1 - K) part of their mutual forces
+ *   mergers, removal      Sect. 2: collisions are perfect mergers; bodies closer
+ *                         than r_in to or farther than r_out from the central
+ *                         body are removed (both leave a massless "ghost")
  *   energy / ang. mom.    Sect. 3.1: dE/E = E(t)/E0 - 1, dL/L = L(t)/L0 - 1
  *
  * Readings where the paper is silent (each one is listed in the design
@@ -427,7 +430,10 @@ typedef struct {
     const double *m, *a, *rc;
     double G, Mstar, n1;
     int mode, form, n_big;
+    const int32_t *ghost;   /* per member: merged away (no force either way); NULL: none */
 } bs_group;
+
+static int bs_ghost(const bs_group *g, int k) { return g->ghost && g->ghost[k]; }
 
 /* State layout: s[6k + 0..2] = position, s[6k + 3..5] = velocity of member k. */
 static void bs_deriv(const bs_group *g, const double *s, double *ds)
@@ -441,7 +447,7 @@ static void bs_deriv(const bs_group *g, const double *s, double *ds)
         double ax = c * xi[0], ay = c * xi[1], az = c * xi[2];
         for (int j = 0; j < g->n; j++) {
             int bj = g->mem[j];
-            if (j == i || tp_pair(g->n_big, bi, bj)) continue;
+            if (j == i || tp_pair(g->n_big, bi, bj) || bs_ghost(g, i) || bs_ghost(g, j)) continue;
             const double *xj = s + 6 * j;
             double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
             double q2 = dx * dx + dy * dy + dz * dz;
@@ -468,7 +474,7 @@ void oracle_bs_acc(int n, const int32_t *mem, const double *x, const double *y, 
                    const double *m, const double *a, const double *rc, double G, double Mstar,
                    double n1, int mode, int form, int n_big, double *acc)
 {
-    bs_group g = {n, mem, m, a, rc, G, Mstar, n1, mode, form, n_big};
+    bs_group g = {n, mem, m, a, rc, G, Mstar, n1, mode, form, n_big, NULL};
     double *s = (double *)calloc((size_t)(6 * n > 0 ? 6 * n : 1), sizeof(double));
     double *ds = (double *)calloc((size_t)(6 * n > 0 ? 6 * n : 1), sizeof(double));
     for (int k = 0; k < n; k++) {
@@ -511,6 +517,46 @@ static void bs_midpoint(const bs_group *g, const double *y0, const double *f0, d
 static int bs_n(int k) { return 2 * (k + 1); }
 
 /*
+ * Perfect mergers (Sect. 2: collisions are perfect mergers) after an accepted
+ * sub-step: the first pair of members (in member order, i < j) that are not
+ * ghosts and overlap, |x_i - x_j| < R_i + R_j, merges -- member i keeps the
+ * total mass, the mass-weighted position and velocity and the radius
+ * (R_i^3 + R_j^3)^(1/3) (equal density); member j becomes a ghost with m = 0,
+ * R = 0 (its state is kept, it exerts and feels no group force) -- and the
+ * search repeats until no pair overlaps.  Returns the number of mergers.
+ */
+static int bs_merge(const bs_group *g, double *yv, double *m, double *R, int32_t *ghost)
+{
+    int merges = 0;
+    for (;;) {
+        int fi = -1, fj = -1;
+        for (int i = 0; i < g->n && fi < 0; i++) {
+            if (ghost[i]) continue;
+            for (int j = i + 1; j < g->n; j++) {
+                if (ghost[j]) continue;
+                double dx = yv[6 * j] - yv[6 * i], dy = yv[6 * j + 1] - yv[6 * i + 1];
+                double dz = yv[6 * j + 2] - yv[6 * i + 2];
+                double rr = R[g->mem[i]] + R[g->mem[j]];
+                if (dx * dx + dy * dy + dz * dz < rr * rr) { fi = i; fj = j; break; }
+            }
+        }
+        if (fi < 0) return merges;
+        int bi = g->mem[fi], bj = g->mem[fj];
+        double mi = m[bi], mj = m[bj], mt = mi + mj;
+        for (int c = 0; c < 6; c++) {
+            double u = yv[6 * fi + c], w = yv[6 * fj + c];
+            yv[6 * fi + c] = (mt > 0.0) ? (mi * u + mj * w) / mt : 0.5 * (u + w);
+        }
+        m[bi] = mt;
+        R[bi] = cbrt(R[bi] * R[bi] * R[bi] + R[bj] * R[bj] * R[bj]);
+        m[bj] = 0.0;
+        R[bj] = 0.0;
+        ghost[fj] = 1;
+        merges++;
+    }
+}
+
+/*
  * Bulirsch-Stoer integration of one group over dt (Stoer & Bulirsch,
  * Introduction to Numerical Analysis, Sect. 7.2.14): each sub-step h runs the
  * modified midpoint rule with n_k = 2, 4, ..., 16 steps and extrapolates the
@@ -522,15 +568,21 @@ static int bs_n(int k) { return 2 * (k + 1); }
  * A sub-step with no accepted column is halved; one accepted at a column
  * <= BS_GROW_COL doubles the next.  Sub-steps are fractions of dt; a sub-step
  * at BS_MIN_FRAC, or the last of BS_MAX_ATTEMPTS attempts (which covers the
- * rest of dt), is accepted at the last column anyway.  Updates the members'
- * entries of x..vz; returns 1 if such a forced acceptance happened, else 0.
+ * rest of dt), is accepted at the last column anyway.  With radii R (per
+ * body, NULL: no collisions) overlapping members merge after every accepted
+ * sub-step (bs_merge); the absorbed bodies get dead[b] = 1 (per body, needed
+ * with R), m = R = 0.  Updates the members' entries of x..vz, m, R; returns 1
+ * if an acceptance was forced, else 0; *merges (optional) accumulates the
+ * mergers.
  */
-int oracle_bs_group(int n, const int32_t *mem, double *x, double *y, double *z,
-                    double *vx, double *vy, double *vz, const double *m, const double *a,
-                    const double *rc, double G, double Mstar, double n1, int mode, int form,
-                    int n_big, double dt, double tol)
+int oracle_bs_group_full(int n, const int32_t *mem, double *x, double *y, double *z,
+                         double *vx, double *vy, double *vz, double *m, const double *a,
+                         const double *rc, double *R, int32_t *dead, double G, double Mstar,
+                         double n1, int mode, int form, int n_big, double dt, double tol,
+                         int *merges)
 {
-    bs_group g = {n, mem, m, a, rc, G, Mstar, n1, mode, form, n_big};
+    int32_t *ghost = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    bs_group g = {n, mem, m, a, rc, G, Mstar, n1, mode, form, n_big, ghost};
     int L = 6 * n;
     double *buf = (double *)malloc(sizeof(double) * (size_t)L * (7 + BS_KMAX * BS_KMAX));
     double *yv = buf, *f0 = yv + L, *zp = f0 + L, *zc = zp + L, *zn = zc + L, *fz = zn + L,
@@ -541,7 +593,7 @@ int oracle_bs_group(int n, const int32_t *mem, double *x, double *y, double *z,
         s[0] = x[b]; s[1] = y[b]; s[2] = z[b]; s[3] = vx[b]; s[4] = vy[b]; s[5] = vz[b];
     }
     double done = 0.0, frac = 1.0;           /* fractions of dt: exact binary values */
-    int forced = 0;
+    int forced = 0, nmerge = 0;
     for (int att = 0; att < BS_MAX_ATTEMPTS && done < 1.0; att++) {
         int last = (att == BS_MAX_ATTEMPTS - 1);
         if (last) frac = 1.0 - done;
@@ -583,6 +635,7 @@ int oracle_bs_group(int n, const int32_t *mem, double *x, double *y, double *z,
         if (acc_col < 0) { frac *= 0.5; continue; }
         const double *Tacc = T + (size_t)(acc_col * BS_KMAX + acc_col) * L;
         for (int q = 0; q < L; q++) yv[q] = Tacc[q];
+        if (R) nmerge += bs_merge(&g, yv, m, R, ghost);
         done += frac;
         if (acc_col <= BS_GROW_COL) frac *= 2.0;
         if (frac > 1.0 - done) frac = 1.0 - done;
@@ -591,30 +644,55 @@ int oracle_bs_group(int n, const int32_t *mem, double *x, double *y, double *z,
         int b = mem[k];
         const double *s = yv + 6 * k;
         x[b] = s[0]; y[b] = s[1]; z[b] = s[2]; vx[b] = s[3]; vy[b] = s[4]; vz[b] = s[5];
+        if (ghost[k] && dead) dead[b] = 1;
     }
+    if (merges) *merges += nmerge;
     free(buf);
+    free(ghost);
     return forced;
+}
+
+/* oracle_bs_group_full without collisions. */
+int oracle_bs_group(int n, const int32_t *mem, double *x, double *y, double *z,
+                    double *vx, double *vy, double *vz, const double *m, const double *a,
+                    const double *rc, double G, double Mstar, double n1, int mode, int form,
+                    int n_big, double dt, double tol)
+{
+    return oracle_bs_group_full(n, mem, x, y, z, vx, vy, vz, (double *)m, a, rc, NULL, NULL, G, Mstar,
+                                n1, mode, form, n_big, dt, tol, NULL);
 }
 
 /*
  * Drift of the hybrid step with the close-encounter level: HC(dt/2); every
  * body outside the groups of `pairs` (the encounter pairs of the step's
- * first kick) on its Kepler orbit, every group by oracle_bs_group (a, rc from
- * that kick); HC(dt/2).  Returns the number of Kepler solves that hit the
- * cap; *bs_forced (optional) gets the number of groups with a forced
- * Bulirsch-Stoer acceptance.
+ * first kick; pairs with a dead body do not count) on its Kepler orbit, every
+ * group by oracle_bs_group_full (a, rc from that kick; mergers when R is
+ * given); HC(dt/2); then removal: a body still alive with |x|^2 < r_in^2 or
+ * |x|^2 > r_out^2 (each test off when its radius is <= 0) becomes dead with
+ * m = 0 (and R = 0).  dead (per body) is needed with R or the radii.
+ * Returns the number of Kepler solves that hit the cap; *bs_forced and
+ * *merges (optional) get the groups with a forced Bulirsch-Stoer acceptance
+ * and the mergers.
  */
-int oracle_drift_groups(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
-                        const double *m, const double *a, const double *rc,
-                        int64_t npairs, const int32_t *pairs, double G, double Mstar, double n1,
-                        int mode, int form, int n_big, double dt, double tol, int max_iter,
-                        int *bs_forced)
+int oracle_drift_groups_full(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                             double *m, const double *a, const double *rc, double *R, int32_t *dead,
+                             int64_t npairs, const int32_t *pairs, double G, double Mstar, double n1,
+                             int mode, int form, int n_big, double dt, double tol, int max_iter,
+                             double r_in, double r_out, int *bs_forced, int *merges)
 {
-    int bad = 0, forced = 0;
+    int bad = 0, forced = 0, nmerge = 0;
     size_t n = (size_t)(N > 0 ? N : 1);
     int32_t *label = (int32_t *)malloc(sizeof(int32_t) * n);
     int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * n);
-    oracle_groups(N, npairs, pairs, label);
+    int32_t *live = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(npairs > 0 ? npairs : 1));
+    int64_t nlive = 0;
+    for (int64_t p = 0; p < npairs; p++) {
+        if (dead && (dead[pairs[2 * p]] || dead[pairs[2 * p + 1]])) continue;
+        live[2 * nlive] = pairs[2 * p];
+        live[2 * nlive + 1] = pairs[2 * p + 1];
+        nlive++;
+    }
+    oracle_groups(N, nlive, live, label);
     oracle_hc_drift(N, x, y, z, vx, vy, vz, m, Mstar, 0.5 * dt);
     #pragma omp parallel for reduction(+:bad)
     for (int i = 0; i < N; i++) {
@@ -629,25 +707,53 @@ int oracle_drift_groups(int N, double *x, double *y, double *z, double *vx, doub
         int cnt = 0;
         for (int v = r; v < N; v++)
             if (label[v] == r) mem[cnt++] = v;
-        forced += oracle_bs_group(cnt, mem, x, y, z, vx, vy, vz, m, a, rc, G, Mstar, n1, mode, form,
-                                  n_big, dt, tol);
+        forced += oracle_bs_group_full(cnt, mem, x, y, z, vx, vy, vz, m, a, rc, R, dead, G, Mstar, n1,
+                                       mode, form, n_big, dt, tol, &nmerge);
     }
     oracle_hc_drift(N, x, y, z, vx, vy, vz, m, Mstar, 0.5 * dt);
+    if (dead && (r_in > 0.0 || r_out > 0.0)) {
+        for (int i = 0; i < N; i++) {
+            if (dead[i]) continue;
+            double r2 = x[i] * x[i] + y[i] * y[i] + z[i] * z[i];
+            if ((r_in > 0.0 && r2 < r_in * r_in) || (r_out > 0.0 && r2 > r_out * r_out)) {
+                dead[i] = 1;
+                m[i] = 0.0;
+                if (R) R[i] = 0.0;
+            }
+        }
+    }
     if (bs_forced) *bs_forced = forced;
+    if (merges) *merges += nmerge;
     free(label);
     free(mem);
+    free(live);
     return bad;
+}
+
+/* oracle_drift_groups_full without collisions or removal. */
+int oracle_drift_groups(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                        const double *m, const double *a, const double *rc,
+                        int64_t npairs, const int32_t *pairs, double G, double Mstar, double n1,
+                        int mode, int form, int n_big, double dt, double tol, int max_iter,
+                        int *bs_forced)
+{
+    return oracle_drift_groups_full(N, x, y, z, vx, vy, vz, (double *)m, a, rc, NULL, NULL, npairs, pairs,
+                                    G, Mstar, n1, mode, form, n_big, dt, tol, max_iter, 0.0, 0.0,
+                                    bs_forced, NULL);
 }
 
 /*
  * Hybrid step with the close-encounter level, repeated nsteps times:
  * r_crit and the encounter pairs of the state, kick(dt/2), the drift of
- * oracle_drift_groups, kick(dt/2).  Returns the Kepler cap count; *bs_forced
- * (optional) accumulates the forced Bulirsch-Stoer acceptances.
+ * oracle_drift_groups_full (mergers with R, removal with r_in / r_out, dead
+ * flags per body), kick(dt/2).  Returns the Kepler cap count; *bs_forced and
+ * *merges (optional) accumulate the forced Bulirsch-Stoer acceptances and the
+ * mergers.
  */
-int oracle_step_bs(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
-                   const double *m, double G, double Mstar, double dt, double n1, double n2,
-                   int mode, int form, int n_big, int max_iter, double tol, int nsteps, int *bs_forced)
+int oracle_step_full(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                     double *m, double *R, int32_t *dead, double G, double Mstar, double dt, double n1,
+                     double n2, int mode, int form, int n_big, int max_iter, double tol, double r_in,
+                     double r_out, int nsteps, int *bs_forced, int *merges)
 {
     int bad = 0, forced = 0;
     size_t n = (size_t)(N > 0 ? N : 1);
@@ -671,14 +777,23 @@ int oracle_step_bs(int N, double *x, double *y, double *z, double *vx, double *v
         }
         oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, n_big, 0.5 * dt, ax, ay, az);
         int f = 0;
-        bad += oracle_drift_groups(N, x, y, z, vx, vy, vz, m, a, rc, np, pairs, G, Mstar, n1, mode, form,
-                                   n_big, dt, tol, max_iter, &f);
+        bad += oracle_drift_groups_full(N, x, y, z, vx, vy, vz, m, a, rc, R, dead, np, pairs, G, Mstar, n1,
+                                        mode, form, n_big, dt, tol, max_iter, r_in, r_out, &f, merges);
         forced += f;
         oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, n_big, 0.5 * dt, ax, ay, az);
     }
     if (bs_forced) *bs_forced += forced;
     free(ax); free(ay); free(az); free(a); free(rc); free(pairs);
     return bad;
+}
+
+/* oracle_step_full without collisions or removal. */
+int oracle_step_bs(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                   const double *m, double G, double Mstar, double dt, double n1, double n2,
+                   int mode, int form, int n_big, int max_iter, double tol, int nsteps, int *bs_forced)
+{
+    return oracle_step_full(N, x, y, z, vx, vy, vz, (double *)m, NULL, NULL, G, Mstar, dt, n1, n2, mode, form,
+                            n_big, max_iter, tol, 0.0, 0.0, nsteps, bs_forced, NULL);
 }
 
 /* ------------------------------------- energy and angular momentum -------- */

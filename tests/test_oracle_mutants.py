@@ -57,11 +57,20 @@ MUTANTS = {
     "level1_weight_is_K": ("double w = 1.0 - oracle_changeover(", "double w = oracle_changeover("),
     "level1_offset_sign": ("double dx = xj[0] - xi[0], dy", "double dx = xi[0] - xj[0], dy"),
     "level1_mass_index": ("double f = g->G * g->m[bj] * w", "double f = g->G * g->m[bi] * w"),
-    "level1_tp_pairs_kept": ("if (j == i || tp_pair(g->n_big, bi, bj)) continue;", "if (j == i) continue;"),
+    "level1_tp_pairs_kept": ("if (j == i || tp_pair(g->n_big, bi, bj) || bs_ghost", "if (j == i || bs_ghost"),
     "midpoint_step_factor": ("zn[q] = zp[q] + 2.0 * H * fz[q];", "zn[q] = zp[q] + H * fz[q];"),
     "extrapolation_in_h_not_h2": ("double cf = (nkj * nkj) / (nk * nk - nkj * nkj);",
                                   "double cf = nkj / (nk - nkj);"),
     "members_also_kepler_drifted": ("        if (label[i] >= 0) continue;\n", ""),
+    # mergers and removal
+    "merger_plain_average": ("yv[6 * fi + c] = (mt > 0.0) ? (mi * u + mj * w) / mt : 0.5 * (u + w);",
+                             "yv[6 * fi + c] = 0.5 * (u + w);"),
+    "merger_radius_sum": ("R[bi] = cbrt(R[bi] * R[bi] * R[bi] + R[bj] * R[bj] * R[bj]);", "R[bi] = R[bi] + R[bj];"),
+    "merger_overlap_one_radius": ("double rr = R[g->mem[i]] + R[g->mem[j]];", "double rr = R[g->mem[i]];"),
+    "merger_survivor_higher_index": ("        ghost[fj] = 1;\n", "        ghost[fi] = 1;\n"),
+    "ghosts_still_pull": ("|| bs_ghost(g, i) || bs_ghost(g, j)) continue;", ") continue;"),
+    "removal_outer_uses_inner": ("(r_out > 0.0 && r2 > r_out * r_out)", "(r_out > 0.0 && r2 > r_in * r_in)"),
+    "dead_pairs_grouped": ("        if (dead && (dead[pairs[2 * p]] || dead[pairs[2 * p + 1]])) continue;\n", ""),
 }
 
 
@@ -79,7 +88,8 @@ def _run_pins(so):
     env = dict(os.environ, ORACLE_LIB=so)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_bs.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_bs.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_merge.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return r.returncode
 
