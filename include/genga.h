@@ -89,6 +89,9 @@ typedef struct {
                                 encounter pairs of the preceding kick with a Bulirsch-Stoer
                                 method at this relative tolerance (1e-12 is typical);
                                 0: off, every body gets the Kepler drift */
+    double r_in, r_out;      /* removal radii (Sect. 2): after every drift a body closer than
+                                r_in to, or farther than r_out from, the central body is removed
+                                (see "ghosts" below); <= 0 switches each test off */
 } genga_params;
 
 typedef struct {
@@ -96,7 +99,18 @@ typedef struct {
     double *x, *y, *z;                   /* heliocentric positions, device [N] */
     double *vx, *vy, *vz;                /* barycentric velocities, device [N] */
     double *m;                           /* masses, device [N], >= 0 */
+    double *radius;                      /* physical radii (au), device [N], optional: with bs_tol > 0
+                                            overlapping members of a close-encounter group merge
+                                            (perfect mergers, Sect. 2); NULL: no collisions */
 } genga_system;
+
+/*
+ * Ghosts.  A body that merged into another one or crossed a removal radius
+ * stays in the arrays as a ghost until genga_compact: its mass is set to
+ * -0.0 (numerically zero; the sign bit is the mark) and its radius to 0, it
+ * exerts no force, is never an encounter pair and never merges again; it
+ * still moves (massless).  A caller may also mark bodies this way.
+ */
 
 typedef struct genga_ctx genga_ctx;
 
@@ -205,6 +219,16 @@ genga_status genga_step_batched(genga_ctx *ctx, genga_system *all, const int32_t
  */
 genga_status genga_energy(genga_ctx *ctx, const genga_system *sys, const genga_params *params,
                           double *E_L, void *stream);
+
+/*
+ * Remove the ghosts (bodies of mass -0.0: merged away or removed by the
+ * radii) from the arrays of `sys`: the other bodies keep their order and
+ * move to the front of x..m and radius, and of `id` (optional device int32
+ * [N] of body labels, moved along; NULL to skip).  Device-side stable
+ * compaction; synchronises `stream` and sets sys->N to the new count.  The
+ * spatial order and the encounter list are rebuilt by the next kick.
+ */
+genga_status genga_compact(genga_ctx *ctx, genga_system *sys, int32_t *id, void *stream);
 
 /* Synchronise `stream`, return the sticky device status (lowest set code) and
  * clear it.  Also returns GENGA_ERR_CUDA if the stream reports an error. */

@@ -522,7 +522,7 @@ static int bs_n(int k) { return 2 * (k + 1); }
  * ghosts and overlap, |x_i - x_j| < R_i + R_j, merges -- member i keeps the
  * total mass, the mass-weighted position and velocity and the radius
  * (R_i^3 + R_j^3)^(1/3) (equal density); member j becomes a ghost with m = 0,
- * R = 0 (its state is kept, it exerts and feels no group force) -- and the
+ * R = 0 (m = -0.0: its state is kept, it exerts and feels no group force) -- and the
  * search repeats until no pair overlaps.  Returns the number of mergers.
  */
 static int bs_merge(const bs_group *g, double *yv, double *m, double *R, int32_t *ghost)
@@ -549,7 +549,7 @@ static int bs_merge(const bs_group *g, double *yv, double *m, double *R, int32_t
         }
         m[bi] = mt;
         R[bi] = cbrt(R[bi] * R[bi] * R[bi] + R[bj] * R[bj] * R[bj]);
-        m[bj] = 0.0;
+        m[bj] = -0.0;                   /* the ghost mark: numerically zero, sign bit set */
         R[bj] = 0.0;
         ghost[fj] = 1;
         merges++;
@@ -717,7 +717,7 @@ int oracle_drift_groups_full(int N, double *x, double *y, double *z, double *vx,
             double r2 = x[i] * x[i] + y[i] * y[i] + z[i] * z[i];
             if ((r_in > 0.0 && r2 < r_in * r_in) || (r_out > 0.0 && r2 > r_out * r_out)) {
                 dead[i] = 1;
-                m[i] = 0.0;
+                m[i] = -0.0;
                 if (R) R[i] = 0.0;
             }
         }

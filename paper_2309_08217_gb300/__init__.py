@@ -36,11 +36,11 @@ class genga_params(C.Structure):
                 ("n1", C.c_double), ("n2", C.c_double),
                 ("rcrit_mode", C.c_int32), ("changeover", C.c_int32),
                 ("precision", C.c_int32), ("kepler_max_iter", C.c_int32), ("n_big", C.c_int32),
-                ("bs_tol", C.c_double)]
+                ("bs_tol", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double)]
 
 
 class genga_system(C.Structure):
-    _fields_ = [("N", C.c_int32)] + [(n, C.c_void_p) for n in ("x", "y", "z", "vx", "vy", "vz", "m")]
+    _fields_ = [("N", C.c_int32)] + [(n, C.c_void_p) for n in ("x", "y", "z", "vx", "vy", "vz", "m", "radius")]
 
 
 class GengaError(RuntimeError):
@@ -92,6 +92,7 @@ def load():
             "genga_tuning_times": ([V, I, C.POINTER(C.c_float), I], I),
             "genga_step_batched": ([V, S, C.POINTER(C.c_int32), I, P, I, V], I),
             "genga_get_kernel_variant": ([V, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], I),
+            "genga_compact": ([V, S, V, V], I),
         }
         for name, (args, res) in sigs.items():
             f = getattr(lib, name)
@@ -123,39 +124,50 @@ def _stream(stream):
 
 def make_params(G, Mstar=1.0, dt=6.0, n1=3.0, n2=0.4, rcrit_mode=GENGA_RCRIT_MUTUAL_HILL,
                 changeover=GENGA_K_CHAMBERS, precision=GENGA_FP32, kepler_max_iter=50, n_big=-1,
-                bs_tol=0.0) -> genga_params:
+                bs_tol=0.0, r_in=0.0, r_out=0.0) -> genga_params:
     """n_big >= 0: test-particle mode 2 (bodies n_big.. feel the first n_big bodies, not each other).
-    bs_tol > 0: the drift integrates the close-encounter groups (Bulirsch-Stoer, that tolerance)."""
+    bs_tol > 0: the drift integrates the close-encounter groups (Bulirsch-Stoer, that tolerance).
+    r_in, r_out > 0: removal radii (bodies inside / beyond become ghosts after each drift)."""
     return genga_params(G, Mstar, dt, n1, n2, rcrit_mode, changeover, precision, kepler_max_iter, n_big,
-                        bs_tol)
+                        bs_tol, r_in, r_out)
 
 
 class DeviceSystem:
-    """Seven float64 CUDA tensors (x, y, z, vx, vy, vz, m) and their genga_system view."""
+    """Seven float64 CUDA tensors (x, y, z, vx, vy, vz, m), optional physical
+    radii, and their genga_system view."""
 
-    def __init__(self, x, y, z, vx, vy, vz, m):
+    def __init__(self, x, y, z, vx, vy, vz, m, radius=None):
         self.tensors = [x, y, z, vx, vy, vz, m]
-        for t in self.tensors:
+        self.radius = radius
+        for t in self.tensors + ([radius] if radius is not None else []):
             if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
                 raise ValueError("state arrays must be contiguous float64 CUDA tensors")
-        self.c = genga_system(int(m.numel()), *[t.data_ptr() for t in self.tensors])
+        self.c = genga_system(int(m.numel()), *[t.data_ptr() for t in self.tensors],
+                              radius.data_ptr() if radius is not None else None)
 
     @property
     def N(self):
         return int(self.c.N)
 
     @classmethod
-    def from_disc(cls, disc, device="cuda"):
+    def from_disc(cls, disc, device="cuda", radius=None):
         import torch
-        return cls(*[torch.tensor(a, dtype=torch.float64, device=device) for a in disc.arrays()])
+        r = None if radius is None else torch.tensor(radius, dtype=torch.float64, device=device)
+        return cls(*[torch.tensor(a, dtype=torch.float64, device=device) for a in disc.arrays()], radius=r)
 
     @classmethod
-    def from_arrays(cls, arrays, device="cuda"):
+    def from_arrays(cls, arrays, device="cuda", radius=None):
         import torch
-        return cls(*[torch.as_tensor(a, dtype=torch.float64).to(device).contiguous() for a in arrays])
+        r = None if radius is None else torch.as_tensor(radius, dtype=torch.float64).to(device).contiguous()
+        return cls(*[torch.as_tensor(a, dtype=torch.float64).to(device).contiguous() for a in arrays], radius=r)
 
     def numpy(self):
-        return [t.detach().cpu().numpy().copy() for t in self.tensors]
+        """The N current bodies' seven arrays (after genga_compact: the first N entries)."""
+        n = self.N
+        return [t.detach()[:n].cpu().numpy().copy() for t in self.tensors]
+
+    def radius_numpy(self):
+        return None if self.radius is None else self.radius.detach()[: self.N].cpu().numpy().copy()
 
 
 class Context:
@@ -241,6 +253,14 @@ def genga_energy(ctx, sys, params, stream=None):
     out = (C.c_double * 4)()
     _check(load().genga_energy(_ctx(ctx), _sys(sys), C.byref(params), out, _stream(stream)), "genga_energy")
     return list(out)
+
+
+def genga_compact(ctx, sys, id=None, stream=None) -> int:
+    """Remove the ghosts (merged or removed bodies) from sys's arrays, keeping the
+    others in order (and id, an optional int32 CUDA tensor, along); returns the
+    new N (sys's view is updated)."""
+    _check(load().genga_compact(_ctx(ctx), _sys(sys), _ptr(id), _stream(stream)), "genga_compact")
+    return int((sys.c if isinstance(sys, DeviceSystem) else sys).N)
 
 
 def genga_get_status(ctx, stream=None) -> int:

@@ -39,6 +39,7 @@ genga_status check_params(const genga_params *p) {
     if (p->kepler_max_iter < 1) return GENGA_ERR_INVALID_ARG;
     if (p->n_big < -1) return GENGA_ERR_INVALID_ARG;
     if (!is_fin(p->bs_tol) || p->bs_tol < 0.0) return GENGA_ERR_INVALID_ARG;
+    if (!is_fin(p->r_in) || !is_fin(p->r_out)) return GENGA_ERR_INVALID_ARG;
     return GENGA_OK;
 }
 
@@ -743,6 +744,28 @@ genga_status genga_energy(genga_ctx *c, const genga_system *sys, const genga_par
         E_L[q] = sum + comp;
     }
     free(host);
+    return GENGA_OK;
+}
+
+genga_status genga_compact(genga_ctx *c, genga_system *sys, int32_t *id, void *stream) {
+    genga_status st;
+    if ((st = check_system(c, sys)) != GENGA_OK) return st;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (sys->N == 0) return GENGA_OK;
+    genga_system s2 = *sys;
+    cudaError_t e = launch_compact(c, s2, id, c->gcount, s);
+    int32_t n = sys->N;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n, c->gcount, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return GENGA_ERR_CUDA;
+    c->launches += 4;
+    if (n != sys->N) {  // the order, the list and the step graph belong to the old arrays
+        c->ordered_N = -1;
+        cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s);
+        c->enc_sorted = true;
+    }
+    sys->N = n;
     return GENGA_OK;
 }
 

@@ -155,6 +155,20 @@ __global__ void drift_kernel(double *__restrict__ x, double *__restrict__ y, dou
     vx[i] = ui; vy[i] = vi; vz[i] = wi;
 }
 
+// Removal radii (Sect. 2): a live body with |x|^2 < r_in^2 or |x|^2 > r_out^2
+// (a test off when its radius is <= 0) becomes a ghost: m = -0.0, R = 0.
+__global__ void removal_kernel(const double *__restrict__ x, const double *__restrict__ y,
+                               const double *__restrict__ z, double *__restrict__ m, double *__restrict__ radius,
+                               int N, double rin2, double rout2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N || signbit(m[i])) return;
+    const double r2 = x[i] * x[i] + y[i] * y[i] + z[i] * z[i];
+    if ((rin2 > 0.0 && r2 < rin2) || (rout2 > 0.0 && r2 > rout2)) {
+        m[i] = -0.0;
+        if (radius) radius[i] = 0.0;
+    }
+}
+
 __global__ void hc_kernel(double *__restrict__ x, double *__restrict__ y, double *__restrict__ z, int N,
                           const double *__restrict__ P, double hM) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -239,6 +253,7 @@ cudaError_t launch_level1(genga_system &sys, const genga_params &p, double dt, g
     b.grp = c->grp;
     b.gmark = c->gmark;
     b.tpf = c->bs_tp;
+    b.radius = sys.radius;
     b.bs = c->bs_work;
     b.slots = c->bs_slots;
     b.G = p.G;
@@ -250,6 +265,13 @@ cudaError_t launch_level1(genga_system &sys, const genga_params &p, double dt, g
     b.changeover = p.changeover;
     b.status = c->status;
     return launch_bs(b, c->sm_count, s);
+}
+
+cudaError_t launch_removal(genga_system &sys, const genga_params &p, cudaStream_t s) {
+    if (sys.N <= 0 || (p.r_in <= 0.0 && p.r_out <= 0.0)) return cudaSuccess;
+    const double rin2 = p.r_in > 0.0 ? p.r_in * p.r_in : 0.0, rout2 = p.r_out > 0.0 ? p.r_out * p.r_out : 0.0;
+    removal_kernel<<<(sys.N + 255) / 256, 256, 0, s>>>(sys.x, sys.y, sys.z, sys.m, sys.radius, sys.N, rin2, rout2);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_drift_batched(genga_system &all, const BatchBodies &bb, const genga_params &p, double dt,
@@ -268,7 +290,8 @@ cudaError_t launch_drift_batched(genga_system &all, const BatchBodies &bb, const
     e = launch_momentum_batched(all, bb, c->Pd, nullptr, s);
     if (e != cudaSuccess) return e;
     hc_batched_kernel<<<(N + 255) / 256, 256, 0, s>>>(all.x, all.y, all.z, c->Pd, 0.5 * dt / p.Mstar, bb);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_removal(all, p, s);
 }
 
 cudaError_t launch_drift(genga_system &sys, const genga_params &p, double dt, genga_ctx *c, cudaStream_t s) {
@@ -287,7 +310,8 @@ cudaError_t launch_drift(genga_system &sys, const genga_params &p, double dt, ge
     e = launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, N, c->mom, nullptr, s);
     if (e != cudaSuccess) return e;
     hc_kernel<<<(N + 255) / 256, 256, 0, s>>>(sys.x, sys.y, sys.z, N, c->mom, 0.5 * dt / p.Mstar);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_removal(sys, p, s);
 }
 
 }  // namespace genga

@@ -207,7 +207,8 @@ enum : int {
     F_M = F_ISC + 2,                      // mass
     F_A = F_M + 1,                        // osculating a of the first kick
     F_RC = F_A + 1,                       // Eq. 1 radius of the first kick
-    F_Z = F_RC + 1,                       // per column k: three rotating midpoint states (18 fields)
+    F_RAD = F_RC + 1,                     // physical radius (mergers)
+    F_Z = F_RAD + 1,                      // per column k: three rotating midpoint states (18 fields)
     F_T = F_Z + 18 * BS_KMAX,             // per column k: the smoothed midpoint result T[k][0] (6 fields)
     F_PR2 = F_T + 6 * BS_KMAX,            // r_crit,ij^2 with the first BS_PAIR_TAB members
     F_PIN = F_PR2 + BS_PAIR_TAB,          // 1 / (0.9 r_crit,ij)
@@ -271,10 +272,12 @@ __device__ void level1_acc(const BSArgs &a, const Work &W, int s, int s0, int n,
     ax = c * xi;
     ay = c * yi;
     az = c * zi;
-    const bool tpi = a.tpf[s] != 0;
+    const int fi = a.tpf[s];
+    if (fi & 2) return;  // a ghost feels the central body only
     const double *__restrict__ M = W.f(F_M);
     for (int t = s0; t < s0 + n; t++) {
-        if (t == s || (tpi && a.tpf[t] != 0)) continue;
+        const int ft = a.tpf[t];
+        if (t == s || (ft & 2) || ((fi & 1) && (ft & 1))) continue;  // self, ghost, two test particles
         const double dx = px[t] - xi, dy = py[t] - yi, dz = pz[t] - zi;
         const double q2 = dx * dx + dy * dy + dz * dz;
         if (q2 == 0.0) continue;
@@ -347,8 +350,8 @@ __device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, 
     const bool act = q < n;
     const int nk = 2 * (k + 1);
     double y[6] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0};  // inactive lanes: a harmless circular state
-    double mq = 0.0, aq = 1.0, rcq = 1.0;
-    int tpq = 0, v = -1;
+    double mq = 0.0, aq = 1.0, rcq = 1.0, Rq = 0.0;
+    int tpq = 0, ghq = 0, v = -1;
     if (act) {
         v = a.gbody[s0 + q];
         const int kp = (int)a.iperm[v];
@@ -358,22 +361,27 @@ __device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, 
         aq = a.a_osc[kp];
         rcq = a.rc_eq1[kp];
         tpq = a.lo[kp].w != 0.f ? 1 : 0;
+        ghq = signbit(mq) ? 1 : 0;  // a ghost (m = -0.0)
+        if (a.radius) Rq = a.radius[v];
     }
-    // partner constants (fixed over the drift)
+    // partner constants (fixed over the drift, recomputed after a merger)
     double gm[4], rc2[4], lo2[4], inv9[4];
     bool use[4];
+    auto partners = [&]() {
 #pragma unroll
-    for (int p = 0; p < 4; p++) {
-        const double mp = shfl_d(mq, 8 * p), ap = shfl_d(aq, 8 * p), rcp = shfl_d(rcq, 8 * p);
-        const int tpp = __shfl_sync(0xffffffffu, tpq, 8 * p);
-        use[p] = act && p < n && p != q && !(tpq && tpp);
-        double rc = 1.0;
-        if (use[p]) rc = pair_radius(a, mq, mp, aq, ap, rcq, rcp);
-        gm[p] = a.G * mp;
-        rc2[p] = rc * rc;
-        lo2[p] = (0.1 * rc) * (0.1 * rc);
-        inv9[p] = 1.0 / (0.9 * rc);
-    }
+        for (int p = 0; p < 4; p++) {
+            const double mp = shfl_d(mq, 8 * p), ap = shfl_d(aq, 8 * p), rcp = shfl_d(rcq, 8 * p);
+            const int tpp = __shfl_sync(0xffffffffu, tpq, 8 * p), ghp = __shfl_sync(0xffffffffu, ghq, 8 * p);
+            use[p] = act && p < n && p != q && !(tpq && tpp) && !ghq && !ghp;
+            double rc = 1.0;
+            if (use[p]) rc = pair_radius(a, mq, mp, aq, ap, rcq, rcp);
+            gm[p] = a.G * mp;
+            rc2[p] = rc * rc;
+            lo2[p] = (0.1 * rc) * (0.1 * rc);
+            inv9[p] = 1.0 / (0.9 * rc);
+        }
+    };
+    partners();
     const double mgm = -a.G * a.Mstar;
     // level-1 acceleration of this lane's member at (x, y, z) of its column
     auto accel = [&](double x, double yy, double z, double &ax, double &ay, double &az) {
@@ -493,6 +501,55 @@ __device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, 
             const double nv = shfl_d(pick, 8 * q + cc);
             if (act) y[cc] = nv;
         }
+        if (a.radius) {  // perfect mergers: the first overlapping pair (i < j), again until none
+            for (int it = 0; it < 3; it++) {
+                double ox[4], oy[4], oz[4], oR[4];
+                int og[4];
+#pragma unroll
+                for (int p = 0; p < 4; p++) {
+                    ox[p] = shfl_d(y[0], 8 * p);
+                    oy[p] = shfl_d(y[1], 8 * p);
+                    oz[p] = shfl_d(y[2], 8 * p);
+                    oR[p] = shfl_d(Rq, 8 * p);
+                    og[p] = __shfl_sync(0xffffffffu, ghq, 8 * p);
+                }
+                int code = 16;  // 4 i + j of the first overlapping pair, 16: none
+                if (act && k == 0 && !ghq) {
+#pragma unroll
+                    for (int p = 3; p > 0; p--) {  // smallest j last
+                        if (p <= q || p >= n || og[p]) continue;
+                        const double dx = ox[p] - y[0], dy = oy[p] - y[1], dz = oz[p] - y[2];
+                        const double rr = Rq + oR[p];
+                        if (dx * dx + dy * dy + dz * dz < rr * rr) code = 4 * q + p;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) code = min(code, __shfl_xor_sync(0xffffffffu, code, o));
+                if (code == 16) break;
+                const int fi = code >> 2, fj = code & 3;
+                const double mi = shfl_d(mq, 8 * fi), mj = shfl_d(mq, 8 * fj), mt = mi + mj;
+                double nyv[6];
+#pragma unroll
+                for (int cc = 0; cc < 6; cc++) {
+                    const double u = shfl_d(y[cc], 8 * fi), w = shfl_d(y[cc], 8 * fj);
+                    nyv[cc] = (mt > 0.0) ? (mi * u + mj * w) / mt : 0.5 * (u + w);
+                }
+                const double Ri = shfl_d(Rq, 8 * fi), Rj = shfl_d(Rq, 8 * fj);
+                const double Rn = cbrt(Ri * Ri * Ri + Rj * Rj * Rj);
+                if (q == fi) {
+#pragma unroll
+                    for (int cc = 0; cc < 6; cc++) y[cc] = nyv[cc];
+                    mq = mt;
+                    Rq = Rn;
+                }
+                if (q == fj) {
+                    mq = 0.0;
+                    Rq = 0.0;
+                    ghq = 1;
+                }
+                partners();
+            }
+        }
         done += frac;
         if (acc_col <= BS_GROW_COL) frac *= 2.0;
         if (frac > 1.0 - done) frac = 1.0 - done;
@@ -500,6 +557,10 @@ __device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, 
     if (act && k == 0) {
         a.x[v] = y[0]; a.y[v] = y[1]; a.z[v] = y[2];
         a.vx[v] = y[3]; a.vy[v] = y[4]; a.vz[v] = y[5];
+        if (a.radius) {
+            a.m[v] = ghq ? -0.0 : mq;
+            a.radius[v] = Rq;
+        }
         a.grp[v] = -1;
         a.gmark[v] = 0;
     }
@@ -524,10 +585,11 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
             W(F_M, s) = a.m[v];
             W(F_A, s) = a.a_osc[k];
             W(F_RC, s) = a.rc_eq1[k];
-            a.tpf[s] = a.lo[k].w != 0.f ? 1 : 0;
+            W(F_RAD, s) = a.radius ? a.radius[v] : 0.0;
+            a.tpf[s] = (a.lo[k].w != 0.f ? 1 : 0) | (signbit(a.m[v]) ? 2 : 0);
         }
         __syncwarp();
-        if (tab) {  // pair radii, fixed over the drift
+        auto pair_table = [&]() {  // pair radii, fixed over the drift (masses change only in mergers)
             for (int idx = lane; idx < n * n; idx += 32) {
                 const int si = s0 + idx / n, ti = idx % n;
                 const double rc = pair_radius(a, W(F_M, si), W(F_M, s0 + ti), W(F_A, si), W(F_A, s0 + ti),
@@ -536,7 +598,8 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
                 W(F_PIN + ti, si) = 1.0 / (0.9 * rc);
             }
             __syncwarp();
-        }
+        };
+        if (tab) pair_table();
         double done = 0.0, frac = 1.0;
         for (int att = 0; att < BS_MAX_ATTEMPTS && done < 1.0; att++) {
             int late = 0;
@@ -636,6 +699,40 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
                 for (int c = 0; c < 6; c++) W(F_Y + c, s) = W(F_T + 6 * acc_col + c, s);
             }
             __syncwarp();
+            if (a.radius) {  // perfect mergers: the first overlapping pair (i < j), again until none
+                for (int it = 0; it < n - 1; it++) {
+                    int code = n * n;  // i n + j of the first overlapping pair
+                    for (int idx = lane; idx < n * n; idx += 32) {
+                        const int i = idx / n, j = idx % n;
+                        if (j <= i) continue;
+                        const int si = s0 + i, sj = s0 + j;
+                        if ((a.tpf[si] | a.tpf[sj]) & 2) continue;
+                        const double dx = W(F_Y, sj) - W(F_Y, si), dy = W(F_Y + 1, sj) - W(F_Y + 1, si);
+                        const double dz = W(F_Y + 2, sj) - W(F_Y + 2, si);
+                        const double rr = W(F_RAD, si) + W(F_RAD, sj);
+                        if (dx * dx + dy * dy + dz * dz < rr * rr) code = min(code, idx);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) code = min(code, __shfl_xor_sync(0xffffffffu, code, o));
+                    if (code == n * n) break;
+                    const int si = s0 + code / n, sj = s0 + code % n;
+                    if (lane == 0) {
+                        const double mi = W(F_M, si), mj = W(F_M, sj), mt = mi + mj;
+                        for (int c = 0; c < 6; c++) {
+                            const double u = W(F_Y + c, si), w = W(F_Y + c, sj);
+                            W(F_Y + c, si) = (mt > 0.0) ? (mi * u + mj * w) / mt : 0.5 * (u + w);
+                        }
+                        const double Ri = W(F_RAD, si), Rj = W(F_RAD, sj);
+                        W(F_RAD, si) = cbrt(Ri * Ri * Ri + Rj * Rj * Rj);
+                        W(F_M, si) = mt;
+                        W(F_M, sj) = 0.0;
+                        W(F_RAD, sj) = 0.0;
+                        a.tpf[sj] |= 2;
+                    }
+                    __syncwarp();
+                    if (tab) pair_table();
+                }
+            }
             done += frac;
             if (acc_col <= BS_GROW_COL) frac *= 2.0;
             if (frac > 1.0 - done) frac = 1.0 - done;
@@ -648,6 +745,10 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
             a.vx[v] = W(F_Y + 3, s);
             a.vy[v] = W(F_Y + 4, s);
             a.vz[v] = W(F_Y + 5, s);
+            if (a.radius) {
+                a.m[v] = (a.tpf[s] & 2) ? -0.0 : W(F_M, s);
+                a.radius[v] = W(F_RAD, s);
+            }
             a.grp[v] = -1;
             a.gmark[v] = 0;
         }

@@ -38,7 +38,7 @@
 
 // Close-encounter level: doubles of level-1 workspace per group member
 // (encounter.cu), and the most members one drift can integrate.
-#define GENGA_BS_FIELDS 238
+#define GENGA_BS_FIELDS 239
 #define GENGA_BS_MAX_SLOTS (1 << 18)
 
 namespace genga {
@@ -201,12 +201,13 @@ struct GroupArgs {              // grouping of the encounter pairs (one CTA)
 
 struct BSArgs {                 // level-1 integration of the groups (one warp per group)
     double *x, *y, *z, *vx, *vy, *vz;
-    const double *m;
+    double *m;                  // written back only by mergers
     const uint32_t *iperm;      // packed position of each body: a_osc, rc_eq1, lo.w (test particle)
     const double *a_osc, *rc_eq1;
     const float4 *lo;
     const int32_t *gcount, *gstart, *gsize, *gmem;
-    int32_t *gbody, *grp, *gmark, *tpf;
+    int32_t *gbody, *grp, *gmark, *tpf;  // tpf per slot: 1 test particle, 2 ghost
+    double *radius;             // physical radii (NULL: no mergers)
     double *bs;                 // GENGA_BS_FIELDS fields of `slots` doubles
     int32_t slots;
     double G, Mstar, n1, dt, tol;
@@ -215,6 +216,8 @@ struct BSArgs {                 // level-1 integration of the groups (one warp p
 };
 
 cudaError_t launch_groups(const GroupArgs &g, cudaStream_t s);
+cudaError_t launch_removal(genga_system &sys, const genga_params &p, cudaStream_t s);
+cudaError_t launch_compact(genga_ctx *c, genga_system &sys, int32_t *id, int32_t *count, cudaStream_t s);
 cudaError_t launch_bs(const BSArgs &b, int sm_count, cudaStream_t s);
 cudaError_t launch_momentum(const double *vx, const double *vy, const double *vz, const double *m,
                             int N, double *P, int32_t *zero_me, cudaStream_t s);

@@ -102,7 +102,8 @@ __device__ __forceinline__ double changeover_K(double y, int form) {
 // Exact FP64 treatment of one screened pair (packed positions i, j of one
 // system whose packed range starts at poff, with Nd bodies that start at
 // body `off` of the caller's arrays): the K-weighted acceleration of i due to
-// j; records the encounter.
+// j; records the encounter unless one of the two is a ghost (merged away or
+// removed: mass -0.0, so its force is zero anyway).
 __device__ __noinline__ double3 screened_pair(const PassArgs &a, int i, int j, int poff, int Nd, int off) {
     double3 f = make_double3(0.0, 0.0, 0.0);
     if (i - poff >= Nd || j - poff >= Nd || i == j) return f;
@@ -121,7 +122,7 @@ __device__ __noinline__ double3 screened_pair(const PassArgs &a, int i, int j, i
     }
     double K = 1.0;
     if (r < rc) {
-        if (oi < oj) {
+        if (oi < oj && !(signbit(a.m[oi]) || signbit(a.m[oj]))) {  // ghosts (m = -0) are never encounter pairs
             const int pos = atomicAdd(a.enc_count, 1);
             if (pos < a.enc_cap) a.enc[pos] = make_int2(oi, oj);
         }

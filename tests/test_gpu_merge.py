@@ -1,0 +1,128 @@
+"""Perfect mergers, removal radii and compaction on the GPU (genga_step with
+bs_tol > 0 and physical radii; params r_in / r_out; genga_compact) against
+the oracle's step with the same switches.
+
+The merged masses, radii and the set of ghosts (mass -0.0) must be
+identical; positions and velocities agree to 1e-10 of |x| and |v| (FP64
+kick) as in the other close-encounter tests.  Compaction keeps the
+survivors' order and moves an id array along.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests.gpu_cases import planted_disc
+from tests.test_gpu_bs import _rel_state, _swarm
+
+pytestmark = pytest.mark.gpu
+
+TOL_BS = 1e-12
+
+
+def _params(g, d, precision=0, n_big=-1, r_in=0.0, r_out=0.0):
+    return g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, n1=3.0, n2=0.4, precision=precision, n_big=n_big,
+                         bs_tol=TOL_BS, r_in=r_in, r_out=r_out)
+
+
+@pytest.fixture(scope="module")
+def ctx(genga):
+    c = genga.Context(4096)
+    yield c
+    c.close()
+
+
+def _run_both(genga, ctx, d, R, steps, precision=0, n_big=-1, r_in=0.0, r_out=0.0):
+    import torch
+    s = genga.DeviceSystem.from_disc(d, radius=R)
+    ids = torch.arange(d.N, dtype=torch.int32, device="cuda")
+    genga.genga_step(ctx, s, _params(genga, d, precision, n_big, r_in, r_out), steps)
+    assert genga.genga_get_status(ctx) == genga.GENGA_OK
+    got = s.numpy()
+    got_R = s.radius_numpy()
+    arr = oracle.disc_arrays(d)
+    Ro = np.array(R, dtype=np.float64).copy()
+    dead = np.zeros(d.N, np.int32)
+    merges, forced = [0], [0]
+    assert oracle.step(arr, d.G, d.Mstar, d.dt, 3.0, 0.4, 1, 0, steps, n_big=n_big, bs_tol=TOL_BS, forced=forced,
+                       radius=Ro, dead=dead, r_in=r_in, r_out=r_out, merges=merges) == 0
+    assert forced[0] == 0
+    return s, ids, got, got_R, arr, Ro, dead, merges[0]
+
+
+def test_head_on_pair_merges(genga, ctx):
+    """planted_disc's closest pair starts at rest relative to each other and
+    falls in during the second step: with radii it merges instead of meeting
+    the singularity."""
+    d = planted_disc(800, 17)
+    R = np.full(d.N, 2e-5)
+    s, ids, got, got_R, arr, Ro, dead, merges = _run_both(genga, ctx, d, R, 3)
+    assert merges >= 1 and dead[1] == 1 and dead[0] == 0
+    assert np.array_equal(np.signbit(got[6]), dead == 1)
+    np.testing.assert_allclose(got[6], arr[6], rtol=1e-15, atol=0)
+    np.testing.assert_allclose(got_R, Ro, rtol=1e-14, atol=0)
+    assert _rel_state(got, arr) < 1e-10
+    # compaction drops exactly the ghosts, in order, with the ids
+    n = genga.genga_compact(ctx, s, ids)
+    assert n == d.N - int(dead.sum())
+    keep = np.nonzero(dead == 0)[0]
+    assert np.array_equal(ids[:n].cpu().numpy(), keep)
+    after = s.numpy()
+    for c in range(7):
+        assert np.array_equal(after[c], got[c][keep])
+    assert np.array_equal(s.radius_numpy(), got_R[keep])
+
+
+def test_removal_radii(genga, ctx):
+    d = planted_disc(1500, 5, a_min=0.5, a_max=3.0)
+    R = np.full(d.N, 1e-6)
+    s, ids, got, got_R, arr, Ro, dead, merges = _run_both(genga, ctx, d, R, 2, precision=1, r_in=0.62, r_out=2.8)
+    assert dead.sum() >= 4
+    assert np.array_equal(np.signbit(got[6]), dead == 1)
+    assert np.array_equal(got_R == 0.0, dead == 1)
+    assert _rel_state(got, arr) < 1e-9
+    n = genga.genga_compact(ctx, s, ids)
+    assert np.array_equal(ids[:n].cpu().numpy(), np.nonzero(dead == 0)[0])
+    # the compacted system steps on like the oracle's compacted one
+    p = _params(genga, d, 1, r_in=0.62, r_out=2.8)
+    genga.genga_step(ctx, s, p, 1)
+    assert genga.genga_get_status(ctx) == genga.GENGA_OK
+    keep = dead == 0
+    arr2 = [a[keep].copy() for a in arr]
+    R2, dead2 = Ro[keep].copy(), np.zeros(int(keep.sum()), np.int32)
+    assert oracle.step(arr2, d.G, d.Mstar, d.dt, 3.0, 0.4, 1, 0, 1, bs_tol=TOL_BS, radius=R2, dead=dead2,
+                       r_in=0.62, r_out=2.8) == 0
+    assert _rel_state(s.numpy(), arr2) < 1e-9
+
+
+@pytest.mark.parametrize("n_big", [-1, 1])
+def test_swarm_mergers_large_group(genga, ctx, n_big):
+    """The planet with 80 bodies around it, with a planet radius of 0.02 au:
+    the bodies inside it at the first sub-step and those that reach it merge
+    into it (body 0, the lowest index); a group wider than a warp."""
+    d = _swarm()
+    R = np.full(d.N, 1e-6)
+    R[0] = 0.02
+    s, ids, got, got_R, arr, Ro, dead, merges = _run_both(genga, ctx, d, R, 2, n_big=n_big)
+    assert merges >= 5 and dead[0] == 0
+    assert np.array_equal(np.signbit(got[6]), dead == 1)
+    np.testing.assert_allclose(got[6], arr[6], rtol=1e-14, atol=0)
+    np.testing.assert_allclose(got_R, Ro, rtol=1e-13, atol=0)
+    assert _rel_state(got, arr) < 1e-10
+
+
+def test_no_radius_no_mergers(genga, ctx):
+    """Without radii the same state keeps every body (and meets the head-on
+    singularity as a forced sub-step)."""
+    d = planted_disc(800, 17)
+    s = genga.DeviceSystem.from_disc(d)
+    genga.genga_step(ctx, s, _params(genga, d), 3)
+    assert genga.genga_get_status(ctx) == genga.GENGA_ERR_BS
+    assert np.all(s.numpy()[6] > 0)
+
+
+def test_invalid_radii_rejected(genga, ctx):
+    d = planted_disc(10, 1)
+    s = genga.DeviceSystem.from_disc(d)
+    for bad in (float("nan"), float("inf")):
+        with pytest.raises(genga.GengaError):
+            genga.genga_drift(ctx, s, _params(genga, d, r_out=bad), 1.0)
