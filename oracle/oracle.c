@@ -565,6 +565,8 @@ static int bs_merge(const bs_group *g, double *yv, double *m, double *R, int32_t
  * Column k (k >= 1) is accepted when, for every member,
  *   max_c |T[k][k] - T[k][k-1]| <= tol * |x| (position) and tol * |v| (velocity)
  * (norms of the member's state at the start of the sub-step; 1 where zero).
+ * The first sub-step is the largest binary fraction f of dt for which no
+ * interacting pair moves by more than its separation (f |dt| |v_ij| <= r_ij).
  * A sub-step with no accepted column is halved; one accepted at a column
  * <= BS_GROW_COL doubles the next.  Sub-steps are fractions of dt; a sub-step
  * at BS_MIN_FRAC, or the last of BS_MAX_ATTEMPTS attempts (which covers the
@@ -594,6 +596,20 @@ int oracle_bs_group_full(int n, const int32_t *mem, double *x, double *y, double
     }
     double done = 0.0, frac = 1.0;           /* fractions of dt: exact binary values */
     int forced = 0, nmerge = 0;
+    /* first sub-step: the largest binary fraction f of dt with f |dt| |v_ij| <= |x_ij|
+       for every interacting pair (no pair crosses more than its separation in it) */
+    for (int i = 0; i < n; i++) {
+        for (int j = i + 1; j < n; j++) {
+            if (tp_pair(n_big, mem[i], mem[j])) continue;
+            const double *si = yv + 6 * i, *sj = yv + 6 * j;
+            double dx = sj[0] - si[0], dy = sj[1] - si[1], dz = sj[2] - si[2];
+            double ux = sj[3] - si[3], uy = sj[4] - si[4], uz = sj[5] - si[5];
+            double r2 = dx * dx + dy * dy + dz * dz, v2 = ux * ux + uy * uy + uz * uz;
+            double f = 1.0;
+            while (f > BS_MIN_FRAC && (f * fabs(dt)) * (f * fabs(dt)) * v2 > r2) f *= 0.5;
+            if (f < frac) frac = f;
+        }
+    }
     for (int att = 0; att < BS_MAX_ATTEMPTS && done < 1.0; att++) {
         int last = (att == BS_MAX_ATTEMPTS - 1);
         if (last) frac = 1.0 - done;

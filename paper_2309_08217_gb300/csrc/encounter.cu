@@ -325,6 +325,33 @@ __device__ __forceinline__ double warp_max(double v) {
 // GENGA_ERR_BS is raised.
 __device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
+// Largest binary fraction f of |dt| with (f |dt|)^2 v2 <= r2 (a pair crosses at
+// most its separation in the first sub-step); rounded products as written,
+// no contraction, so the decision is the oracle's.
+__device__ __forceinline__ double first_frac(double dx, double dy, double dz, double ux, double uy, double uz,
+                                             double adt) {
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    const double v2 = __dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
+    double f = 1.0;
+    for (int it = 0; it < 40 && f > BS_MIN_FRAC; it++) {
+        const double h = __dmul_rn(f, adt);
+        if (!(__dmul_rn(__dmul_rn(h, h), v2) > r2)) break;
+        f *= 0.5;
+    }
+    return f;
+}
+
+// Warp minimum of non-negative doubles, compared as integers.
+__device__ __forceinline__ double warp_min_nonneg(double v) {
+    long long b = __double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long t = __shfl_xor_sync(0xffffffffu, b, o);
+        b = t < b ? t : b;
+    }
+    return __longlong_as_double(b);
+}
+
 // Warp maximum of non-negative doubles, compared as integers (their bit
 // patterns order like the values), off the FP64 pipe.
 __device__ __forceinline__ double warp_max_nonneg(double v) {
@@ -411,7 +438,27 @@ __device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, 
             az = fma(f, dz, az);
         }
     };
-    double done = 0.0, frac = 1.0;
+    double done = 0.0, frac;
+    {  // first sub-step from the fastest interacting pair (lanes 8 q, partners p > q)
+        double f = 1.0;
+        double ox[6][4];
+        int otp[4];
+#pragma unroll
+        for (int p = 0; p < 4; p++) {  // every lane takes part in the shuffles
+#pragma unroll
+            for (int c = 0; c < 6; c++) ox[c][p] = shfl_d(y[c], 8 * p);
+            otp[p] = __shfl_sync(0xffffffffu, tpq, 8 * p);
+        }
+        if (act && k == 0) {
+#pragma unroll
+            for (int p = 1; p < 4; p++) {
+                if (p <= q || p >= n || (tpq && otp[p])) continue;
+                f = fmin(f, first_frac(ox[0][p] - y[0], ox[1][p] - y[1], ox[2][p] - y[2], ox[3][p] - y[3],
+                                       ox[4][p] - y[4], ox[5][p] - y[5], fabs(a.dt)));
+            }
+        }
+        frac = warp_min_nonneg(f);
+    }
     for (int att = 0; att < BS_MAX_ATTEMPTS && done < 1.0; att++) {
         int late = 0;
         if (lane == 0) late = (global_timer_ns() - t0 > BS_TIME_LIMIT_NS) ? 1 : 0;
@@ -600,7 +647,21 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
             __syncwarp();
         };
         if (tab) pair_table();
-        double done = 0.0, frac = 1.0;
+        double done = 0.0, frac;
+        {  // first sub-step from the fastest interacting pair
+            double f = 1.0;
+            for (int idx = lane; idx < n * n; idx += 32) {
+                const int i = idx / n, j = idx % n;
+                if (j <= i) continue;
+                const int si = s0 + i, sj = s0 + j;
+                if (a.tpf[si] & a.tpf[sj] & 1) continue;  // two test particles
+                f = fmin(f, first_frac(W(F_Y, sj) - W(F_Y, si), W(F_Y + 1, sj) - W(F_Y + 1, si),
+                                       W(F_Y + 2, sj) - W(F_Y + 2, si), W(F_Y + 3, sj) - W(F_Y + 3, si),
+                                       W(F_Y + 4, sj) - W(F_Y + 4, si), W(F_Y + 5, sj) - W(F_Y + 5, si),
+                                       fabs(a.dt)));
+            }
+            frac = warp_min_nonneg(f);
+        }
         for (int att = 0; att < BS_MAX_ATTEMPTS && done < 1.0; att++) {
             int late = 0;
             if (lane == 0) late = (global_timer_ns() - t0 > BS_TIME_LIMIT_NS) ? 1 : 0;
