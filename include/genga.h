@@ -87,8 +87,10 @@ typedef struct {
     double bs_tol;           /* close-encounter level (level 1 of the hybrid integrator, Sect. 1):
                                 > 0: genga_drift / genga_step integrate every group of
                                 encounter pairs of the preceding kick with a Bulirsch-Stoer
-                                method at this relative tolerance (1e-12 is typical);
-                                0: off, every body gets the Kepler drift */
+                                method at this relative tolerance (1e-12 is typical, >= 1e-14:
+                                smaller tolerances sit at the rounding of FP64 heliocentric
+                                coordinates and cannot be met); 0: off, every body gets the
+                                Kepler drift */
     double r_in, r_out;      /* removal radii (Sect. 2): after every drift a body closer than
                                 r_in to, or farther than r_out from, the central body is removed
                                 (see "ghosts" below); <= 0 switches each test off */

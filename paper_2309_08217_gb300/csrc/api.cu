@@ -38,7 +38,10 @@ genga_status check_params(const genga_params *p) {
     if (p->precision != GENGA_FP64 && p->precision != GENGA_FP32) return GENGA_ERR_INVALID_ARG;
     if (p->kepler_max_iter < 1) return GENGA_ERR_INVALID_ARG;
     if (p->n_big < -1) return GENGA_ERR_INVALID_ARG;
-    if (!is_fin(p->bs_tol) || p->bs_tol < 0.0) return GENGA_ERR_INVALID_ARG;
+    // bs_tol: 0 (off) or >= 1e-14 -- below that the error estimate of a member's
+    // state is at the rounding of its FP64 heliocentric coordinates and the
+    // sub-steps shrink to the floor without converging
+    if (!is_fin(p->bs_tol) || p->bs_tol < 0.0 || (p->bs_tol > 0.0 && p->bs_tol < 1e-14)) return GENGA_ERR_INVALID_ARG;
     if (!is_fin(p->r_in) || !is_fin(p->r_out)) return GENGA_ERR_INVALID_ARG;
     return GENGA_OK;
 }

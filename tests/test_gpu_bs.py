@@ -223,6 +223,6 @@ def test_level1_off_is_the_level0_drift(genga, ctx):
 def test_invalid_tolerance_rejected(genga, ctx):
     d = planted_disc(10, 1)
     s = genga.DeviceSystem.from_disc(d)
-    for bad in (-1e-12, float("nan"), float("inf")):
+    for bad in (-1e-12, 1e-15, float("nan"), float("inf")):
         with pytest.raises(genga.GengaError):
             genga.genga_drift(ctx, s, _params(genga, d, 0, tol=bad), 1.0)
