@@ -35,8 +35,9 @@ constexpr int BS_GROW_COL = 2;         // a sub-step accepted by column <= 2 dou
 constexpr double BS_MIN_FRAC = 0x1p-30;  // smallest sub-step, as a fraction of the drift
 constexpr int BS_MAX_ATTEMPTS = 4096;  // sub-step attempts per group and drift
 constexpr int BS_WARPS = 4;            // groups in flight per CTA (one warp each)
-// Wall-clock bound of one group's integration; past it the rest of the drift
-// is taken as one forced sub-step (GENGA_ERR_BS).
+// Wall-clock bound of one launch of the level-1 kernel (counted per warp from
+// the launch); past it every group still integrating takes the rest of the
+// drift as one forced sub-step (GENGA_ERR_BS).
 constexpr unsigned long long BS_TIME_LIMIT_NS = 2000000000ull;
 
 __device__ __forceinline__ int ld_cg(const int32_t *p) { return __ldcg(p); }
@@ -823,6 +824,8 @@ __global__ void __launch_bounds__(32 * BS_WARPS) bs_kernel(const __grid_constant
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * BS_WARPS + (threadIdx.x >> 5), nw = gridDim.x * BS_WARPS;
     const int ng = *a.gcount;
+    uint64_t t0 = 0;  // the time limit holds for the whole launch, however many groups a warp takes
+    if (lane == 0) t0 = global_timer_ns();
     for (int g = gw; g < ng; g += nw) {
         const int s0 = a.gstart[g], n = a.gsize[g];
         // members in ascending body order (the order of every sum)
@@ -833,8 +836,6 @@ __global__ void __launch_bounds__(32 * BS_WARPS) bs_kernel(const __grid_constant
             a.gbody[s0 + rank] = v;
         }
         __syncwarp();
-        uint64_t t0 = 0;
-        if (lane == 0) t0 = global_timer_ns();
         bool forced = false;
         if (n <= 4) bs_small(a, s0, n, lane, t0, forced);
         else bs_general(a, s0, n, lane, t0, forced);

@@ -126,3 +126,31 @@ def test_invalid_radii_rejected(genga, ctx):
     for bad in (float("nan"), float("inf")):
         with pytest.raises(genga.GengaError):
             genga.genga_drift(ctx, s, _params(genga, d, r_out=bad), 1.0)
+
+
+@pytest.mark.parametrize("pattern", ["none", "all", "ends", "every_other"])
+def test_compaction_edge_cases(genga, ctx, pattern):
+    import torch
+    d = planted_disc(2500, 3)
+    s = genga.DeviceSystem.from_disc(d, radius=np.full(d.N, 1e-6))
+    ghost = np.zeros(d.N, bool)
+    if pattern == "all":
+        ghost[:] = True
+    elif pattern == "ends":
+        ghost[[0, 1, d.N - 1]] = True
+    elif pattern == "every_other":
+        ghost[::2] = True
+    m = s.tensors[6]
+    m[torch.as_tensor(np.nonzero(ghost)[0], device="cuda")] = -0.0
+    before = s.numpy()
+    ids = torch.arange(d.N, dtype=torch.int32, device="cuda")
+    n = genga.genga_compact(ctx, s, ids)
+    keep = np.nonzero(~ghost)[0]
+    assert n == len(keep) == s.N
+    assert np.array_equal(ids[:n].cpu().numpy(), keep)
+    after = s.numpy()
+    for c in range(7):
+        assert np.array_equal(after[c], before[c][keep])
+    if n:   # the compacted system steps on normally
+        genga.genga_step(ctx, s, _params(genga, d, 1), 1)
+        assert genga.genga_get_status(ctx) == genga.GENGA_OK
