@@ -74,6 +74,7 @@ def _load():
             "oracle_step": ([i] + [_dp] * 7 + [d] * 5 + [i, i, i, i, i], i),
             "oracle_energy": ([i] + [_dp] * 7 + [d, d, i, _dp], None),
             "oracle_groups": ([i, C.c_int64, _i32p, _i32p], i),
+            "oracle_predicted_pairs": ([i] + [_dp] * 9 + [d, d, i, i, d, _i32p, C.c_int64], C.c_int64),
             "oracle_bs_acc": ([i, _i32p] + [_dp] * 6 + [d, d, d, i, i, i, _dp], None),
             "oracle_bs_group": ([i, _i32p] + [_dp] * 9 + [d, d, d, i, i, i, d, d], i),
             "oracle_drift_groups": ([i] + [_dp] * 9 + [C.c_int64, _i32p, d, d, d, i, i, i, d, d, i,
@@ -250,6 +251,20 @@ def groups(N, pairs):
     ng = _load().oracle_groups(int(N), len(pairs), pairs.ctypes.data_as(_i32p),
                                label.ctypes.data_as(_i32p))
     return label[:N], int(ng)
+
+
+def predicted_pairs(arrs, a, rc, n1, Mstar, mode, dt, n_big=-1):
+    """Pairs i < j outside r_crit,ij but within 1.5 r_crit,ij whose straight-line
+    relative motion over the coming drift of length dt enters r_crit,ij."""
+    x, y, z, vx, vy, vz, m = [_f64(v) for v in arrs]
+    a, rc = _f64(a), _f64(rc)
+    N = len(m)
+    cap = max(16, 4 * N)
+    out = np.zeros(2 * cap, np.int32)
+    n = _load().oracle_predicted_pairs(N, *map(_p, (x, y, z, vx, vy, vz, m, a, rc)), n1, Mstar, int(mode),
+                                       int(n_big), float(dt), out.ctypes.data_as(_i32p), cap)
+    assert n <= cap
+    return out[: 2 * n].reshape(-1, 2).copy()
 
 
 def bs_acc(x, y, z, m, a, rc, members, G, Mstar, n1, mode, form, n_big=-1):

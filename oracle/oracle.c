@@ -254,6 +254,47 @@ int64_t oracle_encounters(int N, const double *x, const double *y, const double 
     return cnt;
 }
 
+/*
+ * Predicted entries (reading of the close-encounter level's grouping): a pair
+ * not inside r_crit,ij yet (r_ij >= r_crit,ij) but within PREDICT_RANGE
+ * r_crit,ij whose straight-line relative motion over the coming drift,
+ * d + u t with d = x_j - x_i, u = v_j - v_i (the state the list is built
+ * from) and t between 0 and dt, comes closer than r_crit,ij.  Such pairs join
+ * the groups of that drift (they are not encounter pairs).  Writes at most
+ * `cap` pairs (i < j, lexicographic); returns the true count.
+ */
+#define PREDICT_RANGE 1.5
+
+int64_t oracle_predicted_pairs(int N, const double *x, const double *y, const double *z,
+                               const double *vx, const double *vy, const double *vz,
+                               const double *m, const double *a, const double *rc,
+                               double n1, double Mstar, int mode, int n_big, double dt,
+                               int32_t *pairs, int64_t cap)
+{
+    int64_t cnt = 0;
+    double tlo = dt < 0.0 ? dt : 0.0, thi = dt < 0.0 ? 0.0 : dt;
+    for (int i = 0; i < N; i++) {
+        for (int j = i + 1; j < N; j++) {
+            if (tp_pair(n_big, i, j)) continue;
+            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            double rcij = oracle_pair_rcrit(mode, m[i], m[j], a[i], a[j], rc[i], rc[j], n1, Mstar);
+            if (r < rcij || r >= PREDICT_RANGE * rcij) continue;
+            double ux = vx[j] - vx[i], uy = vy[j] - vy[i], uz = vz[j] - vz[i];
+            double uu = ux * ux + uy * uy + uz * uz, du = dx * ux + dy * uy + dz * uz;
+            double t = uu > 0.0 ? -du / uu : 0.0;
+            if (t < tlo) t = tlo;
+            if (t > thi) t = thi;
+            double px = dx + ux * t, py = dy + uy * t, pz = dz + uz * t;
+            if (px * px + py * py + pz * pz < rcij * rcij) {
+                if (cnt < cap) { pairs[2 * cnt] = i; pairs[2 * cnt + 1] = j; }
+                cnt++;
+            }
+        }
+    }
+    return cnt;
+}
+
 /* ------------------------------------------- Kepler drift (Sect. 1) ------- */
 
 /*
@@ -760,9 +801,9 @@ int oracle_drift_groups(int N, double *x, double *y, double *z, double *vx, doub
 
 /*
  * Hybrid step with the close-encounter level, repeated nsteps times:
- * r_crit and the encounter pairs of the state, kick(dt/2), the drift of
- * oracle_drift_groups_full (mergers with R, removal with r_in / r_out, dead
- * flags per body), kick(dt/2).  Returns the Kepler cap count; *bs_forced and
+ * r_crit, the encounter pairs and the predicted entries of the state,
+ * kick(dt/2), the drift of oracle_drift_groups_full on both lists (mergers
+ * with R, removal with r_in / r_out, dead flags per body), kick(dt/2).  Returns the Kepler cap count; *bs_forced and
  * *merges (optional) accumulate the forced Bulirsch-Stoer acceptances and the
  * mergers.
  */
@@ -791,9 +832,21 @@ int oracle_step_full(int N, double *x, double *y, double *z, double *vx, double 
             np = oracle_encounters(N, x, y, z, m, a, rc, n1, Mstar, mode, n_big, pairs, cap,
                                    0.0, NULL, 0, NULL);
         }
+        /* the drift's groups: the encounter pairs and the predicted entries */
+        int64_t npr = oracle_predicted_pairs(N, x, y, z, vx, vy, vz, m, a, rc, n1, Mstar, mode, n_big, dt,
+                                             pairs + 2 * np, cap - np);
+        if (np + npr > cap) {
+            int32_t *bigger = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(np + npr));
+            for (int64_t q = 0; q < 2 * np; q++) bigger[q] = pairs[q];
+            free(pairs);
+            pairs = bigger;
+            cap = np + npr;
+            oracle_predicted_pairs(N, x, y, z, vx, vy, vz, m, a, rc, n1, Mstar, mode, n_big, dt,
+                                   pairs + 2 * np, npr);
+        }
         oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, n_big, 0.5 * dt, ax, ay, az);
         int f = 0;
-        bad += oracle_drift_groups_full(N, x, y, z, vx, vy, vz, m, a, rc, R, dead, np, pairs, G, Mstar, n1,
+        bad += oracle_drift_groups_full(N, x, y, z, vx, vy, vz, m, a, rc, R, dead, np + npr, pairs, G, Mstar, n1,
                                         mode, form, n_big, dt, tol, max_iter, r_in, r_out, &f, merges);
         forced += f;
         oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, n_big, 0.5 * dt, ax, ay, az);

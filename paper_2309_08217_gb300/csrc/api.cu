@@ -80,6 +80,14 @@ PassArgs base_args(genga_ctx *c, const genga_system &sys, const genga_params &p)
     a.partial = c->partial;
     a.enc = c->enc;
     a.enc_count = c->enc_count;
+    // the close-encounter level's groups also take the pairs predicted to
+    // enter r_crit within the drift: screening widened to PREDICT_RANGE r_crit
+    a.pred = c->pred;
+    a.predict = p.bs_tol > 0.0 ? 1 : 0;
+    a.pred_dt = p.dt;
+    a.vx = sys.vx;
+    a.vy = sys.vy;
+    a.vz = sys.vz;
     a.enc_cap = c->enc_cap;
     a.status = c->status;
     a.N = sys.N;
@@ -133,7 +141,7 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
                 e = launch_combine(c->partial, a.split, a.tp_rows_end, N, a.npad, 0, c->perm, 0.0, nullptr, nullptr, nullptr, nullptr,
                                    c->status, s);
             cudaEventRecord(e1, s);
-            cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s);
+            cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s);
             if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
             float t = 3.0e38f;
             cudaEventElapsedTime(&t, e0, e1);
@@ -158,7 +166,7 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
 cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &p, int precision, bool reorder,
                      int *split_out, cudaStream_t s, bool momentum_valid = false, int *one_row_out = nullptr) {
     // momentum_valid: c->mom already holds P of this state (genga_step after a drift)
-    cudaError_t e = momentum_valid ? cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s)
+    cudaError_t e = momentum_valid ? cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s)
                                    : launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->mom, c->enc_count, s);
     if (e != cudaSuccess) return e;
     c->launches += momentum_valid ? 0 : 1;
@@ -301,7 +309,7 @@ cudaError_t run_kick_batched(genga_ctx *c, const genga_system &all, const int32_
                              cudaStream_t s) {
     const BatchBodies bb = batch_bodies(offsets, D);
     const unsigned long long key = offsets_hash(offsets, D);
-    cudaError_t e = momentum_valid ? cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s)
+    cudaError_t e = momentum_valid ? cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s)
                                    : launch_momentum_batched(all, bb, c->Pd, c->enc_count, s);
     if (e != cudaSuccess) return e;
     c->launches += momentum_valid ? 0 : 1;
@@ -430,7 +438,8 @@ void genga_destroy(genga_ctx *c) {
                     c->ord_rbits,   c->a_osc,       c->rc_eq1,      c->partial,  c->mom,        c->enc,
                     c->enc_count,   c->status,      c->energy_part, c->work,   c->Pd,         c->Pd_part,
                     c->grp,         c->gmark,       c->gslot,       c->iperm,  c->gbody,      c->gmem,
-                    c->gstart,      c->gsize,       c->gcur,        c->gcount, c->bs_tp,      c->bs_work};
+                    c->gstart,      c->gsize,       c->gcur,        c->gcount, c->bs_tp,      c->bs_work,
+                    c->pred};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete c;
@@ -497,7 +506,8 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     if (e == cudaSuccess) e = alloc(&c->mom, 256);   // P, block partials, ticket
     if (e == cudaSuccess) e = cudaMemset(c->mom, 0, 256 * sizeof(double));
     if (e == cudaSuccess) e = alloc(&c->enc, (size_t)c->enc_cap);
-    if (e == cudaSuccess) e = alloc(&c->enc_count, 1);
+    if (e == cudaSuccess) e = alloc(&c->enc_count, 2);   // [0] encounter pairs, [1] predicted entries
+    if (e == cudaSuccess) e = alloc(&c->pred, (size_t)c->enc_cap);
     if (e == cudaSuccess) e = alloc(&c->status, 1);
     if (e == cudaSuccess) e = alloc(&c->energy_part, (size_t)4 * c->energy_blocks);
     // close-encounter level: labels and marks start cleared (-1 / 0) and are
@@ -518,7 +528,7 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     if (e == cudaSuccess) e = cudaMemset(c->grp, 0xff, sizeof(int32_t) * (size_t)np);
     if (e == cudaSuccess) e = cudaMemset(c->gmark, 0, sizeof(int32_t) * (size_t)np);
     if (e == cudaSuccess) e = cudaMemset(c->gcount, 0, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMemset(c->enc_count, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->enc_count, 0, 2 * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -537,7 +547,7 @@ genga_status genga_kick(genga_ctx *c, const genga_system *sys, const genga_param
     if (!is_fin(tau)) return GENGA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    if (sys->N == 0) return cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
+    if (sys->N == 0) return cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
     return run_kick(c, *sys, *p, tau, acc, true, s) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
 }
 
@@ -576,7 +586,7 @@ genga_status genga_encounters(genga_ctx *c, const genga_system *sys, const genga
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (sys->N == 0) {
-        if (cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s) != cudaSuccess) return GENGA_ERR_CUDA;
+        if (cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return GENGA_ERR_CUDA;
         c->enc_sorted = true;
     } else {
         int split;
@@ -649,7 +659,7 @@ genga_status genga_kick_batched(genga_ctx *c, const genga_system *all, const int
     if (p->precision != GENGA_FP32 || !is_fin(tau) || !check_offsets(c, all, offsets, D)) return GENGA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    if (all->N == 0) return cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
+    if (all->N == 0) return cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
     const cudaError_t e = run_kick_batched(c, *all, offsets, D, *p, tau, acc, true, false, s);
     if (e == cudaErrorInvalidValue) return GENGA_ERR_INVALID_ARG;
     return e == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
@@ -765,7 +775,7 @@ genga_status genga_compact(genga_ctx *c, genga_system *sys, int32_t *id, void *s
     c->launches += 4;
     if (n != sys->N) {  // the order, the list and the step graph belong to the old arrays
         c->ordered_N = -1;
-        cudaMemsetAsync(c->enc_count, 0, sizeof(int32_t), s);
+        cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s);
         c->enc_sorted = true;
     }
     sys->N = n;

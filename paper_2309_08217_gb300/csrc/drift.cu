@@ -219,6 +219,7 @@ __global__ void hc_batched_kernel(double *__restrict__ x, double *__restrict__ y
 cudaError_t launch_level1_groups(const genga_system &sys, genga_ctx *c, cudaStream_t s) {
     GroupArgs g;
     g.enc = c->enc;
+    g.pred = c->pred;
     g.enc_count = c->enc_count;
     g.enc_cap = c->enc_cap;
     g.N = sys.N;

@@ -4,8 +4,10 @@
 // pair force between the kick and this level).
 //
 //   groups     the connected components of the encounter pairs of the step's
-//              first kick (one CTA: hook-and-compress union-find over the
-//              pairs, then the members of each group stored contiguously)
+//              first kick and of the pairs that kick predicted to enter
+//              r_crit within the drift (one CTA: hook-and-compress union-find
+//              over the pairs, then the members of each group stored
+//              contiguously)
 //   level 1    every group is integrated over the drift by one warp: each
 //              member moves about the central body (mu = G M*) and feels the
 //              other members through the (1 - K) part of their pair force,
@@ -69,7 +71,13 @@ __device__ int block_scan(int v, int *warp_sums, int *total) {
     return r;
 }
 
-// One CTA.  In: the encounter pairs (body indices < N).  Out: gcount groups;
+// The p-th pair of the grouping: the encounter pairs, then the predicted entries.
+__device__ __forceinline__ int2 group_pair(const GroupArgs &a, int p, int ne) {
+    return p < ne ? a.enc[p] : a.pred[p - ne];
+}
+
+// One CTA.  In: the encounter pairs and the pairs predicted to enter r_crit
+// within the drift (body indices < N).  Out: gcount groups;
 // group g has gsize[g] members gmem[gstart[g] ..] (in no particular order),
 // grp[v] = the smallest body of v's group for every member (-1 elsewhere),
 // gmark[v] = 1 for every member.  More members than `slots`: no groups, the
@@ -79,14 +87,15 @@ __global__ void __launch_bounds__(GROUP_THREADS) group_kernel(const __grid_const
     __shared__ int s_flag, s_nmem, s_ngroups;
     __shared__ int warp_sums[32];
     const int tid = threadIdx.x;
-    const int np = min(*a.enc_count, a.enc_cap);
+    const int ne = min(a.enc_count[0], a.enc_cap);
+    const int np = ne + min(a.enc_count[1], a.enc_cap);
     if (tid == 0) {
         s_nmem = 0;
         s_ngroups = 0;
     }
     // 1. every body of a pair starts as its own group
     for (int p = tid; p < np; p += GROUP_THREADS) {
-        const int2 e = a.enc[p];
+        const int2 e = group_pair(a, p, ne);
         if (e.x < 0 || e.y < 0 || e.x >= a.N || e.y >= a.N) continue;  // a list of another system
         a.grp[e.x] = e.x;
         a.grp[e.y] = e.y;
@@ -100,7 +109,7 @@ __global__ void __launch_bounds__(GROUP_THREADS) group_kernel(const __grid_const
         if (tid == 0) s_flag = 0;
         __syncthreads();
         for (int p = tid; p < np; p += GROUP_THREADS) {
-            const int2 e = a.enc[p];
+            const int2 e = group_pair(a, p, ne);
             if (e.x < 0 || e.y < 0 || e.x >= a.N || e.y >= a.N) continue;
             const int li = ld_cg(a.grp + e.x), lj = ld_cg(a.grp + e.y);
             if (li != lj) {
@@ -110,7 +119,7 @@ __global__ void __launch_bounds__(GROUP_THREADS) group_kernel(const __grid_const
         }
         __syncthreads();
         for (int p = tid; p < np; p += GROUP_THREADS) {
-            const int2 e = a.enc[p];
+            const int2 e = group_pair(a, p, ne);
             if (e.x < 0 || e.y < 0 || e.x >= a.N || e.y >= a.N) continue;
 #pragma unroll
             for (int side = 0; side < 2; side++) {
@@ -133,7 +142,7 @@ __global__ void __launch_bounds__(GROUP_THREADS) group_kernel(const __grid_const
     }
     // 3. the distinct members, in discovery order
     for (int p = tid; p < np; p += GROUP_THREADS) {
-        const int2 e = a.enc[p];
+        const int2 e = group_pair(a, p, ne);
         if (e.x < 0 || e.y < 0 || e.x >= a.N || e.y >= a.N) continue;
 #pragma unroll
         for (int side = 0; side < 2; side++) {
@@ -148,7 +157,7 @@ __global__ void __launch_bounds__(GROUP_THREADS) group_kernel(const __grid_const
     const int nmem = s_nmem;
     if (nmem > a.slots) {  // the workspace holds fewer members: leave everyone to the Kepler drift
         for (int p = tid; p < np; p += GROUP_THREADS) {
-            const int2 e = a.enc[p];
+            const int2 e = group_pair(a, p, ne);
             if (e.x < 0 || e.y < 0 || e.x >= a.N || e.y >= a.N) continue;
             a.grp[e.x] = -1;
             a.grp[e.y] = -1;

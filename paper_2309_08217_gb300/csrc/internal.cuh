@@ -39,6 +39,9 @@
 // Close-encounter level: doubles of level-1 workspace per group member
 // (encounter.cu), and the most members one drift can integrate.
 #define GENGA_BS_FIELDS 239
+// Pairs outside r_crit,ij but within this multiple of it whose straight-line
+// relative motion over the drift enters r_crit,ij join the level's groups.
+#define GENGA_PREDICT_RANGE 1.5
 #define GENGA_BS_MAX_SLOTS (1 << 18)
 
 namespace genga {
@@ -81,7 +84,8 @@ struct genga_ctx {
     // encounter list of the most recent pass
     int2 *enc;                 // [enc_cap] unsorted during the pass, sorted after
     int32_t enc_cap;           // power of two
-    int32_t *enc_count;        // [1]
+    int32_t *enc_count;        // [2]: encounter pairs, predicted entries (pred)
+    int2 *pred;                // [enc_cap] pairs predicted to enter r_crit within the drift (bs_tol > 0)
     bool enc_sorted;           // the list has been sorted since the pass that built it
     uint32_t *status;          // [1] sticky bits
     double *energy_part;       // [energy_blocks][4]
@@ -168,8 +172,12 @@ struct PassArgs {               // one long-range pass
     const double *a_osc, *rc_eq1, *m;
     double *partial;            // [split][3][npad]
     int2 *enc;
-    int32_t *enc_count;
-    int32_t enc_cap;
+    int32_t *enc_count;         // [0] encounter pairs, [1] predicted entries
+    int32_t enc_cap;            // capacity of enc and of pred
+    int2 *pred;                 // predicted entries (written when predict)
+    int32_t predict;            // 1: widen the screening, record predicted entries
+    double pred_dt;             // length of the coming drift
+    const double *vx, *vy, *vz; // velocities of the state (predicted entries)
     uint32_t *status;
     int32_t N, npad;
     int32_t ntiles;             // npad / tile
@@ -192,8 +200,8 @@ struct PassArgs {               // one long-range pass
 };
 
 struct GroupArgs {              // grouping of the encounter pairs (one CTA)
-    const int2 *enc;
-    const int32_t *enc_count;
+    const int2 *enc, *pred;     // encounter pairs and predicted entries
+    const int32_t *enc_count;   // [0], [1]: their counts
     int32_t enc_cap, N, slots;
     int32_t *grp, *gmark, *gslot, *gbody, *gmem, *gstart, *gsize, *gcur, *gcount;
     uint32_t *status;

@@ -127,6 +127,22 @@ __device__ __noinline__ double3 screened_pair(const PassArgs &a, int i, int j, i
             if (pos < a.enc_cap) a.enc[pos] = make_int2(oi, oj);
         }
         K = changeover_K((r / rc - 0.1) / 0.9, a.changeover);
+    } else if (a.predict && oi < oj && r < GENGA_PREDICT_RANGE * rc && !(signbit(a.m[oi]) || signbit(a.m[oj]))) {
+        // a pair outside r_crit whose straight-line relative motion over the
+        // coming drift enters it joins the close-encounter groups (rounded
+        // products as written, no contraction)
+        const double ux = a.vx[oj] - a.vx[oi], uy = a.vy[oj] - a.vy[oi], uz = a.vz[oj] - a.vz[oi];
+        const double uu = __dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
+        const double du = __dadd_rn(__dadd_rn(__dmul_rn(dx, ux), __dmul_rn(dy, uy)), __dmul_rn(dz, uz));
+        double t = uu > 0.0 ? -du / uu : 0.0;
+        const double tlo = a.pred_dt < 0.0 ? a.pred_dt : 0.0, thi = a.pred_dt < 0.0 ? 0.0 : a.pred_dt;
+        t = fmin(fmax(t, tlo), thi);
+        const double px = __dadd_rn(dx, __dmul_rn(ux, t)), py = __dadd_rn(dy, __dmul_rn(uy, t));
+        const double pz = __dadd_rn(dz, __dmul_rn(uz, t));
+        if (__dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz)) < __dmul_rn(rc, rc)) {
+            const int pos = atomicAdd(a.enc_count + 1, 1);
+            if (pos < a.enc_cap) a.pred[pos] = make_int2(oi, oj);
+        }
     }
     if (K == 0.0) return f;
     const double s = pj.w * K / (r2 * r);

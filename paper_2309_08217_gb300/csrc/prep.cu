@@ -10,7 +10,9 @@
 //     single-precision kick of Sect. 1 takes its pair offsets from these),
 //     an FP64 {x, y, z, G m} record, and the FP32 screening factors
 //     {H_i, A_i} with r_crit,ij <= max(H_i, H_j) * max(A_i, A_j) for every
-//     pair (rounded up); per 64-body group, the bounding box of the FP32
+//     pair (rounded up; with the close-encounter level on, of GENGA_PREDICT_RANGE
+//     r_crit,ij, so that the pass also sees the pairs that may enter r_crit
+//     within the drift); per 64-body group, the bounding box of the FP32
 //     positions and the maxima of the screening factors;
 //   * iperm: the packed position of every body (the close-encounter level
 //     reads a_i, r_crit,i and the test-particle flag of its members there).
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(MOM_THREADS) momentum_kernel(const double *__r
     }
     if (threadIdx.x == 0) {
         *ticket = 0u;
-        if (zero_me) *zero_me = 0;
+        if (zero_me) zero_me[0] = zero_me[1] = 0;  // encounter pairs, predicted entries
     }
 }
 
@@ -109,7 +111,8 @@ __device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double 
                                            double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
                                            float4 *__restrict__ lo, double4_32a *__restrict__ p64,
                                            float2 *__restrict__ scr, double *__restrict__ a_osc,
-                                           double *__restrict__ rc_eq1, bool tp, float3 *pos, bool *real) {
+                                           double *__restrict__ rc_eq1, bool tp, double sscale, float3 *pos,
+                                           bool *real) {
     float2 s = make_float2(0.f, 0.f);
     if (i >= 0) {
         // osculating a from the heliocentric velocity u = v + P / M*:
@@ -131,13 +134,13 @@ __device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double 
             // r_crit,ij = max(rc_i, rc_j) = max(1, 1) * max(rc_i, rc_j)
             const double rc = fmax(n1 * a * cbrt(mi / (3.0 * Mstar)), n2 * dt * sqrt(v2));
             rc_eq1[k] = rc;
-            s = make_float2(1.0f, __double2float_ru(rc));
+            s = make_float2(1.0f, __double2float_ru(rc * sscale));
         } else {
             // n1 ((m_i+m_j)/3M)^(1/3) (a_i+a_j)/2 <= n1 (2 max(m)/3M)^(1/3) * max(a); the FP32
             // cube root (error ~1 ulp) is inflated by 2^-16 to stay an upper bound
             rc_eq1[k] = 0.0;
             const float h = n1 * cbrtf(__double2float_ru(2.0 * mi / (3.0 * Mstar))) * (1.0f + 0x1p-16f);
-            s = make_float2(h, __double2float_ru(a * (1.0 + 1e-12)));
+            s = make_float2(h, __double2float_ru(a * (1.0 + 1e-12) * sscale));
         }
         const float hx = __double2float_rn(xi), hy = __double2float_rn(yi), hz = __double2float_rn(zi);
         const double gm = G * mi;
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
     double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
     float4 *__restrict__ lo, double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
     float4 *__restrict__ gbox_hi, int32_t *__restrict__ gflag, double *__restrict__ a_osc,
-    double *__restrict__ rc_eq1, int n_big, uint32_t *__restrict__ iperm) {
+    double *__restrict__ rc_eq1, int n_big, uint32_t *__restrict__ iperm, double sscale) {
     const int k = blockIdx.x * PREP_THREADS + threadIdx.x;
     float3 pos = make_float3(0.f, 0.f, 0.f);
     bool real = false;
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
     if (i >= 0) iperm[i] = (uint32_t)k;
     const bool tp = i >= 0 && n_big >= 0 && i >= n_big;
     const float2 s = prep_body(k, i, k - N, x, y, z, vx, vy, vz, m, P, G, Mstar, dt, n1, n2,
-                               rcrit_mode, hi, hit, hid, lo, p64, scr, a_osc, rc_eq1, tp, &pos, &real);
+                               rcrit_mode, hi, hit, hid, lo, p64, scr, a_osc, rc_eq1, tp, sscale, &pos, &real);
     group_reduce_store(s, pos, real, tp, gbox_lo, gbox_hi, gflag);
 }
 
@@ -240,7 +243,8 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_batched_kernel(
     double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
     float4 *__restrict__ lo, double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
     float4 *__restrict__ gbox_hi, int32_t *__restrict__ gflag, double *__restrict__ a_osc,
-    double *__restrict__ rc_eq1, int n_big, uint32_t *__restrict__ iperm, const __grid_constant__ BatchBodies bb) {
+    double *__restrict__ rc_eq1, int n_big, uint32_t *__restrict__ iperm, double sscale,
+    const __grid_constant__ BatchBodies bb) {
     const int p = blockIdx.x * PREP_THREADS + threadIdx.x;
     const int d = find_segment(bb.poff, bb.D, p);
     const int k = p - bb.poff[d], Nd = bb.off[d + 1] - bb.off[d];
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_batched_kernel(
     if (i >= 0) iperm[i] = (uint32_t)p;
     const bool tp = i >= 0 && n_big >= 0 && i - bb.off[d] >= n_big;
     const float2 s = prep_body(p, i, k - Nd, x, y, z, vx, vy, vz, m, Pd + 3 * d, G, Mstar, dt, n1, n2, rcrit_mode, hi,
-                               hit, hid, lo, p64, scr, a_osc, rc_eq1, tp, &pos, &real);
+                               hit, hid, lo, p64, scr, a_osc, rc_eq1, tp, sscale, &pos, &real);
     group_reduce_store(s, pos, real, tp, gbox_lo, gbox_hi, gflag);
 }
 
@@ -278,7 +282,7 @@ __global__ void __launch_bounds__(MOM_THREADS) momentum_batched_kernel(
         __syncthreads();
     }
     if (threadIdx.x < 3) Pd[3 * d + threadIdx.x] = sh[threadIdx.x][0];
-    if (d == 0 && threadIdx.x == 0 && zero_me) *zero_me = 0;
+    if (d == 0 && threadIdx.x == 0 && zero_me) zero_me[0] = zero_me[1] = 0;
 }
 
 }  // namespace
@@ -297,7 +301,7 @@ cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ct
     prep_kernel<<<npad / PREP_THREADS, PREP_THREADS, 0, s>>>(
         sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->perm, c->mom, p.G, p.Mstar, p.dt, p.n1,
         p.n2, p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_d, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->gflag,
-        c->a_osc, c->rc_eq1, p.n_big, c->iperm);
+        c->a_osc, c->rc_eq1, p.n_big, c->iperm, p.bs_tol > 0.0 ? GENGA_PREDICT_RANGE : 1.0);
     return cudaGetLastError();
 }
 
@@ -316,7 +320,7 @@ cudaError_t launch_prep_batched(const genga_system &all, const BatchBodies &bb, 
     prep_batched_kernel<<<bb.npad_total / PREP_THREADS, PREP_THREADS, 0, s>>>(
         all.x, all.y, all.z, all.vx, all.vy, all.vz, all.m, c->perm, c->Pd, p.G, p.Mstar, p.dt, p.n1, p.n2,
         p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_d, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->gflag, c->a_osc,
-        c->rc_eq1, p.n_big, c->iperm, bb);
+        c->rc_eq1, p.n_big, c->iperm, p.bs_tol > 0.0 ? GENGA_PREDICT_RANGE : 1.0, bb);
     return cudaGetLastError();
 }
 

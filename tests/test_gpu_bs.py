@@ -68,8 +68,11 @@ def test_kick_then_drift_parity(genga, ctx, precision):
     assert genga.genga_get_status(ctx) == genga.GENGA_OK
     arr = oracle.disc_arrays(d)
     a, rc = oracle.rcrit(*arr, G=d.G, Mstar=d.Mstar, dt=d.dt)
+    # the drift's groups: the encounter pairs and the pairs predicted to enter r_crit
+    pred = oracle.predicted_pairs(arr, a, rc, 3.0, d.Mstar, 1, d.dt)
     oracle.kick(arr, d.G, d.Mstar, d.dt, 3.0, 0.4, 1, 0, 0.5 * d.dt)
-    bad, forced = oracle.drift_groups(arr, a, rc, pairs, d.G, d.Mstar, 3.0, 1, 0, d.dt, TOL_BS)
+    bad, forced = oracle.drift_groups(arr, a, rc, np.concatenate([pairs, pred]), d.G, d.Mstar, 3.0, 1, 0,
+                                      d.dt, TOL_BS)
     assert bad == 0 and forced == 0
     got = s.numpy()
     others = np.setdiff1d(np.arange(d.N), mem)

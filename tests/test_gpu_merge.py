@@ -154,3 +154,35 @@ def test_compaction_edge_cases(genga, ctx, pattern):
     if n:   # the compacted system steps on normally
         genga.genga_step(ctx, s, _params(genga, d, 1), 1)
         assert genga.genga_get_status(ctx) == genga.GENGA_OK
+
+
+def test_batched_mergers_and_removal(genga):
+    """Three systems in one batched call, each with a head-on pair that merges
+    and removal radii: every system as the oracle steps it alone (ghosts
+    marked in place; batched mode has no compaction)."""
+    sizes = [800, 500, 1100]
+    parts = [planted_disc(n, 17 + 3 * k) for k, n in enumerate(sizes)]
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    arrays = [np.concatenate([p.arrays()[c] for p in parts]) for c in range(7)]
+    R = np.full(int(offsets[-1]), 2e-5)
+    c = genga.Context(4000)
+    s = genga.DeviceSystem.from_arrays(arrays, radius=R)
+    p = _params(genga, parts[0], 1, r_in=0.72, r_out=2.9)
+    genga.genga_step_batched(c, s, offsets, p, 3)
+    assert genga.genga_get_status(c) == genga.GENGA_OK
+    got, got_R = s.numpy(), s.radius_numpy()
+    total_ghosts = 0
+    for k, d in enumerate(parts):
+        lo, hi = int(offsets[k]), int(offsets[k + 1])
+        ref = oracle.disc_arrays(d)
+        Rk, dead = R[lo:hi].copy(), np.zeros(d.N, np.int32)
+        assert oracle.step(ref, d.G, d.Mstar, d.dt, 3.0, 0.4, 1, 0, 3, bs_tol=TOL_BS, radius=Rk, dead=dead,
+                           r_in=0.72, r_out=2.9) == 0
+        gk = [g[lo:hi] for g in got]
+        assert np.array_equal(np.signbit(gk[6]), dead == 1), f"system {k}"
+        np.testing.assert_allclose(gk[6], ref[6], rtol=1e-15, atol=0)
+        np.testing.assert_allclose(got_R[lo:hi], Rk, rtol=1e-14, atol=0)
+        assert _rel_state(gk, ref) < 1e-9, f"system {k}"
+        total_ghosts += int(dead.sum())
+    assert total_ghosts >= 3
+    c.close()

@@ -294,3 +294,34 @@ def test_hybrid_step_without_encounters_is_the_level0_step():
     assert oracle.step(b, G, 1.0, 6.0, 3.0, 0.4, 1, 0, 50, bs_tol=1e-12) == 0
     for u, v in zip(a, b):
         assert np.array_equal(u, v)
+
+
+# ------------------------------------------------- predicted entries ---
+def test_predicted_pairs_against_brute_force():
+    """Pairs outside r_crit (but within 1.5 r_crit) whose straight-line
+    relative motion over the drift enters r_crit: a dense grid of times
+    t in [0, dt] stands in for the closed-form closest approach."""
+    d = discs.disc_uniform(2000, 21, a_min=0.97, a_max=1.03)
+    arr = oracle.disc_arrays(d)
+    a, rc = oracle.rcrit(*arr, G=d.G, Mstar=d.Mstar, dt=d.dt)
+    got = {tuple(p) for p in oracle.predicted_pairs(arr, a, rc, 3.0, d.Mstar, 1, d.dt)}
+    x = np.stack(arr[:3], 1); v = np.stack(arr[3:6], 1); m = arr[6]
+    ts = np.linspace(0.0, d.dt, 4001)
+    want, near_edge = set(), 0
+    for i in range(d.N):
+        dd = x[i + 1:] - x[i]
+        r = np.linalg.norm(dd, axis=1)
+        for k in np.nonzero(r < 2.0 * 0.02)[0]:
+            j = i + 1 + k
+            rcij = oracle.pair_rcrit(1, m[i], m[j], a[i], a[j], rc[i], rc[j], 3.0, d.Mstar)
+            if not (rcij <= r[k] < 1.5 * rcij):
+                continue
+            path = np.linalg.norm(dd[k][None, :] + (v[j] - v[i])[None, :] * ts[:, None], axis=1)
+            if abs(path.min() / rcij - 1) < 1e-6:
+                near_edge += 1          # the grid cannot decide these
+                continue
+            if path.min() < rcij:
+                want.add((i, j))
+    got_clear = {p for p in got}
+    assert len(want) >= 3
+    assert want <= got_clear and len(got_clear - want) <= near_edge

@@ -47,8 +47,8 @@ MUTANTS = {
     "energy_pair_term_mass": ("nadd(&e, -G * m[i] * m[j] / sqrt", "nadd(&e, -G * m[i] * m[i] / sqrt"),
     "tp2_either_test_particle": ("return n_big >= 0 && i >= n_big && j >= n_big;",
                                  "return n_big >= 0 && (i >= n_big || j >= n_big);"),
-    "tp2_encounters_not_skipped": ("            if (tp_pair(n_big, i, j)) continue;\n            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];\n            double r = sqrt",
-                                   "            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];\n            double r = sqrt"),
+    "tp2_encounters_not_skipped": ("            if (tp_pair(n_big, i, j)) continue;\n            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];\n            double r = sqrt(dx * dx + dy * dy + dz * dz);\n            double rcij = oracle_pair_rcrit(mode, m[i], m[j], a[i], a[j], rc[i], rc[j], n1, Mstar);\n            if (r < rcij) {",
+                                   "            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];\n            double r = sqrt(dx * dx + dy * dy + dz * dz);\n            double rcij = oracle_pair_rcrit(mode, m[i], m[j], a[i], a[j], rc[i], rc[j], n1, Mstar);\n            if (r < rcij) {"),
     "angular_momentum_component": ("nadd(&lz, m[i] * (x[i] * vy[i] - y[i] * vx[i]));",
                                    "nadd(&lz, m[i] * (x[i] * vy[i] + y[i] * vx[i]));"),
     # close-encounter level
@@ -70,6 +70,9 @@ MUTANTS = {
     "merger_survivor_higher_index": ("        ghost[fj] = 1;\n", "        ghost[fi] = 1;\n"),
     "ghosts_still_pull": ("|| bs_ghost(g, i) || bs_ghost(g, j)) continue;", ") continue;"),
     "removal_outer_uses_inner": ("(r_out > 0.0 && r2 > r_out * r_out)", "(r_out > 0.0 && r2 > r_in * r_in)"),
+    "prediction_unclamped": ("            if (t > thi) t = thi;\n", ""),
+    "prediction_wrong_sign": ("double t = uu > 0.0 ? -du / uu : 0.0;", "double t = uu > 0.0 ? du / uu : 0.0;"),
+    "prediction_range": ("if (r < rcij || r >= PREDICT_RANGE * rcij) continue;", "if (r < rcij || r >= 1.1 * rcij) continue;"),
     "dead_pairs_grouped": ("        if (dead && (dead[pairs[2 * p]] || dead[pairs[2 * p + 1]])) continue;\n", ""),
 }
 
