@@ -610,8 +610,9 @@ static int bs_merge(const bs_group *g, double *yv, double *m, double *R, int32_t
  * interacting pair moves by more than its separation (f |dt| |v_ij| <= r_ij).
  * A sub-step with no accepted column is halved; one accepted at a column
  * <= BS_GROW_COL doubles the next.  Sub-steps are fractions of dt; a sub-step
- * at BS_MIN_FRAC, or the last of BS_MAX_ATTEMPTS attempts (which covers the
- * rest of dt), is accepted at the last column anyway.  With radii R (per
+ * at BS_MIN_FRAC is accepted at the last column anyway, and after
+ * BS_MAX_ATTEMPTS attempts the members drift the rest of dt on their Kepler
+ * orbits (both count as forced).  With radii R (per
  * body, NULL: no collisions) overlapping members merge after every accepted
  * sub-step (bs_merge); the absorbed bodies get dead[b] = 1 (per body, needed
  * with R), m = R = 0.  Updates the members' entries of x..vz, m, R; returns 1
@@ -652,8 +653,6 @@ int oracle_bs_group_full(int n, const int32_t *mem, double *x, double *y, double
         }
     }
     for (int att = 0; att < BS_MAX_ATTEMPTS && done < 1.0; att++) {
-        int last = (att == BS_MAX_ATTEMPTS - 1);
-        if (last) frac = 1.0 - done;
         double h = frac * dt;
         for (int k = 0; k < n; k++) {        /* error scales of this sub-step */
             const double *s = yv + 6 * k;
@@ -685,7 +684,7 @@ int oracle_bs_group_full(int n, const int32_t *mem, double *x, double *y, double
             }
             if (err <= tol) { acc_col = k; break; }
         }
-        if (acc_col < 0 && (frac <= BS_MIN_FRAC || last)) {
+        if (acc_col < 0 && frac <= BS_MIN_FRAC) {
             acc_col = BS_KMAX - 1;              /* forced: keep the last column */
             forced = 1;
         }
@@ -696,6 +695,10 @@ int oracle_bs_group_full(int n, const int32_t *mem, double *x, double *y, double
         done += frac;
         if (acc_col <= BS_GROW_COL) frac *= 2.0;
         if (frac > 1.0 - done) frac = 1.0 - done;
+    }
+    if (done < 1.0) {   /* out of attempts: the rest of the drift on Kepler orbits (level 0) */
+        forced = 1;
+        for (int k = 0; k < n; k++) oracle_kepler(G * Mstar, yv + 6 * k, (1.0 - done) * dt, 50);
     }
     for (int k = 0; k < n; k++) {
         int b = mem[k];

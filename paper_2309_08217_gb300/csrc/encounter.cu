@@ -23,7 +23,7 @@
 // body momentum drift only, and this level moves them over dt in between
 // the two momentum drifts.  Everything here is FP64 (Sect. 1, last paragraph:
 // close-encounter forces are always double precision).
-#include "internal.cuh"
+#include "kepler.cuh"
 
 namespace genga {
 
@@ -38,8 +38,8 @@ constexpr double BS_MIN_FRAC = 0x1p-30;  // smallest sub-step, as a fraction of 
 constexpr int BS_MAX_ATTEMPTS = 4096;  // sub-step attempts per group and drift
 constexpr int BS_WARPS = 4;            // groups in flight per CTA (one warp each)
 // Wall-clock bound of one launch of the level-1 kernel (counted per warp from
-// the launch); past it every group still integrating takes the rest of the
-// drift as one forced sub-step (GENGA_ERR_BS).
+// the launch); past it every group still integrating drifts the rest of the
+// step on Kepler orbits (GENGA_ERR_BS).
 constexpr unsigned long long BS_TIME_LIMIT_NS = 2000000000ull;
 
 __device__ __forceinline__ int ld_cg(const int32_t *p) { return __ldcg(p); }
@@ -330,9 +330,9 @@ __device__ __forceinline__ double warp_max(double v) {
 // over all members is accepted -- the same values and the same choice as
 // building the columns one after another.  No accepted column: the sub-step
 // is halved; accepted by column <= BS_GROW_COL: the next one is doubled.  At
-// BS_MIN_FRAC, at the last of BS_MAX_ATTEMPTS attempts (which takes the rest
-// of dt) or past BS_TIME_LIMIT_NS the last column is accepted anyway and
-// GENGA_ERR_BS is raised.
+// BS_MIN_FRAC the last column is accepted anyway; after BS_MAX_ATTEMPTS
+// attempts or past BS_TIME_LIMIT_NS the members drift the rest of dt on
+// Kepler orbits; both raise GENGA_ERR_BS.
 __device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
 // Largest binary fraction f of |dt| with (f |dt|)^2 v2 <= r2 (a pair crosses at
@@ -473,8 +473,7 @@ __device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, 
         int late = 0;
         if (lane == 0) late = (global_timer_ns() - t0 > BS_TIME_LIMIT_NS) ? 1 : 0;
         late = __shfl_sync(0xffffffffu, late, 0);
-        const bool last = (att == BS_MAX_ATTEMPTS - 1) || late;
-        if (last) frac = 1.0 - done;
+        if (late) break;  // the rest of the drift on Kepler orbits, below
         const double h = frac * a.dt;
         const double H = h / nk;
         const double px2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2], pv2 = y[3] * y[3] + y[4] * y[4] + y[5] * y[5];
@@ -541,7 +540,7 @@ __device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, 
             const double e = warp_max_nonneg(ek[kk]);
             if (acc_col < 0 && e <= a.tol) acc_col = kk;
         }
-        if (acc_col < 0 && (frac <= BS_MIN_FRAC || last)) {
+        if (acc_col < 0 && frac <= BS_MIN_FRAC) {
             acc_col = BS_KMAX - 1;
             forced = true;
         }
@@ -611,6 +610,10 @@ __device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, 
         if (acc_col <= BS_GROW_COL) frac *= 2.0;
         if (frac > 1.0 - done) frac = 1.0 - done;
     }
+    if (done < 1.0) {  // out of attempts or time: the rest of the drift on Kepler orbits (level 0)
+        forced = true;
+        kepler_drift(a.G * a.Mstar, (1.0 - done) * a.dt, 50, y[0], y[1], y[2], y[3], y[4], y[5]);
+    }
     if (act && k == 0) {
         a.x[v] = y[0]; a.y[v] = y[1]; a.z[v] = y[2];
         a.vx[v] = y[3]; a.vy[v] = y[4]; a.vz[v] = y[5];
@@ -676,8 +679,7 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
             int late = 0;
             if (lane == 0) late = (global_timer_ns() - t0 > BS_TIME_LIMIT_NS) ? 1 : 0;
             late = __shfl_sync(0xffffffffu, late, 0);
-            const bool last = (att == BS_MAX_ATTEMPTS - 1) || late;
-            if (last) frac = 1.0 - done;
+            if (late) break;  // the rest of the drift on Kepler orbits, below
             const double h = frac * a.dt;
             for (int q = lane; q < n; q += 32) {  // error scales and f(y)
                 const int s = s0 + q;
@@ -757,7 +759,7 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
                 if (acc_col < 0 && e <= a.tol) acc_col = k;
             }
             __syncwarp();
-            if (acc_col < 0 && (frac <= BS_MIN_FRAC || last)) {
+            if (acc_col < 0 && frac <= BS_MIN_FRAC) {
                 acc_col = BS_KMAX - 1;
                 forced = true;
             }
@@ -807,6 +809,18 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
             done += frac;
             if (acc_col <= BS_GROW_COL) frac *= 2.0;
             if (frac > 1.0 - done) frac = 1.0 - done;
+        }
+        if (done < 1.0) {  // out of attempts or time: the rest of the drift on Kepler orbits (level 0)
+            forced = true;
+            for (int q = lane; q < n; q += 32) {
+                const int s = s0 + q;
+                double px = W(F_Y, s), py = W(F_Y + 1, s), pz = W(F_Y + 2, s);
+                double u = W(F_Y + 3, s), vv = W(F_Y + 4, s), w = W(F_Y + 5, s);
+                kepler_drift(a.G * a.Mstar, (1.0 - done) * a.dt, 50, px, py, pz, u, vv, w);
+                W(F_Y, s) = px; W(F_Y + 1, s) = py; W(F_Y + 2, s) = pz;
+                W(F_Y + 3, s) = u; W(F_Y + 4, s) = vv; W(F_Y + 5, s) = w;
+            }
+            __syncwarp();
         }
         for (int q = lane; q < n; q += 32) {
             const int s = s0 + q, v = a.gbody[s];
