@@ -229,3 +229,21 @@ def test_invalid_tolerance_rejected(genga, ctx):
     for bad in (-1e-12, 1e-15, float("nan"), float("inf")):
         with pytest.raises(genga.GengaError):
             genga.genga_drift(ctx, s, _params(genga, d, 0, tol=bad), 1.0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_step_parity_eq1_radius_quintic_weight(genga, ctx, precision):
+    """The level with the per-body Eq. (1) radius (velocity term included)
+    and the quintic changeover, at dt = 1 d."""
+    d = orbiting_pairs_disc(600, 29)
+    dt = 1.0
+    s = genga.DeviceSystem.from_disc(d)
+    p = genga.make_params(G=d.G, Mstar=d.Mstar, dt=dt, n1=3.0, n2=0.4, rcrit_mode=genga.GENGA_RCRIT_EQ1,
+                          changeover=genga.GENGA_K_QUINTIC, precision=precision, bs_tol=TOL_BS)
+    genga.genga_step(ctx, s, p, 3)
+    assert genga.genga_get_status(ctx) == genga.GENGA_OK
+    arr = oracle.disc_arrays(d)
+    forced = [0]
+    assert oracle.step(arr, d.G, d.Mstar, dt, 3.0, 0.4, 0, 1, 3, bs_tol=TOL_BS, forced=forced) == 0
+    assert forced[0] == 0
+    assert _rel_state(s.numpy(), arr) < (1e-10 if precision == 0 else 1e-9)
