@@ -149,7 +149,9 @@ genga_status genga_kick(genga_ctx *ctx, const genga_system *sys, const genga_par
  * With params->bs_tol > 0 the close-encounter level replaces the Kepler drift
  * for the members of every group: the connected components of the encounter
  * pairs of the most recent kick on this context (genga_kick, genga_step,
- * genga_encounters).  Each group is integrated over dt in FP64 by a
+ * genga_encounters) and of the pairs that kick (when it ran with bs_tol > 0)
+ * predicted to come inside r_crit within dt: outside r_crit,ij but within
+ * 1.5 r_crit,ij, entering it along their straight-line relative motion.  Each group is integrated over dt in FP64 by a
  * Bulirsch-Stoer method (modified midpoint rule with 2, 4, ..., 16 steps,
  * polynomial extrapolation, relative tolerance bs_tol on each member's |x|
  * and |v|) under the central body and the (1 - K) part of the members' pair
@@ -186,7 +188,9 @@ genga_status genga_last_encounters(genga_ctx *ctx, int32_t *pairs, int32_t capac
  * level (see genga_drift); with bs_tol = 0 every body gets the Kepler drift
  * and pairs inside r_crit keep only their K-weighted force (exact for
  * systems without encounters).  The encounter list of the last kick stays
- * readable through genga_last_encounters.  The spatial order of the bodies
+ * readable through genga_last_encounters (the closing kick of a step lists
+ * the encounter pairs only; each step's first kick also predicts the entries
+ * its drift integrates, see genga_drift).  The spatial order of the bodies
  * (a performance device of the FP32 pass) is rebuilt every few steps,
  * counted across calls on the context.
  */

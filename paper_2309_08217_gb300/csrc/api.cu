@@ -605,6 +605,8 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
     if (sys->N == 0 || nsteps == 0) return GENGA_OK;
     genga_system s2 = *sys;
     const double h = 0.5 * p->dt;
+    genga_params p_close = *p;  // the closing kick of a step: no predicted entries
+    p_close.bs_tol = 0.0;
     // The spatial order is a performance device (every pass classifies tiles
     // from the current positions; any order gives the same sum up to
     // rounding), so genga_step rebuilds it every GENGA_REORDER_STEPS drifts,
@@ -616,7 +618,9 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
         c->launches += p->bs_tol > 0.0 ? 6 : 4;
         c->steps_since_order++;
         const bool reorder = c->steps_since_order >= GENGA_REORDER_STEPS;
-        if (e == cudaSuccess) e = run_kick(c, s2, *p, h, nullptr, reorder, q, true);
+        // the closing kick needs no predicted entries (the next step's first
+        // kick lists them again), so it screens at r_crit only
+        if (e == cudaSuccess) e = run_kick(c, s2, p_close, h, nullptr, reorder, q, true);
         return e;
     };
     int k = 0;
@@ -678,13 +682,15 @@ genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *
     const BatchBodies bb = batch_bodies(offsets, D);
     const unsigned long long layout = offsets_hash(offsets, D);
     const double h = 0.5 * p->dt;
+    genga_params p_close = *p;  // the closing kick of a step: no predicted entries
+    p_close.bs_tol = 0.0;
     auto one_step = [&](cudaStream_t q) -> cudaError_t {
         cudaError_t e = run_kick_batched(c, a2, offsets, D, *p, h, nullptr, false, false, q);
         if (e == cudaSuccess) e = launch_drift_batched(a2, bb, *p, p->dt, c, q);
         c->launches += p->bs_tol > 0.0 ? 6 : 4;
         c->steps_since_order++;
         const bool reorder = c->steps_since_order >= GENGA_REORDER_STEPS;
-        if (e == cudaSuccess) e = run_kick_batched(c, a2, offsets, D, *p, h, nullptr, reorder, true, q);
+        if (e == cudaSuccess) e = run_kick_batched(c, a2, offsets, D, p_close, h, nullptr, reorder, true, q);
         return e;
     };
     auto status_of = [](cudaError_t e) {
