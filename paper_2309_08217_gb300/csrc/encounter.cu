@@ -18,6 +18,9 @@
 //              Gragg's modified midpoint rule with 2, 4, ..., 16 steps and
 //              Aitken-Neville extrapolation in H^2 (Stoer & Bulirsch), step
 //              halving and doubling as described at bs_kernel.
+//   mergers    with physical radii, overlapping members merge after every
+//              accepted sub-step (Sect. 2: collisions are perfect mergers);
+//              the absorbed body becomes a ghost of mass -0.0
 //
 // The drift kernel skips the members (grp[i] >= 0): they get the central-
 // body momentum drift only, and this level moves them over dt in between
