@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-disc batched workload")
     ap.add_argument("--batched-steps", type=int, default=5)
     ap.add_argument("--no-tp2", action="store_true", help="skip the test-particle-mode-2 kicks on giants100k")
+    ap.add_argument("--long-steps", type=int, default=1000,
+                    help="length of the run whose mean step and pass times are reported (0: skip)")
     ap.add_argument("--bs-tol", type=float, default=1e-12,
                     help="tolerance of the close-encounter (Bulirsch-Stoer) level, timed beside the headline "
                          "step (which is the level-0 path: kick, drift, kick); 0: skip that measurement")
@@ -396,6 +398,32 @@ def run_genga(args):
     tuner_ms = g.genga_tuning_times(ctx, N)
     ms64, pass64, nl64, _, _ = timed_steps(p64, max(1, args.fp64_steps), 3)
 
+    # ---- the 1,000-step run of the workload: mean step and pass times over the
+    # whole run (the state evolves: the spatial order and the NEAR share drift)
+    long_run = None
+    if args.long_steps > 0:
+        sl = g.DeviceSystem.from_disc(d, device=dev)
+        g.genga_profile_enable(ctx, True)
+        el0, el1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        el0.record(stream)
+        g.genga_step(ctx, sl, p32, args.long_steps)
+        el1.record(stream)
+        barrier()
+        lp_ms, lp_n = g.genga_profile_read(ctx)
+        g.genga_profile_enable(ctx, False)
+        if g.genga_get_status(ctx) != g.GENGA_OK:
+            raise RuntimeError("device status after the long run")
+        ms_long = max_over_ranks(el0.elapsed_time(el1), dist, dev)
+        lp_avg = lp_ms / max(1, lp_n)
+        long_run = {"steps": args.long_steps, "ms_per_step": ms_long / args.long_steps,
+                    "value": weak_value(ws, pairs_step, args.long_steps, ms_long), "unit": UNIT,
+                    "pass_ms_avg": lp_avg, "passes": lp_n,
+                    "frac": FLOPS_PER_PAIR * N * (N - 1) / (lp_avg * 1e-3) / 1e12 / (
+                        torch.cuda.get_device_properties(dev).multi_processor_count * 128 * 2 * 2070e6 / 1e12),
+                    "how": "genga_step(ctx, sys, params, steps) from t = 0, one call, step by step (pass events on), "
+                           "no L2 flush inside"}
+
     # ---- compaction of ghosts (mergers / removal): genga_compact on the
     # 40,000-body state with every 100th body a ghost (mass -0.0), with an id array
     compaction = None
@@ -556,6 +584,7 @@ def run_genga(args):
                  "fp32_over_fp64": value / value64},
         "roofline": roof,
         "graph_blocks": graph,
+        "long_run": long_run,
         "level1": level1,
         "compaction": compaction,
         "batched": batched,
