@@ -84,6 +84,12 @@ def _load():
                                                                         C.POINTER(C.c_int), C.POINTER(C.c_int)], i),
             "oracle_bs_group_full": ([i, _i32p] + [_dp] * 10 + [_i32p, d, d, d, i, i, i, d, d,
                                                                   C.POINTER(C.c_int)], i),
+            "oracle_ml_radius": ([d, i, i], d),
+            "oracle_ml_weight": ([d, d, i, i, i, i], d),
+            "oracle_ml_group": ([i, _i32p] + [_dp] * 10 + [_i32p, d, d, d, i, i, i, d, d, i, i, i,
+                                                             C.POINTER(C.c_int), C.POINTER(C.c_int)], i),
+            "oracle_step_ml": ([i] + [_dp] * 8 + [_i32p] + [d] * 5 + [i, i, i, i, d, d, d, i, i, i,
+                                                                      C.POINTER(C.c_int), C.POINTER(C.c_int)], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -204,7 +210,7 @@ def drift(arrs, G, Mstar, dt, max_iter=50):
 
 
 def step(arrs, G, Mstar, dt, n1, n2, mode, form, nsteps, max_iter=50, n_big=-1, bs_tol=0.0,
-         forced=None, radius=None, dead=None, r_in=0.0, r_out=0.0, merges=None):
+         forced=None, radius=None, dead=None, r_in=0.0, r_out=0.0, merges=None, n_levels=0, n_sub=2):
     """nsteps of kick(dt/2) drift(dt) kick(dt/2), in place.  bs_tol > 0: the
     drift integrates the encounter groups of each step's first kick with the
     Bulirsch-Stoer level at that tolerance (forced: optional one-element list
@@ -212,18 +218,21 @@ def step(arrs, G, Mstar, dt, n1, n2, mode, form, nsteps, max_iter=50, n_big=-1, 
     updated) turns on perfect mergers inside that level, r_in / r_out (> 0)
     the removal radii; dead (per body, int32, updated) marks the bodies merged
     away or removed (they stay as massless ghosts); merges: optional
-    one-element list that accumulates the mergers.  Returns the Kepler cap
-    count."""
+    one-element list that accumulates the mergers.  n_levels >= 1: that many
+    intermediate levels of n_sub sub-steps between the kick and the
+    Bulirsch-Stoer level.  Returns the Kepler cap count."""
     x, y, z, vx, vy, vz, m = arrs
-    if radius is not None or dead is not None or r_in > 0.0 or r_out > 0.0:
-        assert bs_tol > 0.0 and dead is not None and dead.dtype == np.int32
+    if radius is not None or dead is not None or r_in > 0.0 or r_out > 0.0 or n_levels > 0:
+        assert bs_tol > 0.0
+        if radius is not None or r_in > 0.0 or r_out > 0.0:
+            assert dead is not None and dead.dtype == np.int32
         f, mg = C.c_int(0), C.c_int(0)
         rp = _p(radius) if radius is not None else None
-        bad = int(_load().oracle_step_full(len(m), *map(_p, (x, y, z, vx, vy, vz, m)), rp,
-                                           dead.ctypes.data_as(_i32p), G, Mstar, dt, n1, n2, int(mode),
-                                           int(form), int(n_big), int(max_iter), float(bs_tol),
-                                           float(r_in), float(r_out), int(nsteps), C.byref(f),
-                                           C.byref(mg)))
+        dp = dead.ctypes.data_as(_i32p) if dead is not None else None
+        bad = int(_load().oracle_step_ml(len(m), *map(_p, (x, y, z, vx, vy, vz, m)), rp, dp, G, Mstar, dt, n1, n2,
+                                         int(mode), int(form), int(n_big), int(max_iter), float(bs_tol),
+                                         float(r_in), float(r_out), int(n_levels), int(n_sub), int(nsteps),
+                                         C.byref(f), C.byref(mg)))
         if forced is not None:
             forced[0] += f.value
         if merges is not None:
@@ -300,6 +309,37 @@ def bs_group(arrs, members, a, rc, G, Mstar, n1, mode, form, dt, tol, n_big=-1, 
     return int(_load().oracle_bs_group(len(mem), mem.ctypes.data_as(_i32p),
                                        *map(_p, (x, y, z, vx, vy, vz, m, a, rc)), G, Mstar, n1,
                                        int(mode), int(form), int(n_big), float(dt), float(tol)))
+
+
+def ml_radius(rc, level, n_sub):
+    """r_crit of level l: rc / n_sub^l."""
+    return float(_load().oracle_ml_radius(float(rc), int(level), int(n_sub)))
+
+
+def ml_weight(q, rc, level, n_levels, n_sub, form):
+    """Share of the pair force at separation q (pair radius rc) that level
+    `level` applies: K_l prod_{k<l}(1 - K_k) for level <= n_levels, the
+    Bulirsch-Stoer share prod_{k<=n_levels}(1 - K_k) for level = n_levels + 1."""
+    return float(_load().oracle_ml_weight(float(q), float(rc), int(level), int(n_levels), int(n_sub), int(form)))
+
+
+def ml_group(arrs, members, a, rc, G, Mstar, n1, mode, form, dt, tol, n_levels, n_sub, n_big=-1,
+             radius=None, dead=None, merges=None, max_iter=50):
+    """One group (ascending body indices) over dt on level 1 with n_levels
+    intermediate levels of n_sub symplectic sub-steps and the Bulirsch-Stoer
+    level below them, in place; returns (forced, Kepler cap count)."""
+    x, y, z, vx, vy, vz, m = arrs
+    mem = np.ascontiguousarray(np.asarray(members, dtype=np.int32))
+    a, rc = _f64(a), _f64(rc)
+    mg, bad = C.c_int(0), C.c_int(0)
+    rp = _p(radius) if radius is not None else None
+    dp = dead.ctypes.data_as(_i32p) if dead is not None else None
+    f = int(_load().oracle_ml_group(len(mem), mem.ctypes.data_as(_i32p), *map(_p, (x, y, z, vx, vy, vz, m, a, rc)),
+                                    rp, dp, G, Mstar, n1, int(mode), int(form), int(n_big), float(dt), float(tol),
+                                    int(n_levels), int(n_sub), int(max_iter), C.byref(mg), C.byref(bad)))
+    if merges is not None:
+        merges[0] += mg.value
+    return f, bad.value
 
 
 def drift_groups(arrs, a, rc, pairs, G, Mstar, n1, mode, form, dt, tol, n_big=-1, max_iter=50):

@@ -20,6 +20,9 @@
  *                         connected groups of encounter pairs are integrated
  *                         over the drift with a Bulirsch-Stoer method under the
  *                         central body and the (1 - K) part of their mutual forces
+ *   intermediate levels   Sect. 1 (the multi-level changeover): symplectic
+ *                         sub-steps between the kick and the Bulirsch-Stoer
+ *                         level, each level with its own changeover radius
  *   mergers, removal      Sect. 2: collisions are perfect mergers; bodies closer
  *                         than r_in to or farther than r_out from the central
  *                         body are removed (both leave a massless "ghost")
@@ -456,6 +459,35 @@ int oracle_groups(int N, int64_t npairs, const int32_t *pairs, int32_t *label)
 }
 
 /*
+ * Levels of the changeover (Sect. 1: intermediate levels between the
+ * symplectic step and the Bulirsch-Stoer integrator, each a symplectic step
+ * with a smaller time step).  Readings: with L intermediate levels and s
+ * sub-steps per level, level l (0 <= l <= L) has the time step dt / s^l and
+ * the pair radius r_crit,l = r_crit,ij / s^l (the velocity term of Eq. 1
+ * shrinks with the step); K_l(r) = K((r / r_crit,l - 0.1) / 0.9).  The pair
+ * force is split into
+ *   level l <= L:           W_l = K_l prod_{k<l} (1 - K_k)
+ *   Bulirsch-Stoer (L + 1): W_{L+1} = prod_{k<=L} (1 - K_k),
+ * which add up to 1 (the products telescope); W_0 = K_0 is the kick's
+ * weight.  s^l is an exact integer, so r_crit,l is one rounded quotient.
+ */
+double oracle_ml_radius(double rc, int l, int s)
+{
+    double p = 1.0;
+    for (int k = 0; k < l; k++) p *= s;
+    return rc / p;
+}
+
+double oracle_ml_weight(double q, double rc, int l, int L, int s, int form)
+{
+    double w = 1.0;
+    for (int k = 0; k < l && k <= L; k++)
+        w *= 1.0 - oracle_changeover((q / oracle_ml_radius(rc, k, s) - 0.1) / 0.9, form);
+    if (l <= L) w *= oracle_changeover((q / oracle_ml_radius(rc, l, s) - 0.1) / 0.9, form);
+    return w;
+}
+
+/*
  * One group of n bodies (body indices mem[0] < mem[1] < ...).  What the
  * Bulirsch-Stoer level integrates over the drift (the level-1 Hamiltonian
  * of the hybrid step): every member moves about the central body
@@ -472,6 +504,7 @@ typedef struct {
     double G, Mstar, n1;
     int mode, form, n_big;
     const int32_t *ghost;   /* per member: merged away (no force either way); NULL: none */
+    int nlev, nsub;         /* intermediate levels L and sub-steps s (0, 1: none) */
 } bs_group;
 
 static int bs_ghost(const bs_group *g, int k) { return g->ghost && g->ghost[k]; }
@@ -496,8 +529,8 @@ static void bs_deriv(const bs_group *g, const double *s, double *ds)
             double q = sqrt(q2);
             double rcij = oracle_pair_rcrit(g->mode, g->m[bi], g->m[bj], g->a[bi], g->a[bj],
                                             g->rc[bi], g->rc[bj], g->n1, g->Mstar);
-            if (q >= rcij) continue;                  /* K = 1: all of it is in the kick */
-            double w = 1.0 - oracle_changeover((q / rcij - 0.1) / 0.9, g->form);
+            if (q >= oracle_ml_radius(rcij, g->nlev, g->nsub)) continue;   /* the kicks have all of it */
+            double w = oracle_ml_weight(q, rcij, g->nlev + 1, g->nlev, g->nsub, g->form);
             double f = g->G * g->m[bj] * w / (q2 * q);
             ax += f * dx;
             ay += f * dy;
@@ -515,7 +548,7 @@ void oracle_bs_acc(int n, const int32_t *mem, const double *x, const double *y, 
                    const double *m, const double *a, const double *rc, double G, double Mstar,
                    double n1, int mode, int form, int n_big, double *acc)
 {
-    bs_group g = {n, mem, m, a, rc, G, Mstar, n1, mode, form, n_big, NULL};
+    bs_group g = {n, mem, m, a, rc, G, Mstar, n1, mode, form, n_big, NULL, 0, 1};
     double *s = (double *)calloc((size_t)(6 * n > 0 ? 6 * n : 1), sizeof(double));
     double *ds = (double *)calloc((size_t)(6 * n > 0 ? 6 * n : 1), sizeof(double));
     for (int k = 0; k < n; k++) {
@@ -619,14 +652,14 @@ static int bs_merge(const bs_group *g, double *yv, double *m, double *R, int32_t
  * if an acceptance was forced, else 0; *merges (optional) accumulates the
  * mergers.
  */
-int oracle_bs_group_full(int n, const int32_t *mem, double *x, double *y, double *z,
-                         double *vx, double *vy, double *vz, double *m, const double *a,
-                         const double *rc, double *R, int32_t *dead, double G, double Mstar,
-                         double n1, int mode, int form, int n_big, double dt, double tol,
-                         int *merges)
+static int bs_group_run(int n, const int32_t *mem, double *x, double *y, double *z,
+                        double *vx, double *vy, double *vz, double *m, const double *a,
+                        const double *rc, double *R, int32_t *dead, double G, double Mstar,
+                        double n1, int mode, int form, int n_big, double dt, double tol,
+                        int *merges, int nlev, int nsub)
 {
     int32_t *ghost = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
-    bs_group g = {n, mem, m, a, rc, G, Mstar, n1, mode, form, n_big, ghost};
+    bs_group g = {n, mem, m, a, rc, G, Mstar, n1, mode, form, n_big, ghost, nlev, nsub};
     int L = 6 * n;
     double *buf = (double *)malloc(sizeof(double) * (size_t)L * (7 + BS_KMAX * BS_KMAX));
     double *yv = buf, *f0 = yv + L, *zp = f0 + L, *zc = zp + L, *zn = zc + L, *fz = zn + L,
@@ -712,6 +745,16 @@ int oracle_bs_group_full(int n, const int32_t *mem, double *x, double *y, double
     return forced;
 }
 
+int oracle_bs_group_full(int n, const int32_t *mem, double *x, double *y, double *z,
+                         double *vx, double *vy, double *vz, double *m, const double *a,
+                         const double *rc, double *R, int32_t *dead, double G, double Mstar,
+                         double n1, int mode, int form, int n_big, double dt, double tol,
+                         int *merges)
+{
+    return bs_group_run(n, mem, x, y, z, vx, vy, vz, m, a, rc, R, dead, G, Mstar, n1, mode, form, n_big,
+                        dt, tol, merges, 0, 1);
+}
+
 /* oracle_bs_group_full without collisions. */
 int oracle_bs_group(int n, const int32_t *mem, double *x, double *y, double *z,
                     double *vx, double *vy, double *vz, const double *m, const double *a,
@@ -723,22 +766,169 @@ int oracle_bs_group(int n, const int32_t *mem, double *x, double *y, double *z,
 }
 
 /*
+ * The intermediate levels (Sect. 1).  ml_level(l, group, T) moves a group of
+ * level l (1 <= l <= L) over T in s sub-steps of h = T / s, each
+ *   kick(h/2):  v_i += h/2 sum_{j in group} G m_j W_l(r_ij) (x_j - x_i) / r_ij^3
+ *   drift(h):   subgroups = connected components of the member pairs with
+ *               r_ij < r_crit,l, and of the pairs with r_crit,l <= r_ij <
+ *               1.5 r_crit,l whose straight-line relative motion over h
+ *               enters r_crit,l (the level's predicted entries, as in the
+ *               step's first kick); members outside every subgroup take the
+ *               Kepler drift over h, each subgroup (in order of its smallest
+ *               body) moves on level l + 1 over h -- the Bulirsch-Stoer
+ *               integrator with W_{L+1} once l = L
+ *   kick(h/2)
+ * Members are in ascending body order, every sum in that order.  Ghosts
+ * (m = -0.0, from mergers in a Bulirsch-Stoer subgroup) feel and exert no
+ * level force, join no subgroup and keep the Kepler drift.  Comparisons of
+ * squares, as written, without contraction.
+ */
+typedef struct {
+    double *x, *y, *z, *vx, *vy, *vz, *m, *R;
+    const double *a, *rc;
+    int32_t *dead;
+    double G, Mstar, n1, tol;
+    int mode, form, n_big, L, s, max_iter;
+    int forced, merges, bad;
+} ml_ctx;
+
+static double ml_pair_rc(const ml_ctx *c, int bi, int bj)
+{
+    return oracle_pair_rcrit(c->mode, c->m[bi], c->m[bj], c->a[bi], c->a[bj], c->rc[bi], c->rc[bj], c->n1,
+                             c->Mstar);
+}
+
+static void ml_kick(ml_ctx *c, int l, int n, const int32_t *mem, double tau)
+{
+    double *acc = (double *)calloc((size_t)(3 * n > 0 ? 3 * n : 1), sizeof(double));
+    for (int i = 0; i < n; i++) {
+        int bi = mem[i];
+        if (signbit(c->m[bi])) continue;
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        for (int j = 0; j < n; j++) {
+            int bj = mem[j];
+            if (j == i || signbit(c->m[bj]) || tp_pair(c->n_big, bi, bj)) continue;
+            double dx = c->x[bj] - c->x[bi], dy = c->y[bj] - c->y[bi], dz = c->z[bj] - c->z[bi];
+            double q2 = dx * dx + dy * dy + dz * dz;
+            if (q2 == 0.0) continue;
+            double q = sqrt(q2), rcij = ml_pair_rc(c, bi, bj);
+            if (q >= rcij) continue;                  /* W_l = 0 outside r_crit,0 */
+            double f = c->G * c->m[bj] * oracle_ml_weight(q, rcij, l, c->L, c->s, c->form) / (q2 * q);
+            ax += f * dx;
+            ay += f * dy;
+            az += f * dz;
+        }
+        acc[3 * i] = ax; acc[3 * i + 1] = ay; acc[3 * i + 2] = az;
+    }
+    for (int i = 0; i < n; i++) {
+        int bi = mem[i];
+        c->vx[bi] += tau * acc[3 * i];
+        c->vy[bi] += tau * acc[3 * i + 1];
+        c->vz[bi] += tau * acc[3 * i + 2];
+    }
+    free(acc);
+}
+
+/* Is (bi, bj) a pair of the subgroups of level l + 1 for a drift of h? */
+static int ml_subpair(const ml_ctx *c, int l, int bi, int bj, double h)
+{
+    if (signbit(c->m[bi]) || signbit(c->m[bj]) || tp_pair(c->n_big, bi, bj)) return 0;
+    double dx = c->x[bj] - c->x[bi], dy = c->y[bj] - c->y[bi], dz = c->z[bj] - c->z[bi];
+    double q2 = dx * dx + dy * dy + dz * dz;
+    double rcl = oracle_ml_radius(ml_pair_rc(c, bi, bj), l, c->s);
+    double rcl2 = rcl * rcl, rout = 1.5 * rcl;
+    if (q2 < rcl2) return 1;
+    if (q2 >= rout * rout) return 0;
+    double ux = c->vx[bj] - c->vx[bi], uy = c->vy[bj] - c->vy[bi], uz = c->vz[bj] - c->vz[bi];
+    double uu = ux * ux + uy * uy + uz * uz, du = dx * ux + dy * uy + dz * uz;
+    double tlo = h < 0.0 ? h : 0.0, thi = h < 0.0 ? 0.0 : h;
+    double t = uu > 0.0 ? -du / uu : 0.0;
+    if (t < tlo) t = tlo;
+    if (t > thi) t = thi;
+    double px = dx + ux * t, py = dy + uy * t, pz = dz + uz * t;
+    return px * px + py * py + pz * pz < rcl2;
+}
+
+static void ml_level(ml_ctx *c, int l, int n, const int32_t *mem, double T)
+{
+    double h = T / c->s;
+    int32_t *root = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *inpair = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *sub = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int step = 0; step < c->s; step++) {
+        ml_kick(c, l, n, mem, 0.5 * h);
+        for (int i = 0; i < n; i++) { root[i] = i; inpair[i] = 0; }
+        for (int i = 0; i < n; i++)
+            for (int j = i + 1; j < n; j++) {
+                if (!ml_subpair(c, l, mem[i], mem[j], h)) continue;
+                inpair[i] = inpair[j] = 1;
+                int ri = uf_root(root, i), rj = uf_root(root, j);
+                if (ri < rj) root[rj] = ri;
+                else if (rj < ri) root[ri] = rj;
+            }
+        for (int i = 0; i < n; i++) {
+            if (inpair[i]) continue;
+            int b = mem[i];
+            double st[6] = {c->x[b], c->y[b], c->z[b], c->vx[b], c->vy[b], c->vz[b]};
+            c->bad += oracle_kepler(c->G * c->Mstar, st, h, c->max_iter);
+            c->x[b] = st[0]; c->y[b] = st[1]; c->z[b] = st[2];
+            c->vx[b] = st[3]; c->vy[b] = st[4]; c->vz[b] = st[5];
+        }
+        for (int r = 0; r < n; r++) {
+            if (!inpair[r] || uf_root(root, r) != r) continue;
+            int cnt = 0;
+            for (int k = r; k < n; k++)
+                if (inpair[k] && uf_root(root, k) == r) sub[cnt++] = mem[k];
+            if (l < c->L)
+                ml_level(c, l + 1, cnt, sub, h);
+            else
+                c->forced += bs_group_run(cnt, sub, c->x, c->y, c->z, c->vx, c->vy, c->vz, c->m, c->a, c->rc, c->R,
+                                          c->dead, c->G, c->Mstar, c->n1, c->mode, c->form, c->n_big, h, c->tol,
+                                          &c->merges, c->L, c->s);
+        }
+        ml_kick(c, l, n, mem, 0.5 * h);
+    }
+    free(root);
+    free(inpair);
+    free(sub);
+}
+
+/* One group of the step's drift on level 1 with L >= 1 intermediate levels and
+ * s sub-steps per level (members in ascending order).  Returns 1 if a
+ * Bulirsch-Stoer acceptance was forced; *merges, *bad (optional) accumulate
+ * the mergers and the Kepler solves that hit the cap. */
+int oracle_ml_group(int n, const int32_t *mem, double *x, double *y, double *z,
+                    double *vx, double *vy, double *vz, double *m, const double *a,
+                    const double *rc, double *R, int32_t *dead, double G, double Mstar,
+                    double n1, int mode, int form, int n_big, double dt, double tol,
+                    int nlev, int nsub, int max_iter, int *merges, int *bad)
+{
+    ml_ctx c = {x, y, z, vx, vy, vz, m, R, a, rc, dead, G, Mstar, n1, tol, mode, form, n_big, nlev, nsub,
+                max_iter, 0, 0, 0};
+    ml_level(&c, 1, n, mem, dt);
+    if (merges) *merges += c.merges;
+    if (bad) *bad += c.bad;
+    return c.forced > 0 ? 1 : 0;
+}
+
+/*
  * Drift of the hybrid step with the close-encounter level: HC(dt/2); every
  * body outside the groups of `pairs` (the encounter pairs of the step's
  * first kick; pairs with a dead body do not count) on its Kepler orbit, every
  * group by oracle_bs_group_full (a, rc from that kick; mergers when R is
- * given); HC(dt/2); then removal: a body still alive with |x|^2 < r_in^2 or
+ * given), or with nlev >= 1 intermediate levels of nsub sub-steps by
+ * oracle_ml_group; HC(dt/2); then removal: a body still alive with |x|^2 < r_in^2 or
  * |x|^2 > r_out^2 (each test off when its radius is <= 0) becomes dead with
  * m = 0 (and R = 0).  dead (per body) is needed with R or the radii.
  * Returns the number of Kepler solves that hit the cap; *bs_forced and
  * *merges (optional) get the groups with a forced Bulirsch-Stoer acceptance
  * and the mergers.
  */
-int oracle_drift_groups_full(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
-                             double *m, const double *a, const double *rc, double *R, int32_t *dead,
-                             int64_t npairs, const int32_t *pairs, double G, double Mstar, double n1,
-                             int mode, int form, int n_big, double dt, double tol, int max_iter,
-                             double r_in, double r_out, int *bs_forced, int *merges)
+int oracle_drift_groups_ml(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                           double *m, const double *a, const double *rc, double *R, int32_t *dead,
+                           int64_t npairs, const int32_t *pairs, double G, double Mstar, double n1,
+                           int mode, int form, int n_big, double dt, double tol, int max_iter,
+                           double r_in, double r_out, int nlev, int nsub, int *bs_forced, int *merges)
 {
     int bad = 0, forced = 0, nmerge = 0;
     size_t n = (size_t)(N > 0 ? N : 1);
@@ -767,8 +957,12 @@ int oracle_drift_groups_full(int N, double *x, double *y, double *z, double *vx,
         int cnt = 0;
         for (int v = r; v < N; v++)
             if (label[v] == r) mem[cnt++] = v;
-        forced += oracle_bs_group_full(cnt, mem, x, y, z, vx, vy, vz, m, a, rc, R, dead, G, Mstar, n1,
-                                       mode, form, n_big, dt, tol, &nmerge);
+        if (nlev > 0)
+            forced += oracle_ml_group(cnt, mem, x, y, z, vx, vy, vz, m, a, rc, R, dead, G, Mstar, n1, mode, form,
+                                      n_big, dt, tol, nlev, nsub, max_iter, &nmerge, &bad);
+        else
+            forced += oracle_bs_group_full(cnt, mem, x, y, z, vx, vy, vz, m, a, rc, R, dead, G, Mstar, n1,
+                                           mode, form, n_big, dt, tol, &nmerge);
     }
     oracle_hc_drift(N, x, y, z, vx, vy, vz, m, Mstar, 0.5 * dt);
     if (dead && (r_in > 0.0 || r_out > 0.0)) {
@@ -790,6 +984,17 @@ int oracle_drift_groups_full(int N, double *x, double *y, double *z, double *vx,
     return bad;
 }
 
+/* oracle_drift_groups_ml without intermediate levels. */
+int oracle_drift_groups_full(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                             double *m, const double *a, const double *rc, double *R, int32_t *dead,
+                             int64_t npairs, const int32_t *pairs, double G, double Mstar, double n1,
+                             int mode, int form, int n_big, double dt, double tol, int max_iter,
+                             double r_in, double r_out, int *bs_forced, int *merges)
+{
+    return oracle_drift_groups_ml(N, x, y, z, vx, vy, vz, m, a, rc, R, dead, npairs, pairs, G, Mstar, n1, mode,
+                                  form, n_big, dt, tol, max_iter, r_in, r_out, 0, 1, bs_forced, merges);
+}
+
 /* oracle_drift_groups_full without collisions or removal. */
 int oracle_drift_groups(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
                         const double *m, const double *a, const double *rc,
@@ -805,15 +1010,16 @@ int oracle_drift_groups(int N, double *x, double *y, double *z, double *vx, doub
 /*
  * Hybrid step with the close-encounter level, repeated nsteps times:
  * r_crit, the encounter pairs and the predicted entries of the state,
- * kick(dt/2), the drift of oracle_drift_groups_full on both lists (mergers
+ * kick(dt/2), the drift of oracle_drift_groups_ml on both lists (nlev
+ * intermediate levels of nsub sub-steps; mergers
  * with R, removal with r_in / r_out, dead flags per body), kick(dt/2).  Returns the Kepler cap count; *bs_forced and
  * *merges (optional) accumulate the forced Bulirsch-Stoer acceptances and the
  * mergers.
  */
-int oracle_step_full(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
-                     double *m, double *R, int32_t *dead, double G, double Mstar, double dt, double n1,
-                     double n2, int mode, int form, int n_big, int max_iter, double tol, double r_in,
-                     double r_out, int nsteps, int *bs_forced, int *merges)
+int oracle_step_ml(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                   double *m, double *R, int32_t *dead, double G, double Mstar, double dt, double n1,
+                   double n2, int mode, int form, int n_big, int max_iter, double tol, double r_in,
+                   double r_out, int nlev, int nsub, int nsteps, int *bs_forced, int *merges)
 {
     int bad = 0, forced = 0;
     size_t n = (size_t)(N > 0 ? N : 1);
@@ -849,14 +1055,24 @@ int oracle_step_full(int N, double *x, double *y, double *z, double *vx, double 
         }
         oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, n_big, 0.5 * dt, ax, ay, az);
         int f = 0;
-        bad += oracle_drift_groups_full(N, x, y, z, vx, vy, vz, m, a, rc, R, dead, np + npr, pairs, G, Mstar, n1,
-                                        mode, form, n_big, dt, tol, max_iter, r_in, r_out, &f, merges);
+        bad += oracle_drift_groups_ml(N, x, y, z, vx, vy, vz, m, a, rc, R, dead, np + npr, pairs, G, Mstar, n1,
+                                      mode, form, n_big, dt, tol, max_iter, r_in, r_out, nlev, nsub, &f, merges);
         forced += f;
         oracle_kick(N, x, y, z, vx, vy, vz, m, G, Mstar, dt, n1, n2, mode, form, n_big, 0.5 * dt, ax, ay, az);
     }
     if (bs_forced) *bs_forced += forced;
     free(ax); free(ay); free(az); free(a); free(rc); free(pairs);
     return bad;
+}
+
+/* oracle_step_ml without intermediate levels. */
+int oracle_step_full(int N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                     double *m, double *R, int32_t *dead, double G, double Mstar, double dt, double n1,
+                     double n2, int mode, int form, int n_big, int max_iter, double tol, double r_in,
+                     double r_out, int nsteps, int *bs_forced, int *merges)
+{
+    return oracle_step_ml(N, x, y, z, vx, vy, vz, m, R, dead, G, Mstar, dt, n1, n2, mode, form, n_big, max_iter,
+                          tol, r_in, r_out, 0, 1, nsteps, bs_forced, merges);
 }
 
 /* oracle_step_full without collisions or removal. */

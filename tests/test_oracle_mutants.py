@@ -54,7 +54,7 @@ MUTANTS = {
     # close-encounter level
     "groups_count_every_member": ("if (label[v] == v) ngroups++;", "ngroups++;"),
     "level1_central_sign": ("double c = -g->G * g->Mstar / (r2 * r);", "double c = g->G * g->Mstar / (r2 * r);"),
-    "level1_weight_is_K": ("double w = 1.0 - oracle_changeover(", "double w = oracle_changeover("),
+    "level1_weight_is_K": ("w *= 1.0 - oracle_changeover(", "w *= oracle_changeover("),
     "level1_offset_sign": ("double dx = xj[0] - xi[0], dy", "double dx = xi[0] - xj[0], dy"),
     "level1_mass_index": ("double f = g->G * g->m[bj] * w", "double f = g->G * g->m[bi] * w"),
     "level1_tp_pairs_kept": ("if (j == i || tp_pair(g->n_big, bi, bj) || bs_ghost", "if (j == i || bs_ghost"),
@@ -71,8 +71,24 @@ MUTANTS = {
     "ghosts_still_pull": ("|| bs_ghost(g, i) || bs_ghost(g, j)) continue;", ") continue;"),
     "removal_outer_uses_inner": ("(r_out > 0.0 && r2 > r_out * r_out)", "(r_out > 0.0 && r2 > r_in * r_in)"),
     "prediction_unclamped": ("            if (t > thi) t = thi;\n", ""),
-    "prediction_wrong_sign": ("double t = uu > 0.0 ? -du / uu : 0.0;", "double t = uu > 0.0 ? du / uu : 0.0;"),
+    "prediction_wrong_sign": ("            double t = uu > 0.0 ? -du / uu : 0.0;",
+                              "            double t = uu > 0.0 ? du / uu : 0.0;"),
     "prediction_range": ("if (r < rcij || r >= PREDICT_RANGE * rcij) continue;", "if (r < rcij || r >= 1.1 * rcij) continue;"),
+    # intermediate levels
+    "levels_weight_drops_level0_keep": ("for (int k = 0; k < l && k <= L; k++)", "for (int k = 1; k < l && k <= L; k++)"),
+    "levels_radius_power": ("for (int k = 0; k < l; k++) p *= s;", "for (int k = 1; k < l; k++) p *= s;"),
+    "levels_last_factor_is_keep": ("if (l <= L) w *= oracle_changeover(", "if (l <= L) w *= 1.0 - oracle_changeover("),
+    "levels_full_first_kick": ("        ml_kick(c, l, n, mem, 0.5 * h);\n        for (int i = 0; i < n; i++) { root[i]",
+                               "        ml_kick(c, l, n, mem, h);\n        for (int i = 0; i < n; i++) { root[i]"),
+    "levels_substep_not_divided": ("double h = T / c->s;", "double h = T;"),
+    "levels_bs_weight_level": ("double w = oracle_ml_weight(q, rcij, g->nlev + 1,", "double w = oracle_ml_weight(q, rcij, g->nlev,"),
+    "levels_subgroup_radius": ("double rcl = oracle_ml_radius(ml_pair_rc(c, bi, bj), l, c->s);",
+                               "double rcl = oracle_ml_radius(ml_pair_rc(c, bi, bj), l + 1, c->s);"),
+    "levels_kick_weight_level": ("oracle_ml_weight(q, rcij, l, c->L, c->s, c->form)",
+                                 "oracle_ml_weight(q, rcij, l + 1, c->L, c->s, c->form)"),
+    "levels_members_not_drifted": ("            if (inpair[i]) continue;\n", "            if (!inpair[i]) continue;\n"),
+    "levels_kick_mass_index": ("double f = c->G * c->m[bj] * oracle_ml_weight", "double f = c->G * c->m[bi] * oracle_ml_weight"),
+    "levels_kick_offset_sign": ("            double dx = c->x[bj] - c->x[bi],", "            double dx = c->x[bi] - c->x[bj],"),
     "dead_pairs_grouped": ("        if (dead && (dead[pairs[2 * p]] || dead[pairs[2 * p + 1]])) continue;\n", ""),
 }
 
@@ -92,7 +108,8 @@ def _run_pins(so):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                         os.path.join(ROOT, "tests", "test_oracle_bs.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_merge.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_merge.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_levels.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return r.returncode
 
