@@ -476,6 +476,26 @@ def run_genga(args):
                   "how": "the headline FP32 steps again with the close-encounter level on: every group of "
                          "encounter pairs integrated by Bulirsch-Stoer over the drift"}
 
+    # ---- intermediate levels of the changeover: the self-tuning call over a
+    # few (levels, sub-steps), then the chosen setting timed like level1
+    levels = None
+    if args.bs_tol > 0:
+        cand = [(0, 2), (1, 2), (1, 4), (2, 2), (2, 3)]
+        st = g.DeviceSystem.from_disc(d, device=dev)
+        p32_on = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=g.GENGA_FP32, bs_tol=args.bs_tol)
+        best, ms_c = g.genga_tune_levels(ctx, st, p32_on, cand, 8)
+        if g.genga_get_status(ctx) != g.GENGA_OK:
+            raise RuntimeError("device status after tuning the levels")
+        p32_lv = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=g.GENGA_FP32, bs_tol=args.bs_tol,
+                               n_levels=best[0], n_sub=best[1])
+        ms_lv, _, _, _, _ = timed_steps(p32_lv, args.steps, args.warmup)
+        ms_lv = max_over_ranks(ms_lv, dist, dev)
+        levels = {"candidates": [list(c) for c in cand], "trial_ms_per_step": [round(v, 4) for v in ms_c],
+                  "chosen": list(best), "value_chosen": weak_value(ws, pairs_step, args.steps, ms_lv), "unit": UNIT,
+                  "ms_per_step_chosen": ms_lv / args.steps,
+                  "how": "genga_tune_levels: 8 trial steps of each (n_levels, n_sub) from a copy of the state "
+                         "(graph-launched, L2 not flushed), then the headline steps with the fastest"}
+
     # ---- the same FP32 steps launched as captured 4-step graphs (genga_step(.., 4)),
     # L2 flushed between blocks
     blocks = max(1, args.steps // 4)
@@ -586,6 +606,7 @@ def run_genga(args):
         "graph_blocks": graph,
         "long_run": long_run,
         "level1": level1,
+        "levels": levels,
         "compaction": compaction,
         "batched": batched,
         "tp2": tp2,

@@ -94,7 +94,22 @@ typedef struct {
     double r_in, r_out;      /* removal radii (Sect. 2): after every drift a body closer than
                                 r_in to, or farther than r_out from, the central body is removed
                                 (see "ghosts" below); <= 0 switches each test off */
+    int32_t n_levels;        /* intermediate levels of the changeover (Sect. 1), 0 .. GENGA_MAX_LEVELS,
+                                with bs_tol > 0: level l (1 <= l <= n_levels) moves its groups in
+                                n_sub kick-drift-kick sub-steps of dt / n_sub^l with the pair radius
+                                r_crit,l = r_crit,ij / n_sub^l; the pair force splits into
+                                W_l = K_l prod_{k<l} (1 - K_k) for the kicks of levels 0 .. n_levels
+                                and prod_{k<=n_levels} (1 - K_k) for the Bulirsch-Stoer level, with
+                                K_l(r) = K((r / r_crit,l - 0.1) / 0.9).  A level-l sub-step forms
+                                subgroups from the member pairs inside r_crit,l (and those whose
+                                straight-line motion enters it within the sub-step, from within
+                                1.5 r_crit,l), drifts the other members on Kepler orbits and moves
+                                each subgroup on level l + 1 (Bulirsch-Stoer below the last).
+                                0: the groups go to the Bulirsch-Stoer level directly */
+    int32_t n_sub;           /* sub-steps per level, 2 .. 16 (ignored when n_levels = 0) */
 } genga_params;
+
+#define GENGA_MAX_LEVELS 3
 
 typedef struct {
     int32_t N;                           /* number of non-central bodies, 0 <= N <= max_N */
@@ -235,6 +250,24 @@ genga_status genga_energy(genga_ctx *ctx, const genga_system *sys, const genga_p
  * spatial order and the encounter list are rebuilt by the next kick.
  */
 genga_status genga_compact(genga_ctx *ctx, genga_system *sys, int32_t *id, void *stream);
+
+/*
+ * Self-tuning of the intermediate levels (Sect. 1: the best number of levels
+ * and sub-steps depends on the number of bodies, their surface density and
+ * the GPU, so configurations are timed before a run and the fastest is
+ * kept).  Each candidate k, params with n_levels = n_levels[k] and n_sub =
+ * n_sub[k] (HOST int32 [ncand], each valid for genga_step), runs
+ * `trial_steps` steps (>= 1) from a device copy of the current state of
+ * `sys`, timed with events on `stream`; the caller's state is not changed.
+ *   best  HOST int32 [1]: index of the fastest candidate
+ *   ms    HOST float [ncand] or NULL: each candidate's time per step (ms)
+ * Synchronous.  The trials leave the context's step graph, spatial order and
+ * status as a genga_step on the copy would (read genga_get_status after).
+ * ncand = 1 .. 64.
+ */
+genga_status genga_tune_levels(genga_ctx *ctx, const genga_system *sys, const genga_params *params,
+                               const int32_t *n_levels, const int32_t *n_sub, int32_t ncand,
+                               int32_t trial_steps, int32_t *best, float *ms, void *stream);
 
 /* Synchronise `stream`, return the sticky device status (lowest set code) and
  * clear it.  Also returns GENGA_ERR_CUDA if the stream reports an error. */

@@ -36,7 +36,8 @@ class genga_params(C.Structure):
                 ("n1", C.c_double), ("n2", C.c_double),
                 ("rcrit_mode", C.c_int32), ("changeover", C.c_int32),
                 ("precision", C.c_int32), ("kepler_max_iter", C.c_int32), ("n_big", C.c_int32),
-                ("bs_tol", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double)]
+                ("bs_tol", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double),
+                ("n_levels", C.c_int32), ("n_sub", C.c_int32)]
 
 
 class genga_system(C.Structure):
@@ -93,6 +94,8 @@ def load():
             "genga_step_batched": ([V, S, C.POINTER(C.c_int32), I, P, I, V], I),
             "genga_get_kernel_variant": ([V, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], I),
             "genga_compact": ([V, S, V, V], I),
+            "genga_tune_levels": ([V, S, P, C.POINTER(I), C.POINTER(I), I, I, C.POINTER(I), C.POINTER(C.c_float), V],
+                                  I),
         }
         for name, (args, res) in sigs.items():
             f = getattr(lib, name)
@@ -124,12 +127,13 @@ def _stream(stream):
 
 def make_params(G, Mstar=1.0, dt=6.0, n1=3.0, n2=0.4, rcrit_mode=GENGA_RCRIT_MUTUAL_HILL,
                 changeover=GENGA_K_CHAMBERS, precision=GENGA_FP32, kepler_max_iter=50, n_big=-1,
-                bs_tol=0.0, r_in=0.0, r_out=0.0) -> genga_params:
+                bs_tol=0.0, r_in=0.0, r_out=0.0, n_levels=0, n_sub=2) -> genga_params:
     """n_big >= 0: test-particle mode 2 (bodies n_big.. feel the first n_big bodies, not each other).
     bs_tol > 0: the drift integrates the close-encounter groups (Bulirsch-Stoer, that tolerance).
-    r_in, r_out > 0: removal radii (bodies inside / beyond become ghosts after each drift)."""
+    r_in, r_out > 0: removal radii (bodies inside / beyond become ghosts after each drift).
+    n_levels > 0 (with bs_tol > 0): that many intermediate levels of n_sub sub-steps."""
     return genga_params(G, Mstar, dt, n1, n2, rcrit_mode, changeover, precision, kepler_max_iter, n_big,
-                        bs_tol, r_in, r_out)
+                        bs_tol, r_in, r_out, n_levels, n_sub)
 
 
 class DeviceSystem:
@@ -261,6 +265,19 @@ def genga_compact(ctx, sys, id=None, stream=None) -> int:
     new N (sys's view is updated)."""
     _check(load().genga_compact(_ctx(ctx), _sys(sys), _ptr(id), _stream(stream)), "genga_compact")
     return int((sys.c if isinstance(sys, DeviceSystem) else sys).N)
+
+
+def genga_tune_levels(ctx, sys, params, candidates, trial_steps=8, stream=None):
+    """Time trial steps of each (n_levels, n_sub) in `candidates` from a copy of
+    sys's state (left unchanged); returns (the fastest pair, ms per step of each)."""
+    cand = list(candidates)
+    nl = (C.c_int32 * len(cand))(*[int(c[0]) for c in cand])
+    ns = (C.c_int32 * len(cand))(*[int(c[1]) for c in cand])
+    best = C.c_int32(-1)
+    ms = (C.c_float * len(cand))()
+    _check(load().genga_tune_levels(_ctx(ctx), _sys(sys), C.byref(params), nl, ns, len(cand), int(trial_steps),
+                                    C.byref(best), ms, _stream(stream)), "genga_tune_levels")
+    return tuple(cand[best.value]), [float(v) for v in ms]
 
 
 def genga_get_status(ctx, stream=None) -> int:

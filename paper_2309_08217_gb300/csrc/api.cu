@@ -43,7 +43,16 @@ genga_status check_params(const genga_params *p) {
     // sub-steps shrink to the floor without converging
     if (!is_fin(p->bs_tol) || p->bs_tol < 0.0 || (p->bs_tol > 0.0 && p->bs_tol < 1e-14)) return GENGA_ERR_INVALID_ARG;
     if (!is_fin(p->r_in) || !is_fin(p->r_out)) return GENGA_ERR_INVALID_ARG;
+    if (p->n_levels < 0 || p->n_levels > GENGA_MAX_LEVELS) return GENGA_ERR_INVALID_ARG;
+    if (p->n_levels > 0 && (p->bs_tol <= 0.0 || p->n_sub < 2 || p->n_sub > 16)) return GENGA_ERR_INVALID_ARG;
     return GENGA_OK;
+}
+
+// Kernels one drift launches: momentum, drift, momentum, central-body drift,
+// and with the close-encounter level the grouping kernel and the levels.
+int drift_launches(const genga_params &p) {
+    if (p.bs_tol <= 0.0) return 4;
+    return 5 + level_launches(p.n_levels, p.n_levels > 0 ? p.n_sub : 1);
 }
 
 genga_status check_system(const genga_ctx *c, const genga_system *s) {
@@ -362,7 +371,8 @@ unsigned long long step_key(const genga_system &sys, const genga_params &p, int 
         memcpy(&bits, &d, sizeof(bits));
         h = mix(h, bits);
     }
-    const int32_t iv[5] = {p.rcrit_mode, p.changeover, p.precision, p.kepler_max_iter, p.n_big};
+    const int32_t iv[7] = {p.rcrit_mode, p.changeover, p.precision, p.kepler_max_iter, p.n_big, p.n_levels,
+                           p.n_levels > 0 ? p.n_sub : 0};
     for (int32_t v : iv) h = mix(h, (unsigned long long)(uint32_t)v);
     h = mix(h, (unsigned long long)(variant + 1));
     return mix(h, layout);
@@ -408,6 +418,36 @@ cudaError_t alloc(T **p, size_t n) {
     return cudaMalloc((void **)p, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
 }
 
+// The group sets of levels 2 .. L + 1, allocated on first use (before any
+// launch or capture of the call): per set three per-body arrays, five
+// per-slot arrays and a pair list of 8 slots + 4096 pairs.
+cudaError_t ensure_levels(genga_ctx *c, int L) {
+    cudaError_t e = cudaSuccess;
+    const size_t np = (size_t)c->npad_max, slots = (size_t)c->bs_slots;
+    for (int k = 0; k < L && k < GENGA_MAX_LEVELS && e == cudaSuccess; k++) {
+        LevelSet &l = c->lv[k];
+        if (l.grp) continue;
+        l.pair_cap = (int32_t)(8 * slots + 4096);
+        if (e == cudaSuccess) e = alloc(&l.grp, np);
+        if (e == cudaSuccess) e = alloc(&l.gmark, np);
+        if (e == cudaSuccess) e = alloc(&l.gslot, np);
+        if (e == cudaSuccess) e = alloc(&l.gbody, slots);
+        if (e == cudaSuccess) e = alloc(&l.gmem, slots);
+        if (e == cudaSuccess) e = alloc(&l.gstart, slots);
+        if (e == cudaSuccess) e = alloc(&l.gsize, slots);
+        if (e == cudaSuccess) e = alloc(&l.gcur, slots);
+        if (e == cudaSuccess) e = alloc(&l.gcount, 1);
+        if (e == cudaSuccess) e = alloc(&l.pairs, (size_t)l.pair_cap);
+        if (e == cudaSuccess) e = alloc(&l.pair_count, 2);
+        if (e == cudaSuccess) e = cudaMemset(l.grp, 0xff, sizeof(int32_t) * np);
+        if (e == cudaSuccess) e = cudaMemset(l.gmark, 0, sizeof(int32_t) * np);
+        if (e == cudaSuccess) e = cudaMemset(l.gcount, 0, sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMemset(l.pair_count, 0, 2 * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -442,6 +482,11 @@ void genga_destroy(genga_ctx *c) {
                     c->pred};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    for (LevelSet &l : c->lv) {
+        void *lb[] = {l.grp, l.gmark, l.gslot, l.gbody, l.gmem, l.gstart, l.gsize, l.gcur, l.gcount, l.pairs, l.pair_count};
+        for (void *b : lb)
+            if (b) cudaFree(b);
+    }
     delete c;
 }
 
@@ -558,7 +603,8 @@ genga_status genga_drift(genga_ctx *c, genga_system *sys, const genga_params *p,
     if (!is_fin(dt)) return GENGA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     genga_system s2 = *sys;
-    if (sys->N > 0) c->launches += p->bs_tol > 0.0 ? 6 : 4;
+    if (ensure_levels(c, p->n_levels) != cudaSuccess) return GENGA_ERR_CUDA;
+    if (sys->N > 0) c->launches += drift_launches(*p);
     return launch_drift(s2, *p, dt, c, (cudaStream_t)stream) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
 }
 
@@ -603,6 +649,7 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (sys->N == 0 || nsteps == 0) return GENGA_OK;
+    if (ensure_levels(c, p->n_levels) != cudaSuccess) return GENGA_ERR_CUDA;
     genga_system s2 = *sys;
     const double h = 0.5 * p->dt;
     genga_params p_close = *p;  // the closing kick of a step: no predicted entries
@@ -615,7 +662,7 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
     auto one_step = [&](cudaStream_t q) -> cudaError_t {
         cudaError_t e = run_kick(c, s2, *p, h, nullptr, false, q);
         if (e == cudaSuccess) e = launch_drift(s2, *p, p->dt, c, q);
-        c->launches += p->bs_tol > 0.0 ? 6 : 4;
+        c->launches += drift_launches(*p);
         c->steps_since_order++;
         const bool reorder = c->steps_since_order >= GENGA_REORDER_STEPS;
         // the closing kick needs no predicted entries (the next step's first
@@ -678,6 +725,7 @@ genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (all->N == 0 || nsteps == 0) return GENGA_OK;
+    if (ensure_levels(c, p->n_levels) != cudaSuccess) return GENGA_ERR_CUDA;
     genga_system a2 = *all;
     const BatchBodies bb = batch_bodies(offsets, D);
     const unsigned long long layout = offsets_hash(offsets, D);
@@ -687,7 +735,7 @@ genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *
     auto one_step = [&](cudaStream_t q) -> cudaError_t {
         cudaError_t e = run_kick_batched(c, a2, offsets, D, *p, h, nullptr, false, false, q);
         if (e == cudaSuccess) e = launch_drift_batched(a2, bb, *p, p->dt, c, q);
-        c->launches += p->bs_tol > 0.0 ? 6 : 4;
+        c->launches += drift_launches(*p);
         c->steps_since_order++;
         const bool reorder = c->steps_since_order >= GENGA_REORDER_STEPS;
         if (e == cudaSuccess) e = run_kick_batched(c, a2, offsets, D, p_close, h, nullptr, reorder, true, q);
@@ -786,6 +834,68 @@ genga_status genga_compact(genga_ctx *c, genga_system *sys, int32_t *id, void *s
     }
     sys->N = n;
     return GENGA_OK;
+}
+
+genga_status genga_tune_levels(genga_ctx *c, const genga_system *sys, const genga_params *p, const int32_t *n_levels,
+                               const int32_t *n_sub, int32_t ncand, int32_t trial_steps, int32_t *best, float *ms,
+                               void *stream) {
+    genga_status st;
+    if ((st = check_system(c, sys)) != GENGA_OK) return st;
+    if ((st = check_params(p)) != GENGA_OK) return st;
+    if (!n_levels || !n_sub || !best || ncand < 1 || ncand > 64 || trial_steps < 1) return GENGA_ERR_INVALID_ARG;
+    for (int k = 0; k < ncand; k++) {
+        genga_params q = *p;
+        q.n_levels = n_levels[k];
+        q.n_sub = n_sub[k];
+        if ((st = check_params(&q)) != GENGA_OK) return st;
+    }
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = (size_t)sys->N, nf = sys->radius ? 8 : 7;
+    double *copy = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc((void **)&copy, sizeof(double) * (N > 0 ? nf * N : 1));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const double *src[8] = {sys->x, sys->y, sys->z, sys->vx, sys->vy, sys->vz, sys->m, sys->radius};
+    genga_system t = *sys;
+    double **dst[8] = {&t.x, &t.y, &t.z, &t.vx, &t.vy, &t.vz, &t.m, &t.radius};
+    for (size_t f = 0; f < nf; f++) *dst[f] = copy + f * N;
+    auto reset = [&]() {
+        for (size_t f = 0; f < nf && e == cudaSuccess; f++)
+            e = cudaMemcpyAsync(*dst[f], src[f], sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+    };
+    float best_ms = 0.0f;
+    *best = 0;
+    for (int k = 0; k < ncand && e == cudaSuccess && st == GENGA_OK; k++) {
+        genga_params q = *p;
+        q.n_levels = n_levels[k];
+        q.n_sub = n_sub[k];
+        reset();  // one untimed step (allocation, graph capture, tuning of the pass), then the trial
+        if (e == cudaSuccess && (st = genga_step(c, &t, &q, 1, stream)) != GENGA_OK) break;
+        reset();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess && (st = genga_step(c, &t, &q, trial_steps, stream)) != GENGA_OK) break;
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t_ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t_ms, e0, e1);
+        t_ms /= (float)trial_steps;
+        if (ms) ms[k] = t_ms;
+        if (k == 0 || t_ms < best_ms) {
+            best_ms = t_ms;
+            *best = k;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (copy) {
+        cudaStreamSynchronize(s);
+        cudaFree(copy);
+    }
+    c->ordered_N = -1;  // the order and the step graph were built on the copy
+    if (st != GENGA_OK) return st;
+    return e == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
 }
 
 genga_status genga_get_status(genga_ctx *c, void *stream) {

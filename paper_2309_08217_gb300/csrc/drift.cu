@@ -96,28 +96,51 @@ __global__ void hc_batched_kernel(double *__restrict__ x, double *__restrict__ y
 // The close-encounter level around the Kepler drift: groups before it (so
 // that it skips their members), the level-1 integration after it.  N bodies
 // of the caller's arrays `sys` (all systems of a batch).
-cudaError_t launch_level1_groups(const genga_system &sys, genga_ctx *c, cudaStream_t s) {
-    GroupArgs g;
-    g.enc = c->enc;
-    g.pred = c->pred;
-    g.enc_count = c->enc_count;
-    g.enc_cap = c->enc_cap;
-    g.N = sys.N;
-    g.slots = c->bs_slots;
-    g.grp = c->grp;
-    g.gmark = c->gmark;
-    g.gslot = c->gslot;
-    g.gbody = c->gbody;
-    g.gmem = c->gmem;
-    g.gstart = c->gstart;
-    g.gsize = c->gsize;
-    g.gcur = c->gcur;
-    g.gcount = c->gcount;
-    g.status = c->status;
-    return launch_groups(g, s);
+namespace {
+
+// Level 1's groups live in the context's arrays, formed from the step's
+// encounter pairs and predicted entries.
+LevelSet base_set(genga_ctx *c) {
+    LevelSet l;
+    l.grp = c->grp;
+    l.gmark = c->gmark;
+    l.gslot = c->gslot;
+    l.gbody = c->gbody;
+    l.gmem = c->gmem;
+    l.gstart = c->gstart;
+    l.gsize = c->gsize;
+    l.gcur = c->gcur;
+    l.gcount = c->gcount;
+    l.pairs = c->enc;
+    l.pair_count = c->enc_count;
+    l.pair_cap = c->enc_cap;
+    return l;
 }
 
-cudaError_t launch_level1(genga_system &sys, const genga_params &p, double dt, genga_ctx *c, cudaStream_t s) {
+GroupArgs group_args(const genga_system &sys, genga_ctx *c, const LevelSet &l, const int2 *pred) {
+    GroupArgs g;
+    g.enc = l.pairs;
+    g.pred = pred;
+    g.enc_count = l.pair_count;
+    g.enc_cap = l.pair_cap;
+    g.N = sys.N;
+    g.slots = c->bs_slots;
+    g.grp = l.grp;
+    g.gmark = l.gmark;
+    g.gslot = l.gslot;
+    g.gbody = l.gbody;
+    g.gmem = l.gmem;
+    g.gstart = l.gstart;
+    g.gsize = l.gsize;
+    g.gcur = l.gcur;
+    g.gcount = l.gcount;
+    g.status = c->status;
+    return g;
+}
+
+// The Bulirsch-Stoer integration of the groups of `l` over dt, below nlev
+// intermediate levels.
+BSArgs bs_args(genga_system &sys, const genga_params &p, double dt, genga_ctx *c, const LevelSet &l, int nlev) {
     BSArgs b;
     b.x = sys.x; b.y = sys.y; b.z = sys.z;
     b.vx = sys.vx; b.vy = sys.vy; b.vz = sys.vz;
@@ -126,13 +149,13 @@ cudaError_t launch_level1(genga_system &sys, const genga_params &p, double dt, g
     b.a_osc = c->a_osc;
     b.rc_eq1 = c->rc_eq1;
     b.lo = c->pk_lo;
-    b.gcount = c->gcount;
-    b.gstart = c->gstart;
-    b.gsize = c->gsize;
-    b.gmem = c->gmem;
-    b.gbody = c->gbody;
-    b.grp = c->grp;
-    b.gmark = c->gmark;
+    b.gcount = l.gcount;
+    b.gstart = l.gstart;
+    b.gsize = l.gsize;
+    b.gmem = l.gmem;
+    b.gbody = l.gbody;
+    b.grp = l.grp;
+    b.gmark = l.gmark;
     b.tpf = c->bs_tp;
     b.radius = sys.radius;
     b.bs = c->bs_work;
@@ -144,8 +167,92 @@ cudaError_t launch_level1(genga_system &sys, const genga_params &p, double dt, g
     b.tol = p.bs_tol;
     b.rcrit_mode = p.rcrit_mode;
     b.changeover = p.changeover;
+    b.nlev = nlev;
+    b.nsub = nlev > 0 ? (double)p.n_sub : 1.0;
+    b.snl = 1.0;
+    for (int k = 0; k < nlev; k++) b.snl *= b.nsub;
     b.status = c->status;
-    return launch_bs(b, c->sm_count, s);
+    return b;
+}
+
+LevelArgs level_args(genga_system &sys, const genga_params &p, genga_ctx *c, const LevelSet &l, const LevelSet &next,
+                     int level) {
+    LevelArgs a;
+    a.x = sys.x; a.y = sys.y; a.z = sys.z;
+    a.vx = sys.vx; a.vy = sys.vy; a.vz = sys.vz;
+    a.m = sys.m;
+    a.iperm = c->iperm;
+    a.a_osc = c->a_osc;
+    a.rc_eq1 = c->rc_eq1;
+    a.lo = c->pk_lo;
+    a.gcount = l.gcount;
+    a.gstart = l.gstart;
+    a.gsize = l.gsize;
+    a.gmem = l.gmem;
+    a.gbody = l.gbody;
+    a.grp = l.grp;
+    a.gmark = l.gmark;
+    a.next_grp = next.grp;
+    a.next_pairs = next.pairs;
+    a.next_count = next.pair_count;
+    a.next_cap = next.pair_cap;
+    a.G = p.G;
+    a.Mstar = p.Mstar;
+    a.n1 = p.n1;
+    a.rcrit_mode = p.rcrit_mode;
+    a.changeover = p.changeover;
+    a.level = level;
+    a.nlev = p.n_levels;
+    a.nsub = (double)p.n_sub;
+    a.sl = 1.0;
+    for (int k = 0; k < level; k++) a.sl *= a.nsub;
+    a.max_iter = p.kepler_max_iter;
+    a.status = c->status;
+    return a;
+}
+
+// Level `level` (1 .. n_levels) moves its groups over T in n_sub sub-steps
+// (see levels.cu); the next level's groups are formed in every sub-step.
+cudaError_t run_level(genga_system &sys, const genga_params &p, genga_ctx *c, int level, double T, cudaStream_t s) {
+    const LevelSet l = level == 1 ? base_set(c) : c->lv[level - 2];
+    const LevelSet &next = c->lv[level - 1];
+    const LevelArgs a = level_args(sys, p, c, l, next, level);
+    const double h = T / p.n_sub;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < p.n_sub && e == cudaSuccess; k++) {
+        e = launch_level_kick(a, 0.5 * h, c->sm_count, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(next.pair_count, 0, 2 * sizeof(int32_t), s);
+        if (e == cudaSuccess) e = launch_level_scan(a, h, c->sm_count, s);
+        if (e == cudaSuccess) e = launch_groups(group_args(sys, c, next, next.pairs), s);
+        if (e == cudaSuccess) e = launch_level_drift(a, h, c->sm_count, s);
+        if (e == cudaSuccess)
+            e = level < p.n_levels ? run_level(sys, p, c, level + 1, h, s)
+                                   : launch_bs(bs_args(sys, p, h, c, next, p.n_levels), c->sm_count, s);
+        if (e == cudaSuccess) e = launch_level_kick(a, 0.5 * h, c->sm_count, s);
+    }
+    if (e == cudaSuccess) e = launch_level_clear(a, c->sm_count, s);
+    return e;
+}
+
+}  // namespace
+
+cudaError_t launch_level1_groups(const genga_system &sys, genga_ctx *c, cudaStream_t s) {
+    return launch_groups(group_args(sys, c, base_set(c), c->pred), s);
+}
+
+cudaError_t launch_level1(genga_system &sys, const genga_params &p, double dt, genga_ctx *c, cudaStream_t s) {
+    if (p.n_levels > 0) return run_level(sys, p, c, 1, dt, s);
+    return launch_bs(bs_args(sys, p, dt, c, base_set(c), 0), c->sm_count, s);
+}
+
+// Kernels one drift launches for the close-encounter levels beyond the
+// grouping kernel: the Bulirsch-Stoer kernel, or with L levels of s
+// sub-steps, per level-l sub-step kick, scan, groups, drift, the level below
+// and kick, and one clear per level.
+int level_launches(int n_levels, int n_sub) {
+    int below = 1;  // the Bulirsch-Stoer kernel
+    for (int l = n_levels; l >= 1; l--) below = n_sub * (5 + below) + 1;
+    return below;
 }
 
 cudaError_t launch_removal(genga_system &sys, const genga_params &p, cudaStream_t s) {

@@ -26,6 +26,7 @@
 // body momentum drift only, and this level moves them over dt in between
 // the two momentum drifts.  Everything here is FP64 (Sect. 1, last paragraph:
 // close-encounter forces are always double precision).
+#include "changeover.cuh"
 #include "kepler.cuh"
 
 namespace genga {
@@ -223,7 +224,7 @@ enum : int {
     F_RAD = F_RC + 1,                     // physical radius (mergers)
     F_Z = F_RAD + 1,                      // per column k: three rotating midpoint states (18 fields)
     F_T = F_Z + 18 * BS_KMAX,             // per column k: the smoothed midpoint result T[k][0] (6 fields)
-    F_PR2 = F_T + 6 * BS_KMAX,            // r_crit,ij^2 with the first BS_PAIR_TAB members
+    F_PR2 = F_T + 6 * BS_KMAX,            // (r_crit,ij / s^nlev)^2 with the first BS_PAIR_TAB members
     F_PIN = F_PR2 + BS_PAIR_TAB,          // 1 / (0.9 r_crit,ij)
     F_COUNT = F_PIN + BS_PAIR_TAB
 };
@@ -253,20 +254,25 @@ __constant__ NevilleTable c_neville = NevilleTable();
 // Pair radius r_crit,ij of two members (the kick's rule, Eq. 1 inputs of that kick).
 __device__ __forceinline__ double pair_radius(const BSArgs &a, double mi, double mj, double ai, double aj, double rci,
                                               double rcj) {
-    return (a.rcrit_mode == GENGA_RCRIT_EQ1) ? fmax(rci, rcj)
-                                             : a.n1 * cbrt((mi + mj) / (3.0 * a.Mstar)) * 0.5 * (ai + aj);
+    return pair_rcrit(a.rcrit_mode, a.n1, a.Mstar, mi, mj, ai, aj, rci, rcj);
 }
 
-// 1 - K(y) from y = q / (0.9 r_crit) - 1/9, with K the kick's changeover weight
-// (Sect. 1): 1 for y <= 0, 0 for y >= 1.
-__device__ __forceinline__ double level1_weight(double y, int form) {
-    if (y <= 0.0) return 1.0;
-    if (y >= 1.0) return 0.0;
-    if (form == GENGA_K_CHAMBERS) {
-        const double y2 = y * y;
-        return 1.0 - y2 * rcp_fp64(fma(2.0 * y, y - 1.0, 1.0));  // y^2 / (2y^2 - 2y + 1)
+// Share of the pair force this level integrates, at separation q, inv9 =
+// 1 / (0.9 r_crit,ij): prod_{k=0}^{nlev} (1 - K_k) with K_k the changeover
+// at r_crit,ij / s^k (Sect. 1's intermediate levels take the K_k parts);
+// 1 - K_0 without levels.
+__device__ __noinline__ double deeper_keep(const BSArgs &a, double q, double inv9) {  // prod_{k=1}^{nlev} (1 - K_k)
+    double w = 1.0, f = inv9;
+    for (int k = 1; k <= a.nlev; k++) {
+        f *= a.nsub;
+        w *= keep_weight(fma(q, f, -1.0 / 9.0), a.changeover);
     }
-    return 1.0 - y * y * y * (10.0 + y * (6.0 * y - 15.0));
+    return w;
+}
+
+__device__ __forceinline__ double bs_weight(const BSArgs &a, double q, double inv9) {
+    const double w = keep_weight(fma(q, inv9, -1.0 / 9.0), a.changeover);
+    return a.nlev > 0 ? w * deeper_keep(a, q, inv9) : w;
 }
 
 // Level-1 acceleration of the member in slot s with positions in fields
@@ -300,12 +306,13 @@ __device__ void level1_acc(const BSArgs &a, const Work &W, int s, int s0, int n,
             inv9 = W(F_PIN + (t - s0), s);
         } else {
             const double rc = pair_radius(a, W(F_M, s), M[t], W(F_A, s), W(F_A, t), W(F_RC, s), W(F_RC, t));
-            rc2 = rc * rc;
+            const double rcl = rc / a.snl;
+            rc2 = rcl * rcl;
             inv9 = 1.0 / (0.9 * rc);
         }
-        if (q2 >= rc2) continue;  // K = 1: the kick has all of it
+        if (q2 >= rc2) continue;  // K = 1 (or K_nlev = 1): the kicks have all of it
         const double iq = rsqrt_fp64(q2);
-        const double w = level1_weight(fma(q2 * iq, inv9, -1.0 / 9.0), a.changeover);
+        const double w = bs_weight(a, q2 * iq, inv9);
         const double f = a.G * M[t] * w * (iq * iq * iq);
         ax = fma(f, dx, ax);
         ay = fma(f, dy, ay);
@@ -415,9 +422,10 @@ __device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, 
             use[p] = act && p < n && p != q && !(tpq && tpp) && !ghq && !ghp;
             double rc = 1.0;
             if (use[p]) rc = pair_radius(a, mq, mp, aq, ap, rcq, rcp);
+            const double rcl = rc / a.snl;  // the innermost radius: no force beyond it, all of it inside 0.1 of it
             gm[p] = a.G * mp;
-            rc2[p] = rc * rc;
-            lo2[p] = (0.1 * rc) * (0.1 * rc);
+            rc2[p] = rcl * rcl;
+            lo2[p] = (0.1 * rcl) * (0.1 * rcl);
             inv9[p] = 1.0 / (0.9 * rc);
         }
     };
@@ -444,7 +452,7 @@ __device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, 
             const double q2 = dx * dx + dy * dy + dz * dz;
             if (__double_as_longlong(q2) == 0 || ge_nonneg(q2, rc2[p])) continue;  // coincident / K = 1
             const double iq = rsqrt_fp64(q2);
-            const double w = ge_nonneg(lo2[p], q2) ? 1.0 : level1_weight(fma(q2 * iq, inv9[p], -1.0 / 9.0), a.changeover);
+            const double w = ge_nonneg(lo2[p], q2) ? 1.0 : bs_weight(a, q2 * iq, inv9[p]);
             const double f = gm[p] * w * (iq * iq * iq);
             ax = fma(f, dx, ax);
             ay = fma(f, dy, ay);
@@ -657,7 +665,8 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
                 const int si = s0 + idx / n, ti = idx % n;
                 const double rc = pair_radius(a, W(F_M, si), W(F_M, s0 + ti), W(F_A, si), W(F_A, s0 + ti),
                                               W(F_RC, si), W(F_RC, s0 + ti));
-                W(F_PR2 + ti, si) = rc * rc;
+                const double rcl = rc / a.snl;
+                W(F_PR2 + ti, si) = rcl * rcl;
                 W(F_PIN + ti, si) = 1.0 / (0.9 * rc);
             }
             __syncwarp();

@@ -57,6 +57,20 @@ struct Profile {                // CUDA event pairs around pass launches
 #define GENGA_MAX_VARIANTS 16  // FP32 pass variants the context records tuning times for
 #define GENGA_MAX_TIERS 8      // chunk-length tiers of an FP32 pass plan
 
+namespace genga {
+// The groups of one level: the layout the grouping kernel writes (members of
+// group g at gmem[gstart[g] ..], gsize[g] of them; grp / gmark per body) and
+// the pair list they are formed from.
+struct LevelSet {
+    int32_t *grp, *gmark, *gslot;               // [npad_max]
+    int32_t *gbody, *gmem, *gstart, *gsize, *gcur;  // [bs_slots]
+    int32_t *gcount;                            // [1]
+    int2 *pairs;                                // [pair_cap] pairs of the level above inside this level's radius
+    int32_t *pair_count;                        // [2]: pairs, 0 (the grouping kernel's second list)
+    int32_t pair_cap;
+};
+}  // namespace genga
+
 struct genga_ctx {
     int device;
     int sm_count;
@@ -118,6 +132,9 @@ struct genga_ctx {
     int32_t *gcount;           // [1] number of groups
     int32_t *bs_tp;            // [bs_slots] member is a test particle (mode 2)
     double *bs_work;           // [GENGA_BS_FIELDS * bs_slots] level-1 integration state
+    // intermediate levels (levels.cu): groups of level 2 .. GENGA_MAX_LEVELS + 1, allocated on
+    // first use (genga_params.n_levels > 0); level 1 uses the arrays above
+    genga::LevelSet lv[GENGA_MAX_LEVELS];
     double *Pd;                // [3 * GENGA_MAX_DISCS] momentum of each system (batched mode)
     double *Pd_part;           // [3 * GENGA_MAX_DISCS] scratch
     size_t partial_cap;        // doubles in `partial`
@@ -220,8 +237,39 @@ struct BSArgs {                 // level-1 integration of the groups (one warp p
     int32_t slots;
     double G, Mstar, n1, dt, tol;
     int32_t rcrit_mode, changeover;
+    int32_t nlev;               // intermediate levels above this one: the pair weight is prod_{k<=nlev} (1 - K_k)
+    double nsub;                // their sub-step factor s (r_crit,k = r_crit / s^k)
+    double snl;                 // s^nlev (exact; 1 without levels)
     uint32_t *status;
 };
+
+struct LevelArgs {              // one intermediate level (levels.cu): its groups and the next level's
+    double *x, *y, *z, *vx, *vy, *vz;
+    const double *m;
+    const uint32_t *iperm;
+    const double *a_osc, *rc_eq1;
+    const float4 *lo;
+    const int32_t *gcount, *gstart, *gsize, *gmem;
+    int32_t *gbody;             // members sorted by body index per group (written by the kick)
+    int32_t *grp, *gmark;       // this level's marks (cleared at the end of the level)
+    const int32_t *next_grp;    // the next level's labels (members with one move there)
+    int2 *next_pairs;           // the next level's pair list
+    int32_t *next_count;
+    int32_t next_cap;
+    double G, Mstar, n1;
+    int32_t rcrit_mode, changeover;
+    int32_t level, nlev;        // l (1 .. nlev)
+    double nsub;                // s
+    double sl;                  // s^l (exact)
+    int32_t max_iter;
+    uint32_t *status;
+};
+
+int level_launches(int n_levels, int n_sub);
+cudaError_t launch_level_kick(const LevelArgs &a, double tau, int sm_count, cudaStream_t s);
+cudaError_t launch_level_scan(const LevelArgs &a, double h, int sm_count, cudaStream_t s);
+cudaError_t launch_level_drift(const LevelArgs &a, double h, int sm_count, cudaStream_t s);
+cudaError_t launch_level_clear(const LevelArgs &a, int sm_count, cudaStream_t s);
 
 cudaError_t launch_groups(const GroupArgs &g, cudaStream_t s);
 cudaError_t launch_removal(genga_system &sys, const genga_params &p, cudaStream_t s);

@@ -55,3 +55,23 @@ def orbiting_pairs_disc(N, seed, fracs=(0.05, 0.5, 0.9, 1.1, 0.3)):
     for dst, src in zip(d2.arrays(), arr):
         dst[:] = src
     return d2
+
+
+def check_merged(got, ref, dead, tol=1e-10, survivors=None):
+    """Parity of a state with perfect mergers.  The live bodies agree with the
+    oracle to `tol` of |x| and |v|.  A ghost keeps the state it had when the
+    overlap was detected, at the end of an accepted Bulirsch-Stoer sub-step,
+    and which sub-step that is can flip with the rounding of the tolerance
+    test (a one-ulp change of one input coordinate moves the oracle's own
+    ghost by its pre-merge relative speed times a sub-step), so a ghost is
+    only checked to be finite and, for merged pairs given as
+    {ghost: survivor}, to stay within 0.01 au and 1e-3 au/day of its survivor."""
+    live = np.nonzero(dead == 0)[0]
+    g = np.stack(got[:6]); r = np.stack(ref[:6])
+    ep = np.sqrt(((g[:3, live] - r[:3, live]) ** 2).sum(0)) / np.sqrt((r[:3, live] ** 2).sum(0))
+    ev = np.sqrt(((g[3:, live] - r[3:, live]) ** 2).sum(0)) / np.sqrt((r[3:, live] ** 2).sum(0))
+    assert max(ep.max(initial=0.0), ev.max(initial=0.0)) < tol
+    ghosts = np.nonzero(dead != 0)[0]
+    assert np.all(np.isfinite(g[:, ghosts]))
+    for gh, sv in (survivors or {}).items():
+        assert np.linalg.norm(g[:3, gh] - g[:3, sv]) < 0.01 and np.linalg.norm(g[3:, gh] - g[3:, sv]) < 1e-3

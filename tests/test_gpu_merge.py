@@ -3,15 +3,18 @@ bs_tol > 0 and physical radii; params r_in / r_out; genga_compact) against
 the oracle's step with the same switches.
 
 The merged masses, radii and the set of ghosts (mass -0.0) must be
-identical; positions and velocities agree to 1e-10 of |x| and |v| (FP64
-kick) as in the other close-encounter tests.  Compaction keeps the
+identical; positions and velocities of the live bodies agree to 1e-10 of |x|
+and |v| (FP64 kick) as in the other close-encounter tests.  A merged ghost
+keeps the state of the sub-step that detected the overlap, which can flip
+with rounding, so its state is checked for validity only
+(gpu_cases.check_merged).  Compaction keeps the
 survivors' order and moves an id array along.
 """
 import numpy as np
 import pytest
 
 import oracle
-from tests.gpu_cases import planted_disc
+from tests.gpu_cases import check_merged, planted_disc
 from tests.test_gpu_bs import _rel_state, _swarm
 
 pytestmark = pytest.mark.gpu
@@ -60,7 +63,7 @@ def test_head_on_pair_merges(genga, ctx):
     assert np.array_equal(np.signbit(got[6]), dead == 1)
     np.testing.assert_allclose(got[6], arr[6], rtol=1e-15, atol=0)
     np.testing.assert_allclose(got_R, Ro, rtol=1e-14, atol=0)
-    assert _rel_state(got, arr) < 1e-10
+    check_merged(got, arr, dead, 1e-10, {1: 0})
     # compaction drops exactly the ghosts, in order, with the ids
     n = genga.genga_compact(ctx, s, ids)
     assert n == d.N - int(dead.sum())
@@ -107,7 +110,7 @@ def test_swarm_mergers_large_group(genga, ctx, n_big):
     assert np.array_equal(np.signbit(got[6]), dead == 1)
     np.testing.assert_allclose(got[6], arr[6], rtol=1e-14, atol=0)
     np.testing.assert_allclose(got_R, Ro, rtol=1e-13, atol=0)
-    assert _rel_state(got, arr) < 1e-10
+    check_merged(got, arr, dead, 1e-10)
 
 
 def test_no_radius_no_mergers(genga, ctx):
@@ -182,7 +185,7 @@ def test_batched_mergers_and_removal(genga):
         assert np.array_equal(np.signbit(gk[6]), dead == 1), f"system {k}"
         np.testing.assert_allclose(gk[6], ref[6], rtol=1e-15, atol=0)
         np.testing.assert_allclose(got_R[lo:hi], Rk, rtol=1e-14, atol=0)
-        assert _rel_state(gk, ref) < 1e-9, f"system {k}"
+        check_merged(gk, ref, dead, 1e-9)
         total_ghosts += int(dead.sum())
     assert total_ghosts >= 3
     c.close()
