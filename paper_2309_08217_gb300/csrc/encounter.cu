@@ -24,7 +24,9 @@
 //
 // The drift kernel skips the members (grp[i] >= 0): they get the central-
 // body momentum drift only, and this level moves them over dt in between
-// the two momentum drifts.  Everything here is FP64 (Sect. 1, last paragraph:
+// the two momentum drifts.  With intermediate levels (levels.cu) this kernel
+// integrates the subgroups of the last level over its sub-step, with the
+// pair share prod_{k=0}^{L} (1 - K_k) in place of 1 - K.  Everything here is FP64 (Sect. 1, last paragraph:
 // close-encounter forces are always double precision).
 #include "changeover.cuh"
 #include "kepler.cuh"
