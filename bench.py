@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-tp2", action="store_true", help="skip the test-particle-mode-2 kicks on giants100k")
     ap.add_argument("--long-steps", type=int, default=1000,
                     help="length of the run whose mean step and pass times are reported (0: skip)")
+    ap.add_argument("--levels", default=None,
+                    help="L:s -- time the disc40k steps of the 'levels' object with L intermediate levels of s "
+                         "sub-steps instead of the tuned setting")
     ap.add_argument("--bs-tol", type=float, default=1e-12,
                     help="tolerance of the close-encounter (Bulirsch-Stoer) level, timed beside the headline "
                          "step (which is the level-0 path: kick, drift, kick); 0: skip that measurement")
@@ -476,6 +479,23 @@ def run_genga(args):
                   "how": "the headline FP32 steps again with the close-encounter level on: every group of "
                          "encounter pairs integrated by Bulirsch-Stoer over the drift"}
 
+    def graph_blocks(params, blocks):
+        """Steps as captured 4-step graphs (genga_step(.., 4)), L2 flushed between
+        blocks; returns (max-over-ranks ms of all blocks, steps)."""
+        sg = g.DeviceSystem.from_disc(d, device=dev)
+        g.genga_step(ctx, sg, params, 8)          # aligns the order and captures the graph
+        evb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(blocks)]
+        barrier()
+        for k in range(blocks):
+            flush.zero_()
+            evb[k][0].record(stream)
+            g.genga_step(ctx, sg, params, 4)
+            evb[k][1].record(stream)
+        barrier()
+        if g.genga_get_status(ctx) != g.GENGA_OK:
+            raise RuntimeError("device status after the graph blocks")
+        return max_over_ranks(sum(a.elapsed_time(b) for a, b in evb), dist, dev), 4 * blocks
+
     # ---- intermediate levels of the changeover: the self-tuning call over a
     # few (levels, sub-steps), then the chosen setting timed like level1
     levels = None
@@ -486,15 +506,40 @@ def run_genga(args):
         best, ms_c = g.genga_tune_levels(ctx, st, p32_on, cand, 8)
         if g.genga_get_status(ctx) != g.GENGA_OK:
             raise RuntimeError("device status after tuning the levels")
+        chosen = tuple(int(v) for v in args.levels.split(":")) if args.levels else best
         p32_lv = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=g.GENGA_FP32, bs_tol=args.bs_tol,
-                               n_levels=best[0], n_sub=best[1])
-        ms_lv, _, _, _, _ = timed_steps(p32_lv, args.steps, args.warmup)
-        ms_lv = max_over_ranks(ms_lv, dist, dev)
+                               n_levels=chosen[0], n_sub=chosen[1])
+        ms_lv, nsteps_lv = graph_blocks(p32_lv, max(1, args.steps // 4))
+        p32_l0 = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=g.GENGA_FP32, bs_tol=args.bs_tol)
+        ms_l0, _ = graph_blocks(p32_l0, max(1, args.steps // 4))
         levels = {"candidates": [list(c) for c in cand], "trial_ms_per_step": [round(v, 4) for v in ms_c],
-                  "chosen": list(best), "value_chosen": weak_value(ws, pairs_step, args.steps, ms_lv), "unit": UNIT,
-                  "ms_per_step_chosen": ms_lv / args.steps,
+                  "tuned": list(best), "timed": list(chosen),
+                  "value_timed": weak_value(ws, pairs_step, nsteps_lv, ms_lv), "unit": UNIT,
+                  "ms_per_step_timed": ms_lv / nsteps_lv, "ms_per_step_no_levels": ms_l0 / nsteps_lv,
                   "how": "genga_tune_levels: 8 trial steps of each (n_levels, n_sub) from a copy of the state "
-                         "(graph-launched, L2 not flushed), then the headline steps with the fastest"}
+                         "(graph-launched, L2 not flushed); then the fastest (or --levels) and the level-1 step "
+                         "without levels, both as captured 4-step graphs with L2 flushed between blocks"}
+        # a dense group: a 10 Earth-mass planet with 80 planetesimals within 0.05 au, in a
+        # 4,000-body disc (one 85-member close-encounter group), where Bulirsch-Stoer alone is slow
+        dsw = discs.workload("swarm4k")
+        csw = g.Context(dsw.N, local)
+        ssw = g.DeviceSystem.from_disc(dsw, device=dev)
+        psw = g.make_params(G=dsw.G, Mstar=dsw.Mstar, dt=dsw.dt, precision=g.GENGA_FP32, bs_tol=args.bs_tol)
+        cand_sw = [(0, 2), (1, 4), (1, 8), (2, 3), (2, 4)]
+        codes_sw = []
+        best_sw, ms_sw = g.genga_tune_levels(csw, ssw, psw, cand_sw, 4, codes=codes_sw)
+        if g.genga_get_status(csw) != g.GENGA_OK:
+            raise RuntimeError("device status after tuning the levels on swarm4k")
+        csw.close()
+        pairs_sw = 2 * dsw.N * (dsw.N - 1)
+        ms_best = ms_sw[cand_sw.index(best_sw)]
+        levels["swarm4k"] = {
+            "N": dsw.N, "candidates": [list(c) for c in cand_sw], "trial_ms_per_step": [round(v, 4) for v in ms_sw],
+            "trial_status": codes_sw, "tuned": list(best_sw), "value_tuned": pairs_sw / (ms_best * 1e-3),
+            "unit": UNIT, "speedup_over_no_levels": ms_sw[0] / ms_best,
+            "how": "genga_tune_levels, 4 graph-launched trial steps per candidate from the same state; a "
+                   "candidate whose trial raised a status (7: the Bulirsch-Stoer level hit its sub-step or "
+                   "time limits and finished on Kepler orbits) is not chosen"}
 
     # ---- the same FP32 steps launched as captured 4-step graphs (genga_step(.., 4)),
     # L2 flushed between blocks

@@ -257,17 +257,22 @@ genga_status genga_compact(genga_ctx *ctx, genga_system *sys, int32_t *id, void 
  * the GPU, so configurations are timed before a run and the fastest is
  * kept).  Each candidate k, params with n_levels = n_levels[k] and n_sub =
  * n_sub[k] (HOST int32 [ncand], each valid for genga_step), runs
- * `trial_steps` steps (>= 1) from a device copy of the current state of
- * `sys`, timed with events on `stream`; the caller's state is not changed.
- *   best  HOST int32 [1]: index of the fastest candidate
- *   ms    HOST float [ncand] or NULL: each candidate's time per step (ms)
- * Synchronous.  The trials leave the context's step graph, spatial order and
- * status as a genga_step on the copy would (read genga_get_status after).
- * ncand = 1 .. 64.
+ * `trial_steps` steps (>= 1, after one untimed step) from a device copy of
+ * the current state of `sys`, timed with events on `stream`; the caller's
+ * state is not changed.
+ *   best   HOST int32 [1]: index of the fastest candidate whose trial raised
+ *          no status (a forced Bulirsch-Stoer acceptance, say, when a dense
+ *          group exhausts the level's sub-step or time limits); if every
+ *          trial raised one, the fastest of all, and its status bits stay set
+ *   ms     HOST float [ncand] or NULL: each candidate's time per step (ms)
+ *   codes  HOST int32 [ncand] or NULL: each candidate's status (lowest code)
+ * Synchronous.  The context's status bits from before the call are kept; the
+ * trials leave the step graph and the spatial order as a genga_step on the
+ * copy would.  ncand = 1 .. 64.
  */
 genga_status genga_tune_levels(genga_ctx *ctx, const genga_system *sys, const genga_params *params,
                                const int32_t *n_levels, const int32_t *n_sub, int32_t ncand,
-                               int32_t trial_steps, int32_t *best, float *ms, void *stream);
+                               int32_t trial_steps, int32_t *best, float *ms, int32_t *codes, void *stream);
 
 /* Synchronise `stream`, return the sticky device status (lowest set code) and
  * clear it.  Also returns GENGA_ERR_CUDA if the stream reports an error. */

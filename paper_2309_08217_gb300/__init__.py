@@ -94,8 +94,8 @@ def load():
             "genga_step_batched": ([V, S, C.POINTER(C.c_int32), I, P, I, V], I),
             "genga_get_kernel_variant": ([V, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], I),
             "genga_compact": ([V, S, V, V], I),
-            "genga_tune_levels": ([V, S, P, C.POINTER(I), C.POINTER(I), I, I, C.POINTER(I), C.POINTER(C.c_float), V],
-                                  I),
+            "genga_tune_levels": ([V, S, P, C.POINTER(I), C.POINTER(I), I, I, C.POINTER(I), C.POINTER(C.c_float),
+                                   C.POINTER(I), V], I),
         }
         for name, (args, res) in sigs.items():
             f = getattr(lib, name)
@@ -267,16 +267,21 @@ def genga_compact(ctx, sys, id=None, stream=None) -> int:
     return int((sys.c if isinstance(sys, DeviceSystem) else sys).N)
 
 
-def genga_tune_levels(ctx, sys, params, candidates, trial_steps=8, stream=None):
+def genga_tune_levels(ctx, sys, params, candidates, trial_steps=8, stream=None, codes=None):
     """Time trial steps of each (n_levels, n_sub) in `candidates` from a copy of
-    sys's state (left unchanged); returns (the fastest pair, ms per step of each)."""
+    sys's state (left unchanged); returns (the fastest pair whose trial raised
+    no status, ms per step of each).  codes: optional list, extended with each
+    candidate's status code."""
     cand = list(candidates)
     nl = (C.c_int32 * len(cand))(*[int(c[0]) for c in cand])
     ns = (C.c_int32 * len(cand))(*[int(c[1]) for c in cand])
     best = C.c_int32(-1)
     ms = (C.c_float * len(cand))()
+    cs = (C.c_int32 * len(cand))()
     _check(load().genga_tune_levels(_ctx(ctx), _sys(sys), C.byref(params), nl, ns, len(cand), int(trial_steps),
-                                    C.byref(best), ms, _stream(stream)), "genga_tune_levels")
+                                    C.byref(best), ms, cs, _stream(stream)), "genga_tune_levels")
+    if codes is not None:
+        codes.extend(int(v) for v in cs)
     return tuple(cand[best.value]), [float(v) for v in ms]
 
 

@@ -436,6 +436,7 @@ cudaError_t ensure_levels(genga_ctx *c, int L) {
         if (e == cudaSuccess) e = alloc(&l.gstart, slots);
         if (e == cudaSuccess) e = alloc(&l.gsize, slots);
         if (e == cudaSuccess) e = alloc(&l.gcur, slots);
+        if (e == cudaSuccess) e = alloc(&l.gof, slots);
         if (e == cudaSuccess) e = alloc(&l.gcount, 1);
         if (e == cudaSuccess) e = alloc(&l.pairs, (size_t)l.pair_cap);
         if (e == cudaSuccess) e = alloc(&l.pair_count, 2);
@@ -478,12 +479,13 @@ void genga_destroy(genga_ctx *c) {
                     c->ord_rbits,   c->a_osc,       c->rc_eq1,      c->partial,  c->mom,        c->enc,
                     c->enc_count,   c->status,      c->energy_part, c->work,   c->Pd,         c->Pd_part,
                     c->grp,         c->gmark,       c->gslot,       c->iperm,  c->gbody,      c->gmem,
-                    c->gstart,      c->gsize,       c->gcur,        c->gcount, c->bs_tp,      c->bs_work,
+                    c->gstart,      c->gsize,       c->gcur,        c->gcount, c->gof,        c->bs_tp,      c->bs_work,
                     c->pred};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (LevelSet &l : c->lv) {
-        void *lb[] = {l.grp, l.gmark, l.gslot, l.gbody, l.gmem, l.gstart, l.gsize, l.gcur, l.gcount, l.pairs, l.pair_count};
+        void *lb[] = {l.grp,  l.gmark,  l.gslot, l.gbody, l.gmem,      l.gstart,
+                      l.gsize, l.gcur,  l.gof,   l.gcount, l.pairs, l.pair_count};
         for (void *b : lb)
             if (b) cudaFree(b);
     }
@@ -568,6 +570,7 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     if (e == cudaSuccess) e = alloc(&c->gsize, c->bs_slots);
     if (e == cudaSuccess) e = alloc(&c->gcur, c->bs_slots);
     if (e == cudaSuccess) e = alloc(&c->gcount, 1);
+    if (e == cudaSuccess) e = alloc(&c->gof, c->bs_slots);
     if (e == cudaSuccess) e = alloc(&c->bs_tp, c->bs_slots);
     if (e == cudaSuccess) e = alloc(&c->bs_work, (size_t)GENGA_BS_FIELDS * c->bs_slots);
     if (e == cudaSuccess) e = cudaMemset(c->grp, 0xff, sizeof(int32_t) * (size_t)np);
@@ -838,7 +841,7 @@ genga_status genga_compact(genga_ctx *c, genga_system *sys, int32_t *id, void *s
 
 genga_status genga_tune_levels(genga_ctx *c, const genga_system *sys, const genga_params *p, const int32_t *n_levels,
                                const int32_t *n_sub, int32_t ncand, int32_t trial_steps, int32_t *best, float *ms,
-                               void *stream) {
+                               int32_t *codes, void *stream) {
     genga_status st;
     if ((st = check_system(c, sys)) != GENGA_OK) return st;
     if ((st = check_params(p)) != GENGA_OK) return st;
@@ -854,7 +857,12 @@ genga_status genga_tune_levels(genga_ctx *c, const genga_system *sys, const geng
     const size_t N = (size_t)sys->N, nf = sys->radius ? 8 : 7;
     double *copy = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaMalloc((void **)&copy, sizeof(double) * (N > 0 ? nf * N : 1));
+    // the caller's status bits are kept aside; each trial's bits are read and cleared
+    uint32_t bits_before = 0, bits_failed = 0;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&bits_before, c->status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&copy, sizeof(double) * (N > 0 ? nf * N : 1));
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const double *src[8] = {sys->x, sys->y, sys->z, sys->vx, sys->vy, sys->vz, sys->m, sys->radius};
@@ -865,7 +873,9 @@ genga_status genga_tune_levels(genga_ctx *c, const genga_system *sys, const geng
         for (size_t f = 0; f < nf && e == cudaSuccess; f++)
             e = cudaMemcpyAsync(*dst[f], src[f], sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
     };
-    float best_ms = 0.0f;
+    float best_ms = 0.0f, fastest_ms = 0.0f;
+    int fastest = 0;
+    bool any_ok = false;
     *best = 0;
     for (int k = 0; k < ncand && e == cudaSuccess && st == GENGA_OK; k++) {
         genga_params q = *p;
@@ -882,11 +892,27 @@ genga_status genga_tune_levels(genga_ctx *c, const genga_system *sys, const geng
         if (e == cudaSuccess) e = cudaEventElapsedTime(&t_ms, e0, e1);
         t_ms /= (float)trial_steps;
         if (ms) ms[k] = t_ms;
-        if (k == 0 || t_ms < best_ms) {
+        uint32_t bits = 0;  // this candidate's status: a candidate that raised one is not chosen
+        if (e == cudaSuccess) e = cudaMemcpy(&bits, c->status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(uint32_t));
+        int code = 0;
+        for (int b = 1; b <= 7 && !code; b++)
+            if (bits & GENGA_BIT(b)) code = b;
+        if (codes) codes[k] = code;
+        bits_failed |= bits;
+        if (k == 0 || t_ms < fastest_ms) {
+            fastest_ms = t_ms;
+            fastest = k;
+        }
+        if (!code && (!any_ok || t_ms < best_ms)) {
             best_ms = t_ms;
             *best = k;
+            any_ok = true;
         }
     }
+    if (!any_ok) *best = fastest;  // every candidate raised a status: the fastest, and its bits stay raised
+    const uint32_t restore = bits_before | (any_ok ? 0u : bits_failed);
+    if (e == cudaSuccess) e = cudaMemcpy(c->status, &restore, sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (copy) {

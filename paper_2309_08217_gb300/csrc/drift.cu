@@ -111,6 +111,7 @@ LevelSet base_set(genga_ctx *c) {
     l.gsize = c->gsize;
     l.gcur = c->gcur;
     l.gcount = c->gcount;
+    l.gof = c->gof;
     l.pairs = c->enc;
     l.pair_count = c->enc_count;
     l.pair_cap = c->enc_cap;
@@ -190,6 +191,7 @@ LevelArgs level_args(genga_system &sys, const genga_params &p, genga_ctx *c, con
     a.gsize = l.gsize;
     a.gmem = l.gmem;
     a.gbody = l.gbody;
+    a.gof = l.gof;
     a.grp = l.grp;
     a.gmark = l.gmark;
     a.next_grp = next.grp;
@@ -218,7 +220,7 @@ cudaError_t run_level(genga_system &sys, const genga_params &p, genga_ctx *c, in
     const LevelSet &next = c->lv[level - 1];
     const LevelArgs a = level_args(sys, p, c, l, next, level);
     const double h = T / p.n_sub;
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = launch_level_sort(a, c->sm_count, s);
     for (int k = 0; k < p.n_sub && e == cudaSuccess; k++) {
         e = launch_level_kick(a, 0.5 * h, c->sm_count, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(next.pair_count, 0, 2 * sizeof(int32_t), s);
@@ -248,10 +250,10 @@ cudaError_t launch_level1(genga_system &sys, const genga_params &p, double dt, g
 // Kernels one drift launches for the close-encounter levels beyond the
 // grouping kernel: the Bulirsch-Stoer kernel, or with L levels of s
 // sub-steps, per level-l sub-step kick, scan, groups, drift, the level below
-// and kick, and one clear per level.
+// and kick, and one sort and one clear per level.
 int level_launches(int n_levels, int n_sub) {
     int below = 1;  // the Bulirsch-Stoer kernel
-    for (int l = n_levels; l >= 1; l--) below = n_sub * (5 + below) + 1;
+    for (int l = n_levels; l >= 1; l--) below = n_sub * (5 + below) + 2;
     return below;
 }
 

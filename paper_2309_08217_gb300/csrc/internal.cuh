@@ -64,6 +64,7 @@ namespace genga {
 struct LevelSet {
     int32_t *grp, *gmark, *gslot;               // [npad_max]
     int32_t *gbody, *gmem, *gstart, *gsize, *gcur;  // [bs_slots]
+    int32_t *gof;                               // [bs_slots] group of each member slot (levels.cu)
     int32_t *gcount;                            // [1]
     int2 *pairs;                                // [pair_cap] pairs of the level above inside this level's radius
     int32_t *pair_count;                        // [2]: pairs, 0 (the grouping kernel's second list)
@@ -130,6 +131,7 @@ struct genga_ctx {
     int32_t *gmem;             // [bs_slots] members grouped
     int32_t *gstart, *gsize, *gcur;  // [bs_slots] per group: first slot, members, placement cursor
     int32_t *gcount;           // [1] number of groups
+    int32_t *gof;              // [bs_slots] group of each member slot (intermediate levels)
     int32_t *bs_tp;            // [bs_slots] member is a test particle (mode 2)
     double *bs_work;           // [GENGA_BS_FIELDS * bs_slots] level-1 integration state
     // intermediate levels (levels.cu): groups of level 2 .. GENGA_MAX_LEVELS + 1, allocated on
@@ -250,7 +252,8 @@ struct LevelArgs {              // one intermediate level (levels.cu): its group
     const double *a_osc, *rc_eq1;
     const float4 *lo;
     const int32_t *gcount, *gstart, *gsize, *gmem;
-    int32_t *gbody;             // members sorted by body index per group (written by the kick)
+    int32_t *gbody;             // members sorted by body index per group (written by the sort)
+    int32_t *gof;               // group of each member slot (written by the sort)
     int32_t *grp, *gmark;       // this level's marks (cleared at the end of the level)
     const int32_t *next_grp;    // the next level's labels (members with one move there)
     int2 *next_pairs;           // the next level's pair list
@@ -266,6 +269,7 @@ struct LevelArgs {              // one intermediate level (levels.cu): its group
 };
 
 int level_launches(int n_levels, int n_sub);
+cudaError_t launch_level_sort(const LevelArgs &a, int sm_count, cudaStream_t s);
 cudaError_t launch_level_kick(const LevelArgs &a, double tau, int sm_count, cudaStream_t s);
 cudaError_t launch_level_scan(const LevelArgs &a, double h, int sm_count, cudaStream_t s);
 cudaError_t launch_level_drift(const LevelArgs &a, double h, int sm_count, cudaStream_t s);

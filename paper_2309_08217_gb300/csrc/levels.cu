@@ -21,9 +21,12 @@
 //   kick(h/2)
 // The host issues these launches level by level (all groups of a level share
 // the time grid), so a step's launch count grows with s^L; the whole
-// sequence is part of the captured step graph.  One warp per group in every
-// kernel here; FP64 throughout (Sect. 1: close-encounter forces in double
-// precision).  The subgroup decision is taken with correctly rounded
+// sequence is part of the captured step graph.  The kick and the scan run
+// one warp per member (lanes over its partners), so a large group spreads
+// over many FP64 pipes (on GB300 one FP64 warp instruction holds an SMSP's
+// pipe ~64 cycles whatever the active lanes); the sort, drift and clear one
+// warp per group.  FP64 throughout (Sect. 1: close-encounter forces in
+// double precision).  The subgroup decision is taken with correctly rounded
 // operations as written (no contraction), the oracle's arithmetic.
 #include "changeover.cuh"
 #include "kepler.cuh"
@@ -59,10 +62,9 @@ __device__ __forceinline__ double pair_rc(const LevelArgs &a, const Body &i, con
 }
 
 // The members of every group sorted by body index into gbody (the order of
-// every sum), then kick(tau) of each member by the level's share of the
-// other members' pair forces.  Positions are only read, so the members'
-// velocities are updated in place.
-__global__ void __launch_bounds__(32 * LV_WARPS) level_kick_kernel(const __grid_constant__ LevelArgs a, double tau) {
+// every sum) and the group of every member slot into gof; once per level,
+// after the grouping kernel formed it.  One warp per group.
+__global__ void __launch_bounds__(32 * LV_WARPS) level_sort_kernel(const __grid_constant__ LevelArgs a) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * LV_WARPS + (threadIdx.x >> 5), nw = gridDim.x * LV_WARPS;
     const int ng = *a.gcount;
@@ -73,54 +75,85 @@ __global__ void __launch_bounds__(32 * LV_WARPS) level_kick_kernel(const __grid_
             int rank = 0;
             for (int r = 0; r < n; r++) rank += (a.gmem[s0 + r] < v) ? 1 : 0;
             a.gbody[s0 + rank] = v;
+            a.gof[s0 + q] = g;
         }
-        __syncwarp();
-        for (int q = lane; q < n; q += 32) {
-            const int vi = a.gbody[s0 + q];
-            const Body bi = body(a, vi);
-            if (signbit(bi.m)) continue;  // a ghost: no level force
-            const double xi = a.x[vi], yi = a.y[vi], zi = a.z[vi];
-            double ax = 0.0, ay = 0.0, az = 0.0;
-            for (int t = 0; t < n; t++) {
-                if (t == q) continue;
-                const int vj = a.gbody[s0 + t];
-                const Body bj = body(a, vj);
-                if (signbit(bj.m) || (bi.tp && bj.tp)) continue;
-                const double dx = a.x[vj] - xi, dy = a.y[vj] - yi, dz = a.z[vj] - zi;
-                const double q2 = dx * dx + dy * dy + dz * dz;
-                if (q2 == 0.0) continue;
-                const double rc = pair_rc(a, bi, bj);
-                if (q2 >= rc * rc) continue;  // outside r_crit,0 the step's kick has it all
-                const double iq = rsqrt_fp64(q2);
-                const double w = level_kick_weight(q2 * iq, 1.0 / (0.9 * rc), a.level, a.nsub, a.changeover);
-                const double f = a.G * bj.m * w * (iq * iq * iq);
-                ax = fma(f, dx, ax);
-                ay = fma(f, dy, ay);
-                az = fma(f, dz, az);
-            }
+    }
+}
+
+// Member slots of all groups: the groups are stored one after another.
+__device__ __forceinline__ int member_slots(const LevelArgs &a) {
+    const int ng = *a.gcount;
+    return ng > 0 ? a.gstart[ng - 1] + a.gsize[ng - 1] : 0;
+}
+
+// Warp sum in a fixed butterfly order (every lane ends with the same value).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// kick(tau) of every member by the level's share of the other members' pair
+// forces: one warp per member (a group of n members occupies n warps, so a
+// large group spreads over the SMs' FP64 pipes), lanes over its partners in
+// body order, a fixed-order warp sum.  Positions are only read, so the
+// members' velocities are updated in place.
+__global__ void __launch_bounds__(32 * LV_WARPS) level_kick_kernel(const __grid_constant__ LevelArgs a, double tau) {
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * LV_WARPS + (threadIdx.x >> 5), nw = gridDim.x * LV_WARPS;
+    const int ns = member_slots(a);
+    for (int item = gw; item < ns; item += nw) {
+        const int g = a.gof[item], s0 = a.gstart[g], n = a.gsize[g];
+        const int vi = a.gbody[item];
+        const Body bi = body(a, vi);
+        if (signbit(bi.m)) continue;  // a ghost: no level force (warp-uniform)
+        const double xi = a.x[vi], yi = a.y[vi], zi = a.z[vi];
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        for (int t = lane; t < n; t += 32) {
+            const int vj = a.gbody[s0 + t];
+            if (vj == vi) continue;
+            const Body bj = body(a, vj);
+            if (signbit(bj.m) || (bi.tp && bj.tp)) continue;
+            const double dx = a.x[vj] - xi, dy = a.y[vj] - yi, dz = a.z[vj] - zi;
+            const double q2 = dx * dx + dy * dy + dz * dz;
+            if (q2 == 0.0) continue;
+            const double rc = pair_rc(a, bi, bj);
+            if (q2 >= rc * rc) continue;  // outside r_crit,0 the step's kick has it all
+            const double iq = rsqrt_fp64(q2);
+            const double w = level_kick_weight(q2 * iq, 1.0 / (0.9 * rc), a.level, a.nsub, a.changeover);
+            const double f = a.G * bj.m * w * (iq * iq * iq);
+            ax = fma(f, dx, ax);
+            ay = fma(f, dy, ay);
+            az = fma(f, dz, az);
+        }
+        ax = warp_sum(ax);
+        ay = warp_sum(ay);
+        az = warp_sum(az);
+        if (lane == 0) {
             a.vx[vi] = fma(tau, ax, a.vx[vi]);
             a.vy[vi] = fma(tau, ay, a.vy[vi]);
             a.vz[vi] = fma(tau, az, a.vz[vi]);
         }
-        __syncwarp();
     }
 }
 
 // The member pairs of every group that form the next level's subgroups for a
-// drift of h (list appended; its count was zeroed before the launch).
+// drift of h (list appended; its count was zeroed before the launch): one
+// warp per member i, lanes over its partners j after it in body order.
 __global__ void __launch_bounds__(32 * LV_WARPS) level_scan_kernel(const __grid_constant__ LevelArgs a, double h) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * LV_WARPS + (threadIdx.x >> 5), nw = gridDim.x * LV_WARPS;
-    const int ng = *a.gcount;
+    const int ns = member_slots(a);
     const double tlo = h < 0.0 ? h : 0.0, thi = h < 0.0 ? 0.0 : h;
-    for (int g = gw; g < ng; g += nw) {
-        const int s0 = a.gstart[g], n = a.gsize[g];
-        for (long long idx = lane; idx < (long long)n * n; idx += 32) {
-            const int i = (int)(idx / n), j = (int)(idx % n);
-            if (j <= i) continue;
-            const int vi = a.gbody[s0 + i], vj = a.gbody[s0 + j];
-            const Body bi = body(a, vi), bj = body(a, vj);
-            if (signbit(bi.m) || signbit(bj.m) || (bi.tp && bj.tp)) continue;
+    for (int item = gw; item < ns; item += nw) {
+        const int g = a.gof[item], s0 = a.gstart[g], n = a.gsize[g];
+        const int vi = a.gbody[item];
+        const Body bi = body(a, vi);
+        if (signbit(bi.m)) continue;
+        for (int t = item - s0 + 1 + lane; t < n; t += 32) {
+            const int vj = a.gbody[s0 + t];
+            const Body bj = body(a, vj);
+            if (signbit(bj.m) || (bi.tp && bj.tp)) continue;
             const double dx = __dsub_rn(a.x[vj], a.x[vi]), dy = __dsub_rn(a.y[vj], a.y[vi]);
             const double dz = __dsub_rn(a.z[vj], a.z[vi]);
             const double q2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
@@ -132,11 +165,11 @@ __global__ void __launch_bounds__(32 * LV_WARPS) level_scan_kernel(const __grid_
                 const double uz = __dsub_rn(a.vz[vj], a.vz[vi]);
                 const double uu = __dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
                 const double du = __dadd_rn(__dadd_rn(__dmul_rn(dx, ux), __dmul_rn(dy, uy)), __dmul_rn(dz, uz));
-                double t = uu > 0.0 ? __ddiv_rn(-du, uu) : 0.0;
-                t = t < tlo ? tlo : t;
-                t = t > thi ? thi : t;
-                const double px = __dadd_rn(dx, __dmul_rn(ux, t)), py = __dadd_rn(dy, __dmul_rn(uy, t));
-                const double pz = __dadd_rn(dz, __dmul_rn(uz, t));
+                double t_c = uu > 0.0 ? __ddiv_rn(-du, uu) : 0.0;
+                t_c = t_c < tlo ? tlo : t_c;
+                t_c = t_c > thi ? thi : t_c;
+                const double px = __dadd_rn(dx, __dmul_rn(ux, t_c)), py = __dadd_rn(dy, __dmul_rn(uy, t_c));
+                const double pz = __dadd_rn(dz, __dmul_rn(uz, t_c));
                 in = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz)) < rcl2;
             }
             if (!in) continue;
@@ -183,6 +216,11 @@ __global__ void __launch_bounds__(32 * LV_WARPS) level_clear_kernel(const __grid
 }
 
 }  // namespace
+
+cudaError_t launch_level_sort(const LevelArgs &a, int sm_count, cudaStream_t s) {
+    level_sort_kernel<<<2 * sm_count, 32 * LV_WARPS, 0, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_level_kick(const LevelArgs &a, double tau, int sm_count, cudaStream_t s) {
     level_kick_kernel<<<2 * sm_count, 32 * LV_WARPS, 0, s>>>(a, tau);

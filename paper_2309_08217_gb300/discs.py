@@ -19,6 +19,7 @@ use, so these seeded discs stand in for them; shapes follow Sect. 2):
 * ``embryo_disc``   -- a few embryos plus many planetesimals
 * ``giants_disc``   -- four giant planets plus an outer planetesimal belt
 * ``batch_of_discs``-- many independent discs of log-uniform size
+* ``planet_swarm``  -- a planet with a dense swarm around it inside a disc
 """
 from __future__ import annotations
 
@@ -214,6 +215,39 @@ def batch_of_discs(D=256, seed=4, n_lo=1000, n_hi=16000) -> List[Disc]:
 
 
 # Named workloads (sizes and recipes as stated in the design notes).
+def planet_swarm(n_disc=4000, n_swarm=80, seed=6, m_planet=10 * M_EARTH, r_lo=0.01, r_hi=0.05,
+                 sigma_v=3e-4) -> Disc:
+    """A planet on a circular orbit at 1 au (body 0) with n_swarm planetesimals
+    placed 0.01-0.05 au from it in random directions, moving with the planet
+    plus a Gaussian velocity dispersion sigma_v (au/day), followed by a
+    uniform disc of n_disc planetesimals on 0.7-3 au: one dense
+    close-encounter group of a protoplanet and its feeding zone (Sect. 2's
+    embryo runs) inside an ordinary disc."""
+    d = disc_uniform(n_disc, seed)
+    rng = np.random.default_rng(seed + 1000)
+    n = 1 + n_swarm + n_disc
+    arr = [np.zeros(n) for _ in range(7)]
+    pos = np.array([1.0, 0.0, 0.0])
+    vel = np.array([0.0, np.sqrt(G_GAUSS * (1.0 + m_planet)), 0.0])
+    for c in range(3):
+        arr[c][0] = pos[c]
+        arr[3 + c][0] = vel[c]
+    arr[6][0] = m_planet
+    m_pl = d.m[0]
+    for k in range(1, n_swarm + 1):
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        r = rng.uniform(r_lo, r_hi)
+        for c in range(3):
+            arr[c][k] = pos[c] + r * u[c]
+            arr[3 + c][k] = vel[c] + sigma_v * rng.normal()
+        arr[6][k] = m_pl
+    for c, src in enumerate(d.arrays()):
+        arr[c][1 + n_swarm:] = src
+    return Disc(f"swarm-N{n}-s{seed}", *arr, Mstar=1.0, G=G_GAUSS, dt=6.0,
+                meta={"seed": seed, "kind": "planet_swarm", "n_swarm": n_swarm})
+
+
 def workload(name: str):
     if name == "disc2048":        # 2,048 planetesimals, 0.7-3.0 au, 2.5 Earth masses
         return disc_uniform(2048, 1)
@@ -225,4 +259,6 @@ def workload(name: str):
         return batch_of_discs(256, 4)
     if name == "giants100k":      # 4 giants + 100,000 planetesimals
         return giants_disc(100_000, 5)
+    if name == "swarm4k":         # a 10 Earth-mass planet with 80 planetesimals around it + 4,000
+        return planet_swarm(4000, 80, 6)
     raise KeyError(name)

@@ -164,3 +164,26 @@ def test_tune_levels_times_candidates_without_touching_the_state(genga, ctx):
     assert _rel_state(st.numpy(), _oracle_step(d, 2, best[0], best[1])) < 1e-9
     with pytest.raises(genga.GengaError):
         genga.genga_tune_levels(ctx, st, p, [(1, 2), (4, 2)], 2)
+
+
+def test_tune_levels_skips_candidates_that_raise_a_status(genga, ctx):
+    # every trial meets the head-on singularity (no radii): a forced sub-step in
+    # each candidate, so the fastest comes back and the status stays raised
+    d = planted_disc(800, 17)
+    st = genga.DeviceSystem.from_disc(d)
+    p = _params(genga, d, 1, 0, 2)
+    codes = []
+    best, ms = genga.genga_tune_levels(ctx, st, p, [(0, 2), (1, 2)], 3, codes=codes)
+    assert len(codes) == 2 and all(k != genga.GENGA_OK for k in codes) and genga.GENGA_ERR_BS in codes
+    assert ms[[(0, 2), (1, 2)].index(best)] == min(ms)
+    assert genga.genga_get_status(ctx) != genga.GENGA_OK
+    # a dense swarm: a candidate whose trial raised a status is never the one chosen
+    dsw = discs.workload("swarm4k")
+    c = genga.Context(dsw.N)
+    ssw = genga.DeviceSystem.from_disc(dsw)
+    codes = []
+    cand = [(0, 2), (2, 4)]
+    best, ms = genga.genga_tune_levels(c, ssw, _params(genga, dsw, 1, 0, 2), cand, 4, codes=codes)
+    assert codes[1] == 0 and codes[cand.index(best)] == 0
+    assert genga.genga_get_status(c) == genga.GENGA_OK
+    c.close()
