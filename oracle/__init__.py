@@ -88,6 +88,8 @@ def _load():
             "oracle_ml_weight": ([d, d, i, i, i, i], d),
             "oracle_ml_group": ([i, _i32p] + [_dp] * 10 + [_i32p, d, d, d, i, i, i, d, d, i, i, i,
                                                              C.POINTER(C.c_int), C.POINTER(C.c_int)], i),
+            "oracle_drift_groups_ml": ([i] + [_dp] * 10 + [_i32p, C.c_int64, _i32p, d, d, d, i, i, i, d, d, i, d, d,
+                                                         i, i, C.POINTER(C.c_int), C.POINTER(C.c_int)], i),
             "oracle_step_ml": ([i] + [_dp] * 8 + [_i32p] + [d] * 5 + [i, i, i, i, d, d, d, i, i, i,
                                                                       C.POINTER(C.c_int), C.POINTER(C.c_int)], i),
         }
@@ -342,14 +344,22 @@ def ml_group(arrs, members, a, rc, G, Mstar, n1, mode, form, dt, tol, n_levels, 
     return f, bad.value
 
 
-def drift_groups(arrs, a, rc, pairs, G, Mstar, n1, mode, form, dt, tol, n_big=-1, max_iter=50):
+def drift_groups(arrs, a, rc, pairs, G, Mstar, n1, mode, form, dt, tol, n_big=-1, max_iter=50, n_levels=0,
+                 n_sub=2):
     """HC(dt/2); Kepler for bodies outside the groups of `pairs`, the
-    Bulirsch-Stoer level for each group; HC(dt/2).  In place; returns
-    (Kepler cap count, groups with a forced acceptance)."""
+    Bulirsch-Stoer level for each group (below n_levels intermediate levels of
+    n_sub sub-steps); HC(dt/2).  In place; returns (Kepler cap count, groups
+    with a forced acceptance)."""
     x, y, z, vx, vy, vz, m = arrs
     pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
     a, rc = _f64(a), _f64(rc)
     f = C.c_int(0)
+    if n_levels > 0:
+        bad = int(_load().oracle_drift_groups_ml(len(m), *map(_p, (x, y, z, vx, vy, vz, m, a, rc)), None, None,
+                                                 len(pairs), pairs.ctypes.data_as(_i32p), G, Mstar, n1, int(mode),
+                                                 int(form), int(n_big), float(dt), float(tol), int(max_iter), 0.0, 0.0,
+                                                 int(n_levels), int(n_sub), C.byref(f), None))
+        return bad, f.value
     bad = int(_load().oracle_drift_groups(len(m), *map(_p, (x, y, z, vx, vy, vz, m, a, rc)),
                                           len(pairs), pairs.ctypes.data_as(_i32p), G, Mstar, n1,
                                           int(mode), int(form), int(n_big), float(dt), float(tol),

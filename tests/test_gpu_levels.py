@@ -187,3 +187,37 @@ def test_tune_levels_skips_candidates_that_raise_a_status(genga, ctx):
     assert codes[1] == 0 and codes[cand.index(best)] == 0
     assert genga.genga_get_status(c) == genga.GENGA_OK
     c.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-9)])
+def test_swarm4k_parity(genga, precision, tol):
+    """The benchmark's dense case: a planet with 80 planetesimals around it in
+    a 4,000-body disc (one 85-member group), 2 levels of 4 sub-steps, 2 steps."""
+    d = discs.workload("swarm4k")
+    c = genga.Context(d.N)
+    st = genga.DeviceSystem.from_disc(d)
+    genga.genga_step(c, st, _params(genga, d, precision, 2, 4), 2)
+    assert genga.genga_get_status(c) == genga.GENGA_OK
+    assert _rel_state(st.numpy(), _oracle_step(d, 2, 2, 4)) < tol
+    c.close()
+
+
+@pytest.mark.parametrize("L,s", [(1, 3), (2, 2)])
+def test_kick_then_drift_parity(genga, ctx, L, s):
+    """genga_kick then genga_drift with levels against the oracle's kick and
+    drift of the groups of the kick's pairs and predicted entries."""
+    d = orbiting_pairs_disc(800, 17)
+    st = genga.DeviceSystem.from_disc(d)
+    p = _params(genga, d, 0, L, s)
+    genga.genga_kick(ctx, st, p, 0.5 * d.dt)
+    genga.genga_drift(ctx, st, p, d.dt)
+    assert genga.genga_get_status(ctx) == genga.GENGA_OK
+    arr = oracle.disc_arrays(d)
+    a, rc = oracle.rcrit(*arr, G=d.G, Mstar=d.Mstar, dt=d.dt)
+    pairs, _ = oracle.encounters(arr[0], arr[1], arr[2], arr[6], a, rc, 3.0, d.Mstar, 1)
+    pred = oracle.predicted_pairs(arr, a, rc, 3.0, d.Mstar, 1, d.dt)
+    oracle.kick(arr, d.G, d.Mstar, d.dt, 3.0, 0.4, 1, 0, 0.5 * d.dt)
+    bad, forced = oracle.drift_groups(arr, a, rc, np.concatenate([pairs, pred]), d.G, d.Mstar, 3.0, 1, 0, d.dt,
+                                      TOL_BS, n_levels=L, n_sub=s)
+    assert bad == 0 and forced == 0
+    assert _rel_state(st.numpy(), arr) < 1e-10
