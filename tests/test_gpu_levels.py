@@ -221,3 +221,31 @@ def test_kick_then_drift_parity(genga, ctx, L, s):
                                       TOL_BS, n_levels=L, n_sub=s)
     assert bad == 0 and forced == 0
     assert _rel_state(st.numpy(), arr) < 1e-10
+
+
+def test_disc40k_drift_with_levels(genga):
+    """The 40,000-body benchmark disc in the benchmark's launch configuration:
+    an FP32 kick of length 0 (the pair lists of the state, velocities
+    unchanged), then the drift with 2 levels of 3 sub-steps, against the
+    oracle's lists and level drift of the same state -- every body."""
+    d = discs.workload("disc40k")
+    c = genga.Context(d.N)
+    st = genga.DeviceSystem.from_disc(d)
+    p = _params(genga, d, 1, 2, 3)
+    genga.genga_kick(c, st, p, 0.0)
+    genga.genga_drift(c, st, p, d.dt)
+    assert genga.genga_get_status(c) == genga.GENGA_OK
+    c.close()
+    arr = oracle.disc_arrays(d)
+    a, rc = oracle.rcrit(*arr, G=d.G, Mstar=d.Mstar, dt=d.dt)
+    pairs, _ = oracle.encounters(arr[0], arr[1], arr[2], arr[6], a, rc, 3.0, d.Mstar, 1)
+    pred = oracle.predicted_pairs(arr, a, rc, 3.0, d.Mstar, 1, d.dt)
+    assert len(pairs) > 50
+    bad, forced = oracle.drift_groups(arr, a, rc, np.concatenate([pairs, pred]), d.G, d.Mstar, 3.0, 1, 0, d.dt,
+                                      TOL_BS, n_levels=2, n_sub=3)
+    assert bad == 0 and forced == 0
+    got = st.numpy()
+    members = np.unique(np.concatenate([pairs, pred]).ravel())
+    others = np.setdiff1d(np.arange(d.N), members)
+    assert _rel_state(got, arr, others) < 1e-12
+    assert _rel_state(got, arr, members) < 1e-10
