@@ -445,6 +445,13 @@ cudaError_t ensure_levels(genga_ctx *c, int L) {
         if (e == cudaSuccess) e = cudaMemset(l.gcount, 0, sizeof(int32_t));
         if (e == cudaSuccess) e = cudaMemset(l.pair_count, 0, 2 * sizeof(int32_t));
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {  // a set is complete or absent, never half allocated
+            void *lb[] = {l.grp,  l.gmark,  l.gslot, l.gbody, l.gmem,      l.gstart,
+                          l.gsize, l.gcur,  l.gof,   l.gcount, l.pairs, l.pair_count};
+            for (void *b : lb)
+                if (b) cudaFree(b);
+            l = LevelSet{};
+        }
     }
     return e;
 }
