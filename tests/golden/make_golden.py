@@ -3,9 +3,10 @@
 The fixture is a 24-body disc (seed 24) with three planted close pairs:
 one at ~0.5 r_crit (changeover region), one at ~0.05 r_crit (K = 0) and
 one just outside r_crit.  It stores the oracle's critical radii, kick
-accelerations, encounter pairs and the state after one level-0 step and
-after one step with the close-encounter level, so a later change of the
-oracle's arithmetic shows up as a diff of this file.
+accelerations, encounter pairs and the state after one level-0 step, after
+one step with the close-encounter level and after one step with two
+intermediate levels of three sub-steps above it (Sect. 1), so a later
+change of the oracle's arithmetic shows up as a diff of this file.
 
 Run:  python tests/golden/make_golden.py
 """
@@ -61,6 +62,13 @@ def main():
     out["kepler_failures_bs"] = oracle.step(st, G, M, d.dt, 3.0, 0.4, 1, 0, 1, bs_tol=1e-12, forced=forced)
     out["bs_forced"] = forced[0]
     out["after_one_step_bs_mode1_form0"] = [v.tolist() for v in st]
+    # the same step with 2 intermediate levels of 3 sub-steps above Bulirsch-Stoer
+    st = [np.array(v) for v in out["state"]]
+    forced = [0]
+    out["kepler_failures_levels"] = oracle.step(st, G, M, d.dt, 3.0, 0.4, 1, 0, 1, bs_tol=1e-12, forced=forced,
+                                                n_levels=2, n_sub=3)
+    out["levels_forced"] = forced[0]
+    out["after_one_step_levels2_3_mode1_form0"] = [v.tolist() for v in st]
     out["energy"] = oracle.energy([np.array(v) for v in out["state"]], G, M).tolist()
     with open(os.path.join(HERE, "oracle_disc24.json"), "w") as f:
         json.dump(out, f, indent=1)

@@ -49,3 +49,13 @@ def test_oracle_reproduces_stored_fixture():
     moved = [np.abs(np.array(u) - np.array(w)).max()
              for u, w in zip(g["after_one_step_bs_mode1_form0"], g["after_one_step_mode1_form0"])]
     assert max(moved) > 1e-9          # the level changes the planted pairs' motion
+    # with 2 intermediate levels of 3 sub-steps (Sect. 1's hierarchy)
+    st = [np.array(v) for v in g["state"]]
+    forced = [0]
+    assert oracle.step(st, G, M, dt, 3.0, 0.4, 1, 0, 1, bs_tol=1e-12, forced=forced, n_levels=2, n_sub=3) == 0
+    assert forced[0] == 0 == g["levels_forced"]
+    for v, w in zip(st, g["after_one_step_levels2_3_mode1_form0"]):
+        assert np.allclose(v, np.array(w), rtol=1e-12, atol=1e-18)
+    moved = [np.abs(np.array(u) - np.array(w)).max()
+             for u, w in zip(g["after_one_step_levels2_3_mode1_form0"], g["after_one_step_bs_mode1_form0"])]
+    assert max(moved) > 1e-12         # the pair at 0.5 r_crit is outside r_crit / 3: level-1 kicks instead
