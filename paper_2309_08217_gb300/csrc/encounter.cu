@@ -501,59 +501,62 @@ __device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, 
             zc[c] = fma(H, f0[c], y[c]);
             T[c] = 0.0;
         }
+        // The columns advance together and column kc is complete after stage
+        // n_kc = 2 (kc + 1): its Neville row is built then, and the first
+        // column kc >= 1 that meets the tolerance ends the stages (the later
+        // columns could not change that choice).  Lane 8 q + c (c < 6) holds
+        // component c of member q: the source lane of column kc sends each
+        // of its six components in turn.
+        const int c = k;
+        const bool item = act && c < 6;
+        const double isc = c < 3 ? isx : isv;
+        double row[BS_KMAX];
+        double pick = 0.0;  // T[kc][kc] of the last column built
+        int acc_col = -1;
         for (int m = 1; m <= 2 * BS_KMAX; m++) {  // every lane evaluates (the shuffles need all lanes)
             double ax, ay, az;
             accel(zc[0], zc[1], zc[2], ax, ay, az);
             const double fv[6] = {zc[3], zc[4], zc[5], ax, ay, az};
             if (m < nk) {
 #pragma unroll
-                for (int c = 0; c < 6; c++) {
-                    const double zn = fma(2.0 * H, fv[c], zp[c]);
-                    zp[c] = zc[c];
-                    zc[c] = zn;
+                for (int c6 = 0; c6 < 6; c6++) {
+                    const double zn = fma(2.0 * H, fv[c6], zp[c6]);
+                    zp[c6] = zc[c6];
+                    zc[c6] = zn;
                 }
             } else if (m == nk) {
 #pragma unroll
-                for (int c = 0; c < 6; c++) T[c] = 0.5 * (zc[c] + zp[c] + H * fv[c]);
+                for (int c6 = 0; c6 < 6; c6++) T[c6] = 0.5 * (zc[c6] + zp[c6] + H * fv[c6]);
             }
-        }
-        // lane 8 q + c (c < 6): component c of member q over the columns; the
-        // source lane of column kk sends each of its six components in turn
-        const int c = k;
-        double tk[BS_KMAX];
-#pragma unroll
-        for (int kk = 0; kk < BS_KMAX; kk++) {
-            tk[kk] = 0.0;
+            if (m & 1) continue;
+            const int kc = (m >> 1) - 1;  // warp-uniform
+            double cur = 0.0;
 #pragma unroll
             for (int cc = 0; cc < 6; cc++) {
-                const double t = shfl_d(T[cc], 8 * q + kk);
-                if (cc == c) tk[kk] = t;
+                const double t = shfl_d(T[cc], 8 * q + kc);
+                if (cc == c) cur = t;
             }
-        }
-        const bool item = act && c < 6;
-        const double isc = c < 3 ? isx : isv;
-        double row[BS_KMAX], diag[BS_KMAX], ek[BS_KMAX];
+            double dprev = 0.0;
 #pragma unroll
-        for (int kk = 0; kk < BS_KMAX; kk++) {
-            double cur = tk[kk], dprev = 0.0;
-#pragma unroll
-            for (int j = 1; j <= kk; j++) {
-                const double prev = row[j - 1];
-                row[j - 1] = cur;
+            for (int jn = 1; jn < BS_KMAX; jn++) {
+                if (jn > kc) break;
+                const double prev = row[jn - 1];  // T[kc-1][jn-1]
+                row[jn - 1] = cur;                // T[kc][jn-1]
                 dprev = cur;
-                cur = fma(cur - prev, c_neville.c[kk * BS_KMAX + j], cur);
+                cur = fma(cur - prev, c_neville.c[kc * BS_KMAX + jn], cur);
             }
-            row[kk] = cur;
-            diag[kk] = cur;
-            ek[kk] = (item && kk >= 1) ? fabs(cur - dprev) * isc : 0.0;
-        }
-        int acc_col = -1;
 #pragma unroll
-        for (int kk = 1; kk < BS_KMAX; kk++) {
-            const double e = warp_max_nonneg(ek[kk]);
-            if (acc_col < 0 && e <= a.tol) acc_col = kk;
+            for (int jj = 0; jj < BS_KMAX; jj++)
+                if (jj == kc) row[jj] = cur;
+            pick = cur;
+            if (kc == 0) continue;
+            const double e = warp_max_nonneg(item ? fabs(cur - dprev) * isc : 0.0);
+            if (e <= a.tol) {
+                acc_col = kc;
+                break;
+            }
         }
-        if (acc_col < 0 && frac <= BS_MIN_FRAC) {
+        if (acc_col < 0 && frac <= BS_MIN_FRAC) {  // pick holds the last column's T[7][7]
             acc_col = BS_KMAX - 1;
             forced = true;
         }
@@ -561,10 +564,6 @@ __device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, 
             frac *= 0.5;
             continue;
         }
-        double pick = diag[0];
-#pragma unroll
-        for (int kk = 1; kk < BS_KMAX; kk++)
-            if (kk == acc_col) pick = diag[kk];
 #pragma unroll
         for (int cc = 0; cc < 6; cc++) {
             const double nv = shfl_d(pick, 8 * q + cc);
