@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-tp2", action="store_true", help="skip the test-particle-mode-2 kicks on giants100k")
     ap.add_argument("--long-steps", type=int, default=1000,
                     help="length of the run whose mean step and pass times are reported (0: skip)")
+    ap.add_argument("--no-levels", action="store_true", help="skip the intermediate-levels object")
     ap.add_argument("--levels", default=None,
                     help="L:s -- time the disc40k steps of the 'levels' object with L intermediate levels of s "
                          "sub-steps instead of the tuned setting")
@@ -499,7 +500,7 @@ def run_genga(args):
     # ---- intermediate levels of the changeover: the self-tuning call over a
     # few (levels, sub-steps), then the chosen setting timed like level1
     levels = None
-    if args.bs_tol > 0:
+    if args.bs_tol > 0 and not args.no_levels:
         cand = [(0, 2), (1, 2), (1, 4), (2, 2), (2, 3)]
         st = g.DeviceSystem.from_disc(d, device=dev)
         p32_on = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=g.GENGA_FP32, bs_tol=args.bs_tol)
