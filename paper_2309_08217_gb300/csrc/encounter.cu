@@ -447,15 +447,30 @@ __device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, 
         ax = c * x;
         ay = c * yy;
         az = c * z;
+        // member q's partners in ascending order: the jn-th is p = jn + (jn >= q).
+        // One pass of the pair term per partner slot (n - 1 passes) instead of one
+        // per member with the lanes of that member masked off (n passes: on this
+        // GPU an FP64 warp instruction costs the same whatever lanes are active)
 #pragma unroll
-        for (int p = 0; p < 4; p++) {
-            if (!use[p]) continue;
-            const double dx = px[p] - x, dy = py[p] - yy, dz = pz[p] - z;
+        for (int jn = 0; jn < 3; jn++) {
+            if (jn >= n - 1) break;  // warp-uniform
+            const int p = jn + (jn >= q ? 1 : 0);
+            double sx = px[0], sy = py[0], sz = pz[0], gp = gm[0], r2p = rc2[0], l2p = lo2[0], i9p = inv9[0];
+            bool up = use[0];
+#pragma unroll
+            for (int pp = 1; pp < 4; pp++)
+                if (p == pp) {
+                    sx = px[pp]; sy = py[pp]; sz = pz[pp];
+                    gp = gm[pp]; r2p = rc2[pp]; l2p = lo2[pp]; i9p = inv9[pp];
+                    up = use[pp];
+                }
+            if (!up) continue;
+            const double dx = sx - x, dy = sy - yy, dz = sz - z;
             const double q2 = dx * dx + dy * dy + dz * dz;
-            if (__double_as_longlong(q2) == 0 || ge_nonneg(q2, rc2[p])) continue;  // coincident / K = 1
+            if (__double_as_longlong(q2) == 0 || ge_nonneg(q2, r2p)) continue;  // coincident / K = 1
             const double iq = rsqrt_fp64(q2);
-            const double w = ge_nonneg(lo2[p], q2) ? 1.0 : bs_weight(a, q2 * iq, inv9[p]);
-            const double f = gm[p] * w * (iq * iq * iq);
+            const double w = ge_nonneg(l2p, q2) ? 1.0 : bs_weight(a, q2 * iq, i9p);
+            const double f = gp * w * (iq * iq * iq);
             ax = fma(f, dx, ax);
             ay = fma(f, dy, ay);
             az = fma(f, dz, az);
