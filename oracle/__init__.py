@@ -86,6 +86,9 @@ def _load():
                                                                   C.POINTER(C.c_int)], i),
             "oracle_ml_radius": ([d, i, i], d),
             "oracle_ml_weight": ([d, d, i, i, i, i], d),
+            "oracle_ml_level_acc": ([i, _i32p] + [_dp] * 6 + [d, d, d, i, i, i, i, i, i, _dp], None),
+            "oracle_ml_subpairs": ([i, _i32p] + [_dp] * 9 + [d, d, i, i, i, i, d, _i32p, C.c_int64], C.c_int64),
+            "oracle_bs_acc_ml": ([i, _i32p] + [_dp] * 6 + [d, d, d, i, i, i, i, i, _dp], None),
             "oracle_ml_group": ([i, _i32p] + [_dp] * 10 + [_i32p, d, d, d, i, i, i, d, d, i, i, i,
                                                              C.POINTER(C.c_int), C.POINTER(C.c_int)], i),
             "oracle_drift_groups_ml": ([i] + [_dp] * 10 + [_i32p, C.c_int64, _i32p, d, d, d, i, i, i, d, d, i, d, d,
@@ -323,6 +326,39 @@ def ml_weight(q, rc, level, n_levels, n_sub, form):
     `level` applies: K_l prod_{k<l}(1 - K_k) for level <= n_levels, the
     Bulirsch-Stoer share prod_{k<=n_levels}(1 - K_k) for level = n_levels + 1."""
     return float(_load().oracle_ml_weight(float(q), float(rc), int(level), int(n_levels), int(n_sub), int(form)))
+
+
+def ml_level_acc(x, y, z, m, a, rc, members, G, Mstar, n1, mode, form, level, n_levels, n_sub, n_big=-1):
+    """Level `level`'s share of the pair forces on each member (no central
+    term), shape (3, n)."""
+    mem = np.ascontiguousarray(np.asarray(members, dtype=np.int32))
+    acc = np.zeros(3 * max(len(mem), 1))
+    _load().oracle_ml_level_acc(len(mem), mem.ctypes.data_as(_i32p), *map(_p, [_f64(v) for v in (x, y, z, m, a, rc)]),
+                                G, Mstar, n1, int(mode), int(form), int(n_big), int(level), int(n_levels), int(n_sub),
+                                _p(acc))
+    return acc[: 3 * len(mem)].reshape(-1, 3).T
+
+
+def bs_acc_ml(x, y, z, m, a, rc, members, G, Mstar, n1, mode, form, n_levels, n_sub, n_big=-1):
+    """The Bulirsch-Stoer level's acceleration of each member (central term
+    plus the share prod_{k<=L}(1 - K_k) of the pair forces), shape (3, n)."""
+    mem = np.ascontiguousarray(np.asarray(members, dtype=np.int32))
+    acc = np.zeros(3 * max(len(mem), 1))
+    _load().oracle_bs_acc_ml(len(mem), mem.ctypes.data_as(_i32p), *map(_p, [_f64(v) for v in (x, y, z, m, a, rc)]),
+                             G, Mstar, n1, int(mode), int(form), int(n_big), int(n_levels), int(n_sub), _p(acc))
+    return acc[: 3 * len(mem)].reshape(-1, 3).T
+
+
+def ml_subpairs(arrs, members, a, rc, n1, Mstar, mode, level, n_sub, h, n_big=-1):
+    """The member pairs that form the subgroups of level + 1 for a drift of h."""
+    x, y, z, vx, vy, vz, m = [_f64(v) for v in arrs]
+    mem = np.ascontiguousarray(np.asarray(members, dtype=np.int32))
+    cap = max(16, len(mem) * len(mem))
+    out = np.zeros(2 * cap, np.int32)
+    n = _load().oracle_ml_subpairs(len(mem), mem.ctypes.data_as(_i32p), *map(_p, (x, y, z, vx, vy, vz, m)),
+                                   *map(_p, (_f64(a), _f64(rc))), n1, Mstar, int(mode), int(n_big), int(level),
+                                   int(n_sub), float(h), out.ctypes.data_as(_i32p), cap)
+    return out[: 2 * n].reshape(-1, 2).copy()
 
 
 def ml_group(arrs, members, a, rc, G, Mstar, n1, mode, form, dt, tol, n_levels, n_sub, n_big=-1,

@@ -543,12 +543,13 @@ static void bs_deriv(const bs_group *g, const double *s, double *ds)
 }
 
 /* The level-1 acceleration of each member of a group (bs_deriv's velocity
- * half) at the given state: acc[3k + c] for member k. */
-void oracle_bs_acc(int n, const int32_t *mem, const double *x, const double *y, const double *z,
-                   const double *m, const double *a, const double *rc, double G, double Mstar,
-                   double n1, int mode, int form, int n_big, double *acc)
+ * half) at the given state: acc[3k + c] for member k; below nlev intermediate
+ * levels of nsub sub-steps (0, 1: none). */
+void oracle_bs_acc_ml(int n, const int32_t *mem, const double *x, const double *y, const double *z,
+                      const double *m, const double *a, const double *rc, double G, double Mstar,
+                      double n1, int mode, int form, int n_big, int nlev, int nsub, double *acc)
 {
-    bs_group g = {n, mem, m, a, rc, G, Mstar, n1, mode, form, n_big, NULL, 0, 1};
+    bs_group g = {n, mem, m, a, rc, G, Mstar, n1, mode, form, n_big, NULL, nlev, nsub};
     double *s = (double *)calloc((size_t)(6 * n > 0 ? 6 * n : 1), sizeof(double));
     double *ds = (double *)calloc((size_t)(6 * n > 0 ? 6 * n : 1), sizeof(double));
     for (int k = 0; k < n; k++) {
@@ -559,6 +560,13 @@ void oracle_bs_acc(int n, const int32_t *mem, const double *x, const double *y, 
         for (int c = 0; c < 3; c++) acc[3 * k + c] = ds[6 * k + 3 + c];
     free(s);
     free(ds);
+}
+
+void oracle_bs_acc(int n, const int32_t *mem, const double *x, const double *y, const double *z,
+                   const double *m, const double *a, const double *rc, double G, double Mstar,
+                   double n1, int mode, int form, int n_big, double *acc)
+{
+    oracle_bs_acc_ml(n, mem, x, y, z, m, a, rc, G, Mstar, n1, mode, form, n_big, 0, 1, acc);
 }
 
 /*
@@ -792,34 +800,42 @@ typedef struct {
     int forced, merges, bad;
 } ml_ctx;
 
-static double ml_pair_rc(const ml_ctx *c, int bi, int bj)
+/* The level-l share of the pair forces on each member of a group (ascending
+ * body indices), without the central term: acc[3k + c] for member k,
+ *   sum_{j in group} G m_j W_l(r_kj) (x_j - x_k) / r_kj^3
+ * (ghosts and pairs of two test particles excluded). */
+void oracle_ml_level_acc(int n, const int32_t *mem, const double *x, const double *y, const double *z,
+                         const double *m, const double *a, const double *rc, double G, double Mstar, double n1,
+                         int mode, int form, int n_big, int l, int L, int s, double *acc)
 {
-    return oracle_pair_rcrit(c->mode, c->m[bi], c->m[bj], c->a[bi], c->a[bj], c->rc[bi], c->rc[bj], c->n1,
-                             c->Mstar);
+    for (int i = 0; i < n; i++) {
+        int bi = mem[i];
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        if (!signbit(m[bi])) {
+            for (int j = 0; j < n; j++) {
+                int bj = mem[j];
+                if (j == i || signbit(m[bj]) || tp_pair(n_big, bi, bj)) continue;
+                double dx = x[bj] - x[bi], dy = y[bj] - y[bi], dz = z[bj] - z[bi];
+                double q2 = dx * dx + dy * dy + dz * dz;
+                if (q2 == 0.0) continue;
+                double q = sqrt(q2);
+                double rcij = oracle_pair_rcrit(mode, m[bi], m[bj], a[bi], a[bj], rc[bi], rc[bj], n1, Mstar);
+                if (q >= rcij) continue;                  /* W_l = 0 outside r_crit,0 */
+                double f = G * m[bj] * oracle_ml_weight(q, rcij, l, L, s, form) / (q2 * q);
+                ax += f * dx;
+                ay += f * dy;
+                az += f * dz;
+            }
+        }
+        acc[3 * i] = ax; acc[3 * i + 1] = ay; acc[3 * i + 2] = az;
+    }
 }
 
 static void ml_kick(ml_ctx *c, int l, int n, const int32_t *mem, double tau)
 {
     double *acc = (double *)calloc((size_t)(3 * n > 0 ? 3 * n : 1), sizeof(double));
-    for (int i = 0; i < n; i++) {
-        int bi = mem[i];
-        if (signbit(c->m[bi])) continue;
-        double ax = 0.0, ay = 0.0, az = 0.0;
-        for (int j = 0; j < n; j++) {
-            int bj = mem[j];
-            if (j == i || signbit(c->m[bj]) || tp_pair(c->n_big, bi, bj)) continue;
-            double dx = c->x[bj] - c->x[bi], dy = c->y[bj] - c->y[bi], dz = c->z[bj] - c->z[bi];
-            double q2 = dx * dx + dy * dy + dz * dz;
-            if (q2 == 0.0) continue;
-            double q = sqrt(q2), rcij = ml_pair_rc(c, bi, bj);
-            if (q >= rcij) continue;                  /* W_l = 0 outside r_crit,0 */
-            double f = c->G * c->m[bj] * oracle_ml_weight(q, rcij, l, c->L, c->s, c->form) / (q2 * q);
-            ax += f * dx;
-            ay += f * dy;
-            az += f * dz;
-        }
-        acc[3 * i] = ax; acc[3 * i + 1] = ay; acc[3 * i + 2] = az;
-    }
+    oracle_ml_level_acc(n, mem, c->x, c->y, c->z, c->m, c->a, c->rc, c->G, c->Mstar, c->n1, c->mode, c->form,
+                        c->n_big, l, c->L, c->s, acc);
     for (int i = 0; i < n; i++) {
         int bi = mem[i];
         c->vx[bi] += tau * acc[3 * i];
@@ -830,16 +846,19 @@ static void ml_kick(ml_ctx *c, int l, int n, const int32_t *mem, double tau)
 }
 
 /* Is (bi, bj) a pair of the subgroups of level l + 1 for a drift of h? */
-static int ml_subpair(const ml_ctx *c, int l, int bi, int bj, double h)
+static int subpair(const double *x, const double *y, const double *z, const double *vx, const double *vy,
+                   const double *vz, const double *m, const double *a, const double *rc, double n1, double Mstar,
+                   int mode, int n_big, int l, int s, int bi, int bj, double h)
 {
-    if (signbit(c->m[bi]) || signbit(c->m[bj]) || tp_pair(c->n_big, bi, bj)) return 0;
-    double dx = c->x[bj] - c->x[bi], dy = c->y[bj] - c->y[bi], dz = c->z[bj] - c->z[bi];
+    if (signbit(m[bi]) || signbit(m[bj]) || tp_pair(n_big, bi, bj)) return 0;
+    double dx = x[bj] - x[bi], dy = y[bj] - y[bi], dz = z[bj] - z[bi];
     double q2 = dx * dx + dy * dy + dz * dz;
-    double rcl = oracle_ml_radius(ml_pair_rc(c, bi, bj), l, c->s);
+    double rcij = oracle_pair_rcrit(mode, m[bi], m[bj], a[bi], a[bj], rc[bi], rc[bj], n1, Mstar);
+    double rcl = oracle_ml_radius(rcij, l, s);
     double rcl2 = rcl * rcl, rout = 1.5 * rcl;
     if (q2 < rcl2) return 1;
     if (q2 >= rout * rout) return 0;
-    double ux = c->vx[bj] - c->vx[bi], uy = c->vy[bj] - c->vy[bi], uz = c->vz[bj] - c->vz[bi];
+    double ux = vx[bj] - vx[bi], uy = vy[bj] - vy[bi], uz = vz[bj] - vz[bi];
     double uu = ux * ux + uy * uy + uz * uz, du = dx * ux + dy * uy + dz * uz;
     double tlo = h < 0.0 ? h : 0.0, thi = h < 0.0 ? 0.0 : h;
     double t = uu > 0.0 ? -du / uu : 0.0;
@@ -847,6 +866,31 @@ static int ml_subpair(const ml_ctx *c, int l, int bi, int bj, double h)
     if (t > thi) t = thi;
     double px = dx + ux * t, py = dy + uy * t, pz = dz + uz * t;
     return px * px + py * py + pz * pz < rcl2;
+}
+
+static int ml_subpair(const ml_ctx *c, int l, int bi, int bj, double h)
+{
+    return subpair(c->x, c->y, c->z, c->vx, c->vy, c->vz, c->m, c->a, c->rc, c->n1, c->Mstar, c->mode, c->n_big,
+                   l, c->s, bi, bj, h);
+}
+
+/* The member pairs (i < j, member order) of a level-l group that form the
+ * subgroups of level l + 1 for a drift of h: inside r_crit,l, or within
+ * 1.5 r_crit,l and entering r_crit,l on their straight-line relative motion
+ * within h.  Writes at most `cap` pairs of body indices; returns the count. */
+int64_t oracle_ml_subpairs(int n, const int32_t *mem, const double *x, const double *y, const double *z,
+                           const double *vx, const double *vy, const double *vz, const double *m, const double *a,
+                           const double *rc, double n1, double Mstar, int mode, int n_big, int l, int s, double h,
+                           int32_t *pairs, int64_t cap)
+{
+    int64_t cnt = 0;
+    for (int i = 0; i < n; i++)
+        for (int j = i + 1; j < n; j++) {
+            if (!subpair(x, y, z, vx, vy, vz, m, a, rc, n1, Mstar, mode, n_big, l, s, mem[i], mem[j], h)) continue;
+            if (cnt < cap) { pairs[2 * cnt] = mem[i]; pairs[2 * cnt + 1] = mem[j]; }
+            cnt++;
+        }
+    return cnt;
 }
 
 static void ml_level(ml_ctx *c, int l, int n, const int32_t *mem, double T)

@@ -202,3 +202,95 @@ def test_step_without_groups_ignores_the_levels():
     oracle.step(arr, d.G, d.Mstar, d.dt, 3.0, 0.4, 1, 0, 1, bs_tol=TOL, n_levels=2, n_sub=3)
     for c in range(7):
         assert np.array_equal(arr[c], ref[c])
+
+
+@pytest.mark.parametrize("mode,form,L,s", [(1, 0, 1, 2), (1, 1, 2, 3), (0, 0, 3, 2), (1, 0, 2, 4)])
+@pytest.mark.parametrize("n_big", [-1, 2])
+def test_kick_plus_levels_plus_bulirsch_stoer_is_newton(mode, form, L, s, n_big):
+    """K_0 (the kick) + the level-l shares + the Bulirsch-Stoer share minus its
+    central term = the whole Newtonian pair force, for pairs spread from deep
+    inside r_crit / s^L to beyond r_crit; in test-particle mode 2 the pairs of
+    two test particles have no share anywhere."""
+    rng = np.random.default_rng(7 + mode + 2 * form + 3 * L)
+    n = 8
+    x = 1.0 + 0.02 * rng.standard_normal(n)
+    y = 0.02 * rng.standard_normal(n)
+    z = 0.005 * rng.standard_normal(n)
+    m = rng.uniform(1e-7, 1e-5, n)
+    a = rng.uniform(0.98, 1.02, n)
+    rc = rng.uniform(0.005, 0.03, n)
+    x[1], y[1], z[1] = x[0] + 2e-4, y[0] - 1e-4, z[0]        # one pair deep inside every radius
+    for l in range(1, min(L, 3) + 1):                        # one pair in the band of level l (with a big body)
+        i, j = (l - 1) % 2, 2 * l + 1
+        rcij = oracle.pair_rcrit(mode, m[i], m[j], a[i], a[j], rc[i], rc[j], 3.0, 1.0)
+        sep = 0.6 * rcij / s ** (l - 1)                      # inside r_crit,(l-1), outside r_crit,l for s >= 2
+        x[j], y[j], z[j] = x[i] + 0.6 * sep, y[i] + 0.8 * sep, z[i]
+    mem = np.arange(n)
+    k = oracle.kick_acc(x, y, z, m, a, rc, G, 1.0, 3.0, mode, form, n_big=n_big)
+    levels = sum(oracle.ml_level_acc(x, y, z, m, a, rc, mem, G, 1.0, 3.0, mode, form, l, L, s, n_big=n_big)
+                 for l in range(1, L + 1))
+    bs = oracle.bs_acc_ml(x, y, z, m, a, rc, mem, G, 1.0, 3.0, mode, form, L, s, n_big=n_big)
+    pos = np.stack([x, y, z])
+    central = -G * pos / np.linalg.norm(pos, axis=0) ** 3
+    newton = np.zeros((3, n))
+    for i in range(n):
+        for j in range(n):
+            if i != j and not (n_big >= 0 and i >= n_big and j >= n_big):
+                d = pos[:, j] - pos[:, i]
+                newton[:, i] += G * m[j] * d / np.linalg.norm(d) ** 3
+    got = k + levels + bs - central
+    assert np.abs(got - newton).max() <= 1e-13 * np.abs(newton).max()
+    # the pairs span every level: some inside 0.1 r_crit / s^L, some between levels, some beyond r_crit
+    r = np.linalg.norm(pos[:, :, None] - pos[:, None, :], axis=0)
+    rcij = np.array([[oracle.pair_rcrit(mode, m[i], m[j], a[i], a[j], rc[i], rc[j], 3.0, 1.0)
+                      for j in range(n)] for i in range(n)])
+    q = (r / rcij)[~np.eye(n, dtype=bool)]
+    assert (q < 0.1 / s ** L).any() and ((q > 1.0 / s ** L) & (q < 1.0)).any() and (q > 1).any()
+    for l in range(1, L + 1):       # every level carries part of the force
+        assert np.abs(oracle.ml_level_acc(x, y, z, m, a, rc, mem, G, 1.0, 3.0, mode, form, l, L, s,
+                                          n_big=n_big)).max() > 0.0
+
+
+@pytest.mark.parametrize("level,s", [(1, 2), (1, 4), (2, 3)])
+def test_subgroup_pairs_against_brute_force(level, s):
+    """The pairs a level-l group forms its subgroups from: inside r_crit / s^l,
+    or within 1.5 r_crit / s^l and entering r_crit / s^l on the straight-line
+    relative motion within h (a dense time grid stands in for the closed form);
+    a ghost (m = -0.0) and, in test-particle mode 2, two test particles never
+    pair."""
+    rng = np.random.default_rng(11 + level + s)
+    n = 60
+    h = 6.0 / s ** level
+    rcl = 0.01 / s ** level
+    sx, sv = 2.5 * rcl, rcl / h                         # a cloud a few r_crit,l wide, crossing r_crit,l in ~h
+    arr = [1.0 + sx * rng.standard_normal(n), sx * rng.standard_normal(n), 0.3 * sx * rng.standard_normal(n),
+           0.01 + sv * rng.standard_normal(n), 0.017 + sv * rng.standard_normal(n),
+           0.3 * sv * rng.standard_normal(n), rng.uniform(1e-7, 1e-6, n)]
+    arr[6][5] = -0.0                                    # a ghost
+    a, rc = np.ones(n), np.full(n, 0.01)
+    mem = np.arange(n)
+    n_big = 40
+    got = {tuple(p) for p in oracle.ml_subpairs(arr, mem, a, rc, 3.0, 1.0, 0, level, s, h, n_big=n_big)}
+    x = np.stack(arr[:3], 1); v = np.stack(arr[3:6], 1)
+    ts = np.linspace(0.0, h, 4001)
+    want, edge, inside, entering = set(), 0, 0, 0
+    for i in range(n):
+        for j in range(i + 1, n):
+            if i == 5 or j == 5 or (i >= n_big and j >= n_big):
+                continue
+            d = x[j] - x[i]
+            r = np.linalg.norm(d)
+            if r < rcl:
+                want.add((i, j)); inside += 1
+                continue
+            if r >= 1.5 * rcl:
+                continue
+            path = np.linalg.norm(d[None, :] + (v[j] - v[i])[None, :] * ts[:, None], axis=1)
+            if abs(path.min() / rcl - 1) < 1e-6:
+                edge += 1
+                continue
+            if path.min() < rcl:
+                want.add((i, j)); entering += 1
+    assert inside >= 3 and entering >= 3
+    assert want <= got and len(got - want) <= edge
+    assert all(5 not in p for p in got) and all(not (p[0] >= n_big and p[1] >= n_big) for p in got)

@@ -82,13 +82,20 @@ MUTANTS = {
                                "        ml_kick(c, l, n, mem, h);\n        for (int i = 0; i < n; i++) { root[i]"),
     "levels_substep_not_divided": ("double h = T / c->s;", "double h = T;"),
     "levels_bs_weight_level": ("double w = oracle_ml_weight(q, rcij, g->nlev + 1,", "double w = oracle_ml_weight(q, rcij, g->nlev,"),
-    "levels_subgroup_radius": ("double rcl = oracle_ml_radius(ml_pair_rc(c, bi, bj), l, c->s);",
-                               "double rcl = oracle_ml_radius(ml_pair_rc(c, bi, bj), l + 1, c->s);"),
-    "levels_kick_weight_level": ("oracle_ml_weight(q, rcij, l, c->L, c->s, c->form)",
-                                 "oracle_ml_weight(q, rcij, l + 1, c->L, c->s, c->form)"),
+    "levels_subgroup_radius": ("double rcl = oracle_ml_radius(rcij, l, s);", "double rcl = oracle_ml_radius(rcij, l + 1, s);"),
+    "levels_kick_weight_level": ("oracle_ml_weight(q, rcij, l, L, s, form)", "oracle_ml_weight(q, rcij, l + 1, L, s, form)"),
     "levels_members_not_drifted": ("            if (inpair[i]) continue;\n", "            if (!inpair[i]) continue;\n"),
-    "levels_kick_mass_index": ("double f = c->G * c->m[bj] * oracle_ml_weight", "double f = c->G * c->m[bi] * oracle_ml_weight"),
-    "levels_kick_offset_sign": ("            double dx = c->x[bj] - c->x[bi],", "            double dx = c->x[bi] - c->x[bj],"),
+    "levels_kick_mass_index": ("double f = G * m[bj] * oracle_ml_weight", "double f = G * m[bi] * oracle_ml_weight"),
+    "levels_prediction_dropped": ("    if (q2 >= rout * rout) return 0;\n", "    return 0;\n"),
+    "levels_prediction_range": ("rout = 1.5 * rcl;", "rout = 1.1 * rcl;"),
+    "levels_second_kick_dropped": ("                                          &c->merges, c->L, c->s);\n        }\n        ml_kick(c, l, n, mem, 0.5 * h);\n",
+                                   "                                          &c->merges, c->L, c->s);\n        }\n"),
+    "levels_tp_pairs_kicked": ("                if (j == i || signbit(m[bj]) || tp_pair(n_big, bi, bj)) continue;",
+                               "                if (j == i || signbit(m[bj])) continue;"),
+    "levels_ghosts_in_subgroups": ("    if (signbit(m[bi]) || signbit(m[bj]) || tp_pair(n_big, bi, bj)) return 0;",
+                                   "    if (tp_pair(n_big, bi, bj)) return 0;"),
+    "levels_kick_offset_sign": ("                double dx = x[bj] - x[bi], dy = y[bj] - y[bi], dz = z[bj] - z[bi];\n                double q2",
+                                "                double dx = x[bi] - x[bj], dy = y[bj] - y[bi], dz = z[bj] - z[bi];\n                double q2"),
     "dead_pairs_grouped": ("        if (dead && (dead[pairs[2 * p]] || dead[pairs[2 * p + 1]])) continue;\n", ""),
 }
 
