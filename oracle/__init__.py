@@ -86,6 +86,8 @@ def _load():
                                                                   C.POINTER(C.c_int)], i),
             "oracle_ml_radius": ([d, i, i], d),
             "oracle_ml_weight": ([d, d, i, i, i, i], d),
+            "oracle_bs_group_counted": ([i, _i32p] + [_dp] * 9 + [d, d, d, i, i, i, d, d, C.POINTER(C.c_int),
+                                                                   C.POINTER(C.c_int)], i),
             "oracle_ml_level_acc": ([i, _i32p] + [_dp] * 6 + [d, d, d, i, i, i, i, i, i, _dp], None),
             "oracle_ml_subpairs": ([i, _i32p] + [_dp] * 9 + [d, d, i, i, i, i, d, _i32p, C.c_int64], C.c_int64),
             "oracle_bs_acc_ml": ([i, _i32p] + [_dp] * 6 + [d, d, d, i, i, i, i, i, _dp], None),
@@ -378,6 +380,18 @@ def ml_group(arrs, members, a, rc, G, Mstar, n1, mode, form, dt, tol, n_levels, 
     if merges is not None:
         merges[0] += mg.value
     return f, bad.value
+
+
+def bs_group_counted(arrs, members, a, rc, G, Mstar, n1, mode, form, dt, tol, n_big=-1):
+    """bs_group without collisions; returns (forced, accepted sub-steps, attempts)."""
+    x, y, z, vx, vy, vz, m = arrs
+    mem = np.ascontiguousarray(np.asarray(members, dtype=np.int32))
+    acc_, att_ = C.c_int(0), C.c_int(0)
+    f = int(_load().oracle_bs_group_counted(len(mem), mem.ctypes.data_as(_i32p),
+                                            *map(_p, (x, y, z, vx, vy, vz, m, _f64(a), _f64(rc))), G, Mstar, n1,
+                                            int(mode), int(form), int(n_big), float(dt), float(tol),
+                                            C.byref(acc_), C.byref(att_)))
+    return f, acc_.value, att_.value
 
 
 def drift_groups(arrs, a, rc, pairs, G, Mstar, n1, mode, form, dt, tol, n_big=-1, max_iter=50, n_levels=0,

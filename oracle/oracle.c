@@ -664,7 +664,7 @@ static int bs_group_run(int n, const int32_t *mem, double *x, double *y, double 
                         double *vx, double *vy, double *vz, double *m, const double *a,
                         const double *rc, double *R, int32_t *dead, double G, double Mstar,
                         double n1, int mode, int form, int n_big, double dt, double tol,
-                        int *merges, int nlev, int nsub)
+                        int *merges, int nlev, int nsub, int *accepted, int *attempts)
 {
     int32_t *ghost = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
     bs_group g = {n, mem, m, a, rc, G, Mstar, n1, mode, form, n_big, ghost, nlev, nsub};
@@ -693,8 +693,10 @@ static int bs_group_run(int n, const int32_t *mem, double *x, double *y, double 
             if (f < frac) frac = f;
         }
     }
+    int n_acc = 0, n_att = 0;
     for (int att = 0; att < BS_MAX_ATTEMPTS && done < 1.0; att++) {
         double h = frac * dt;
+        n_att++;
         for (int k = 0; k < n; k++) {        /* error scales of this sub-step */
             const double *s = yv + 6 * k;
             double px = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
@@ -733,6 +735,7 @@ static int bs_group_run(int n, const int32_t *mem, double *x, double *y, double 
         const double *Tacc = T + (size_t)(acc_col * BS_KMAX + acc_col) * L;
         for (int q = 0; q < L; q++) yv[q] = Tacc[q];
         if (R) nmerge += bs_merge(&g, yv, m, R, ghost);
+        n_acc++;
         done += frac;
         if (acc_col <= BS_GROW_COL) frac *= 2.0;
         if (frac > 1.0 - done) frac = 1.0 - done;
@@ -748,6 +751,8 @@ static int bs_group_run(int n, const int32_t *mem, double *x, double *y, double 
         if (ghost[k] && dead) dead[b] = 1;
     }
     if (merges) *merges += nmerge;
+    if (accepted) *accepted = n_acc;
+    if (attempts) *attempts = n_att;
     free(buf);
     free(ghost);
     return forced;
@@ -760,7 +765,18 @@ int oracle_bs_group_full(int n, const int32_t *mem, double *x, double *y, double
                          int *merges)
 {
     return bs_group_run(n, mem, x, y, z, vx, vy, vz, m, a, rc, R, dead, G, Mstar, n1, mode, form, n_big,
-                        dt, tol, merges, 0, 1);
+                        dt, tol, merges, 0, 1, NULL, NULL);
+}
+
+/* oracle_bs_group without collisions, also reporting the accepted sub-steps
+ * and the attempts of the step-size control. */
+int oracle_bs_group_counted(int n, const int32_t *mem, double *x, double *y, double *z,
+                            double *vx, double *vy, double *vz, const double *m, const double *a,
+                            const double *rc, double G, double Mstar, double n1, int mode, int form,
+                            int n_big, double dt, double tol, int *accepted, int *attempts)
+{
+    return bs_group_run(n, mem, x, y, z, vx, vy, vz, (double *)m, a, rc, NULL, NULL, G, Mstar, n1, mode, form,
+                        n_big, dt, tol, NULL, 0, 1, accepted, attempts);
 }
 
 /* oracle_bs_group_full without collisions. */
@@ -928,7 +944,7 @@ static void ml_level(ml_ctx *c, int l, int n, const int32_t *mem, double T)
             else
                 c->forced += bs_group_run(cnt, sub, c->x, c->y, c->z, c->vx, c->vy, c->vz, c->m, c->a, c->rc, c->R,
                                           c->dead, c->G, c->Mstar, c->n1, c->mode, c->form, c->n_big, h, c->tol,
-                                          &c->merges, c->L, c->s);
+                                          &c->merges, c->L, c->s, NULL, NULL);
         }
         ml_kick(c, l, n, mem, 0.5 * h);
     }

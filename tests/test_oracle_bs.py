@@ -325,3 +325,47 @@ def test_predicted_pairs_against_brute_force():
     got_clear = {p for p in got}
     assert len(want) >= 3
     assert want <= got_clear and len(got_clear - want) <= near_edge
+
+
+def test_step_size_control_trace():
+    """The sub-step control on a case its rules decide by hand: two massless
+    bodies in free space (straight lines, so every column extrapolates the
+    exact motion and column 1 is accepted), 0.01 au apart with relative speed
+    8 x 0.01 au / dt.  The first sub-step is the largest binary fraction with
+    f dt |v_ij| <= r_ij: dt/8; each acceptance by column <= 2 doubles the next,
+    clipped to what is left: dt/8, dt/4, dt/2, dt/8 -- four sub-steps, no
+    rejections, and the exact straight-line end state."""
+    dt = 8.0
+    x0 = [np.array([1.0, 1.01]), np.zeros(2), np.zeros(2)]
+    v0 = [np.zeros(2), np.array([0.0, 0.01]), np.zeros(2)]
+    arr = [a.copy() for a in x0 + v0] + [np.zeros(2)]
+    f, accepted, attempts = oracle.bs_group_counted(arr, [0, 1], np.ones(2), np.zeros(2), 1.0, 1e-20, 3.0, 1, 0,
+                                                   dt, 1e-12)
+    assert (f, accepted, attempts) == (0, 4, 4)
+    for c in range(3):
+        np.testing.assert_allclose(arr[c], x0[c] + v0[c] * dt, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(arr[3 + c], v0[c], rtol=0, atol=1e-15)
+
+
+def test_attempt_limit_completes_the_remaining_time_on_kepler_orbits():
+    """A tolerance no column can meet (except where the columns agree to the
+    last bit): the sub-steps are halved to the floor (dt 2^-30) and accepted
+    there as forced, 4,096 attempts pass, and the
+    members drift the rest of dt on their Kepler orbits (straight lines in
+    free space).  Momentum is conserved by both parts, so the centre of mass
+    ends at c0 + V dt exactly as a uniform motion -- a completion over the
+    whole dt instead of the remainder would overshoot by V times the time
+    already integrated."""
+    Gc, Ms, dt = 1.0, 1e-20, 8.0
+    m = np.array([1e-3, 2e-3])
+    V = np.array([0.05, -0.02, 0.01])
+    x0 = np.array([[1.0, 2.0, 0.5], [1.01, 2.0, 0.5]])
+    v0 = np.array([V + [0.0, 0.001, 0.0], V - [0.0, 0.0005, 0.0]])
+    arr = [x0[:, c].copy() for c in range(3)] + [v0[:, c].copy() for c in range(3)] + [m.copy()]
+    f, accepted, attempts = oracle.bs_group_counted(arr, [0, 1], np.ones(2), np.full(2, 1.0), Gc, Ms, 3.0, 0, 0,
+                                                   dt, 1e-300)
+    assert f == 1 and attempts == 4096 and 0 < accepted < 4096
+    c0 = (m[:, None] * x0).sum(0) / m.sum()
+    cend = np.array([(m * arr[c]).sum() / m.sum() for c in range(3)])
+    vcm = (m[:, None] * v0).sum(0) / m.sum()
+    assert np.abs(cend - (c0 + vcm * dt)).max() < 1e-10      # rounding of 4,096 forced sub-steps: ~1e-12

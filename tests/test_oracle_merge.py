@@ -106,3 +106,27 @@ def test_ghosts_are_inert():
     for c in range(7):
         assert np.array_equal(with_g[c][keep], arr[c])
     assert dead_g[40] == 1 and dead_g[keep].sum() == 0
+
+
+def test_simultaneous_overlaps_all_merge_after_one_substep():
+    """Three bodies overlapping at once, drifted over a time short enough for
+    a single accepted sub-step: the search repeats until no pair overlaps, so
+    both mergers happen after that sub-step -- one survivor (the lowest index)
+    with the total mass, the mass-weighted velocity and the equal-density
+    radius of all three."""
+    Gc, Ms = 1.0, 1e-20
+    m = [3e-3, 1e-3, 2e-3]
+    pos = [np.array([1.0, 2.0, 0.5]), np.array([1.0005, 2.0, 0.5]), np.array([1.0, 2.0006, 0.5])]
+    vel = [np.array([0.01, 0.0, 0.0]), np.array([0.0, 0.02, 0.0]), np.array([0.0, 0.0, -0.03])]
+    arr = [np.array([p[c] for p in pos]) for c in range(3)] + [np.array([v[c] for v in vel]) for c in range(3)] + \
+          [np.array(m)]
+    R = np.array([1e-3, 1e-3, 1e-3])
+    dead = np.zeros(3, np.int32)
+    merges = [0]
+    forced = oracle.bs_group(arr, [0, 1, 2], np.ones(3), np.full(3, 1.0), Gc, Ms, 3.0, 0, 0, 1e-6, 1e-12,
+                             radius=R, dead=dead, merges=merges)
+    assert forced == 0 and merges[0] == 2 and dead.tolist() == [0, 1, 1]
+    assert arr[6][0] == pytest.approx(6e-3, rel=1e-15) and np.all(np.signbit(arr[6][1:]))
+    vcm = sum(mi * v for mi, v in zip(m, vel)) / sum(m)
+    assert np.abs(np.array([arr[c][0] for c in range(3, 6)]) - vcm).max() < 1e-9
+    assert R[0] == pytest.approx(3 ** (1 / 3) * 1e-3, rel=1e-14)

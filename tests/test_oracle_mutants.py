@@ -62,7 +62,13 @@ MUTANTS = {
     "extrapolation_in_h_not_h2": ("double cf = (nkj * nkj) / (nk * nk - nkj * nkj);",
                                   "double cf = nkj / (nk - nkj);"),
     "members_also_kepler_drifted": ("        if (label[i] >= 0) continue;\n", ""),
+    "bs_no_step_growth": ("        if (acc_col <= BS_GROW_COL) frac *= 2.0;\n", ""),
+    "bs_first_frac_no_velocity": ("(f * fabs(dt)) * (f * fabs(dt)) * v2 > r2", "(f * fabs(dt)) * (f * fabs(dt)) > r2"),
+    "bs_kepler_completion_full_dt": ("oracle_kepler(G * Mstar, yv + 6 * k, (1.0 - done) * dt, 50);",
+                                     "oracle_kepler(G * Mstar, yv + 6 * k, dt, 50);"),
+    "bs_kepler_completion_skipped": ("        for (int k = 0; k < n; k++) oracle_kepler(G * Mstar, yv + 6 * k, (1.0 - done) * dt, 50);\n", ""),
     # mergers and removal
+    "merge_once_only": ("        merges++;\n    }\n}", "        merges++;\n        return merges;\n    }\n}"),
     "merger_plain_average": ("yv[6 * fi + c] = (mt > 0.0) ? (mi * u + mj * w) / mt : 0.5 * (u + w);",
                              "yv[6 * fi + c] = 0.5 * (u + w);"),
     "merger_radius_sum": ("R[bi] = cbrt(R[bi] * R[bi] * R[bi] + R[bj] * R[bj] * R[bj]);", "R[bi] = R[bi] + R[bj];"),
@@ -88,8 +94,8 @@ MUTANTS = {
     "levels_kick_mass_index": ("double f = G * m[bj] * oracle_ml_weight", "double f = G * m[bi] * oracle_ml_weight"),
     "levels_prediction_dropped": ("    if (q2 >= rout * rout) return 0;\n", "    return 0;\n"),
     "levels_prediction_range": ("rout = 1.5 * rcl;", "rout = 1.1 * rcl;"),
-    "levels_second_kick_dropped": ("                                          &c->merges, c->L, c->s);\n        }\n        ml_kick(c, l, n, mem, 0.5 * h);\n",
-                                   "                                          &c->merges, c->L, c->s);\n        }\n"),
+    "levels_second_kick_dropped": ("&c->merges, c->L, c->s, NULL, NULL);\n        }\n        ml_kick(c, l, n, mem, 0.5 * h);\n",
+                                   "&c->merges, c->L, c->s, NULL, NULL);\n        }\n"),
     "levels_tp_pairs_kicked": ("                if (j == i || signbit(m[bj]) || tp_pair(n_big, bi, bj)) continue;",
                                "                if (j == i || signbit(m[bj])) continue;"),
     "levels_ghosts_in_subgroups": ("    if (signbit(m[bi]) || signbit(m[bj]) || tp_pair(n_big, bi, bj)) return 0;",
