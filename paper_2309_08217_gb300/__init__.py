@@ -12,6 +12,10 @@ is no CPU fallback.
     sys = g.DeviceSystem.from_disc(disc)       # float64 tensors on cuda
     p = g.make_params(G=disc.G, Mstar=1.0, dt=6.0, precision=g.GENGA_FP32)
     g.genga_kick(ctx, sys, p, tau=3.0, acc=acc_tensor)
+    # hybrid steps with the close-encounter level and tuned intermediate levels
+    p = g.make_params(G=disc.G, Mstar=1.0, dt=6.0, precision=g.GENGA_FP32, bs_tol=1e-12)
+    (p.n_levels, p.n_sub), ms = g.genga_tune_levels(ctx, sys, p, [(0, 2), (2, 3), (2, 4)])
+    g.genga_step(ctx, sys, p, 1000)
 """
 from __future__ import annotations
 
