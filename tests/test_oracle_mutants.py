@@ -92,6 +92,10 @@ MUTANTS = {
     "levels_kick_weight_level": ("oracle_ml_weight(q, rcij, l, L, s, form)", "oracle_ml_weight(q, rcij, l + 1, L, s, form)"),
     "levels_members_not_drifted": ("            if (inpair[i]) continue;\n", "            if (!inpair[i]) continue;\n"),
     "levels_kick_mass_index": ("double f = G * m[bj] * oracle_ml_weight", "double f = G * m[bi] * oracle_ml_weight"),
+    "levels_bs_skip_radius_one_level_deeper": ("if (q >= oracle_ml_radius(rcij, g->nlev, g->nsub)) continue;",
+                                               "if (q >= oracle_ml_radius(rcij, g->nlev + 1, g->nsub)) continue;"),
+    "levels_weight_radius_uses_level0": ("w *= 1.0 - oracle_changeover((q / oracle_ml_radius(rc, k, s) - 0.1) / 0.9, form);",
+                                         "w *= 1.0 - oracle_changeover((q / oracle_ml_radius(rc, 0, s) - 0.1) / 0.9, form);"),
     "levels_prediction_dropped": ("    if (q2 >= rout * rout) return 0;\n", "    return 0;\n"),
     "levels_prediction_range": ("rout = 1.5 * rcl;", "rout = 1.1 * rcl;"),
     "levels_second_kick_dropped": ("&c->merges, c->L, c->s, NULL, NULL);\n        }\n        ml_kick(c, l, n, mem, 0.5 * h);\n",
