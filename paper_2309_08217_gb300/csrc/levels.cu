@@ -35,7 +35,7 @@ namespace genga {
 
 namespace {
 
-constexpr int LV_WARPS = 4;  // groups in flight per CTA
+constexpr int LV_WARPS = 4;  // warps per CTA (each takes one group or one member at a time)
 
 // W_l at separation q with inv9 = 1 / (0.9 r_crit,ij): prod_{k<l} (1 - K_k) * K_l.
 __device__ __forceinline__ double level_kick_weight(double q, double inv9, int l, double s, int form) {
