@@ -369,3 +369,49 @@ def test_attempt_limit_completes_the_remaining_time_on_kepler_orbits():
     cend = np.array([(m * arr[c]).sum() / m.sum() for c in range(3)])
     vcm = (m[:, None] * v0).sum(0) / m.sum()
     assert np.abs(cend - (c0 + vcm * dt)).max() < 1e-10      # rounding of 4,096 forced sub-steps: ~1e-12
+
+
+def test_predicted_pairs_of_two_test_particles_are_dropped():
+    """Test-particle mode 2: a pair of two test particles is never an entry
+    (it has no force), while the same disc without the mode has such pairs."""
+    d = discs.disc_uniform(2000, 21, a_min=0.97, a_max=1.03)
+    arr = oracle.disc_arrays(d)
+    a, rc = oracle.rcrit(*arr, G=d.G, Mstar=d.Mstar, dt=d.dt)
+    n_big = 1000
+    every = oracle.predicted_pairs(arr, a, rc, 3.0, d.Mstar, 1, d.dt)
+    tp = oracle.predicted_pairs(arr, a, rc, 3.0, d.Mstar, 1, d.dt, n_big=n_big)
+    both = [(i, j) for i, j in every if i >= n_big and j >= n_big]
+    assert len(both) >= 1
+    assert {tuple(p) for p in tp} == {tuple(p) for p in every} - set(both)
+
+
+def _fast_pass():
+    """Two Earth-mass planets near 1 au: planet 1 starts 1.3 r_crit behind
+    planet 0 (three mutual Hill radii), 0.3 r_crit outward, 0.01 au/day
+    faster -- it passes at 0.3 r_crit and leaves r_crit again within 10 days."""
+    m = np.array([3e-6, 3e-6])
+    rc = 3.0 * (2 * 3e-6 / 3.0) ** (1 / 3)
+    b, v = 0.3 * rc, 0.01
+    s0 = math.sqrt((1.3 * rc) ** 2 - b ** 2)
+    x0 = np.array([1.0, 0.0, 0.0]); v0 = np.array([0.0, math.sqrt(G * (1 + m[0])), 0.0])
+    x1 = x0 + np.array([b, -s0, 0.0]); v1 = v0 + np.array([0.0, v, 0.0])
+    xs, vh = np.stack([x0, x1]), np.stack([v0, v1])
+    vb = vh - (m[:, None] * vh).sum(0) / (1 + m.sum())
+    return [xs[:, 0].copy(), xs[:, 1].copy(), xs[:, 2].copy(), vb[:, 0].copy(), vb[:, 1].copy(), vb[:, 2].copy(), m]
+
+
+def test_a_pass_within_one_step_is_grouped_by_its_predicted_entry():
+    """With dt = 12 d the pair is outside r_crit at both step starts, so only
+    the predicted entry (R10) puts it into a group: the step then follows the
+    independent DOP853 integration 5x better than without the level, where
+    the whole pass keeps only its K part."""
+    T, dt = 24.0, 12.0
+    ref = _truth(_fast_pass(), T)
+    errs = {}
+    for tol in (0.0, 1e-12):
+        arr = _fast_pass()
+        forced = [0]
+        assert oracle.step(arr, G, 1.0, dt, 3.0, 0.4, 1, 0, 2, bs_tol=tol, forced=forced) == 0
+        assert forced[0] == 0
+        errs[tol] = np.abs(np.stack(arr[:3], 1) - ref).max()
+    assert errs[1e-12] < 0.3 * errs[0.0]

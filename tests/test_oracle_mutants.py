@@ -76,6 +76,9 @@ MUTANTS = {
     "merger_survivor_higher_index": ("        ghost[fj] = 1;\n", "        ghost[fi] = 1;\n"),
     "ghosts_still_pull": ("|| bs_ghost(g, i) || bs_ghost(g, j)) continue;", ") continue;"),
     "removal_outer_uses_inner": ("(r_out > 0.0 && r2 > r_out * r_out)", "(r_out > 0.0 && r2 > r_in * r_in)"),
+    "prediction_not_used_by_the_step": ("        int64_t npr = oracle_predicted_pairs(", "        int64_t npr = 0 * oracle_predicted_pairs("),
+    "prediction_keeps_test_particle_pairs": ("            if (tp_pair(n_big, i, j)) continue;\n            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];\n            double r = sqrt(dx * dx + dy * dy + dz * dz);\n            double rcij = oracle_pair_rcrit(mode, m[i], m[j], a[i], a[j], rc[i], rc[j], n1, Mstar);\n            if (r < rcij || r >= PREDICT_RANGE",
+                                             "            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];\n            double r = sqrt(dx * dx + dy * dy + dz * dz);\n            double rcij = oracle_pair_rcrit(mode, m[i], m[j], a[i], a[j], rc[i], rc[j], n1, Mstar);\n            if (r < rcij || r >= PREDICT_RANGE"),
     "prediction_unclamped": ("            if (t > thi) t = thi;\n", ""),
     "prediction_wrong_sign": ("            double t = uu > 0.0 ? -du / uu : 0.0;",
                               "            double t = uu > 0.0 ? du / uu : 0.0;"),
