@@ -130,3 +130,24 @@ def test_simultaneous_overlaps_all_merge_after_one_substep():
     vcm = sum(mi * v for mi, v in zip(m, vel)) / sum(m)
     assert np.abs(np.array([arr[c][0] for c in range(3, 6)]) - vcm).max() < 1e-9
     assert R[0] == pytest.approx(3 ** (1 / 3) * 1e-3, rel=1e-14)
+
+
+def test_a_ghost_moves_on_its_kepler_orbit():
+    """Two massless bodies overlapping at t = 0 near the Sun merge after the
+    first accepted sub-step (no pair force ever acts: m = 0); the absorbed one
+    then feels the central body only (R24), so at the end of the drift it is
+    where the Kepler solution of its initial state puts it."""
+    vc = math.sqrt(G)
+    arr = _pair([1.0, 0.0, 0.0], [1.0 + 5e-6, 1e-6, 0.0], [0.0, vc, 0.0], [1e-4, 1.02 * vc, 2e-4], [0.0, 0.0])
+    x1 = [arr[c][1] for c in range(6)]
+    R = np.array([1e-5, 1e-5])
+    dead = np.zeros(2, np.int32)
+    merges = [0]
+    dt = 10.0
+    forced = oracle.bs_group(arr, [0, 1], np.ones(2), np.full(2, 1.0), G, 1.0, 3.0, 0, 0, dt, 1e-12,
+                             radius=R, dead=dead, merges=merges)
+    assert forced == 0 and merges[0] == 1 and dead.tolist() == [0, 1]
+    want, status = oracle.kepler(G, x1, dt)
+    assert status == 0
+    got = np.array([arr[c][1] for c in range(6)])
+    assert np.abs(got[:3] - want[:3]).max() < 1e-11 and np.abs(got[3:] - want[3:]).max() < 1e-12

@@ -74,6 +74,8 @@ MUTANTS = {
     "merger_radius_sum": ("R[bi] = cbrt(R[bi] * R[bi] * R[bi] + R[bj] * R[bj] * R[bj]);", "R[bi] = R[bi] + R[bj];"),
     "merger_overlap_one_radius": ("double rr = R[g->mem[i]] + R[g->mem[j]];", "double rr = R[g->mem[i]];"),
     "merger_survivor_higher_index": ("        ghost[fj] = 1;\n", "        ghost[fi] = 1;\n"),
+    "ghost_feels_no_central_body": ("        double c = -g->G * g->Mstar / (r2 * r);",
+                                    "        double c = bs_ghost(g, i) ? 0.0 : -g->G * g->Mstar / (r2 * r);"),
     "ghosts_still_pull": ("|| bs_ghost(g, i) || bs_ghost(g, j)) continue;", ") continue;"),
     "removal_outer_uses_inner": ("(r_out > 0.0 && r2 > r_out * r_out)", "(r_out > 0.0 && r2 > r_in * r_in)"),
     "prediction_not_used_by_the_step": ("        int64_t npr = oracle_predicted_pairs(", "        int64_t npr = 0 * oracle_predicted_pairs("),
