@@ -31,9 +31,12 @@ extern "C" {
  *   params->precision must be GENGA_FP64.
  *   N > GENGA_NOALLOC_MAX_N, bad pointers or parameters: GENGA_ERR_INVALID_ARG,
  *   nothing is enqueued.
- * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  The scratch keeps the last call's contents and
+ * The first call in each CUDA context (the current device's primary context,
+ * or whichever context the caller has made current) looks up the scratch
+ * array's device address there (cudaGetSymbolAddress) and keeps it for that
+ * context only; a new context -- after cudaDeviceReset, say -- gets its own
+ * lookup on its first call.  Make that first call before any stream capture.
+ * The scratch keeps the last call's contents and
  * is re-initialised by each call; calls that overlap on the GPU (several
  * streams or host threads at once) race on it and must be serialised by the
  * caller.  No encounter list and no sticky status are produced.

@@ -12,8 +12,14 @@
 // arrays and the acceleration output.
 //
 // Host code cannot use the array's name as a device address, so the first
-// call on each device looks the address up with cudaGetSymbolAddress (with
-// that device current) and caches it; later calls reuse it.
+// call in each CUDA context looks the address up with cudaGetSymbolAddress
+// (with that context current) and caches it under the context's unique id;
+// later calls in the same context reuse it.  A new context on the same device
+// (after cudaDeviceReset, or a caller's own driver context) has a new id, so
+// its first call looks the address up again instead of reusing an address
+// that belongs to another context.
+#include <cuda.h>  // CUcontext and CUresult only; the driver calls are resolved at run time
+
 #include <mutex>
 
 #include "../../include/genga_noalloc.h"
@@ -165,24 +171,69 @@ __global__ void na_acc(const double *__restrict__ x, const double *__restrict__ 
     }
 }
 
-// Per-device address of g_noalloc_scratch, looked up once per device.
-constexpr int NA_MAX_DEVICES = 64;
+// Address of g_noalloc_scratch per CUDA context, keyed by the context's
+// unique id (cuCtxGetId), so an address is never used in another context.
+// The two driver calls are taken from the runtime's driver entry-point table,
+// so the library links against the CUDA runtime only.
+constexpr int NA_MAX_CONTEXTS = 64;
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+struct NaEntry {
+    unsigned long long ctx_id;
+    double *ptr;
+};
 std::mutex g_na_mutex;
-double *g_na_ptr[NA_MAX_DEVICES] = {};
+NaEntry g_na_cache[NA_MAX_CONTEXTS];
+int g_na_used = 0, g_na_next = 0;
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
 
-cudaError_t scratch_for_current_device(double **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+cudaError_t current_context_id(unsigned long long *id) {
+    if (!g_ctx_current || !g_ctx_id) {
+        void *f0 = nullptr, *f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0 = cudaDriverEntryPointSymbolNotFound, q1 = q0;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0);
         if (e != cudaSuccess) return e;
-        g_na_ptr[dev] = static_cast<double *>(p);
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return e;
+        if (q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+            return cudaErrorNotSupported;
+        g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f0);
+        g_ctx_id = reinterpret_cast<CtxGetIdFn>(f1);
     }
-    *out = g_na_ptr[dev];
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+    if (!ctx) {
+        // no context is current yet: cudaSetDevice on the current device
+        // binds its primary context (and allocates nothing)
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaSetDevice(dev);
+        if (e != cudaSuccess) return e;
+        if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorContextIsDestroyed;
+    }
+    return g_ctx_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorContextIsDestroyed;
+}
+
+cudaError_t scratch_for_current_context(double **out) {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    unsigned long long id = 0;
+    cudaError_t e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < g_na_used; k++) {
+        if (g_na_cache[k].ctx_id == id) {
+            *out = g_na_cache[k].ptr;
+            return cudaSuccess;
+        }
+    }
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    // a full table replaces its oldest entry (a context seen again later is
+    // looked up again)
+    const int k = g_na_used < NA_MAX_CONTEXTS ? g_na_used++ : (g_na_next++ % NA_MAX_CONTEXTS);
+    g_na_cache[k] = NaEntry{id, static_cast<double *>(p)};
+    *out = static_cast<double *>(p);
     return cudaSuccess;
 }
 
@@ -194,13 +245,14 @@ extern "C" genga_status genga_kick_noalloc(const genga_system *sys, const genga_
     if (sys->N < 0 || sys->N > GENGA_NOALLOC_MAX_N) return GENGA_ERR_INVALID_ARG;
     if (sys->N > 0 && (!sys->x || !sys->y || !sys->z || !sys->vx || !sys->vy || !sys->vz || !sys->m))
         return GENGA_ERR_INVALID_ARG;
-    if (p->precision != GENGA_FP64 || !(p->Mstar > 0.0) || !(p->G >= 0.0) || p->n1 < 0.0 || p->n2 < 0.0 ||
-        (p->rcrit_mode != GENGA_RCRIT_EQ1 && p->rcrit_mode != GENGA_RCRIT_MUTUAL_HILL) ||
+    if (p->precision != GENGA_FP64 || !isfinite(p->G) || !(p->G >= 0.0) || !isfinite(p->Mstar) ||
+        !(p->Mstar > 0.0) || !isfinite(p->dt) || !isfinite(p->n1) || !isfinite(p->n2) || p->n1 < 0.0 ||
+        p->n2 < 0.0 || (p->rcrit_mode != GENGA_RCRIT_EQ1 && p->rcrit_mode != GENGA_RCRIT_MUTUAL_HILL) ||
         (p->changeover != GENGA_K_CHAMBERS && p->changeover != GENGA_K_QUINTIC) || p->n_big < -1 || !isfinite(tau))
         return GENGA_ERR_INVALID_ARG;
     if (sys->N == 0) return GENGA_OK;
     double *scratch = nullptr;
-    if (scratch_for_current_device(&scratch) != cudaSuccess) return GENGA_ERR_CUDA;
+    if (scratch_for_current_context(&scratch) != cudaSuccess) return GENGA_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     const int N = sys->N;
     // the momentum kernel's completion ticket must start at zero on every call

@@ -83,3 +83,37 @@ def test_host_argument_checks_without_device(lib):
     assert lib.genga_create(None, 10, 0) == g.GENGA_ERR_INVALID_ARG
     assert lib.genga_create(C.byref(h), -1, 0) == g.GENGA_ERR_INVALID_ARG
     lib.genga_destroy(None)                                   # no-op
+
+
+def test_noalloc_argument_checks_without_device(lib):
+    """genga_kick_noalloc rejects bad sizes and parameters on the host,
+    before any CUDA call (each case below fails one check)."""
+    import paper_2309_08217_gb300 as g
+    fake = 0x1000  # never dereferenced: every call is rejected first
+    ok = dict(G=2.959122082855911e-4, Mstar=1.0, dt=6.0, precision=g.GENGA_FP64)
+
+    def call(N=100, tau=0.0, **kw):
+        p = g.make_params(**{**ok, **kw})
+        s = g.genga_system(N, *([fake] * 7), None)
+        return lib.genga_kick_noalloc(C.byref(s), C.byref(p), tau, None, None)
+
+    inf, nan = float("inf"), float("nan")
+    assert call(N=g.GENGA_NOALLOC_MAX_N + 1) == g.GENGA_ERR_INVALID_ARG
+    assert call(N=-1) == g.GENGA_ERR_INVALID_ARG
+    assert call(precision=g.GENGA_FP32) == g.GENGA_ERR_INVALID_ARG
+    assert call(rcrit_mode=7) == g.GENGA_ERR_INVALID_ARG
+    assert call(changeover=5) == g.GENGA_ERR_INVALID_ARG
+    assert call(n_big=-2) == g.GENGA_ERR_INVALID_ARG
+    assert call(tau=inf) == g.GENGA_ERR_INVALID_ARG
+    assert call(tau=nan) == g.GENGA_ERR_INVALID_ARG
+    for name in ("G", "Mstar", "dt", "n1", "n2"):
+        for bad in (inf, nan):
+            assert call(**{name: bad}) == g.GENGA_ERR_INVALID_ARG, (name, bad)
+    assert call(G=-1.0) == g.GENGA_ERR_INVALID_ARG
+    assert call(Mstar=0.0) == g.GENGA_ERR_INVALID_ARG
+    assert call(n1=-1.0) == g.GENGA_ERR_INVALID_ARG
+    s = g.genga_system(10, None, *([fake] * 6), None)   # a NULL state array
+    p = g.make_params(**ok)
+    assert lib.genga_kick_noalloc(C.byref(s), C.byref(p), 0.0, None, None) == g.GENGA_ERR_INVALID_ARG
+    assert lib.genga_kick_noalloc(None, C.byref(p), 0.0, None, None) == g.GENGA_ERR_INVALID_ARG
+    assert lib.genga_kick_noalloc(C.byref(s), None, 0.0, None, None) == g.GENGA_ERR_INVALID_ARG
