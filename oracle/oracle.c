@@ -28,8 +28,7 @@
  *                         body are removed (both leave a massless "ghost")
  *   energy / ang. mom.    Sect. 3.1: dE/E = E(t)/E0 - 1, dL/L = L(t)/L0 - 1
  *
- * Readings where the paper is silent (each one is listed in the design
- * notes): democratic-heliocentric coordinates (heliocentric x, barycentric
+ * Readings where the paper is silent: democratic-heliocentric coordinates (heliocentric x, barycentric
  * v; Kepler mu = G M*; the central-body momentum drift x += tau P / M*);
  * the Kepler velocity of Eq. (1) is the heliocentric speed v + P/M*;
  * a_i is the osculating semi-major axis with mu_i = G (M* + m_i), and

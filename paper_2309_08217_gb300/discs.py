@@ -214,7 +214,7 @@ def batch_of_discs(D=256, seed=4, n_lo=1000, n_hi=16000) -> List[Disc]:
     return out
 
 
-# Named workloads (sizes and recipes as stated in the design notes).
+# Named workloads: the sizes, distributions and seeds of the benchmark and test configurations.
 def planet_swarm(n_disc=4000, n_swarm=80, seed=6, m_planet=10 * M_EARTH, r_lo=0.01, r_hi=0.05,
                  sigma_v=3e-4) -> Disc:
     """A planet on a circular orbit at 1 au (body 0) with n_swarm planetesimals

@@ -85,7 +85,7 @@ def test_mergers_at_the_deepest_level(genga, ctx):
     assert np.array_equal(np.signbit(got[6]), dead == 1)
     np.testing.assert_allclose(got[6], ref[6], rtol=1e-15, atol=0)
     np.testing.assert_allclose(st.radius_numpy(), Ro, rtol=1e-14, atol=0)
-    check_merged(got, ref, dead)
+    check_merged(got, ref, dead, 1e-10, {1: 0}, m0=d.m, dt=d.dt)
 
 
 def test_batched_step_parity(genga):
