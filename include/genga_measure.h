@@ -52,6 +52,31 @@ genga_status genga_set_kernel_variant(genga_ctx *ctx, int32_t variant);
  * size has not been tuned yet), and the number of variants; HOST memory. */
 genga_status genga_get_kernel_variant(genga_ctx *ctx, int32_t N, int32_t *variant, int32_t *num_variants);
 
+/* Shape of FP32 pass variant `variant` (HOST memory outputs): kind 0 = the
+ * one-sided pass (every ordered pair from the side of its i-body), 1 = the
+ * mutual pass (each unordered pair once, its terms added to both bodies);
+ * consumer warps per CTA, i-bodies per thread, resident CTAs per SM.
+ * Out-of-range variant: GENGA_ERR_INVALID_ARG. */
+genga_status genga_kernel_variant_info(int32_t variant, int32_t *kind, int32_t *warps, int32_t *bodies_per_thread,
+                                       int32_t *ctas_per_sm);
+
+/* Name of the most recent CUDA runtime error (cudaGetErrorName) that an
+ * entry point called from this thread turned into GENGA_ERR_CUDA, or
+ * "cudaSuccess" if none has; a static string. */
+const char *genga_last_cuda_error(void);
+
+/* Failure-detection test hook for the bounded waits of the FP32 passes
+ * (every mbarrier wait of a pass gives up after a time limit, sets
+ * GENGA_ERR_TIMEOUT in the sticky status and returns, so a stalled pipeline
+ * ends the kernel instead of hanging the GPU).  wait_ns_log2 > 0 sets that
+ * limit to 2^wait_ns_log2 ns (0: the default of 2 s); hold != 0 makes each
+ * CTA's producer warp return before it fills its first ring slot, without
+ * issuing any copy, so that the consumers' waits run out and the next
+ * genga_get_status returns GENGA_ERR_TIMEOUT; the context stays usable.  Both
+ * are off by default and stay set until changed.  wait_ns_log2 outside
+ * [0, 40]: GENGA_ERR_INVALID_ARG. */
+genga_status genga_set_test_waits(genga_ctx *ctx, int32_t wait_ns_log2, int32_t hold);
+
 /* Step graphs: genga_step and genga_step_batched capture a CUDA graph of 4
  * steps (one rebuild of the spatial order per block) and replay it for the
  * whole 4-step blocks of a call, once the order has just been rebuilt and the

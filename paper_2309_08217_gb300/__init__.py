@@ -51,7 +51,10 @@ class genga_system(C.Structure):
 class GengaError(RuntimeError):
     def __init__(self, code, where=""):
         self.code = int(code)
-        super().__init__(f"{where}: {genga_status_string(code)} (code {code})")
+        extra = ""
+        if self.code == GENGA_ERR_CUDA and _lib is not None:
+            extra = f", {_lib.genga_last_cuda_error().decode()}"
+        super().__init__(f"{where}: {genga_status_string(code)} (code {code}{extra})")
 
 
 _lib = None
@@ -89,6 +92,9 @@ def load():
             "genga_profile_read": ([V, C.POINTER(C.c_double), C.POINTER(C.c_int32), I], I),
             "genga_measure_alu_peaks": ([I, C.POINTER(C.c_double), C.POINTER(C.c_double)], I),
             "genga_set_kernel_variant": ([V, I], I),
+            "genga_set_test_waits": ([V, I, I], I),
+            "genga_last_cuda_error": ([], C.c_char_p),
+            "genga_kernel_variant_info": ([I] + [C.POINTER(I)] * 4, I),
             "genga_set_step_graphs": ([V, I], I),
             "genga_kick_noalloc": ([S, P, D, V, V], I),
             "genga_measure_fma2_peak": ([I, C.POINTER(C.c_double)], I),
@@ -344,6 +350,19 @@ def genga_set_step_graphs(ctx, enable=True):
 def genga_set_kernel_variant(ctx, variant=-1):
     """Force an FP32 pass variant (>= 0) or return to autotuning (-1)."""
     _check(load().genga_set_kernel_variant(_ctx(ctx), int(variant)), "genga_set_kernel_variant")
+
+
+def genga_kernel_variant_info(variant):
+    """{'kind': 0 one-sided / 1 mutual, 'warps', 'bodies_per_thread', 'ctas_per_sm'} of an FP32 variant."""
+    vals = [C.c_int32() for _ in range(4)]
+    _check(load().genga_kernel_variant_info(int(variant), *[C.byref(v) for v in vals]), "genga_kernel_variant_info")
+    return dict(zip(("kind", "warps", "bodies_per_thread", "ctas_per_sm"), (v.value for v in vals)))
+
+
+def genga_set_test_waits(ctx, wait_ns_log2=0, hold=False):
+    """Test hook of the FP32 passes' bounded waits: limit 2^wait_ns_log2 ns
+    (0: the default 2 s); hold: the producers withhold their first stage."""
+    _check(load().genga_set_test_waits(_ctx(ctx), int(wait_ns_log2), int(bool(hold))), "genga_set_test_waits")
 
 
 def genga_get_kernel_variant(ctx, N):

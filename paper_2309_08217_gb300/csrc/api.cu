@@ -27,6 +27,16 @@ struct DeviceGuard {  // run on the context's device, restore the caller's after
 
 inline bool is_fin(double v) { return isfinite(v) != 0; }
 
+// The most recent CUDA error an entry point of this thread turned into
+// GENGA_ERR_CUDA (genga_last_cuda_error, genga_measure.h).
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
+inline genga_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return GENGA_OK;
+    g_last_cuda_error = e;
+    return GENGA_ERR_CUDA;
+}
+
 genga_status check_params(const genga_params *p) {
     if (!p) return GENGA_ERR_INVALID_ARG;
     if (!is_fin(p->G) || p->G < 0.0) return GENGA_ERR_INVALID_ARG;
@@ -75,6 +85,12 @@ PassArgs base_args(genga_ctx *c, const genga_system &sys, const genga_params &p)
     a.hi = c->pk_hi;
     a.hit = c->pk_t;
     a.hid = c->pk_d;
+    a.rel = c->pk_r;
+    a.rell = c->pk_rl;
+    a.gctr = c->gctr;
+    a.mp = MutualPlan{0, 0, 0, 0, 0, 0, nullptr, nullptr};
+    a.wait_ns_log2 = c->test_wait_log2;
+    a.hold = c->test_hold;
     a.lo = c->pk_lo;
     a.p64 = c->pk64;
     a.scr = c->scr;
@@ -119,15 +135,56 @@ PassArgs base_args(genga_ctx *c, const genga_system &sys, const genga_params &p)
     return a;
 }
 
+inline int num_all_variants() { return num_fp32_variants() + num_mutual_variants(); }
+inline bool is_mutual(int v) { return v >= num_fp32_variants(); }
+
+// Launches the pass of FP32 variant v (one-sided or mutual) with the work plan
+// for a.N bodies; *mp gets the mutual plan (the combine needs it).  False when
+// a mutual plan cannot be had (built during a capture): nothing launched.
+bool launch_fp32_variant(genga_ctx *c, PassArgs a, int v, cudaStream_t s, MutualPlan *mp, int *split,
+                         int *one_row, cudaError_t *err) {
+    *err = cudaSuccess;
+    if (is_mutual(v)) {
+        if (!mutual_plan(c, a.N, v - num_fp32_variants(), s, mp)) return false;
+        a.partial = c->partial;  // a mutual plan may have enlarged (reallocated) the partial rows
+        a.mp = *mp;
+        *split = 0;
+        *one_row = 0;
+        *err = launch_pass_mutual(a, v - num_fp32_variants(), c->sm_count, s);
+        return true;
+    }
+    int grid = 1;
+    a.partial = c->partial;  // the rows may have been reallocated since `a` was filled (tuning)
+    plan_pass(a.N, GENGA_FP32, v, c->sm_count, c->partial_cap, &a, &grid);
+    *split = a.split;
+    *one_row = a.tp_rows_end;
+    *err = launch_pass(a, GENGA_FP32, v, grid, s);
+    return true;
+}
+
+cudaError_t launch_combine_any(genga_ctx *c, bool mutual, const MutualPlan &mp, int split, int one_row, int N,
+                               int fp64_rows, double tau, double *acc, const genga_system &sys, cudaStream_t s) {
+    if (mutual)
+        return launch_combine_mutual(c->partial, mp, N, npad_of(N), c->perm, tau, acc, sys.vx, sys.vy, sys.vz,
+                                     c->status, s);
+    return launch_combine(c->partial, split, one_row, N, npad_of(N), fp64_rows, c->perm, tau, acc, sys.vx, sys.vy,
+                          sys.vz, c->status, s);
+}
+
 // The FP32 pass variant for this size: forced, already tuned, or tuned now.
 // Tuning runs every variant's pass and combine (with no kick applied) four
 // times on the packed state (the encounter list is cleared after each run)
-// and keeps the variant with the fastest of its last three runs; it synchronises the stream, so it is skipped while
-// the stream is captured.
+// and keeps the variant with the fastest of its last three runs; it
+// synchronises the stream, so it is skipped while the stream is captured.
+// Test-particle mode 2 has its own table over the one-sided variants (the
+// mutual pass does not implement it); a forced mutual variant falls back to
+// variant 0 there.
 int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
-    if (c->forced_variant >= 0) return c->forced_variant;
+    const bool tp2 = base.n_big >= 0;
+    if (c->forced_variant >= 0) return (tp2 && is_mutual(c->forced_variant)) ? 0 : c->forced_variant;
     const int b = size_bucket(N);
-    if (c->f32_variant[b] >= 0) return c->f32_variant[b];
+    int8_t *table = tp2 ? c->f32_variant_tp : c->f32_variant;
+    if (table[b] >= 0) return table[b];
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 0;
     cudaEvent_t e0, e1;
@@ -138,17 +195,19 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
     }
     int best = 0;
     float best_ms = 3.0e38f;
-    for (int v = 0; v < num_fp32_variants(); v++) {
-        PassArgs a = base;
-        int grid = 1;
-        plan_pass(N, GENGA_FP32, v, c->sm_count, c->partial_cap, &a, &grid);
+    const int nv = tp2 ? num_fp32_variants() : num_all_variants();
+    for (int v = 0; v < nv; v++) {
         float ms = 3.0e38f;
         for (int rep = 0; rep < 4; rep++) {  // pass + combine (no kick applied, no output)
+            MutualPlan mp{};
+            int split = 1, one_row = 0;
+            cudaError_t e = cudaSuccess;
             cudaEventRecord(e0, s);
-            cudaError_t e = launch_pass(a, GENGA_FP32, v, grid, s);
+            if (!launch_fp32_variant(c, base, v, s, &mp, &split, &one_row, &e)) break;
+            genga_system none{};
+            none.N = N;
             if (e == cudaSuccess)
-                e = launch_combine(c->partial, a.split, a.tp_rows_end, N, a.npad, 0, c->perm, 0.0, nullptr, nullptr, nullptr, nullptr,
-                                   c->status, s);
+                e = launch_combine_any(c, is_mutual(v), mp, split, one_row, N, 0, 0.0, nullptr, none, s);
             cudaEventRecord(e1, s);
             cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s);
             if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
@@ -156,7 +215,7 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
             cudaEventElapsedTime(&t, e0, e1);
             if (rep > 0 && t < ms) ms = t;
         }
-        if (v < GENGA_MAX_VARIANTS) c->tune_ms[b][v] = ms;
+        if (!tp2 && v < GENGA_MAX_VARIANTS) c->tune_ms[b][v] = ms < 3.0e38f ? ms : 0.f;
         if (ms < best_ms) {
             best_ms = ms;
             best = v;
@@ -164,16 +223,23 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->f32_variant[b] = (int8_t)best;
+    table[b] = (int8_t)best;
     return best;
 }
 
+// Result of a long-range pass: where its partial sums are and how to combine them.
+struct PassOut {
+    int split = 1, one_row = 0;
+    bool mutual = false;
+    MutualPlan mp{};
+};
+
 // Long-range pass over the current state: momentum (and list reset), the
 // spatial order (skipped when the positions are those of the previous pass),
-// prep, pass, and the sort of the encounter list.  Leaves FP64 partials in
+// prep, pass, and the sort of the encounter list.  Leaves the partial sums in
 // c->partial, indexed by position in the spatial order.
 cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &p, int precision, bool reorder,
-                     int *split_out, cudaStream_t s, bool momentum_valid = false, int *one_row_out = nullptr) {
+                     PassOut *out, cudaStream_t s, bool momentum_valid = false) {
     // momentum_valid: c->mom already holds P of this state (genga_step after a drift)
     cudaError_t e = momentum_valid ? cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s)
                                    : launch_momentum(sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->mom, c->enc_count, s);
@@ -189,29 +255,38 @@ cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &
     if ((e = launch_prep(sys, p, c, s)) != cudaSuccess) return e;
     c->launches += 1;
     PassArgs a = base_args(c, sys, p);
-    const int variant = (precision == GENGA_FP32) ? fp32_variant(c, a, sys.N, s) : 0;
-    int grid = 1;
-    plan_pass(sys.N, precision, variant, c->sm_count, c->partial_cap, &a, &grid);
-    const int split = a.split;
+    *out = PassOut{};
     profile_before_pass(c, s);
-    e = launch_pass(a, precision, variant, grid, s);
+    if (precision == GENGA_FP32) {
+        int variant = fp32_variant(c, a, sys.N, s);
+        if (is_mutual(variant) && p.n_big >= 0) variant = 0;
+        out->mutual = is_mutual(variant);
+        if (!launch_fp32_variant(c, a, variant, s, &out->mp, &out->split, &out->one_row, &e)) {
+            out->mutual = false;  // no mutual plan now (a capture): the one-sided default
+            launch_fp32_variant(c, a, 0, s, &out->mp, &out->split, &out->one_row, &e);
+        }
+    } else {
+        int grid = 1;
+        plan_pass(sys.N, precision, 0, c->sm_count, c->partial_cap, &a, &grid);
+        out->split = a.split;
+        out->one_row = a.tp_rows_end;
+        e = launch_pass(a, precision, 0, grid, s);
+    }
     profile_after_pass(c, s);
     if (e != cudaSuccess) return e;
     c->launches += 1;
     c->enc_sorted = false;  // sorted when the list is read
-    *split_out = split;
-    if (one_row_out) *one_row_out = a.tp_rows_end;
     return cudaSuccess;
 }
 
 cudaError_t run_kick(genga_ctx *c, const genga_system &sys, const genga_params &p, double tau, double *acc,
                      bool reorder, cudaStream_t s, bool momentum_valid = false) {
-    int split = 1, one_row = 0;
-    cudaError_t e = run_pass(c, sys, p, p.precision, reorder, &split, s, momentum_valid, &one_row);
+    PassOut po;
+    cudaError_t e = run_pass(c, sys, p, p.precision, reorder, &po, s, momentum_valid);
     if (e != cudaSuccess) return e;
     c->launches += 1;
-    return launch_combine(c->partial, split, one_row, sys.N, npad_of(sys.N), p.precision == GENGA_FP64 ? 1 : 0,
-                          c->perm, tau, acc, sys.vx, sys.vy, sys.vz, c->status, s);
+    return launch_combine_any(c, po.mutual, po.mp, po.split, po.one_row, sys.N, p.precision == GENGA_FP64 ? 1 : 0,
+                              tau, acc, sys, s);
 }
 
 // ------------------------------------------------------------ batched mode
@@ -333,7 +408,7 @@ cudaError_t run_kick_batched(genga_ctx *c, const genga_system &all, const int32_
     c->launches += 1;
     PassArgs a = base_args(c, all, p);
     a.npad = bb.npad_total;
-    const int variant = c->forced_variant >= 0 ? c->forced_variant : 0;
+    const int variant = (c->forced_variant >= 0 && !is_mutual(c->forced_variant)) ? c->forced_variant : 0;
     BatchItems bi;
     int grid = 1;
     if (!plan_batch(c, bb, variant, &bi, &grid)) return cudaErrorInvalidValue;
@@ -411,7 +486,9 @@ bool step_graph(genga_ctx *c, unsigned long long key, Block block) {
     return true;
 }
 
-bool fp32_tuned(const genga_ctx *c, int N) { return c->forced_variant >= 0 || c->f32_variant[size_bucket(N)] >= 0; }
+bool fp32_tuned(const genga_ctx *c, int N, int n_big) {
+    return c->forced_variant >= 0 || (n_big >= 0 ? c->f32_variant_tp : c->f32_variant)[size_bucket(N)] >= 0;
+}
 
 template <class T>
 cudaError_t alloc(T **p, size_t n) {
@@ -479,9 +556,11 @@ void genga_destroy(genga_ctx *c) {
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
     profile_free(c);
+    free_mutual_cache(c);
     if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    void *bufs[] = {c->pk_hi,       c->pk_t,        c->pk_d,        c->pk_lo,       c->pk64,        c->scr,      c->gbox_lo,    c->gbox_hi,    c->gflag,
+    void *bufs[] = {c->pk_r,        c->pk_rl,       c->gctr,
+                    c->pk_hi,       c->pk_t,        c->pk_d,        c->pk_lo,       c->pk64,        c->scr,      c->gbox_lo,    c->gbox_hi,    c->gflag,
                     c->perm,        c->ord_keys[0], c->ord_keys[1], c->ord_vals[0], c->ord_vals[1], c->ord_hist,
                     c->ord_rbits,   c->a_osc,       c->rc_eq1,      c->partial,  c->mom,        c->enc,
                     c->enc_count,   c->status,      c->energy_part, c->work,   c->Pd,         c->Pd_part,
@@ -513,7 +592,7 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     memset(c, 0, sizeof(*c));
     c->device = device;
     c->max_N = max_N;
-    for (int b = 0; b < 32; b++) c->f32_variant[b] = -1;
+    for (int b = 0; b < 32; b++) c->f32_variant[b] = c->f32_variant_tp[b] = -1;
     c->forced_variant = -1;
     c->ordered_N = -1;
     c->step_graphs = 1;
@@ -534,11 +613,15 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     c->enc_cap = (int32_t)ecap;
     c->energy_blocks = np / 256;
     cudaError_t e = init_pass_kernels();
+    if (e == cudaSuccess) e = init_mutual_kernels();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = alloc(&c->pk_hi, np);
     if (e == cudaSuccess) e = alloc(&c->pk_lo, np);
     if (e == cudaSuccess) e = alloc(&c->pk_t, 4 * (size_t)np);
     if (e == cudaSuccess) e = alloc(&c->pk_d, 2 * (size_t)np);
+    if (e == cudaSuccess) e = alloc(&c->pk_r, 2 * (size_t)np);
+    if (e == cudaSuccess) e = alloc(&c->pk_rl, np);
+    if (e == cudaSuccess) e = alloc(&c->gctr, np / 64);
     if (e == cudaSuccess) e = alloc(&c->pk64, np);
     if (e == cudaSuccess) e = alloc(&c->scr, np);
     if (e == cudaSuccess) e = alloc(&c->gbox_lo, np / 64);
@@ -588,7 +671,7 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         genga_destroy(c);
-        return GENGA_ERR_CUDA;
+        return cuda_status(e);
     }
     *out = c;
     return GENGA_OK;
@@ -602,8 +685,8 @@ genga_status genga_kick(genga_ctx *c, const genga_system *sys, const genga_param
     if (!is_fin(tau)) return GENGA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    if (sys->N == 0) return cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
-    return run_kick(c, *sys, *p, tau, acc, true, s) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
+    if (sys->N == 0) return cuda_status(cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s));
+    return cuda_status(run_kick(c, *sys, *p, tau, acc, true, s));
 }
 
 genga_status genga_drift(genga_ctx *c, genga_system *sys, const genga_params *p, double dt, void *stream) {
@@ -613,9 +696,9 @@ genga_status genga_drift(genga_ctx *c, genga_system *sys, const genga_params *p,
     if (!is_fin(dt)) return GENGA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     genga_system s2 = *sys;
-    if (ensure_levels(c, p->n_levels) != cudaSuccess) return GENGA_ERR_CUDA;
+    if (const cudaError_t e_ = ensure_levels(c, p->n_levels); e_ != cudaSuccess) return cuda_status(e_);
     if (sys->N > 0) c->launches += drift_launches(*p);
-    return launch_drift(s2, *p, dt, c, (cudaStream_t)stream) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
+    return cuda_status(launch_drift(s2, *p, dt, c, (cudaStream_t)stream));
 }
 
 genga_status genga_last_encounters(genga_ctx *c, int32_t *pairs, int32_t capacity, int32_t *count, void *stream) {
@@ -623,7 +706,7 @@ genga_status genga_last_encounters(genga_ctx *c, int32_t *pairs, int32_t capacit
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (!c->enc_sorted) {  // the list is in discovery order until first read
-        if (launch_sort_pairs(c->enc, c->enc_cap, c->enc_count, s) != cudaSuccess) return GENGA_ERR_CUDA;
+        if (const cudaError_t e_ = launch_sort_pairs(c->enc, c->enc_cap, c->enc_count, s); e_ != cudaSuccess) return cuda_status(e_);
         c->enc_sorted = true;
         c->launches += 1;
     }
@@ -642,11 +725,11 @@ genga_status genga_encounters(genga_ctx *c, const genga_system *sys, const genga
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (sys->N == 0) {
-        if (cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return GENGA_ERR_CUDA;
+        if (const cudaError_t e_ = cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s); e_ != cudaSuccess) return cuda_status(e_);
         c->enc_sorted = true;
     } else {
-        int split;
-        if (run_pass(c, *sys, *p, GENGA_FP32, true, &split, s) != cudaSuccess) return GENGA_ERR_CUDA;
+        PassOut po;
+        if (const cudaError_t e_ = run_pass(c, *sys, *p, GENGA_FP32, true, &po, s); e_ != cudaSuccess) return cuda_status(e_);
     }
     return genga_last_encounters(c, pairs, capacity, count, stream);
 }
@@ -659,7 +742,7 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (sys->N == 0 || nsteps == 0) return GENGA_OK;
-    if (ensure_levels(c, p->n_levels) != cudaSuccess) return GENGA_ERR_CUDA;
+    if (const cudaError_t e_ = ensure_levels(c, p->n_levels); e_ != cudaSuccess) return cuda_status(e_);
     genga_system s2 = *sys;
     const double h = 0.5 * p->dt;
     genga_params p_close = *p;  // the closing kick of a step: no predicted entries
@@ -683,14 +766,20 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
     int k = 0;
     auto aligned = [&]() {
         return c->steps_since_order == 0 && c->ordered_N == s2.N && c->ordered_nbig == p->n_big &&
-               (p->precision != GENGA_FP32 || fp32_tuned(c, s2.N));
+               (p->precision != GENGA_FP32 || fp32_tuned(c, s2.N, p->n_big));
     };
     for (; k < nsteps && !(aligned() && nsteps - k >= GENGA_REORDER_STEPS); k++)
-        if (one_step(s) != cudaSuccess) return GENGA_ERR_CUDA;
+        if (const cudaError_t e_ = one_step(s); e_ != cudaSuccess) return cuda_status(e_);
     if (k < nsteps && graphs_usable(c)) {
-        const int variant = p->precision == GENGA_FP32 ? (c->forced_variant >= 0 ? c->forced_variant
-                                                                                 : c->f32_variant[size_bucket(s2.N)])
-                                                       : -1;
+        int variant = -1;
+        if (p->precision == GENGA_FP32) {
+            PassArgs pa = base_args(c, s2, *p);
+            variant = fp32_variant(c, pa, s2.N, s);  // tuned already (aligned() holds)
+            if (is_mutual(variant) && p->n_big < 0) {
+                MutualPlan mp;  // the plan is built outside the capture
+                if (!mutual_plan(c, s2.N, variant - num_fp32_variants(), s, &mp)) variant = 0;
+            }
+        }
         const unsigned long long key = step_key(s2, *p, variant, 0);
         const bool ok = step_graph(c, key, [&](cudaStream_t q) {
             for (int b = 0; b < GENGA_REORDER_STEPS; b++) {
@@ -701,14 +790,14 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
         });
         if (ok) {
             for (; nsteps - k >= GENGA_REORDER_STEPS; k += GENGA_REORDER_STEPS) {
-                if (cudaGraphLaunch(c->step_exec, s) != cudaSuccess) return GENGA_ERR_CUDA;
+                if (const cudaError_t e_ = cudaGraphLaunch(c->step_exec, s); e_ != cudaSuccess) return cuda_status(e_);
                 c->launches += c->step_launches;
             }
             c->enc_sorted = false;
         }
     }
     for (; k < nsteps; k++)
-        if (one_step(s) != cudaSuccess) return GENGA_ERR_CUDA;
+        if (const cudaError_t e_ = one_step(s); e_ != cudaSuccess) return cuda_status(e_);
     return GENGA_OK;
 }
 
@@ -720,10 +809,10 @@ genga_status genga_kick_batched(genga_ctx *c, const genga_system *all, const int
     if (p->precision != GENGA_FP32 || !is_fin(tau) || !check_offsets(c, all, offsets, D)) return GENGA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    if (all->N == 0) return cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s) == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
+    if (all->N == 0) return cuda_status(cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s));
     const cudaError_t e = run_kick_batched(c, *all, offsets, D, *p, tau, acc, true, false, s);
     if (e == cudaErrorInvalidValue) return GENGA_ERR_INVALID_ARG;
-    return e == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
+    return cuda_status(e);
 }
 
 genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *offsets, int32_t D,
@@ -735,7 +824,7 @@ genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (all->N == 0 || nsteps == 0) return GENGA_OK;
-    if (ensure_levels(c, p->n_levels) != cudaSuccess) return GENGA_ERR_CUDA;
+    if (const cudaError_t e_ = ensure_levels(c, p->n_levels); e_ != cudaSuccess) return cuda_status(e_);
     genga_system a2 = *all;
     const BatchBodies bb = batch_bodies(offsets, D);
     const unsigned long long layout = offsets_hash(offsets, D);
@@ -761,7 +850,7 @@ genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *
         if (e != cudaSuccess) return status_of(e);
     }
     if (k < nsteps && graphs_usable(c)) {
-        const int variant = c->forced_variant >= 0 ? c->forced_variant : 0;
+        const int variant = (c->forced_variant >= 0 && !is_mutual(c->forced_variant)) ? c->forced_variant : 0;
         const unsigned long long key = step_key(a2, *p, variant, mix(layout, 0xba7c4ull));
         const bool ok = step_graph(c, key, [&](cudaStream_t q) {
             for (int b = 0; b < GENGA_REORDER_STEPS; b++) {
@@ -772,7 +861,7 @@ genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *
         });
         if (ok) {
             for (; nsteps - k >= GENGA_REORDER_STEPS; k += GENGA_REORDER_STEPS) {
-                if (cudaGraphLaunch(c->step_exec, s) != cudaSuccess) return GENGA_ERR_CUDA;
+                if (const cudaError_t e_ = cudaGraphLaunch(c->step_exec, s); e_ != cudaSuccess) return cuda_status(e_);
                 c->launches += c->step_launches;
             }
             c->enc_sorted = false;
@@ -794,7 +883,7 @@ genga_status genga_energy(genga_ctx *c, const genga_system *sys, const genga_par
     cudaStream_t s = (cudaStream_t)stream;
     for (int k = 0; k < 4; k++) E_L[k] = 0.0;
     if (sys->N == 0) return GENGA_OK;
-    if (launch_energy(*sys, *p, c, s) != cudaSuccess) return GENGA_ERR_CUDA;
+    if (const cudaError_t e_ = launch_energy(*sys, *p, c, s); e_ != cudaSuccess) return cuda_status(e_);
     if (launch_momentum(sys->vx, sys->vy, sys->vz, sys->m, sys->N, c->mom, nullptr, s) != cudaSuccess)
         return GENGA_ERR_CUDA;
     const int nb = (sys->N + 255) / 256;
@@ -835,7 +924,7 @@ genga_status genga_compact(genga_ctx *c, genga_system *sys, int32_t *id, void *s
     int32_t n = sys->N;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&n, c->gcount, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return GENGA_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_status(e);
     c->launches += 4;
     if (n != sys->N) {  // the order, the list and the step graph belong to the old arrays
         c->ordered_N = -1;
@@ -928,8 +1017,10 @@ genga_status genga_tune_levels(genga_ctx *c, const genga_system *sys, const geng
     }
     c->ordered_N = -1;  // the order and the step graph were built on the copy
     if (st != GENGA_OK) return st;
-    return e == cudaSuccess ? GENGA_OK : GENGA_ERR_CUDA;
+    return cuda_status(e);
 }
+
+const char *genga_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_error); }
 
 genga_status genga_get_status(genga_ctx *c, void *stream) {
     if (!c) return GENGA_ERR_INVALID_ARG;
@@ -939,7 +1030,7 @@ genga_status genga_get_status(genga_ctx *c, void *stream) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&bits, c->status, sizeof(bits), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(bits));
-    if (e != cudaSuccess) return GENGA_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_status(e);
     for (int code = 1; code <= 7; code++)
         if (bits & GENGA_BIT(code)) return (genga_status)code;
     return GENGA_OK;

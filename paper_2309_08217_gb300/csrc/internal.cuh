@@ -56,6 +56,29 @@ struct Profile {                // CUDA event pairs around pass launches
 
 #define GENGA_MAX_VARIANTS 16  // FP32 pass variants the context records tuning times for
 #define GENGA_MAX_TIERS 8      // chunk-length tiers of an FP32 pass plan
+#define GENGA_MUTUAL_MAX_ITEMS 16384  // work items of one mutual FP32 pass plan
+
+namespace genga {
+// Work plan of the mutual (symmetric) FP32 pass over one system of
+// `ngroups` 64-body groups, in i-blocks of gpb groups (i-tiles of NP groups,
+// one per consumer warp).  Pairs inside a block are evaluated one-sided by
+// its diagonal items: every warp takes its i-tile against a range of the
+// block's own groups (each ordered pair once, i-side only).  Pairs between
+// blocks are evaluated once, for both bodies, by the strip items of the
+// earlier block: chunks of the groups after it.  Item q of the table is
+// {block, first group, end group, i-row}: the partial row the item writes for
+// the block's bodies (each row 3 x npad double-float pairs): diagonal items
+// rows 0 .. cnt.x - 1, strip chunks rows S .. S + cnt.y - 1 (S = the most
+// diagonal items of any block); strip items of block b also write j-row
+// irows + b for the groups they cover.  A body of block B sums i-rows
+// [0, cnt.x), [S, S + cnt.y) and j-rows irows + [0, B).
+struct MutualPlan {
+    int32_t nb, gpb, ngroups, items, irows, S;
+    const int4 *item;           // [items] {block, first group, end group, i-row}
+    const int2 *blk;            // [nb] {diagonal items, strip chunks} of each block
+};
+struct MutualCache;             // host plans per (N, variant), mutual.cu
+}  // namespace genga
 
 namespace genga {
 // The groups of one level: the layout the grouping kernel writes (members of
@@ -82,6 +105,9 @@ struct genga_ctx {
     float4 *pk_lo;             // [npad] {x - x_hi, y - y_hi, z - z_hi, 0}
     float *pk_t;               // [4 npad] tile-blocked {x_hi}, {y_hi}, {z_hi}, {G m} per 256 bodies
     float4 *pk_d;              // [2 npad] duplicated pairs {x_hi, x_hi, y_hi, y_hi}, {z_hi, z_hi, G m, G m}
+    float4 *pk_r;              // [2 npad] group-centred {X, X, Y, Y}, {Z, Z, G m, G m}, X = fl32(x - c_group)
+    float4 *pk_rl;             // [npad] their residuals {x - c - X, y - c - Y, z - c - Z, test particle}
+    float4 *gctr;              // [npad / 64] group centre c (FP32) and the precision distance of the group
     double4_32a *pk64;             // [npad] {x, y, z, G m}
     float2 *scr;               // [npad] screening bound factors {H_i, A_i} (rounded up)
     float4 *gbox_lo;           // [npad / 64] per 64-body group: {min x, min y, min z, max H}
@@ -108,6 +134,9 @@ struct genga_ctx {
     genga::Profile *prof;      // measurement hooks (genga_measure.h), NULL when unused
     int32_t *work;             // [1] work-item counter of the persistent pass
     int8_t f32_variant[32];    // autotuned FP32 pass variant per log2(npad) bucket, -1 = not tuned
+    int8_t f32_variant_tp[32]; // the same for test-particle mode 2 (one-sided variants only)
+    int32_t test_wait_log2;    // test hook: bounded waits of the FP32 passes give up after 2^this ns (0: 2 s)
+    int32_t test_hold;         // test hook: the FP32 passes' producers withhold their first stage
     float tune_ms[32][GENGA_MAX_VARIANTS];  // the autotuner's time of each variant per bucket
     int32_t forced_variant;    // >= 0: use this FP32 variant (genga_set_kernel_variant)
     int32_t steps_since_order; // genga_step: drifts since the spatial order was built
@@ -140,6 +169,7 @@ struct genga_ctx {
     double *Pd;                // [3 * GENGA_MAX_DISCS] momentum of each system (batched mode)
     double *Pd_part;           // [3 * GENGA_MAX_DISCS] scratch
     size_t partial_cap;        // doubles in `partial`
+    genga::MutualCache *mcache;  // plans of the mutual FP32 pass (mutual.cu), NULL until first used
 };
 
 // -------------------------------------------------------------- launchers
@@ -182,6 +212,8 @@ struct PassArgs {               // one long-range pass
     const float4 *hi, *lo;
     const float *hit;           // tile-blocked copy of hi
     const float4 *hid;          // duplicated-pair copy of hi (two float4 per body)
+    const float4 *rel, *rell;   // group-centred copy and residuals (mutual pass)
+    const float4 *gctr;         // group centres and precision distances (mutual pass)
     const double4_32a *p64;
     const float2 *scr;
     const float4 *gbox_lo, *gbox_hi;
@@ -216,6 +248,9 @@ struct PassArgs {               // one long-range pass
     int32_t tp_b0, tp_t0;
     int32_t tp_rows_end;        // packed positions below it have one partial row (tp_b0 i-blocks)
     int32_t tier_len[GENGA_MAX_TIERS], tier_n[GENGA_MAX_TIERS];
+    MutualPlan mp;              // mutual FP32 pass (variants of kind mutual)
+    int32_t wait_ns_log2;       // > 0: bounded waits give up after 2^this ns (test hook); 0: GENGA_WAIT_LIMIT_NS
+    int32_t hold;               // test hook: the producer withholds its first stage (no copy issued)
 };
 
 struct GroupArgs {              // grouping of the encounter pairs (one CTA)
@@ -286,7 +321,18 @@ cudaError_t launch_order(const genga_system &sys, double Mstar, int n_big, genga
 size_t order_hist_entries(int nmax);
 cudaError_t init_pass_kernels();
 cudaError_t launch_pass(const PassArgs &a, int precision, int variant, int grid, cudaStream_t s);
-int num_fp32_variants();
+int num_fp32_variants();               // one-sided FP32 pass variants (kick.cu)
+// mutual FP32 pass (mutual.cu): variants numbered after the one-sided ones
+int num_mutual_variants();
+void fp32_variant_shape(int variant, int *cw, int *bpt, int *ctas_per_sm);
+void mutual_variant_shape(int v, int *cw, int *bpt);
+bool mutual_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P);
+void free_mutual_cache(genga_ctx *c);
+cudaError_t init_mutual_kernels();
+cudaError_t launch_pass_mutual(const PassArgs &a, int v, int sm_count, cudaStream_t s);
+cudaError_t launch_combine_mutual(const double *partial, const MutualPlan &P, int N, int npad, const uint32_t *perm,
+                                  double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
+                                  cudaStream_t s);
 void plan_pass(int N, int precision, int variant, int sm_count, size_t partial_cap, PassArgs *a, int *grid);
 cudaError_t launch_combine(const double *partial, int split, int one_row_end, int N, int npad, int fp64_rows,
                            const uint32_t *perm,
@@ -399,18 +445,26 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
     return t;
 }
 
-// Wait for phase `parity` of `bar`, at most GENGA_WAIT_LIMIT_NS.  Returns
-// false (and sets the TIMEOUT bit) when the limit is reached.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t *status) {
+// Wait for phase `parity` of `bar`, at most `limit_ns` (GENGA_WAIT_LIMIT_NS
+// by default).  Returns false (and sets the TIMEOUT bit) when the limit is
+// reached.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t *status,
+                                                  uint64_t limit_ns = GENGA_WAIT_LIMIT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     while (!mbar_try_wait(bar, parity)) {
-        if (global_timer_ns() - t0 > GENGA_WAIT_LIMIT_NS) {
+        if (global_timer_ns() - t0 > limit_ns) {
             atomicOr(status, GENGA_BIT(GENGA_ERR_TIMEOUT));
             return false;
         }
     }
     return true;
+}
+
+// The wait limit of a pass: GENGA_WAIT_LIMIT_NS, or 2^wait_ns_log2 ns when the
+// test hook of genga_measure.h has set a short one.
+__device__ __forceinline__ uint64_t pass_wait_limit(int wait_ns_log2) {
+    return wait_ns_log2 > 0 ? (1ull << wait_ns_log2) : GENGA_WAIT_LIMIT_NS;
 }
 
 }  // namespace genga

@@ -187,13 +187,40 @@ genga_status genga_tuning_times(genga_ctx *c, int32_t N, float *ms, int32_t n) {
     int b = 0;
     for (int v = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD; v > 1; v >>= 1) b++;
     b = b < 32 ? b : 31;
-    for (int q = 0; q < n; q++) ms[q] = (q < GENGA_MAX_VARIANTS && q < num_fp32_variants()) ? c->tune_ms[b][q] : 0.f;
+    const int nv = num_fp32_variants() + num_mutual_variants();
+    for (int q = 0; q < n; q++) ms[q] = (q < GENGA_MAX_VARIANTS && q < nv) ? c->tune_ms[b][q] : 0.f;
     return GENGA_OK;
 }
 
 genga_status genga_set_kernel_variant(genga_ctx *c, int32_t variant) {
-    if (!c || variant < -1 || variant >= num_fp32_variants()) return GENGA_ERR_INVALID_ARG;
+    if (!c || variant < -1 || variant >= num_fp32_variants() + num_mutual_variants()) return GENGA_ERR_INVALID_ARG;
     c->forced_variant = variant;
+    return GENGA_OK;
+}
+
+genga_status genga_kernel_variant_info(int32_t variant, int32_t *kind, int32_t *warps, int32_t *bodies_per_thread,
+                                       int32_t *ctas_per_sm) {
+    const int n1 = num_fp32_variants();
+    if (!kind || !warps || !bodies_per_thread || !ctas_per_sm || variant < 0 || variant >= n1 + num_mutual_variants())
+        return GENGA_ERR_INVALID_ARG;
+    int cw = 0, bpt = 0, minb = 1;
+    if (variant < n1) {
+        fp32_variant_shape(variant, &cw, &bpt, &minb);
+        *kind = 0;
+    } else {
+        mutual_variant_shape(variant - n1, &cw, &bpt);
+        *kind = 1;
+    }
+    *warps = cw;
+    *bodies_per_thread = bpt;
+    *ctas_per_sm = minb;
+    return GENGA_OK;
+}
+
+genga_status genga_set_test_waits(genga_ctx *c, int32_t wait_ns_log2, int32_t hold) {
+    if (!c || wait_ns_log2 < 0 || wait_ns_log2 > 40) return GENGA_ERR_INVALID_ARG;
+    c->test_wait_log2 = wait_ns_log2;
+    c->test_hold = hold ? 1 : 0;
     return GENGA_OK;
 }
 
@@ -209,7 +236,7 @@ genga_status genga_get_kernel_variant(genga_ctx *c, int32_t N, int32_t *variant,
     for (int v = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD; v > 1; v >>= 1) b++;
     b = b < 32 ? b : 31;
     *variant = (c->forced_variant >= 0) ? c->forced_variant : c->f32_variant[b];
-    *num_variants = num_fp32_variants();
+    *num_variants = num_fp32_variants() + num_mutual_variants();
     return GENGA_OK;
 }
 

@@ -1,0 +1,927 @@
+// mutual.cu -- the mutual (symmetric) FP32 long-range pass of the kick
+// (Sect. 1, the single-precision long-range forces):
+//
+//   a_i = sum_{j != i} G m_j K(y_ij) (x_j - x_i) / r_ij^3
+//
+// evaluated once per unordered pair {i, j}: the pair's inverse cube serves
+// both bodies, a_i += G m_j r^-3 (x_j - x_i) and a_j += G m_i r^-3 (x_i - x_j)
+// (Newton's third law), so a pair costs 16 FP32 operations for two
+// interactions instead of 12 for one.  The sums and their tolerances are
+// those of the one-sided FP32 pass in kick.cu; only the order of the
+// evaluation changes.
+//
+// Layout.  Bodies in the spatial (Morton) order, 64-body groups.  A CTA has
+// CW consumer warps, one producer warp and one reducer warp.  A CTA's
+// i-block is CW NP groups; consumer warp w holds NP of them in registers,
+// interleaved over the block (groups w, w + CW, w + 2 CW, ...: a j-group
+// next to one part of the block is then near one i-group of several warps,
+// not of one warp only); packed register q holds bodies l and l + 32 of its
+// group q (lane l).  The producer stages one
+// 64-body j-group per ring slot (bulk copies completed on an mbarrier).  In a
+// slot, lane l takes j-body (l + t) mod 32 at step t of a 32-step rotation:
+// it adds the pair's i-side terms to its own i-sums and the j-side terms to a
+// running j-sum that then moves one lane down (shuffle), so after 32 steps
+// every j-sum is back in the lane of its j-body, complete over the warp's
+// i-tile.  The reducer warp adds the CW warps' j-sums of a slot in warp order
+// (double-float) into the j-side partial row of the item's i-block, then
+// frees the slot; so every sum has a fixed order and results are bitwise
+// reproducible.
+//
+// Work.  Items come from a table built on the host (plan_mutual): the
+// diagonal item of each i-block (its own groups; warp w takes tile t of the
+// block if (t - w) mod n lies in [1, n/2) -- or equals n/2 with w < t --, so
+// every pair of tiles is evaluated once, and its own tile one-sided), then
+// chunks of each block's strip (the groups after the block), longest first.
+// A persistent grid takes items from a global counter.
+//
+// Precision.  Offsets come from positions relative to the centre c of the
+// j-group: X_j = fl32(x_j - c) (the FP64 difference rounded, computed by the
+// prep kernel) and X_i = fl32(fl32(x_i,hi - c) + x_i,lo).  A group is FAR for
+// an i-tile when every pair is beyond both the r_crit bound and the group's
+// precision distance (half its half-diagonal), so the offset X_j - X_i is
+// within ~3 u (1 + 2) of x_j - x_i (u = 2^-24): there the pair terms need no
+// screening.  Otherwise (NEAR) the offsets carry the exact residuals, every
+// pair is compared with an FP32 upper bound of r_crit,ij^2, and the pairs
+// under it are evaluated exactly in FP64 afterwards (K-weighted, both sides,
+// encounter list) -- close-encounter forces are always FP64 (Sect. 1).
+// i-sums: FP32 per slot, folded every 4 slots into double-float per-body
+// sums in shared memory, written as the item's i-row at its end.
+#include <algorithm>
+#include <cmath>
+#include <functional>
+#include <new>
+#include <queue>
+#include <vector>
+
+#include "internal.cuh"
+#include "pass_common.cuh"
+
+namespace genga {
+
+struct MutualCache {            // host-built plans, one per FP32 variant slot
+    struct Entry {
+        int N = -1, nb = 0, gpb = 0, ngroups = 0, items = 0, irows = 0, S = 0;
+        bool ok = false;  // false: no plan fits (for this N): one-sided passes instead
+        int4 *d_item = nullptr;
+        int2 *d_blk = nullptr;
+    };
+    Entry e[GENGA_MAX_VARIANTS];
+};
+
+namespace {
+
+constexpr int MG = 64;           // bodies per staged j-group
+constexpr int MUTUAL_MAX_ROWS = 192;  // partial rows a mutual plan may use (its workspace grows to them)
+constexpr int M_FOLD = 4;        // slots between folds of the FP32 i-sums into double-float
+
+struct MHdr {
+    int item, group, flags, pad;  // flags: 1 first slot of the item, 2 last, 4 no more work
+};
+
+__device__ __forceinline__ f32x2 shfl2(f32x2 v, int src) {
+    float a, b;
+    up2(v, a, b);
+    a = __shfl_sync(0xffffffffu, a, src);
+    b = __shfl_sync(0xffffffffu, b, src);
+    return pk2(a, b);
+}
+
+__device__ __forceinline__ f32x2 rsq2(f32x2 r2) {
+    float a, b;
+    up2(r2, a, b);
+    return pk2(rsqrt_sfu(a), rsqrt_sfu(b));
+}
+
+// True when every pair between box u (an i-tile) and box v (a j-group) is
+// beyond the r_crit bound and beyond the group's precision distance.
+__device__ __forceinline__ bool far_mutual(const Box &u, const Box &v, float prec) {
+    if (u.lo.x > u.hi.x || v.lo.x > v.hi.x) return true;  // an empty box: no real body on that side
+    const float gx = fmaxf(0.f, fmaxf(v.lo.x - u.hi.x, u.lo.x - v.hi.x));
+    const float gy = fmaxf(0.f, fmaxf(v.lo.y - u.hi.y, u.lo.y - v.hi.y));
+    const float gz = fmaxf(0.f, fmaxf(v.lo.z - u.hi.z, u.lo.z - v.hi.z));
+    const float gap2 = gx * gx + gy * gy + gz * gz;
+    const float need = fmaxf(fmaxf(u.lo.w, v.lo.w) * fmaxf(u.hi.w, v.hi.w) * (1.0f + 0x1p-10f), prec);
+    return gap2 > need * need;
+}
+
+// x - c = X + residual to ~u^2, where X = fl(fl(xh - c) + xl) is the value
+// the packed loop uses: the rounding error of xh - c (two-sum) plus that of
+// the second addition.
+__device__ __forceinline__ float centred_residual(float xh, float xl, float c, float X) {
+    const float t = xh - c;
+    const float bp = t - xh;
+    const float e = (xh - (t - bp)) + (-c - bp);
+    return e + ((t - X) + xl);
+}
+
+// The exact FP64 treatment of a screened pair (packed positions i, j of one
+// system whose packed range starts at poff, Nd bodies from caller index off):
+// the K-weighted terms on i (fi) and on j (fj).  The encounter pair and the
+// predicted entry are recorded as (smaller, larger) body index -- for every
+// visit when `both` (the pass visits the pair once), else only from the side
+// with the smaller index (the one-sided own tile visits it twice).  Ghosts
+// (mass -0.0) are never pairs.
+__device__ __noinline__ void screened_pair_mutual(const PassArgs &a, int i, int j, int poff, int Nd, int off,
+                                                  bool both, double3 *fi, double3 *fj) {
+    *fi = *fj = make_double3(0.0, 0.0, 0.0);
+    if (i - poff >= Nd || j - poff >= Nd || i == j) return;
+    const double4_32a pi = a.p64[i], pj = a.p64[j];
+    const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 == 0.0) return;  // coincident bodies: no direction, no force
+    const double r = sqrt(r2);
+    const int oi = (int)a.perm[off + i - poff], oj = (int)a.perm[off + j - poff];
+    double rc;
+    if (a.rcrit_mode == GENGA_RCRIT_EQ1) {
+        rc = fmax(a.rc_eq1[i], a.rc_eq1[j]);
+    } else {
+        rc = a.n1 * cbrt((a.m[oi] + a.m[oj]) / (3.0 * a.Mstar)) * 0.5 * (a.a_osc[i] + a.a_osc[j]);
+    }
+    const bool record = both || oi < oj;
+    const bool ghost = signbit(a.m[oi]) || signbit(a.m[oj]);
+    const int lo = oi < oj ? oi : oj, hi = oi < oj ? oj : oi;
+    double K = 1.0;
+    if (r < rc) {
+        if (record && !ghost) {
+            const int pos = atomicAdd(a.enc_count, 1);
+            if (pos < a.enc_cap) a.enc[pos] = make_int2(lo, hi);
+        }
+        K = changeover_K((r / rc - 0.1) / 0.9, a.changeover);
+    } else if (a.predict && record && r < GENGA_PREDICT_RANGE * rc && !ghost) {
+        // straight-line relative motion over the coming drift (rounded
+        // products as written, no contraction; the test is the same from
+        // either side)
+        const double ux = a.vx[oj] - a.vx[oi], uy = a.vy[oj] - a.vy[oi], uz = a.vz[oj] - a.vz[oi];
+        const double uu = __dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
+        const double du = __dadd_rn(__dadd_rn(__dmul_rn(dx, ux), __dmul_rn(dy, uy)), __dmul_rn(dz, uz));
+        double t = uu > 0.0 ? -du / uu : 0.0;
+        const double tlo = a.pred_dt < 0.0 ? a.pred_dt : 0.0, thi = a.pred_dt < 0.0 ? 0.0 : a.pred_dt;
+        t = fmin(fmax(t, tlo), thi);
+        const double px = __dadd_rn(dx, __dmul_rn(ux, t)), py = __dadd_rn(dy, __dmul_rn(uy, t));
+        const double pz = __dadd_rn(dz, __dmul_rn(uz, t));
+        if (__dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz)) < __dmul_rn(rc, rc)) {
+            const int pos = atomicAdd(a.enc_count + 1, 1);
+            if (pos < a.enc_cap) a.pred[pos] = make_int2(lo, hi);
+        }
+    }
+    if (K == 0.0) return;
+    const double s = K / (r2 * r);
+    const double si = pj.w * s, sj = -pi.w * s;
+    *fi = make_double3(si * dx, si * dy, si * dz);
+    *fj = make_double3(sj * dx, sj * dy, sj * dz);
+}
+
+template <int NP, int CW, int STAGES>
+struct MLayout {
+    static constexpr int BPT = 2 * NP, NC = CW * 32;
+    static constexpr size_t r_off = 0;                                         // float4 [STAGES][2 MG]
+    static constexpr size_t l_off = r_off + (size_t)STAGES * 2 * MG * 16;      // float4 [STAGES][MG]
+    static constexpr size_t g_off = l_off + (size_t)STAGES * MG * 16;          // float4 [STAGES][4]
+    static constexpr size_t p_off = g_off + (size_t)STAGES * 4 * 16;           // float [STAGES][CW][3][MG]
+    static constexpr size_t a_off = p_off + (size_t)STAGES * CW * 3 * MG * 4;  // DF [3][BPT][NC]
+    static constexpr size_t i_off = a_off + (size_t)3 * BPT * NC * 8;          // float4 [2][BPT][NC]
+    static constexpr size_t q_off = i_off + (size_t)2 * BPT * NC * 16;         // float4 [CW][NP][2]
+    static constexpr size_t m_off = q_off + (size_t)CW * NP * 2 * 16;          // uint32 [BPT][NC]
+    static constexpr size_t e_off = m_off + (size_t)BPT * NC * 4;              // f32x2 [NP][3][NC]
+    static constexpr size_t b_off = e_off + (size_t)NP * 3 * NC * 8;           // uint64 [3][STAGES]
+    static constexpr size_t h_off = b_off + (size_t)3 * STAGES * 8;            // MHdr [STAGES]
+    static constexpr size_t bytes = h_off + (size_t)STAGES * sizeof(MHdr);
+    static_assert(bytes <= 227 * 1024, "one CTA per SM: at most 227 KB of shared memory");
+};
+
+// Registers per thread: as many as one CTA of `warps` warps per SM allows; a
+// block's warps take registers in units of 4 warps (measured: 14 warps of 144
+// registers do not launch), so the count is that of the next multiple of 4.
+constexpr int mutual_maxreg(int warps) {
+    return ((65536 / (((warps + 3) / 4) * 4 * 32)) / 8 * 8) > 255 ? 255
+                                                                  : ((65536 / (((warps + 3) / 4) * 4 * 32)) / 8 * 8);
+}
+
+template <int NP, int CW, int STAGES, int UNR>
+__global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __grid_constant__ PassArgs a) {
+    using L = MLayout<NP, CW, STAGES>;
+    constexpr int BPT = L::BPT, NC = L::NC;
+    constexpr uint32_t STAGE_BYTES = 2 * MG * 16 + MG * 16 + 3 * 16;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float4 *s_r = reinterpret_cast<float4 *>(smem_raw + L::r_off);
+    float4 *s_l = reinterpret_cast<float4 *>(smem_raw + L::l_off);
+    float4 *s_g = reinterpret_cast<float4 *>(smem_raw + L::g_off);
+    float *s_part = reinterpret_cast<float *>(smem_raw + L::p_off);
+    DF *s_acc = reinterpret_cast<DF *>(smem_raw + L::a_off);
+    float4 *s_ip = reinterpret_cast<float4 *>(smem_raw + L::i_off);
+    float4 *s_qb = reinterpret_cast<float4 *>(smem_raw + L::q_off);
+    uint32_t *mk = reinterpret_cast<uint32_t *>(smem_raw + L::m_off) + threadIdx.x;  // mk[k * NC]: screened pairs of i-body k
+    f32x2 *res = reinterpret_cast<f32x2 *>(smem_raw + L::e_off) + threadIdx.x;     // res[(q * 3 + c) * NC]: residuals
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + L::b_off);
+    uint64_t *pdone = full + STAGES, *empty = pdone + STAGES;
+    MHdr *hdr = reinterpret_cast<MHdr *>(smem_raw + L::h_off);
+
+    const MutualPlan &P = a.mp;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t wlim = pass_wait_limit(a.wait_ns_log2);
+    const size_t np = (size_t)a.npad;
+    float2 *rows = reinterpret_cast<float2 *>(a.partial);
+
+    if (tid == 0) {
+        for (int q = 0; q < STAGES; q++) {
+            mbar_init(&full[q], 1);
+            mbar_init(&pdone[q], CW);
+            mbar_init(&empty[q], 1);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (warp == CW) {  // -------------------------------------------- producer
+        if (lane != 0) return;
+        unsigned n = 0;
+        for (;;) {
+            const int q = atomicAdd(a.work, 1);
+            const bool done = q >= P.items;
+            const int4 it = done ? make_int4(0, 0, 0, 0) : P.item[q];
+            for (int g = it.y; done || g < it.z; g++, n++) {
+                const int slot = n % STAGES;
+                const unsigned u = n / STAGES;
+                if (u > 0 && !mbar_wait_bounded(&empty[slot], (u - 1) & 1, a.status, wlim)) return;
+                if (done) {
+                    hdr[slot] = MHdr{q, 0, 4, 0};
+                    mbar_arrive(&full[slot]);
+                    return;
+                }
+                if (a.hold) return;  // test hook: no stage is ever filled (and no copy issued)
+                hdr[slot] = MHdr{q, g, (g == it.y ? 1 : 0) | (g == it.z - 1 ? 2 : 0), 0};
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&full[slot], STAGE_BYTES);
+                bulk_g2s(s_r + slot * 2 * MG, a.rel + (size_t)g * 2 * MG, 2 * MG * 16, &full[slot]);
+                bulk_g2s(s_l + slot * MG, a.rell + (size_t)g * MG, MG * 16, &full[slot]);
+                bulk_g2s(s_g + slot * 4, a.gbox_lo + g, 16, &full[slot]);
+                bulk_g2s(s_g + slot * 4 + 1, a.gbox_hi + g, 16, &full[slot]);
+                bulk_g2s(s_g + slot * 4 + 2, a.gctr + g, 16, &full[slot]);
+            }
+        }
+    }
+
+    if (warp == CW + 1) {  // ------------------------------------------ reducer
+        float2 *jrow = nullptr;    // NULL: a diagonal item (one-sided, no j-side sums)
+        for (unsigned n = 0;; n++) {
+            const int slot = n % STAGES;
+            const uint32_t par = (n / STAGES) & 1;
+            if (!mbar_wait_bounded(&full[slot], par, a.status, wlim)) return;
+            const MHdr h = hdr[slot];
+            if (h.flags & 4) return;
+            if (!mbar_wait_bounded(&pdone[slot], par, a.status, wlim)) return;
+            if (h.flags & 1) {
+                const int4 it = P.item[h.item];
+                jrow = it.w < P.S ? nullptr : rows + (size_t)(P.irows + it.x) * 3 * np;
+            }
+            if (jrow) {
+                const float *sp = s_part + (size_t)slot * CW * 3 * MG;
+#pragma unroll
+                for (int half = 0; half < 2; half++) {
+                    const int jj = lane + 32 * half;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        DF t{0.f, 0.f};
+#pragma unroll
+                        for (int w = 0; w < CW; w++) t = df_add(t, sp[(w * 3 + c) * MG + jj], 0.f);
+                        jrow[c * np + (size_t)h.group * MG + jj] = make_float2(t.hi, t.lo);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+        }
+    }
+
+    // ---------------------------------------------------------------- consumers
+    const int src = (lane + 1) & 31;  // the rotation: lane l receives lane l+1's j-sums
+    f32x2 MN[NP], TX[NP], TY[NP], TZ[NP];
+#pragma unroll
+    for (int q = 0; q < NP; q++) MN[q] = TX[q] = TY[q] = TZ[q] = 0ull;
+    Box wbox = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    bool in = false, diag = false;
+    int row = 0, gw = 0, nf = 0;
+    unsigned qin = 0u;            // bit q: packed register q holds i-group gw + q CW of the block
+    DF *acc = s_acc + tid;        // acc[(c * BPT + k) * NC]: double-float sums of i-body k, component c
+    float4 *ip = s_ip + tid;      // ip[k * NC]: {x_hi, y_hi, z_hi, H}, ip[(BPT + k) * NC]: {x_lo, y_lo, z_lo, A}
+    float4 *qb = s_qb + warp * NP * 2;  // the boxes of the warp's i-groups
+
+    for (unsigned n = 0;; n++) {
+        const int slot = n % STAGES;
+        if (!mbar_wait_bounded(&full[slot], (n / STAGES) & 1, a.status, wlim)) return;
+        const MHdr h = hdr[slot];
+        if (h.flags & 4) return;
+        if (h.flags & 1) {  // first slot of an item: this warp's i-tile
+            const int4 it = P.item[h.item];
+            row = it.w;
+            diag = row < P.S;
+            // the warp's i-groups are interleaved over the block (gw, gw + CW,
+            // ...), so a j-group next to one part of the block is near one
+            // i-group of several warps rather than all of one warp's
+            const int gb0 = it.x * P.gpb, gb1 = min(gb0 + P.gpb, P.ngroups);
+            gw = gb0 + warp;
+            qin = 0u;
+#pragma unroll
+            for (int q = 0; q < NP; q++)
+                if (gw + q * CW < gb1) qin |= 1u << q;
+            in = qin != 0u;
+            if (in) {
+                const float INF = __int_as_float(0x7f800000);
+#pragma unroll
+                for (int k = 0; k < BPT; k++) {
+                    const bool ok = (qin >> (k >> 1)) & 1u;
+                    const int i = (gw + (k >> 1) * CW) * MG + 32 * (k & 1) + lane;
+                    // an i-group past a partial last block: massless, far away
+                    const float4 hi = ok ? a.hi[i] : make_float4(GENGA_PAD_POS, GENGA_PAD_POS, GENGA_PAD_POS, 0.f);
+                    const float4 lo = ok ? a.lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float2 sc = ok ? a.scr[i] : make_float2(0.f, 0.f);
+                    ip[k * NC] = make_float4(hi.x, hi.y, hi.z, sc.x);
+                    ip[(BPT + k) * NC] = make_float4(lo.x, lo.y, lo.z, sc.y);
+                    if (k & 1) {
+                        float m0, m1;
+                        up2(MN[k >> 1], m0, m1);
+                        MN[k >> 1] = pk2(m0, -hi.w);
+                    } else {
+                        MN[k >> 1] = pk2(-hi.w, 0.f);
+                    }
+                }
+                if (lane < 2 * NP) {
+                    const int q = lane >> 1;
+                    const bool ok = (qin >> q) & 1u;
+                    const float4 empty_lo = make_float4(INF, INF, INF, 0.f), empty_hi = make_float4(-INF, -INF, -INF, 0.f);
+                    qb[lane] = (lane & 1) ? (ok ? a.gbox_hi[gw + q * CW] : empty_hi) : (ok ? a.gbox_lo[gw + q * CW] : empty_lo);
+                }
+#pragma unroll
+                for (int k = 0; k < 3 * BPT; k++) acc[k * NC] = DF{0.f, 0.f};
+            }
+            __syncwarp();
+            if (in) {  // the box of all the warp's i-groups
+                wbox = Box{qb[0], qb[1]};
+#pragma unroll
+                for (int q = 1; q < NP; q++) {
+                    const float4 l = qb[2 * q], u = qb[2 * q + 1];
+                    wbox.lo = make_float4(fminf(wbox.lo.x, l.x), fminf(wbox.lo.y, l.y), fminf(wbox.lo.z, l.z),
+                                          fmaxf(wbox.lo.w, l.w));
+                    wbox.hi = make_float4(fmaxf(wbox.hi.x, u.x), fmaxf(wbox.hi.y, u.y), fmaxf(wbox.hi.z, u.z),
+                                          fmaxf(wbox.hi.w, u.w));
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < NP; q++) TX[q] = TY[q] = TZ[q] = 0ull;
+            nf = 0;
+        }
+        const int g = h.group;
+        float *part = s_part + ((size_t)slot * CW + warp) * 3 * MG;
+        if (in) {
+            // strip items: both sides of every pair; diagonal items: the
+            // i-side only (every ordered pair inside the block is visited)
+            const bool both = !diag;
+            const Box gb = {s_g[slot * 4], s_g[slot * 4 + 1]};
+            const float4 ctr = s_g[slot * 4 + 2];
+            const float4 *tr = s_r + slot * 2 * MG;
+            // the warp's i-bodies relative to the group centre
+            f32x2 XI[NP], YI[NP], ZI[NP];
+#pragma unroll
+            for (int q = 0; q < NP; q++) {
+                const float4 h0 = ip[(2 * q) * NC], h1 = ip[(2 * q + 1) * NC];
+                const float4 l0 = ip[(BPT + 2 * q) * NC], l1 = ip[(BPT + 2 * q + 1) * NC];
+                XI[q] = pk2((h0.x - ctr.x) + l0.x, (h1.x - ctr.x) + l1.x);
+                YI[q] = pk2((h0.y - ctr.y) + l0.y, (h1.y - ctr.y) + l1.y);
+                ZI[q] = pk2((h0.z - ctr.z) + l0.z, (h1.z - ctr.z) + l1.z);
+            }
+            // which i-groups are NEAR the j-group (all of them for a diagonal
+            // item's own tile): a tile FAR as a whole needs no per-group test
+            unsigned qnear = 0u;
+            if (!far_mutual(wbox, gb, ctr.w)) {
+#pragma unroll
+                for (int q = 0; q < NP; q++)
+                    if (!far_mutual(Box{qb[2 * q], qb[2 * q + 1]}, gb, ctr.w)) qnear |= 1u << q;
+            }
+            // ------------------------------------------------ FAR i-groups
+            // plain terms; both sides (strip items) or the i-side only
+            auto far_loop = [&](auto both_tag) {
+                constexpr bool BOTH = decltype(both_tag)::value;
+#pragma unroll 1
+                for (int sb = 0; sb < 2; sb++) {
+                    f32x2 JX = 0ull, JY = 0ull, JZ = 0ull;
+#pragma unroll(UNR)
+                    for (int t = 0; t < 32; t++) {
+                        const int j = sb * 32 + ((lane + t) & 31);
+                        const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(tr + 2 * j);      // {X X}, {Y Y}
+                        const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(tr + 2 * j + 1);  // {Z Z}, {Gm Gm}
+#pragma unroll
+                        for (int q = 0; q < NP; q++) {
+                            const f32x2 DX = sub2(A.x, XI[q]), DY = sub2(A.y, YI[q]), DZ = sub2(B.x, ZI[q]);
+                            const f32x2 R2 = fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
+                            const f32x2 RI = rsq2(R2);
+                            const f32x2 R3 = mul2(mul2(RI, RI), RI);
+                            const f32x2 SI = mul2(B.y, R3);
+                            TX[q] = fma2(SI, DX, TX[q]);
+                            TY[q] = fma2(SI, DY, TY[q]);
+                            TZ[q] = fma2(SI, DZ, TZ[q]);
+                            if constexpr (BOTH) {
+                                const f32x2 SJ = mul2(MN[q], R3);
+                                JX = fma2(SJ, DX, JX);
+                                JY = fma2(SJ, DY, JY);
+                                JZ = fma2(SJ, DZ, JZ);
+                            }
+                        }
+                        if constexpr (BOTH) {
+                            JX = shfl2(JX, src);
+                            JY = shfl2(JY, src);
+                            JZ = shfl2(JZ, src);
+                        }
+                    }
+                    if constexpr (BOTH) {
+                        float u0, u1;
+                        up2(JX, u0, u1);
+                        part[0 * MG + sb * 32 + lane] = u0 + u1;
+                        up2(JY, u0, u1);
+                        part[1 * MG + sb * 32 + lane] = u0 + u1;
+                        up2(JZ, u0, u1);
+                        part[2 * MG + sb * 32 + lane] = u0 + u1;
+                    }
+                }
+            };
+            if (qnear == 0u) {
+                if (both) far_loop(std::true_type{});
+                else far_loop(std::false_type{});
+            } else {
+                // ---------------------------------------------- NEAR i-groups
+                // rotations over QP i-groups at a time: a FAR i-group takes
+                // the plain terms, a NEAR one exact offsets (residuals) with
+                // every pair screened
+                const float4 *tl = s_l + slot * MG;
+                // the group of the warp's own tile (diagonal items): i-body k
+                // meets itself at step 0 of packed register q = the group's
+                // place in the warp's set, half sb; that pair is always
+                // screened out (its FP32 offset is zero only up to rounding)
+                // and the FP64 pass skips i = j
+                const int dg = g - gw;
+                const int gself = (both || dg < 0 || dg % CW != 0 || dg / CW >= NP) ? -1 : dg / CW;
+                // residuals of the NEAR i-groups (shared memory: they are read
+                // only for those) and their screening bounds (the i-group's
+                // largest H and A against the j-group's)
+                float thr[NP];
+#pragma unroll
+                for (int q = 0; q < NP; q++) {
+                    thr[q] = 0.f;
+                    if (qnear & (1u << q)) {
+                        const float4 h0 = ip[(2 * q) * NC], h1 = ip[(2 * q + 1) * NC];
+                        const float4 l0 = ip[(BPT + 2 * q) * NC], l1 = ip[(BPT + 2 * q + 1) * NC];
+                        float x0, x1, y0, y1, z0, z1;
+                        up2(XI[q], x0, x1);
+                        up2(YI[q], y0, y1);
+                        up2(ZI[q], z0, z1);
+                        res[(q * 3 + 0) * NC] = pk2(centred_residual(h0.x, l0.x, ctr.x, x0), centred_residual(h1.x, l1.x, ctr.x, x1));
+                        res[(q * 3 + 1) * NC] = pk2(centred_residual(h0.y, l0.y, ctr.y, y0), centred_residual(h1.y, l1.y, ctr.y, y1));
+                        res[(q * 3 + 2) * NC] = pk2(centred_residual(h0.z, l0.z, ctr.z, z0), centred_residual(h1.z, l1.z, ctr.z, z1));
+                        thr[q] = screen_threshold(qb[2 * q].w, qb[2 * q + 1].w, gb.lo.w, gb.hi.w);
+                    }
+                }
+#pragma unroll 1
+                for (int sb = 0; sb < 2; sb++) {
+                    f32x2 JX = 0ull, JY = 0ull, JZ = 0ull;
+                    // bit jj of mk[k * NC]: pair (i_k, j = sb * 32 + jj) is under the screening bound
+#pragma unroll
+                    for (int k = 0; k < BPT; k++) mk[k * NC] = 0u;
+#pragma unroll 1
+                    for (int t = 0; t < 32; t++) {
+                        const int jj = (lane + t) & 31, j = sb * 32 + jj;
+                        const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(tr + 2 * j);
+                        const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(tr + 2 * j + 1);
+                        const float4 R = tl[j];
+#pragma unroll
+                        for (int q = 0; q < NP; q++) {
+                            f32x2 DX = sub2(A.x, XI[q]), DY = sub2(A.y, YI[q]), DZ = sub2(B.x, ZI[q]);
+                            const bool qn = (qnear >> q) & 1u;
+                            if (qn) {
+                                DX = add2(DX, sub2(pk2(R.x, R.x), res[(q * 3 + 0) * NC]));
+                                DY = add2(DY, sub2(pk2(R.y, R.y), res[(q * 3 + 1) * NC]));
+                                DZ = add2(DZ, sub2(pk2(R.z, R.z), res[(q * 3 + 2) * NC]));
+                            }
+                            const f32x2 R2 = fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
+                            const f32x2 RI = rsq2(R2);
+                            const f32x2 R3 = mul2(mul2(RI, RI), RI);
+                            f32x2 SI = mul2(B.y, R3), SJ = mul2(MN[q], R3);
+                            if (qn) {
+                                float ra, rb;
+                                up2(R2, ra, rb);
+                                const bool self = t == 0 && q == gself;
+                                const bool na = ra < thr[q] || (self && sb == 0);
+                                const bool nb = rb < thr[q] || (self && sb == 1);
+                                if (na || nb) {  // rare: screened pairs leave the FP32 sums
+                                    float sa, sb_;
+                                    up2(SI, sa, sb_);
+                                    SI = pk2(na ? 0.f : sa, nb ? 0.f : sb_);
+                                    up2(SJ, sa, sb_);
+                                    SJ = pk2(na ? 0.f : sa, nb ? 0.f : sb_);
+                                    mk[(2 * q) * NC] |= (unsigned)na << jj;
+                                    mk[(2 * q + 1) * NC] |= (unsigned)nb << jj;
+                                }
+                            }
+                            TX[q] = fma2(SI, DX, TX[q]);
+                            TY[q] = fma2(SI, DY, TY[q]);
+                            TZ[q] = fma2(SI, DZ, TZ[q]);
+                            if (both) {
+                                JX = fma2(SJ, DX, JX);
+                                JY = fma2(SJ, DY, JY);
+                                JZ = fma2(SJ, DZ, JZ);
+                            }
+                        }
+                        if (both) {
+                            JX = shfl2(JX, src);
+                            JY = shfl2(JY, src);
+                            JZ = shfl2(JZ, src);
+                        }
+                    }
+                    if (both) {
+                        float u0, u1;
+                        up2(JX, u0, u1);
+                        part[0 * MG + sb * 32 + lane] = u0 + u1;
+                        up2(JY, u0, u1);
+                        part[1 * MG + sb * 32 + lane] = u0 + u1;
+                        up2(JZ, u0, u1);
+                        part[2 * MG + sb * 32 + lane] = u0 + u1;
+                    }
+                    // the screened pairs of this half of the group, exactly in
+                    // FP64: all lanes evaluate one pair each per round; the
+                    // j-side terms are added in lane order (a fixed order)
+                    __syncwarp();
+                    for (;;) {
+                        int kk = -1, jj = 0;
+                        for (int k = 0; k < BPT && kk < 0; k++) {
+                            const unsigned m = mk[k * NC];
+                            if (m) {
+                                kk = k;
+                                jj = __ffs((int)m) - 1;
+                                mk[k * NC] = m & (m - 1u);
+                            }
+                        }
+                        if (!__any_sync(0xffffffffu, kk >= 0)) break;
+                        double3 fi = make_double3(0.0, 0.0, 0.0), fj = fi;
+                        if (kk >= 0) {
+                            const int i = (gw + (kk >> 1) * CW) * MG + 32 * (kk & 1) + lane, j = g * MG + sb * 32 + jj;
+                            screened_pair_mutual(a, i, j, 0, a.N, 0, both, &fi, &fj);
+                            const double f3[3] = {fi.x, fi.y, fi.z};
+#pragma unroll
+                            for (int c = 0; c < 3; c++) {
+                                DF &t = acc[(c * BPT + kk) * NC];
+                                const DF d = df_of_double(f3[c]);
+                                t = df_add(t, d.hi, d.lo);
+                            }
+                        }
+                        if (both) {
+                            const int js = kk >= 0 ? sb * 32 + jj : -1;
+                            const float fx = (float)fj.x, fy = (float)fj.y, fz = (float)fj.z;
+                            for (int s = 0; s < 32; s++) {
+                                const int j2 = __shfl_sync(0xffffffffu, js, s);
+                                const float gx = __shfl_sync(0xffffffffu, fx, s);
+                                const float gy = __shfl_sync(0xffffffffu, fy, s);
+                                const float gz = __shfl_sync(0xffffffffu, fz, s);
+                                if (lane == 0 && j2 >= 0) {
+                                    part[0 * MG + j2] += gx;
+                                    part[1 * MG + j2] += gy;
+                                    part[2 * MG + j2] += gz;
+                                }
+                            }
+                            __syncwarp();
+                        }
+                    }
+                }
+            }
+        } else if (!diag) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) part[c * MG + lane] = part[c * MG + 32 + lane] = 0.f;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&pdone[slot]);  // this warp's j-sums are in; the slot may be reduced
+        if (in) {
+            if (++nf == M_FOLD || (h.flags & 2)) {  // fold the FP32 i-sums into the double-float sums
+#pragma unroll
+                for (int q = 0; q < NP; q++) {
+                    float e, o;
+                    up2(TX[q], e, o);
+                    acc[(0 * BPT + 2 * q) * NC] = df_add(acc[(0 * BPT + 2 * q) * NC], e, 0.f);
+                    acc[(0 * BPT + 2 * q + 1) * NC] = df_add(acc[(0 * BPT + 2 * q + 1) * NC], o, 0.f);
+                    up2(TY[q], e, o);
+                    acc[(1 * BPT + 2 * q) * NC] = df_add(acc[(1 * BPT + 2 * q) * NC], e, 0.f);
+                    acc[(1 * BPT + 2 * q + 1) * NC] = df_add(acc[(1 * BPT + 2 * q + 1) * NC], o, 0.f);
+                    up2(TZ[q], e, o);
+                    acc[(2 * BPT + 2 * q) * NC] = df_add(acc[(2 * BPT + 2 * q) * NC], e, 0.f);
+                    acc[(2 * BPT + 2 * q + 1) * NC] = df_add(acc[(2 * BPT + 2 * q + 1) * NC], o, 0.f);
+                    TX[q] = TY[q] = TZ[q] = 0ull;
+                }
+                nf = 0;
+            }
+            if (h.flags & 2) {  // last slot of the item: its i-row
+                float2 *out = rows + (size_t)row * 3 * np;
+#pragma unroll
+                for (int k = 0; k < BPT; k++) {
+                    if (!((qin >> (k >> 1)) & 1u)) continue;
+                    const size_t i = (size_t)(gw + (k >> 1) * CW) * MG + 32 * (k & 1) + lane;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        const DF t = acc[(c * BPT + k) * NC];
+                        out[c * np + i] = make_float2(t.hi, t.lo);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// One thread per (body, component): the body's i-rows then its j-rows, in
+// row order, in double-float; then the optional acc output and v += acc tau.
+__global__ void combine_mutual_kernel(const double *__restrict__ partial, const __grid_constant__ MutualPlan P,
+                                      int N, int npad, const uint32_t *__restrict__ perm, double tau,
+                                      double *__restrict__ acc, double *__restrict__ vx, double *__restrict__ vy,
+                                      double *__restrict__ vz, uint32_t *__restrict__ status) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (k >= N) return;
+    const int b = k / (P.gpb * MG);
+    const size_t stride = 3 * (size_t)npad;
+    const float2 *p = reinterpret_cast<const float2 *>(partial) + (size_t)c * npad + k;
+    const int2 bk = P.blk[b];
+    // the rows in order: diagonal i-rows, strip i-rows, j-rows of the blocks before b
+    const int n0 = bk.x, n1 = n0 + bk.y, n2 = n1 + b;
+    DF t{0.f, 0.f};
+    constexpr int BATCH = 16;
+    for (int r0 = 0; r0 < n2; r0 += BATCH) {
+        float2 v[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; u++) {
+            const int r = r0 + u;
+            const int rr = r < n0 ? r : r < n1 ? P.S + (r - n0) : P.irows + (r - n1);
+            v[u] = r < n2 ? p[(size_t)rr * stride] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < BATCH; u++)
+            if (r0 + u < n2) t = df_add(t, v[u].x, v[u].y);
+    }
+    const double s = (double)t.hi + (double)t.lo;
+    if (!isfinite(s)) atomicOr(status, GENGA_BIT(GENGA_ERR_NONFINITE));
+    const int i = (int)perm[k];
+    if (acc) acc[c * (size_t)N + i] = s;
+    if (tau != 0.0) {
+        double *v = c == 0 ? vx : (c == 1 ? vy : vz);
+        v[i] += s * tau;
+    }
+}
+
+// --------------------------------------------------------------- variants
+struct MVariant {
+    int np, cw;
+    void (*fn)(const PassArgs);
+    size_t smem;
+};
+#define GENGA_MV(NP, CW, ST, UNR) \
+    {NP, CW, pass_mutual_kernel<NP, CW, ST, UNR>, MLayout<NP, CW, ST>::bytes}
+const MVariant kMVariants[] = {GENGA_MV(4, 10, 4, 2), GENGA_MV(4, 8, 6, 2), GENGA_MV(2, 12, 6, 2)};
+#undef GENGA_MV
+constexpr int kNumMVariants = sizeof(kMVariants) / sizeof(kMVariants[0]);
+
+// ---------------------------------------------------------------- planner
+// Cost model, in units of one slot of far pairs for both sides (every warp
+// on one group): groups next to an i-block (its own, in the diagonal items,
+// evaluated one-sided; the first near_span groups of its strip) are mostly
+// NEAR and cost about DIAG_COST and NEAR_COST.
+constexpr double DIAG_COST = 1.5, NEAR_COST = 2.0, ITEM_COST = 0.1;
+
+struct Chunk {
+    double cost;
+    int4 item;
+    int tail;     // 1: a tail item (handed out last)
+    double near;  // share of the item's cost in NEAR groups (its cost is the least certain)
+};
+
+// Items of one plan: diagonal items (the block's groups in D ranges); each
+// strip in chunks of Ln groups next to the block (near_span groups), Lm
+// groups after them, and its last T groups in tail chunks of Lt groups.
+// Strip i-rows follow the diagonal items' rows in strip order; handout
+// order: largest first, the tail last.
+void build_items(int ngroups, int gpb, int D, int Lm, int Ln, int near_span, int T, int Lt, std::vector<Chunk> *out,
+                 std::vector<int2> *blk, int *S) {
+    const int nb = (ngroups + gpb - 1) / gpb;
+    out->clear();
+    blk->assign(nb, make_int2(0, 0));
+    *S = 0;
+    for (int b = 0; b < nb; b++) {
+        const int g0 = b * gpb, g1 = std::min(g0 + gpb, ngroups), n = g1 - g0;
+        const int d = std::min(D, n);
+        for (int k = 0; k < d; k++) {
+            const int a0 = g0 + (int)((long long)n * k / d), a1 = g0 + (int)((long long)n * (k + 1) / d);
+            out->push_back(Chunk{(a1 - a0) * DIAG_COST + ITEM_COST, make_int4(b, a0, a1, k), 0, 1.0});
+        }
+        (*blk)[b].x = d;
+        *S = std::max(*S, d);
+    }
+    for (int b = 0; b < nb; b++) {
+        const int s0 = (b + 1) * gpb, Sb = std::max(0, ngroups - s0);
+        const int tail0 = std::max(0, Sb - T);  // the strip's tail starts here
+        const int nspan = std::min(near_span, tail0);
+        int pos = 0, nch = 0;
+        auto emit = [&](int L, int tl) {
+            const int nnear = std::max(0, std::min(pos + L, near_span) - pos);
+            const double c = nnear * NEAR_COST + (L - nnear) + ITEM_COST;
+            out->push_back(Chunk{c, make_int4(b, s0 + pos, s0 + pos + L, -1), tl, nnear * NEAR_COST / c});
+            pos += L;
+            nch++;
+        };
+        while (pos < nspan) emit(std::min(Ln, nspan - pos), 0);
+        while (pos < tail0) emit(std::min(Lm, tail0 - pos), 0);
+        while (pos < Sb) emit(std::min(Lt, Sb - pos), 1);
+        (*blk)[b].y = nch;
+    }
+    std::vector<int> next(nb, 0);
+    for (Chunk &c : *out)
+        if (c.item.w < 0) c.item.w = *S + next[c.item.x]++;
+    std::stable_sort(out->begin(), out->end(), [](const Chunk &x, const Chunk &y) {
+        return x.tail != y.tail ? y.tail : x.cost > y.cost;
+    });
+}
+
+// Makespan of handing the items in order to the first free of C CTAs, the
+// worst of a few draws in which each item's cost is off by a fixed
+// pseudo-random factor (up to +-60 % of its NEAR share, +-10 % otherwise):
+// the cost model is rough, so plans whose balance rests on it are avoided.
+double makespan(const std::vector<Chunk> &items, int C) {
+    double worst = 0.0;
+    for (uint32_t seed = 1; seed <= 3; seed++) {
+        std::priority_queue<double, std::vector<double>, std::greater<double>> q;
+        for (int k = 0; k < C; k++) q.push(0.0);
+        double m = 0.0;
+        uint32_t h = seed * 2654435761u;
+        for (const Chunk &c : items) {
+            h ^= h << 13;
+            h ^= h >> 17;
+            h ^= h << 5;
+            const double r = (double)(h & 0xffff) / 65535.0 * 2.0 - 1.0;  // in [-1, 1]
+            const double t = q.top() + c.cost * (1.0 + r * (0.1 + 0.5 * c.near));
+            q.pop();
+            q.push(t);
+            m = std::max(m, t);
+        }
+        worst = std::max(worst, m);
+    }
+    return worst;
+}
+
+// The plan with the best estimated makespan (plus a small cost per partial
+// row, which the combine reads) over the diagonal split, the chunk lengths
+// and the tail.  Chunks stay at most a quarter of a CTA's share, and the
+// tail holds about two single-group or two-group items per CTA, so that the
+// CTAs run out of work together whatever the mix of NEAR and FAR pairs.
+void plan_items(int npad, int cw, int NPg, int ctas, int max_rows, std::vector<int4> *best_items,
+                std::vector<int2> *best_blk, int *best_S) {
+    const int ngroups = npad / MG, gpb = cw * NPg, nb = (ngroups + gpb - 1) / gpb;
+    std::vector<Chunk> items;
+    std::vector<int2> blk;
+    int S = 0;
+    build_items(ngroups, gpb, 1, 1, 1, 2 * gpb, 0, 1, &items, &blk, &S);
+    double total = 0.0;
+    for (const Chunk &c : items) total += c.cost;
+    const double per = total / ctas;
+    const int nstrips = std::max(1, nb - 1);
+    double best = 1e300;
+    const double fr[] = {0.06, 0.09, 0.12, 0.18, 0.25};
+    const int Ds[] = {2, 4, 6, 8, 12};
+    for (int D : Ds) {
+        for (double f : fr) {
+            const int Lm = std::max(1, (int)std::lround(per * f));
+            for (int Lt = 1; Lt <= 2; Lt++) {
+                for (double tau : {2.0, 3.0, 4.0}) {
+                    const int T = (int)std::ceil(tau * ctas * Lt / nstrips);
+                    const int Ln = std::max(1, std::min(Lm, 2 * NPg));
+                    build_items(ngroups, gpb, D, Lm, Ln, 2 * gpb, T, Lt, &items, &blk, &S);
+                    if ((int)items.size() > GENGA_MUTUAL_MAX_ITEMS) continue;
+                    int maxr = 0;
+                    for (const int2 &b : blk) maxr = std::max(maxr, S + b.y);
+                    if (maxr + nb > max_rows) continue;  // the partial rows must fit the workspace
+                    const double score = makespan(items, ctas) + 0.005 * (maxr + nb);
+                    if (score < best) {
+                        best = score;
+                        best_items->clear();
+                        for (const Chunk &c : items) best_items->push_back(c.item);
+                        *best_blk = blk;
+                        *best_S = S;
+                    }
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int num_mutual_variants() { return kNumMVariants; }
+void mutual_variant_shape(int v, int *cw, int *bpt) {
+    *cw = kMVariants[v].cw;
+    *bpt = 2 * kMVariants[v].np;
+}
+
+void free_mutual_cache(genga_ctx *c) {
+    if (!c->mcache) return;
+    for (auto &e : c->mcache->e) {
+        if (e.d_item) cudaFree(e.d_item);
+        if (e.d_blk) cudaFree(e.d_blk);
+    }
+    delete c->mcache;
+    c->mcache = nullptr;
+}
+
+// The plan of mutual variant v for N bodies, built (and uploaded) on first
+// use.  Returns false when it must be built while `s` is being captured, or
+// when it does not fit the partial rows: the caller then uses a one-sided
+// variant.
+bool mutual_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P) {
+    if (v < 0 || v >= kNumMVariants || v >= GENGA_MAX_VARIANTS) return false;
+    if (!c->mcache) {
+        c->mcache = new (std::nothrow) MutualCache();
+        if (!c->mcache) return false;
+    }
+    MutualCache::Entry &e = c->mcache->e[v];
+    const int npad = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
+    if (e.N != N) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+        std::vector<int4> items;
+        std::vector<int2> blk;
+        int S = 0;
+        // partial rows: up to MUTUAL_MAX_ROWS (the workspace grows to the plan's need)
+        const int max_rows = std::max((int)std::min<size_t>(c->partial_cap / (3 * (size_t)npad), 1 << 20),
+                                      MUTUAL_MAX_ROWS);
+        plan_items(npad, kMVariants[v].cw, kMVariants[v].np, c->sm_count, max_rows, &items, &blk, &S);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return false;  // the old tables may be in use
+        if (e.d_item) cudaFree(e.d_item);
+        if (e.d_blk) cudaFree(e.d_blk);
+        e = MutualCache::Entry{};
+        e.N = N;  // remembered also when no plan fits, so that it is not searched again
+        if (items.empty()) return false;
+        int irows = 0;
+        for (const int2 &b : blk) irows = std::max(irows, S + b.y);
+        const int nb = (int)blk.size();
+        const size_t need = (size_t)(irows + nb) * 3 * npad;
+        if (need > c->partial_cap) {  // a larger workspace for the rows; captured step graphs used the old one
+            double *bigger = nullptr;
+            if (cudaMalloc(&bigger, need * sizeof(double)) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            cudaFree(c->partial);
+            c->partial = bigger;
+            c->partial_cap = need;
+            if (c->step_exec) {
+                cudaGraphExecDestroy(c->step_exec);
+                c->step_exec = nullptr;
+            }
+        }
+        if (cudaMalloc(&e.d_item, items.size() * sizeof(int4)) != cudaSuccess) return false;
+        if (cudaMalloc(&e.d_blk, blk.size() * sizeof(int2)) != cudaSuccess) return false;
+        if (cudaMemcpy(e.d_item, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(e.d_blk, blk.data(), blk.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+            return false;
+        e.nb = nb;
+        e.gpb = kMVariants[v].cw * kMVariants[v].np;
+        e.ngroups = npad / MG;
+        e.items = (int)items.size();
+        e.irows = irows;
+        e.S = S;
+        e.ok = true;
+    }
+    if (!e.ok) return false;
+    *P = MutualPlan{e.nb, e.gpb, e.ngroups, e.items, e.irows, e.S, e.d_item, e.d_blk};
+    return true;
+}
+
+cudaError_t init_mutual_kernels() {
+    for (int q = 0; q < kNumMVariants; q++) {
+        cudaError_t e = cudaFuncSetAttribute(kMVariants[q].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kMVariants[q].smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_pass_mutual(const PassArgs &a0, int v, int sm_count, cudaStream_t s) {
+    PassArgs a = a0;
+    const MVariant &mv = kMVariants[v];
+    cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(sm_count, a.mp.items);
+    mv.fn<<<grid, (mv.cw + 2) * 32, mv.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine_mutual(const double *partial, const MutualPlan &P, int N, int npad, const uint32_t *perm,
+                                  double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
+                                  cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    combine_mutual_kernel<<<dim3((N + 255) / 256, 3), 256, 0, s>>>(partial, P, N, npad, perm, tau, acc, vx, vy, vz,
+                                                                    status);
+    return cudaGetLastError();
+}
+
+}  // namespace genga

@@ -17,6 +17,7 @@
 //   * iperm: the packed position of every body (the close-encounter level
 //     reads a_i, r_crit,i and the test-particle flag of its members there).
 #include "internal.cuh"
+#include "pass_common.cuh"
 
 namespace genga {
 
@@ -112,7 +113,7 @@ __device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double 
                                            float4 *__restrict__ lo, double4_32a *__restrict__ p64,
                                            float2 *__restrict__ scr, double *__restrict__ a_osc,
                                            double *__restrict__ rc_eq1, bool tp, double sscale, float3 *pos,
-                                           bool *real) {
+                                           bool *real, double4 *pos64) {
     float2 s = make_float2(0.f, 0.f);
     if (i >= 0) {
         // osculating a from the heliocentric velocity u = v + P / M*:
@@ -151,6 +152,7 @@ __device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double 
                             __double2float_rn(zi - (double)hz), tp ? 1.f : 0.f);  // w: test particle (mode 2)
         p64[k] = make_double4_32a(xi, yi, zi, gm);
         *pos = make_float3(hx, hy, hz);
+        *pos64 = make_double4(xi, yi, zi, gm);
         *real = true;
     } else {
         const float px = GENGA_PAD_POS + 64.0f * (float)pad;
@@ -161,6 +163,7 @@ __device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double 
         p64[k] = make_double4_32a((double)px, GENGA_PAD_POS, GENGA_PAD_POS, 0.0);
         a_osc[k] = 0.0;
         rc_eq1[k] = 0.0;
+        *pos64 = make_double4((double)px, GENGA_PAD_POS, GENGA_PAD_POS, 0.0);
         *real = false;
     }
     scr[k] = s;
@@ -171,9 +174,9 @@ __device__ __forceinline__ float2 prep_body(int k, int i, int pad, const double 
 // its screening factors and its flags (GENGA_GROUP_BIG: holds a body that is
 // not a test particle, GENGA_GROUP_TP: holds a test particle); one block =
 // one 64-body group.
-__device__ __forceinline__ void group_reduce_store(float2 s, float3 pos, bool real, bool tp,
-                                                   float4 *__restrict__ gbox_lo, float4 *__restrict__ gbox_hi,
-                                                   int32_t *__restrict__ gflag) {
+__device__ __forceinline__ Box group_reduce_store(float2 s, float3 pos, bool real, bool tp,
+                                                  float4 *__restrict__ gbox_lo, float4 *__restrict__ gbox_hi,
+                                                  int32_t *__restrict__ gflag) {
     const unsigned big_w = __ballot_sync(0xffffffffu, real && !tp), tp_w = __ballot_sync(0xffffffffu, real && tp);
     const float INF = __int_as_float(0x7f800000);
     float3 bl = real ? pos : make_float3(INF, INF, INF);
@@ -192,6 +195,7 @@ __device__ __forceinline__ void group_reduce_store(float2 s, float3 pos, bool re
     }
     __shared__ float4 wl[PREP_THREADS / 32], wh[PREP_THREADS / 32];
     __shared__ int32_t wf[PREP_THREADS / 32];
+    __shared__ Box box;
     if ((threadIdx.x & 31) == 0) {
         wl[threadIdx.x >> 5] = make_float4(bl.x, bl.y, bl.z, hmax);
         wh[threadIdx.x >> 5] = make_float4(bh.x, bh.y, bh.z, amax);
@@ -209,6 +213,44 @@ __device__ __forceinline__ void group_reduce_store(float2 s, float3 pos, bool re
         gbox_lo[blockIdx.x] = l;
         gbox_hi[blockIdx.x] = h;
         gflag[blockIdx.x] = f;
+        box = Box{l, h};
+    }
+    __syncthreads();
+    return box;
+}
+
+// Group-centred copies for the mutual FP32 pass: c = the centre of the
+// group's box (an FP32 value), each body's offset from it as the FP64
+// difference rounded to FP32 (X = fl32(x - c)), duplicated for the packed
+// loop ({X, X, Y, Y}, {Z, Z, G m, G m}), and its rounding residual
+// {x - c - X, y - c - Y, z - c - Z, test-particle flag}; per group
+// {c, PRECISION_KAPPA * h}, h an upper bound of |x - c| over the group (the
+// pass treats a group as far from a set of bodies only beyond that distance,
+// which bounds the relative error of an offset Xj - Xi to about
+// 3 u (1 + 1/PRECISION_KAPPA) = 15 u, u = 2^-24).  An empty group (padding
+// only) has c = 0 and distance 0.
+constexpr float PRECISION_KAPPA = 0.25f;
+
+__device__ __forceinline__ void store_centred(int k, const Box &b, double4 p, bool tp, float4 *__restrict__ rel,
+                                              float4 *__restrict__ rell, float4 *__restrict__ gctr) {
+    const bool empty = !(b.lo.x <= b.hi.x);
+    const float cx = empty ? 0.f : 0.5f * (b.lo.x + b.hi.x), cy = empty ? 0.f : 0.5f * (b.lo.y + b.hi.y);
+    const float cz = empty ? 0.f : 0.5f * (b.lo.z + b.hi.z);
+    const double dx = p.x - (double)cx, dy = p.y - (double)cy, dz = p.z - (double)cz;
+    const float X = __double2float_rn(dx), Y = __double2float_rn(dy), Z = __double2float_rn(dz);
+    const float w = __double2float_rn(p.w);
+    rel[2 * (size_t)k] = make_float4(X, X, Y, Y);
+    rel[2 * (size_t)k + 1] = make_float4(Z, Z, w, w);
+    rell[k] = make_float4(__double2float_rn(dx - (double)X), __double2float_rn(dy - (double)Y),
+                          __double2float_rn(dz - (double)Z), tp ? 1.f : 0.f);
+    if (threadIdx.x == 0) {
+        float h = 0.f;
+        if (!empty) {  // half-diagonal of the box about c, rounded up
+            const float ex = fmaxf(b.hi.x - cx, cx - b.lo.x), ey = fmaxf(b.hi.y - cy, cy - b.lo.y);
+            const float ez = fmaxf(b.hi.z - cz, cz - b.lo.z);
+            h = __fsqrt_ru(__fmaf_ru(ex, ex, __fmaf_ru(ey, ey, __fmul_ru(ez, ez)))) * (1.0f + 0x1p-20f);
+        }
+        gctr[blockIdx.x] = make_float4(cx, cy, cz, PRECISION_KAPPA * h);
     }
 }
 
@@ -221,16 +263,19 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
     double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
     float4 *__restrict__ lo, double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
     float4 *__restrict__ gbox_hi, int32_t *__restrict__ gflag, double *__restrict__ a_osc,
-    double *__restrict__ rc_eq1, int n_big, uint32_t *__restrict__ iperm, double sscale) {
+    double *__restrict__ rc_eq1, int n_big, uint32_t *__restrict__ iperm, double sscale, float4 *__restrict__ rel,
+    float4 *__restrict__ rell, float4 *__restrict__ gctr) {
     const int k = blockIdx.x * PREP_THREADS + threadIdx.x;
     float3 pos = make_float3(0.f, 0.f, 0.f);
+    double4 p4;
     bool real = false;
     const int i = k < N ? (int)perm[k] : -1;
     if (i >= 0) iperm[i] = (uint32_t)k;
     const bool tp = i >= 0 && n_big >= 0 && i >= n_big;
     const float2 s = prep_body(k, i, k - N, x, y, z, vx, vy, vz, m, P, G, Mstar, dt, n1, n2,
-                               rcrit_mode, hi, hit, hid, lo, p64, scr, a_osc, rc_eq1, tp, sscale, &pos, &real);
-    group_reduce_store(s, pos, real, tp, gbox_lo, gbox_hi, gflag);
+                               rcrit_mode, hi, hit, hid, lo, p64, scr, a_osc, rc_eq1, tp, sscale, &pos, &real, &p4);
+    const Box b = group_reduce_store(s, pos, real, tp, gbox_lo, gbox_hi, gflag);
+    store_centred(k, b, p4, tp, rel, rell, gctr);
 }
 
 // Batched: packed position p belongs to system d = segment of p in poff; its
@@ -243,19 +288,21 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_batched_kernel(
     double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
     float4 *__restrict__ lo, double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
     float4 *__restrict__ gbox_hi, int32_t *__restrict__ gflag, double *__restrict__ a_osc,
-    double *__restrict__ rc_eq1, int n_big, uint32_t *__restrict__ iperm, double sscale,
-    const __grid_constant__ BatchBodies bb) {
+    double *__restrict__ rc_eq1, int n_big, uint32_t *__restrict__ iperm, double sscale, float4 *__restrict__ rel,
+    float4 *__restrict__ rell, float4 *__restrict__ gctr, const __grid_constant__ BatchBodies bb) {
     const int p = blockIdx.x * PREP_THREADS + threadIdx.x;
     const int d = find_segment(bb.poff, bb.D, p);
     const int k = p - bb.poff[d], Nd = bb.off[d + 1] - bb.off[d];
     float3 pos = make_float3(0.f, 0.f, 0.f);
+    double4 p4;
     bool real = false;
     const int i = k < Nd ? (int)perm[bb.off[d] + k] : -1;
     if (i >= 0) iperm[i] = (uint32_t)p;
     const bool tp = i >= 0 && n_big >= 0 && i - bb.off[d] >= n_big;
     const float2 s = prep_body(p, i, k - Nd, x, y, z, vx, vy, vz, m, Pd + 3 * d, G, Mstar, dt, n1, n2, rcrit_mode, hi,
-                               hit, hid, lo, p64, scr, a_osc, rc_eq1, tp, sscale, &pos, &real);
-    group_reduce_store(s, pos, real, tp, gbox_lo, gbox_hi, gflag);
+                               hit, hid, lo, p64, scr, a_osc, rc_eq1, tp, sscale, &pos, &real, &p4);
+    const Box b = group_reduce_store(s, pos, real, tp, gbox_lo, gbox_hi, gflag);
+    store_centred(p, b, p4, tp, rel, rell, gctr);
 }
 
 // Batched momentum: block d sums system d (strided per thread, fixed tree).
@@ -301,7 +348,8 @@ cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ct
     prep_kernel<<<npad / PREP_THREADS, PREP_THREADS, 0, s>>>(
         sys.x, sys.y, sys.z, sys.vx, sys.vy, sys.vz, sys.m, sys.N, c->perm, c->mom, p.G, p.Mstar, p.dt, p.n1,
         p.n2, p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_d, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->gflag,
-        c->a_osc, c->rc_eq1, p.n_big, c->iperm, p.bs_tol > 0.0 ? GENGA_PREDICT_RANGE : 1.0);
+        c->a_osc, c->rc_eq1, p.n_big, c->iperm, p.bs_tol > 0.0 ? GENGA_PREDICT_RANGE : 1.0, c->pk_r, c->pk_rl,
+        c->gctr);
     return cudaGetLastError();
 }
 
@@ -320,7 +368,7 @@ cudaError_t launch_prep_batched(const genga_system &all, const BatchBodies &bb, 
     prep_batched_kernel<<<bb.npad_total / PREP_THREADS, PREP_THREADS, 0, s>>>(
         all.x, all.y, all.z, all.vx, all.vy, all.vz, all.m, c->perm, c->Pd, p.G, p.Mstar, p.dt, p.n1, p.n2,
         p.rcrit_mode, c->pk_hi, c->pk_t, c->pk_d, c->pk_lo, c->pk64, c->scr, c->gbox_lo, c->gbox_hi, c->gflag, c->a_osc,
-        c->rc_eq1, p.n_big, c->iperm, p.bs_tol > 0.0 ? GENGA_PREDICT_RANGE : 1.0, bb);
+        c->rc_eq1, p.n_big, c->iperm, p.bs_tol > 0.0 ? GENGA_PREDICT_RANGE : 1.0, c->pk_r, c->pk_rl, c->gctr, bb);
     return cudaGetLastError();
 }
 

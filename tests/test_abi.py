@@ -117,3 +117,22 @@ def test_noalloc_argument_checks_without_device(lib):
     assert lib.genga_kick_noalloc(C.byref(s), C.byref(p), 0.0, None, None) == g.GENGA_ERR_INVALID_ARG
     assert lib.genga_kick_noalloc(None, C.byref(p), 0.0, None, None) == g.GENGA_ERR_INVALID_ARG
     assert lib.genga_kick_noalloc(C.byref(s), None, 0.0, None, None) == g.GENGA_ERR_INVALID_ARG
+
+
+def test_variant_info_and_test_hook_without_device(lib):
+    import paper_2309_08217_gb300 as g
+    kinds = set()
+    v = 0
+    while True:
+        try:
+            info = g.genga_kernel_variant_info(v)
+        except g.GengaError as e:
+            assert e.code == g.GENGA_ERR_INVALID_ARG
+            break
+        assert info["kind"] in (0, 1) and info["warps"] >= 1 and info["bodies_per_thread"] >= 1
+        kinds.add(info["kind"])
+        v += 1
+    assert kinds == {0, 1}
+    with pytest.raises(g.GengaError):
+        g.genga_kernel_variant_info(-1)
+    assert lib.genga_set_test_waits(None, 20, 1) == g.GENGA_ERR_INVALID_ARG
