@@ -698,11 +698,13 @@ struct Chunk {
 };
 
 // Items of one plan: diagonal items (the block's groups in D ranges); each
-// strip in chunks of Ln groups next to the block (near_span groups), Lm
-// groups after them, and its last T groups in tail chunks of Lt groups.
-// Strip i-rows follow the diagonal items' rows in strip order; handout
-// order: largest first, the tail last.
-void build_items(int ngroups, int gpb, int D, int Lm, int Ln, int near_span, int T, int Lt, std::vector<Chunk> *out,
+// strip's first near_span groups (next to the block, mostly NEAR) in chunks
+// of at most Ln groups, the rest in chunks of Lm groups (Lm = 0: about R
+// chunks per strip, their length following the strip's, so that handing the
+// items out longest first ends on the short chunks of the short strips), its
+// last T groups in single-group tail items.  Strip i-rows follow the diagonal
+// items' rows in strip order; handout order: largest first, the tail last.
+void build_items(int ngroups, int gpb, int D, int R, int Lm, int Ln, int near_span, int T, std::vector<Chunk> *out,
                  std::vector<int2> *blk, int *S) {
     const int nb = (ngroups + gpb - 1) / gpb;
     out->clear();
@@ -720,8 +722,9 @@ void build_items(int ngroups, int gpb, int D, int Lm, int Ln, int near_span, int
     }
     for (int b = 0; b < nb; b++) {
         const int s0 = (b + 1) * gpb, Sb = std::max(0, ngroups - s0);
-        const int tail0 = std::max(0, Sb - T);  // the strip's tail starts here
+        const int tail0 = std::max(0, Sb - T);
         const int nspan = std::min(near_span, tail0);
+        const int Lb = Lm > 0 ? Lm : std::max(1, (Sb + R - 1) / R);
         int pos = 0, nch = 0;
         auto emit = [&](int L, int tl) {
             const int nnear = std::max(0, std::min(pos + L, near_span) - pos);
@@ -730,9 +733,9 @@ void build_items(int ngroups, int gpb, int D, int Lm, int Ln, int near_span, int
             pos += L;
             nch++;
         };
-        while (pos < nspan) emit(std::min(Ln, nspan - pos), 0);
-        while (pos < tail0) emit(std::min(Lm, tail0 - pos), 0);
-        while (pos < Sb) emit(std::min(Lt, Sb - pos), 1);
+        while (pos < nspan) emit(std::min(std::min(Ln, Lb), nspan - pos), 0);
+        while (pos < tail0) emit(std::min(Lb, tail0 - pos), 0);
+        while (pos < Sb) emit(1, 1);
         (*blk)[b].y = nch;
     }
     std::vector<int> next(nb, 0);
@@ -770,44 +773,44 @@ double makespan(const std::vector<Chunk> &items, int C) {
 }
 
 // The plan with the best estimated makespan (plus a small cost per partial
-// row, which the combine reads) over the diagonal split, the chunk lengths
-// and the tail.  Chunks stay at most a quarter of a CTA's share, and the
-// tail holds about two single-group or two-group items per CTA, so that the
-// CTAs run out of work together whatever the mix of NEAR and FAR pairs.
+// row, which the combine reads) over the diagonal split, the chunks per strip
+// and the tail (single groups, a few per CTA in all).
 void plan_items(int npad, int cw, int NPg, int ctas, int max_rows, std::vector<int4> *best_items,
                 std::vector<int2> *best_blk, int *best_S) {
     const int ngroups = npad / MG, gpb = cw * NPg, nb = (ngroups + gpb - 1) / gpb;
+    const int nstrips = std::max(1, nb - 1);
     std::vector<Chunk> items;
     std::vector<int2> blk;
     int S = 0;
-    build_items(ngroups, gpb, 1, 1, 1, 2 * gpb, 0, 1, &items, &blk, &S);
+    double best = 1e300;
     double total = 0.0;
+    build_items(ngroups, gpb, 1, 1, 1, NPg, 2 * gpb, 0, &items, &blk, &S);
     for (const Chunk &c : items) total += c.cost;
     const double per = total / ctas;
-    const int nstrips = std::max(1, nb - 1);
-    double best = 1e300;
-    const double fr[] = {0.06, 0.09, 0.12, 0.18, 0.25};
-    const int Ds[] = {2, 4, 6, 8, 12};
-    for (int D : Ds) {
-        for (double f : fr) {
-            const int Lm = std::max(1, (int)std::lround(per * f));
-            for (int Lt = 1; Lt <= 2; Lt++) {
-                for (double tau : {2.0, 3.0, 4.0}) {
-                    const int T = (int)std::ceil(tau * ctas * Lt / nstrips);
-                    const int Ln = std::max(1, std::min(Lm, 2 * NPg));
-                    build_items(ngroups, gpb, D, Lm, Ln, 2 * gpb, T, Lt, &items, &blk, &S);
-                    if ((int)items.size() > GENGA_MUTUAL_MAX_ITEMS) continue;
-                    int maxr = 0;
-                    for (const int2 &b : blk) maxr = std::max(maxr, S + b.y);
-                    if (maxr + nb > max_rows) continue;  // the partial rows must fit the workspace
-                    const double score = makespan(items, ctas) + 0.005 * (maxr + nb);
-                    if (score < best) {
-                        best = score;
-                        best_items->clear();
-                        for (const Chunk &c : items) best_items->push_back(c.item);
-                        *best_blk = blk;
-                        *best_S = S;
-                    }
+    // two families: fixed chunk lengths (fractions of a CTA's share) and a
+    // fixed number of chunks per strip
+    struct Shape {
+        int R, Lm;
+    };
+    std::vector<Shape> shapes;
+    for (int R : {16, 24, 32, 48, 64}) shapes.push_back(Shape{R, 0});
+    for (double f : {0.06, 0.09, 0.12, 0.18, 0.25}) shapes.push_back(Shape{0, std::max(1, (int)std::lround(per * f))});
+    for (int D : {2, 4, 8, 12}) {
+        for (const Shape &sh : shapes) {
+            for (int tau : {2, 4, 6}) {
+                const int T = (tau * ctas + nstrips - 1) / nstrips;
+                build_items(ngroups, gpb, D, sh.R, sh.Lm, NPg, 2 * gpb, T, &items, &blk, &S);
+                if ((int)items.size() > GENGA_MUTUAL_MAX_ITEMS) continue;
+                int maxr = 0;
+                for (const int2 &b : blk) maxr = std::max(maxr, S + b.y);
+                if (maxr + nb > max_rows) continue;  // the partial rows must fit the workspace
+                const double score = makespan(items, ctas) + 0.01 * (maxr + nb);
+                if (score < best) {
+                    best = score;
+                    best_items->clear();
+                    for (const Chunk &c : items) best_items->push_back(c.item);
+                    *best_blk = blk;
+                    *best_S = S;
                 }
             }
         }
