@@ -60,15 +60,36 @@ genga_status genga_get_kernel_variant(genga_ctx *ctx, int32_t N, int32_t *varian
 genga_status genga_kernel_variant_info(int32_t variant, int32_t *kind, int32_t *warps, int32_t *bodies_per_thread,
                                        int32_t *ctas_per_sm);
 
+/* FP64 pass variants: 0 = the one-sided FP64 pass, 1 .. = the mutual FP64
+ * pass (each unordered pair once, its terms added to both bodies) in several
+ * shapes.  genga_set_fp64_variant forces `variant` (>= 0) or, with -1 (the
+ * default), lets the context time every variant the first time it meets a
+ * size bucket and keep the fastest, as for the FP32 pass; test-particle mode
+ * 2 always takes variant 0.  Out-of-range values: GENGA_ERR_INVALID_ARG. */
+genga_status genga_set_fp64_variant(genga_ctx *ctx, int32_t variant);
+
+/* The FP64 variant used for systems of N bodies (-1 when not tuned yet) and
+ * the number of FP64 variants; HOST memory. */
+genga_status genga_get_fp64_variant(genga_ctx *ctx, int32_t N, int32_t *variant, int32_t *num_variants);
+
+/* Shape of FP64 variant `variant` (HOST memory outputs): kind 0 one-sided,
+ * 1 mutual; warps per CTA doing pair work; i-bodies per thread. */
+genga_status genga_fp64_variant_info(int32_t variant, int32_t *kind, int32_t *warps, int32_t *bodies_per_thread);
+
+/* The autotuner's measured pass time (ms) of each FP64 variant for systems of
+ * N bodies (0 where not measured); ms is HOST memory [n]. */
+genga_status genga_fp64_tuning_times(genga_ctx *ctx, int32_t N, float *ms, int32_t n);
+
 /* Name of the most recent CUDA runtime error (cudaGetErrorName) that an
  * entry point called from this thread turned into GENGA_ERR_CUDA, or
  * "cudaSuccess" if none has; a static string. */
 const char *genga_last_cuda_error(void);
 
-/* Failure-detection test hook for the bounded waits of the FP32 passes
- * (every mbarrier wait of a pass gives up after a time limit, sets
- * GENGA_ERR_TIMEOUT in the sticky status and returns, so a stalled pipeline
- * ends the kernel instead of hanging the GPU).  wait_ns_log2 > 0 sets that
+/* Failure-detection test hook for the bounded waits of the pipelined passes
+ * (the FP32 passes and the mutual FP64 pass; every mbarrier wait of a pass
+ * gives up after a time limit, sets GENGA_ERR_TIMEOUT in the sticky status
+ * and returns, so a stalled pipeline ends the kernel instead of hanging the
+ * GPU).  wait_ns_log2 > 0 sets that
  * limit to 2^wait_ns_log2 ns (0: the default of 2 s); hold != 0 makes each
  * CTA's producer warp return before it fills its first ring slot, without
  * issuing any copy, so that the consumers' waits run out and the next

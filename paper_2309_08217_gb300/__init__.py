@@ -103,6 +103,10 @@ def load():
             "genga_tuning_times": ([V, I, C.POINTER(C.c_float), I], I),
             "genga_step_batched": ([V, S, C.POINTER(C.c_int32), I, P, I, V], I),
             "genga_get_kernel_variant": ([V, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], I),
+            "genga_set_fp64_variant": ([V, I], I),
+            "genga_get_fp64_variant": ([V, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], I),
+            "genga_fp64_variant_info": ([I] + [C.POINTER(I)] * 3, I),
+            "genga_fp64_tuning_times": ([V, I, C.POINTER(C.c_float), I], I),
             "genga_compact": ([V, S, V, V], I),
             "genga_tune_levels": ([V, S, P, C.POINTER(I), C.POINTER(I), I, I, C.POINTER(I), C.POINTER(C.c_float),
                                    C.POINTER(I), V], I),
@@ -360,7 +364,7 @@ def genga_kernel_variant_info(variant):
 
 
 def genga_set_test_waits(ctx, wait_ns_log2=0, hold=False):
-    """Test hook of the FP32 passes' bounded waits: limit 2^wait_ns_log2 ns
+    """Test hook of the pipelined passes' bounded waits: limit 2^wait_ns_log2 ns
     (0: the default 2 s); hold: the producers withhold their first stage."""
     _check(load().genga_set_test_waits(_ctx(ctx), int(wait_ns_log2), int(bool(hold))), "genga_set_test_waits")
 
@@ -370,6 +374,33 @@ def genga_get_kernel_variant(ctx, N):
     v, n = C.c_int32(), C.c_int32()
     _check(load().genga_get_kernel_variant(_ctx(ctx), int(N), C.byref(v), C.byref(n)), "genga_get_kernel_variant")
     return v.value, n.value
+
+
+def genga_set_fp64_variant(ctx, variant=-1):
+    """Force an FP64 pass variant (0 one-sided, >= 1 mutual) or return to autotuning (-1)."""
+    _check(load().genga_set_fp64_variant(_ctx(ctx), int(variant)), "genga_set_fp64_variant")
+
+
+def genga_get_fp64_variant(ctx, N):
+    """(FP64 variant in use for N bodies or -1 if not tuned yet, number of FP64 variants)."""
+    v, n = C.c_int32(), C.c_int32()
+    _check(load().genga_get_fp64_variant(_ctx(ctx), int(N), C.byref(v), C.byref(n)), "genga_get_fp64_variant")
+    return v.value, n.value
+
+
+def genga_fp64_variant_info(variant):
+    """{'kind': 0 one-sided / 1 mutual, 'warps', 'bodies_per_thread'} of an FP64 variant."""
+    vals = [C.c_int32() for _ in range(3)]
+    _check(load().genga_fp64_variant_info(int(variant), *[C.byref(v) for v in vals]), "genga_fp64_variant_info")
+    return dict(zip(("kind", "warps", "bodies_per_thread"), (v.value for v in vals)))
+
+
+def genga_fp64_tuning_times(ctx, N):
+    """The autotuner's pass time (ms) of each FP64 variant for N bodies."""
+    n = genga_get_fp64_variant(ctx, N)[1]
+    arr = (C.c_float * n)()
+    _check(load().genga_fp64_tuning_times(_ctx(ctx), int(N), arr, n), "genga_fp64_tuning_times")
+    return list(arr)
 
 
 # ------------------------------------------- kick without device allocation ---

@@ -162,13 +162,74 @@ bool launch_fp32_variant(genga_ctx *c, PassArgs a, int v, cudaStream_t s, Mutual
     return true;
 }
 
-cudaError_t launch_combine_any(genga_ctx *c, bool mutual, const MutualPlan &mp, int split, int one_row, int N,
+// FP64 pass variants: 0 = the one-sided pass, 1 .. = the mutual FP64 pass.
+inline int num_f64_variants() { return 1 + num_mutual64_variants(); }
+
+// Launches FP64 pass variant v; as launch_fp32_variant.
+bool launch_fp64_variant(genga_ctx *c, PassArgs a, int v, cudaStream_t s, MutualPlan *mp, int *split, int *one_row,
+                         cudaError_t *err) {
+    *err = cudaSuccess;
+    if (v > 0) {
+        if (!mutual64_plan(c, a.N, v - 1, s, mp)) return false;
+        a.partial = c->partial;
+        a.mp = *mp;
+        *split = 0;
+        *one_row = 0;
+        *err = launch_pass_mutual64(a, v - 1, c->sm_count, s);
+        return true;
+    }
+    int grid = 1;
+    a.partial = c->partial;
+    plan_pass(a.N, GENGA_FP64, 0, c->sm_count, c->partial_cap, &a, &grid);
+    *split = a.split;
+    *one_row = a.tp_rows_end;
+    *err = launch_pass(a, GENGA_FP64, 0, grid, s);
+    return true;
+}
+
+// mutual: 0 = the rows of a one-sided pass, 1 = mutual FP32, 2 = mutual FP64.
+cudaError_t launch_combine_any(genga_ctx *c, int mutual, const MutualPlan &mp, int split, int one_row, int N,
                                int fp64_rows, double tau, double *acc, const genga_system &sys, cudaStream_t s) {
+    if (mutual == 2)
+        return launch_combine_mutual64(c->partial, mp, N, npad_of(N), c->perm, tau, acc, sys.vx, sys.vy, sys.vz,
+                                       c->status, s);
     if (mutual)
         return launch_combine_mutual(c->partial, mp, N, npad_of(N), c->perm, tau, acc, sys.vx, sys.vy, sys.vz,
                                      c->status, s);
     return launch_combine(c->partial, split, one_row, N, npad_of(N), fp64_rows, c->perm, tau, acc, sys.vx, sys.vy,
                           sys.vz, c->status, s);
+}
+
+// Times one variant for the autotuner: pass + combine (no kick applied, no
+// output) `reps` times on the packed state, clearing the encounter list after
+// each run; the fastest run after the first, 3e38 if a run failed.
+template <class Launch>
+float time_variant(genga_ctx *c, int N, int reps, int kind, int fp64_rows, cudaStream_t s, cudaEvent_t e0,
+                   cudaEvent_t e1, Launch launch) {
+    float ms = 3.0e38f;
+    for (int rep = 0; rep < reps; rep++) {
+        MutualPlan mp{};
+        int split = 1, one_row = 0;
+        cudaError_t e = cudaSuccess;
+        cudaEventRecord(e0, s);
+        if (!launch(&mp, &split, &one_row, &e)) break;
+        genga_system none{};
+        none.N = N;
+        if (e == cudaSuccess) e = launch_combine_any(c, kind, mp, split, one_row, N, fp64_rows, 0.0, nullptr, none, s);
+        cudaEventRecord(e1, s);
+        cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s);
+        if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
+        float t = 3.0e38f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0 && t < ms) ms = t;
+        if (rep > 0 && t > 20.f) break;  // long passes: one timed run is enough
+    }
+    return ms;
+}
+
+bool can_tune(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
 }
 
 // The FP32 pass variant for this size: forced, already tuned, or tuned now.
@@ -185,8 +246,7 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
     const int b = size_bucket(N);
     int8_t *table = tp2 ? c->f32_variant_tp : c->f32_variant;
     if (table[b] >= 0) return table[b];
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 0;
+    if (!can_tune(s)) return 0;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return 0;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -197,24 +257,10 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
     float best_ms = 3.0e38f;
     const int nv = tp2 ? num_fp32_variants() : num_all_variants();
     for (int v = 0; v < nv; v++) {
-        float ms = 3.0e38f;
-        for (int rep = 0; rep < 4; rep++) {  // pass + combine (no kick applied, no output)
-            MutualPlan mp{};
-            int split = 1, one_row = 0;
-            cudaError_t e = cudaSuccess;
-            cudaEventRecord(e0, s);
-            if (!launch_fp32_variant(c, base, v, s, &mp, &split, &one_row, &e)) break;
-            genga_system none{};
-            none.N = N;
-            if (e == cudaSuccess)
-                e = launch_combine_any(c, is_mutual(v), mp, split, one_row, N, 0, 0.0, nullptr, none, s);
-            cudaEventRecord(e1, s);
-            cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s);
-            if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
-            float t = 3.0e38f;
-            cudaEventElapsedTime(&t, e0, e1);
-            if (rep > 0 && t < ms) ms = t;
-        }
+        const float ms = time_variant(c, N, 4, is_mutual(v) ? 1 : 0, 0, s, e0, e1,
+                                      [&](MutualPlan *mp, int *split, int *one_row, cudaError_t *e) {
+                                          return launch_fp32_variant(c, base, v, s, mp, split, one_row, e);
+                                      });
         if (!tp2 && v < GENGA_MAX_VARIANTS) c->tune_ms[b][v] = ms < 3.0e38f ? ms : 0.f;
         if (ms < best_ms) {
             best_ms = ms;
@@ -227,10 +273,43 @@ int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
     return best;
 }
 
+// The FP64 pass variant for this size, chosen the same way (test-particle
+// mode 2 always takes the one-sided pass, variant 0).
+int fp64_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
+    if (base.n_big >= 0) return 0;
+    if (c->forced_f64 >= 0) return c->forced_f64;
+    const int b = size_bucket(N);
+    if (c->f64_variant[b] >= 0) return c->f64_variant[b];
+    if (!can_tune(s)) return 0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return 0;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return 0;
+    }
+    int best = 0;
+    float best_ms = 3.0e38f;
+    for (int v = 0; v < num_f64_variants(); v++) {
+        const float ms = time_variant(c, N, 4, v > 0 ? 2 : 0, 1, s, e0, e1,
+                                      [&](MutualPlan *mp, int *split, int *one_row, cudaError_t *e) {
+                                          return launch_fp64_variant(c, base, v, s, mp, split, one_row, e);
+                                      });
+        if (v < GENGA_MAX_VARIANTS) c->tune64_ms[b][v] = ms < 3.0e38f ? ms : 0.f;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->f64_variant[b] = (int8_t)best;
+    return best;
+}
+
 // Result of a long-range pass: where its partial sums are and how to combine them.
 struct PassOut {
     int split = 1, one_row = 0;
-    bool mutual = false;
+    int mutual = 0;  // 0 one-sided rows, 1 mutual FP32, 2 mutual FP64
     MutualPlan mp{};
 };
 
@@ -260,17 +339,18 @@ cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &
     if (precision == GENGA_FP32) {
         int variant = fp32_variant(c, a, sys.N, s);
         if (is_mutual(variant) && p.n_big >= 0) variant = 0;
-        out->mutual = is_mutual(variant);
+        out->mutual = is_mutual(variant) ? 1 : 0;
         if (!launch_fp32_variant(c, a, variant, s, &out->mp, &out->split, &out->one_row, &e)) {
-            out->mutual = false;  // no mutual plan now (a capture): the one-sided default
+            out->mutual = 0;  // no mutual plan now (a capture): the one-sided default
             launch_fp32_variant(c, a, 0, s, &out->mp, &out->split, &out->one_row, &e);
         }
     } else {
-        int grid = 1;
-        plan_pass(sys.N, precision, 0, c->sm_count, c->partial_cap, &a, &grid);
-        out->split = a.split;
-        out->one_row = a.tp_rows_end;
-        e = launch_pass(a, precision, 0, grid, s);
+        const int variant = fp64_variant(c, a, sys.N, s);
+        out->mutual = variant > 0 ? 2 : 0;
+        if (!launch_fp64_variant(c, a, variant, s, &out->mp, &out->split, &out->one_row, &e)) {
+            out->mutual = 0;
+            launch_fp64_variant(c, a, 0, s, &out->mp, &out->split, &out->one_row, &e);
+        }
     }
     profile_after_pass(c, s);
     if (e != cudaSuccess) return e;
@@ -486,6 +566,10 @@ bool step_graph(genga_ctx *c, unsigned long long key, Block block) {
     return true;
 }
 
+bool fp64_tuned(const genga_ctx *c, int N, int n_big) {
+    return n_big >= 0 || c->forced_f64 >= 0 || c->f64_variant[size_bucket(N)] >= 0;
+}
+
 bool fp32_tuned(const genga_ctx *c, int N, int n_big) {
     return c->forced_variant >= 0 || (n_big >= 0 ? c->f32_variant_tp : c->f32_variant)[size_bucket(N)] >= 0;
 }
@@ -594,6 +678,8 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     c->max_N = max_N;
     for (int b = 0; b < 32; b++) c->f32_variant[b] = c->f32_variant_tp[b] = -1;
     c->forced_variant = -1;
+    for (int b = 0; b < 32; b++) c->f64_variant[b] = -1;
+    c->forced_f64 = -1;
     c->ordered_N = -1;
     c->step_graphs = 1;
     cudaDeviceProp prop;
@@ -766,7 +852,7 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
     int k = 0;
     auto aligned = [&]() {
         return c->steps_since_order == 0 && c->ordered_N == s2.N && c->ordered_nbig == p->n_big &&
-               (p->precision != GENGA_FP32 || fp32_tuned(c, s2.N, p->n_big));
+               (p->precision == GENGA_FP32 ? fp32_tuned(c, s2.N, p->n_big) : fp64_tuned(c, s2.N, p->n_big));
     };
     for (; k < nsteps && !(aligned() && nsteps - k >= GENGA_REORDER_STEPS); k++)
         if (const cudaError_t e_ = one_step(s); e_ != cudaSuccess) return cuda_status(e_);
@@ -779,6 +865,14 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
                 MutualPlan mp;  // the plan is built outside the capture
                 if (!mutual_plan(c, s2.N, variant - num_fp32_variants(), s, &mp)) variant = 0;
             }
+        } else {
+            PassArgs pa = base_args(c, s2, *p);
+            variant = fp64_variant(c, pa, s2.N, s);  // tuned already (aligned() holds)
+            if (variant > 0) {
+                MutualPlan mp;  // the plan is built outside the capture
+                if (!mutual64_plan(c, s2.N, variant - 1, s, &mp)) variant = 0;
+            }
+            variant += 1000;  // FP64 variants apart from FP32 ones in the graph key
         }
         const unsigned long long key = step_key(s2, *p, variant, 0);
         const bool ok = step_graph(c, key, [&](cudaStream_t q) {

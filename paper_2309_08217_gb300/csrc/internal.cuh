@@ -135,10 +135,13 @@ struct genga_ctx {
     int32_t *work;             // [1] work-item counter of the persistent pass
     int8_t f32_variant[32];    // autotuned FP32 pass variant per log2(npad) bucket, -1 = not tuned
     int8_t f32_variant_tp[32]; // the same for test-particle mode 2 (one-sided variants only)
-    int32_t test_wait_log2;    // test hook: bounded waits of the FP32 passes give up after 2^this ns (0: 2 s)
-    int32_t test_hold;         // test hook: the FP32 passes' producers withhold their first stage
+    int32_t test_wait_log2;    // test hook: bounded waits of the pipelined passes give up after 2^this ns (0: 2 s)
+    int32_t test_hold;         // test hook: the pipelined passes' producers withhold their first stage
     float tune_ms[32][GENGA_MAX_VARIANTS];  // the autotuner's time of each variant per bucket
     int32_t forced_variant;    // >= 0: use this FP32 variant (genga_set_kernel_variant)
+    int8_t f64_variant[32];    // autotuned FP64 pass variant per bucket (0 one-sided, 1.. mutual), -1 = not tuned
+    float tune64_ms[32][GENGA_MAX_VARIANTS];  // the autotuner's time of each FP64 variant per bucket
+    int32_t forced_f64;        // >= 0: use this FP64 variant (genga_set_fp64_variant)
     int32_t steps_since_order; // genga_step: drifts since the spatial order was built
     int32_t ordered_N;         // N of the system the spatial order was built for (-1: none, -2: a batch)
     unsigned long long ordered_key;  // layout hash of the batch the order was built for
@@ -327,6 +330,15 @@ int num_mutual_variants();
 void fp32_variant_shape(int variant, int *cw, int *bpt, int *ctas_per_sm);
 void mutual_variant_shape(int v, int *cw, int *bpt);
 bool mutual_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P);
+// FP64 mutual pass (mutual.cu): FP64 pass variants 1 .. (variant 0 is the one-sided FP64 pass)
+int num_mutual64_variants();
+void fp64_pass_shape(int *warps, int *bpt);  // the one-sided FP64 pass (kick.cu)
+void mutual64_variant_shape(int v, int *cw, int *bpt);
+bool mutual64_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P);
+cudaError_t launch_pass_mutual64(const PassArgs &a, int v, int sm_count, cudaStream_t s);
+cudaError_t launch_combine_mutual64(const double *partial, const MutualPlan &P, int N, int npad, const uint32_t *perm,
+                                    double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
+                                    cudaStream_t s);
 void free_mutual_cache(genga_ctx *c);
 cudaError_t init_mutual_kernels();
 cudaError_t launch_pass_mutual(const PassArgs &a, int v, int sm_count, cudaStream_t s);
@@ -380,6 +392,20 @@ __device__ __forceinline__ double rsqrt_fp64(double x) {
     const double e = fma(-t, y0, 1.0);
     const double p = fma(e, 0.375, 0.5);
     return fma(y0 * e, p, y0);
+}
+
+// x^(-3/2) in FP64 (the inverse cube of r from r^2): the SFU seed
+// y0 ~ x^(-1/2) as above, e = 1 - x y0^2, then x^(-3/2) = y0^3 (1 - e)^(-3/2)
+// ~ y0^3 (1 + 3e/2 + 15e^2/8) from the binomial series; truncation error
+// O(e^3).  Six FP64 operations where 1/sqrt and two products take seven.
+__device__ __forceinline__ double rsqrt3_fp64(double x) {
+    double y0;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(x));
+    const double y2 = y0 * y0;
+    const double y3 = y2 * y0;
+    const double e = fma(-x, y2, 1.0);
+    const double p = fma(e, 1.875, 1.5);
+    return fma(y3 * e, p, y3);
 }
 
 // 1/x in FP64 (x normal): the approximate FP64 reciprocal of the SFU as seed

@@ -667,8 +667,7 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
                     for (int k = 0; k < BPT; k++) {
                         const double dx = pj.x - xi[k], dy = pj.y - yi[k], dz = pj.z - zi[k];
                         const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-                        const double ri = rsqrt_fp64(r2);
-                        const double s = (pj.w * ri) * (ri * ri);
+                        const double s = pj.w * rsqrt3_fp64(r2);
                         px[k] = fma(s, dx, px[k]);
                         py[k] = fma(s, dy, py[k]);
                         pz[k] = fma(s, dz, pz[k]);
@@ -684,11 +683,10 @@ __global__ void __launch_bounds__(KB, 2) pass_fp64_kernel(const __grid_constant_
                     for (int k = 0; k < BPT; k++) {
                         const double dx = pj.x - xi[k], dy = pj.y - yi[k], dz = pj.z - zi[k];
                         const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-                        const double ri = rsqrt_fp64(r2);
                         const bool skip = jtp && (itp >> k & 1u);  // two test particles: no force
                         const bool near = r2 < thr[k] && !skip;
                         screened |= (unsigned)near << k;
-                        const double s = (near || skip) ? 0.0 : (pj.w * ri) * (ri * ri);
+                        const double s = (near || skip) ? 0.0 : pj.w * rsqrt3_fp64(r2);
                         px[k] = fma(s, dx, px[k]);
                         py[k] = fma(s, dy, py[k]);
                         pz[k] = fma(s, dz, pz[k]);
@@ -1108,6 +1106,11 @@ cudaError_t launch_copy_pairs(const int2 *enc, const int32_t *count, int32_t enc
                               int32_t capacity, int32_t *count_out, uint32_t *status, cudaStream_t s) {
     copy_pairs_kernel<<<64, 256, 0, s>>>(enc, count, enc_cap, pairs, capacity, count_out, status);
     return cudaGetLastError();
+}
+
+void fp64_pass_shape(int *warps, int *bpt) {
+    *warps = KB / 32;
+    *bpt = F64_BPT;
 }
 
 }  // namespace genga

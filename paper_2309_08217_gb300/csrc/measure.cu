@@ -217,6 +217,48 @@ genga_status genga_kernel_variant_info(int32_t variant, int32_t *kind, int32_t *
     return GENGA_OK;
 }
 
+genga_status genga_set_fp64_variant(genga_ctx *c, int32_t variant) {
+    if (!c || variant < -1 || variant >= 1 + num_mutual64_variants()) return GENGA_ERR_INVALID_ARG;
+    c->forced_f64 = variant;
+    return GENGA_OK;
+}
+
+genga_status genga_get_fp64_variant(genga_ctx *c, int32_t N, int32_t *variant, int32_t *num_variants) {
+    if (!c || !variant || !num_variants || N < 0) return GENGA_ERR_INVALID_ARG;
+    int b = 0;
+    for (int v = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD; v > 1; v >>= 1) b++;
+    b = b < 32 ? b : 31;
+    *variant = (c->forced_f64 >= 0) ? c->forced_f64 : c->f64_variant[b];
+    *num_variants = 1 + num_mutual64_variants();
+    return GENGA_OK;
+}
+
+genga_status genga_fp64_variant_info(int32_t variant, int32_t *kind, int32_t *warps, int32_t *bodies_per_thread) {
+    if (!kind || !warps || !bodies_per_thread || variant < 0 || variant >= 1 + num_mutual64_variants())
+        return GENGA_ERR_INVALID_ARG;
+    int cw = 0, bpt = 0;
+    if (variant == 0) {
+        fp64_pass_shape(&cw, &bpt);
+        *kind = 0;
+    } else {
+        mutual64_variant_shape(variant - 1, &cw, &bpt);
+        *kind = 1;
+    }
+    *warps = cw;
+    *bodies_per_thread = bpt;
+    return GENGA_OK;
+}
+
+genga_status genga_fp64_tuning_times(genga_ctx *c, int32_t N, float *ms, int32_t n) {
+    if (!c || !ms || n < 0 || N < 0) return GENGA_ERR_INVALID_ARG;
+    int b = 0;
+    for (int v = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD; v > 1; v >>= 1) b++;
+    b = b < 32 ? b : 31;
+    const int nv = 1 + num_mutual64_variants();
+    for (int q = 0; q < n; q++) ms[q] = (q < GENGA_MAX_VARIANTS && q < nv) ? c->tune64_ms[b][q] : 0.f;
+    return GENGA_OK;
+}
+
 genga_status genga_set_test_waits(genga_ctx *c, int32_t wait_ns_log2, int32_t hold) {
     if (!c || wait_ns_log2 < 0 || wait_ns_log2 > 40) return GENGA_ERR_INVALID_ARG;
     c->test_wait_log2 = wait_ns_log2;

@@ -671,6 +671,369 @@ __global__ void combine_mutual_kernel(const double *__restrict__ partial, const 
     }
 }
 
+// ------------------------------------------------------- FP64 mutual pass
+// The same plan, staging and reduction with FP64 arithmetic (the FP64 kick
+// of Sect. 1): i-bodies as FP64 registers, j-groups as the FP64 records
+// {x, y, z, G m}, 1/r from an FP32 SFU seed with a third-order correction,
+// FP64 sums per slot folded into Neumaier-compensated per-body sums.  NEAR
+// means inside the r_crit bound only (FP64 offsets need no precision
+// distance).  On this GPU every FP64 warp instruction holds the FP64 pipe for
+// tens of cycles, so the pair's 20 FP64 operations for two interactions (17
+// for one in the one-sided pass) set the time; everything else overlaps.
+struct CompS {  // Neumaier-compensated FP64 sum
+    double s, c;
+};
+
+__device__ __forceinline__ void comp_add(CompS &a, double v) {
+    const double t = a.s + v;
+    // |a.s| >= |v| compared on the bit patterns (integer pipe, not FP64)
+    const bool big = (__double_as_longlong(a.s) & 0x7fffffffffffffffll) >= (__double_as_longlong(v) & 0x7fffffffffffffffll);
+    a.c += big ? ((a.s - t) + v) : ((v - t) + a.s);
+    a.s = t;
+}
+
+template <int BPT, int CW, int STAGES>
+struct M64Layout {
+    static constexpr int NC = CW * 32, NPG = BPT / 2;
+    static constexpr size_t p_off = 0;                                          // double4 [STAGES][MG]
+    static constexpr size_t g_off = p_off + (size_t)STAGES * MG * 32;           // float4 [STAGES][2]
+    static constexpr size_t j_off = g_off + (size_t)STAGES * 2 * 16;            // double [STAGES][CW][3][MG]
+    static constexpr size_t c_off = j_off + (size_t)STAGES * CW * 3 * MG * 8;   // CompS [3][BPT][NC]
+    static constexpr size_t q_off = c_off + (size_t)3 * BPT * NC * 16;          // float4 [CW][NPG][2]
+    static constexpr size_t m_off = q_off + (size_t)CW * NPG * 2 * 16;          // uint32 [BPT][NC]
+    static constexpr size_t b_off = m_off + (size_t)BPT * NC * 4;               // uint64 [3][STAGES]
+    static constexpr size_t h_off = b_off + (size_t)3 * STAGES * 8;             // MHdr [STAGES]
+    static constexpr size_t bytes = h_off + (size_t)STAGES * sizeof(MHdr);
+    static_assert(bytes <= 227 * 1024, "one CTA per SM: at most 227 KB of shared memory");
+};
+
+template <int BPT, int CW, int STAGES>
+__global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __grid_constant__ PassArgs a) {
+    using L = M64Layout<BPT, CW, STAGES>;
+    constexpr int NC = L::NC, NPG = L::NPG;
+    constexpr uint32_t STAGE_BYTES = MG * 32 + 2 * 16;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    double4_32a *s_p = reinterpret_cast<double4_32a *>(smem_raw + L::p_off);
+    float4 *s_g = reinterpret_cast<float4 *>(smem_raw + L::g_off);
+    double *s_part = reinterpret_cast<double *>(smem_raw + L::j_off);
+    CompS *s_acc = reinterpret_cast<CompS *>(smem_raw + L::c_off);
+    float4 *s_qb = reinterpret_cast<float4 *>(smem_raw + L::q_off);
+    uint32_t *mk = reinterpret_cast<uint32_t *>(smem_raw + L::m_off) + threadIdx.x;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + L::b_off);
+    uint64_t *pdone = full + STAGES, *empty = pdone + STAGES;
+    MHdr *hdr = reinterpret_cast<MHdr *>(smem_raw + L::h_off);
+
+    const MutualPlan &P = a.mp;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t wlim = pass_wait_limit(a.wait_ns_log2);
+    const size_t np = (size_t)a.npad;
+    double *rows = a.partial;
+
+    if (tid == 0) {
+        for (int q = 0; q < STAGES; q++) {
+            mbar_init(&full[q], 1);
+            mbar_init(&pdone[q], CW);
+            mbar_init(&empty[q], 1);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (warp == CW) {  // -------------------------------------------- producer
+        if (lane != 0) return;
+        unsigned n = 0;
+        for (;;) {
+            const int q = atomicAdd(a.work, 1);
+            const bool done = q >= P.items;
+            const int4 it = done ? make_int4(0, 0, 0, 0) : P.item[q];
+            for (int g = it.y; done || g < it.z; g++, n++) {
+                const int slot = n % STAGES;
+                const unsigned u = n / STAGES;
+                if (u > 0 && !mbar_wait_bounded(&empty[slot], (u - 1) & 1, a.status, wlim)) return;
+                if (done) {
+                    hdr[slot] = MHdr{q, 0, 4, 0};
+                    mbar_arrive(&full[slot]);
+                    return;
+                }
+                if (a.hold) return;  // test hook: no stage is ever filled (and no copy issued)
+                hdr[slot] = MHdr{q, g, (g == it.y ? 1 : 0) | (g == it.z - 1 ? 2 : 0), 0};
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&full[slot], STAGE_BYTES);
+                bulk_g2s(s_p + slot * MG, a.p64 + (size_t)g * MG, MG * 32, &full[slot]);
+                bulk_g2s(s_g + slot * 2, a.gbox_lo + g, 16, &full[slot]);
+                bulk_g2s(s_g + slot * 2 + 1, a.gbox_hi + g, 16, &full[slot]);
+            }
+        }
+    }
+
+    if (warp == CW + 1) {  // ------------------------------------------ reducer
+        double *jrow = nullptr;
+        for (unsigned n = 0;; n++) {
+            const int slot = n % STAGES;
+            const uint32_t par = (n / STAGES) & 1;
+            if (!mbar_wait_bounded(&full[slot], par, a.status, wlim)) return;
+            const MHdr h = hdr[slot];
+            if (h.flags & 4) return;
+            if (!mbar_wait_bounded(&pdone[slot], par, a.status, wlim)) return;
+            if (h.flags & 1) {
+                const int4 it = P.item[h.item];
+                jrow = it.w < P.S ? nullptr : rows + (size_t)(P.irows + it.x) * 3 * np;
+            }
+            if (jrow) {
+                const double *sp = s_part + (size_t)slot * CW * 3 * MG;
+#pragma unroll
+                for (int half = 0; half < 2; half++) {
+                    const int jj = lane + 32 * half;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        CompS t{0.0, 0.0};
+#pragma unroll
+                        for (int w = 0; w < CW; w++) comp_add(t, sp[(w * 3 + c) * MG + jj]);
+                        jrow[c * np + (size_t)h.group * MG + jj] = t.s + t.c;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+        }
+    }
+
+    // ---------------------------------------------------------------- consumers
+    const int src = (lane + 1) & 31;
+    double XI[BPT], YI[BPT], ZI[BPT], MN[BPT];
+#pragma unroll
+    for (int k = 0; k < BPT; k++) XI[k] = YI[k] = ZI[k] = MN[k] = 0.0;
+    Box wbox = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    bool in = false, diag = false;
+    int row = 0, gw = 0;
+    unsigned qin = 0u;
+    CompS *acc = s_acc + tid;           // acc[(c * BPT + k) * NC]
+    float4 *qb = s_qb + warp * NPG * 2;
+
+    for (unsigned n = 0;; n++) {
+        const int slot = n % STAGES;
+        if (!mbar_wait_bounded(&full[slot], (n / STAGES) & 1, a.status, wlim)) return;
+        const MHdr h = hdr[slot];
+        if (h.flags & 4) return;
+        if (h.flags & 1) {  // first slot of an item: this warp's i-bodies (groups gw + q CW)
+            const int4 it = P.item[h.item];
+            row = it.w;
+            diag = row < P.S;
+            const int gb0 = it.x * P.gpb, gb1 = min(gb0 + P.gpb, P.ngroups);
+            gw = gb0 + warp;
+            qin = 0u;
+#pragma unroll
+            for (int q = 0; q < NPG; q++)
+                if (gw + q * CW < gb1) qin |= 1u << q;
+            in = qin != 0u;
+            if (in) {
+                const float INF = __int_as_float(0x7f800000);
+#pragma unroll
+                for (int k = 0; k < BPT; k++) {
+                    const bool ok = (qin >> (k >> 1)) & 1u;
+                    const int i = (gw + (k >> 1) * CW) * MG + 32 * (k & 1) + lane;
+                    const double4_32a p = ok ? a.p64[i] : make_double4_32a(GENGA_PAD_POS, GENGA_PAD_POS, GENGA_PAD_POS, 0.0);
+                    XI[k] = p.x;
+                    YI[k] = p.y;
+                    ZI[k] = p.z;
+                    MN[k] = -p.w;
+                }
+                if (lane < 2 * NPG) {
+                    const int q = lane >> 1;
+                    const bool ok = (qin >> q) & 1u;
+                    qb[lane] = (lane & 1) ? (ok ? a.gbox_hi[gw + q * CW] : make_float4(-INF, -INF, -INF, 0.f))
+                                          : (ok ? a.gbox_lo[gw + q * CW] : make_float4(INF, INF, INF, 0.f));
+                }
+#pragma unroll
+                for (int k = 0; k < 3 * BPT; k++) acc[k * NC] = CompS{0.0, 0.0};
+            }
+            __syncwarp();
+            if (in) {
+                wbox = Box{qb[0], qb[1]};
+#pragma unroll
+                for (int q = 1; q < NPG; q++) {
+                    const float4 l = qb[2 * q], u = qb[2 * q + 1];
+                    wbox.lo = make_float4(fminf(wbox.lo.x, l.x), fminf(wbox.lo.y, l.y), fminf(wbox.lo.z, l.z),
+                                          fmaxf(wbox.lo.w, l.w));
+                    wbox.hi = make_float4(fmaxf(wbox.hi.x, u.x), fmaxf(wbox.hi.y, u.y), fmaxf(wbox.hi.z, u.z),
+                                          fmaxf(wbox.hi.w, u.w));
+                }
+            }
+        }
+        const int g = h.group;
+        double *part = s_part + ((size_t)slot * CW + warp) * 3 * MG;
+        if (in) {
+            const bool both = !diag;
+            const Box gb = {s_g[slot * 2], s_g[slot * 2 + 1]};
+            const double4_32a *tp = s_p + slot * MG;
+            // NEAR i-groups (inside the r_crit bound of the j-group): their
+            // pairs are compared with the screening bound (integer compare of
+            // the FP64 bit patterns of r^2 and of the bound: both positive)
+            unsigned qnear = 0u;
+            long long thr[NPG];
+#pragma unroll
+            for (int q = 0; q < NPG; q++) {
+                thr[q] = 0;
+                if (!far_pair_of_boxes(wbox, gb, false) && !far_pair_of_boxes(Box{qb[2 * q], qb[2 * q + 1]}, gb, false)) {
+                    qnear |= 1u << q;
+                    thr[q] = __double_as_longlong((double)screen_threshold(qb[2 * q].w, qb[2 * q + 1].w, gb.lo.w, gb.hi.w));
+                }
+            }
+            const int dg = g - gw;
+            const int gself = (both || dg < 0 || dg % CW != 0 || dg / CW >= NPG) ? -1 : dg / CW;
+            double PX[BPT], PY[BPT], PZ[BPT];
+#pragma unroll
+            for (int k = 0; k < BPT; k++) PX[k] = PY[k] = PZ[k] = 0.0;
+#pragma unroll 1
+            for (int sb = 0; sb < 2; sb++) {
+                double JX = 0.0, JY = 0.0, JZ = 0.0;
+                if (qnear) {
+#pragma unroll
+                    for (int k = 0; k < BPT; k++) mk[k * NC] = 0u;
+                }
+#pragma unroll 2
+                for (int t = 0; t < 32; t++) {
+                    const int jj = (lane + t) & 31;
+                    const double4_32a pj = tp[sb * 32 + jj];
+#pragma unroll
+                    for (int k = 0; k < BPT; k++) {
+                        const double dx = pj.x - XI[k], dy = pj.y - YI[k], dz = pj.z - ZI[k];
+                        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+                        const double r3 = rsqrt3_fp64(r2);
+                        double si = pj.w * r3, sj = MN[k] * r3;
+                        if ((qnear >> (k >> 1)) & 1u) {
+                            const bool self = t == 0 && (k >> 1) == gself && (k & 1) == sb;
+                            if (__double_as_longlong(r2) < thr[k >> 1] || self) {  // rare: exact FP64 afterwards
+                                si = 0.0;
+                                sj = 0.0;
+                                mk[k * NC] |= 1u << jj;
+                            }
+                        }
+                        PX[k] = fma(si, dx, PX[k]);
+                        PY[k] = fma(si, dy, PY[k]);
+                        PZ[k] = fma(si, dz, PZ[k]);
+                        if (both) {
+                            JX = fma(sj, dx, JX);
+                            JY = fma(sj, dy, JY);
+                            JZ = fma(sj, dz, JZ);
+                        }
+                    }
+                    if (both) {
+                        JX = __shfl_sync(0xffffffffu, JX, src);
+                        JY = __shfl_sync(0xffffffffu, JY, src);
+                        JZ = __shfl_sync(0xffffffffu, JZ, src);
+                    }
+                }
+                if (both) {
+                    part[0 * MG + sb * 32 + lane] = JX;
+                    part[1 * MG + sb * 32 + lane] = JY;
+                    part[2 * MG + sb * 32 + lane] = JZ;
+                }
+                if (qnear) {  // screened pairs exactly (K-weighted), both sides
+                    __syncwarp();
+                    for (;;) {
+                        int kk = -1, jj = 0;
+                        for (int k = 0; k < BPT && kk < 0; k++) {
+                            const unsigned m = mk[k * NC];
+                            if (m) {
+                                kk = k;
+                                jj = __ffs((int)m) - 1;
+                                mk[k * NC] = m & (m - 1u);
+                            }
+                        }
+                        if (!__any_sync(0xffffffffu, kk >= 0)) break;
+                        double3 fi = make_double3(0.0, 0.0, 0.0), fj = fi;
+                        if (kk >= 0) {
+                            const int i = (gw + (kk >> 1) * CW) * MG + 32 * (kk & 1) + lane, j = g * MG + sb * 32 + jj;
+                            screened_pair_mutual(a, i, j, 0, a.N, 0, both, &fi, &fj);
+                            comp_add(acc[(0 * BPT + kk) * NC], fi.x);
+                            comp_add(acc[(1 * BPT + kk) * NC], fi.y);
+                            comp_add(acc[(2 * BPT + kk) * NC], fi.z);
+                        }
+                        if (both) {
+                            const int js = kk >= 0 ? sb * 32 + jj : -1;
+                            for (int s2 = 0; s2 < 32; s2++) {
+                                const int j2 = __shfl_sync(0xffffffffu, js, s2);
+                                const double gx = __shfl_sync(0xffffffffu, fj.x, s2);
+                                const double gy = __shfl_sync(0xffffffffu, fj.y, s2);
+                                const double gz = __shfl_sync(0xffffffffu, fj.z, s2);
+                                if (lane == 0 && j2 >= 0) {
+                                    part[0 * MG + j2] += gx;
+                                    part[1 * MG + j2] += gy;
+                                    part[2 * MG + j2] += gz;
+                                }
+                            }
+                            __syncwarp();
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < BPT; k++) {  // this slot's sums into the compensated per-body sums
+                comp_add(acc[(0 * BPT + k) * NC], PX[k]);
+                comp_add(acc[(1 * BPT + k) * NC], PY[k]);
+                comp_add(acc[(2 * BPT + k) * NC], PZ[k]);
+            }
+        } else if (!diag) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) part[c * MG + lane] = part[c * MG + 32 + lane] = 0.0;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&pdone[slot]);
+        if (in && (h.flags & 2)) {  // last slot of the item: its i-row
+            double *out = rows + (size_t)row * 3 * np;
+#pragma unroll
+            for (int k = 0; k < BPT; k++) {
+                if (!((qin >> (k >> 1)) & 1u)) continue;
+                const size_t i = (size_t)(gw + (k >> 1) * CW) * MG + 32 * (k & 1) + lane;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const CompS t = acc[(c * BPT + k) * NC];
+                    out[c * np + i] = t.s + t.c;
+                }
+            }
+        }
+    }
+}
+
+// One thread per (body, component): the FP64 rows of a mutual FP64 pass in
+// the order of combine_mutual_kernel, Neumaier-compensated.
+__global__ void combine_mutual64_kernel(const double *__restrict__ partial, const __grid_constant__ MutualPlan P,
+                                        int N, int npad, const uint32_t *__restrict__ perm, double tau,
+                                        double *__restrict__ acc, double *__restrict__ vx, double *__restrict__ vy,
+                                        double *__restrict__ vz, uint32_t *__restrict__ status) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (k >= N) return;
+    const int b = k / (P.gpb * MG);
+    const size_t stride = 3 * (size_t)npad;
+    const double *p = partial + (size_t)c * npad + k;
+    const int2 bk = P.blk[b];
+    const int n0 = bk.x, n1 = n0 + bk.y, n2 = n1 + b;
+    CompS t{0.0, 0.0};
+    constexpr int BATCH = 16;
+    for (int r0 = 0; r0 < n2; r0 += BATCH) {
+        double v[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; u++) {
+            const int r = r0 + u;
+            const int rr = r < n0 ? r : r < n1 ? P.S + (r - n0) : P.irows + (r - n1);
+            v[u] = r < n2 ? p[(size_t)rr * stride] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < BATCH; u++)
+            if (r0 + u < n2) comp_add(t, v[u]);
+    }
+    const double s = t.s + t.c;
+    if (!isfinite(s)) atomicOr(status, GENGA_BIT(GENGA_ERR_NONFINITE));
+    const int i = (int)perm[k];
+    if (acc) acc[c * (size_t)N + i] = s;
+    if (tau != 0.0) {
+        double *v = c == 0 ? vx : (c == 1 ? vy : vz);
+        v[i] += s * tau;
+    }
+}
+
 // --------------------------------------------------------------- variants
 struct MVariant {
     int np, cw;
@@ -682,6 +1045,18 @@ struct MVariant {
 const MVariant kMVariants[] = {GENGA_MV(4, 10, 4, 2), GENGA_MV(4, 8, 6, 2), GENGA_MV(2, 12, 6, 2)};
 #undef GENGA_MV
 constexpr int kNumMVariants = sizeof(kMVariants) / sizeof(kMVariants[0]);
+
+struct M64Variant {
+    int bpt, cw;
+    void (*fn)(const PassArgs);
+    size_t smem;
+};
+#define GENGA_M64(BPT, CW, ST) \
+    {BPT, CW, pass_mutual64_kernel<BPT, CW, ST>, M64Layout<BPT, CW, ST>::bytes}
+const M64Variant kM64Variants[] = {GENGA_M64(4, 8, 4), GENGA_M64(8, 4, 4), GENGA_M64(2, 12, 4)};
+#undef GENGA_M64
+constexpr int kNumM64Variants = sizeof(kM64Variants) / sizeof(kM64Variants[0]);
+static_assert(kNumMVariants + kNumM64Variants <= GENGA_MAX_VARIANTS, "plan cache slots");
 
 // ---------------------------------------------------------------- planner
 // Cost model, in units of one slot of far pairs for both sides (every warp
@@ -820,6 +1195,11 @@ void plan_items(int npad, int cw, int NPg, int ctas, int max_rows, std::vector<i
 }  // namespace
 
 int num_mutual_variants() { return kNumMVariants; }
+int num_mutual64_variants() { return kNumM64Variants; }
+void mutual64_variant_shape(int v, int *cw, int *bpt) {
+    *cw = kM64Variants[v].cw;
+    *bpt = kM64Variants[v].bpt;
+}
 void mutual_variant_shape(int v, int *cw, int *bpt) {
     *cw = kMVariants[v].cw;
     *bpt = 2 * kMVariants[v].np;
@@ -835,12 +1215,12 @@ void free_mutual_cache(genga_ctx *c) {
     c->mcache = nullptr;
 }
 
-// The plan of mutual variant v for N bodies, built (and uploaded) on first
-// use.  Returns false when it must be built while `s` is being captured, or
+// The plan for N bodies of the variant in cache slot v (cw consumer warps of
+// npg groups each), built (and uploaded) on first use.  Returns false when it must be built while `s` is being captured, or
 // when it does not fit the partial rows: the caller then uses a one-sided
 // variant.
-bool mutual_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P) {
-    if (v < 0 || v >= kNumMVariants || v >= GENGA_MAX_VARIANTS) return false;
+static bool plan_for_shape(genga_ctx *c, int N, int v, int cw, int npg, cudaStream_t s, MutualPlan *P) {
+    if (v < 0 || v >= GENGA_MAX_VARIANTS) return false;
     if (!c->mcache) {
         c->mcache = new (std::nothrow) MutualCache();
         if (!c->mcache) return false;
@@ -856,7 +1236,7 @@ bool mutual_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P) {
         // partial rows: up to MUTUAL_MAX_ROWS (the workspace grows to the plan's need)
         const int max_rows = std::max((int)std::min<size_t>(c->partial_cap / (3 * (size_t)npad), 1 << 20),
                                       MUTUAL_MAX_ROWS);
-        plan_items(npad, kMVariants[v].cw, kMVariants[v].np, c->sm_count, max_rows, &items, &blk, &S);
+        plan_items(npad, cw, npg, c->sm_count, max_rows, &items, &blk, &S);
         if (cudaStreamSynchronize(s) != cudaSuccess) return false;  // the old tables may be in use
         if (e.d_item) cudaFree(e.d_item);
         if (e.d_blk) cudaFree(e.d_blk);
@@ -887,7 +1267,7 @@ bool mutual_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P) {
             cudaMemcpy(e.d_blk, blk.data(), blk.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
             return false;
         e.nb = nb;
-        e.gpb = kMVariants[v].cw * kMVariants[v].np;
+        e.gpb = cw * npg;
         e.ngroups = npad / MG;
         e.items = (int)items.size();
         e.irows = irows;
@@ -899,13 +1279,47 @@ bool mutual_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P) {
     return true;
 }
 
+bool mutual_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P) {
+    if (v < 0 || v >= kNumMVariants) return false;
+    return plan_for_shape(c, N, v, kMVariants[v].cw, kMVariants[v].np, s, P);
+}
+
+bool mutual64_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P) {
+    if (v < 0 || v >= kNumM64Variants) return false;
+    return plan_for_shape(c, N, kNumMVariants + v, kM64Variants[v].cw, kM64Variants[v].bpt / 2, s, P);
+}
+
 cudaError_t init_mutual_kernels() {
     for (int q = 0; q < kNumMVariants; q++) {
         cudaError_t e = cudaFuncSetAttribute(kMVariants[q].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kMVariants[q].smem);
         if (e != cudaSuccess) return e;
     }
+    for (int q = 0; q < kNumM64Variants; q++) {
+        cudaError_t e = cudaFuncSetAttribute(kM64Variants[q].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kM64Variants[q].smem);
+        if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
+}
+
+cudaError_t launch_pass_mutual64(const PassArgs &a0, int v, int sm_count, cudaStream_t s) {
+    PassArgs a = a0;
+    const M64Variant &mv = kM64Variants[v];
+    cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(sm_count, a.mp.items);
+    mv.fn<<<grid, (mv.cw + 2) * 32, mv.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine_mutual64(const double *partial, const MutualPlan &P, int N, int npad, const uint32_t *perm,
+                                    double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
+                                    cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    combine_mutual64_kernel<<<dim3((N + 255) / 256, 3), 256, 0, s>>>(partial, P, N, npad, perm, tau, acc, vx, vy, vz,
+                                                                      status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pass_mutual(const PassArgs &a0, int v, int sm_count, cudaStream_t s) {
