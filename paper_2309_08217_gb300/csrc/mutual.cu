@@ -78,12 +78,14 @@ struct MHdr {
     int item, group, flags, pad;  // flags: 1 first slot of the item, 2 last, 4 no more work
 };
 
-__device__ __forceinline__ f32x2 shfl2(f32x2 v, int src) {
-    float a, b;
-    up2(v, a, b);
-    a = __shfl_sync(0xffffffffu, a, src);
-    b = __shfl_sync(0xffffffffu, b, src);
-    return pk2(a, b);
+// J += S.lo D.lo + S.hi D.hi: a j-body's terms from the two i-bodies of a
+// packed register, in one scalar running sum (one shuffle per component and
+// step instead of two; the same FMA-pipe cycles as one packed FMA)
+__device__ __forceinline__ void jsum(float &J, f32x2 S, f32x2 D) {
+    float s0, s1, d0, d1;
+    up2(S, s0, s1);
+    up2(D, d0, d1);
+    J = fmaf(s1, d1, fmaf(s0, d0, J));
 }
 
 __device__ __forceinline__ f32x2 rsq2(f32x2 r2) {
@@ -174,8 +176,8 @@ __device__ __noinline__ void screened_pair_mutual(const PassArgs &a, int i, int 
 template <int NP, int CW, int STAGES>
 struct MLayout {
     static constexpr int BPT = 2 * NP, NC = CW * 32;
-    static constexpr size_t r_off = 0;                                         // float4 [STAGES][2 MG]
-    static constexpr size_t l_off = r_off + (size_t)STAGES * 2 * MG * 16;      // float4 [STAGES][MG]
+    static constexpr size_t r_off = 0;                                         // float [STAGES][4][MG]
+    static constexpr size_t l_off = r_off + (size_t)STAGES * 4 * MG * 4;       // float4 [STAGES][MG]
     static constexpr size_t g_off = l_off + (size_t)STAGES * MG * 16;          // float4 [STAGES][4]
     static constexpr size_t p_off = g_off + (size_t)STAGES * 4 * 16;           // float [STAGES][CW][3][MG]
     static constexpr size_t a_off = p_off + (size_t)STAGES * CW * 3 * MG * 4;  // DF [3][BPT][NC]
@@ -201,9 +203,9 @@ template <int NP, int CW, int STAGES, int UNR>
 __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __grid_constant__ PassArgs a) {
     using L = MLayout<NP, CW, STAGES>;
     constexpr int BPT = L::BPT, NC = L::NC;
-    constexpr uint32_t STAGE_BYTES = 2 * MG * 16 + MG * 16 + 3 * 16;
+    constexpr uint32_t STAGE_BYTES = 4 * MG * 4 + MG * 16 + 3 * 16;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float4 *s_r = reinterpret_cast<float4 *>(smem_raw + L::r_off);
+    float *s_r = reinterpret_cast<float *>(smem_raw + L::r_off);
     float4 *s_l = reinterpret_cast<float4 *>(smem_raw + L::l_off);
     float4 *s_g = reinterpret_cast<float4 *>(smem_raw + L::g_off);
     float *s_part = reinterpret_cast<float *>(smem_raw + L::p_off);
@@ -252,7 +254,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                 hdr[slot] = MHdr{q, g, (g == it.y ? 1 : 0) | (g == it.z - 1 ? 2 : 0), 0};
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&full[slot], STAGE_BYTES);
-                bulk_g2s(s_r + slot * 2 * MG, a.rel + (size_t)g * 2 * MG, 2 * MG * 16, &full[slot]);
+                bulk_g2s(s_r + slot * 4 * MG, a.rel + (size_t)g * 4 * MG, 4 * MG * 4, &full[slot]);
                 bulk_g2s(s_l + slot * MG, a.rell + (size_t)g * MG, MG * 16, &full[slot]);
                 bulk_g2s(s_g + slot * 4, a.gbox_lo + g, 16, &full[slot]);
                 bulk_g2s(s_g + slot * 4 + 1, a.gbox_hi + g, 16, &full[slot]);
@@ -379,7 +381,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
             const bool both = !diag;
             const Box gb = {s_g[slot * 4], s_g[slot * 4 + 1]};
             const float4 ctr = s_g[slot * 4 + 2];
-            const float4 *tr = s_r + slot * 2 * MG;
+            const float *tr = s_r + slot * 4 * MG;  // X[64], Y[64], Z[64], G m[64] of the j-group
             // the warp's i-bodies relative to the group centre
             f32x2 XI[NP], YI[NP], ZI[NP];
 #pragma unroll
@@ -404,43 +406,40 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                 constexpr bool BOTH = decltype(both_tag)::value;
 #pragma unroll 1
                 for (int sb = 0; sb < 2; sb++) {
-                    f32x2 JX = 0ull, JY = 0ull, JZ = 0ull;
+                    float JX = 0.f, JY = 0.f, JZ = 0.f;
 #pragma unroll(UNR)
                     for (int t = 0; t < 32; t++) {
+                        // consecutive j across the lanes: conflict-free scalar loads
                         const int j = sb * 32 + ((lane + t) & 31);
-                        const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(tr + 2 * j);      // {X X}, {Y Y}
-                        const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(tr + 2 * j + 1);  // {Z Z}, {Gm Gm}
+                        const float xj = tr[j], yj = tr[MG + j], zj = tr[2 * MG + j], mj = tr[3 * MG + j];
+                        const f32x2 AX = pk2(xj, xj), AY = pk2(yj, yj), AZ = pk2(zj, zj), AM = pk2(mj, mj);
 #pragma unroll
                         for (int q = 0; q < NP; q++) {
-                            const f32x2 DX = sub2(A.x, XI[q]), DY = sub2(A.y, YI[q]), DZ = sub2(B.x, ZI[q]);
+                            const f32x2 DX = sub2(AX, XI[q]), DY = sub2(AY, YI[q]), DZ = sub2(AZ, ZI[q]);
                             const f32x2 R2 = fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
                             const f32x2 RI = rsq2(R2);
                             const f32x2 R3 = mul2(mul2(RI, RI), RI);
-                            const f32x2 SI = mul2(B.y, R3);
+                            const f32x2 SI = mul2(AM, R3);
                             TX[q] = fma2(SI, DX, TX[q]);
                             TY[q] = fma2(SI, DY, TY[q]);
                             TZ[q] = fma2(SI, DZ, TZ[q]);
                             if constexpr (BOTH) {
                                 const f32x2 SJ = mul2(MN[q], R3);
-                                JX = fma2(SJ, DX, JX);
-                                JY = fma2(SJ, DY, JY);
-                                JZ = fma2(SJ, DZ, JZ);
+                                jsum(JX, SJ, DX);
+                                jsum(JY, SJ, DY);
+                                jsum(JZ, SJ, DZ);
                             }
                         }
                         if constexpr (BOTH) {
-                            JX = shfl2(JX, src);
-                            JY = shfl2(JY, src);
-                            JZ = shfl2(JZ, src);
+                            JX = __shfl_sync(0xffffffffu, JX, src);
+                            JY = __shfl_sync(0xffffffffu, JY, src);
+                            JZ = __shfl_sync(0xffffffffu, JZ, src);
                         }
                     }
                     if constexpr (BOTH) {
-                        float u0, u1;
-                        up2(JX, u0, u1);
-                        part[0 * MG + sb * 32 + lane] = u0 + u1;
-                        up2(JY, u0, u1);
-                        part[1 * MG + sb * 32 + lane] = u0 + u1;
-                        up2(JZ, u0, u1);
-                        part[2 * MG + sb * 32 + lane] = u0 + u1;
+                        part[0 * MG + sb * 32 + lane] = JX;
+                        part[1 * MG + sb * 32 + lane] = JY;
+                        part[2 * MG + sb * 32 + lane] = JZ;
                     }
                 }
             };
@@ -482,19 +481,19 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                 }
 #pragma unroll 1
                 for (int sb = 0; sb < 2; sb++) {
-                    f32x2 JX = 0ull, JY = 0ull, JZ = 0ull;
+                    float JX = 0.f, JY = 0.f, JZ = 0.f;
                     // bit jj of mk[k * NC]: pair (i_k, j = sb * 32 + jj) is under the screening bound
 #pragma unroll
                     for (int k = 0; k < BPT; k++) mk[k * NC] = 0u;
 #pragma unroll 1
                     for (int t = 0; t < 32; t++) {
                         const int jj = (lane + t) & 31, j = sb * 32 + jj;
-                        const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(tr + 2 * j);
-                        const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(tr + 2 * j + 1);
+                        const float xj = tr[j], yj = tr[MG + j], zj = tr[2 * MG + j], mj = tr[3 * MG + j];
+                        const f32x2 AX = pk2(xj, xj), AY = pk2(yj, yj), AZ = pk2(zj, zj), AM = pk2(mj, mj);
                         const float4 R = tl[j];
 #pragma unroll
                         for (int q = 0; q < NP; q++) {
-                            f32x2 DX = sub2(A.x, XI[q]), DY = sub2(A.y, YI[q]), DZ = sub2(B.x, ZI[q]);
+                            f32x2 DX = sub2(AX, XI[q]), DY = sub2(AY, YI[q]), DZ = sub2(AZ, ZI[q]);
                             const bool qn = (qnear >> q) & 1u;
                             if (qn) {
                                 DX = add2(DX, sub2(pk2(R.x, R.x), res[(q * 3 + 0) * NC]));
@@ -504,7 +503,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                             const f32x2 R2 = fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
                             const f32x2 RI = rsq2(R2);
                             const f32x2 R3 = mul2(mul2(RI, RI), RI);
-                            f32x2 SI = mul2(B.y, R3), SJ = mul2(MN[q], R3);
+                            f32x2 SI = mul2(AM, R3), SJ = mul2(MN[q], R3);
                             if (qn) {
                                 float ra, rb;
                                 up2(R2, ra, rb);
@@ -525,25 +524,21 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                             TY[q] = fma2(SI, DY, TY[q]);
                             TZ[q] = fma2(SI, DZ, TZ[q]);
                             if (both) {
-                                JX = fma2(SJ, DX, JX);
-                                JY = fma2(SJ, DY, JY);
-                                JZ = fma2(SJ, DZ, JZ);
+                                jsum(JX, SJ, DX);
+                                jsum(JY, SJ, DY);
+                                jsum(JZ, SJ, DZ);
                             }
                         }
                         if (both) {
-                            JX = shfl2(JX, src);
-                            JY = shfl2(JY, src);
-                            JZ = shfl2(JZ, src);
+                            JX = __shfl_sync(0xffffffffu, JX, src);
+                            JY = __shfl_sync(0xffffffffu, JY, src);
+                            JZ = __shfl_sync(0xffffffffu, JZ, src);
                         }
                     }
                     if (both) {
-                        float u0, u1;
-                        up2(JX, u0, u1);
-                        part[0 * MG + sb * 32 + lane] = u0 + u1;
-                        up2(JY, u0, u1);
-                        part[1 * MG + sb * 32 + lane] = u0 + u1;
-                        up2(JZ, u0, u1);
-                        part[2 * MG + sb * 32 + lane] = u0 + u1;
+                        part[0 * MG + sb * 32 + lane] = JX;
+                        part[1 * MG + sb * 32 + lane] = JY;
+                        part[2 * MG + sb * 32 + lane] = JZ;
                     }
                     // the screened pairs of this half of the group, exactly in
                     // FP64: all lanes evaluate one pair each per round; the
