@@ -38,9 +38,9 @@
 // j-group: X_j = fl32(x_j - c) (the FP64 difference rounded, computed by the
 // prep kernel) and X_i = fl32(fl32(x_i,hi - c) + x_i,lo).  A group is FAR for
 // an i-tile when every pair is beyond both the r_crit bound and the group's
-// precision distance (half its half-diagonal), so the offset X_j - X_i is
-// within ~3 u (1 + 2) of x_j - x_i (u = 2^-24): there the pair terms need no
-// screening.  Otherwise (NEAR) the offsets carry the exact residuals, every
+// precision distance (a tenth of its half-diagonal h), so the offset
+// X_j - X_i is within 3 u (1 + 10) relative of x_j - x_i (u = 2^-24): there
+// the pair terms need no screening.  Otherwise (NEAR) the offsets carry the exact residuals, every
 // pair is compared with an FP32 upper bound of r_crit,ij^2, and the pairs
 // under it are evaluated exactly in FP64 afterwards (K-weighted, both sides,
 // encounter list) -- close-encounter forces are always FP64 (Sect. 1).
@@ -203,6 +203,7 @@ template <int NP, int CW, int STAGES, int UNR>
 __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __grid_constant__ PassArgs a) {
     using L = MLayout<NP, CW, STAGES>;
     constexpr int BPT = L::BPT, NC = L::NC;
+    constexpr int NEAR_UNR = NP <= 2 ? 2 : 1;  // NEAR-loop unroll (register budget)
     constexpr uint32_t STAGE_BYTES = 4 * MG * 4 + MG * 16 + 3 * 16;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *s_r = reinterpret_cast<float *>(smem_raw + L::r_off);
@@ -485,7 +486,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                     // bit jj of mk[k * NC]: pair (i_k, j = sb * 32 + jj) is under the screening bound
 #pragma unroll
                     for (int k = 0; k < BPT; k++) mk[k * NC] = 0u;
-#pragma unroll 1
+#pragma unroll(NEAR_UNR)
                     for (int t = 0; t < 32; t++) {
                         const int jj = (lane + t) & 31, j = sb * 32 + jj;
                         const float xj = tr[j], yj = tr[MG + j], zj = tr[2 * MG + j], mj = tr[3 * MG + j];

@@ -221,15 +221,17 @@ __device__ __forceinline__ Box group_reduce_store(float2 s, float3 pos, bool rea
 
 // Group-centred copies for the mutual FP32 pass: c = the centre of the
 // group's box (an FP32 value), each body's offset from it as the FP64
-// difference rounded to FP32 (X = fl32(x - c)), duplicated for the packed
-// loop ({X, X, Y, Y}, {Z, Z, G m, G m}), and its rounding residual
+// difference rounded to FP32 (X = fl32(x - c)), stored per 64-body group as
+// four arrays X[64], Y[64], Z[64], G m[64], and its rounding residual
 // {x - c - X, y - c - Y, z - c - Z, test-particle flag}; per group
-// {c, PRECISION_KAPPA * h}, h an upper bound of |x - c| over the group (the
-// pass treats a group as far from a set of bodies only beyond that distance,
-// which bounds the relative error of an offset Xj - Xi to about
-// 3 u (1 + 1/PRECISION_KAPPA) = 15 u, u = 2^-24).  An empty group (padding
-// only) has c = 0 and distance 0.
-constexpr float PRECISION_KAPPA = 0.25f;
+// {c, PRECISION_KAPPA * h}, h an upper bound of |x - c| over the group.  The
+// pass treats a group as far from a set of bodies only beyond that distance:
+// with |x_j - c| <= h, |x_i - c| <= r + h and three roundings (X_j, the
+// two-step X_i, the difference) the offset X_j - X_i is within
+// 3 u (r + h) of x_j - x_i, a relative error of at most
+// 3 u (1 + 1/PRECISION_KAPPA) = 33 u ~ 2e-6 (u = 2^-24), about 6e-6 on the
+// pair's force.  An empty group (padding only) has c = 0 and distance 0.
+constexpr float PRECISION_KAPPA = 0.1f;
 
 __device__ __forceinline__ void store_centred(int k, const Box &b, double4 p, bool tp, float *__restrict__ rel,
                                               float4 *__restrict__ rell, float4 *__restrict__ gctr) {
