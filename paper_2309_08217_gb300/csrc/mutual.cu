@@ -73,6 +73,7 @@ namespace {
 constexpr int MG = 64;           // bodies per staged j-group
 constexpr int MUTUAL_MAX_ROWS = 192;  // partial rows a mutual plan may use (its workspace grows to them)
 constexpr int M_FOLD = 4;        // slots between folds of the FP32 i-sums into double-float
+constexpr int M_CLAIM = 3;       // a producer claims an item when the leading warp has at most M_CLAIM - 1 slots left
 
 struct MHdr {
     int item, group, flags, pad;  // flags: 1 first slot of the item, 2 last, 4 no more work
@@ -86,6 +87,22 @@ __device__ __forceinline__ void jsum(float &J, f32x2 S, f32x2 D) {
     up2(S, s0, s1);
     up2(D, d0, d1);
     J = fmaf(s1, d1, fmaf(s0, d0, J));
+}
+
+// Wait until the leading consumer warp has finished `target` slots, bounded
+// like the mbarrier waits (a progress hint: no data passes through it).
+__device__ __forceinline__ bool wait_lead(const unsigned *lead, unsigned target, uint32_t *status,
+                                          uint64_t limit_ns) {
+    if (*(volatile const unsigned *)lead >= target) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (*(volatile const unsigned *)lead < target) {
+        if (global_timer_ns() - t0 > limit_ns) {
+            atomicOr(status, GENGA_BIT(GENGA_ERR_TIMEOUT));
+            return false;
+        }
+        __nanosleep(32);
+    }
+    return true;
 }
 
 __device__ __forceinline__ f32x2 rsq2(f32x2 r2) {
@@ -225,6 +242,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
     const size_t np = (size_t)a.npad;
     float2 *rows = reinterpret_cast<float2 *>(a.partial);
 
+    __shared__ unsigned s_lead;  // slots the leading consumer warp has finished
     if (tid == 0) {
         for (int q = 0; q < STAGES; q++) {
             mbar_init(&full[q], 1);
@@ -232,6 +250,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
             mbar_init(&empty[q], 1);
         }
         fence_barrier_init();
+        s_lead = 0u;
     }
     __syncthreads();
 
@@ -239,6 +258,12 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
         if (lane != 0) return;
         unsigned n = 0;
         for (;;) {
+            // claim the next item only when the leading consumer warp is
+            // within M_CLAIM - 1 filled slots of the end of this CTA's work
+            // (inside an item the ring still runs up to STAGES slots ahead of
+            // the slowest warp): a CTA then holds no queued slots that an
+            // idle CTA could have taken, which evens out the CTAs' end times
+            if (n >= (unsigned)M_CLAIM && !wait_lead(&s_lead, n - M_CLAIM + 1, a.status, wlim)) return;
             const int q = atomicAdd(a.work, 1);
             const bool done = q >= P.items;
             const int4 it = done ? make_int4(0, 0, 0, 0) : P.item[q];
@@ -464,10 +489,11 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                 // only for those) and their screening bounds (the i-group's
                 // largest H and A against the j-group's)
                 float thr[NP];
+                const unsigned qres = NP <= 2 ? qnear : (1u << NP) - 1u;  // i-groups taking the NEAR treatment
 #pragma unroll
                 for (int q = 0; q < NP; q++) {
                     thr[q] = 0.f;
-                    if (qnear & (1u << q)) {
+                    if (qres & (1u << q)) {
                         const float4 h0 = ip[(2 * q) * NC], h1 = ip[(2 * q + 1) * NC];
                         const float4 l0 = ip[(BPT + 2 * q) * NC], l1 = ip[(BPT + 2 * q + 1) * NC];
                         float x0, x1, y0, y1, z0, z1;
@@ -480,111 +506,138 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                         thr[q] = screen_threshold(qb[2 * q].w, qb[2 * q + 1].w, gb.lo.w, gb.hi.w);
                     }
                 }
+                // the NEAR loop, specialised on the set QN of NEAR i-groups
+                // (known at compile time: no branches between the packed
+                // chains); a screened pair's flag goes to a per-lane bit mask
+                auto near_loop = [&](auto both_tag, auto mask_tag) {
+                    constexpr bool BOTH = decltype(both_tag)::value;
+                    constexpr unsigned QN = decltype(mask_tag)::value;
 #pragma unroll 1
-                for (int sb = 0; sb < 2; sb++) {
-                    float JX = 0.f, JY = 0.f, JZ = 0.f;
-                    // bit jj of mk[k * NC]: pair (i_k, j = sb * 32 + jj) is under the screening bound
+                    for (int sb = 0; sb < 2; sb++) {
+                        float JX = 0.f, JY = 0.f, JZ = 0.f;
+                        // bit jj of M0[q] / M1[q]: pair (i_{2q} / i_{2q+1}, j = sb * 32 + jj) is screened
+                        unsigned M0[NP], M1[NP];
 #pragma unroll
-                    for (int k = 0; k < BPT; k++) mk[k * NC] = 0u;
+                        for (int q = 0; q < NP; q++) M0[q] = M1[q] = 0u;
 #pragma unroll(NEAR_UNR)
-                    for (int t = 0; t < 32; t++) {
-                        const int jj = (lane + t) & 31, j = sb * 32 + jj;
-                        const float xj = tr[j], yj = tr[MG + j], zj = tr[2 * MG + j], mj = tr[3 * MG + j];
-                        const f32x2 AX = pk2(xj, xj), AY = pk2(yj, yj), AZ = pk2(zj, zj), AM = pk2(mj, mj);
-                        const float4 R = tl[j];
+                        for (int t = 0; t < 32; t++) {
+                            const int jj = (lane + t) & 31, j = sb * 32 + jj;
+                            const float xj = tr[j], yj = tr[MG + j], zj = tr[2 * MG + j], mj = tr[3 * MG + j];
+                            const f32x2 AX = pk2(xj, xj), AY = pk2(yj, yj), AZ = pk2(zj, zj), AM = pk2(mj, mj);
+                            const float4 R = tl[j];
+                            const f32x2 RX = pk2(R.x, R.x), RY = pk2(R.y, R.y), RZ = pk2(R.z, R.z);
 #pragma unroll
-                        for (int q = 0; q < NP; q++) {
-                            f32x2 DX = sub2(AX, XI[q]), DY = sub2(AY, YI[q]), DZ = sub2(AZ, ZI[q]);
-                            const bool qn = (qnear >> q) & 1u;
-                            if (qn) {
-                                DX = add2(DX, sub2(pk2(R.x, R.x), res[(q * 3 + 0) * NC]));
-                                DY = add2(DY, sub2(pk2(R.y, R.y), res[(q * 3 + 1) * NC]));
-                                DZ = add2(DZ, sub2(pk2(R.z, R.z), res[(q * 3 + 2) * NC]));
-                            }
-                            const f32x2 R2 = fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
-                            const f32x2 RI = rsq2(R2);
-                            const f32x2 R3 = mul2(mul2(RI, RI), RI);
-                            f32x2 SI = mul2(AM, R3), SJ = mul2(MN[q], R3);
-                            if (qn) {
-                                float ra, rb;
-                                up2(R2, ra, rb);
-                                const bool self = t == 0 && q == gself;
-                                const bool na = ra < thr[q] || (self && sb == 0);
-                                const bool nb = rb < thr[q] || (self && sb == 1);
-                                if (na || nb) {  // rare: screened pairs leave the FP32 sums
-                                    float sa, sb_;
+                            for (int q = 0; q < NP; q++) {
+                                f32x2 DX = sub2(AX, XI[q]), DY = sub2(AY, YI[q]), DZ = sub2(AZ, ZI[q]);
+                                if (((QN >> q) & 1u) != 0u) {  // folded at compile time (q unrolled)
+                                    DX = add2(DX, sub2(RX, res[(q * 3 + 0) * NC]));
+                                    DY = add2(DY, sub2(RY, res[(q * 3 + 1) * NC]));
+                                    DZ = add2(DZ, sub2(RZ, res[(q * 3 + 2) * NC]));
+                                }
+                                const f32x2 R2 = fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
+                                const f32x2 RI = rsq2(R2);
+                                const f32x2 R3 = mul2(mul2(RI, RI), RI);
+                                f32x2 SI = mul2(AM, R3), SJ = mul2(MN[q], R3);
+                                if (((QN >> q) & 1u) != 0u) {  // folded at compile time (q unrolled)
+                                    float ra, rb, sa, sb_, ja, jb;
+                                    up2(R2, ra, rb);
+                                    const bool self = t == 0 && q == gself;
+                                    const bool na = ra < thr[q] || (self && sb == 0);
+                                    const bool nb = rb < thr[q] || (self && sb == 1);
+                                    // screened pairs leave the FP32 sums (exact FP64 afterwards)
                                     up2(SI, sa, sb_);
                                     SI = pk2(na ? 0.f : sa, nb ? 0.f : sb_);
-                                    up2(SJ, sa, sb_);
-                                    SJ = pk2(na ? 0.f : sa, nb ? 0.f : sb_);
-                                    mk[(2 * q) * NC] |= (unsigned)na << jj;
-                                    mk[(2 * q + 1) * NC] |= (unsigned)nb << jj;
+                                    up2(SJ, ja, jb);
+                                    SJ = pk2(na ? 0.f : ja, nb ? 0.f : jb);
+                                    M0[q] |= (unsigned)na << jj;
+                                    M1[q] |= (unsigned)nb << jj;
+                                }
+                                TX[q] = fma2(SI, DX, TX[q]);
+                                TY[q] = fma2(SI, DY, TY[q]);
+                                TZ[q] = fma2(SI, DZ, TZ[q]);
+                                if constexpr (BOTH) {
+                                    jsum(JX, SJ, DX);
+                                    jsum(JY, SJ, DY);
+                                    jsum(JZ, SJ, DZ);
                                 }
                             }
-                            TX[q] = fma2(SI, DX, TX[q]);
-                            TY[q] = fma2(SI, DY, TY[q]);
-                            TZ[q] = fma2(SI, DZ, TZ[q]);
-                            if (both) {
-                                jsum(JX, SJ, DX);
-                                jsum(JY, SJ, DY);
-                                jsum(JZ, SJ, DZ);
+                            if constexpr (BOTH) {
+                                JX = __shfl_sync(0xffffffffu, JX, src);
+                                JY = __shfl_sync(0xffffffffu, JY, src);
+                                JZ = __shfl_sync(0xffffffffu, JZ, src);
                             }
                         }
-                        if (both) {
-                            JX = __shfl_sync(0xffffffffu, JX, src);
-                            JY = __shfl_sync(0xffffffffu, JY, src);
-                            JZ = __shfl_sync(0xffffffffu, JZ, src);
+                        if constexpr (BOTH) {
+                            part[0 * MG + sb * 32 + lane] = JX;
+                            part[1 * MG + sb * 32 + lane] = JY;
+                            part[2 * MG + sb * 32 + lane] = JZ;
                         }
-                    }
-                    if (both) {
-                        part[0 * MG + sb * 32 + lane] = JX;
-                        part[1 * MG + sb * 32 + lane] = JY;
-                        part[2 * MG + sb * 32 + lane] = JZ;
-                    }
-                    // the screened pairs of this half of the group, exactly in
-                    // FP64: all lanes evaluate one pair each per round; the
-                    // j-side terms are added in lane order (a fixed order)
-                    __syncwarp();
-                    for (;;) {
-                        int kk = -1, jj = 0;
-                        for (int k = 0; k < BPT && kk < 0; k++) {
-                            const unsigned m = mk[k * NC];
-                            if (m) {
-                                kk = k;
-                                jj = __ffs((int)m) - 1;
-                                mk[k * NC] = m & (m - 1u);
-                            }
-                        }
-                        if (!__any_sync(0xffffffffu, kk >= 0)) break;
-                        double3 fi = make_double3(0.0, 0.0, 0.0), fj = fi;
-                        if (kk >= 0) {
-                            const int i = (gw + (kk >> 1) * CW) * MG + 32 * (kk & 1) + lane, j = g * MG + sb * 32 + jj;
-                            screened_pair_mutual(a, i, j, 0, a.N, 0, both, &fi, &fj);
-                            const double f3[3] = {fi.x, fi.y, fi.z};
 #pragma unroll
-                            for (int c = 0; c < 3; c++) {
-                                DF &t = acc[(c * BPT + kk) * NC];
-                                const DF d = df_of_double(f3[c]);
-                                t = df_add(t, d.hi, d.lo);
-                            }
+                        for (int q = 0; q < NP; q++) {
+                            mk[(2 * q) * NC] = M0[q];
+                            mk[(2 * q + 1) * NC] = M1[q];
                         }
-                        if (both) {
-                            const int js = kk >= 0 ? sb * 32 + jj : -1;
-                            const float fx = (float)fj.x, fy = (float)fj.y, fz = (float)fj.z;
-                            for (int s = 0; s < 32; s++) {
-                                const int j2 = __shfl_sync(0xffffffffu, js, s);
-                                const float gx = __shfl_sync(0xffffffffu, fx, s);
-                                const float gy = __shfl_sync(0xffffffffu, fy, s);
-                                const float gz = __shfl_sync(0xffffffffu, fz, s);
-                                if (lane == 0 && j2 >= 0) {
-                                    part[0 * MG + j2] += gx;
-                                    part[1 * MG + j2] += gy;
-                                    part[2 * MG + j2] += gz;
+                        // the screened pairs of this half of the group, exactly in
+                        // FP64: all lanes evaluate one pair each per round; the
+                        // j-side terms are added in lane order (a fixed order)
+                        __syncwarp();
+                        for (;;) {
+                            int kk = -1, jj = 0;
+                            for (int k = 0; k < BPT && kk < 0; k++) {
+                                const unsigned m = mk[k * NC];
+                                if (m) {
+                                    kk = k;
+                                    jj = __ffs((int)m) - 1;
+                                    mk[k * NC] = m & (m - 1u);
                                 }
                             }
-                            __syncwarp();
+                            if (!__any_sync(0xffffffffu, kk >= 0)) break;
+                            double3 fi = make_double3(0.0, 0.0, 0.0), fj = fi;
+                            if (kk >= 0) {
+                                const int i = (gw + (kk >> 1) * CW) * MG + 32 * (kk & 1) + lane, j = g * MG + sb * 32 + jj;
+                                screened_pair_mutual(a, i, j, 0, a.N, 0, BOTH, &fi, &fj);
+                                const double f3[3] = {fi.x, fi.y, fi.z};
+#pragma unroll
+                                for (int c = 0; c < 3; c++) {
+                                    DF &t = acc[(c * BPT + kk) * NC];
+                                    const DF d = df_of_double(f3[c]);
+                                    t = df_add(t, d.hi, d.lo);
+                                }
+                            }
+                            if constexpr (BOTH) {
+                                const int js = kk >= 0 ? sb * 32 + jj : -1;
+                                const float fx = (float)fj.x, fy = (float)fj.y, fz = (float)fj.z;
+                                for (int s = 0; s < 32; s++) {
+                                    const int j2 = __shfl_sync(0xffffffffu, js, s);
+                                    const float gx = __shfl_sync(0xffffffffu, fx, s);
+                                    const float gy = __shfl_sync(0xffffffffu, fy, s);
+                                    const float gz = __shfl_sync(0xffffffffu, fz, s);
+                                    if (lane == 0 && j2 >= 0) {
+                                        part[0 * MG + j2] += gx;
+                                        part[1 * MG + j2] += gy;
+                                        part[2 * MG + j2] += gz;
+                                    }
+                                }
+                                __syncwarp();
+                            }
                         }
                     }
+                };
+                if constexpr (NP <= 2) {
+                    if (qnear == 1u) {
+                        if (both) near_loop(std::true_type{}, std::integral_constant<unsigned, 1u>{});
+                        else near_loop(std::false_type{}, std::integral_constant<unsigned, 1u>{});
+                    } else if (qnear == 2u) {
+                        if (both) near_loop(std::true_type{}, std::integral_constant<unsigned, 2u>{});
+                        else near_loop(std::false_type{}, std::integral_constant<unsigned, 2u>{});
+                    } else {
+                        if (both) near_loop(std::true_type{}, std::integral_constant<unsigned, 3u>{});
+                        else near_loop(std::false_type{}, std::integral_constant<unsigned, 3u>{});
+                    }
+                } else {  // every i-group takes the NEAR treatment (residuals and thresholds of all)
+                    constexpr unsigned ALL = (1u << NP) - 1u;
+                    if (both) near_loop(std::true_type{}, std::integral_constant<unsigned, ALL>{});
+                    else near_loop(std::false_type{}, std::integral_constant<unsigned, ALL>{});
                 }
             }
         } else if (!diag) {
@@ -592,7 +645,10 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
             for (int c = 0; c < 3; c++) part[c * MG + lane] = part[c * MG + 32 + lane] = 0.f;
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&pdone[slot]);  // this warp's j-sums are in; the slot may be reduced
+        if (lane == 0) {
+            mbar_arrive(&pdone[slot]);  // this warp's j-sums are in; the slot may be reduced
+            atomicMax(&s_lead, n + 1);
+        }
         if (in) {
             if (++nf == M_FOLD || (h.flags & 2)) {  // fold the FP32 i-sums into the double-float sums
 #pragma unroll
@@ -725,6 +781,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
     const size_t np = (size_t)a.npad;
     double *rows = a.partial;
 
+    __shared__ unsigned s_lead;  // slots the leading consumer warp has finished
     if (tid == 0) {
         for (int q = 0; q < STAGES; q++) {
             mbar_init(&full[q], 1);
@@ -732,6 +789,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
             mbar_init(&empty[q], 1);
         }
         fence_barrier_init();
+        s_lead = 0u;
     }
     __syncthreads();
 
@@ -739,6 +797,12 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
         if (lane != 0) return;
         unsigned n = 0;
         for (;;) {
+            // claim the next item only when the leading consumer warp is
+            // within M_CLAIM - 1 filled slots of the end of this CTA's work
+            // (inside an item the ring still runs up to STAGES slots ahead of
+            // the slowest warp): a CTA then holds no queued slots that an
+            // idle CTA could have taken, which evens out the CTAs' end times
+            if (n >= (unsigned)M_CLAIM && !wait_lead(&s_lead, n - M_CLAIM + 1, a.status, wlim)) return;
             const int q = atomicAdd(a.work, 1);
             const bool done = q >= P.items;
             const int4 it = done ? make_int4(0, 0, 0, 0) : P.item[q];
@@ -975,7 +1039,10 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
             for (int c = 0; c < 3; c++) part[c * MG + lane] = part[c * MG + 32 + lane] = 0.0;
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&pdone[slot]);
+        if (lane == 0) {
+            mbar_arrive(&pdone[slot]);
+            atomicMax(&s_lead, n + 1);
+        }
         if (in && (h.flags & 2)) {  // last slot of the item: its i-row
             double *out = rows + (size_t)row * 3 * np;
 #pragma unroll
