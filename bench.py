@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variant", type=int, default=-1, help="force an FP32 pass variant (-1: autotune)")
+    ap.add_argument("--fp64-variant", type=int, default=-1, help="force an FP64 pass variant (-1: autotune)")
     ap.add_argument("--no-sweep", action="store_true", help="skip timing every FP32 variant")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-disc batched workload")
     ap.add_argument("--batched-steps", type=int, default=5)
@@ -150,14 +151,21 @@ def weak_value(ws, pairs_per_step, steps, ms_max):
     return ws * pairs_per_step * steps / (ms_max * 1e-3)
 
 
-def kernel_traffic(kernel_file="kick.cu"):
-    """dram bytes per launch of the pass kernel from the committed ncu summary,
-    or None when the kernel source has changed since it was captured."""
+KERNEL_SOURCE = {"pass_fp32_kernel": "kick.cu", "pass_mutual_kernel": "mutual.cu", "pass_fp64_kernel": "kick.cu",
+                 "pass_mutual64_kernel": "mutual.cu"}
+
+
+def kernel_traffic(kernel):
+    """dram bytes per launch of a pass kernel from the committed ncu summary
+    (profiles/traffic.json, one record per kernel), or None when there is no
+    record or the kernel's source file has changed since it was captured."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2309_08217_gb300", "csrc", kernel_file)
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCE:
         return None
-    rec = json.load(open(path))
+    rec = json.load(open(path)).get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2309_08217_gb300", "csrc", KERNEL_SOURCE[kernel])
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     if rec.get("source_sha256") != sha:
         return None
@@ -208,6 +216,8 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": pairs_step / value * 1e3,
+        "ms_per_step_how": "derived, not timed: pairs_per_step / value (the oracle is timed on row samples "
+                           "of the pair sum, not on whole steps)",
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": d.N, "pairs_per_step": pairs_step,
                    "sample": "each step: the oracle's FP64 pair sum over a random sample of body rows "
@@ -394,6 +404,7 @@ def run_genga(args):
         g.genga_profile_enable(ctx, False)
         variants[str(v)] = pms / max(1, pn)
     g.genga_set_kernel_variant(ctx, args.variant)
+    g.genga_set_fp64_variant(ctx, args.fp64_variant)
 
     # ---- FP32 step (the headline) and FP64 step on the same GPU
     ms32, pass32, nl32, clk, s32 = timed_steps(p32, args.steps, args.warmup, clocks=True)
@@ -401,6 +412,8 @@ def run_genga(args):
     chosen, _ = g.genga_get_kernel_variant(ctx, N)
     tuner_ms = g.genga_tuning_times(ctx, N)
     ms64, pass64, nl64, _, _ = timed_steps(p64, max(1, args.fp64_steps), 3)
+    chosen64, _ = g.genga_get_fp64_variant(ctx, N)
+    tuner64_ms = g.genga_fp64_tuning_times(ctx, N)
 
     # ---- the 1,000-step run of the workload: mean step and pass times over the
     # whole run (the state evolves: the spatial order and the NEAR share drift)
@@ -507,14 +520,14 @@ def run_genga(args):
         best, ms_c = g.genga_tune_levels(ctx, st, p32_on, cand, 8)
         if g.genga_get_status(ctx) != g.GENGA_OK:
             raise RuntimeError("device status after tuning the levels")
-        chosen = tuple(int(v) for v in args.levels.split(":")) if args.levels else best
+        chosen_lv = tuple(int(v) for v in args.levels.split(":")) if args.levels else best
         p32_lv = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=g.GENGA_FP32, bs_tol=args.bs_tol,
-                               n_levels=chosen[0], n_sub=chosen[1])
+                               n_levels=chosen_lv[0], n_sub=chosen_lv[1])
         ms_lv, nsteps_lv = graph_blocks(p32_lv, max(1, args.steps // 4))
         p32_l0 = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=g.GENGA_FP32, bs_tol=args.bs_tol)
         ms_l0, _ = graph_blocks(p32_l0, max(1, args.steps // 4))
         levels = {"candidates": [list(c) for c in cand], "trial_ms_per_step": [round(v, 4) for v in ms_c],
-                  "tuned": list(best), "timed": list(chosen),
+                  "tuned": list(best), "timed": list(chosen_lv),
                   "value_timed": weak_value(ws, pairs_step, nsteps_lv, ms_lv), "unit": UNIT,
                   "ms_per_step_timed": ms_lv / nsteps_lv, "ms_per_step_no_levels": ms_l0 / nsteps_lv,
                   "how": "genga_tune_levels: 8 trial steps of each (n_levels, n_sub) from a copy of the state "
@@ -604,9 +617,11 @@ def run_genga(args):
     pass64_avg = pass64 / max(1, nl64)
     achieved = FLOPS_PER_PAIR * N * (N - 1) / (pass_avg * 1e-3) / 1e12
     achieved64 = FLOPS_PER_PAIR * N * (N - 1) / (pass64_avg * 1e-3) / 1e12
-    traffic = kernel_traffic()
+    info = g.genga_kernel_variant_info(chosen) if chosen >= 0 else {"kind": 0}
+    kname = "pass_mutual_kernel" if info["kind"] == 1 else "pass_fp32_kernel"
+    traffic = kernel_traffic(kname)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s", "frac": achieved / peak32,
-            "traffic": traffic, "kernel": "pass_fp32_kernel",
+            "traffic": traffic, "kernel": kname, "variant_shape": info,
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x {max_mhz:.0f} MHz",
             "flops_per_pair": FLOPS_PER_PAIR, "pass_ms_avg": pass_avg,
             "measured_ffma_tflops": f32_meas, "frac_of_measured_ffma": achieved / f32_meas,
@@ -647,7 +662,11 @@ def run_genga(args):
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64_max / max(1, args.fp64_steps),
                  "steps": max(1, args.fp64_steps), "pass_ms_avg": pass64_avg, "achieved_tflops": achieved64,
                  "measured_dfma_tflops": f64_meas, "frac_of_measured_dfma": achieved64 / f64_meas,
-                 "fp32_over_fp64": value / value64},
+                 "fp32_over_fp64": value / value64, "fp64_variant": chosen64,
+                 "kernel": "pass_mutual64_kernel" if chosen64 > 0 else "pass_fp64_kernel",
+                 "variant_shape": g.genga_fp64_variant_info(chosen64) if chosen64 >= 0 else None,
+                 "autotuner_pass_ms": tuner64_ms,
+                 "traffic": kernel_traffic("pass_mutual64_kernel" if chosen64 > 0 else "pass_fp64_kernel")},
         "roofline": roof,
         "graph_blocks": graph,
         "long_run": long_run,

@@ -1105,7 +1105,7 @@ struct MVariant {
 };
 #define GENGA_MV(NP, CW, ST, UNR) \
     {NP, CW, pass_mutual_kernel<NP, CW, ST, UNR>, MLayout<NP, CW, ST>::bytes}
-const MVariant kMVariants[] = {GENGA_MV(4, 10, 4, 2), GENGA_MV(4, 8, 6, 2), GENGA_MV(2, 12, 6, 2)};
+const MVariant kMVariants[] = {GENGA_MV(2, 12, 6, 8), GENGA_MV(2, 12, 6, 4), GENGA_MV(2, 12, 8, 8), GENGA_MV(4, 8, 6, 4)};
 #undef GENGA_MV
 constexpr int kNumMVariants = sizeof(kMVariants) / sizeof(kMVariants[0]);
 
