@@ -56,8 +56,25 @@ typedef enum {
                                   workspace (those bodies then got the Kepler drift) */
 } genga_status;
 
-/* Precision of the long-range kick (Sect. 1; "Do Kick in single precision", Sect. 4). */
-enum { GENGA_FP64 = 0, GENGA_FP32 = 1 };
+/* Precision of the long-range kick (Sect. 1; "Do Kick in single precision", Sect. 4).
+ *   GENGA_FP64           every pair term in FP64.
+ *   GENGA_FP32_HILO      FP32 pair terms from the hi/lo split x = x_hi + x_lo of the FP64
+ *                        positions (x_hi = fl32(x)); where every pair of a 32-body warp
+ *                        tile and a 64-body group is farther apart than 0.025 max|x| the
+ *                        lo parts are dropped (offset error <= ~5e-6 relative).  The
+ *                        one-sided pass: each ordered pair from its i-body's side.
+ *   GENGA_FP32_BLOCKREL  FP32 pair terms from block-relative offsets: X = fl32(x - c), the
+ *                        FP64 difference rounded, c the centre of the j-body's 64-body
+ *                        group; closer than a tenth of the group's half-diagonal (or the
+ *                        r_crit bound) the rounding residuals x - c - X are added back.
+ *                        The mutual pass: each unordered pair once, its terms added to
+ *                        both bodies.  Not with test-particle mode 2 (n_big >= 0) nor in
+ *                        batched mode: GENGA_ERR_INVALID_ARG.
+ *   GENGA_FP32           either FP32 form, whichever the autotuner finds faster for the
+ *                        size bucket (genga_measure.h).
+ * In every FP32 mode: r^2, rsqrt (SFU) and the pair terms in FP32, per-body sums in
+ * double-float (about 48 bits), close-encounter pairs exactly in FP64 with K. */
+enum { GENGA_FP64 = 0, GENGA_FP32_HILO = 1, GENGA_FP32_BLOCKREL = 2, GENGA_FP32 = 3 };
 
 /* Pair critical radius r_crit,ij (Eq. 1 gives the per-body radius):
  *   GENGA_RCRIT_EQ1         max(r_crit,i, r_crit,j), r_crit,i = max(n1 R_H,i, n2 dt v_i)
@@ -76,7 +93,7 @@ typedef struct {
     double n1, n2;           /* Eq. 1 constants; the paper's typical values are 3 and 0.4 */
     int32_t rcrit_mode;      /* GENGA_RCRIT_* */
     int32_t changeover;      /* GENGA_K_* */
-    int32_t precision;       /* GENGA_FP64 or GENGA_FP32 */
+    int32_t precision;       /* GENGA_FP64, GENGA_FP32_HILO, GENGA_FP32_BLOCKREL or GENGA_FP32 */
     int32_t kepler_max_iter; /* iteration cap of the f/g solver, >= 1 (50 is ample) */
     int32_t n_big;           /* test-particle mode 2 (the giant-planet runs of Sect. 3): with
                                 n_big >= 0, bodies n_big..N-1 (of each system in batched mode)
@@ -221,7 +238,8 @@ genga_status genga_step(genga_ctx *ctx, genga_system *sys, const genga_params *p
  *   offsets  HOST int32 [D+1], offsets[0] = 0, non-decreasing, offsets[D] = all->N
  *   D        1 .. GENGA_MAX_BATCH (256)
  * The context's max_N must cover the padded total sum_d roundup(N_d, 1024).
- * params->precision must be GENGA_FP32 (the batched pass is the FP32 kick).
+ * params->precision must be GENGA_FP32 or GENGA_FP32_HILO (the batched pass is the
+ * one-sided FP32 kick).
  * genga_kick_batched: the kick of every system (acc layout acc[c*all->N + i],
  * or NULL), the encounter list of every system with indices into `all`.
  * genga_step_batched: nsteps level-0 steps of every system.

@@ -30,7 +30,7 @@ LIB_PATH = os.path.join(_HERE, "libgenga.so")
 
 GENGA_OK, GENGA_ERR_INVALID_ARG, GENGA_ERR_CUDA, GENGA_ERR_CAPACITY = 0, 1, 2, 3
 GENGA_ERR_KEPLER, GENGA_ERR_NONFINITE, GENGA_ERR_TIMEOUT, GENGA_ERR_BS = 4, 5, 6, 7
-GENGA_FP64, GENGA_FP32 = 0, 1
+GENGA_FP64, GENGA_FP32_HILO, GENGA_FP32_BLOCKREL, GENGA_FP32 = 0, 1, 2, 3
 GENGA_RCRIT_EQ1, GENGA_RCRIT_MUTUAL_HILL = 0, 1
 GENGA_K_CHAMBERS, GENGA_K_QUINTIC = 0, 1
 

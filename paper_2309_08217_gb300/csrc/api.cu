@@ -37,6 +37,14 @@ inline genga_status cuda_status(cudaError_t e) {
     return GENGA_ERR_CUDA;
 }
 
+inline bool is_fp32(int precision) {
+    return precision == GENGA_FP32 || precision == GENGA_FP32_HILO || precision == GENGA_FP32_BLOCKREL;
+}
+// variant family of an FP32 precision mode: 0 all variants, 1 one-sided, 2 mutual
+inline int family_of(int precision) {
+    return precision == GENGA_FP32_HILO ? 1 : precision == GENGA_FP32_BLOCKREL ? 2 : 0;
+}
+
 genga_status check_params(const genga_params *p) {
     if (!p) return GENGA_ERR_INVALID_ARG;
     if (!is_fin(p->G) || p->G < 0.0) return GENGA_ERR_INVALID_ARG;
@@ -45,7 +53,8 @@ genga_status check_params(const genga_params *p) {
         return GENGA_ERR_INVALID_ARG;
     if (p->rcrit_mode != GENGA_RCRIT_EQ1 && p->rcrit_mode != GENGA_RCRIT_MUTUAL_HILL) return GENGA_ERR_INVALID_ARG;
     if (p->changeover != GENGA_K_CHAMBERS && p->changeover != GENGA_K_QUINTIC) return GENGA_ERR_INVALID_ARG;
-    if (p->precision != GENGA_FP64 && p->precision != GENGA_FP32) return GENGA_ERR_INVALID_ARG;
+    if (p->precision != GENGA_FP64 && !is_fp32(p->precision)) return GENGA_ERR_INVALID_ARG;
+    if (p->precision == GENGA_FP32_BLOCKREL && p->n_big >= 0) return GENGA_ERR_INVALID_ARG;  // no mode-2 mutual pass
     if (p->kepler_max_iter < 1) return GENGA_ERR_INVALID_ARG;
     if (p->n_big < -1) return GENGA_ERR_INVALID_ARG;
     // bs_tol: 0 (off) or >= 1e-14 -- below that the error estimate of a member's
@@ -237,31 +246,39 @@ bool can_tune(cudaStream_t s) {
 // times on the packed state (the encounter list is cleared after each run)
 // and keeps the variant with the fastest of its last three runs; it
 // synchronises the stream, so it is skipped while the stream is captured.
-// Test-particle mode 2 has its own table over the one-sided variants (the
-// mutual pass does not implement it); a forced mutual variant falls back to
-// variant 0 there.
-int fp32_variant(genga_ctx *c, const PassArgs &base, int N, cudaStream_t s) {
+// The precision mode sets the family of variants: GENGA_FP32 all of them,
+// GENGA_FP32_HILO the one-sided pass (hi/lo split), GENGA_FP32_BLOCKREL the
+// mutual pass (group-centred offsets); each family has its own table, and a
+// variant already timed for the bucket is not timed again.  Test-particle
+// mode 2 has its own table over the one-sided variants (the mutual pass does
+// not implement it).  A forced variant outside the family is not used.
+int fp32_variant(genga_ctx *c, const PassArgs &base, int N, int precision, cudaStream_t s) {
     const bool tp2 = base.n_big >= 0;
-    if (c->forced_variant >= 0) return (tp2 && is_mutual(c->forced_variant)) ? 0 : c->forced_variant;
+    const int fam = tp2 ? 1 : family_of(precision);
+    auto in_family = [&](int v) { return fam == 0 || (fam == 1) == !is_mutual(v); };
+    const int first = fam == 2 ? num_fp32_variants() : 0;
+    if (c->forced_variant >= 0 && in_family(c->forced_variant)) return c->forced_variant;
     const int b = size_bucket(N);
-    int8_t *table = tp2 ? c->f32_variant_tp : c->f32_variant;
+    int8_t *table = tp2 ? c->f32_variant_tp : c->f32_variant[fam];
     if (table[b] >= 0) return table[b];
-    if (!can_tune(s)) return 0;
+    if (!can_tune(s)) return first;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return 0;
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
         return 0;
     }
-    int best = 0;
+    int best = first;
     float best_ms = 3.0e38f;
-    const int nv = tp2 ? num_fp32_variants() : num_all_variants();
-    for (int v = 0; v < nv; v++) {
-        const float ms = time_variant(c, N, 4, is_mutual(v) ? 1 : 0, 0, s, e0, e1,
-                                      [&](MutualPlan *mp, int *split, int *one_row, cudaError_t *e) {
-                                          return launch_fp32_variant(c, base, v, s, mp, split, one_row, e);
-                                      });
-        if (!tp2 && v < GENGA_MAX_VARIANTS) c->tune_ms[b][v] = ms < 3.0e38f ? ms : 0.f;
+    for (int v = 0; v < num_all_variants(); v++) {
+        if (!in_family(v)) continue;
+        const bool known = !tp2 && v < GENGA_MAX_VARIANTS && c->tune_ms[b][v] > 0.f;
+        const float ms = known ? c->tune_ms[b][v]
+                               : time_variant(c, N, 4, is_mutual(v) ? 1 : 0, 0, s, e0, e1,
+                                              [&](MutualPlan *mp, int *split, int *one_row, cudaError_t *e) {
+                                                  return launch_fp32_variant(c, base, v, s, mp, split, one_row, e);
+                                              });
+        if (!tp2 && !known && v < GENGA_MAX_VARIANTS) c->tune_ms[b][v] = ms < 3.0e38f ? ms : 0.f;
         if (ms < best_ms) {
             best_ms = ms;
             best = v;
@@ -336,12 +353,18 @@ cudaError_t run_pass(genga_ctx *c, const genga_system &sys, const genga_params &
     PassArgs a = base_args(c, sys, p);
     *out = PassOut{};
     profile_before_pass(c, s);
-    if (precision == GENGA_FP32) {
-        int variant = fp32_variant(c, a, sys.N, s);
+    if (is_fp32(precision)) {
+        int variant = fp32_variant(c, a, sys.N, precision, s);
         if (is_mutual(variant) && p.n_big >= 0) variant = 0;
         out->mutual = is_mutual(variant) ? 1 : 0;
         if (!launch_fp32_variant(c, a, variant, s, &out->mp, &out->split, &out->one_row, &e)) {
-            out->mutual = 0;  // no mutual plan now (a capture): the one-sided default
+            // no mutual plan now: the one-sided default, except where the
+            // caller asked for the group-centred form
+            if (precision == GENGA_FP32_BLOCKREL) {
+                profile_after_pass(c, s);
+                return cudaErrorMemoryAllocation;
+            }
+            out->mutual = 0;
             launch_fp32_variant(c, a, 0, s, &out->mp, &out->split, &out->one_row, &e);
         }
     } else {
@@ -570,8 +593,10 @@ bool fp64_tuned(const genga_ctx *c, int N, int n_big) {
     return n_big >= 0 || c->forced_f64 >= 0 || c->f64_variant[size_bucket(N)] >= 0;
 }
 
-bool fp32_tuned(const genga_ctx *c, int N, int n_big) {
-    return c->forced_variant >= 0 || (n_big >= 0 ? c->f32_variant_tp : c->f32_variant)[size_bucket(N)] >= 0;
+bool fp32_tuned(const genga_ctx *c, int N, int n_big, int precision) {
+    const int fam = n_big >= 0 ? 1 : family_of(precision);
+    const bool forced_ok = c->forced_variant >= 0 && (fam == 0 || (fam == 1) == !is_mutual(c->forced_variant));
+    return forced_ok || (n_big >= 0 ? c->f32_variant_tp : c->f32_variant[fam])[size_bucket(N)] >= 0;
 }
 
 template <class T>
@@ -676,7 +701,7 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     memset(c, 0, sizeof(*c));
     c->device = device;
     c->max_N = max_N;
-    for (int b = 0; b < 32; b++) c->f32_variant[b] = c->f32_variant_tp[b] = -1;
+    for (int b = 0; b < 32; b++) c->f32_variant[0][b] = c->f32_variant[1][b] = c->f32_variant[2][b] = c->f32_variant_tp[b] = -1;
     c->forced_variant = -1;
     for (int b = 0; b < 32; b++) c->f64_variant[b] = -1;
     c->forced_f64 = -1;
@@ -815,7 +840,7 @@ genga_status genga_encounters(genga_ctx *c, const genga_system *sys, const genga
         c->enc_sorted = true;
     } else {
         PassOut po;
-        if (const cudaError_t e_ = run_pass(c, *sys, *p, GENGA_FP32, true, &po, s); e_ != cudaSuccess) return cuda_status(e_);
+        if (const cudaError_t e_ = run_pass(c, *sys, *p, GENGA_FP32_HILO, true, &po, s); e_ != cudaSuccess) return cuda_status(e_);
     }
     return genga_last_encounters(c, pairs, capacity, count, stream);
 }
@@ -852,18 +877,21 @@ genga_status genga_step(genga_ctx *c, genga_system *sys, const genga_params *p, 
     int k = 0;
     auto aligned = [&]() {
         return c->steps_since_order == 0 && c->ordered_N == s2.N && c->ordered_nbig == p->n_big &&
-               (p->precision == GENGA_FP32 ? fp32_tuned(c, s2.N, p->n_big) : fp64_tuned(c, s2.N, p->n_big));
+               (is_fp32(p->precision) ? fp32_tuned(c, s2.N, p->n_big, p->precision) : fp64_tuned(c, s2.N, p->n_big));
     };
     for (; k < nsteps && !(aligned() && nsteps - k >= GENGA_REORDER_STEPS); k++)
         if (const cudaError_t e_ = one_step(s); e_ != cudaSuccess) return cuda_status(e_);
     if (k < nsteps && graphs_usable(c)) {
         int variant = -1;
-        if (p->precision == GENGA_FP32) {
+        if (is_fp32(p->precision)) {
             PassArgs pa = base_args(c, s2, *p);
-            variant = fp32_variant(c, pa, s2.N, s);  // tuned already (aligned() holds)
+            variant = fp32_variant(c, pa, s2.N, p->precision, s);  // tuned already (aligned() holds)
             if (is_mutual(variant) && p->n_big < 0) {
                 MutualPlan mp;  // the plan is built outside the capture
-                if (!mutual_plan(c, s2.N, variant - num_fp32_variants(), s, &mp)) variant = 0;
+                if (!mutual_plan(c, s2.N, variant - num_fp32_variants(), s, &mp)) {
+                    if (p->precision == GENGA_FP32_BLOCKREL) return GENGA_ERR_CUDA;
+                    variant = 0;
+                }
             }
         } else {
             PassArgs pa = base_args(c, s2, *p);
@@ -900,7 +928,9 @@ genga_status genga_kick_batched(genga_ctx *c, const genga_system *all, const int
     genga_status st;
     if ((st = check_system(c, all)) != GENGA_OK) return st;
     if ((st = check_params(p)) != GENGA_OK) return st;
-    if (p->precision != GENGA_FP32 || !is_fin(tau) || !check_offsets(c, all, offsets, D)) return GENGA_ERR_INVALID_ARG;
+    if ((p->precision != GENGA_FP32 && p->precision != GENGA_FP32_HILO) || !is_fin(tau) ||
+        !check_offsets(c, all, offsets, D))
+        return GENGA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (all->N == 0) return cuda_status(cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s));
@@ -914,7 +944,9 @@ genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *
     genga_status st;
     if ((st = check_system(c, all)) != GENGA_OK) return st;
     if ((st = check_params(p)) != GENGA_OK) return st;
-    if (p->precision != GENGA_FP32 || nsteps < 0 || !check_offsets(c, all, offsets, D)) return GENGA_ERR_INVALID_ARG;
+    if ((p->precision != GENGA_FP32 && p->precision != GENGA_FP32_HILO) || nsteps < 0 ||
+        !check_offsets(c, all, offsets, D))
+        return GENGA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (all->N == 0 || nsteps == 0) return GENGA_OK;

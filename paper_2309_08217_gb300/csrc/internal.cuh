@@ -133,7 +133,7 @@ struct genga_ctx {
     int32_t energy_blocks;
     genga::Profile *prof;      // measurement hooks (genga_measure.h), NULL when unused
     int32_t *work;             // [1] work-item counter of the persistent pass
-    int8_t f32_variant[32];    // autotuned FP32 pass variant per log2(npad) bucket, -1 = not tuned
+    int8_t f32_variant[3][32]; // autotuned FP32 pass variant per family (all, one-sided, mutual) and log2(npad) bucket, -1 = not tuned
     int8_t f32_variant_tp[32]; // the same for test-particle mode 2 (one-sided variants only)
     int32_t test_wait_log2;    // test hook: bounded waits of the pipelined passes give up after 2^this ns (0: 2 s)
     int32_t test_hold;         // test hook: the pipelined passes' producers withhold their first stage

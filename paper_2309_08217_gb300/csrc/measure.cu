@@ -277,7 +277,7 @@ genga_status genga_get_kernel_variant(genga_ctx *c, int32_t N, int32_t *variant,
     int b = 0;
     for (int v = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD; v > 1; v >>= 1) b++;
     b = b < 32 ? b : 31;
-    *variant = (c->forced_variant >= 0) ? c->forced_variant : c->f32_variant[b];
+    *variant = (c->forced_variant >= 0) ? c->forced_variant : c->f32_variant[0][b];
     *num_variants = num_fp32_variants() + num_mutual_variants();
     return GENGA_OK;
 }
