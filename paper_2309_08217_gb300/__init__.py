@@ -104,6 +104,7 @@ def load():
             "genga_step_batched": ([V, S, C.POINTER(C.c_int32), I, P, I, V], I),
             "genga_get_kernel_variant": ([V, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], I),
             "genga_set_fp64_variant": ([V, I], I),
+            "genga_batched_tuning": ([V, C.POINTER(C.c_int32), I, C.POINTER(C.c_int32), C.POINTER(C.c_float), I], I),
             "genga_get_fp64_variant": ([V, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], I),
             "genga_fp64_variant_info": ([I] + [C.POINTER(I)] * 3, I),
             "genga_fp64_tuning_times": ([V, I, C.POINTER(C.c_float), I], I),
@@ -374,6 +375,15 @@ def genga_get_kernel_variant(ctx, N):
     v, n = C.c_int32(), C.c_int32()
     _check(load().genga_get_kernel_variant(_ctx(ctx), int(N), C.byref(v), C.byref(n)), "genga_get_kernel_variant")
     return v.value, n.value
+
+
+def genga_batched_tuning(ctx, offsets):
+    """(FP32 variant tuned for this batch layout or -1, batched pass ms of each one-sided variant)."""
+    off, D = _offsets(offsets)
+    n = genga_get_kernel_variant(ctx, 1)[1]
+    v, arr = C.c_int32(), (C.c_float * n)()
+    _check(load().genga_batched_tuning(_ctx(ctx), off, D, C.byref(v), arr, n), "genga_batched_tuning")
+    return v.value, list(arr)
 
 
 def genga_set_fp64_variant(ctx, variant=-1):

@@ -489,6 +489,59 @@ bool plan_batch(const genga_ctx *c, const BatchBodies &bb, int variant, BatchIte
     return false;
 }
 
+// The FP32 variant of a batch: forced (one-sided variants only), already
+// tuned for this batch layout, or tuned now: every one-sided variant's
+// batched pass (its own work plan) run three times on the packed state, the
+// fastest of the last two kept.  The context remembers GENGA_BATCH_LAYOUTS
+// layouts (the oldest is replaced).  Tuning synchronises the stream, so it is
+// skipped during a capture (variant 0).
+int batch_variant(genga_ctx *c, const PassArgs &a, const BatchBodies &bb, unsigned long long key, cudaStream_t s,
+                  bool tune = true) {
+    if (c->forced_variant >= 0 && !is_mutual(c->forced_variant)) return c->forced_variant;
+    for (int q = 0; q < GENGA_BATCH_LAYOUTS; q++)
+        if (c->bt_var[q] >= 0 && c->bt_key[q] == key) return c->bt_var[q];
+    if (!tune || !can_tune(s)) return 0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return 0;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return 0;
+    }
+    const int slot = c->bt_next;
+    c->bt_next = (c->bt_next + 1) % GENGA_BATCH_LAYOUTS;
+    int best = 0;
+    float best_ms = 3.0e38f;
+    for (int v = 0; v < num_fp32_variants() && v < GENGA_MAX_VARIANTS; v++) {
+        c->bt_ms[slot][v] = 0.f;
+        BatchItems bi;
+        int grid = 1;
+        if (!plan_batch(c, bb, v, &bi, &grid)) continue;
+        PassArgs av = a;
+        av.partial = c->partial;
+        float ms = 3.0e38f;
+        for (int rep = 0; rep < 3; rep++) {
+            cudaEventRecord(e0, s);
+            const cudaError_t e = launch_pass_batched(av, bb, bi, v, grid, s);
+            cudaEventRecord(e1, s);
+            cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s);
+            if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
+            float t = 3.0e38f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0 && t < ms) ms = t;
+        }
+        c->bt_ms[slot][v] = ms < 3.0e38f ? ms : 0.f;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->bt_key[slot] = key;
+    c->bt_var[slot] = (int8_t)best;
+    return best;
+}
+
 // One batched kick: momenta (list reset), spatial order (when asked or when
 // the batch layout changed), prep, FP32 pass, list sort, combine.
 cudaError_t run_kick_batched(genga_ctx *c, const genga_system &all, const int32_t *offsets, int D,
@@ -511,7 +564,7 @@ cudaError_t run_kick_batched(genga_ctx *c, const genga_system &all, const int32_
     c->launches += 1;
     PassArgs a = base_args(c, all, p);
     a.npad = bb.npad_total;
-    const int variant = (c->forced_variant >= 0 && !is_mutual(c->forced_variant)) ? c->forced_variant : 0;
+    const int variant = batch_variant(c, a, bb, key, s);
     BatchItems bi;
     int grid = 1;
     if (!plan_batch(c, bb, variant, &bi, &grid)) return cudaErrorInvalidValue;
@@ -704,6 +757,8 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     for (int b = 0; b < 32; b++) c->f32_variant[0][b] = c->f32_variant[1][b] = c->f32_variant[2][b] = c->f32_variant_tp[b] = -1;
     c->forced_variant = -1;
     for (int b = 0; b < 32; b++) c->f64_variant[b] = -1;
+    for (int q = 0; q < GENGA_BATCH_LAYOUTS; q++) c->bt_var[q] = -1;
+    c->bt_next = 0;
     c->forced_f64 = -1;
     c->ordered_N = -1;
     c->step_graphs = 1;
@@ -976,7 +1031,7 @@ genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *
         if (e != cudaSuccess) return status_of(e);
     }
     if (k < nsteps && graphs_usable(c)) {
-        const int variant = (c->forced_variant >= 0 && !is_mutual(c->forced_variant)) ? c->forced_variant : 0;
+        const int variant = batch_variant(c, PassArgs{}, bb, layout, s, false);  // tuned by the steps above
         const unsigned long long key = step_key(a2, *p, variant, mix(layout, 0xba7c4ull));
         const bool ok = step_graph(c, key, [&](cudaStream_t q) {
             for (int b = 0; b < GENGA_REORDER_STEPS; b++) {
@@ -996,6 +1051,21 @@ genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *
     for (; k < nsteps; k++) {
         const cudaError_t e = one_step(s);
         if (e != cudaSuccess) return status_of(e);
+    }
+    return GENGA_OK;
+}
+
+genga_status genga_batched_tuning(genga_ctx *c, const int32_t *offsets, int32_t D, int32_t *variant, float *ms,
+                                  int32_t n) {
+    if (!c || !offsets || !variant || D < 1 || D > GENGA_MAX_DISCS || n < 0 || (n > 0 && !ms))
+        return GENGA_ERR_INVALID_ARG;
+    const unsigned long long key = offsets_hash(offsets, D);
+    *variant = -1;
+    for (int q = 0; q < n; q++) ms[q] = 0.f;
+    for (int k = 0; k < GENGA_BATCH_LAYOUTS; k++) {
+        if (c->bt_var[k] < 0 || c->bt_key[k] != key) continue;
+        *variant = c->bt_var[k];
+        for (int q = 0; q < n && q < GENGA_MAX_VARIANTS && q < num_fp32_variants(); q++) ms[q] = c->bt_ms[k][q];
     }
     return GENGA_OK;
 }

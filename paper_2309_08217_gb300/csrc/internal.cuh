@@ -54,6 +54,7 @@ struct Profile {                // CUDA event pairs around pass launches
 };
 }  // namespace genga
 
+#define GENGA_BATCH_LAYOUTS 8  // batch layouts whose tuned FP32 variant a context remembers
 #define GENGA_MAX_VARIANTS 16  // FP32 pass variants the context records tuning times for
 #define GENGA_MAX_TIERS 8      // chunk-length tiers of an FP32 pass plan
 #define GENGA_MUTUAL_MAX_ITEMS 16384  // work items of one mutual FP32 pass plan
@@ -142,6 +143,11 @@ struct genga_ctx {
     int8_t f64_variant[32];    // autotuned FP64 pass variant per bucket (0 one-sided, 1.. mutual), -1 = not tuned
     float tune64_ms[32][GENGA_MAX_VARIANTS];  // the autotuner's time of each FP64 variant per bucket
     int32_t forced_f64;        // >= 0: use this FP64 variant (genga_set_fp64_variant)
+    // batched mode: the tuned FP32 variant of the last GENGA_BATCH_LAYOUTS batch layouts
+    unsigned long long bt_key[GENGA_BATCH_LAYOUTS];  // layout hash (offsets)
+    int8_t bt_var[GENGA_BATCH_LAYOUTS];              // -1: empty
+    float bt_ms[GENGA_BATCH_LAYOUTS][GENGA_MAX_VARIANTS];  // batched pass time of each one-sided variant
+    int32_t bt_next;                                 // slot the next tuned layout replaces
     int32_t steps_since_order; // genga_step: drifts since the spatial order was built
     int32_t ordered_N;         // N of the system the spatial order was built for (-1: none, -2: a batch)
     unsigned long long ordered_key;  // layout hash of the batch the order was built for

@@ -123,3 +123,30 @@ def test_batched_argument_checks(genga, bctx):
     p64 = genga.make_params(G=d.G, precision=genga.GENGA_FP64)
     with pytest.raises(genga.GengaError):
         genga.genga_kick_batched(bctx, s, [0, 100], p64, 0.0, None)
+
+
+def test_batched_variant_is_tuned_per_layout(genga):
+    """The first batched kick of a layout times every one-sided variant's
+    batched pass and keeps the fastest; a second layout gets its own entry;
+    the tuned kick still meets the oracle."""
+    import torch
+    c = genga.Context(40_000)
+    for sizes, seed in (([9000, 1200, 5000, 300], 70), ([2500] * 6, 80)):
+        parts, offsets, arrays = _batch(sizes, seed)
+        assert genga.genga_batched_tuning(c, offsets)[0] == -1
+        NT = int(offsets[-1])
+        s = genga.DeviceSystem.from_arrays(arrays)
+        acc = torch.zeros(3 * NT, dtype=torch.float64, device="cuda")
+        genga.genga_kick_batched(c, s, offsets, _params(genga, parts[0]), 0.0, acc)
+        assert genga.genga_get_status(c) == genga.GENGA_OK
+        v, ms = genga.genga_batched_tuning(c, offsets)
+        one_sided = [u for u in range(len(ms)) if genga.genga_kernel_variant_info(u)["kind"] == 0]
+        assert v in one_sided and all(ms[u] > 0 for u in one_sided)
+        assert ms[v] == min(ms[u] for u in one_sided)
+        got = acc.view(3, NT).cpu().numpy()
+        for k, d in enumerate(parts):
+            arr = oracle.disc_arrays(d)
+            a, rc = oracle.rcrit(*arr, G=d.G, Mstar=d.Mstar, dt=d.dt, n1=3.0, n2=0.4)
+            ref = oracle.kick_acc(arr[0], arr[1], arr[2], arr[6], a, rc, d.G, d.Mstar, 3.0, 1, 0)
+            assert _rel(got[:, offsets[k]:offsets[k + 1]], ref).max() <= 2e-5
+    c.close()
