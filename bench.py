@@ -67,7 +67,8 @@ def parse():
                          "step (which is the level-0 path: kick, drift, kick); 0: skip that measurement")
     ap.add_argument("--conservation", default=None,
                     help="instead of the benchmark: energy and angular-momentum drift of FP32 vs FP64 runs, "
-                         "comma-separated workload:steps:sample_every (e.g. embryo6625:20000:1000,giants100k:100:10)")
+                         "comma-separated workload:steps:sample_every[:n_big] (e.g. "
+                         "embryo6625:100000:5000,giants100k:10000:500:4; n_big: test-particle mode 2)")
     return ap.parse_args()
 
 
@@ -267,6 +268,7 @@ def run_batched(g, torch, dev, stream, flush, args, rank, ws=1, dist=None):
     ms_bg = timed(lambda: g.genga_step_batched(ctxb, allsys, offsets, p, 4)) / 4
     if g.genga_get_status(ctxb) != g.GENGA_OK:
         raise RuntimeError("device status after the batched steps")
+    bvar, bms = g.genga_batched_tuning(ctxb, offsets)
     ctxb.close()
     ctxs = g.Context(int(sizes.max()), dev.index)
     systems = [g.DeviceSystem.from_disc(d, device=dev) for d in ds]
@@ -286,6 +288,8 @@ def run_batched(g, torch, dev, stream, flush, args, rank, ws=1, dist=None):
     return {"workload": BATCH_WORKLOAD, "discs": len(ds), "bodies": int(sizes.sum()), "pairs_per_step": pairs_step,
             "steps": K, "value": vb, "unit": UNIT, "ms_per_step": ms_b / K, "sequential_value": vs,
             "sequential_ms_per_step": ms_s / K, "speedup_vs_sequential": vb / vs,
+            "tuned_variant": bvar, "tuned_variant_shape": g.genga_kernel_variant_info(bvar) if bvar >= 0 else None,
+            "variant_pass_ms": [round(v, 4) for v in bms],
             "graph_blocks": {"value": weak_value(ws, pairs_step, K, ms_bg), "ms_per_step": ms_bg / K,
                              "how": "genga_step_batched(.., 4): one captured CUDA graph per 4-step block"}}
 
@@ -705,14 +709,28 @@ def run_conservation(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     for spec in args.conservation.split(","):
-        name, steps, every = spec.split(":")
-        steps, every = int(steps), int(every)
+        fields = spec.split(":")
+        name, steps, every = fields[0], int(fields[1]), int(fields[2])
+        n_big = int(fields[3]) if len(fields) > 3 else -1   # test-particle mode 2 with n_big big bodies
         d = discs.workload(name)
         ctx = g.Context(d.N, 0)
         out = {"mode": "conservation", "workload": name, "N": d.N, "dt": d.dt, "steps": steps,
-               "sample_every": every, "data": "synthetic", "bs_tol": args.bs_tol}
+               "sample_every": every, "data": "synthetic", "bs_tol": args.bs_tol, "n_big": n_big}
+        # per-body error of the FP32 kick against the FP64 kick at t = 0
+        accs = []
+        for prec in (g.GENGA_FP32, g.GENGA_FP64):
+            p = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=prec, n_big=n_big)
+            s = g.DeviceSystem.from_disc(d, device=dev)
+            acc = torch.zeros(3 * d.N, dtype=torch.float64, device=dev)
+            g.genga_kick(ctx, s, p, 0.0, acc)
+            accs.append(acc.view(3, d.N).cpu().numpy())
+        num = np.sqrt(((accs[0] - accs[1]) ** 2).sum(0))
+        den = np.sqrt((accs[1] ** 2).sum(0))
+        rel = num[den > 0] / den[den > 0]
+        out["fp32_kick_rel_err_vs_fp64"] = {"max": float(rel.max()), "median": float(np.median(rel)),
+                                             "p99": float(np.quantile(rel, 0.99))}
         for label, prec in (("fp32", g.GENGA_FP32), ("fp64", g.GENGA_FP64)):
-            p = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=prec, bs_tol=args.bs_tol)
+            p = g.make_params(G=d.G, Mstar=d.Mstar, dt=d.dt, precision=prec, bs_tol=args.bs_tol, n_big=n_big)
             s = g.DeviceSystem.from_disc(d, device=dev)
             E0, *L0 = g.genga_energy(ctx, s, p)
             L0 = np.array(L0)
