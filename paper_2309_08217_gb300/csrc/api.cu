@@ -780,6 +780,7 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     c->energy_blocks = np / 256;
     cudaError_t e = init_pass_kernels();
     if (e == cudaSuccess) e = init_mutual_kernels();
+    if (e == cudaSuccess) e = init_bs_kernel(c->sm_count);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = alloc(&c->pk_hi, np);
     if (e == cudaSuccess) e = alloc(&c->pk_lo, np);

@@ -28,6 +28,9 @@
 // integrates the subgroups of the last level over its sub-step, with the
 // pair share prod_{k=0}^{L} (1 - K_k) in place of 1 - K.  Everything here is FP64 (Sect. 1, last paragraph:
 // close-encounter forces are always double precision).
+#include <algorithm>
+#include <cooperative_groups.h>
+
 #include "changeover.cuh"
 #include "kepler.cuh"
 
@@ -43,6 +46,10 @@ constexpr int BS_GROW_COL = 2;         // a sub-step accepted by column <= 2 dou
 constexpr double BS_MIN_FRAC = 0x1p-30;  // smallest sub-step, as a fraction of the drift
 constexpr int BS_MAX_ATTEMPTS = 4096;  // sub-step attempts per group and drift
 constexpr int BS_WARPS = 4;            // groups in flight per CTA (one warp each)
+// Groups of more than BS_TEAM_MIN members are integrated by a whole cluster of
+// BS_TEAM_CTAS CTAs (32 warps on 32 SMSPs) instead of one warp.
+constexpr int BS_TEAM_CTAS = 8;
+constexpr int BS_TEAM_MIN = 24;
 // Wall-clock bound of one launch of the level-1 kernel (counted per warp from
 // the launch); past it every group still integrating drifts the rest of the
 // step on Kepler orbits (GENGA_ERR_BS).
@@ -390,6 +397,89 @@ __device__ __forceinline__ bool ge_nonneg(double a, double b) {  // a >= b for a
     return __double_as_longlong(a) >= __double_as_longlong(b);
 }
 
+// The threads that integrate one group in the workspace path, and the
+// operations the path needs from them: a barrier, and reductions whose
+// results do not depend on the order of combination (so both teams give the
+// same values).  WarpTeam: one warp.
+struct WarpTeam {
+    static constexpr int T = 32;
+    int t;  // lane
+    __device__ void sync() const { __syncwarp(); }
+    __device__ double min_nonneg(double v) const { return warp_min_nonneg(v); }
+    __device__ void max_of(double *v, int cnt) const {  // fmax over the team of v[0..cnt), in place
+        for (int k = 0; k < cnt; k++) v[k] = warp_max(v[k]);
+    }
+    __device__ int min_int(int v) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    }
+    __device__ bool late(uint64_t t0) const {  // the launch's time limit, lane 0's clock
+        int l = 0;
+        if (t == 0) l = (global_timer_ns() - t0 > BS_TIME_LIMIT_NS) ? 1 : 0;
+        return __shfl_sync(0xffffffffu, l, 0) != 0;
+    }
+};
+
+// ClusterTeam: the BS_TEAM_CTAS CTAs of a thread-block cluster.  The barrier
+// is the cluster barrier (release / acquire at cluster scope, which also
+// orders the workspace in global memory); a reduction reduces each warp by
+// shuffles, puts the warp results in its CTA's shared memory (two slots used
+// alternately, so a slot is rewritten only after every thread has passed the
+// next reduction's barrier) and every thread combines all warps' results
+// through distributed shared memory.
+struct ClusterTeam {
+    static constexpr int T = BS_TEAM_CTAS * 32 * BS_WARPS;
+    static constexpr int NW = BS_TEAM_CTAS * BS_WARPS;
+    int t;
+    double *red;  // this CTA's shared [2][BS_WARPS][BS_KMAX]
+    int *redi;    // this CTA's shared [2][BS_WARPS]
+    mutable unsigned k;  // reductions so far (selects the shared slot)
+    __device__ void sync() const { cooperative_groups::this_cluster().sync(); }
+    __device__ void max_of(double *v, int cnt) const {
+        const int slot = k++ & 1, w = (threadIdx.x >> 5), lane = threadIdx.x & 31;
+        for (int q = 0; q < cnt; q++) {
+            const double m = warp_max(v[q]);
+            if (lane == 0) red[(slot * BS_WARPS + w) * BS_KMAX + q] = m;
+        }
+        sync();
+        auto cl = cooperative_groups::this_cluster();
+        for (int r = 0; r < BS_TEAM_CTAS; r++) {
+            const double *rr = cl.map_shared_rank(red, r);
+            for (int ww = 0; ww < BS_WARPS; ww++)
+                for (int q = 0; q < cnt; q++) {
+                    const double x = rr[(slot * BS_WARPS + ww) * BS_KMAX + q];
+                    v[q] = (r == 0 && ww == 0) ? x : fmax(v[q], x);  // fmax of every warp's value, as a warp does
+                }
+        }
+    }
+    __device__ double min_nonneg(double v) const {
+        double b = -warp_min_nonneg(v);  // max of the negatives, via max_of on one value
+        max_of(&b, 1);
+        return -b;
+    }
+    __device__ int min_int(int v) const {
+        const int slot = k++ & 1, w = (threadIdx.x >> 5), lane = threadIdx.x & 31;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) redi[slot * BS_WARPS + w] = v;
+        sync();
+        auto cl = cooperative_groups::this_cluster();
+        int r0 = v;
+        for (int r = 0; r < BS_TEAM_CTAS; r++) {
+            const int *rr = cl.map_shared_rank(redi, r);
+            for (int ww = 0; ww < BS_WARPS; ww++) r0 = min(r0, rr[slot * BS_WARPS + ww]);
+        }
+        return r0;
+    }
+    __device__ bool late(uint64_t t0) const {  // any warp past the time limit (its lane 0's clock)
+        int l = 0;
+        if ((threadIdx.x & 31) == 0) l = (global_timer_ns() - t0 > BS_TIME_LIMIT_NS) ? 1 : 0;
+        l = __shfl_sync(0xffffffffu, l, 0);
+        return min_int(-l) < 0;
+    }
+};
+
 // Groups of up to 4 members, everything in registers: lane 8 q + k holds
 // member q (q < n) for extrapolation column k; partners' positions come from
 // lanes 8 p + k by shuffles.  The same arithmetic as bs_general, in the same
@@ -653,14 +743,17 @@ __device__ void bs_small(const BSArgs &a, int s0, int n, int lane, uint64_t t0, 
     }
 }
 
-__device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0, bool &forced) {
+template <class Team>
+__device__ void bs_general(const BSArgs &a, int s0, int n, const Team &tm, uint64_t t0, bool &forced) {
+    constexpr int T = Team::T;
+    const int lane = tm.t;  // this thread's rank in the team
     const int kcol = lane & 7, qs = lane >> 3;
     const int nk = 2 * (kcol + 1);
     const Work W{a.bs, (size_t)a.slots};
     const int fz = F_Z + 18 * kcol;  // this lane's column: buffers fz + 6 b + c
     {
         const bool tab = n <= BS_PAIR_TAB;
-        for (int q = lane; q < n; q += 32) {
+        for (int q = lane; q < n; q += T) {
             const int s = s0 + q, v = a.gbody[s];
             const int k = (int)a.iperm[v];
             W(F_Y + 0, s) = a.x[v];
@@ -675,9 +768,9 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
             W(F_RAD, s) = a.radius ? a.radius[v] : 0.0;
             a.tpf[s] = (a.lo[k].w != 0.f ? 1 : 0) | (signbit(a.m[v]) ? 2 : 0);
         }
-        __syncwarp();
+        tm.sync();
         auto pair_table = [&]() {  // pair radii, fixed over the drift (masses change only in mergers)
-            for (int idx = lane; idx < n * n; idx += 32) {
+            for (int idx = lane; idx < n * n; idx += T) {
                 const int si = s0 + idx / n, ti = idx % n;
                 const double rc = pair_radius(a, W(F_M, si), W(F_M, s0 + ti), W(F_A, si), W(F_A, s0 + ti),
                                               W(F_RC, si), W(F_RC, s0 + ti));
@@ -685,13 +778,13 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
                 W(F_PR2 + ti, si) = rcl * rcl;
                 W(F_PIN + ti, si) = 1.0 / (0.9 * rc);
             }
-            __syncwarp();
+            tm.sync();
         };
         if (tab) pair_table();
         double done = 0.0, frac;
         {  // first sub-step from the fastest interacting pair
             double f = 1.0;
-            for (int idx = lane; idx < n * n; idx += 32) {
+            for (int idx = lane; idx < n * n; idx += T) {
                 const int i = idx / n, j = idx % n;
                 if (j <= i) continue;
                 const int si = s0 + i, sj = s0 + j;
@@ -701,15 +794,12 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
                                        W(F_Y + 4, sj) - W(F_Y + 4, si), W(F_Y + 5, sj) - W(F_Y + 5, si),
                                        fabs(a.dt)));
             }
-            frac = warp_min_nonneg(f);
+            frac = tm.min_nonneg(f);
         }
         for (int att = 0; att < BS_MAX_ATTEMPTS && done < 1.0; att++) {
-            int late = 0;
-            if (lane == 0) late = (global_timer_ns() - t0 > BS_TIME_LIMIT_NS) ? 1 : 0;
-            late = __shfl_sync(0xffffffffu, late, 0);
-            if (late) break;  // the rest of the drift on Kepler orbits, below
+            if (tm.late(t0)) break;  // the rest of the drift on Kepler orbits, below
             const double h = frac * a.dt;
-            for (int q = lane; q < n; q += 32) {  // error scales and f(y)
+            for (int q = lane; q < n; q += T) {  // error scales and f(y)
                 const int s = s0 + q;
                 const double x = W(F_Y, s), y = W(F_Y + 1, s), z = W(F_Y + 2, s);
                 const double u = W(F_Y + 3, s), v = W(F_Y + 4, s), w = W(F_Y + 5, s);
@@ -722,9 +812,9 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
                 W(F_F0 + 1, s) = ay;
                 W(F_F0 + 2, s) = az;
             }
-            __syncwarp();
+            tm.sync();
             const double H = h / nk;
-            for (int q = qs; q < n; q += 4) {  // z_0 = y, z_1 = y + H f(y), every column
+            for (int q = qs; q < n; q += T / 8) {  // z_0 = y, z_1 = y + H f(y), every column
                 const int s = s0 + q;
                 for (int c = 0; c < 6; c++) {
                     const double yc = W(F_Y + c, s);
@@ -733,13 +823,13 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
                     W(fz + 6 + c, s) = fma(H, fc, yc);
                 }
             }
-            __syncwarp();
+            tm.sync();
             // stage m: z_{m+1} from z_m (m < n_k) or the smoothing step (m = n_k);
             // after m - 1 stages z_m is buffer m mod 3 and z_{m-1} buffer (m - 1) mod 3
             for (int m = 1; m <= 2 * BS_KMAX; m++) {
                 if (m <= nk) {
                     const int bc = m % 3, bp = (m + 2) % 3, bn = (m + 1) % 3;
-                    for (int q = qs; q < n; q += 4) {
+                    for (int q = qs; q < n; q += T / 8) {
                         const int s = s0 + q;
                         double ax, ay, az;
                         level1_acc(a, W, s, s0, n, fz + 6 * bc, tab, ax, ay, az);
@@ -755,12 +845,12 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
                         }
                     }
                 }
-                __syncwarp();
+                tm.sync();
             }
-            // extrapolation and error per (member, component); lane handles items lane, lane + 32, ...
+            // extrapolation and error per (member, component); a thread takes items lane, lane + T, ...
             double ek[BS_KMAX];
             for (int k = 0; k < BS_KMAX; k++) ek[k] = 0.0;
-            for (int item = lane; item < 6 * n; item += 32) {
+            for (int item = lane; item < 6 * n; item += T) {
                 const int q = item / 6, c = item % 6, s = s0 + q;
                 const double isc = W(F_ISC + (c < 3 ? 0 : 1), s);
                 double row[BS_KMAX];   // row k of the table, in place
@@ -782,11 +872,10 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
                 for (int k = 0; k < BS_KMAX; k++) W(F_T + 6 * k + c, s) = diag[k];
             }
             int acc_col = -1;
-            for (int k = 1; k < BS_KMAX; k++) {
-                const double e = warp_max(ek[k]);
-                if (acc_col < 0 && e <= a.tol) acc_col = k;
-            }
-            __syncwarp();
+            tm.max_of(ek, BS_KMAX);  // every column's error over the team
+            for (int k = 1; k < BS_KMAX; k++)
+                if (acc_col < 0 && ek[k] <= a.tol) acc_col = k;
+            tm.sync();
             if (acc_col < 0 && frac <= BS_MIN_FRAC) {
                 acc_col = BS_KMAX - 1;
                 forced = true;
@@ -795,15 +884,15 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
                 frac *= 0.5;
                 continue;
             }
-            for (int q = lane; q < n; q += 32) {
+            for (int q = lane; q < n; q += T) {
                 const int s = s0 + q;
                 for (int c = 0; c < 6; c++) W(F_Y + c, s) = W(F_T + 6 * acc_col + c, s);
             }
-            __syncwarp();
+            tm.sync();
             if (a.radius) {  // perfect mergers: the first overlapping pair (i < j), again until none
                 for (int it = 0; it < n - 1; it++) {
                     int code = n * n;  // i n + j of the first overlapping pair
-                    for (int idx = lane; idx < n * n; idx += 32) {
+                    for (int idx = lane; idx < n * n; idx += T) {
                         const int i = idx / n, j = idx % n;
                         if (j <= i) continue;
                         const int si = s0 + i, sj = s0 + j;
@@ -813,11 +902,10 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
                         const double rr = W(F_RAD, si) + W(F_RAD, sj);
                         if (dx * dx + dy * dy + dz * dz < rr * rr) code = min(code, idx);
                     }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) code = min(code, __shfl_xor_sync(0xffffffffu, code, o));
+                    code = tm.min_int(code);
                     if (code == n * n) break;
                     const int si = s0 + code / n, sj = s0 + code % n;
-                    if (lane == 0) {
+                    if (lane == 0) {  // the team's first thread
                         const double mi = W(F_M, si), mj = W(F_M, sj), mt = mi + mj;
                         for (int c = 0; c < 6; c++) {
                             const double u = W(F_Y + c, si), w = W(F_Y + c, sj);
@@ -830,7 +918,7 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
                         W(F_RAD, sj) = 0.0;
                         a.tpf[sj] |= 2;
                     }
-                    __syncwarp();
+                    tm.sync();
                     if (tab) pair_table();
                 }
             }
@@ -840,7 +928,7 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
         }
         if (done < 1.0) {  // out of attempts or time: the rest of the drift on Kepler orbits (level 0)
             forced = true;
-            for (int q = lane; q < n; q += 32) {
+            for (int q = lane; q < n; q += T) {
                 const int s = s0 + q;
                 double px = W(F_Y, s), py = W(F_Y + 1, s), pz = W(F_Y + 2, s);
                 double u = W(F_Y + 3, s), vv = W(F_Y + 4, s), w = W(F_Y + 5, s);
@@ -848,9 +936,9 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
                 W(F_Y, s) = px; W(F_Y + 1, s) = py; W(F_Y + 2, s) = pz;
                 W(F_Y + 3, s) = u; W(F_Y + 4, s) = vv; W(F_Y + 5, s) = w;
             }
-            __syncwarp();
+            tm.sync();
         }
-        for (int q = lane; q < n; q += 32) {
+        for (int q = lane; q < n; q += T) {
             const int s = s0 + q, v = a.gbody[s];
             a.x[v] = W(F_Y, s);
             a.y[v] = W(F_Y + 1, s);
@@ -868,28 +956,63 @@ __device__ void bs_general(const BSArgs &a, int s0, int n, int lane, uint64_t t0
     }
 }
 
-// One warp per group: members sorted by body index, then the register path
-// (n <= 4) or the workspace path.
-__global__ void __launch_bounds__(32 * BS_WARPS) bs_kernel(const __grid_constant__ BSArgs a) {
+// Members of group (s0, n) in ascending body order (the order of every sum),
+// by the threads t = 0, T, 2T, ... of a team.
+__device__ __forceinline__ void sort_members(const BSArgs &a, int s0, int n, int t, int T) {
+    for (int q = t; q < n; q += T) {
+        const int v = a.gmem[s0 + q];
+        int rank = 0;
+        for (int r = 0; r < n; r++) rank += (a.gmem[s0 + r] < v) ? 1 : 0;
+        a.gbody[s0 + rank] = v;
+    }
+}
+
+// Launched as clusters of BS_TEAM_CTAS CTAs.  First every group of more than
+// BS_TEAM_MIN members, one cluster per group (the k-th such group goes to
+// cluster k mod clusters), on the workspace path with the cluster as its
+// team; then every other group on one warp: the register path (n <= 4) or
+// the workspace path.
+__global__ void __cluster_dims__(BS_TEAM_CTAS, 1, 1) __launch_bounds__(32 * BS_WARPS, 2)
+    bs_kernel(const __grid_constant__ BSArgs a) {
     static_assert(BS_KMAX == 8, "lane = 8 * member slice + column");
+    __shared__ double s_red[2 * BS_WARPS * BS_KMAX];
+    __shared__ int s_redi[2 * BS_WARPS];
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * BS_WARPS + (threadIdx.x >> 5), nw = gridDim.x * BS_WARPS;
     const int ng = *a.gcount;
     uint64_t t0 = 0;  // the time limit holds for the whole launch, however many groups a warp takes
     if (lane == 0) t0 = global_timer_ns();
+    {
+        auto cl = cooperative_groups::this_cluster();
+        ClusterTeam tm{(int)cl.block_rank() * 32 * BS_WARPS + (int)threadIdx.x, s_red, s_redi, 0u};
+        const int ncl = (int)(gridDim.x / BS_TEAM_CTAS), cid = (int)(blockIdx.x / BS_TEAM_CTAS);
+        int big = 0;
+        for (int g0 = 0; g0 < ng; g0 += 32) {  // every warp finds the same large groups
+            const bool large = g0 + lane < ng && a.gsize[g0 + lane] > BS_TEAM_MIN;
+            unsigned m = __ballot_sync(0xffffffffu, large);
+            while (m) {
+                const int g = g0 + __ffs((int)m) - 1;
+                m &= m - 1u;
+                if (big++ % ncl != cid) continue;
+                const int s0 = a.gstart[g], n = a.gsize[g];
+                sort_members(a, s0, n, tm.t, ClusterTeam::T);
+                tm.sync();
+                bool forced = false;
+                bs_general(a, s0, n, tm, t0, forced);
+                if (forced && tm.t == 0) atomicOr(a.status, GENGA_BIT(GENGA_ERR_BS));
+                tm.sync();
+            }
+        }
+    }
+    const int gw = blockIdx.x * BS_WARPS + (threadIdx.x >> 5), nw = gridDim.x * BS_WARPS;
+    const WarpTeam wt{lane};
     for (int g = gw; g < ng; g += nw) {
         const int s0 = a.gstart[g], n = a.gsize[g];
-        // members in ascending body order (the order of every sum)
-        for (int q = lane; q < n; q += 32) {
-            const int v = a.gmem[s0 + q];
-            int rank = 0;
-            for (int r = 0; r < n; r++) rank += (a.gmem[s0 + r] < v) ? 1 : 0;
-            a.gbody[s0 + rank] = v;
-        }
+        if (n > BS_TEAM_MIN) continue;
+        sort_members(a, s0, n, lane, 32);
         __syncwarp();
         bool forced = false;
         if (n <= 4) bs_small(a, s0, n, lane, t0, forced);
-        else bs_general(a, s0, n, lane, t0, forced);
+        else bs_general(a, s0, n, wt, t0, forced);
         if (forced && lane == 0) atomicOr(a.status, GENGA_BIT(GENGA_ERR_BS));
         __syncwarp();
     }
@@ -902,8 +1025,28 @@ cudaError_t launch_groups(const GroupArgs &g, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Clusters of the level-1 kernel resident at once (queried when a context is
+// created, outside any capture; one GPU model per process).
+int g_bs_clusters = 0;
+
+cudaError_t init_bs_kernel(int sm_count) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((2 * sm_count) / BS_TEAM_CTAS * BS_TEAM_CTAS));
+    cfg.blockDim = dim3(32 * BS_WARPS);
+    int ncl = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&ncl, (void *)bs_kernel, &cfg);
+    if (e != cudaSuccess) return e;
+    g_bs_clusters = ncl > 0 ? ncl : 1;
+    return cudaSuccess;
+}
+
 cudaError_t launch_bs(const BSArgs &b, int sm_count, cudaStream_t s) {
-    bs_kernel<<<2 * sm_count, 32 * BS_WARPS, 0, s>>>(b);
+    // as many clusters as are resident at once (the kernel hands out its
+    // groups statically, so a second wave of CTAs would run after the first),
+    // at most two CTAs per SM
+    const int resident = g_bs_clusters > 0 ? g_bs_clusters : 1;
+    const int grid = std::min(resident, (2 * sm_count) / BS_TEAM_CTAS) * BS_TEAM_CTAS;
+    bs_kernel<<<grid > 0 ? grid : BS_TEAM_CTAS, 32 * BS_WARPS, 0, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -324,6 +324,7 @@ cudaError_t launch_groups(const GroupArgs &g, cudaStream_t s);
 cudaError_t launch_removal(genga_system &sys, const genga_params &p, cudaStream_t s);
 cudaError_t launch_compact(genga_ctx *c, genga_system &sys, int32_t *id, int32_t *count, cudaStream_t s);
 cudaError_t launch_bs(const BSArgs &b, int sm_count, cudaStream_t s);
+cudaError_t init_bs_kernel(int sm_count);  // the level-1 kernel's resident clusters (at context creation)
 cudaError_t launch_momentum(const double *vx, const double *vy, const double *vz, const double *m,
                             int N, double *P, int32_t *zero_me, cudaStream_t s);
 cudaError_t launch_prep(const genga_system &sys, const genga_params &p, genga_ctx *c, cudaStream_t s);
