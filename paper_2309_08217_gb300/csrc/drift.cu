@@ -222,16 +222,19 @@ cudaError_t run_level(genga_system &sys, const genga_params &p, genga_ctx *c, in
     const double h = T / p.n_sub;
     cudaError_t e = launch_level_sort(a, c->sm_count, s);
     for (int k = 0; k < p.n_sub && e == cudaSuccess; k++) {
-        e = launch_level_kick(a, 0.5 * h, c->sm_count, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(next.pair_count, 0, 2 * sizeof(int32_t), s);
+        // the closing half kick of sub-step k - 1 and the opening one of
+        // sub-step k act at the same positions with the same weights: one
+        // kick of h (h / 2 for the first), which also empties the next
+        // level's pair list for this sub-step's scan
+        e = launch_level_kick(a, k == 0 ? 0.5 * h : h, true, c->sm_count, s);
         if (e == cudaSuccess) e = launch_level_scan(a, h, c->sm_count, s);
         if (e == cudaSuccess) e = launch_groups(group_args(sys, c, next, next.pairs), s);
         if (e == cudaSuccess) e = launch_level_drift(a, h, c->sm_count, s);
         if (e == cudaSuccess)
             e = level < p.n_levels ? run_level(sys, p, c, level + 1, h, s)
                                    : launch_bs(bs_args(sys, p, h, c, next, p.n_levels), c->sm_count, s);
-        if (e == cudaSuccess) e = launch_level_kick(a, 0.5 * h, c->sm_count, s);
     }
+    if (e == cudaSuccess) e = launch_level_kick(a, 0.5 * h, false, c->sm_count, s);  // the last closing half kick
     if (e == cudaSuccess) e = launch_level_clear(a, c->sm_count, s);
     return e;
 }
@@ -253,7 +256,9 @@ cudaError_t launch_level1(genga_system &sys, const genga_params &p, double dt, g
 // and kick, and one sort and one clear per level.
 int level_launches(int n_levels, int n_sub) {
     int below = 1;  // the Bulirsch-Stoer kernel
-    for (int l = n_levels; l >= 1; l--) below = n_sub * (5 + below) + 2;
+    // per sub-step kick, scan, groups, drift and the level below; sort, the
+    // last closing kick and clear once per level
+    for (int l = n_levels; l >= 1; l--) below = n_sub * (4 + below) + 3;
     return below;
 }
 

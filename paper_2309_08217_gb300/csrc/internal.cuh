@@ -315,7 +315,7 @@ struct LevelArgs {              // one intermediate level (levels.cu): its group
 
 int level_launches(int n_levels, int n_sub);
 cudaError_t launch_level_sort(const LevelArgs &a, int sm_count, cudaStream_t s);
-cudaError_t launch_level_kick(const LevelArgs &a, double tau, int sm_count, cudaStream_t s);
+cudaError_t launch_level_kick(const LevelArgs &a, double tau, bool zero_next, int sm_count, cudaStream_t s);
 cudaError_t launch_level_scan(const LevelArgs &a, double h, int sm_count, cudaStream_t s);
 cudaError_t launch_level_drift(const LevelArgs &a, double h, int sm_count, cudaStream_t s);
 cudaError_t launch_level_clear(const LevelArgs &a, int sm_count, cudaStream_t s);

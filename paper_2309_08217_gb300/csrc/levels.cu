@@ -98,8 +98,11 @@ __device__ __forceinline__ double warp_sum(double v) {
 // large group spreads over the SMs' FP64 pipes), lanes over its partners in
 // body order, a fixed-order warp sum.  Positions are only read, so the
 // members' velocities are updated in place.
-__global__ void __launch_bounds__(32 * LV_WARPS) level_kick_kernel(const __grid_constant__ LevelArgs a, double tau) {
+__global__ void __launch_bounds__(32 * LV_WARPS) level_kick_kernel(const __grid_constant__ LevelArgs a, double tau,
+                                                                   int zero_next) {
     const int lane = threadIdx.x & 31;
+    // the next level's pair list starts empty for the scan that follows this kick
+    if (zero_next && blockIdx.x == 0 && threadIdx.x < 2) a.next_count[threadIdx.x] = 0;
     const int gw = blockIdx.x * LV_WARPS + (threadIdx.x >> 5), nw = gridDim.x * LV_WARPS;
     const int ns = member_slots(a);
     for (int item = gw; item < ns; item += nw) {
@@ -222,8 +225,8 @@ cudaError_t launch_level_sort(const LevelArgs &a, int sm_count, cudaStream_t s) 
     return cudaGetLastError();
 }
 
-cudaError_t launch_level_kick(const LevelArgs &a, double tau, int sm_count, cudaStream_t s) {
-    level_kick_kernel<<<2 * sm_count, 32 * LV_WARPS, 0, s>>>(a, tau);
+cudaError_t launch_level_kick(const LevelArgs &a, double tau, bool zero_next, int sm_count, cudaStream_t s) {
+    level_kick_kernel<<<2 * sm_count, 32 * LV_WARPS, 0, s>>>(a, tau, zero_next ? 1 : 0);
     return cudaGetLastError();
 }
 
