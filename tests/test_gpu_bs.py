@@ -247,3 +247,28 @@ def test_step_parity_eq1_radius_quintic_weight(genga, ctx, precision):
     assert oracle.step(arr, d.G, d.Mstar, dt, 3.0, 0.4, 0, 1, 3, bs_tol=TOL_BS, forced=forced) == 0
     assert forced[0] == 0
     assert _rel_state(s.numpy(), arr) < (1e-10 if precision == 0 else 1e-9)
+
+
+@pytest.mark.parametrize("n_swarm", [23, 24, 30])
+def test_group_sizes_around_the_cluster_threshold(genga, ctx, n_swarm):
+    """Groups of 24 members run on one warp, of 25 and more on a cluster of
+    CTAs (the same workspace path with cluster barriers and reductions):
+    both against the oracle's Bulirsch-Stoer steps, and bitwise repeatable."""
+    d = _swarm(n_swarm=n_swarm, seed=5)
+    mem, ng, pairs = _members(d)
+    label, _ = oracle.groups(d.N, pairs)
+    assert int((label == label[0]).sum()) == n_swarm + 1   # the planet's group
+    arr = oracle.disc_arrays(d)
+    forced = [0]
+    assert oracle.step(arr, d.G, d.Mstar, d.dt, 3.0, 0.4, 1, 0, 2, bs_tol=TOL_BS, forced=forced) == 0
+    assert forced[0] == 0
+    got = []
+    for _ in range(2):  # fresh contexts: the same spatial order and plans
+        c = genga.Context(d.N)
+        s = genga.DeviceSystem.from_disc(d)
+        genga.genga_step(c, s, _params(genga, d, 0), 2)
+        assert genga.genga_get_status(c) == genga.GENGA_OK
+        got.append(np.stack(s.numpy()))
+        c.close()
+    assert np.array_equal(got[0], got[1])
+    assert _rel_state(list(got[0]), arr) < 1e-10

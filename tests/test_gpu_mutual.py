@@ -225,3 +225,26 @@ def test_mutual_plan_grows_the_workspace(genga):
     assert genga.genga_get_status(c) == genga.GENGA_OK
     assert np.all(np.isfinite(np.stack(s.numpy())))
     c.close()
+
+
+def test_mutual_200k_sampled(genga):
+    """200,000 bodies (longer sums: the per-body error grows with N), each
+    mutual variant on 512 sampled bodies against the oracle."""
+    import torch
+    d = discs.disc_powerlaw(200_000, 9)
+    c = genga.Context(d.N)
+    p = _params(genga, d)
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(d.N, 512, replace=False))
+    arr = oracle.disc_arrays(d)
+    a, rc = oracle.rcrit(*arr, G=d.G, Mstar=d.Mstar, dt=d.dt, n1=3.0, n2=0.4)
+    ref = oracle.kick_acc(arr[0], arr[1], arr[2], arr[6], a, rc, d.G, d.Mstar, 3.0, 1, 0, idx=idx)
+    s = genga.DeviceSystem.from_disc(d)
+    for v in _mutual_variants(genga):
+        genga.genga_set_kernel_variant(c, v)
+        acc = torch.zeros(3 * d.N, dtype=torch.float64, device="cuda")
+        genga.genga_kick(c, s, p, 0.0, acc)
+        assert genga.genga_get_status(c) == genga.GENGA_OK
+        got = acc.view(3, d.N).cpu().numpy()[:, idx]
+        assert _rel(got, ref).max() <= TOL32, f"variant {v}"
+    c.close()
