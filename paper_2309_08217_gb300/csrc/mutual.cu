@@ -684,42 +684,54 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
     }
 }
 
-// One thread per (body, component): the body's i-rows then its j-rows, in
-// row order, in double-float; then the optional acc output and v += acc tau.
+// One thread per (two consecutive bodies, component): the bodies' i-rows
+// then their j-rows, in row order, in double-float; then the optional acc
+// output and v += acc tau.  Two bodies per thread make every row load 16
+// bytes per lane (512 contiguous bytes per warp): the rows are ~1 MB apart,
+// and 8-byte lanes left DRAM at ~40 % of its rate.  Both bodies are in the
+// same i-block (blocks are whole 64-body groups), so they share the rows.
 __global__ void combine_mutual_kernel(const double *__restrict__ partial, const __grid_constant__ MutualPlan P,
                                       int N, int npad, const uint32_t *__restrict__ perm, double tau,
                                       double *__restrict__ acc, double *__restrict__ vx, double *__restrict__ vy,
                                       double *__restrict__ vz, uint32_t *__restrict__ status) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int c = blockIdx.y;
     if (k >= N) return;
     const int b = k / (P.gpb * MG);
-    const size_t stride = 3 * (size_t)npad;
-    const float2 *p = reinterpret_cast<const float2 *>(partial) + (size_t)c * npad + k;
+    const size_t stride = 3 * (size_t)npad / 2;  // float4 units (two float2 entries)
+    const float4 *p = reinterpret_cast<const float4 *>(partial) + ((size_t)c * npad + k) / 2;
     const int2 bk = P.blk[b];
     // the rows in order: diagonal i-rows, strip i-rows, j-rows of the blocks before b
     const int n0 = bk.x, n1 = n0 + bk.y, n2 = n1 + b;
-    DF t{0.f, 0.f};
+    DF t0{0.f, 0.f}, t1{0.f, 0.f};
     constexpr int BATCH = 16;
     for (int r0 = 0; r0 < n2; r0 += BATCH) {
-        float2 v[BATCH];
+        float4 v[BATCH];
 #pragma unroll
         for (int u = 0; u < BATCH; u++) {
             const int r = r0 + u;
             const int rr = r < n0 ? r : r < n1 ? P.S + (r - n0) : P.irows + (r - n1);
-            v[u] = r < n2 ? p[(size_t)rr * stride] : make_float2(0.f, 0.f);
+            v[u] = r < n2 ? p[(size_t)rr * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < BATCH; u++)
-            if (r0 + u < n2) t = df_add(t, v[u].x, v[u].y);
+            if (r0 + u < n2) {
+                t0 = df_add(t0, v[u].x, v[u].y);
+                t1 = df_add(t1, v[u].z, v[u].w);
+            }
     }
-    const double s = (double)t.hi + (double)t.lo;
-    if (!isfinite(s)) atomicOr(status, GENGA_BIT(GENGA_ERR_NONFINITE));
-    const int i = (int)perm[k];
-    if (acc) acc[c * (size_t)N + i] = s;
-    if (tau != 0.0) {
-        double *v = c == 0 ? vx : (c == 1 ? vy : vz);
-        v[i] += s * tau;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        if (k + h >= N) break;
+        const DF &t = h ? t1 : t0;
+        const double s = (double)t.hi + (double)t.lo;
+        if (!isfinite(s)) atomicOr(status, GENGA_BIT(GENGA_ERR_NONFINITE));
+        const int i = (int)perm[k + h];
+        if (acc) acc[c * (size_t)N + i] = s;
+        if (tau != 0.0) {
+            double *v = c == 0 ? vx : (c == 1 ? vy : vz);
+            v[i] += s * tau;
+        }
     }
 }
 
@@ -1059,41 +1071,50 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
     }
 }
 
-// One thread per (body, component): the FP64 rows of a mutual FP64 pass in
-// the order of combine_mutual_kernel, Neumaier-compensated.
+// One thread per (two consecutive bodies, component): the FP64 rows of a
+// mutual FP64 pass in the order of combine_mutual_kernel (16-byte loads, as
+// there), Neumaier-compensated.
 __global__ void combine_mutual64_kernel(const double *__restrict__ partial, const __grid_constant__ MutualPlan P,
                                         int N, int npad, const uint32_t *__restrict__ perm, double tau,
                                         double *__restrict__ acc, double *__restrict__ vx, double *__restrict__ vy,
                                         double *__restrict__ vz, uint32_t *__restrict__ status) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int c = blockIdx.y;
     if (k >= N) return;
     const int b = k / (P.gpb * MG);
-    const size_t stride = 3 * (size_t)npad;
-    const double *p = partial + (size_t)c * npad + k;
+    const size_t stride = 3 * (size_t)npad / 2;  // double2 units
+    const double2 *p = reinterpret_cast<const double2 *>(partial) + ((size_t)c * npad + k) / 2;
     const int2 bk = P.blk[b];
     const int n0 = bk.x, n1 = n0 + bk.y, n2 = n1 + b;
-    CompS t{0.0, 0.0};
+    CompS t0{0.0, 0.0}, t1{0.0, 0.0};
     constexpr int BATCH = 16;
     for (int r0 = 0; r0 < n2; r0 += BATCH) {
-        double v[BATCH];
+        double2 v[BATCH];
 #pragma unroll
         for (int u = 0; u < BATCH; u++) {
             const int r = r0 + u;
             const int rr = r < n0 ? r : r < n1 ? P.S + (r - n0) : P.irows + (r - n1);
-            v[u] = r < n2 ? p[(size_t)rr * stride] : 0.0;
+            v[u] = r < n2 ? p[(size_t)rr * stride] : make_double2(0.0, 0.0);
         }
 #pragma unroll
         for (int u = 0; u < BATCH; u++)
-            if (r0 + u < n2) comp_add(t, v[u]);
+            if (r0 + u < n2) {
+                comp_add(t0, v[u].x);
+                comp_add(t1, v[u].y);
+            }
     }
-    const double s = t.s + t.c;
-    if (!isfinite(s)) atomicOr(status, GENGA_BIT(GENGA_ERR_NONFINITE));
-    const int i = (int)perm[k];
-    if (acc) acc[c * (size_t)N + i] = s;
-    if (tau != 0.0) {
-        double *v = c == 0 ? vx : (c == 1 ? vy : vz);
-        v[i] += s * tau;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        if (k + h >= N) break;
+        const CompS &t = h ? t1 : t0;
+        const double s = t.s + t.c;
+        if (!isfinite(s)) atomicOr(status, GENGA_BIT(GENGA_ERR_NONFINITE));
+        const int i = (int)perm[k + h];
+        if (acc) acc[c * (size_t)N + i] = s;
+        if (tau != 0.0) {
+            double *v = c == 0 ? vx : (c == 1 ? vy : vz);
+            v[i] += s * tau;
+        }
     }
 }
 
@@ -1380,8 +1401,8 @@ cudaError_t launch_combine_mutual64(const double *partial, const MutualPlan &P, 
                                     double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
                                     cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    combine_mutual64_kernel<<<dim3((N + 255) / 256, 3), 256, 0, s>>>(partial, P, N, npad, perm, tau, acc, vx, vy, vz,
-                                                                      status);
+    combine_mutual64_kernel<<<dim3(((N + 1) / 2 + 255) / 256, 3), 256, 0, s>>>(partial, P, N, npad, perm, tau, acc,
+                                                                                vx, vy, vz, status);
     return cudaGetLastError();
 }
 
@@ -1399,8 +1420,8 @@ cudaError_t launch_combine_mutual(const double *partial, const MutualPlan &P, in
                                   double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
                                   cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    combine_mutual_kernel<<<dim3((N + 255) / 256, 3), 256, 0, s>>>(partial, P, N, npad, perm, tau, acc, vx, vy, vz,
-                                                                    status);
+    combine_mutual_kernel<<<dim3(((N + 1) / 2 + 255) / 256, 3), 256, 0, s>>>(partial, P, N, npad, perm, tau, acc, vx,
+                                                                              vy, vz, status);
     return cudaGetLastError();
 }
 
