@@ -73,6 +73,7 @@ namespace {
 constexpr int MG = 64;           // bodies per staged j-group
 constexpr int MUTUAL_MAX_ROWS = 192;  // partial rows a mutual plan may use (its workspace grows to them)
 constexpr int M_FOLD = 2;        // slots between folds of the FP32 i-sums into double-float (2: max error 8e-6 at 200k bodies, 1.3e-5 with 4)
+constexpr int NEAR_SPEC_NP = 2;  // NEAR loops specialised per set of NEAR i-groups up to this NP (NP = 3 measured slower overall)
 constexpr int M_CLAIM = 3;       // a producer claims an item when the leading warp has at most M_CLAIM - 1 slots left
 
 struct MHdr {
@@ -103,6 +104,18 @@ __device__ __forceinline__ bool wait_lead(const unsigned *lead, unsigned target,
         __nanosleep(32);
     }
     return true;
+}
+
+// f(integral_constant<unsigned, m>) for the run-time value m in [M, MAXM].
+template <unsigned M, unsigned MAXM, class F>
+__device__ __forceinline__ void dispatch_mask(unsigned m, F &f) {
+    if constexpr (M <= MAXM) {
+        if (m == M) {
+            f(std::integral_constant<unsigned, M>{});
+            return;
+        }
+        dispatch_mask<M + 1, MAXM>(m, f);
+    }
 }
 
 __device__ __forceinline__ f32x2 rsq2(f32x2 r2) {
@@ -489,7 +502,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                 // only for those) and their screening bounds (the i-group's
                 // largest H and A against the j-group's)
                 float thr[NP];
-                const unsigned qres = NP <= 2 ? qnear : (1u << NP) - 1u;  // i-groups taking the NEAR treatment
+                const unsigned qres = NP <= NEAR_SPEC_NP ? qnear : (1u << NP) - 1u;  // i-groups taking the NEAR treatment
 #pragma unroll
                 for (int q = 0; q < NP; q++) {
                     thr[q] = 0.f;
@@ -623,17 +636,12 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                         }
                     }
                 };
-                if constexpr (NP <= 2) {
-                    if (qnear == 1u) {
-                        if (both) near_loop(std::true_type{}, std::integral_constant<unsigned, 1u>{});
-                        else near_loop(std::false_type{}, std::integral_constant<unsigned, 1u>{});
-                    } else if (qnear == 2u) {
-                        if (both) near_loop(std::true_type{}, std::integral_constant<unsigned, 2u>{});
-                        else near_loop(std::false_type{}, std::integral_constant<unsigned, 2u>{});
-                    } else {
-                        if (both) near_loop(std::true_type{}, std::integral_constant<unsigned, 3u>{});
-                        else near_loop(std::false_type{}, std::integral_constant<unsigned, 3u>{});
-                    }
+                if constexpr (NP <= NEAR_SPEC_NP) {  // one instantiation per non-empty set of NEAR i-groups
+                    auto run = [&](auto mask_tag) {
+                        if (both) near_loop(std::true_type{}, mask_tag);
+                        else near_loop(std::false_type{}, mask_tag);
+                    };
+                    dispatch_mask<1u, (1u << NP) - 1u>(qnear, run);
                 } else {  // every i-group takes the NEAR treatment (residuals and thresholds of all)
                     constexpr unsigned ALL = (1u << NP) - 1u;
                     if (both) near_loop(std::true_type{}, std::integral_constant<unsigned, ALL>{});
