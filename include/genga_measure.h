@@ -81,13 +81,14 @@ genga_status genga_fp64_variant_info(int32_t variant, int32_t *kind, int32_t *wa
 genga_status genga_fp64_tuning_times(genga_ctx *ctx, int32_t N, float *ms, int32_t n);
 
 /* Batched mode: the FP32 variant the context tuned for the batch layout
- * `offsets` (D + 1 ints, HOST memory, as for genga_kick_batched) -- -1 when
- * this layout has not been tuned (or was forgotten: a context remembers the
- * last 8 layouts) -- and the batched pass time (ms) of each one-sided variant
- * measured then (0 where not measured); variant and ms[n] are HOST memory.
- * A layout is tuned by its first batched kick or step outside a stream
- * capture (every one-sided variant's batched pass timed; genga_set_kernel_variant
- * with a one-sided variant skips that). */
+ * `offsets` (D + 1 ints, HOST memory, as for genga_kick_batched) in the
+ * autotuned precision mode GENGA_FP32 -- -1 when this layout has not been
+ * tuned (or was forgotten: a context remembers the last 8 layouts and modes)
+ * -- and the batched pass + combine time (ms) of each variant measured then
+ * (0 where not measured); variant and ms[n] are HOST memory.  A layout is
+ * tuned by its first batched kick or step outside a stream capture (every
+ * variant of the mode's family: one-sided and mutual for GENGA_FP32;
+ * genga_set_kernel_variant skips that). */
 genga_status genga_batched_tuning(genga_ctx *ctx, const int32_t *offsets, int32_t D, int32_t *variant, float *ms,
                                   int32_t n);
 

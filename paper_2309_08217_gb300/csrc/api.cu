@@ -97,7 +97,7 @@ PassArgs base_args(genga_ctx *c, const genga_system &sys, const genga_params &p)
     a.rel = c->pk_r;
     a.rell = c->pk_rl;
     a.gctr = c->gctr;
-    a.mp = MutualPlan{0, 0, 0, 0, 0, 0, nullptr, nullptr};
+    a.mp = MutualPlan{};
     a.wait_ns_log2 = c->test_wait_log2;
     a.hold = c->test_hold;
     a.lo = c->pk_lo;
@@ -489,39 +489,81 @@ bool plan_batch(const genga_ctx *c, const BatchBodies &bb, int variant, BatchIte
     return false;
 }
 
-// The FP32 variant of a batch: forced (one-sided variants only), already
-// tuned for this batch layout, or tuned now: every one-sided variant's
-// batched pass (its own work plan) run three times on the packed state, the
-// fastest of the last two kept.  The context remembers GENGA_BATCH_LAYOUTS
-// layouts (the oldest is replaced).  Tuning synchronises the stream, so it is
-// skipped during a capture (variant 0).
-int batch_variant(genga_ctx *c, const PassArgs &a, const BatchBodies &bb, unsigned long long key, cudaStream_t s,
-                  bool tune = true) {
-    if (c->forced_variant >= 0 && !is_mutual(c->forced_variant)) return c->forced_variant;
+// Launches the batched pass of FP32 variant v (one-sided: its BatchItems
+// plan; mutual: the plan over the batch's systems) and its combine.  False
+// when a mutual plan cannot be had (built during a capture, or none fits):
+// nothing launched.
+bool launch_batched_variant(genga_ctx *c, PassArgs a, const BatchBodies &bb, unsigned long long key, int v,
+                            double tau, double *acc, const genga_system &all, cudaStream_t s, bool profile,
+                            cudaError_t *err) {
+    *err = cudaSuccess;
+    if (is_mutual(v)) {
+        MutualPlan mp;
+        if (!mutual_plan_batched(c, bb, key, v - num_fp32_variants(), s, &mp)) return false;
+        a.partial = c->partial;  // the plan may have enlarged (reallocated) the partial rows
+        a.mp = mp;
+        if (profile) profile_before_pass(c, s);
+        *err = launch_pass_mutual(a, v - num_fp32_variants(), c->sm_count, s);
+        if (profile) profile_after_pass(c, s);
+        if (*err == cudaSuccess)
+            *err = launch_combine_mutual(c->partial, mp, bb.N_total, bb.npad_total, c->perm, tau, acc, all.vx,
+                                         all.vy, all.vz, c->status, s);
+        return true;
+    }
+    BatchItems bi;
+    int grid = 1;
+    if (!plan_batch(c, bb, v, &bi, &grid)) {
+        *err = cudaErrorInvalidValue;
+        return true;
+    }
+    a.partial = c->partial;
+    if (profile) profile_before_pass(c, s);
+    *err = launch_pass_batched(a, bb, bi, v, grid, s);
+    if (profile) profile_after_pass(c, s);
+    if (*err == cudaSuccess)
+        *err = launch_combine_batched(bb, bi, c->partial, c->perm, tau, acc, all.vx, all.vy, all.vz, c->status, s);
+    return true;
+}
+
+// The FP32 variant of a batch: forced (within the precision mode's family),
+// already tuned for this batch layout and family, or tuned now: every
+// variant of the family (one-sided in test-particle mode 2 and for
+// GENGA_FP32_HILO, mutual for GENGA_FP32_BLOCKREL, both for GENGA_FP32) run
+// three times -- batched pass and combine, no kick applied -- on the packed
+// state, the fastest of the last two kept.  The context remembers
+// GENGA_BATCH_LAYOUTS (layout, family) pairs (the oldest is replaced).
+// Tuning synchronises the stream, so it is skipped during a capture (the
+// family's first variant).
+int batch_variant(genga_ctx *c, const PassArgs &a, const BatchBodies &bb, unsigned long long key, int precision,
+                  cudaStream_t s, bool tune = true) {
+    const int fam = a.n_big >= 0 ? 1 : family_of(precision);
+    auto in_family = [&](int v) { return fam == 0 || (fam == 1) == !is_mutual(v); };
+    const int first = fam == 2 ? num_fp32_variants() : 0;
+    if (c->forced_variant >= 0 && in_family(c->forced_variant)) return c->forced_variant;
+    const unsigned long long fkey = key ^ (0x9e3779b97f4a7c15ull * (unsigned long long)(fam + 1));
     for (int q = 0; q < GENGA_BATCH_LAYOUTS; q++)
-        if (c->bt_var[q] >= 0 && c->bt_key[q] == key) return c->bt_var[q];
-    if (!tune || !can_tune(s)) return 0;
+        if (c->bt_var[q] >= 0 && c->bt_key[q] == fkey) return c->bt_var[q];
+    if (!tune || !can_tune(s)) return first;
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return 0;
+    if (cudaEventCreate(&e0) != cudaSuccess) return first;
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
-        return 0;
+        return first;
     }
     const int slot = c->bt_next;
     c->bt_next = (c->bt_next + 1) % GENGA_BATCH_LAYOUTS;
-    int best = 0;
+    genga_system none{};
+    none.N = bb.N_total;
+    int best = first;
     float best_ms = 3.0e38f;
-    for (int v = 0; v < num_fp32_variants() && v < GENGA_MAX_VARIANTS; v++) {
+    for (int v = 0; v < num_all_variants() && v < GENGA_MAX_VARIANTS; v++) {
         c->bt_ms[slot][v] = 0.f;
-        BatchItems bi;
-        int grid = 1;
-        if (!plan_batch(c, bb, v, &bi, &grid)) continue;
-        PassArgs av = a;
-        av.partial = c->partial;
+        if (!in_family(v)) continue;
         float ms = 3.0e38f;
         for (int rep = 0; rep < 3; rep++) {
+            cudaError_t e = cudaSuccess;
             cudaEventRecord(e0, s);
-            const cudaError_t e = launch_pass_batched(av, bb, bi, v, grid, s);
+            if (!launch_batched_variant(c, a, bb, key, v, 0.0, nullptr, none, s, false, &e)) break;
             cudaEventRecord(e1, s);
             cudaMemsetAsync(c->enc_count, 0, 2 * sizeof(int32_t), s);
             if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
@@ -537,7 +579,7 @@ int batch_variant(genga_ctx *c, const PassArgs &a, const BatchBodies &bb, unsign
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->bt_key[slot] = key;
+    c->bt_key[slot] = fkey;
     c->bt_var[slot] = (int8_t)best;
     return best;
 }
@@ -564,17 +606,17 @@ cudaError_t run_kick_batched(genga_ctx *c, const genga_system &all, const int32_
     c->launches += 1;
     PassArgs a = base_args(c, all, p);
     a.npad = bb.npad_total;
-    const int variant = batch_variant(c, a, bb, key, s);
-    BatchItems bi;
-    int grid = 1;
-    if (!plan_batch(c, bb, variant, &bi, &grid)) return cudaErrorInvalidValue;
-    profile_before_pass(c, s);
-    e = launch_pass_batched(a, bb, bi, variant, grid, s);
-    profile_after_pass(c, s);
+    const int variant = batch_variant(c, a, bb, key, p.precision, s);
+    if (!launch_batched_variant(c, a, bb, key, variant, tau, acc, all, s, true, &e)) {
+        // no mutual plan now: the one-sided default, except where the caller
+        // asked for the group-centred form
+        if (p.precision == GENGA_FP32_BLOCKREL) return cudaErrorMemoryAllocation;
+        launch_batched_variant(c, a, bb, key, 0, tau, acc, all, s, true, &e);
+    }
     if (e != cudaSuccess) return e;
     c->enc_sorted = false;
     c->launches += 2;
-    return launch_combine_batched(bb, bi, c->partial, c->perm, tau, acc, all.vx, all.vy, all.vz, c->status, s);
+    return cudaSuccess;
 }
 
 // ------------------------------------------------------------ step graphs
@@ -984,7 +1026,7 @@ genga_status genga_kick_batched(genga_ctx *c, const genga_system *all, const int
     genga_status st;
     if ((st = check_system(c, all)) != GENGA_OK) return st;
     if ((st = check_params(p)) != GENGA_OK) return st;
-    if ((p->precision != GENGA_FP32 && p->precision != GENGA_FP32_HILO) || !is_fin(tau) ||
+    if (!is_fp32(p->precision) || !is_fin(tau) ||
         !check_offsets(c, all, offsets, D))
         return GENGA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
@@ -1000,7 +1042,7 @@ genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *
     genga_status st;
     if ((st = check_system(c, all)) != GENGA_OK) return st;
     if ((st = check_params(p)) != GENGA_OK) return st;
-    if ((p->precision != GENGA_FP32 && p->precision != GENGA_FP32_HILO) || nsteps < 0 ||
+    if (!is_fp32(p->precision) || nsteps < 0 ||
         !check_offsets(c, all, offsets, D))
         return GENGA_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
@@ -1032,7 +1074,15 @@ genga_status genga_step_batched(genga_ctx *c, genga_system *all, const int32_t *
         if (e != cudaSuccess) return status_of(e);
     }
     if (k < nsteps && graphs_usable(c)) {
-        const int variant = batch_variant(c, PassArgs{}, bb, layout, s, false);  // tuned by the steps above
+        PassArgs pa = base_args(c, a2, *p);
+        int variant = batch_variant(c, pa, bb, layout, p->precision, s, false);  // tuned by the steps above
+        if (is_mutual(variant)) {
+            MutualPlan mp;  // the plan is built outside the capture
+            if (!mutual_plan_batched(c, bb, layout, variant - num_fp32_variants(), s, &mp)) {
+                if (p->precision == GENGA_FP32_BLOCKREL) return GENGA_ERR_CUDA;
+                variant = 0;
+            }
+        }
         const unsigned long long key = step_key(a2, *p, variant, mix(layout, 0xba7c4ull));
         const bool ok = step_graph(c, key, [&](cudaStream_t q) {
             for (int b = 0; b < GENGA_REORDER_STEPS; b++) {
@@ -1060,13 +1110,14 @@ genga_status genga_batched_tuning(genga_ctx *c, const int32_t *offsets, int32_t 
                                   int32_t n) {
     if (!c || !offsets || !variant || D < 1 || D > GENGA_MAX_DISCS || n < 0 || (n > 0 && !ms))
         return GENGA_ERR_INVALID_ARG;
-    const unsigned long long key = offsets_hash(offsets, D);
+    // the entry of the autotuned mode (GENGA_FP32, family 0) for this layout
+    const unsigned long long key = offsets_hash(offsets, D) ^ 0x9e3779b97f4a7c15ull;
     *variant = -1;
     for (int q = 0; q < n; q++) ms[q] = 0.f;
     for (int k = 0; k < GENGA_BATCH_LAYOUTS; k++) {
         if (c->bt_var[k] < 0 || c->bt_key[k] != key) continue;
         *variant = c->bt_var[k];
-        for (int q = 0; q < n && q < GENGA_MAX_VARIANTS && q < num_fp32_variants(); q++) ms[q] = c->bt_ms[k][q];
+        for (int q = 0; q < n && q < GENGA_MAX_VARIANTS && q < num_all_variants(); q++) ms[q] = c->bt_ms[k][q];
     }
     return GENGA_OK;
 }

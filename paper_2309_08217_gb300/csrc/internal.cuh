@@ -57,26 +57,37 @@ struct Profile {                // CUDA event pairs around pass launches
 #define GENGA_BATCH_LAYOUTS 8  // batch layouts whose tuned FP32 variant a context remembers
 #define GENGA_MAX_VARIANTS 16  // FP32 pass variants the context records tuning times for
 #define GENGA_MAX_TIERS 8      // chunk-length tiers of an FP32 pass plan
-#define GENGA_MUTUAL_MAX_ITEMS 16384  // work items of one mutual FP32 pass plan
+#define GENGA_MUTUAL_MAX_ITEMS 65536  // work items of one mutual pass plan
 
 namespace genga {
-// Work plan of the mutual (symmetric) FP32 pass over one system of
-// `ngroups` 64-body groups, in i-blocks of gpb groups (i-tiles of NP groups,
-// one per consumer warp).  Pairs inside a block are evaluated one-sided by
-// its diagonal items: every warp takes its i-tile against a range of the
-// block's own groups (each ordered pair once, i-side only).  Pairs between
-// blocks are evaluated once, for both bodies, by the strip items of the
-// earlier block: chunks of the groups after it.  Item q of the table is
-// {block, first group, end group, i-row}: the partial row the item writes for
-// the block's bodies (each row 3 x npad double-float pairs): diagonal items
-// rows 0 .. cnt.x - 1, strip chunks rows S .. S + cnt.y - 1 (S = the most
-// diagonal items of any block); strip items of block b also write j-row
-// irows + b for the groups they cover.  A body of block B sums i-rows
-// [0, cnt.x), [S, S + cnt.y) and j-rows irows + [0, B).
+// Work plan of the mutual (symmetric) passes over one or more independent
+// systems (a batch), each a range of 64-body groups cut into i-blocks of gpb
+// groups (i-tiles of NP groups, one per consumer warp).  Pairs inside a block
+// are evaluated one-sided by its diagonal items: every warp takes its i-tile
+// against a range of the block's own groups (each ordered pair once, i-side
+// only).  Pairs between blocks of a system are evaluated once, for both
+// bodies, by the strip items of the earlier block: chunks of the system's
+// groups after it.  Item q of the table is {block, first group, end group,
+// i-row}: the partial row the item writes for the block's bodies (rows of a
+// system are 3 x np entries -- double-float pairs or doubles -- from its
+// pbase): diagonal items rows 0 .. cnt.x - 1, strip chunks rows
+// S .. S + cnt.y - 1 (S = the most diagonal items of any block of the
+// system); strip items of the system's block b also write j-row irows + b for
+// the groups they cover.  A body of the system's block b sums i-rows
+// [0, cnt.x), [S, S + cnt.y) and j-rows irows + [0, b).
+struct MSys {
+    int32_t poff, np;           // first packed position (a multiple of 64), packed length (its rows' length)
+    int32_t N, off;             // bodies, first caller index (perm[off + k] is packed position poff + k)
+    int32_t irows, S;           // first j-row, diagonal rows of its blocks
+    int32_t g1, blk0;           // end of its groups holding bodies (a global group index), its first block
+    long long pbase;            // first 8-byte entry of its partial rows
+};
 struct MutualPlan {
-    int32_t nb, gpb, ngroups, items, irows, S;
-    const int4 *item;           // [items] {block, first group, end group, i-row}
+    int32_t nb, gpb, items, nsys;
+    const int4 *item;           // [items] {block, first group, end group, i-row}: global blocks and groups
     const int2 *blk;            // [nb] {diagonal items, strip chunks} of each block
+    const int32_t *bsys;        // [nb] the system of each block
+    const MSys *sys;            // [nsys]
 };
 struct MutualCache;             // host plans per (N, variant), mutual.cu
 }  // namespace genga
@@ -338,6 +349,9 @@ int num_mutual_variants();
 void fp32_variant_shape(int variant, int *cw, int *bpt, int *ctas_per_sm);
 void mutual_variant_shape(int v, int *cw, int *bpt);
 bool mutual_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P);
+// the plan of FP32 mutual variant v over the systems of a batch (layout hash key)
+bool mutual_plan_batched(genga_ctx *c, const BatchBodies &bb, unsigned long long key, int v, cudaStream_t s,
+                         MutualPlan *P);
 // FP64 mutual pass (mutual.cu): FP64 pass variants 1 .. (variant 0 is the one-sided FP64 pass)
 int num_mutual64_variants();
 void fp64_pass_shape(int *warps, int *bpt);  // the one-sided FP64 pass (kick.cu)

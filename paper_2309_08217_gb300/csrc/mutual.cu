@@ -58,14 +58,18 @@
 
 namespace genga {
 
-struct MutualCache {            // host-built plans, one per FP32 variant slot
+struct MutualCache {            // host-built plans, one per variant slot
     struct Entry {
-        int N = -1, nb = 0, gpb = 0, ngroups = 0, items = 0, irows = 0, S = 0;
-        bool ok = false;  // false: no plan fits (for this N): one-sided passes instead
+        unsigned long long key = ~0ull;  // N (single systems) or the batch layout hash the plan is for
+        bool ok = false;  // false: no plan fits: one-sided passes instead
+        int nb = 0, gpb = 0, items = 0, nsys = 0;
         int4 *d_item = nullptr;
         int2 *d_blk = nullptr;
+        int32_t *d_bsys = nullptr;
+        MSys *d_sys = nullptr;
     };
-    Entry e[GENGA_MAX_VARIANTS];
+    Entry e[GENGA_MAX_VARIANTS];   // single systems: FP32 variants, then FP64 ones
+    Entry eb[GENGA_MAX_VARIANTS];  // batches: FP32 variants
 };
 
 namespace {
@@ -252,10 +256,10 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
     const MutualPlan &P = a.mp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t wlim = pass_wait_limit(a.wait_ns_log2);
-    const size_t np = (size_t)a.npad;
     float2 *rows = reinterpret_cast<float2 *>(a.partial);
 
     __shared__ unsigned s_lead;  // slots the leading consumer warp has finished
+    __shared__ MSys s_wsys[CW];  // the system of each consumer warp's current item
     if (tid == 0) {
         for (int q = 0; q < STAGES; q++) {
             mbar_init(&full[q], 1);
@@ -304,6 +308,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
 
     if (warp == CW + 1) {  // ------------------------------------------ reducer
         float2 *jrow = nullptr;    // NULL: a diagonal item (one-sided, no j-side sums)
+        int jnp = 0, jpoff = 0;    // the j-row's length and first packed position
         for (unsigned n = 0;; n++) {
             const int slot = n % STAGES;
             const uint32_t par = (n / STAGES) & 1;
@@ -313,7 +318,10 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
             if (!mbar_wait_bounded(&pdone[slot], par, a.status, wlim)) return;
             if (h.flags & 1) {
                 const int4 it = P.item[h.item];
-                jrow = it.w < P.S ? nullptr : rows + (size_t)(P.irows + it.x) * 3 * np;
+                const MSys sy = P.sys[P.bsys[it.x]];
+                jrow = it.w < sy.S ? nullptr : rows + sy.pbase + (size_t)(sy.irows + it.x - sy.blk0) * 3 * sy.np;
+                jnp = sy.np;
+                jpoff = sy.poff;
             }
             if (jrow) {
                 const float *sp = s_part + (size_t)slot * CW * 3 * MG;
@@ -325,7 +333,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                         DF t{0.f, 0.f};
 #pragma unroll
                         for (int w = 0; w < CW; w++) t = df_add(t, sp[(w * 3 + c) * MG + jj], 0.f);
-                        jrow[c * np + (size_t)h.group * MG + jj] = make_float2(t.hi, t.lo);
+                        jrow[(size_t)c * jnp + (h.group * MG + jj - jpoff)] = make_float2(t.hi, t.lo);
                     }
                 }
             }
@@ -355,11 +363,14 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
         if (h.flags & 1) {  // first slot of an item: this warp's i-tile
             const int4 it = P.item[h.item];
             row = it.w;
-            diag = row < P.S;
+            if (lane == 0) s_wsys[warp] = P.sys[P.bsys[it.x]];
+            __syncwarp();
+            const MSys &sy = s_wsys[warp];
+            diag = row < sy.S;
             // the warp's i-groups are interleaved over the block (gw, gw + CW,
             // ...), so a j-group next to one part of the block is near one
             // i-group of several warps rather than all of one warp's
-            const int gb0 = it.x * P.gpb, gb1 = min(gb0 + P.gpb, P.ngroups);
+            const int gb0 = sy.poff / MG + (it.x - sy.blk0) * P.gpb, gb1 = min(gb0 + P.gpb, sy.g1);
             gw = gb0 + warp;
             qin = 0u;
 #pragma unroll
@@ -608,7 +619,8 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                             double3 fi = make_double3(0.0, 0.0, 0.0), fj = fi;
                             if (kk >= 0) {
                                 const int i = (gw + (kk >> 1) * CW) * MG + 32 * (kk & 1) + lane, j = g * MG + sb * 32 + jj;
-                                screened_pair_mutual(a, i, j, 0, a.N, 0, BOTH, &fi, &fj);
+                                const MSys &sy = s_wsys[warp];
+                                screened_pair_mutual(a, i, j, sy.poff, sy.N, sy.off, BOTH, &fi, &fj);
                                 const double f3[3] = {fi.x, fi.y, fi.z};
 #pragma unroll
                                 for (int c = 0; c < 3; c++) {
@@ -676,15 +688,16 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                 nf = 0;
             }
             if (h.flags & 2) {  // last slot of the item: its i-row
-                float2 *out = rows + (size_t)row * 3 * np;
+                const MSys &sy = s_wsys[warp];
+                float2 *out = rows + sy.pbase + (size_t)row * 3 * sy.np;
 #pragma unroll
                 for (int k = 0; k < BPT; k++) {
                     if (!((qin >> (k >> 1)) & 1u)) continue;
-                    const size_t i = (size_t)(gw + (k >> 1) * CW) * MG + 32 * (k & 1) + lane;
+                    const size_t i = (size_t)((gw + (k >> 1) * CW) * MG + 32 * (k & 1) + lane - sy.poff);
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
                         const DF t = acc[(c * BPT + k) * NC];
-                        out[c * np + i] = make_float2(t.hi, t.lo);
+                        out[(size_t)c * sy.np + i] = make_float2(t.hi, t.lo);
                     }
                 }
             }
@@ -692,25 +705,39 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
     }
 }
 
+// The system of packed position p (the largest whose first position is <= p).
+__device__ __forceinline__ int plan_system(const MutualPlan &P, int p) {
+    int lo = 0, hi = P.nsys - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.sys[mid].poff <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // One thread per (two consecutive bodies, component): the bodies' i-rows
 // then their j-rows, in row order, in double-float; then the optional acc
-// output and v += acc tau.  Two bodies per thread make every row load 16
-// bytes per lane (512 contiguous bytes per warp): the rows are ~1 MB apart,
-// and 8-byte lanes left DRAM at ~40 % of its rate.  Both bodies are in the
-// same i-block (blocks are whole 64-body groups), so they share the rows.
+// output and v += acc tau (acc[c * Ntot + body], body = perm[off + k]).  Two
+// bodies per thread make every row load 16 bytes per lane (512 contiguous
+// bytes per warp).  Both bodies are in the same i-block (blocks are whole
+// 64-body groups of one system), so they share the rows.
 __global__ void combine_mutual_kernel(const double *__restrict__ partial, const __grid_constant__ MutualPlan P,
-                                      int N, int npad, const uint32_t *__restrict__ perm, double tau,
+                                      int Ntot, int npad, const uint32_t *__restrict__ perm, double tau,
                                       double *__restrict__ acc, double *__restrict__ vx, double *__restrict__ vy,
                                       double *__restrict__ vz, uint32_t *__restrict__ status) {
-    const int k = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int p = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int c = blockIdx.y;
-    if (k >= N) return;
-    const int b = k / (P.gpb * MG);
-    const size_t stride = 3 * (size_t)npad / 2;  // float4 units (two float2 entries)
-    const float4 *p = reinterpret_cast<const float4 *>(partial) + ((size_t)c * npad + k) / 2;
-    const int2 bk = P.blk[b];
-    // the rows in order: diagonal i-rows, strip i-rows, j-rows of the blocks before b
-    const int n0 = bk.x, n1 = n0 + bk.y, n2 = n1 + b;
+    if (p >= npad) return;
+    const MSys sy = P.sys[plan_system(P, p)];
+    const int k = p - sy.poff;
+    if (k >= sy.N) return;
+    const int bl = (k / MG) / P.gpb;  // block within the system
+    const size_t stride = 3 * (size_t)sy.np / 2;  // float4 units (two float2 entries)
+    const float4 *pr = reinterpret_cast<const float4 *>(partial + sy.pbase) + ((size_t)c * sy.np + k) / 2;
+    const int2 bk = P.blk[sy.blk0 + bl];
+    // the rows in order: diagonal i-rows, strip i-rows, j-rows of the system's blocks before bl
+    const int n0 = bk.x, n1 = n0 + bk.y, n2 = n1 + bl;
     DF t0{0.f, 0.f}, t1{0.f, 0.f};
     constexpr int BATCH = 16;
     for (int r0 = 0; r0 < n2; r0 += BATCH) {
@@ -718,8 +745,8 @@ __global__ void combine_mutual_kernel(const double *__restrict__ partial, const 
 #pragma unroll
         for (int u = 0; u < BATCH; u++) {
             const int r = r0 + u;
-            const int rr = r < n0 ? r : r < n1 ? P.S + (r - n0) : P.irows + (r - n1);
-            v[u] = r < n2 ? p[(size_t)rr * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int rr = r < n0 ? r : r < n1 ? sy.S + (r - n0) : sy.irows + (r - n1);
+            v[u] = r < n2 ? pr[(size_t)rr * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < BATCH; u++)
@@ -730,12 +757,12 @@ __global__ void combine_mutual_kernel(const double *__restrict__ partial, const 
     }
 #pragma unroll
     for (int h = 0; h < 2; h++) {
-        if (k + h >= N) break;
+        if (k + h >= sy.N) break;
         const DF &t = h ? t1 : t0;
         const double s = (double)t.hi + (double)t.lo;
         if (!isfinite(s)) atomicOr(status, GENGA_BIT(GENGA_ERR_NONFINITE));
-        const int i = (int)perm[k + h];
-        if (acc) acc[c * (size_t)N + i] = s;
+        const int i = (int)perm[sy.off + k + h];
+        if (acc) acc[c * (size_t)Ntot + i] = s;
         if (tau != 0.0) {
             double *v = c == 0 ? vx : (c == 1 ? vy : vz);
             v[i] += s * tau;
@@ -798,10 +825,10 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
     const MutualPlan &P = a.mp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t wlim = pass_wait_limit(a.wait_ns_log2);
-    const size_t np = (size_t)a.npad;
     double *rows = a.partial;
 
     __shared__ unsigned s_lead;  // slots the leading consumer warp has finished
+    __shared__ MSys s_wsys[CW];  // the system of each consumer warp's current item
     if (tid == 0) {
         for (int q = 0; q < STAGES; q++) {
             mbar_init(&full[q], 1);
@@ -848,6 +875,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
 
     if (warp == CW + 1) {  // ------------------------------------------ reducer
         double *jrow = nullptr;
+        int jnp = 0, jpoff = 0;
         for (unsigned n = 0;; n++) {
             const int slot = n % STAGES;
             const uint32_t par = (n / STAGES) & 1;
@@ -857,7 +885,10 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
             if (!mbar_wait_bounded(&pdone[slot], par, a.status, wlim)) return;
             if (h.flags & 1) {
                 const int4 it = P.item[h.item];
-                jrow = it.w < P.S ? nullptr : rows + (size_t)(P.irows + it.x) * 3 * np;
+                const MSys sy = P.sys[P.bsys[it.x]];
+                jrow = it.w < sy.S ? nullptr : rows + sy.pbase + (size_t)(sy.irows + it.x - sy.blk0) * 3 * sy.np;
+                jnp = sy.np;
+                jpoff = sy.poff;
             }
             if (jrow) {
                 const double *sp = s_part + (size_t)slot * CW * 3 * MG;
@@ -869,7 +900,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
                         CompS t{0.0, 0.0};
 #pragma unroll
                         for (int w = 0; w < CW; w++) comp_add(t, sp[(w * 3 + c) * MG + jj]);
-                        jrow[c * np + (size_t)h.group * MG + jj] = t.s + t.c;
+                        jrow[(size_t)c * jnp + (h.group * MG + jj - jpoff)] = t.s + t.c;
                     }
                 }
             }
@@ -898,8 +929,11 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
         if (h.flags & 1) {  // first slot of an item: this warp's i-bodies (groups gw + q CW)
             const int4 it = P.item[h.item];
             row = it.w;
-            diag = row < P.S;
-            const int gb0 = it.x * P.gpb, gb1 = min(gb0 + P.gpb, P.ngroups);
+            if (lane == 0) s_wsys[warp] = P.sys[P.bsys[it.x]];
+            __syncwarp();
+            const MSys &sy = s_wsys[warp];
+            diag = row < sy.S;
+            const int gb0 = sy.poff / MG + (it.x - sy.blk0) * P.gpb, gb1 = min(gb0 + P.gpb, sy.g1);
             gw = gb0 + warp;
             qin = 0u;
 #pragma unroll
@@ -1025,7 +1059,8 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
                         double3 fi = make_double3(0.0, 0.0, 0.0), fj = fi;
                         if (kk >= 0) {
                             const int i = (gw + (kk >> 1) * CW) * MG + 32 * (kk & 1) + lane, j = g * MG + sb * 32 + jj;
-                            screened_pair_mutual(a, i, j, 0, a.N, 0, both, &fi, &fj);
+                            const MSys &sy = s_wsys[warp];
+                            screened_pair_mutual(a, i, j, sy.poff, sy.N, sy.off, both, &fi, &fj);
                             comp_add(acc[(0 * BPT + kk) * NC], fi.x);
                             comp_add(acc[(1 * BPT + kk) * NC], fi.y);
                             comp_add(acc[(2 * BPT + kk) * NC], fi.z);
@@ -1064,15 +1099,16 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
             atomicMax(&s_lead, n + 1);
         }
         if (in && (h.flags & 2)) {  // last slot of the item: its i-row
-            double *out = rows + (size_t)row * 3 * np;
+            const MSys &sy = s_wsys[warp];
+            double *out = rows + sy.pbase + (size_t)row * 3 * sy.np;
 #pragma unroll
             for (int k = 0; k < BPT; k++) {
                 if (!((qin >> (k >> 1)) & 1u)) continue;
-                const size_t i = (size_t)(gw + (k >> 1) * CW) * MG + 32 * (k & 1) + lane;
+                const size_t i = (size_t)((gw + (k >> 1) * CW) * MG + 32 * (k & 1) + lane - sy.poff);
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
                     const CompS t = acc[(c * BPT + k) * NC];
-                    out[c * np + i] = t.s + t.c;
+                    out[(size_t)c * sy.np + i] = t.s + t.c;
                 }
             }
         }
@@ -1083,17 +1119,20 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
 // mutual FP64 pass in the order of combine_mutual_kernel (16-byte loads, as
 // there), Neumaier-compensated.
 __global__ void combine_mutual64_kernel(const double *__restrict__ partial, const __grid_constant__ MutualPlan P,
-                                        int N, int npad, const uint32_t *__restrict__ perm, double tau,
+                                        int Ntot, int npad, const uint32_t *__restrict__ perm, double tau,
                                         double *__restrict__ acc, double *__restrict__ vx, double *__restrict__ vy,
                                         double *__restrict__ vz, uint32_t *__restrict__ status) {
-    const int k = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int p = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int c = blockIdx.y;
-    if (k >= N) return;
-    const int b = k / (P.gpb * MG);
-    const size_t stride = 3 * (size_t)npad / 2;  // double2 units
-    const double2 *p = reinterpret_cast<const double2 *>(partial) + ((size_t)c * npad + k) / 2;
-    const int2 bk = P.blk[b];
-    const int n0 = bk.x, n1 = n0 + bk.y, n2 = n1 + b;
+    if (p >= npad) return;
+    const MSys sy = P.sys[plan_system(P, p)];
+    const int k = p - sy.poff;
+    if (k >= sy.N) return;
+    const int bl = (k / MG) / P.gpb;
+    const size_t stride = 3 * (size_t)sy.np / 2;  // double2 units
+    const double2 *pr = reinterpret_cast<const double2 *>(partial + sy.pbase) + ((size_t)c * sy.np + k) / 2;
+    const int2 bk = P.blk[sy.blk0 + bl];
+    const int n0 = bk.x, n1 = n0 + bk.y, n2 = n1 + bl;
     CompS t0{0.0, 0.0}, t1{0.0, 0.0};
     constexpr int BATCH = 16;
     for (int r0 = 0; r0 < n2; r0 += BATCH) {
@@ -1101,8 +1140,8 @@ __global__ void combine_mutual64_kernel(const double *__restrict__ partial, cons
 #pragma unroll
         for (int u = 0; u < BATCH; u++) {
             const int r = r0 + u;
-            const int rr = r < n0 ? r : r < n1 ? P.S + (r - n0) : P.irows + (r - n1);
-            v[u] = r < n2 ? p[(size_t)rr * stride] : make_double2(0.0, 0.0);
+            const int rr = r < n0 ? r : r < n1 ? sy.S + (r - n0) : sy.irows + (r - n1);
+            v[u] = r < n2 ? pr[(size_t)rr * stride] : make_double2(0.0, 0.0);
         }
 #pragma unroll
         for (int u = 0; u < BATCH; u++)
@@ -1113,12 +1152,12 @@ __global__ void combine_mutual64_kernel(const double *__restrict__ partial, cons
     }
 #pragma unroll
     for (int h = 0; h < 2; h++) {
-        if (k + h >= N) break;
+        if (k + h >= sy.N) break;
         const CompS &t = h ? t1 : t0;
         const double s = t.s + t.c;
         if (!isfinite(s)) atomicOr(status, GENGA_BIT(GENGA_ERR_NONFINITE));
-        const int i = (int)perm[k + h];
-        if (acc) acc[c * (size_t)N + i] = s;
+        const int i = (int)perm[sy.off + k + h];
+        if (acc) acc[c * (size_t)Ntot + i] = s;
         if (tau != 0.0) {
             double *v = c == 0 ? vx : (c == 1 ? vy : vz);
             v[i] += s * tau;
@@ -1239,20 +1278,46 @@ double makespan(const std::vector<Chunk> &items, int C) {
     return worst;
 }
 
-// The plan with the best estimated makespan (plus a small cost per partial
-// row, which the combine reads) over the diagonal split, the chunks per strip
-// and the tail (single groups, a few per CTA in all).
-void plan_items(int npad, int cw, int NPg, int ctas, int max_rows, std::vector<int4> *best_items,
-                std::vector<int2> *best_blk, int *best_S) {
-    const int ngroups = npad / MG, gpb = cw * NPg, nb = (ngroups + gpb - 1) / gpb;
-    const int nstrips = std::max(1, nb - 1);
-    std::vector<Chunk> items;
+// A system as the planner sees it: packed range [poff, poff + np), N bodies,
+// caller indices from off.
+struct HSys {
+    int poff, np, N, off;
+};
+
+struct PlanOut {
+    std::vector<int4> item;
+    std::vector<int2> blk;
+    std::vector<int32_t> bsys;
+    std::vector<MSys> sys;
+    size_t row_entries = 0;  // 8-byte entries of all partial rows
+};
+
+// The plan with the best estimated makespan over all systems' items (plus a
+// small cost per partial row a body reads in the combine) over the diagonal
+// split, the chunks per strip and the tail (single groups, a few per CTA in
+// all); each system's rows at most max_rows.  out->item is empty when no
+// plan fits.
+void plan_systems(const std::vector<HSys> &hs, int cw, int NPg, int ctas, int max_rows, PlanOut *out) {
+    const int gpb = cw * NPg;
+    const int ns = (int)hs.size();
+    std::vector<int> G(ns), nbs(ns);
+    int nstrips = 0;
+    long long npos = 0;
+    for (int d = 0; d < ns; d++) {
+        G[d] = (hs[d].N + MG - 1) / MG;
+        nbs[d] = (G[d] + gpb - 1) / gpb;
+        nstrips += std::max(0, nbs[d] - 1);
+        npos += hs[d].np;
+    }
+    nstrips = std::max(1, nstrips);
+    std::vector<Chunk> items, all;
     std::vector<int2> blk;
     int S = 0;
-    double best = 1e300;
     double total = 0.0;
-    build_items(ngroups, gpb, 1, 1, 1, NPg, 2 * gpb, 0, &items, &blk, &S);
-    for (const Chunk &c : items) total += c.cost;
+    for (int d = 0; d < ns; d++) {
+        build_items(G[d], gpb, 1, 1, 1, NPg, 2 * gpb, 0, &items, &blk, &S);
+        for (const Chunk &c : items) total += c.cost;
+    }
     const double per = total / ctas;
     // two families: fixed chunk lengths (fractions of a CTA's share) and a
     // fixed number of chunks per strip
@@ -1262,26 +1327,66 @@ void plan_items(int npad, int cw, int NPg, int ctas, int max_rows, std::vector<i
     std::vector<Shape> shapes;
     for (int R : {16, 24, 32, 48, 64}) shapes.push_back(Shape{R, 0});
     for (double f : {0.06, 0.09, 0.12, 0.18, 0.25}) shapes.push_back(Shape{0, std::max(1, (int)std::lround(per * f))});
+    double best = 1e300;
+    out->item.clear();
+    PlanOut cand;
     for (int D : {2, 4, 8, 12}) {
         for (const Shape &sh : shapes) {
             for (int tau : {2, 4, 6}) {
                 const int T = (tau * ctas + nstrips - 1) / nstrips;
-                build_items(ngroups, gpb, D, sh.R, sh.Lm, NPg, 2 * gpb, T, &items, &blk, &S);
-                if ((int)items.size() > GENGA_MUTUAL_MAX_ITEMS) continue;
-                int maxr = 0;
-                for (const int2 &b : blk) maxr = std::max(maxr, S + b.y);
-                if (maxr + nb > max_rows) continue;  // the partial rows must fit the workspace
-                const double score = makespan(items, ctas) + 0.01 * (maxr + nb);
+                all.clear();
+                cand.blk.clear();
+                cand.bsys.clear();
+                cand.sys.clear();
+                bool fits = true;
+                int blk0 = 0;
+                double rows_read = 0.0;  // partial rows per packed position, on average
+                for (int d = 0; d < ns && fits; d++) {
+                    if (G[d] == 0) continue;
+                    build_items(G[d], gpb, D, sh.R, sh.Lm, NPg, 2 * gpb, T, &items, &blk, &S);
+                    int irows = 0;
+                    for (const int2 &b : blk) irows = std::max(irows, S + b.y);
+                    const int rows = irows + (int)blk.size();
+                    if (rows > max_rows) fits = false;
+                    const int g0 = hs[d].poff / MG, sd = (int)cand.sys.size();
+                    for (Chunk c : items) {
+                        c.item.x += blk0;
+                        c.item.y += g0;
+                        c.item.z += g0;
+                        all.push_back(c);
+                    }
+                    for (const int2 &b : blk) {
+                        cand.blk.push_back(b);
+                        cand.bsys.push_back(sd);
+                    }
+                    cand.sys.push_back(MSys{hs[d].poff, hs[d].np, hs[d].N, hs[d].off, irows, S, g0 + G[d], blk0, 0});
+                    blk0 += (int)blk.size();
+                    rows_read += (double)rows * hs[d].np / (double)npos;
+                }
+                if (!fits || (int)all.size() > GENGA_MUTUAL_MAX_ITEMS) continue;
+                std::stable_sort(all.begin(), all.end(), [](const Chunk &x, const Chunk &y) {
+                    return x.tail != y.tail ? y.tail : x.cost > y.cost;
+                });
+                const double score = makespan(all, ctas) + 0.01 * rows_read;
                 if (score < best) {
                     best = score;
-                    best_items->clear();
-                    for (const Chunk &c : items) best_items->push_back(c.item);
-                    *best_blk = blk;
-                    *best_S = S;
+                    out->item.clear();
+                    for (const Chunk &c : all) out->item.push_back(c.item);
+                    out->blk = cand.blk;
+                    out->bsys = cand.bsys;
+                    out->sys = cand.sys;
                 }
             }
         }
     }
+    size_t pb = 0;  // each system's rows (irows + its blocks) after the previous systems'
+    for (size_t q = 0; q < out->sys.size(); q++) {
+        MSys &y = out->sys[q];
+        const int nb = (q + 1 < out->sys.size() ? out->sys[q + 1].blk0 : (int)out->blk.size()) - y.blk0;
+        y.pbase = (long long)pb;
+        pb += (size_t)(y.irows + nb) * 3 * (size_t)y.np;
+    }
+    out->row_entries = pb;
 }
 
 }  // namespace
@@ -1299,46 +1404,38 @@ void mutual_variant_shape(int v, int *cw, int *bpt) {
 
 void free_mutual_cache(genga_ctx *c) {
     if (!c->mcache) return;
-    for (auto &e : c->mcache->e) {
-        if (e.d_item) cudaFree(e.d_item);
-        if (e.d_blk) cudaFree(e.d_blk);
-    }
+    for (MutualCache::Entry *t : {c->mcache->e, c->mcache->eb})
+        for (int q = 0; q < GENGA_MAX_VARIANTS; q++) {
+            MutualCache::Entry &e = t[q];
+            if (e.d_item) cudaFree(e.d_item);
+            if (e.d_blk) cudaFree(e.d_blk);
+            if (e.d_bsys) cudaFree(e.d_bsys);
+            if (e.d_sys) cudaFree(e.d_sys);
+        }
     delete c->mcache;
     c->mcache = nullptr;
 }
 
-// The plan for N bodies of the variant in cache slot v (cw consumer warps of
-// npg groups each), built (and uploaded) on first use.  Returns false when it must be built while `s` is being captured, or
-// when it does not fit the partial rows: the caller then uses a one-sided
-// variant.
-static bool plan_for_shape(genga_ctx *c, int N, int v, int cw, int npg, cudaStream_t s, MutualPlan *P) {
-    if (v < 0 || v >= GENGA_MAX_VARIANTS) return false;
-    if (!c->mcache) {
-        c->mcache = new (std::nothrow) MutualCache();
-        if (!c->mcache) return false;
-    }
-    MutualCache::Entry &e = c->mcache->e[v];
-    const int npad = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
-    if (e.N != N) {
+// The plan of cache entry e for `key` (the systems hs, cw consumer warps of
+// npg groups each), built and uploaded on first use.  Returns false when it
+// must be built while `s` is being captured, or when no plan fits: the caller
+// then uses a one-sided variant.
+static bool plan_cached(genga_ctx *c, MutualCache::Entry &e, unsigned long long key, const std::vector<HSys> &hs,
+                        int cw, int npg, cudaStream_t s, MutualPlan *P) {
+    if (e.key != key) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
-        std::vector<int4> items;
-        std::vector<int2> blk;
-        int S = 0;
-        // partial rows: up to MUTUAL_MAX_ROWS (the workspace grows to the plan's need)
-        const int max_rows = std::max((int)std::min<size_t>(c->partial_cap / (3 * (size_t)npad), 1 << 20),
-                                      MUTUAL_MAX_ROWS);
-        plan_items(npad, cw, npg, c->sm_count, max_rows, &items, &blk, &S);
+        PlanOut po;
+        plan_systems(hs, cw, npg, c->sm_count, MUTUAL_MAX_ROWS, &po);
         if (cudaStreamSynchronize(s) != cudaSuccess) return false;  // the old tables may be in use
         if (e.d_item) cudaFree(e.d_item);
         if (e.d_blk) cudaFree(e.d_blk);
+        if (e.d_bsys) cudaFree(e.d_bsys);
+        if (e.d_sys) cudaFree(e.d_sys);
         e = MutualCache::Entry{};
-        e.N = N;  // remembered also when no plan fits, so that it is not searched again
-        if (items.empty()) return false;
-        int irows = 0;
-        for (const int2 &b : blk) irows = std::max(irows, S + b.y);
-        const int nb = (int)blk.size();
-        const size_t need = (size_t)(irows + nb) * 3 * npad;
+        e.key = key;  // remembered also when no plan fits, so that it is not searched again
+        if (po.item.empty() || po.sys.empty()) return false;
+        const size_t need = po.row_entries;
         if (need > c->partial_cap) {  // a larger workspace for the rows; captured step graphs used the old one
             double *bigger = nullptr;
             if (cudaMalloc(&bigger, need * sizeof(double)) != cudaSuccess) {
@@ -1353,32 +1450,57 @@ static bool plan_for_shape(genga_ctx *c, int N, int v, int cw, int npg, cudaStre
                 c->step_exec = nullptr;
             }
         }
-        if (cudaMalloc(&e.d_item, items.size() * sizeof(int4)) != cudaSuccess) return false;
-        if (cudaMalloc(&e.d_blk, blk.size() * sizeof(int2)) != cudaSuccess) return false;
-        if (cudaMemcpy(e.d_item, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(e.d_blk, blk.data(), blk.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMalloc(&e.d_item, po.item.size() * sizeof(int4)) != cudaSuccess ||
+            cudaMalloc(&e.d_blk, po.blk.size() * sizeof(int2)) != cudaSuccess ||
+            cudaMalloc(&e.d_bsys, po.bsys.size() * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&e.d_sys, po.sys.size() * sizeof(MSys)) != cudaSuccess)
             return false;
-        e.nb = nb;
+        if (cudaMemcpy(e.d_item, po.item.data(), po.item.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(e.d_blk, po.blk.data(), po.blk.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(e.d_bsys, po.bsys.data(), po.bsys.size() * sizeof(int32_t), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(e.d_sys, po.sys.data(), po.sys.size() * sizeof(MSys), cudaMemcpyHostToDevice) != cudaSuccess)
+            return false;
+        e.nb = (int)po.blk.size();
         e.gpb = cw * npg;
-        e.ngroups = npad / MG;
-        e.items = (int)items.size();
-        e.irows = irows;
-        e.S = S;
+        e.items = (int)po.item.size();
+        e.nsys = (int)po.sys.size();
         e.ok = true;
     }
     if (!e.ok) return false;
-    *P = MutualPlan{e.nb, e.gpb, e.ngroups, e.items, e.irows, e.S, e.d_item, e.d_blk};
+    *P = MutualPlan{e.nb, e.gpb, e.items, e.nsys, e.d_item, e.d_blk, e.d_bsys, e.d_sys};
     return true;
 }
 
+static MutualCache *cache_of(genga_ctx *c) {
+    if (!c->mcache) c->mcache = new (std::nothrow) MutualCache();
+    return c->mcache;
+}
+
 bool mutual_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P) {
-    if (v < 0 || v >= kNumMVariants) return false;
-    return plan_for_shape(c, N, v, kMVariants[v].cw, kMVariants[v].np, s, P);
+    if (v < 0 || v >= kNumMVariants || !cache_of(c)) return false;
+    const int npad = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
+    return plan_cached(c, c->mcache->e[v], (unsigned long long)N, {HSys{0, npad, N, 0}}, kMVariants[v].cw,
+                       kMVariants[v].np, s, P);
 }
 
 bool mutual64_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P) {
-    if (v < 0 || v >= kNumM64Variants) return false;
-    return plan_for_shape(c, N, kNumMVariants + v, kM64Variants[v].cw, kM64Variants[v].bpt / 2, s, P);
+    if (v < 0 || v >= kNumM64Variants || !cache_of(c)) return false;
+    const int npad = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
+    return plan_cached(c, c->mcache->e[kNumMVariants + v], (unsigned long long)N, {HSys{0, npad, N, 0}},
+                       kM64Variants[v].cw, kM64Variants[v].bpt / 2, s, P);
+}
+
+bool mutual_plan_batched(genga_ctx *c, const BatchBodies &bb, unsigned long long key, int v, cudaStream_t s,
+                         MutualPlan *P) {
+    if (v < 0 || v >= kNumMVariants || !cache_of(c)) return false;
+    std::vector<HSys> hs;
+    for (int d = 0; d < bb.D; d++) {
+        const int n = bb.off[d + 1] - bb.off[d];
+        if (n > 0) hs.push_back(HSys{bb.poff[d], bb.poff[d + 1] - bb.poff[d], n, bb.off[d]});
+    }
+    if (hs.empty()) return false;
+    return plan_cached(c, c->mcache->eb[v], key, hs, kMVariants[v].cw, kMVariants[v].np, s, P);
 }
 
 cudaError_t init_mutual_kernels() {
@@ -1409,8 +1531,8 @@ cudaError_t launch_combine_mutual64(const double *partial, const MutualPlan &P, 
                                     double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
                                     cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    combine_mutual64_kernel<<<dim3(((N + 1) / 2 + 255) / 256, 3), 256, 0, s>>>(partial, P, N, npad, perm, tau, acc,
-                                                                                vx, vy, vz, status);
+    combine_mutual64_kernel<<<dim3((npad / 2 + 255) / 256, 3), 256, 0, s>>>(partial, P, N, npad, perm, tau, acc, vx,
+                                                                             vy, vz, status);
     return cudaGetLastError();
 }
 
@@ -1428,8 +1550,8 @@ cudaError_t launch_combine_mutual(const double *partial, const MutualPlan &P, in
                                   double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
                                   cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    combine_mutual_kernel<<<dim3(((N + 1) / 2 + 255) / 256, 3), 256, 0, s>>>(partial, P, N, npad, perm, tau, acc, vx,
-                                                                              vy, vz, status);
+    combine_mutual_kernel<<<dim3((npad / 2 + 255) / 256, 3), 256, 0, s>>>(partial, P, N, npad, perm, tau, acc, vx,
+                                                                           vy, vz, status);
     return cudaGetLastError();
 }
 

@@ -105,16 +105,53 @@ def test_blockrel_steps(genga):
     c.close()
 
 
-def test_blockrel_refuses_tp2_and_batched(genga):
-    import torch
+def test_blockrel_refuses_tp2(genga):
     d = planted_disc(3000, 46)
     c = genga.Context(2 * d.N)
     s = genga.DeviceSystem.from_disc(d)
     with pytest.raises(genga.GengaError):
         genga.genga_kick(c, s, _params(genga, d, genga.GENGA_FP32_BLOCKREL, n_big=5), 0.0, None)
-    off = torch.tensor([0, d.N], dtype=torch.int32)
+    off = [0, d.N]
     with pytest.raises(genga.GengaError):
-        genga.genga_kick_batched(c, s, off.numpy(), _params(genga, d, genga.GENGA_FP32_BLOCKREL), 0.0, None)
-    genga.genga_kick_batched(c, s, off.numpy(), _params(genga, d, genga.GENGA_FP32_HILO), 0.0, None)
+        genga.genga_kick_batched(c, s, off, _params(genga, d, genga.GENGA_FP32_BLOCKREL, n_big=5), 0.0, None)
+    c.close()
+
+
+@pytest.mark.parametrize("mode", ["GENGA_FP32_HILO", "GENGA_FP32_BLOCKREL", "GENGA_FP32"])
+def test_modes_in_batched_mode(genga, mode):
+    """Each FP32 mode in batched mode (the mutual pass over the systems of a
+    batch for BLOCKREL): every system against the oracle run on it alone,
+    kick and encounter list with global indices."""
+    import torch
+    sizes = [7000, 1, 0, 3001, 12000, 64, 2500]
+    parts = [planted_disc(n, 300 + k) if n > 0 else None for k, n in enumerate(sizes)]
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    arrays = [np.concatenate([q.arrays()[comp] for q in parts if q is not None]) for comp in range(7)]
+    NT = int(offsets[-1])
+    c = genga.Context(NT + 8 * 1024)
+    s = genga.DeviceSystem.from_arrays(arrays)
+    p = _params(genga, parts[0], getattr(genga, mode))
+    acc = torch.zeros(3 * NT, dtype=torch.float64, device="cuda")
+    genga.genga_kick_batched(c, s, offsets, p, 0.0, acc)
     assert genga.genga_get_status(c) == genga.GENGA_OK
+    cap = 4 * NT
+    pairs = torch.zeros(2 * cap, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    genga.genga_last_encounters(c, pairs, cap, cnt)
+    got_pairs = set(map(tuple, pairs[: 2 * int(cnt.item())].view(-1, 2).cpu().numpy().tolist()))
+    got = acc.view(3, NT).cpu().numpy()
+    want, band_all = set(), set()
+    for k, d in enumerate(parts):
+        if d is None or d.N < 2:
+            continue
+        arr = oracle.disc_arrays(d)
+        a, rc = oracle.rcrit(*arr, G=d.G, Mstar=d.Mstar, dt=d.dt, n1=3.0, n2=0.4)
+        ref = oracle.kick_acc(arr[0], arr[1], arr[2], arr[6], a, rc, d.G, d.Mstar, 3.0, 1, 0)
+        err = _rel(got[:, offsets[k]:offsets[k + 1]], ref)
+        assert err.max() <= TOL32, f"{mode} system {k}: {err.max():.3e}"
+        pr, band = oracle.encounters(arr[0], arr[1], arr[2], arr[6], a, rc, 3.0, d.Mstar, 1, band=1e-9)
+        o = int(offsets[k])
+        want |= {(int(i) + o, int(j) + o) for i, j in pr}
+        band_all |= {(int(i) + o, int(j) + o) for i, j in band}
+    assert got_pairs - band_all == want - band_all
     c.close()
