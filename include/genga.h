@@ -68,8 +68,8 @@ typedef enum {
  *                        group; closer than a tenth of the group's half-diagonal (or the
  *                        r_crit bound) the rounding residuals x - c - X are added back.
  *                        The mutual pass: each unordered pair once, its terms added to
- *                        both bodies.  Not with test-particle mode 2 (n_big >= 0) nor in
- *                        batched mode: GENGA_ERR_INVALID_ARG.
+ *                        both bodies.  Not with test-particle mode 2 (n_big >= 0):
+ *                        GENGA_ERR_INVALID_ARG.
  *   GENGA_FP32           either FP32 form, whichever the autotuner finds faster for the
  *                        size bucket (genga_measure.h).
  * In every FP32 mode: r^2, rsqrt (SFU) and the pair terms in FP32, per-body sums in
@@ -238,8 +238,10 @@ genga_status genga_step(genga_ctx *ctx, genga_system *sys, const genga_params *p
  *   offsets  HOST int32 [D+1], offsets[0] = 0, non-decreasing, offsets[D] = all->N
  *   D        1 .. GENGA_MAX_BATCH (256)
  * The context's max_N must cover the padded total sum_d roundup(N_d, 1024).
- * params->precision must be GENGA_FP32 or GENGA_FP32_HILO (the batched pass is the
- * one-sided FP32 kick).
+ * params->precision must be one of the FP32 modes (the batched pass is the FP32
+ * kick: one-sided for GENGA_FP32_HILO, mutual over each system's pairs for
+ * GENGA_FP32_BLOCKREL, the faster of the two -- tuned per batch layout -- for
+ * GENGA_FP32).
  * genga_kick_batched: the kick of every system (acc layout acc[c*all->N + i],
  * or NULL), the encounter list of every system with indices into `all`.
  * genga_step_batched: nsteps level-0 steps of every system.
