@@ -84,6 +84,7 @@ struct MSys {
 };
 struct MutualPlan {
     int32_t nb, gpb, items, nsys;
+    int32_t nreal;              // > 0: the bodies of system 0 (a single-system plan, built for the padded length)
     const int4 *item;           // [items] {block, first group, end group, i-row}: global blocks and groups
     const int2 *blk;            // [nb] {diagonal items, strip chunks} of each block
     const int32_t *bsys;        // [nb] the system of each block

@@ -58,9 +58,13 @@
 
 namespace genga {
 
-struct MutualCache {            // host-built plans, one per variant slot
+constexpr int MC_WAYS = 16;        // single-system plans kept per variant (one per padded length)
+constexpr int MC_BATCH_WAYS = 4;   // batch plans kept per variant (one per batch layout)
+
+struct MutualCache {            // host-built plans per variant slot
     struct Entry {
-        unsigned long long key = ~0ull;  // N (single systems) or the batch layout hash the plan is for
+        unsigned long long key = ~0ull;  // the padded length (single systems) or the batch layout hash
+        unsigned long long used = 0;     // last use (the least recently used entry is replaced)
         bool ok = false;  // false: no plan fits: one-sided passes instead
         int nb = 0, gpb = 0, items = 0, nsys = 0;
         int4 *d_item = nullptr;
@@ -68,8 +72,9 @@ struct MutualCache {            // host-built plans, one per variant slot
         int32_t *d_bsys = nullptr;
         MSys *d_sys = nullptr;
     };
-    Entry e[GENGA_MAX_VARIANTS];   // single systems: FP32 variants, then FP64 ones
-    Entry eb[GENGA_MAX_VARIANTS];  // batches: FP32 variants
+    Entry e[GENGA_MAX_VARIANTS][MC_WAYS];         // single systems: FP32 variants, then FP64 ones
+    Entry eb[GENGA_MAX_VARIANTS][MC_BATCH_WAYS];  // batches: FP32 variants
+    unsigned long long tick = 0;
 };
 
 namespace {
@@ -283,7 +288,16 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
             if (n >= (unsigned)M_CLAIM && !wait_lead(&s_lead, n - M_CLAIM + 1, a.status, wlim)) return;
             const int q = atomicAdd(a.work, 1);
             const bool done = q >= P.items;
-            const int4 it = done ? make_int4(0, 0, 0, 0) : P.item[q];
+            int4 it = done ? make_int4(0, 0, 0, 0) : P.item[q];
+            if (!done && P.nreal > 0) {  // a plan for the padded length: only the groups that hold bodies
+                const int greal = (P.nreal + MG - 1) / MG;
+                if (it.x * P.gpb >= greal) continue;  // a block of padding only: its rows are never read
+                it.z = min(it.z, greal);
+                if (it.y >= it.z) {  // no j-group with bodies: one empty slot writes the item's (zero) i-row
+                    it.y = -1;
+                    it.z = 0;
+                }
+            }
             for (int g = it.y; done || g < it.z; g++, n++) {
                 const int slot = n % STAGES;
                 const unsigned u = n / STAGES;
@@ -295,6 +309,10 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                 }
                 if (a.hold) return;  // test hook: no stage is ever filled (and no copy issued)
                 hdr[slot] = MHdr{q, g, (g == it.y ? 1 : 0) | (g == it.z - 1 ? 2 : 0), 0};
+                if (g < 0) {  // the empty slot: no copy
+                    mbar_arrive(&full[slot]);
+                    continue;
+                }
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&full[slot], STAGE_BYTES);
                 bulk_g2s(s_r + slot * 4 * MG, a.rel + (size_t)g * 4 * MG, 4 * MG * 4, &full[slot]);
@@ -323,7 +341,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                 jnp = sy.np;
                 jpoff = sy.poff;
             }
-            if (jrow) {
+            if (jrow && h.group >= 0) {
                 const float *sp = s_part + (size_t)slot * CW * 3 * MG;
 #pragma unroll
                 for (int half = 0; half < 2; half++) {
@@ -363,14 +381,18 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
         if (h.flags & 1) {  // first slot of an item: this warp's i-tile
             const int4 it = P.item[h.item];
             row = it.w;
-            if (lane == 0) s_wsys[warp] = P.sys[P.bsys[it.x]];
+            if (lane == 0) {
+                s_wsys[warp] = P.sys[P.bsys[it.x]];
+                if (P.nreal > 0) s_wsys[warp].N = P.nreal;
+            }
             __syncwarp();
             const MSys &sy = s_wsys[warp];
             diag = row < sy.S;
             // the warp's i-groups are interleaved over the block (gw, gw + CW,
             // ...), so a j-group next to one part of the block is near one
             // i-group of several warps rather than all of one warp's
-            const int gb0 = sy.poff / MG + (it.x - sy.blk0) * P.gpb, gb1 = min(gb0 + P.gpb, sy.g1);
+            const int gb0 = sy.poff / MG + (it.x - sy.blk0) * P.gpb;
+            const int gb1 = min(gb0 + P.gpb, (sy.poff + sy.N + MG - 1) / MG);  // groups holding bodies
             gw = gb0 + warp;
             qin = 0u;
 #pragma unroll
@@ -425,7 +447,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
         }
         const int g = h.group;
         float *part = s_part + ((size_t)slot * CW + warp) * 3 * MG;
-        if (in) {
+        if (in && g >= 0) {  // (g < 0: an item without j-groups, its i-row only)
             // strip items: both sides of every pair; diagonal items: the
             // i-side only (every ordered pair inside the block is visited)
             const bool both = !diag;
@@ -660,7 +682,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                     else near_loop(std::false_type{}, std::integral_constant<unsigned, ALL>{});
                 }
             }
-        } else if (!diag) {
+        } else if (!diag && g >= 0) {
 #pragma unroll
             for (int c = 0; c < 3; c++) part[c * MG + lane] = part[c * MG + 32 + lane] = 0.f;
         }
@@ -729,7 +751,8 @@ __global__ void combine_mutual_kernel(const double *__restrict__ partial, const 
     const int p = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int c = blockIdx.y;
     if (p >= npad) return;
-    const MSys sy = P.sys[plan_system(P, p)];
+    MSys sy = P.sys[plan_system(P, p)];
+    if (P.nreal > 0) sy.N = P.nreal;
     const int k = p - sy.poff;
     if (k >= sy.N) return;
     const int bl = (k / MG) / P.gpb;  // block within the system
@@ -852,7 +875,16 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
             if (n >= (unsigned)M_CLAIM && !wait_lead(&s_lead, n - M_CLAIM + 1, a.status, wlim)) return;
             const int q = atomicAdd(a.work, 1);
             const bool done = q >= P.items;
-            const int4 it = done ? make_int4(0, 0, 0, 0) : P.item[q];
+            int4 it = done ? make_int4(0, 0, 0, 0) : P.item[q];
+            if (!done && P.nreal > 0) {  // a plan for the padded length: only the groups that hold bodies
+                const int greal = (P.nreal + MG - 1) / MG;
+                if (it.x * P.gpb >= greal) continue;  // a block of padding only: its rows are never read
+                it.z = min(it.z, greal);
+                if (it.y >= it.z) {  // no j-group with bodies: one empty slot writes the item's (zero) i-row
+                    it.y = -1;
+                    it.z = 0;
+                }
+            }
             for (int g = it.y; done || g < it.z; g++, n++) {
                 const int slot = n % STAGES;
                 const unsigned u = n / STAGES;
@@ -864,6 +896,10 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
                 }
                 if (a.hold) return;  // test hook: no stage is ever filled (and no copy issued)
                 hdr[slot] = MHdr{q, g, (g == it.y ? 1 : 0) | (g == it.z - 1 ? 2 : 0), 0};
+                if (g < 0) {  // the empty slot: no copy
+                    mbar_arrive(&full[slot]);
+                    continue;
+                }
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&full[slot], STAGE_BYTES);
                 bulk_g2s(s_p + slot * MG, a.p64 + (size_t)g * MG, MG * 32, &full[slot]);
@@ -890,7 +926,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
                 jnp = sy.np;
                 jpoff = sy.poff;
             }
-            if (jrow) {
+            if (jrow && h.group >= 0) {
                 const double *sp = s_part + (size_t)slot * CW * 3 * MG;
 #pragma unroll
                 for (int half = 0; half < 2; half++) {
@@ -929,11 +965,15 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
         if (h.flags & 1) {  // first slot of an item: this warp's i-bodies (groups gw + q CW)
             const int4 it = P.item[h.item];
             row = it.w;
-            if (lane == 0) s_wsys[warp] = P.sys[P.bsys[it.x]];
+            if (lane == 0) {
+                s_wsys[warp] = P.sys[P.bsys[it.x]];
+                if (P.nreal > 0) s_wsys[warp].N = P.nreal;
+            }
             __syncwarp();
             const MSys &sy = s_wsys[warp];
             diag = row < sy.S;
-            const int gb0 = sy.poff / MG + (it.x - sy.blk0) * P.gpb, gb1 = min(gb0 + P.gpb, sy.g1);
+            const int gb0 = sy.poff / MG + (it.x - sy.blk0) * P.gpb;
+            const int gb1 = min(gb0 + P.gpb, (sy.poff + sy.N + MG - 1) / MG);  // groups holding bodies
             gw = gb0 + warp;
             qin = 0u;
 #pragma unroll
@@ -976,7 +1016,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
         }
         const int g = h.group;
         double *part = s_part + ((size_t)slot * CW + warp) * 3 * MG;
-        if (in) {
+        if (in && g >= 0) {  // (g < 0: an item without j-groups, its i-row only)
             const bool both = !diag;
             const Box gb = {s_g[slot * 2], s_g[slot * 2 + 1]};
             const double4_32a *tp = s_p + slot * MG;
@@ -1089,7 +1129,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
                 comp_add(acc[(1 * BPT + k) * NC], PY[k]);
                 comp_add(acc[(2 * BPT + k) * NC], PZ[k]);
             }
-        } else if (!diag) {
+        } else if (!diag && g >= 0) {
 #pragma unroll
             for (int c = 0; c < 3; c++) part[c * MG + lane] = part[c * MG + 32 + lane] = 0.0;
         }
@@ -1125,7 +1165,8 @@ __global__ void combine_mutual64_kernel(const double *__restrict__ partial, cons
     const int p = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int c = blockIdx.y;
     if (p >= npad) return;
-    const MSys sy = P.sys[plan_system(P, p)];
+    MSys sy = P.sys[plan_system(P, p)];
+    if (P.nreal > 0) sy.N = P.nreal;
     const int k = p - sy.poff;
     if (k >= sy.N) return;
     const int bl = (k / MG) / P.gpb;
@@ -1404,14 +1445,16 @@ void mutual_variant_shape(int v, int *cw, int *bpt) {
 
 void free_mutual_cache(genga_ctx *c) {
     if (!c->mcache) return;
-    for (MutualCache::Entry *t : {c->mcache->e, c->mcache->eb})
-        for (int q = 0; q < GENGA_MAX_VARIANTS; q++) {
-            MutualCache::Entry &e = t[q];
-            if (e.d_item) cudaFree(e.d_item);
-            if (e.d_blk) cudaFree(e.d_blk);
-            if (e.d_bsys) cudaFree(e.d_bsys);
-            if (e.d_sys) cudaFree(e.d_sys);
-        }
+    auto drop = [](MutualCache::Entry &e) {
+        if (e.d_item) cudaFree(e.d_item);
+        if (e.d_blk) cudaFree(e.d_blk);
+        if (e.d_bsys) cudaFree(e.d_bsys);
+        if (e.d_sys) cudaFree(e.d_sys);
+    };
+    for (int q = 0; q < GENGA_MAX_VARIANTS; q++) {
+        for (MutualCache::Entry &e : c->mcache->e[q]) drop(e);
+        for (MutualCache::Entry &e : c->mcache->eb[q]) drop(e);
+    }
     delete c->mcache;
     c->mcache = nullptr;
 }
@@ -1420,8 +1463,18 @@ void free_mutual_cache(genga_ctx *c) {
 // npg groups each), built and uploaded on first use.  Returns false when it
 // must be built while `s` is being captured, or when no plan fits: the caller
 // then uses a one-sided variant.
-static bool plan_cached(genga_ctx *c, MutualCache::Entry &e, unsigned long long key, const std::vector<HSys> &hs,
-                        int cw, int npg, cudaStream_t s, MutualPlan *P) {
+static bool plan_cached(genga_ctx *c, MutualCache::Entry *ways, int nways, unsigned long long key,
+                        const std::vector<HSys> &hs, int cw, int npg, cudaStream_t s, MutualPlan *P) {
+    MutualCache::Entry *pe = nullptr;
+    for (int w = 0; w < nways && !pe; w++)
+        if (ways[w].key == key) pe = &ways[w];
+    if (!pe) {  // the least recently used entry makes room
+        pe = &ways[0];
+        for (int w = 1; w < nways; w++)
+            if (ways[w].used < pe->used) pe = &ways[w];
+    }
+    MutualCache::Entry &e = *pe;
+    e.used = ++c->mcache->tick;
     if (e.key != key) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
@@ -1434,6 +1487,7 @@ static bool plan_cached(genga_ctx *c, MutualCache::Entry &e, unsigned long long 
         if (e.d_sys) cudaFree(e.d_sys);
         e = MutualCache::Entry{};
         e.key = key;  // remembered also when no plan fits, so that it is not searched again
+        e.used = c->mcache->tick;
         if (po.item.empty() || po.sys.empty()) return false;
         const size_t need = po.row_entries;
         if (need > c->partial_cap) {  // a larger workspace for the rows; captured step graphs used the old one
@@ -1468,7 +1522,7 @@ static bool plan_cached(genga_ctx *c, MutualCache::Entry &e, unsigned long long 
         e.ok = true;
     }
     if (!e.ok) return false;
-    *P = MutualPlan{e.nb, e.gpb, e.items, e.nsys, e.d_item, e.d_blk, e.d_bsys, e.d_sys};
+    *P = MutualPlan{e.nb, e.gpb, e.items, e.nsys, 0, e.d_item, e.d_blk, e.d_bsys, e.d_sys};
     return true;
 }
 
@@ -1477,18 +1531,27 @@ static MutualCache *cache_of(genga_ctx *c) {
     return c->mcache;
 }
 
+// Single systems: the plan is built for the padded length (every group of
+// it, the padding bodies massless) and serves every N of that length; the
+// bodies' count goes with the returned plan.
 bool mutual_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P) {
-    if (v < 0 || v >= kNumMVariants || !cache_of(c)) return false;
+    if (N <= 0 || v < 0 || v >= kNumMVariants || !cache_of(c)) return false;
     const int npad = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
-    return plan_cached(c, c->mcache->e[v], (unsigned long long)N, {HSys{0, npad, N, 0}}, kMVariants[v].cw,
-                       kMVariants[v].np, s, P);
+    if (!plan_cached(c, c->mcache->e[v], MC_WAYS, (unsigned long long)npad, {HSys{0, npad, npad, 0}},
+                     kMVariants[v].cw, kMVariants[v].np, s, P))
+        return false;
+    P->nreal = N;
+    return true;
 }
 
 bool mutual64_plan(genga_ctx *c, int N, int v, cudaStream_t s, MutualPlan *P) {
-    if (v < 0 || v >= kNumM64Variants || !cache_of(c)) return false;
+    if (N <= 0 || v < 0 || v >= kNumM64Variants || !cache_of(c)) return false;
     const int npad = (N + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
-    return plan_cached(c, c->mcache->e[kNumMVariants + v], (unsigned long long)N, {HSys{0, npad, N, 0}},
-                       kM64Variants[v].cw, kM64Variants[v].bpt / 2, s, P);
+    if (!plan_cached(c, c->mcache->e[kNumMVariants + v], MC_WAYS, (unsigned long long)npad,
+                     {HSys{0, npad, npad, 0}}, kM64Variants[v].cw, kM64Variants[v].bpt / 2, s, P))
+        return false;
+    P->nreal = N;
+    return true;
 }
 
 bool mutual_plan_batched(genga_ctx *c, const BatchBodies &bb, unsigned long long key, int v, cudaStream_t s,
@@ -1500,7 +1563,7 @@ bool mutual_plan_batched(genga_ctx *c, const BatchBodies &bb, unsigned long long
         if (n > 0) hs.push_back(HSys{bb.poff[d], bb.poff[d + 1] - bb.poff[d], n, bb.off[d]});
     }
     if (hs.empty()) return false;
-    return plan_cached(c, c->mcache->eb[v], key, hs, kMVariants[v].cw, kMVariants[v].np, s, P);
+    return plan_cached(c, c->mcache->eb[v], MC_BATCH_WAYS, key, hs, kMVariants[v].cw, kMVariants[v].np, s, P);
 }
 
 cudaError_t init_mutual_kernels() {
