@@ -1,5 +1,6 @@
-// mutual.cu -- the mutual (symmetric) FP32 long-range pass of the kick
-// (Sect. 1, the single-precision long-range forces):
+// mutual.cu -- the mutual (symmetric) long-range passes of the kick, FP32
+// and FP64 (Sect. 1, the single-precision long-range forces and the FP64
+// kick they are measured against):
 //
 //   a_i = sum_{j != i} G m_j K(y_ij) (x_j - x_i) / r_ij^3
 //
@@ -7,8 +8,9 @@
 // both bodies, a_i += G m_j r^-3 (x_j - x_i) and a_j += G m_i r^-3 (x_i - x_j)
 // (Newton's third law), so a pair costs 16 FP32 operations for two
 // interactions instead of 12 for one.  The sums and their tolerances are
-// those of the one-sided FP32 pass in kick.cu; only the order of the
-// evaluation changes.
+// those of the one-sided passes in kick.cu; only the order of the
+// evaluation changes.  One plan and kernel serve a single disc and a batch
+// of independent discs (a table of systems).
 //
 // Layout.  Bodies in the spatial (Morton) order, 64-body groups.  A CTA has
 // CW consumer warps, one producer warp and one reducer warp.  A CTA's
@@ -27,12 +29,14 @@
 // frees the slot; so every sum has a fixed order and results are bitwise
 // reproducible.
 //
-// Work.  Items come from a table built on the host (plan_mutual): the
-// diagonal item of each i-block (its own groups; warp w takes tile t of the
-// block if (t - w) mod n lies in [1, n/2) -- or equals n/2 with w < t --, so
-// every pair of tiles is evaluated once, and its own tile one-sided), then
-// chunks of each block's strip (the groups after the block), longest first.
-// A persistent grid takes items from a global counter.
+// Work.  Items come from a table built on the host (plan_systems): the
+// diagonal items of each i-block (its own groups, one-sided: every warp takes
+// its i-groups against a range of the block's groups, each ordered pair from
+// its i-side, the self pair screened out), then chunks of each block's strip
+// (the groups of its system after the block, both sides), longest first, a
+// tail of single-group items last.  A persistent grid takes items from a
+// global counter; a CTA's producer claims its next item only when the
+// leading consumer warp is close to the end of its queued slots.
 //
 // Precision.  Offsets come from positions relative to the centre c of the
 // j-group: X_j = fl32(x_j - c) (the FP64 difference rounded, computed by the
@@ -40,10 +44,11 @@
 // an i-tile when every pair is beyond both the r_crit bound and the group's
 // precision distance (a tenth of its half-diagonal h), so the offset
 // X_j - X_i is within 3 u (1 + 10) relative of x_j - x_i (u = 2^-24): there
-// the pair terms need no screening.  Otherwise (NEAR) the offsets carry the exact residuals, every
-// pair is compared with an FP32 upper bound of r_crit,ij^2, and the pairs
-// under it are evaluated exactly in FP64 afterwards (K-weighted, both sides,
-// encounter list) -- close-encounter forces are always FP64 (Sect. 1).
+// the pair terms need no screening.  Otherwise (NEAR) the offsets carry the
+// exact residuals, every pair is compared with an FP32 upper bound of
+// r_crit,ij^2, and the pairs under it are evaluated exactly in FP64
+// afterwards (K-weighted, both sides, encounter list) -- close-encounter
+// forces are always FP64 (Sect. 1).
 // i-sums: FP32 per slot, folded every 2 slots into double-float per-body
 // sums in shared memory, written as the item's i-row at its end.
 #include <algorithm>
