@@ -92,6 +92,20 @@ genga_status genga_fp64_tuning_times(genga_ctx *ctx, int32_t N, float *ms, int32
 genga_status genga_batched_tuning(genga_ctx *ctx, const int32_t *offsets, int32_t D, int32_t *variant, float *ms,
                                   int32_t n);
 
+/* Host-only self-check of the mutual passes' work plan (no device, no
+ * context): builds the plan for a batch of nsys systems of n[d] bodies (HOST
+ * memory; nsys = 1: a single system) for cw consumer warps of npg 64-body
+ * groups each and ctas persistent CTAs, and verifies by enumeration that
+ * every pair of groups of a system is visited exactly once (both orders
+ * inside an i-block, one visit across blocks), that no item leaves its
+ * system or reaches a group without bodies, and that each block's partial
+ * rows are exactly the rows its combine reads, each written by one item.
+ * stats (HOST, 4 values): items, the largest rows of a system, group-pair
+ * visits, 8-byte entries of all rows.  GENGA_ERR_CAPACITY: no plan fits;
+ * GENGA_ERR_INVALID_ARG: bad arguments or a check failed. */
+genga_status genga_mutual_plan_check(int32_t nsys, const int32_t *n, int32_t cw, int32_t npg, int32_t ctas,
+                                     int64_t *stats);
+
 /* Name of the most recent CUDA runtime error (cudaGetErrorName) that an
  * entry point called from this thread turned into GENGA_ERR_CUDA, or
  * "cudaSuccess" if none has; a static string. */

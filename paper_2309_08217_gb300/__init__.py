@@ -104,6 +104,7 @@ def load():
             "genga_step_batched": ([V, S, C.POINTER(C.c_int32), I, P, I, V], I),
             "genga_get_kernel_variant": ([V, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], I),
             "genga_set_fp64_variant": ([V, I], I),
+            "genga_mutual_plan_check": ([I, C.POINTER(C.c_int32), I, I, I, C.POINTER(C.c_int64)], I),
             "genga_batched_tuning": ([V, C.POINTER(C.c_int32), I, C.POINTER(C.c_int32), C.POINTER(C.c_float), I], I),
             "genga_get_fp64_variant": ([V, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], I),
             "genga_fp64_variant_info": ([I] + [C.POINTER(I)] * 3, I),
@@ -384,6 +385,15 @@ def genga_batched_tuning(ctx, offsets):
     v, arr = C.c_int32(), (C.c_float * n)()
     _check(load().genga_batched_tuning(_ctx(ctx), off, D, C.byref(v), arr, n), "genga_batched_tuning")
     return v.value, list(arr)
+
+
+def genga_mutual_plan_check(sizes, cw, npg, ctas=152):
+    """Host-only check of the mutual work plan for systems of the given sizes;
+    returns (items, largest rows of a system, group-pair visits, row entries)."""
+    n = (C.c_int32 * len(sizes))(*[int(v) for v in sizes])
+    st = (C.c_int64 * 4)()
+    _check(load().genga_mutual_plan_check(len(sizes), n, int(cw), int(npg), int(ctas), st), "genga_mutual_plan_check")
+    return tuple(st)
 
 
 def genga_set_fp64_variant(ctx, variant=-1):

@@ -1624,3 +1624,98 @@ cudaError_t launch_combine_mutual(const double *partial, const MutualPlan &P, in
 }
 
 }  // namespace genga
+
+// ------------------------------------------------- host check of a plan
+// Builds the mutual plan of a batch of systems of n[d] bodies (padded to
+// GENGA_PAD, a single system for nsys = 1) for cw consumer warps of npg
+// groups, and verifies by enumeration what the pass relies on: inside a
+// block every ordered pair of groups is visited once by its diagonal items;
+// every pair of groups in different blocks of a system once, by a strip item
+// of the earlier block; no item crosses a system or reaches a group without
+// bodies; each block's rows are the rows its combine reads, each written by
+// one item; the rows fit the plan's row space.
+extern "C" genga_status genga_mutual_plan_check(int32_t nsys, const int32_t *n, int32_t cw, int32_t npg,
+                                                int32_t ctas, int64_t *stats) {
+    using namespace genga;
+    if (nsys < 1 || nsys > GENGA_MAX_DISCS || !n || cw < 1 || npg < 1 || ctas < 1 || !stats)
+        return GENGA_ERR_INVALID_ARG;
+    std::vector<HSys> hs;
+    int poff = 0, off = 0;
+    for (int d = 0; d < nsys; d++) {
+        if (n[d] < 0) return GENGA_ERR_INVALID_ARG;
+        const int np = (n[d] + GENGA_PAD - 1) / GENGA_PAD * GENGA_PAD;
+        if (n[d] > 0) hs.push_back(HSys{poff, np, n[d], off});
+        poff += np;
+        off += n[d];
+    }
+    for (int q = 0; q < 4; q++) stats[q] = 0;
+    if (hs.empty()) return GENGA_OK;
+    PlanOut po;
+    plan_systems(hs, cw, npg, ctas, MUTUAL_MAX_ROWS, &po);
+    if (po.item.empty()) return GENGA_ERR_CAPACITY;  // no plan fits
+    const int gpb = cw * npg;
+    const int ngr = poff / MG;
+    std::vector<int> gsys(ngr, -1);  // system of each group holding bodies
+    for (size_t d = 0; d < po.sys.size(); d++)
+        for (int g = po.sys[d].poff / MG; g < po.sys[d].g1; g++) gsys[g] = (int)d;
+    auto block_of = [&](int g) {
+        const MSys &y = po.sys[gsys[g]];
+        return y.blk0 + (g - y.poff / MG) / gpb;
+    };
+    auto block_groups = [&](int B, int *g0, int *g1) {
+        const MSys &y = po.sys[po.bsys[B]];
+        *g0 = y.poff / MG + (B - y.blk0) * gpb;
+        *g1 = std::min(*g0 + gpb, y.g1);
+    };
+    // visits of each (i-group, j-group): ordered for diagonal items, unordered
+    // (counted on (earlier, later)) for strip items
+    std::vector<std::vector<int>> rows_seen(po.blk.size());
+    std::vector<std::vector<uint8_t>> hit(ngr);
+    for (size_t d = 0; d < po.sys.size(); d++)  // row gi: the groups of its system
+        for (int g = po.sys[d].poff / MG; g < po.sys[d].g1; g++) hit[g].assign(po.sys[d].g1 - po.sys[d].poff / MG, 0);
+    long long visits = 0;
+    for (const int4 &it : po.item) {
+        if (it.x < 0 || it.x >= (int)po.blk.size()) return GENGA_ERR_INVALID_ARG;
+        int b0, b1;
+        block_groups(it.x, &b0, &b1);
+        const MSys &y = po.sys[po.bsys[it.x]];
+        if (it.y < y.poff / MG || it.z > y.g1 || it.y >= it.z) return GENGA_ERR_INVALID_ARG;
+        rows_seen[it.x].push_back(it.w);
+        const bool diag = it.w < y.S;
+        if (diag && (it.y < b0 || it.z > b1)) return GENGA_ERR_INVALID_ARG;
+        if (!diag && it.y < b1) return GENGA_ERR_INVALID_ARG;  // strips start after the block
+        for (int gi = b0; gi < b1; gi++)
+            for (int gj = it.y; gj < it.z; gj++) {
+                if (++hit[gi][gj - y.poff / MG] > 1) return GENGA_ERR_INVALID_ARG;
+                visits++;
+            }
+    }
+    for (size_t d = 0; d < po.sys.size(); d++) {
+        const int a0 = po.sys[d].poff / MG, a1 = po.sys[d].g1;
+        for (int gi = a0; gi < a1; gi++)
+            for (int gj = a0; gj < a1; gj++) {
+                const int bi = block_of(gi), bj = block_of(gj);
+                const int want = bi == bj ? 1 : (bi < bj ? 1 : 0);
+                if (hit[gi][gj - a0] != want) return GENGA_ERR_INVALID_ARG;
+            }
+    }
+    int max_rows = 0;
+    for (size_t B = 0; B < po.blk.size(); B++) {
+        const MSys &y = po.sys[po.bsys[B]];
+        const int nb = (po.bsys[B] + 1 < (int)po.sys.size() ? po.sys[po.bsys[B] + 1].blk0 : (int)po.blk.size()) - y.blk0;
+        std::vector<int> want;
+        for (int r = 0; r < po.blk[B].x; r++) want.push_back(r);
+        for (int r = 0; r < po.blk[B].y; r++) want.push_back(y.S + r);
+        std::vector<int> got = rows_seen[B];
+        std::sort(got.begin(), got.end());
+        if (got != want) return GENGA_ERR_INVALID_ARG;  // each row written once, every row read is written
+        for (int r : got)
+            if (r >= y.irows) return GENGA_ERR_INVALID_ARG;
+        max_rows = std::max(max_rows, y.irows + nb);
+    }
+    stats[0] = (int64_t)po.item.size();
+    stats[1] = max_rows;
+    stats[2] = visits;
+    stats[3] = (int64_t)po.row_entries;
+    return GENGA_OK;
+}
