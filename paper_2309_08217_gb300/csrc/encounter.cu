@@ -1034,8 +1034,10 @@ cudaError_t init_bs_kernel(int sm_count) {
     cfg.gridDim = dim3((unsigned)((2 * sm_count) / BS_TEAM_CTAS * BS_TEAM_CTAS));
     cfg.blockDim = dim3(32 * BS_WARPS);
     int ncl = 0;
-    const cudaError_t e = cudaOccupancyMaxActiveClusters(&ncl, (void *)bs_kernel, &cfg);
-    if (e != cudaSuccess) return e;
+    if (cudaOccupancyMaxActiveClusters(&ncl, (void *)bs_kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();  // not fatal: one cluster at a time still runs every group
+        ncl = 1;
+    }
     g_bs_clusters = ncl > 0 ? ncl : 1;
     return cudaSuccess;
 }
