@@ -63,7 +63,7 @@ _lock = threading.Lock()
 
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile libgenga.so for sm_103a (nvcc) into the package directory."""
-    from .build import build as _b
+    from .nvcc_build import build as _b  # (a submodule named "build" would replace this function on import)
     return _b(force=force, verbose=verbose)
 
 

@@ -4,7 +4,7 @@ Each translation unit under csrc/ is compiled in parallel into _build/,
 then linked into paper_2309_08217_gb300/libgenga.so (shared CUDA runtime,
 so device pointers and streams from the calling process are valid here).
 
-    python -m paper_2309_08217_gb300.build [--force] [--verbose]
+    python -m paper_2309_08217_gb300.nvcc_build [--force] [--verbose]
 """
 from __future__ import annotations
 
