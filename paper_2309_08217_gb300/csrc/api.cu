@@ -828,7 +828,7 @@ genga_status genga_create(genga_ctx **out, int32_t max_N, int32_t device) {
     if (e == cudaSuccess) e = alloc(&c->pk_lo, np);
     if (e == cudaSuccess) e = alloc(&c->pk_t, 4 * (size_t)np);
     if (e == cudaSuccess) e = alloc(&c->pk_d, 2 * (size_t)np);
-    if (e == cudaSuccess) e = alloc(&c->pk_r, 4 * (size_t)np);
+    if (e == cudaSuccess) e = alloc(&c->pk_r, np);
     if (e == cudaSuccess) e = alloc(&c->pk_rl, np);
     if (e == cudaSuccess) e = alloc(&c->gctr, np / 64);
     if (e == cudaSuccess) e = alloc(&c->pk64, np);

@@ -118,7 +118,7 @@ struct genga_ctx {
     float4 *pk_lo;             // [npad] {x - x_hi, y - y_hi, z - z_hi, 0}
     float *pk_t;               // [4 npad] tile-blocked {x_hi}, {y_hi}, {z_hi}, {G m} per 256 bodies
     float4 *pk_d;              // [2 npad] duplicated pairs {x_hi, x_hi, y_hi, y_hi}, {z_hi, z_hi, G m, G m}
-    float *pk_r;               // [4 npad] group-centred X, Y, Z, G m: per 64-body group four arrays of 64 floats, X = fl32(x - c_group)
+    float4 *pk_r;              // [npad] group-centred {X, Y, Z, G m}, X = fl32(x - c_group)
     float4 *pk_rl;             // [npad] their residuals {x - c - X, y - c - Y, z - c - Z, test particle}
     float4 *gctr;              // [npad / 64] group centre c (FP32) and the precision distance of the group
     double4_32a *pk64;             // [npad] {x, y, z, G m}
@@ -233,7 +233,7 @@ struct PassArgs {               // one long-range pass
     const float4 *hi, *lo;
     const float *hit;           // tile-blocked copy of hi
     const float4 *hid;          // duplicated-pair copy of hi (two float4 per body)
-    const float *rel;           // group-centred copy (mutual pass): per group X[64], Y[64], Z[64], G m[64]
+    const float4 *rel;          // group-centred copy (mutual pass): {X, Y, Z, G m} per body
     const float4 *rell;         // residuals of the group-centred copy (mutual pass)
     const float4 *gctr;         // group centres and precision distances (mutual pass)
     const double4_32a *p64;

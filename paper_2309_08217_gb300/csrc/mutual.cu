@@ -220,8 +220,8 @@ __device__ __noinline__ void screened_pair_mutual(const PassArgs &a, int i, int 
 template <int NP, int CW, int STAGES>
 struct MLayout {
     static constexpr int BPT = 2 * NP, NC = CW * 32;
-    static constexpr size_t r_off = 0;                                         // float [STAGES][4][MG]
-    static constexpr size_t l_off = r_off + (size_t)STAGES * 4 * MG * 4;       // float4 [STAGES][MG]
+    static constexpr size_t r_off = 0;                                         // float4 [STAGES][MG]
+    static constexpr size_t l_off = r_off + (size_t)STAGES * MG * 16;          // float4 [STAGES][MG]
     static constexpr size_t g_off = l_off + (size_t)STAGES * MG * 16;          // float4 [STAGES][4]
     static constexpr size_t p_off = g_off + (size_t)STAGES * 4 * 16;           // float [STAGES][CW][3][MG]
     static constexpr size_t a_off = p_off + (size_t)STAGES * CW * 3 * MG * 4;  // DF [3][BPT][NC]
@@ -250,7 +250,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
     constexpr int NEAR_UNR = NP <= 2 ? 2 : 1;  // NEAR-loop unroll (register budget)
     constexpr uint32_t STAGE_BYTES = 4 * MG * 4 + MG * 16 + 3 * 16;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *s_r = reinterpret_cast<float *>(smem_raw + L::r_off);
+    float4 *s_r = reinterpret_cast<float4 *>(smem_raw + L::r_off);
     float4 *s_l = reinterpret_cast<float4 *>(smem_raw + L::l_off);
     float4 *s_g = reinterpret_cast<float4 *>(smem_raw + L::g_off);
     float *s_part = reinterpret_cast<float *>(smem_raw + L::p_off);
@@ -320,7 +320,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                 }
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&full[slot], STAGE_BYTES);
-                bulk_g2s(s_r + slot * 4 * MG, a.rel + (size_t)g * 4 * MG, 4 * MG * 4, &full[slot]);
+                bulk_g2s(s_r + slot * MG, a.rel + (size_t)g * MG, MG * 16, &full[slot]);
                 bulk_g2s(s_l + slot * MG, a.rell + (size_t)g * MG, MG * 16, &full[slot]);
                 bulk_g2s(s_g + slot * 4, a.gbox_lo + g, 16, &full[slot]);
                 bulk_g2s(s_g + slot * 4 + 1, a.gbox_hi + g, 16, &full[slot]);
@@ -458,7 +458,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
             const bool both = !diag;
             const Box gb = {s_g[slot * 4], s_g[slot * 4 + 1]};
             const float4 ctr = s_g[slot * 4 + 2];
-            const float *tr = s_r + slot * 4 * MG;  // X[64], Y[64], Z[64], G m[64] of the j-group
+            const float4 *tr = s_r + slot * MG;  // {X, Y, Z, G m} of the j-group's bodies
             // the warp's i-bodies relative to the group centre
             f32x2 XI[NP], YI[NP], ZI[NP];
 #pragma unroll
@@ -486,10 +486,10 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
                     float JX = 0.f, JY = 0.f, JZ = 0.f;
 #pragma unroll(UNR)
                     for (int t = 0; t < 32; t++) {
-                        // consecutive j across the lanes: conflict-free scalar loads
+                        // consecutive j across the lanes: one conflict-free 16-byte load
                         const int j = sb * 32 + ((lane + t) & 31);
-                        const float xj = tr[j], yj = tr[MG + j], zj = tr[2 * MG + j], mj = tr[3 * MG + j];
-                        const f32x2 AX = pk2(xj, xj), AY = pk2(yj, yj), AZ = pk2(zj, zj), AM = pk2(mj, mj);
+                        const float4 B = tr[j];
+                        const f32x2 AX = pk2(B.x, B.x), AY = pk2(B.y, B.y), AZ = pk2(B.z, B.z), AM = pk2(B.w, B.w);
 #pragma unroll
                         for (int q = 0; q < NP; q++) {
                             const f32x2 DX = sub2(AX, XI[q]), DY = sub2(AY, YI[q]), DZ = sub2(AZ, ZI[q]);
@@ -573,8 +573,8 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
 #pragma unroll(NEAR_UNR)
                         for (int t = 0; t < 32; t++) {
                             const int jj = (lane + t) & 31, j = sb * 32 + jj;
-                            const float xj = tr[j], yj = tr[MG + j], zj = tr[2 * MG + j], mj = tr[3 * MG + j];
-                            const f32x2 AX = pk2(xj, xj), AY = pk2(yj, yj), AZ = pk2(zj, zj), AM = pk2(mj, mj);
+                            const float4 B = tr[j];
+                            const f32x2 AX = pk2(B.x, B.x), AY = pk2(B.y, B.y), AZ = pk2(B.z, B.z), AM = pk2(B.w, B.w);
                             const float4 R = tl[j];
                             const f32x2 RX = pk2(R.x, R.x), RY = pk2(R.y, R.y), RZ = pk2(R.z, R.z);
 #pragma unroll
@@ -1219,7 +1219,7 @@ struct MVariant {
 };
 #define GENGA_MV(NP, CW, ST, UNR) \
     {NP, CW, pass_mutual_kernel<NP, CW, ST, UNR>, MLayout<NP, CW, ST>::bytes}
-const MVariant kMVariants[] = {GENGA_MV(2, 12, 6, 8), GENGA_MV(2, 12, 6, 4), GENGA_MV(2, 12, 8, 8), GENGA_MV(4, 8, 6, 4)};
+const MVariant kMVariants[] = {GENGA_MV(2, 12, 4, 8), GENGA_MV(2, 12, 8, 4), GENGA_MV(2, 12, 8, 8), GENGA_MV(4, 8, 6, 4)};
 #undef GENGA_MV
 constexpr int kNumMVariants = sizeof(kMVariants) / sizeof(kMVariants[0]);
 

@@ -221,8 +221,9 @@ __device__ __forceinline__ Box group_reduce_store(float2 s, float3 pos, bool rea
 
 // Group-centred copies for the mutual FP32 pass: c = the centre of the
 // group's box (an FP32 value), each body's offset from it as the FP64
-// difference rounded to FP32 (X = fl32(x - c)), stored per 64-body group as
-// four arrays X[64], Y[64], Z[64], G m[64], and its rounding residual
+// difference rounded to FP32 (X = fl32(x - c)), stored as the record
+// {X, Y, Z, G m} (the pass reads a j-body with one 16-byte load), and its
+// rounding residual
 // {x - c - X, y - c - Y, z - c - Z, test-particle flag}; per group
 // {c, PRECISION_KAPPA * h}, h an upper bound of |x - c| over the group.  The
 // pass treats a group as far from a set of bodies only beyond that distance:
@@ -233,7 +234,7 @@ __device__ __forceinline__ Box group_reduce_store(float2 s, float3 pos, bool rea
 // pair's force.  An empty group (padding only) has c = 0 and distance 0.
 constexpr float PRECISION_KAPPA = 0.1f;
 
-__device__ __forceinline__ void store_centred(int k, const Box &b, double4 p, bool tp, float *__restrict__ rel,
+__device__ __forceinline__ void store_centred(int k, const Box &b, double4 p, bool tp, float4 *__restrict__ rel,
                                               float4 *__restrict__ rell, float4 *__restrict__ gctr) {
     const bool empty = !(b.lo.x <= b.hi.x);
     const float cx = empty ? 0.f : 0.5f * (b.lo.x + b.hi.x), cy = empty ? 0.f : 0.5f * (b.lo.y + b.hi.y);
@@ -241,11 +242,7 @@ __device__ __forceinline__ void store_centred(int k, const Box &b, double4 p, bo
     const double dx = p.x - (double)cx, dy = p.y - (double)cy, dz = p.z - (double)cz;
     const float X = __double2float_rn(dx), Y = __double2float_rn(dy), Z = __double2float_rn(dz);
     const float w = __double2float_rn(p.w);
-    float *r = rel + (size_t)(k >> 6) * 256 + (k & 63);  // the group's X[64], Y[64], Z[64], G m[64]
-    r[0] = X;
-    r[64] = Y;
-    r[128] = Z;
-    r[192] = w;
+    rel[k] = make_float4(X, Y, Z, w);
     rell[k] = make_float4(__double2float_rn(dx - (double)X), __double2float_rn(dy - (double)Y),
                           __double2float_rn(dz - (double)Z), tp ? 1.f : 0.f);
     if (threadIdx.x == 0) {
@@ -268,7 +265,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(
     double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
     float4 *__restrict__ lo, double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
     float4 *__restrict__ gbox_hi, int32_t *__restrict__ gflag, double *__restrict__ a_osc,
-    double *__restrict__ rc_eq1, int n_big, uint32_t *__restrict__ iperm, double sscale, float *__restrict__ rel,
+    double *__restrict__ rc_eq1, int n_big, uint32_t *__restrict__ iperm, double sscale, float4 *__restrict__ rel,
     float4 *__restrict__ rell, float4 *__restrict__ gctr) {
     const int k = blockIdx.x * PREP_THREADS + threadIdx.x;
     float3 pos = make_float3(0.f, 0.f, 0.f);
@@ -293,7 +290,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_batched_kernel(
     double Mstar, double dt, double n1, double n2, int rcrit_mode, float4 *__restrict__ hi, float *__restrict__ hit, float4 *__restrict__ hid,
     float4 *__restrict__ lo, double4_32a *__restrict__ p64, float2 *__restrict__ scr, float4 *__restrict__ gbox_lo,
     float4 *__restrict__ gbox_hi, int32_t *__restrict__ gflag, double *__restrict__ a_osc,
-    double *__restrict__ rc_eq1, int n_big, uint32_t *__restrict__ iperm, double sscale, float *__restrict__ rel,
+    double *__restrict__ rc_eq1, int n_big, uint32_t *__restrict__ iperm, double sscale, float4 *__restrict__ rel,
     float4 *__restrict__ rell, float4 *__restrict__ gctr, const __grid_constant__ BatchBodies bb) {
     const int p = blockIdx.x * PREP_THREADS + threadIdx.x;
     const int d = find_segment(bb.poff, bb.D, p);
