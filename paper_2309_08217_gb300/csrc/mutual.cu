@@ -743,46 +743,69 @@ __device__ __forceinline__ int plan_system(const MutualPlan &P, int p) {
     return lo;
 }
 
-// One thread per (two consecutive bodies, component): the bodies' i-rows
-// then their j-rows, in row order, in double-float; then the optional acc
-// output and v += acc tau (acc[c * Ntot + body], body = perm[off + k]).  Two
-// bodies per thread make every row load 16 bytes per lane (512 contiguous
-// bytes per warp).  Both bodies are in the same i-block (blocks are whole
-// 64-body groups of one system), so they share the rows.
+// COMBINE_LANES lanes per (two consecutive bodies, component): lane r of
+// the group adds rows r, r + COMBINE_LANES, ... of the bodies' rows (their
+// i-rows, then the j-rows of the earlier blocks) in double-float; the
+// partial sums are then joined in a fixed tree (lane r with r ^ 1, then
+// with r ^ 2) and lane 0 writes the optional acc output and v += acc tau
+// (acc[c * Ntot + body], body = perm[off + k]).  Every sum has a fixed order
+// (bitwise reproducible); splitting a body's rows over lanes puts four
+// times the loads in flight and gives a grid of several blocks per SM.  Two
+// bodies per group make every row load 16 bytes per lane (128 contiguous
+// bytes per 8 groups); both bodies are in the same i-block (blocks are
+// whole 64-body groups of one system), so they share the rows.
+constexpr int COMBINE_LANES = 4;
+
 __global__ void combine_mutual_kernel(const double *__restrict__ partial, const __grid_constant__ MutualPlan P,
                                       int Ntot, int npad, const uint32_t *__restrict__ perm, double tau,
                                       double *__restrict__ acc, double *__restrict__ vx, double *__restrict__ vy,
                                       double *__restrict__ vz, uint32_t *__restrict__ status) {
-    const int p = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = 2 * (gt / COMBINE_LANES), r = gt % COMBINE_LANES;
     const int c = blockIdx.y;
-    if (p >= npad) return;
-    MSys sy = P.sys[plan_system(P, p)];
-    if (P.nreal > 0) sy.N = P.nreal;
-    const int k = p - sy.poff;
-    if (k >= sy.N) return;
-    const int bl = (k / MG) / P.gpb;  // block within the system
-    const size_t stride = 3 * (size_t)sy.np / 2;  // float4 units (two float2 entries)
-    const float4 *pr = reinterpret_cast<const float4 *>(partial + sy.pbase) + ((size_t)c * sy.np + k) / 2;
-    const int2 bk = P.blk[sy.blk0 + bl];
-    // the rows in order: diagonal i-rows, strip i-rows, j-rows of the system's blocks before bl
-    const int n0 = bk.x, n1 = n0 + bk.y, n2 = n1 + bl;
-    DF t0{0.f, 0.f}, t1{0.f, 0.f};
-    constexpr int BATCH = 16;
-    for (int r0 = 0; r0 < n2; r0 += BATCH) {
-        float4 v[BATCH];
-#pragma unroll
-        for (int u = 0; u < BATCH; u++) {
-            const int r = r0 + u;
-            const int rr = r < n0 ? r : r < n1 ? sy.S + (r - n0) : sy.irows + (r - n1);
-            v[u] = r < n2 ? pr[(size_t)rr * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < BATCH; u++)
-            if (r0 + u < n2) {
-                t0 = df_add(t0, v[u].x, v[u].y);
-                t1 = df_add(t1, v[u].z, v[u].w);
-            }
+    const unsigned gmask = 0xfu << (threadIdx.x & 28u);  // the group's lanes (every lane reaches the shuffles)
+    MSys sy{};
+    int k = 0;
+    bool live = p < npad;
+    if (live) {
+        sy = P.sys[plan_system(P, p)];
+        if (P.nreal > 0) sy.N = P.nreal;
+        k = p - sy.poff;
+        live = k < sy.N;
     }
+    DF t0{0.f, 0.f}, t1{0.f, 0.f};
+    if (live) {
+        const int bl = (k / MG) / P.gpb;  // block within the system
+        const size_t stride = 3 * (size_t)sy.np / 2;  // float4 units (two float2 entries)
+        const float4 *pr = reinterpret_cast<const float4 *>(partial + sy.pbase) + ((size_t)c * sy.np + k) / 2;
+        const int2 bk = P.blk[sy.blk0 + bl];
+        // the rows in order: diagonal i-rows, strip i-rows, j-rows of the system's blocks before bl
+        const int n0 = bk.x, n1 = n0 + bk.y, n2 = n1 + bl;
+        constexpr int BATCH = 8;
+        for (int r0 = r; r0 < n2; r0 += BATCH * COMBINE_LANES) {
+            float4 v[BATCH];
+#pragma unroll
+            for (int u = 0; u < BATCH; u++) {
+                const int rw = r0 + u * COMBINE_LANES;
+                const int rr = rw < n0 ? rw : rw < n1 ? sy.S + (rw - n0) : sy.irows + (rw - n1);
+                v[u] = rw < n2 ? pr[(size_t)rr * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < BATCH; u++)
+                if (r0 + u * COMBINE_LANES < n2) {
+                    t0 = df_add(t0, v[u].x, v[u].y);
+                    t1 = df_add(t1, v[u].z, v[u].w);
+                }
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < COMBINE_LANES; o <<= 1) {
+        const float h0 = __shfl_xor_sync(gmask, t0.hi, o), l0 = __shfl_xor_sync(gmask, t0.lo, o);
+        const float h1 = __shfl_xor_sync(gmask, t1.hi, o), l1 = __shfl_xor_sync(gmask, t1.lo, o);
+        t0 = df_add(t0, h0, l0);
+        t1 = df_add(t1, h1, l1);
+    }
+    if (!live || r != 0) return;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         if (k + h >= sy.N) break;
@@ -1160,42 +1183,60 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
     }
 }
 
-// One thread per (two consecutive bodies, component): the FP64 rows of a
-// mutual FP64 pass in the order of combine_mutual_kernel (16-byte loads, as
-// there), Neumaier-compensated.
+// The FP64 rows of a mutual FP64 pass, combined as in combine_mutual_kernel
+// (COMBINE_LANES lanes per two bodies and component, 16-byte loads, a fixed
+// tree), Neumaier-compensated.
 __global__ void combine_mutual64_kernel(const double *__restrict__ partial, const __grid_constant__ MutualPlan P,
                                         int Ntot, int npad, const uint32_t *__restrict__ perm, double tau,
                                         double *__restrict__ acc, double *__restrict__ vx, double *__restrict__ vy,
                                         double *__restrict__ vz, uint32_t *__restrict__ status) {
-    const int p = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = 2 * (gt / COMBINE_LANES), r = gt % COMBINE_LANES;
     const int c = blockIdx.y;
-    if (p >= npad) return;
-    MSys sy = P.sys[plan_system(P, p)];
-    if (P.nreal > 0) sy.N = P.nreal;
-    const int k = p - sy.poff;
-    if (k >= sy.N) return;
-    const int bl = (k / MG) / P.gpb;
-    const size_t stride = 3 * (size_t)sy.np / 2;  // double2 units
-    const double2 *pr = reinterpret_cast<const double2 *>(partial + sy.pbase) + ((size_t)c * sy.np + k) / 2;
-    const int2 bk = P.blk[sy.blk0 + bl];
-    const int n0 = bk.x, n1 = n0 + bk.y, n2 = n1 + bl;
-    CompS t0{0.0, 0.0}, t1{0.0, 0.0};
-    constexpr int BATCH = 16;
-    for (int r0 = 0; r0 < n2; r0 += BATCH) {
-        double2 v[BATCH];
-#pragma unroll
-        for (int u = 0; u < BATCH; u++) {
-            const int r = r0 + u;
-            const int rr = r < n0 ? r : r < n1 ? sy.S + (r - n0) : sy.irows + (r - n1);
-            v[u] = r < n2 ? pr[(size_t)rr * stride] : make_double2(0.0, 0.0);
-        }
-#pragma unroll
-        for (int u = 0; u < BATCH; u++)
-            if (r0 + u < n2) {
-                comp_add(t0, v[u].x);
-                comp_add(t1, v[u].y);
-            }
+    const unsigned gmask = 0xfu << (threadIdx.x & 28u);
+    MSys sy{};
+    int k = 0;
+    bool live = p < npad;
+    if (live) {
+        sy = P.sys[plan_system(P, p)];
+        if (P.nreal > 0) sy.N = P.nreal;
+        k = p - sy.poff;
+        live = k < sy.N;
     }
+    CompS t0{0.0, 0.0}, t1{0.0, 0.0};
+    if (live) {
+        const int bl = (k / MG) / P.gpb;
+        const size_t stride = 3 * (size_t)sy.np / 2;  // double2 units
+        const double2 *pr = reinterpret_cast<const double2 *>(partial + sy.pbase) + ((size_t)c * sy.np + k) / 2;
+        const int2 bk = P.blk[sy.blk0 + bl];
+        const int n0 = bk.x, n1 = n0 + bk.y, n2 = n1 + bl;
+        constexpr int BATCH = 8;
+        for (int r0 = r; r0 < n2; r0 += BATCH * COMBINE_LANES) {
+            double2 v[BATCH];
+#pragma unroll
+            for (int u = 0; u < BATCH; u++) {
+                const int rw = r0 + u * COMBINE_LANES;
+                const int rr = rw < n0 ? rw : rw < n1 ? sy.S + (rw - n0) : sy.irows + (rw - n1);
+                v[u] = rw < n2 ? pr[(size_t)rr * stride] : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int u = 0; u < BATCH; u++)
+                if (r0 + u * COMBINE_LANES < n2) {
+                    comp_add(t0, v[u].x);
+                    comp_add(t1, v[u].y);
+                }
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < COMBINE_LANES; o <<= 1) {
+        const double s0 = __shfl_xor_sync(gmask, t0.s, o), c0 = __shfl_xor_sync(gmask, t0.c, o);
+        const double s1 = __shfl_xor_sync(gmask, t1.s, o), c1 = __shfl_xor_sync(gmask, t1.c, o);
+        comp_add(t0, s0);
+        t0.c += c0;
+        comp_add(t1, s1);
+        t1.c += c1;
+    }
+    if (!live || r != 0) return;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         if (k + h >= sy.N) break;
@@ -1599,7 +1640,7 @@ cudaError_t launch_combine_mutual64(const double *partial, const MutualPlan &P, 
                                     double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
                                     cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    combine_mutual64_kernel<<<dim3((npad / 2 + 255) / 256, 3), 256, 0, s>>>(partial, P, N, npad, perm, tau, acc, vx,
+    combine_mutual64_kernel<<<dim3((npad / 2 * COMBINE_LANES + 255) / 256, 3), 256, 0, s>>>(partial, P, N, npad, perm, tau, acc, vx,
                                                                              vy, vz, status);
     return cudaGetLastError();
 }
@@ -1618,7 +1659,7 @@ cudaError_t launch_combine_mutual(const double *partial, const MutualPlan &P, in
                                   double tau, double *acc, double *vx, double *vy, double *vz, uint32_t *status,
                                   cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    combine_mutual_kernel<<<dim3((npad / 2 + 255) / 256, 3), 256, 0, s>>>(partial, P, N, npad, perm, tau, acc, vx,
+    combine_mutual_kernel<<<dim3((npad / 2 * COMBINE_LANES + 255) / 256, 3), 256, 0, s>>>(partial, P, N, npad, perm, tau, acc, vx,
                                                                            vy, vz, status);
     return cudaGetLastError();
 }
