@@ -13,7 +13,7 @@
 // of independent discs (a table of systems).
 //
 // Layout.  Bodies in the spatial (Morton) order, 64-body groups.  A CTA has
-// CW consumer warps, one producer warp and one reducer warp.  A CTA's
+// CW consumer warps, one producer warp and three reducer warps.  A CTA's
 // i-block is CW NP groups; consumer warp w holds NP of them in registers,
 // interleaved over the block (groups w, w + CW, w + 2 CW, ...: a j-group
 // next to one part of the block is then near one i-group of several warps,
@@ -24,10 +24,11 @@
 // it adds the pair's i-side terms to its own i-sums and the j-side terms to a
 // running j-sum that then moves one lane down (shuffle), so after 32 steps
 // every j-sum is back in the lane of its j-body, complete over the warp's
-// i-tile.  The reducer warp adds the CW warps' j-sums of a slot in warp order
-// (double-float) into the j-side partial row of the item's i-block, then
-// frees the slot; so every sum has a fixed order and results are bitwise
-// reproducible.
+// i-tile.  The reducer warps add the CW warps' j-sums of a slot in warp
+// order (double-float) into the j-side partial row of the item's i-block,
+// each a third of the (half, component) sums (so no scheduler of the SM
+// carries the whole reduction), then free the slot; so every sum has a
+// fixed order and results are bitwise reproducible.
 //
 // Work.  Items come from a table built on the host (plan_systems): the
 // diagonal items of each i-block (its own groups, one-sided: every warp takes
@@ -243,8 +244,11 @@ constexpr int mutual_maxreg(int warps) {
                                                                   : ((65536 / (((warps + 3) / 4) * 4 * 32)) / 8 * 8);
 }
 
-template <int NP, int CW, int STAGES, int UNR>
-__global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __grid_constant__ PassArgs a) {
+// NR reducer warps (warps CW + 1 ...): reducer r sums the (half, component)
+// j-sums r, r + NR, ... of a slot, so with NR = 3 the reduction is spread
+// over three of the SM's four schedulers instead of loading one.
+template <int NP, int CW, int STAGES, int UNR, int NR>
+__global__ void __maxnreg__(mutual_maxreg(CW + 1 + NR)) pass_mutual_kernel(const __grid_constant__ PassArgs a) {
     using L = MLayout<NP, CW, STAGES>;
     constexpr int BPT = L::BPT, NC = L::NC;
     constexpr int NEAR_UNR = NP <= 2 ? 2 : 1;  // NEAR-loop unroll (register budget)
@@ -274,7 +278,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
         for (int q = 0; q < STAGES; q++) {
             mbar_init(&full[q], 1);
             mbar_init(&pdone[q], CW);
-            mbar_init(&empty[q], 1);
+            mbar_init(&empty[q], NR);
         }
         fence_barrier_init();
         s_lead = 0u;
@@ -329,7 +333,8 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
         }
     }
 
-    if (warp == CW + 1) {  // ------------------------------------------ reducer
+    if (warp > CW) {  // --------------------------------------------- reducers
+        const int rw = NR == 1 ? 0 : warp - CW - 1;  // this reducer's share: (half, component) pairs rw, rw + NR, ...
         float2 *jrow = nullptr;    // NULL: a diagonal item (one-sided, no j-side sums)
         int jnp = 0, jpoff = 0;    // the j-row's length and first packed position
         for (unsigned n = 0;; n++) {
@@ -349,15 +354,12 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual_kernel(const __gr
             if (jrow && h.group >= 0) {
                 const float *sp = s_part + (size_t)slot * CW * 3 * MG;
 #pragma unroll
-                for (int half = 0; half < 2; half++) {
-                    const int jj = lane + 32 * half;
+                for (int hc = rw; hc < 6; hc += NR) {
+                    const int jj = lane + 32 * (hc / 3), c = hc % 3;
+                    DF t{0.f, 0.f};
 #pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        DF t{0.f, 0.f};
-#pragma unroll
-                        for (int w = 0; w < CW; w++) t = df_add(t, sp[(w * 3 + c) * MG + jj], 0.f);
-                        jrow[(size_t)c * jnp + (h.group * MG + jj - jpoff)] = make_float2(t.hi, t.lo);
-                    }
+                    for (int w = 0; w < CW; w++) t = df_add(t, sp[(w * 3 + c) * MG + jj], 0.f);
+                    jrow[(size_t)c * jnp + (h.group * MG + jj - jpoff)] = make_float2(t.hi, t.lo);
                 }
             }
             __syncwarp();
@@ -857,8 +859,8 @@ struct M64Layout {
     static_assert(bytes <= 227 * 1024, "one CTA per SM: at most 227 KB of shared memory");
 };
 
-template <int BPT, int CW, int STAGES>
-__global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __grid_constant__ PassArgs a) {
+template <int BPT, int CW, int STAGES, int NR>
+__global__ void __maxnreg__(mutual_maxreg(CW + 1 + NR)) pass_mutual64_kernel(const __grid_constant__ PassArgs a) {
     using L = M64Layout<BPT, CW, STAGES>;
     constexpr int NC = L::NC, NPG = L::NPG;
     constexpr uint32_t STAGE_BYTES = MG * 32 + 2 * 16;
@@ -884,7 +886,7 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
         for (int q = 0; q < STAGES; q++) {
             mbar_init(&full[q], 1);
             mbar_init(&pdone[q], CW);
-            mbar_init(&empty[q], 1);
+            mbar_init(&empty[q], NR);
         }
         fence_barrier_init();
         s_lead = 0u;
@@ -937,7 +939,8 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
         }
     }
 
-    if (warp == CW + 1) {  // ------------------------------------------ reducer
+    if (warp > CW) {  // --------------------------------------------- reducers
+        const int rw = NR == 1 ? 0 : warp - CW - 1;  // (half, component) pairs rw, rw + NR, ... as in the FP32 pass
         double *jrow = nullptr;
         int jnp = 0, jpoff = 0;
         for (unsigned n = 0;; n++) {
@@ -957,15 +960,12 @@ __global__ void __maxnreg__(mutual_maxreg(CW + 2)) pass_mutual64_kernel(const __
             if (jrow && h.group >= 0) {
                 const double *sp = s_part + (size_t)slot * CW * 3 * MG;
 #pragma unroll
-                for (int half = 0; half < 2; half++) {
-                    const int jj = lane + 32 * half;
+                for (int hc = rw; hc < 6; hc += NR) {
+                    const int jj = lane + 32 * (hc / 3), c = hc % 3;
+                    CompS t{0.0, 0.0};
 #pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        CompS t{0.0, 0.0};
-#pragma unroll
-                        for (int w = 0; w < CW; w++) comp_add(t, sp[(w * 3 + c) * MG + jj]);
-                        jrow[(size_t)c * jnp + (h.group * MG + jj - jpoff)] = t.s + t.c;
-                    }
+                    for (int w = 0; w < CW; w++) comp_add(t, sp[(w * 3 + c) * MG + jj]);
+                    jrow[(size_t)c * jnp + (h.group * MG + jj - jpoff)] = t.s + t.c;
                 }
             }
             __syncwarp();
@@ -1254,24 +1254,27 @@ __global__ void combine_mutual64_kernel(const double *__restrict__ partial, cons
 
 // --------------------------------------------------------------- variants
 struct MVariant {
-    int np, cw;
+    int np, cw, nr;
     void (*fn)(const PassArgs);
     size_t smem;
 };
-#define GENGA_MV(NP, CW, ST, UNR) \
-    {NP, CW, pass_mutual_kernel<NP, CW, ST, UNR>, MLayout<NP, CW, ST>::bytes}
-const MVariant kMVariants[] = {GENGA_MV(2, 12, 4, 8), GENGA_MV(2, 12, 8, 4), GENGA_MV(2, 12, 8, 8), GENGA_MV(4, 8, 6, 4)};
+#define GENGA_MV(NP, CW, ST, UNR, NR) \
+    {NP, CW, NR, pass_mutual_kernel<NP, CW, ST, UNR, NR>, MLayout<NP, CW, ST>::bytes}
+// three reducer warps in every shape (one reducer: 0.562 against 0.552 ms
+// for the (2, 12, 4, 8) pass at 40k)
+const MVariant kMVariants[] = {GENGA_MV(2, 12, 4, 8, 3), GENGA_MV(2, 12, 8, 4, 3), GENGA_MV(2, 12, 8, 8, 3),
+                               GENGA_MV(4, 8, 6, 4, 3)};
 #undef GENGA_MV
 constexpr int kNumMVariants = sizeof(kMVariants) / sizeof(kMVariants[0]);
 
 struct M64Variant {
-    int bpt, cw;
+    int bpt, cw, nr;
     void (*fn)(const PassArgs);
     size_t smem;
 };
-#define GENGA_M64(BPT, CW, ST) \
-    {BPT, CW, pass_mutual64_kernel<BPT, CW, ST>, M64Layout<BPT, CW, ST>::bytes}
-const M64Variant kM64Variants[] = {GENGA_M64(4, 8, 4), GENGA_M64(8, 4, 4), GENGA_M64(2, 12, 4)};
+#define GENGA_M64(BPT, CW, ST, NR) \
+    {BPT, CW, NR, pass_mutual64_kernel<BPT, CW, ST, NR>, M64Layout<BPT, CW, ST>::bytes}
+const M64Variant kM64Variants[] = {GENGA_M64(4, 8, 4, 3), GENGA_M64(8, 4, 4, 3), GENGA_M64(2, 12, 4, 3)};
 #undef GENGA_M64
 constexpr int kNumM64Variants = sizeof(kM64Variants) / sizeof(kM64Variants[0]);
 static_assert(kNumMVariants + kNumM64Variants <= GENGA_MAX_VARIANTS, "plan cache slots");
@@ -1632,7 +1635,7 @@ cudaError_t launch_pass_mutual64(const PassArgs &a0, int v, int sm_count, cudaSt
     cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     const int grid = std::min(sm_count, a.mp.items);
-    mv.fn<<<grid, (mv.cw + 2) * 32, mv.smem, s>>>(a);
+    mv.fn<<<grid, (mv.cw + 1 + mv.nr) * 32, mv.smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1651,7 +1654,7 @@ cudaError_t launch_pass_mutual(const PassArgs &a0, int v, int sm_count, cudaStre
     cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     const int grid = std::min(sm_count, a.mp.items);
-    mv.fn<<<grid, (mv.cw + 2) * 32, mv.smem, s>>>(a);
+    mv.fn<<<grid, (mv.cw + 1 + mv.nr) * 32, mv.smem, s>>>(a);
     return cudaGetLastError();
 }
 
