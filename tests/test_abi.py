@@ -28,6 +28,16 @@ def declared_functions():
     return sorted(set(names))
 
 
+def test_build_can_be_called_again(lib):
+    """build() stays the package's function after it has run (its compiler
+    driver is a submodule of another name), so a process may call it twice,
+    as the build step followed by the smoke test does."""
+    import paper_2309_08217_gb300 as g
+    assert callable(g.build)
+    assert g.build() == g.build()
+    assert callable(g.build)
+
+
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("genga_create", "genga_destroy", "genga_kick", "genga_drift", "genga_encounters",
